@@ -1,0 +1,105 @@
+"""Seeded synthetic workloads shared by the CUDA path's tests/bench and the oracle.
+
+This module holds only workload descriptions and random draws: model
+parameters, grid sizes, bond lists (lattice geometry the caller chooses) and
+seeded random states.  It contains none of the method's arithmetic (no
+dispersion, form factor, loop, projection or flow formula), so that the oracle
+and the CUDA path can both take their inputs from here without sharing code.
+
+All inputs are analytic model inputs of the t-t' Hubbard model on the square
+lattice (Sec. 4 of the paper); no dataset is involved.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Bond vectors of the square lattice grouped into shells of equal length
+# (onsite, 1st NN, 2nd NN, ...).  "Truncation at the n-th nearest neighbour"
+# (Sec. 3) keeps shells 0..n.  Within a shell the order is fixed so that both
+# implementations enumerate bonds identically.
+SHELLS = [
+    [(0, 0)],
+    [(1, 0), (0, 1), (-1, 0), (0, -1)],
+    [(1, 1), (-1, 1), (-1, -1), (1, -1)],
+    [(2, 0), (0, 2), (-2, 0), (0, -2)],
+    [(2, 1), (1, 2), (-1, 2), (-2, 1), (-2, -1), (-1, -2), (1, -2), (2, -1)],
+    [(2, 2), (-2, 2), (-2, -2), (2, -2)],
+    [(3, 0), (0, 3), (-3, 0), (0, -3)],
+]
+
+
+def bonds_for_shells(n_shells: int) -> np.ndarray:
+    """Bond list (int32 [n][2]) of all shells 0..n_shells (complete shells)."""
+    out = []
+    for s in range(n_shells + 1):
+        out.extend(SHELLS[s])
+    return np.asarray(out, dtype=np.int32)
+
+
+def n_ff_for_shells(n_shells: int) -> int:
+    return sum(len(SHELLS[s]) for s in range(n_shells + 1))
+
+
+# Workloads on which the flow is run (t in units of 1; energies in units of t).
+# cfg1: small case the oracle finishes in seconds.
+# cfg2: production size (three t' values, van Hove filling mu = 4 t').
+# cfg5: large scale.
+CONFIGS = {
+    "cfg1": dict(t=1.0, tp=-0.25, mu=-1.0, U=3.0, shells=1, nc=8, nf=96,
+                 lambda0=10.0, lambda_min=1e-3, threshold=50.0),
+    "cfg2": dict(t=1.0, tp=-0.25, mu=-1.0, U=3.0, shells=3, nc=24, nf=480,
+                 lambda0=10.0, lambda_min=1e-3, threshold=50.0),
+    "cfg5": dict(t=1.0, tp=-0.3, mu=-1.2, U=3.5, shells=5, nc=48, nf=960,
+                 lambda0=10.0, lambda_min=1e-3, threshold=50.0),
+}
+CFG2_TPRIME = (-0.1, -0.25, -0.35)
+
+
+def config(name: str, **over) -> dict:
+    c = dict(CONFIGS[name])
+    c.update(over)
+    return c
+
+
+def random_state(seed: int, nl: int, nff: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded random coupling state y = (P, C, D) as float64 [3][nl][nff][nff].
+
+    Each matrix is symmetric in (m, n), as exchange propagators are.
+    """
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((3, nl, nff, nff)) * scale
+    return 0.5 * (a + np.swapaxes(a, -1, -2))
+
+
+def random_scalars(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=n)
+
+
+# Batched phase-diagram scan: seeded draws of (t', U, density) and grid sizes.
+BATCH_SEED = 1604062960
+BATCH_NC = (16, 20, 24, 30, 32)
+BATCH_SHELLS = (1, 2, 3, 4)          # Nff = 5, 9, 13, 21
+BATCH_NF = (240, 320, 384, 480)
+
+
+def batch_points(n: int, seed: int = BATCH_SEED) -> list[dict]:
+    """n seeded phase-diagram points with uneven grids and form-factor counts.
+
+    t' ~ U[-0.45, 0], U ~ U[2, 4], density ~ U[0.6, 1.0]; (nc, nf) drawn
+    uniformly from the pairs with nf % (2 nc) == 0 and nf % 4 == 0, so that
+    l/2 +- p stays on the fine grid.
+    """
+    rng = np.random.default_rng(seed)
+    pairs = [(nc, nf) for nc in BATCH_NC for nf in BATCH_NF
+             if nf % (2 * nc) == 0 and nf % 4 == 0]
+    pts = []
+    for _ in range(n):
+        tp = float(rng.uniform(-0.45, 0.0))
+        U = float(rng.uniform(2.0, 4.0))
+        dens = float(rng.uniform(0.6, 1.0))
+        nc, nf = pairs[int(rng.integers(len(pairs)))]
+        shells = int(BATCH_SHELLS[int(rng.integers(len(BATCH_SHELLS)))])
+        pts.append(dict(t=1.0, tp=tp, U=U, density=dens, nc=nc, nf=nf,
+                        shells=shells))
+    return pts
