@@ -1,0 +1,393 @@
+"""Benchmark of the TUfRG Lambda-flow right-hand side on GB300.
+
+A step is one adaptive Dormand-Prince step of the flow (six right-hand-side
+evaluations -- per-scale tables, loop contraction, projections, products --
+plus the stage combinations, error norm, step control and accept), run by
+tufrg_flow_step on the production workload (t-t' Hubbard, t' = -0.25,
+mu = 4t', U = 3, coarse 24x24, Nff = 13, fine 480x480) starting at
+Lambda0 = 10 from the bare interaction.  value = right-hand-side evaluations
+per second over exactly K timed steps (CUDA events per step on the calling
+stream; L2 flushed between steps).  Under torchrun every rank runs its own
+phase-diagram point (independent problems, no collective): weak scaling.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "fRG RHS evals/s & flow time to Λ_c (mixed/learned vs FP64 GPU, same acc.)"
+UNIT = "RHS evals/s"
+WORKLOAD = "cfg2"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_desc(tp):
+    c = W.config(WORKLOAD)
+    return (f"t-t' Hubbard square lattice, t'={tp}, mu=4t', U={c['U']}; coarse "
+            f"{c['nc']}x{c['nc']} ({c['nc'] ** 2} l), Nff={W.n_ff_for_shells(c['shells'])} "
+            f"(bonds <= 2), fine {c['nf']}x{c['nf']}; DoPri5 steps from Lambda0={c['lambda0']}")
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "MEASURED_PEAKS.json"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def fp64_peak_tflops(torch):
+    """Measured FP64 rate of this GPU: best of 3 cuBLAS DGEMM 4096^3 (CUDA events)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 2 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def profile_traffic(kernel_file, profile_name):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current source of the kernel (sha256 recorded in the summary)."""
+    path = os.path.join(ROOT, "profiles", profile_name)
+    src = os.path.join(ROOT, "paper_1604_06296_gb300", "csrc", kernel_file)
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+def cpu_oracle_rhs_sample(tp, l_sample=48):
+    """One FP64 oracle right-hand side at the workload, loops on l_sample of
+    the Nl points (scaled to all Nl), projections and products on all l."""
+    from oracle import loops, projections, rhs
+    from oracle.model import Problem
+    c = W.config(WORKLOAD)
+    p = Problem(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"], c["nc"],
+                c["nf"], c["nf"]).check()
+    y = W.random_state(0, p.nl, p.nff, 0.1)
+    sel = np.linspace(0, p.nl - 1, l_sample).astype(int)
+    t0 = time.perf_counter()
+    chi = loops.chi_dot(p, 0.5, sel)
+    t_loops = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    V = projections.project(p, y)
+    t_proj = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rhs.products(V[:, sel], *chi)
+    t_prod = time.perf_counter() - t0
+    scale = p.nl / l_sample
+    est = t_loops * scale + t_proj + t_prod * scale
+    sample = (f"oracle RHS at the workload: loops on {l_sample} of {p.nl} l "
+              f"(x{scale:g}), projections on all l, products on the sampled l (x{scale:g})")
+    return est, sample
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return 0
+    tp = W.CFG2_TPRIME[1]
+    for _ in range(args.warmup):
+        cpu_oracle_rhs_sample(tp, l_sample=24)
+    times = []
+    sample = ""
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        est, sample = cpu_oracle_rhs_sample(tp, l_sample=24)
+        times.append(est)
+    wall = time.perf_counter() - t_wall
+    value = len(times) / sum(times)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_desc(tp), "precision": "fp64 (CPU oracle)"},
+           "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT,
+                            "cores": os.cpu_count(), "sample": sample + "; one RHS per step",
+                            "wall_s": wall},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "3xtf32", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-flow-time", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+
+    c = W.config(WORKLOAD)
+    tp = W.CFG2_TPRIME[(1 + rank) % len(W.CFG2_TPRIME)]
+    solver = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"],
+                          c["nf"], precision=args.precision)
+    flow_kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
+                   rtol=1e-8, atol=1e-10, h0=0.05)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    solver.flow_init(**flow_kw)
+    for _ in range(args.warmup):
+        r = solver.flow_step(1)
+        if r["finished"]:
+            solver.flow_init(**flow_kw)
+    torch.cuda.synchronize()
+
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    step_ms, rhs_count = [], 0
+    prev = solver.flow_step(0)["n_rhs"]
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = solver.flow_step(1)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        rhs_count += r["n_rhs"] - prev
+        prev = r["n_rhs"]
+        if r["finished"]:
+            solver.flow_init(**flow_kw)
+            prev = solver.flow_step(0)["n_rhs"]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+
+    device_s = sum(step_ms) / 1e3
+    if pg:
+        t = torch.tensor([device_s, float(rhs_count)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        device_s_max, total_rhs = float(tmax[0]), float(t[1])
+    else:
+        device_s_max, total_rhs = device_s, float(rhs_count)
+    value = total_rhs / device_s_max
+
+    # dominant kernel: the loop contraction, timed alone on the launching stream
+    peaks, peak_src = measured_peaks()
+    f64_peak = fp64_peak_tflops(torch)
+    chi = solver.empty(2)
+    kms = []
+    for _ in range(max(3, args.steps)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        solver.loops(0.5, out=chi)
+        e1.record()
+        e1.synchronize()
+        kms.append(e0.elapsed_time(e1))
+    k_ms = statistics.median(kms)
+    p = solver.params
+    nf = p.nf_x * p.nf_y
+    kdim = p.nf_x * (p.nf_y // 2 - 1) + 2 * (p.nf_x // 2 + 1)
+    k = np.array([0.3, -1.1]), np.array([0.7, 0.4])
+    par = np.sign(tufrg.tufrg_eval_formfactors(solver._bonds, -k[0], -k[1])[:, 0]
+                  * tufrg.tufrg_eval_formfactors(solver._bonds, k[0], k[1])[:, 0])
+    npair = int(sum(1 for m in range(solver.nff) for n in range(m, solver.nff)
+                    if par[m] * par[n] > 0))
+    flops = 2.0 * 2 * npair * kdim * solver.nl        # 2 channels, FMA = 2 flop
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": f64_peak, "unit": "TFLOP/s",
+                "frac": achieved / f64_peak, "traffic": profile_traffic(
+                    "loops_fp64.cu", "loops_fp64_cfg2.txt"),
+                "kernel": "loops_fp64_kernel (+ per-scale table, split-K reduce)",
+                "kernel_ms": k_ms, "algorithmic_flop_per_launch": flops,
+                "peak_source": "FP64: cuBLAS DGEMM 4096^3 measured in this run (of measured)"}
+
+    # end to end through the C ABI with host buffers: H2D state, RHS, D2H result
+    y_host = torch.from_numpy(W.random_state(1, solver.nl, solver.nff, 0.1)).pin_memory()
+    dy_host = torch.empty_like(y_host).pin_memory()
+    y_dev, dy_dev = solver.empty(3), solver.empty(3)
+    for _ in range(2):
+        y_dev.copy_(y_host, non_blocking=True)
+        solver.rhs(0.5, y_dev, out=dy_dev)
+        dy_host.copy_(dy_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    ems = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        y_dev.copy_(y_host, non_blocking=True)
+        solver.rhs(0.5, y_dev, out=dy_dev)
+        dy_host.copy_(dy_dev, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        ems.append(e0.elapsed_time(e1))
+    e2e = {"value": world * len(ems) / (sum(ems) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": y_host.numel() * 8, "d2h_bytes_per_step": dy_host.numel() * 8,
+           "call": "tufrg_rhs with pinned host copies in/out"}
+
+    flow_info = None
+    if not args.no_flow_time:
+        y0 = solver.zeros(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, res, _ = solver.flow(y0, **flow_kw)
+        e1.record()
+        e1.synchronize()
+        flow_info = {"flow_time_to_lambda_c_s": e0.elapsed_time(e1) / 1e3,
+                     "lambda_c": res["lambda_c"], "diverged": res["diverged"],
+                     "kind": res["kind"], "l_index": res["l_index"], "m": res["m"],
+                     "n": res["n"], "rhs_evals": res["n_rhs"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, sample = cpu_oracle_rhs_sample(tp)
+        cpu = {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample}
+
+    # kernels of the library per timed step: 6 stages x (combination, per-scale
+    # table, loop contraction, split-K reduce, to_bond, dft_keys, contract,
+    # products) + error + control + accept
+    launches_per_step = 6 * 8 + 3
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": workload_desc(tp), "precision": args.precision,
+                          "step": "one DoPri5 step (6 RHS evaluations + stage/error/control)",
+                          "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                          "parallelism": f"{world} independent phase-diagram points"
+                                         if world > 1 else "single point"},
+               "rhs_evals_timed": total_rhs, "wall_s": wall,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+               "flow": flow_info, "peaks_source": peak_src}
+        print(json.dumps(out))
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

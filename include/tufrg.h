@@ -1,0 +1,219 @@
+/*
+ * tufrg.h -- C ABI of the GB300 TUfRG right-hand-side library.
+ *
+ * The library computes the right-hand side of the Lambda-flow of the
+ * truncated-unity fRG (Lichtenstein et al., arXiv:1604.06296) for the
+ * exchange propagators P, C, D of the t-t' Hubbard model on the square
+ * lattice in a bond form-factor basis, and integrates that flow.
+ *
+ * Conventions shared by every call
+ *  - Energies are in units of the hopping t (any t > 0 is accepted).
+ *  - Momentum grids: n points per direction at k_i = -pi + 2 pi i / n.
+ *    The coarse (bosonic, "l") grid has Nl = nc_x * nc_y points, index
+ *    l = ix * nc_y + iy.  The fine loop grid has nf_x * nf_y points.
+ *  - Form factors: the library builds Nff real orthonormal C4v-adapted
+ *    functions from the bond list (Sec. 3).  Their order is canonical:
+ *    shell by shell; within a shell A1, then B1/B2/A2, then E pairs
+ *    (x-like, y-like), in the order
+ *      shell 0: 1
+ *      shell 1: cx+cy, cx-cy, r2 sx, r2 sy
+ *      shell 2: 2cxcy, 2sxsy, 2sxcy, 2cxsy
+ *      shell 3: c2x+c2y, c2x-c2y, r2 s2x, r2 s2y
+ *      shell 4: r2(c2x cy+cx c2y), r2(c2x cy-cx c2y), r2(s2x sy+sx s2y),
+ *               r2(s2x sy-sx s2y), 2 s2x cy, 2 cx s2y, 2 sx c2y, 2 c2x sy
+ *      shell 5: 2c2xc2y, 2s2xs2y, 2s2xc2y, 2c2xs2y
+ *      shell 6: c3x+c3y, c3x-c3y, r2 s3x, r2 s3y
+ *    (c = cos, s = sin, r2 = sqrt 2, arguments k_x, k_y).
+ *  - State layout: y = (P, C, D) as double [3][Nl][Nff][Nff], row-major.
+ *    Loops: double [2][Nl][Nff][Nff] (pp, ph).  Projected couplings:
+ *    double [3][Nl][Nff][Nff] (V^P, V^C, V^D).
+ *  - Pointers named *_dev are device pointers owned by the caller (e.g.
+ *    allocated by torch); the library never frees them.  Host pointers are
+ *    read during the call only.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  All
+ *    device work of a call is ordered on that stream; calls return once the
+ *    work is enqueued, except tufrg_flow (returns when the flow finished).
+ *  - Every call returns a tufrg_status and never aborts the process.  An
+ *    invalid argument returns TUFRG_ERR_ARG before any device work.  A CUDA
+ *    error returns TUFRG_ERR_CUDA; errors of asynchronous work can surface
+ *    at a later call on the same stream.
+ *  - Readings of the paper the results depend on: the Omega-cutoff
+ *    propagator G = k0^2/(k0^2 + Omega^2) / (i k0 - xi_k) at T = 0 with the
+ *    frequency integral done in closed form; loops at bosonic frequency 0;
+ *    every bosonic momentum is folded into [-pi, pi)^2 and the half momenta
+ *    l/2 are formed from that representative; the k, k' integrals of the
+ *    projections are averages over the coarse grid; V0 = U on site.
+ */
+#ifndef TUFRG_H
+#define TUFRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tufrg_ctx tufrg_ctx;
+
+typedef enum {
+  TUFRG_OK = 0,
+  TUFRG_ERR_ARG = -1,            /* invalid argument or unsupported size */
+  TUFRG_ERR_CUDA = -2,           /* a CUDA runtime call or launch failed */
+  TUFRG_ERR_NONFINITE = -3,      /* NaN/Inf in the state during a flow */
+  TUFRG_ERR_STEP_UNDERFLOW = -4, /* adaptive step fell below 1e-12 in ln Lambda */
+  TUFRG_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
+  TUFRG_ERR_OOM = -6,            /* device allocation failed */
+  TUFRG_ERR_STATE = -7           /* call out of order (e.g. a step before tufrg_flow_init) */
+} tufrg_status;
+
+typedef enum {
+  TUFRG_FP64 = 0,    /* loops in FP64 (DFMA) */
+  TUFRG_3XTF32 = 1,  /* loops on tcgen05, kind::tf32, hi/lo split, 3 products */
+  TUFRG_BF16X3 = 2   /* loops on tcgen05, kind::f16 (bf16), hi/lo split, 3 products */
+} tufrg_precision;
+
+typedef enum {
+  TUFRG_DOPRI5 = 0,  /* adaptive Dormand-Prince 5(4) in s = ln Lambda */
+  TUFRG_RK4 = 1      /* classic RK4, fixed step h0 in s = ln Lambda */
+} tufrg_method;
+
+/* Model and discretisation of one phase-diagram point. */
+typedef struct {
+  int32_t lattice;        /* 0 = square lattice (the only one supported) */
+  double t, tp, mu, U;    /* hoppings t, t' (Eq. hubb-disp), chemical potential,
+                             on-site U (bare V0 = U) */
+  int32_t n_bonds;        /* bond list: lattice vectors (x, y), host memory */
+  const int32_t* bonds;   /* [n_bonds][2]; must be complete shells 0..n, n <= 6 */
+  int32_t nc_x, nc_y;     /* coarse grid; even, >= 2*max|R|+1 */
+  int32_t nf_x, nf_y;     /* fine grid; nf % (2 nc) == 0 and nf % 4 == 0 */
+  int32_t precision;      /* tufrg_precision of the loop contraction */
+  int32_t feedback;       /* 1 = full inter-channel projections (Eqs. proj_VP..VD);
+                             0 = projections off: V^P = V0 - P, V^C = V0 + C,
+                             V^D = V0 + D (single-channel ladders) */
+} tufrg_params;
+
+/* Options of tufrg_flow. */
+typedef struct {
+  double lambda0;         /* initial scale (> lambda_min) */
+  double lambda_min;      /* final scale if no divergence */
+  double threshold;       /* stop when max |B_mn(l)|, B in {P,C,D}, exceeds it */
+  double rtol, atol;      /* DoPri5 error control (max norm) */
+  double h0;              /* initial (DoPri5) or fixed (RK4) step |h| in ln Lambda */
+  int32_t method;         /* tufrg_method */
+  int32_t max_steps;      /* tufrg_flow: step budget (accepted + rejected attempts) */
+  int32_t n_checkpoints;  /* dense output at these scales (host array, any order) */
+  const double* checkpoints;
+  double* checkpoint_states_dev; /* [n_checkpoints][3][Nl][Nff][Nff]; entries of
+                                    scales not reached are left untouched; must stay
+                                    valid until the flow has finished */
+} tufrg_flow_opts;
+
+/* Result of tufrg_flow / tufrg_flow_step / tufrg_flow_state. */
+typedef struct {
+  double lambda_c;        /* critical scale if diverged, else the scale reached */
+  double h_next;          /* size |h| in ln Lambda of the next step attempt */
+  int32_t diverged;       /* 1 if the threshold was crossed */
+  int32_t finished;       /* 1 if diverged or Lambda_min was reached */
+  int32_t channel;        /* 0 = P (pairing), 1 = C (magnetic), 2 = D (charge) */
+  int32_t l_index, m, n;  /* location of max |B| in the state (smallest flat index);
+                             filled by tufrg_flow and tufrg_flow_state */
+  double max_abs;         /* max |B| of the state (tufrg_flow, tufrg_flow_state) */
+  int64_t n_rhs, n_accepted, n_rejected;
+} tufrg_result;
+
+/* Sec. 2-4: build the problem (bond basis, grids, dispersion table,
+ * scale-independent projection tables, workspace) on the current device.
+ * Returns TUFRG_ERR_ARG for an unsupported lattice, incomplete shells, bad
+ * grid sizes or precision.  *out receives a context owned by the caller and
+ * released by tufrg_destroy.  Blocks until the tables are on the device. */
+tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** out);
+
+/* Releases all device and host memory of the context (synchronises). */
+void tufrg_destroy(tufrg_ctx* ctx);
+
+/* Sizes: Nl, Nff and the number of bonds.  Any pointer may be NULL. */
+tufrg_status tufrg_dims(const tufrg_ctx* ctx, int32_t* nl, int32_t* nff, int32_t* nb);
+
+/* Host evaluation of the form factors that tufrg_setup builds from this
+ * bond list (Sec. 3, footnote): out[m * n + i] = f_m(kx[i], ky[i]) for
+ * m < Nff (*nff_out receives Nff; out may be NULL to query it).  Host memory
+ * only; no device work.  TUFRG_ERR_ARG for an invalid bond list. */
+tufrg_status tufrg_eval_formfactors(int32_t n_bonds, const int32_t* bonds, int32_t n,
+                                    const double* kx, const double* ky, double* out,
+                                    int32_t* nff_out);
+
+/* Step ii, Eq. (chis): scale derivatives of the form-factor projected loops,
+ *   chi_dot^pp_mn(l) = d/dLambda (1/Nf) sum_p int dp0/2pi G(l/2+p) G(l/2-p) f_m f_n,
+ *   chi_dot^ph_mn(l) = d/dLambda (1/Nf) sum_p int dp0/2pi G(p+l/2) G(p-l/2) f_m f_n,
+ * with the Omega-cutoff propagator at T = 0 and Lambda = Omega > 0, in the
+ * context's precision.  chi_dot_dev: [2][Nl][Nff][Nff] (pp, ph). */
+tufrg_status tufrg_loops(tufrg_ctx* ctx, double lambda, double* chi_dot_dev,
+                         void* cuda_stream);
+
+/* Step i, Eqs. (proj_VP/VC/VD): projected couplings V^P, V^C, V^D from the
+ * state y = (P, C, D) and the bare U (honours the feedback flag).
+ * y_dev: [3][Nl][Nff][Nff]; v_dev: [3][Nl][Nff][Nff]; may not alias. */
+tufrg_status tufrg_project(tufrg_ctx* ctx, const double* y_dev, double* v_dev,
+                           void* cuda_stream);
+
+/* Step iii, Eqs. (matmul-P/C/D), per l:
+ *   dP = V^P chi^pp V^P, dC = -V^C chi^ph V^C,
+ *   dD = 2 V^D chi^ph V^D - V^C chi^ph V^D - V^D chi^ph V^C.
+ * v_dev: [3][Nl][Nff][Nff]; chi_dot_dev: [2][Nl][Nff][Nff];
+ * dy_dev: [3][Nl][Nff][Nff] (may not alias the inputs). */
+tufrg_status tufrg_products(tufrg_ctx* ctx, const double* v_dev, const double* chi_dot_dev,
+                            double* dy_dev, void* cuda_stream);
+
+/* Steps i-iii: dy/dLambda at scale lambda.  y_dev, dy_dev: [3][Nl][Nff][Nff];
+ * may not alias.  Uses the context's workspace: calls on one context must be
+ * stream-ordered (not concurrent). */
+tufrg_status tufrg_rhs(tufrg_ctx* ctx, double lambda, const double* y_dev, double* dy_dev,
+                       void* cuda_stream);
+
+/* Sec. 3/4: integrates the flow in s = ln Lambda from opts->lambda0 down to
+ * opts->lambda_min, or until max |B| exceeds opts->threshold; the critical
+ * scale is then located on the cubic Hermite dense output by bisection and
+ * the state is returned there, with the classification of its largest
+ * element.  y_dev: in = initial state (zeros: bare U), out = final state.
+ * Equivalent to tufrg_flow_init + tufrg_flow_step(max_steps) +
+ * tufrg_flow_state.  Running out of max_steps is not an error: the result
+ * then has finished = 0 and the flow can be resumed (lambda0 = lambda_c,
+ * h0 = h_next).  Blocks until done. */
+tufrg_status tufrg_flow(tufrg_ctx* ctx, const tufrg_flow_opts* opts, double* y_dev,
+                        tufrg_result* res, void* cuda_stream);
+
+/* Stepwise flow (resume, external control, timing of single steps).  The
+ * integrator state lives in the context (one flow per context at a time).
+ * tufrg_flow_init copies y0_dev, takes the options (checkpoint scales are
+ * copied; checkpoint_states_dev is kept) and evaluates the first stage
+ * (one right-hand side).  Blocks until done. */
+tufrg_status tufrg_flow_init(tufrg_ctx* ctx, const tufrg_flow_opts* opts, const double* y0_dev,
+                             void* cuda_stream);
+
+/* Performs up to n_steps step attempts (DoPri5: accepted or rejected, 6
+ * right-hand sides each; RK4: n_steps steps of 4), stopping early when the
+ * flow finishes; a threshold crossing is resolved (Lambda_c and the state
+ * there) inside the step that crosses it.  res (may be NULL) receives the
+ * progress (classification fields are not filled).  Blocks until done. */
+tufrg_status tufrg_flow_step(tufrg_ctx* ctx, int32_t n_steps, tufrg_result* res,
+                             void* cuda_stream);
+
+/* Copies the integrator's current state (at Lambda_c after a divergence)
+ * into y_dev ([3][Nl][Nff][Nff], may be NULL) and fills res including the
+ * classification of the largest element.  Blocks until done. */
+tufrg_status tufrg_flow_state(tufrg_ctx* ctx, double* y_dev, tufrg_result* res,
+                              void* cuda_stream);
+
+/* Chemical potential for filling n (particles per site, both spins):
+ * bisection on n(mu) = (2/Nf) sum_k [eps0_k < mu] (ties count 1/2) over the
+ * nf_x x nf_y grid.  Host computation. */
+tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x,
+                                  int32_t nf_y, double* mu_out);
+
+const char* tufrg_status_string(tufrg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUFRG_H */

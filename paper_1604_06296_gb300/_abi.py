@@ -1,0 +1,188 @@
+"""ctypes binding of include/tufrg.h (argument marshalling only).
+
+Every function has the C name and takes plain numbers and pointers; device
+pointers are passed as integers (e.g. torch.Tensor.data_ptr()), streams as
+the integer value of a cudaStream_t.  A non-zero status raises TufrgError.
+The library must have been built (paper_1604_06296_gb300.build); there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_double, c_int32, c_int64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtufrg.so")
+
+TUFRG_FP64, TUFRG_3XTF32, TUFRG_BF16X3 = 0, 1, 2
+TUFRG_DOPRI5, TUFRG_RK4 = 0, 1
+STATUS = {0: "TUFRG_OK", -1: "TUFRG_ERR_ARG", -2: "TUFRG_ERR_CUDA", -3: "TUFRG_ERR_NONFINITE",
+          -4: "TUFRG_ERR_STEP_UNDERFLOW", -5: "TUFRG_ERR_TIMEOUT", -6: "TUFRG_ERR_OOM",
+          -7: "TUFRG_ERR_STATE"}
+
+
+class TufrgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class tufrg_params(Structure):
+    _fields_ = [("lattice", c_int32), ("t", c_double), ("tp", c_double), ("mu", c_double),
+                ("U", c_double), ("n_bonds", c_int32), ("bonds", POINTER(c_int32)),
+                ("nc_x", c_int32), ("nc_y", c_int32), ("nf_x", c_int32), ("nf_y", c_int32),
+                ("precision", c_int32), ("feedback", c_int32)]
+
+
+class tufrg_flow_opts(Structure):
+    _fields_ = [("lambda0", c_double), ("lambda_min", c_double), ("threshold", c_double),
+                ("rtol", c_double), ("atol", c_double), ("h0", c_double),
+                ("method", c_int32), ("max_steps", c_int32), ("n_checkpoints", c_int32),
+                ("checkpoints", POINTER(c_double)), ("checkpoint_states_dev", c_void_p)]
+
+
+class tufrg_result(Structure):
+    _fields_ = [("lambda_c", c_double), ("h_next", c_double), ("diverged", c_int32),
+                ("finished", c_int32), ("channel", c_int32), ("l_index", c_int32),
+                ("m", c_int32), ("n", c_int32), ("max_abs", c_double),
+                ("n_rhs", c_int64), ("n_accepted", c_int64), ("n_rejected", c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+# name -> (argtypes, restype); restype c_int32 means a tufrg_status to check
+SIGNATURES = {
+    "tufrg_setup": ([POINTER(tufrg_params), c_void_p, POINTER(c_void_p)], c_int32),
+    "tufrg_destroy": ([c_void_p], None),
+    "tufrg_dims": ([c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)], c_int32),
+    "tufrg_eval_formfactors": ([c_int32, POINTER(c_int32), c_int32, POINTER(c_double),
+                                POINTER(c_double), POINTER(c_double), POINTER(c_int32)],
+                               c_int32),
+    "tufrg_loops": ([c_void_p, c_double, c_void_p, c_void_p], c_int32),
+    "tufrg_project": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "tufrg_products": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "tufrg_rhs": ([c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
+    "tufrg_flow": ([c_void_p, POINTER(tufrg_flow_opts), c_void_p, POINTER(tufrg_result),
+                    c_void_p], c_int32),
+    "tufrg_flow_init": ([c_void_p, POINTER(tufrg_flow_opts), c_void_p, c_void_p], c_int32),
+    "tufrg_flow_step": ([c_void_p, c_int32, POINTER(tufrg_result), c_void_p], c_int32),
+    "tufrg_flow_state": ([c_void_p, c_void_p, POINTER(tufrg_result), c_void_p], c_int32),
+    "tufrg_mu_for_density": ([c_double, c_double, c_double, c_int32, c_int32,
+                              POINTER(c_double)], c_int32),
+    "tufrg_status_string": ([c_int32], ctypes.c_char_p),
+}
+
+
+def lib():
+    """The loaded libtufrg.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_1604_06296_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise TufrgError(status, where)
+
+
+def _dptr(p) -> c_void_p:
+    return c_void_p(int(p) if p else 0)
+
+
+def tufrg_setup(params: tufrg_params, stream: int = 0) -> c_void_p:
+    ctx = c_void_p()
+    _check(lib().tufrg_setup(byref(params), _dptr(stream), byref(ctx)), "tufrg_setup")
+    return ctx
+
+
+def tufrg_destroy(ctx: c_void_p) -> None:
+    lib().tufrg_destroy(ctx)
+
+
+def tufrg_dims(ctx: c_void_p) -> tuple[int, int, int]:
+    nl, nff, nb = c_int32(), c_int32(), c_int32()
+    _check(lib().tufrg_dims(ctx, byref(nl), byref(nff), byref(nb)), "tufrg_dims")
+    return nl.value, nff.value, nb.value
+
+
+def tufrg_eval_formfactors(bonds, kx, ky):
+    """bonds: int32 array [n][2]; kx, ky: float64 arrays [n]. Returns [Nff][n]."""
+    import numpy as np
+    b = np.ascontiguousarray(bonds, dtype=np.int32)
+    kx = np.ascontiguousarray(kx, dtype=np.float64)
+    ky = np.ascontiguousarray(ky, dtype=np.float64)
+    nff = c_int32()
+    bp = b.ctypes.data_as(POINTER(c_int32))
+    _check(lib().tufrg_eval_formfactors(len(b), bp, 0, None, None, None, byref(nff)),
+           "tufrg_eval_formfactors")
+    out = np.empty((nff.value, len(kx)), dtype=np.float64)
+    _check(lib().tufrg_eval_formfactors(len(b), bp, len(kx), kx.ctypes.data_as(POINTER(c_double)),
+                                        ky.ctypes.data_as(POINTER(c_double)),
+                                        out.ctypes.data_as(POINTER(c_double)), None),
+           "tufrg_eval_formfactors")
+    return out
+
+
+def tufrg_loops(ctx, lam: float, chi_dot_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_loops(ctx, lam, _dptr(chi_dot_dev), _dptr(stream)), "tufrg_loops")
+
+
+def tufrg_project(ctx, y_dev: int, v_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_project(ctx, _dptr(y_dev), _dptr(v_dev), _dptr(stream)), "tufrg_project")
+
+
+def tufrg_products(ctx, v_dev: int, chi_dev: int, dy_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_products(ctx, _dptr(v_dev), _dptr(chi_dev), _dptr(dy_dev),
+                                _dptr(stream)), "tufrg_products")
+
+
+def tufrg_rhs(ctx, lam: float, y_dev: int, dy_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_rhs(ctx, lam, _dptr(y_dev), _dptr(dy_dev), _dptr(stream)), "tufrg_rhs")
+
+
+def tufrg_flow(ctx, opts: tufrg_flow_opts, y_dev: int, stream: int = 0) -> tufrg_result:
+    res = tufrg_result()
+    _check(lib().tufrg_flow(ctx, byref(opts), _dptr(y_dev), byref(res), _dptr(stream)),
+           "tufrg_flow")
+    return res
+
+
+def tufrg_flow_init(ctx, opts: tufrg_flow_opts, y0_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_flow_init(ctx, byref(opts), _dptr(y0_dev), _dptr(stream)),
+           "tufrg_flow_init")
+
+
+def tufrg_flow_step(ctx, n_steps: int, stream: int = 0) -> tufrg_result:
+    res = tufrg_result()
+    _check(lib().tufrg_flow_step(ctx, n_steps, byref(res), _dptr(stream)), "tufrg_flow_step")
+    return res
+
+
+def tufrg_flow_state(ctx, y_dev: int, stream: int = 0) -> tufrg_result:
+    res = tufrg_result()
+    _check(lib().tufrg_flow_state(ctx, _dptr(y_dev), byref(res), _dptr(stream)),
+           "tufrg_flow_state")
+    return res
+
+
+def tufrg_mu_for_density(t: float, tp: float, n: float, nf_x: int, nf_y: int) -> float:
+    mu = c_double()
+    _check(lib().tufrg_mu_for_density(t, tp, n, nf_x, nf_y, byref(mu)), "tufrg_mu_for_density")
+    return mu.value
+
+
+def tufrg_status_string(status: int) -> str:
+    return lib().tufrg_status_string(status).decode()

@@ -1,0 +1,254 @@
+// extern "C" entry points of include/tufrg.h.
+#include <cmath>
+#include <new>
+
+#include "internal.h"
+
+tufrg_status tufrg_cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return TUFRG_ERR_OOM;
+  return TUFRG_ERR_CUDA;
+}
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+tufrg_status validate(const tufrg_params* p) {
+  if (!p || p->lattice != 0) return TUFRG_ERR_ARG;
+  if (!std::isfinite(p->t) || p->t == 0.0 || !std::isfinite(p->tp) || !std::isfinite(p->mu) ||
+      !std::isfinite(p->U))
+    return TUFRG_ERR_ARG;
+  if (p->nc_x < 2 || p->nc_y < 2 || (p->nc_x & 1) || (p->nc_y & 1)) return TUFRG_ERR_ARG;
+  if (p->nf_x < 4 || p->nf_y < 4) return TUFRG_ERR_ARG;
+  if (p->nf_x % (2 * p->nc_x) || p->nf_y % (2 * p->nc_y)) return TUFRG_ERR_ARG;
+  if (p->nf_x % 4 || p->nf_y % 4) return TUFRG_ERR_ARG;
+  if ((long long)p->nf_x * p->nf_y > (1LL << 26)) return TUFRG_ERR_ARG;
+  if ((long long)p->nc_x * p->nc_y > (1LL << 16)) return TUFRG_ERR_ARG;
+  if (p->precision < TUFRG_FP64 || p->precision > TUFRG_BF16X3) return TUFRG_ERR_ARG;
+  if (p->feedback != 0 && p->feedback != 1) return TUFRG_ERR_ARG;
+  return TUFRG_OK;
+}
+
+}  // namespace
+
+namespace tufrg {
+
+tufrg_status rhs_device(tufrg_ctx* c, const double* y, double* dy, const double* d_scale,
+                        cudaStream_t st) {
+  TUFRG_CHECK(launch_scale_tables(c, st));
+  TUFRG_CHECK(launch_loops_fp64(c, c->d_chi, st));
+  TUFRG_CHECK(launch_project(c, y, c->d_V, st));
+  TUFRG_CHECK(launch_products(c, c->d_V, c->d_chi, dy, d_scale, st));
+  return TUFRG_OK;
+}
+
+}  // namespace tufrg
+
+extern "C" {
+
+tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** out) {
+  if (!out) return TUFRG_ERR_ARG;
+  *out = nullptr;
+  TUFRG_CHECK(validate(p));
+  tufrg_ctx* c = new (std::nothrow) tufrg_ctx();
+  if (!c) return TUFRG_ERR_OOM;
+  c->p = *p;
+  if (p->n_bonds > 0 && p->bonds) c->bonds.assign(p->bonds, p->bonds + 2 * p->n_bonds);
+  c->p.bonds = c->bonds.data();
+  tufrg_status s = c->basis.build(p->n_bonds, p->bonds);
+  if (s == TUFRG_OK && (p->nc_x < 2 * c->basis.max_component + 1 ||
+                        p->nc_y < 2 * c->basis.max_component + 1))
+    s = TUFRG_ERR_ARG;  // coarse grid must resolve the basis
+  if (s != TUFRG_OK) {
+    delete c;
+    return s;
+  }
+  c->ncx = p->nc_x;
+  c->ncy = p->nc_y;
+  c->nl = c->ncx * c->ncy;
+  c->nfx = p->nf_x;
+  c->nfy = p->nf_y;
+  c->nf = c->nfx * c->nfy;
+  c->nff = c->basis.nff;
+  c->nb = c->basis.nb;
+  s = tufrg::setup_device(c, (cudaStream_t)cuda_stream);
+  if (s != TUFRG_OK) {
+    tufrg::free_device(c);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return TUFRG_OK;
+}
+
+void tufrg_destroy(tufrg_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  tufrg::free_device(c);
+  delete c;
+}
+
+tufrg_status tufrg_dims(const tufrg_ctx* c, int32_t* nl, int32_t* nff, int32_t* nb) {
+  if (!c) return TUFRG_ERR_ARG;
+  if (nl) *nl = c->nl;
+  if (nff) *nff = c->nff;
+  if (nb) *nb = c->nb;
+  return TUFRG_OK;
+}
+
+tufrg_status tufrg_eval_formfactors(int32_t n_bonds, const int32_t* bonds, int32_t n,
+                                    const double* kx, const double* ky, double* out,
+                                    int32_t* nff_out) {
+  tufrg::Basis basis;
+  TUFRG_CHECK(basis.build(n_bonds, bonds));
+  if (nff_out) *nff_out = basis.nff;
+  if (!out) return TUFRG_OK;
+  if (n < 0 || (n > 0 && (!kx || !ky))) return TUFRG_ERR_ARG;
+  for (int m = 0; m < basis.nff; ++m)
+    for (int i = 0; i < n; ++i) out[(size_t)m * n + i] = basis.eval(m, kx[i], ky[i]);
+  return TUFRG_OK;
+}
+
+tufrg_status tufrg_loops(tufrg_ctx* c, double lambda, double* chi_dot_dev, void* stream) {
+  if (!c || !chi_dot_dev || !finite_pos(lambda)) return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
+  TUFRG_CHECK(tufrg::launch_scale_tables(c, st));
+  return tufrg::launch_loops_fp64(c, chi_dot_dev, st);
+}
+
+tufrg_status tufrg_project(tufrg_ctx* c, const double* y_dev, double* v_dev, void* stream) {
+  if (!c || !y_dev || !v_dev || y_dev == v_dev) return TUFRG_ERR_ARG;
+  return tufrg::launch_project(c, y_dev, v_dev, (cudaStream_t)stream);
+}
+
+tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi_dot_dev,
+                            double* dy_dev, void* stream) {
+  if (!c || !v_dev || !chi_dot_dev || !dy_dev || dy_dev == v_dev || dy_dev == chi_dot_dev)
+    return TUFRG_ERR_ARG;
+  return tufrg::launch_products(c, v_dev, chi_dot_dev, dy_dev, nullptr, (cudaStream_t)stream);
+}
+
+tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double* dy_dev,
+                       void* stream) {
+  if (!c || !y_dev || !dy_dev || y_dev == dy_dev || !finite_pos(lambda)) return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
+  return tufrg::rhs_device(c, y_dev, dy_dev, nullptr, st);
+}
+
+namespace {
+
+tufrg_status check_opts(const tufrg_flow_opts* o) {
+  if (!o) return TUFRG_ERR_ARG;
+  if (!finite_pos(o->lambda0) || !finite_pos(o->lambda_min) || o->lambda_min >= o->lambda0)
+    return TUFRG_ERR_ARG;
+  if (!finite_pos(o->threshold) || !(o->rtol >= 0.0) || !(o->atol >= 0.0) ||
+      o->rtol + o->atol <= 0.0 || !finite_pos(o->h0))
+    return TUFRG_ERR_ARG;
+  if (o->method != TUFRG_DOPRI5 && o->method != TUFRG_RK4) return TUFRG_ERR_ARG;
+  if (o->n_checkpoints < 0 ||
+      (o->n_checkpoints > 0 && (!o->checkpoints || !o->checkpoint_states_dev)))
+    return TUFRG_ERR_ARG;
+  for (int i = 0; i < o->n_checkpoints; ++i)
+    if (!finite_pos(o->checkpoints[i])) return TUFRG_ERR_ARG;
+  return TUFRG_OK;
+}
+
+// flows run on the context's stream, ordered after / before the caller's
+tufrg_status enter(tufrg_ctx* c, cudaStream_t user) {
+  TUFRG_CUDA(cudaEventRecord(c->ev_in, user));
+  TUFRG_CUDA(cudaStreamWaitEvent(c->fstream, c->ev_in, 0));
+  return TUFRG_OK;
+}
+
+tufrg_status leave(tufrg_ctx* c, cudaStream_t user, tufrg_status s) {
+  if (cudaEventRecord(c->ev_out, c->fstream) != cudaSuccess ||
+      cudaStreamWaitEvent(user, c->ev_out, 0) != cudaSuccess)
+    return s == TUFRG_OK ? TUFRG_ERR_CUDA : s;
+  return s;
+}
+
+}  // namespace
+
+tufrg_status tufrg_flow(tufrg_ctx* c, const tufrg_flow_opts* o, double* y_dev,
+                        tufrg_result* res, void* stream) {
+  if (!c || !y_dev || !res || o == nullptr || o->max_steps <= 0) return TUFRG_ERR_ARG;
+  TUFRG_CHECK(check_opts(o));
+  cudaStream_t user = (cudaStream_t)stream;
+  TUFRG_CHECK(enter(c, user));
+  tufrg_status s = tufrg::flow_init(c, o, y_dev, c->fstream);
+  if (s == TUFRG_OK) s = tufrg::flow_step(c, o->max_steps, nullptr, c->fstream);
+  tufrg_status s2 = tufrg::flow_state(c, y_dev, res, c->fstream);
+  if (s == TUFRG_OK) s = s2;
+  return leave(c, user, s);
+}
+
+tufrg_status tufrg_flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0_dev,
+                             void* stream) {
+  if (!c || !y0_dev) return TUFRG_ERR_ARG;
+  TUFRG_CHECK(check_opts(o));
+  cudaStream_t user = (cudaStream_t)stream;
+  TUFRG_CHECK(enter(c, user));
+  return leave(c, user, tufrg::flow_init(c, o, y0_dev, c->fstream));
+}
+
+tufrg_status tufrg_flow_step(tufrg_ctx* c, int32_t n_steps, tufrg_result* res, void* stream) {
+  if (!c || n_steps < 0) return TUFRG_ERR_ARG;
+  cudaStream_t user = (cudaStream_t)stream;
+  TUFRG_CHECK(enter(c, user));
+  return leave(c, user, tufrg::flow_step(c, n_steps, res, c->fstream));
+}
+
+tufrg_status tufrg_flow_state(tufrg_ctx* c, double* y_dev, tufrg_result* res, void* stream) {
+  if (!c) return TUFRG_ERR_ARG;
+  cudaStream_t user = (cudaStream_t)stream;
+  TUFRG_CHECK(enter(c, user));
+  return leave(c, user, tufrg::flow_state(c, y_dev, res, c->fstream));
+}
+
+tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x, int32_t nf_y,
+                                  double* mu_out) {
+  if (!mu_out || nf_x < 2 || nf_y < 2 || !(n > 0.0 && n < 2.0) || !std::isfinite(t) ||
+      !std::isfinite(tp))
+    return TUFRG_ERR_ARG;
+  std::vector<double> cx(nf_x), cy(nf_y);
+  for (int i = 0; i < nf_x; ++i) cx[i] = std::cos(-M_PI + 2.0 * M_PI * i / nf_x);
+  for (int i = 0; i < nf_y; ++i) cy[i] = std::cos(-M_PI + 2.0 * M_PI * i / nf_y);
+  auto density = [&](double mu) {
+    double below = 0.0;
+    for (int i = 0; i < nf_x; ++i)
+      for (int j = 0; j < nf_y; ++j) {
+        double e0 = -2.0 * t * (cx[i] + cy[j]) - 4.0 * tp * cx[i] * cy[j];
+        below += e0 < mu ? 1.0 : (e0 == mu ? 0.5 : 0.0);
+      }
+    return 2.0 * below / ((double)nf_x * nf_y);
+  };
+  double lo = -4.0 * std::fabs(t) - 4.0 * std::fabs(tp) - 1.0;
+  double hi = 4.0 * std::fabs(t) + 4.0 * std::fabs(tp) + 1.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (density(mid) < n)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  *mu_out = 0.5 * (lo + hi);
+  return TUFRG_OK;
+}
+
+const char* tufrg_status_string(tufrg_status s) {
+  switch (s) {
+    case TUFRG_OK: return "ok";
+    case TUFRG_ERR_ARG: return "invalid argument";
+    case TUFRG_ERR_CUDA: return "CUDA error";
+    case TUFRG_ERR_NONFINITE: return "non-finite state";
+    case TUFRG_ERR_STEP_UNDERFLOW: return "step size underflow";
+    case TUFRG_ERR_TIMEOUT: return "device wait timed out";
+    case TUFRG_ERR_OOM: return "out of device memory";
+    case TUFRG_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

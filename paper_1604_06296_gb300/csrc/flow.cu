@@ -1,0 +1,574 @@
+// Sec. 3/4: integration of the flow dy/ds = Lambda dy/dLambda, s = ln Lambda,
+// from ln Lambda0 downwards with Dormand-Prince 5(4) (published tableau,
+// Dormand & Prince 1980) or fixed-step RK4, until max |B| exceeds the
+// threshold or Lambda_min is reached.  The critical scale is the first point
+// where max |B| reaches the threshold on the cubic Hermite interpolant of the
+// crossing step, located by 100 bisection steps; the state there is
+// classified by the channel / l / (m, n) of its largest element.
+//
+// Step control runs on the device (one thread), so one DoPri5 attempt is a
+// fixed sequence of kernels -- six stages of (combination, right-hand side),
+// error norm, control, accept -- captured once as a CUDA graph on the
+// library's own stream and replayed; the host reads a small status block
+// after each attempt.  Control:
+//   err = max_i |h sum_j e_j k_j| / (atol + rtol max(|y_i|, |y_new,i|))
+//   accept if err <= 1; factor 0.9 err^(-1/5) clipped to [0.2, 5], no growth
+//   right after a rejection; the next step is clipped to land on ln Lambda_min.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace tufrg {
+namespace {
+
+// Dormand-Prince 5(4) tableau
+const double kC[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+const double kA[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+const double kB[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
+const double kBs[7] = {5179.0 / 57600, 0.0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200,
+                       187.0 / 2100, 1.0 / 40};
+constexpr double kFacSafety = 0.9, kFacMin = 0.2, kFacMax = 5.0;
+constexpr int kBisect = 100;
+
+struct FlowCtl {
+  double s, h, s_end, s_prev;
+  double rtol, atol, thr, dir;
+  unsigned long long err_u, max_u, bis_u, arg_u;
+  double bis_a, bis_b;
+  int nonfinite, accepted, last_rejected, crossed, done, status;
+  long long n_acc, n_rej, n_rhs;
+};
+
+struct Combo {
+  const double* k[7];
+  double a[7];
+  int nk;
+  double c;  // stage node: Lambda = exp(s + c h)
+};
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+__device__ void block_max_u(unsigned long long v, unsigned long long* target) {
+  __shared__ unsigned long long red[32];
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0 && v) atomicMax(target, v);
+  }
+  __syncthreads();
+}
+
+// out = y + h * sum_j a_j k_j ; one thread also publishes Lambda for the RHS
+__global__ void combo_kernel(const double* __restrict__ y, double* __restrict__ out, Combo cb,
+                             const FlowCtl* __restrict__ ctl, double* __restrict__ lam,
+                             size_t n, int set_lambda) {
+  const double h = ctl->h;
+  if (set_lambda && blockIdx.x == 0 && threadIdx.x == 0) {
+    const double L = exp(ctl->s + cb.c * h);
+    lam[0] = L;
+    lam[1] = L;
+  }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < cb.nk; ++j) acc = fma(cb.a[j], cb.k[j][i], acc);
+    out[i] = y[i] + h * acc;
+  }
+}
+
+__global__ void error_kernel(const double* __restrict__ y, const double* __restrict__ ynew,
+                             Combo e, FlowCtl* __restrict__ ctl, size_t n) {
+  const double h = ctl->h, rtol = ctl->rtol, atol = ctl->atol;
+  unsigned long long emax = 0, ymax = 0;
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < e.nk; ++j) acc = fma(e.a[j], e.k[j][i], acc);
+    const double yn = ynew[i];
+    const double sc = atol + rtol * fmax(fabs(y[i]), fabs(yn));
+    const double r = fabs(h * acc) / sc;
+    if (!isfinite(yn) || !isfinite(r)) bad = 1;
+    emax = max(emax, abs_bits(r));
+    ymax = max(ymax, abs_bits(yn));
+  }
+  if (bad) ctl->nonfinite = 1;
+  block_max_u(emax, &ctl->err_u);
+  block_max_u(ymax, &ctl->max_u);
+}
+
+__global__ void control_kernel(FlowCtl* c) {
+  const double err = __longlong_as_double((long long)c->err_u);
+  c->accepted = 0;
+  c->crossed = 0;
+  if (c->nonfinite || !isfinite(err)) {
+    c->status = TUFRG_ERR_NONFINITE;
+    c->done = 1;
+    return;
+  }
+  c->n_rhs += 6;
+  if (err <= 1.0) {
+    double fac = err == 0.0 ? kFacMax : fmin(kFacMax, fmax(kFacMin, kFacSafety * pow(err, -0.2)));
+    if (c->last_rejected) fac = fmin(fac, 1.0);
+    c->s_prev = c->s;
+    c->s = c->s + c->h;
+    c->accepted = 1;
+    c->n_acc += 1;
+    const double ymax = __longlong_as_double((long long)c->max_u);
+    c->crossed = ymax > c->thr;
+    c->h = c->h * fac;
+    c->last_rejected = 0;
+    if (c->crossed || (c->s_end - c->s) * c->dir <= 0.0) c->done = 1;
+  } else {
+    c->n_rej += 1;
+    c->h = c->h * fmax(kFacMin, kFacSafety * pow(err, -0.2));
+    c->last_rejected = 1;
+  }
+  if (!c->done && fabs(c->h) < 1e-12) {
+    c->status = TUFRG_ERR_STEP_UNDERFLOW;
+    c->done = 1;
+  }
+  if ((c->s + c->h - c->s_end) * c->dir > 0.0) c->h = c->s_end - c->s;
+  c->err_u = 0;
+  c->max_u = 0;
+}
+
+// on acceptance: keep the previous point for dense output and move on (FSAL)
+__global__ void accept_kernel(double* __restrict__ y, const double* __restrict__ ynew,
+                              double* __restrict__ yprev, double* __restrict__ k1,
+                              const double* __restrict__ k7, double* __restrict__ k1prev,
+                              const FlowCtl* __restrict__ ctl, size_t n) {
+  if (!ctl->accepted) return;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    yprev[i] = y[i];
+    y[i] = ynew[i];
+    k1prev[i] = k1[i];
+    k1[i] = k7[i];
+  }
+}
+
+__device__ __forceinline__ double hermite(double s0, double y0, double f0, double s1, double y1,
+                                          double f1, double s) {
+  const double h = s1 - s0, th = (s - s0) / h;
+  const double h00 = 2 * th * th * th - 3 * th * th + 1;
+  const double h10 = th * th * th - 2 * th * th + th;
+  const double h01 = -2 * th * th * th + 3 * th * th;
+  const double h11 = th * th * th - th * th;
+  return h00 * y0 + h10 * h * f0 + h01 * y1 + h11 * h * f1;
+}
+
+// Interpolant of the last accepted step at s_fixed (or at the bisection
+// midpoint when use_mid); writes it to out if non-null and, when track,
+// accumulates max |value| into ctl->bis_u.
+__global__ void hermite_kernel(const double* __restrict__ y0, const double* __restrict__ f0,
+                               const double* __restrict__ y1, const double* __restrict__ f1,
+                               FlowCtl* __restrict__ ctl, double s_fixed, int use_mid,
+                               double* __restrict__ out, size_t n, int track) {
+  const double s0 = ctl->s_prev, s1 = ctl->s;
+  const double s = use_mid ? 0.5 * (ctl->bis_a + ctl->bis_b) : s_fixed;
+  unsigned long long m = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = hermite(s0, y0[i], f0[i], s1, y1[i], f1[i], s);
+    if (out) out[i] = v;
+    m = max(m, abs_bits(v));
+  }
+  if (track) block_max_u(m, &ctl->bis_u);
+}
+
+__global__ void bisect_update_kernel(FlowCtl* c) {
+  const double m = 0.5 * (c->bis_a + c->bis_b);
+  const double g = __longlong_as_double((long long)c->bis_u);
+  if (g > c->thr)
+    c->bis_b = m;
+  else
+    c->bis_a = m;
+  c->bis_u = 0;
+}
+
+__global__ void max_kernel(const double* __restrict__ y, FlowCtl* __restrict__ ctl, size_t n,
+                           int check_finite) {
+  unsigned long long m = 0;
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    m = max(m, abs_bits(y[i]));
+    if (check_finite && !isfinite(y[i])) bad = 1;
+  }
+  if (bad) ctl->nonfinite = 1;
+  block_max_u(m, &ctl->max_u);
+}
+
+__global__ void argmax_kernel(const double* __restrict__ y, FlowCtl* __restrict__ ctl, size_t n) {
+  const unsigned long long target = ctl->max_u;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (abs_bits(y[i]) == target) atomicMin(&ctl->arg_u, (unsigned long long)i);
+}
+
+double bits_to_double(unsigned long long u) {
+  double d;
+  std::memcpy(&d, &u, sizeof d);
+  return d;
+}
+
+int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+
+}  // namespace
+
+// Integrator state kept in the context between tufrg_flow_* calls.
+struct FlowState {
+  bool initialized = false, finished = false, crossed = false;
+  int method = TUFRG_DOPRI5;
+  double threshold = 0.0;
+  std::vector<std::pair<double, int>> cks;  // (ln Lambda, output slot), largest first
+  size_t next_ck = 0;
+  double* ck_out = nullptr;
+  long long rk4_rhs = 0;
+  FlowCtl* hc = nullptr;  // pinned host mirror of the control block
+  double* base = nullptr;
+  size_t bytes = 0;
+  double *y, *k[7], *ytmp, *ynew, *yprev, *k1prev;
+  FlowCtl* ctl = nullptr;
+  cudaGraphExec_t attempt = nullptr;
+};
+
+namespace {
+
+tufrg_status ensure_buffers(tufrg_ctx* c) {
+  if (!c->flow) {
+    c->flow = new (std::nothrow) FlowState();
+    if (!c->flow) return TUFRG_ERR_OOM;
+  }
+  FlowState& f = *c->flow;
+  if (!f.hc) TUFRG_CUDA(cudaMallocHost((void**)&f.hc, sizeof(FlowCtl)));
+  const size_t n = c->state_elems();
+  const size_t need = sizeof(double) * n * 12 + 1024;
+  if (f.bytes < need) {
+    if (f.attempt) cudaGraphExecDestroy(f.attempt);
+    f.attempt = nullptr;
+    if (f.base) cudaFree(f.base);
+    f.base = nullptr;
+    f.bytes = 0;
+    if (cudaMalloc((void**)&f.base, need) != cudaSuccess) return TUFRG_ERR_OOM;
+    f.bytes = need;
+  }
+  double* p = f.base;
+  f.y = p;
+  for (int i = 0; i < 7; ++i) f.k[i] = p + n * (1 + i);
+  f.ytmp = p + n * 8;
+  f.ynew = p + n * 9;
+  f.yprev = p + n * 10;
+  f.k1prev = p + n * 11;
+  f.ctl = (FlowCtl*)(p + n * 12);
+  return TUFRG_OK;
+}
+
+tufrg_status stage(tufrg_ctx* c, const double* y, double* out,
+                   const std::vector<std::pair<double, const double*>>& terms, double cnode,
+                   double* k_out, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  Combo cb{};
+  cb.nk = (int)terms.size();
+  for (int j = 0; j < cb.nk; ++j) {
+    cb.a[j] = terms[j].first;
+    cb.k[j] = terms[j].second;
+  }
+  cb.c = cnode;
+  const size_t n = c->state_elems();
+  combo_kernel<<<grid_for(n), 256, 0, st>>>(y, out, cb, f.ctl, c->d_lambda, n, 1);
+  TUFRG_CUDA(cudaGetLastError());
+  return rhs_device(c, out, k_out, c->d_lambda + 1, st);
+}
+
+// One DoPri5 attempt: stages 2..7, error norm, control, accept.
+tufrg_status enqueue_attempt(tufrg_ctx* c, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  const size_t n = c->state_elems();
+  for (int i = 1; i < 7; ++i) {
+    std::vector<std::pair<double, const double*>> t;
+    for (int j = 0; j < i; ++j)
+      if (kA[i][j] != 0.0) t.push_back({kA[i][j], f.k[j]});
+    TUFRG_CHECK(stage(c, f.y, i == 6 ? f.ynew : f.ytmp, t, kC[i], f.k[i], st));
+  }
+  Combo ce{};
+  for (int j = 0; j < 7; ++j)
+    if (kB[j] != kBs[j]) {
+      ce.a[ce.nk] = kB[j] - kBs[j];
+      ce.k[ce.nk] = f.k[j];
+      ++ce.nk;
+    }
+  const int G = grid_for(n);
+  error_kernel<<<G, 256, 0, st>>>(f.y, f.ynew, ce, f.ctl, n);
+  control_kernel<<<1, 1, 0, st>>>(f.ctl);
+  accept_kernel<<<G, 256, 0, st>>>(f.y, f.ynew, f.yprev, f.k[0], f.k[6], f.k1prev, f.ctl, n);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+tufrg_status read_ctl(tufrg_ctx* c, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  TUFRG_CUDA(cudaMemcpyAsync(f.hc, f.ctl, sizeof(FlowCtl), cudaMemcpyDeviceToHost, st));
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  return TUFRG_OK;
+}
+
+tufrg_status write_ctl(tufrg_ctx* c, const FlowCtl& v, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  *f.hc = v;
+  TUFRG_CUDA(cudaMemcpyAsync(f.ctl, f.hc, sizeof(FlowCtl), cudaMemcpyHostToDevice, st));
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  return TUFRG_OK;
+}
+
+// max |B| crossed the threshold inside [s, s_prev]: bisection on the Hermite
+// interpolant, then the state at the crossing replaces y.
+tufrg_status resolve_crossing(tufrg_ctx* c, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  const size_t n = c->state_elems();
+  const int G = grid_for(n);
+  FlowCtl cur = *f.hc;
+  cur.bis_a = cur.s_prev;
+  cur.bis_b = cur.s;
+  cur.bis_u = 0;
+  TUFRG_CHECK(write_ctl(c, cur, st));
+  for (int it = 0; it < kBisect; ++it) {
+    hermite_kernel<<<G, 256, 0, st>>>(f.yprev, f.k1prev, f.y, f.k[0], f.ctl, 0.0, 1, nullptr, n,
+                                      1);
+    bisect_update_kernel<<<1, 1, 0, st>>>(f.ctl);
+  }
+  TUFRG_CUDA(cudaGetLastError());
+  TUFRG_CHECK(read_ctl(c, st));
+  const double sc = f.hc->bis_b;
+  hermite_kernel<<<G, 256, 0, st>>>(f.yprev, f.k1prev, f.y, f.k[0], f.ctl, sc, 0, f.ytmp, n, 0);
+  TUFRG_CUDA(cudaGetLastError());
+  TUFRG_CUDA(cudaMemcpyAsync(f.y, f.ytmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  FlowCtl fin = *f.hc;
+  fin.s = sc;
+  return write_ctl(c, fin, st);
+}
+
+tufrg_status checkpoints_in_last_step(tufrg_ctx* c, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  const size_t n = c->state_elems();
+  while (f.next_ck < f.cks.size() && f.cks[f.next_ck].first >= f.hc->s &&
+         f.cks[f.next_ck].first <= f.hc->s_prev) {
+    double* dst = f.ck_out + n * f.cks[f.next_ck].second;
+    hermite_kernel<<<grid_for(n), 256, 0, st>>>(f.yprev, f.k1prev, f.y, f.k[0], f.ctl,
+                                                f.cks[f.next_ck].first, 0, dst, n, 0);
+    TUFRG_CUDA(cudaGetLastError());
+    ++f.next_ck;
+  }
+  return TUFRG_OK;
+}
+
+tufrg_status dopri5_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  if (!f.attempt) {
+    cudaGraph_t g = nullptr;
+    TUFRG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    tufrg_status s = enqueue_attempt(c, st);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s != TUFRG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    TUFRG_CUDA(e);
+    e = cudaGraphInstantiate(&f.attempt, g, 0);
+    cudaGraphDestroy(g);
+    TUFRG_CUDA(e);
+  }
+  for (int i = 0; i < n_steps && !f.finished; ++i) {
+    TUFRG_CUDA(cudaGraphLaunch(f.attempt, st));
+    TUFRG_CHECK(read_ctl(c, st));
+    if (f.hc->status != TUFRG_OK) {
+      f.finished = true;
+      return (tufrg_status)f.hc->status;
+    }
+    if (f.hc->accepted) TUFRG_CHECK(checkpoints_in_last_step(c, st));
+    if (f.hc->crossed) {
+      f.crossed = true;
+      f.finished = true;
+      TUFRG_CHECK(resolve_crossing(c, st));
+    } else if (f.hc->done) {
+      f.finished = true;
+    }
+  }
+  return TUFRG_OK;
+}
+
+// Classic RK4 with equal steps; stops early when max |y| exceeds the threshold.
+tufrg_status rk4_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  const size_t n = c->state_elems();
+  const int G = grid_for(n);
+  for (int i = 0; i < n_steps && !f.finished; ++i) {
+    if ((f.hc->s_end - f.hc->s) * f.hc->dir >= -1e-12) {
+      f.finished = true;
+      break;
+    }
+    TUFRG_CHECK(stage(c, f.y, f.ytmp, {}, 0.0, f.k[0], st));
+    TUFRG_CHECK(stage(c, f.y, f.ytmp, {{0.5, f.k[0]}}, 0.5, f.k[1], st));
+    TUFRG_CHECK(stage(c, f.y, f.ytmp, {{0.5, f.k[1]}}, 0.5, f.k[2], st));
+    TUFRG_CHECK(stage(c, f.y, f.ytmp, {{1.0, f.k[2]}}, 1.0, f.k[3], st));
+    f.rk4_rhs += 4;
+    Combo cb{};
+    cb.nk = 4;
+    const double w[4] = {1.0 / 6, 2.0 / 6, 2.0 / 6, 1.0 / 6};
+    for (int j = 0; j < 4; ++j) {
+      cb.a[j] = w[j];
+      cb.k[j] = f.k[j];
+    }
+    combo_kernel<<<G, 256, 0, st>>>(f.y, f.ynew, cb, f.ctl, c->d_lambda, n, 0);
+    TUFRG_CUDA(cudaGetLastError());
+    TUFRG_CUDA(cudaMemcpyAsync(f.y, f.ynew, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    TUFRG_CHECK(read_ctl(c, st));
+    FlowCtl adv = *f.hc;
+    adv.s_prev = adv.s;
+    adv.s = adv.s + adv.h;
+    adv.n_acc += 1;
+    adv.max_u = 0;
+    adv.nonfinite = 0;
+    TUFRG_CHECK(write_ctl(c, adv, st));
+    max_kernel<<<G, 256, 0, st>>>(f.y, f.ctl, n, 1);
+    TUFRG_CUDA(cudaGetLastError());
+    TUFRG_CHECK(read_ctl(c, st));
+    if (f.hc->nonfinite) {
+      f.finished = true;
+      return TUFRG_ERR_NONFINITE;
+    }
+    if (bits_to_double(f.hc->max_u) > f.threshold) {
+      f.crossed = true;
+      f.finished = true;
+    }
+  }
+  return TUFRG_OK;
+}
+
+void fill_progress(tufrg_ctx* c, tufrg_result* r) {
+  FlowState& f = *c->flow;
+  r->lambda_c = std::exp(f.hc->s);
+  r->h_next = std::fabs(f.hc->h);
+  r->diverged = f.crossed ? 1 : 0;
+  r->finished = f.finished ? 1 : 0;
+  r->n_accepted = f.hc->n_acc;
+  r->n_rejected = f.hc->n_rej;
+  r->n_rhs = f.method == TUFRG_RK4 ? f.rk4_rhs : 1 + f.hc->n_rhs;
+}
+
+}  // namespace
+
+void free_flow(tufrg_ctx* c) {
+  if (!c->flow) return;
+  FlowState& f = *c->flow;
+  if (f.attempt) cudaGraphExecDestroy(f.attempt);
+  if (f.base) cudaFree(f.base);
+  if (f.hc) cudaFreeHost(f.hc);
+  delete c->flow;
+  c->flow = nullptr;
+}
+
+tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
+                       cudaStream_t st) {
+  TUFRG_CHECK(ensure_buffers(c));
+  FlowState& f = *c->flow;
+  f.initialized = false;
+  f.finished = f.crossed = false;
+  f.method = o->method;
+  f.threshold = o->threshold;
+  f.rk4_rhs = 0;
+  f.cks.clear();
+  for (int i = 0; i < o->n_checkpoints; ++i) f.cks.push_back({std::log(o->checkpoints[i]), i});
+  std::sort(f.cks.begin(), f.cks.end(), [](auto& a, auto& b) { return a.first > b.first; });
+  f.next_ck = 0;
+  f.ck_out = o->checkpoint_states_dev;
+  const size_t n = c->state_elems();
+
+  FlowCtl h0{};
+  h0.s = std::log(o->lambda0);
+  h0.s_end = std::log(o->lambda_min);
+  h0.dir = -1.0;
+  h0.rtol = o->rtol;
+  h0.atol = o->atol;
+  h0.thr = o->threshold;
+  h0.h = -std::fabs(o->h0);
+  if (o->method == TUFRG_RK4) {
+    const int steps = std::max(1, (int)std::lround((h0.s - h0.s_end) / std::fabs(o->h0)));
+    h0.h = (h0.s_end - h0.s) / steps;
+  } else if (h0.s + h0.h < h0.s_end) {
+    h0.h = h0.s_end - h0.s;
+  }
+  TUFRG_CUDA(cudaMemcpyAsync(f.y, y0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  TUFRG_CHECK(write_ctl(c, h0, st));
+  if (o->method == TUFRG_DOPRI5) {
+    TUFRG_CHECK(stage(c, f.y, f.ytmp, {}, 0.0, f.k[0], st));  // k1 = f(s0, y0)
+    TUFRG_CUDA(cudaStreamSynchronize(st));
+  }
+  f.initialized = true;
+  return TUFRG_OK;
+}
+
+tufrg_status flow_step(tufrg_ctx* c, int n_steps, tufrg_result* r, cudaStream_t st) {
+  if (!c->flow || !c->flow->initialized) return TUFRG_ERR_STATE;
+  FlowState& f = *c->flow;
+  tufrg_status s = f.method == TUFRG_RK4 ? rk4_steps(c, n_steps, st) : dopri5_steps(c, n_steps, st);
+  if (r) {
+    TUFRG_CHECK(read_ctl(c, st));
+    fill_progress(c, r);
+  }
+  return s;
+}
+
+tufrg_status flow_state(tufrg_ctx* c, double* y_out, tufrg_result* r, cudaStream_t st) {
+  if (!c->flow || !c->flow->initialized) return TUFRG_ERR_STATE;
+  FlowState& f = *c->flow;
+  const size_t n = c->state_elems();
+  const int G = grid_for(n);
+  TUFRG_CHECK(read_ctl(c, st));
+  FlowCtl cur = *f.hc;
+  cur.max_u = 0;
+  cur.arg_u = ~0ull;
+  TUFRG_CHECK(write_ctl(c, cur, st));
+  max_kernel<<<G, 256, 0, st>>>(f.y, f.ctl, n, 0);
+  argmax_kernel<<<G, 256, 0, st>>>(f.y, f.ctl, n);
+  TUFRG_CUDA(cudaGetLastError());
+  if (y_out)
+    TUFRG_CUDA(cudaMemcpyAsync(y_out, f.y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  TUFRG_CHECK(read_ctl(c, st));
+  if (r) {
+    fill_progress(c, r);
+    const size_t per_ch = (size_t)c->nl * c->nff * c->nff;
+    const unsigned long long idx = f.hc->arg_u;
+    r->max_abs = bits_to_double(f.hc->max_u);
+    if (idx < n) {
+      r->channel = (int32_t)(idx / per_ch);
+      size_t rem = idx % per_ch;
+      r->l_index = (int32_t)(rem / ((size_t)c->nff * c->nff));
+      rem %= (size_t)c->nff * c->nff;
+      r->m = (int32_t)(rem / c->nff);
+      r->n = (int32_t)(rem % c->nff);
+    } else {
+      r->channel = r->l_index = r->m = r->n = -1;
+    }
+  }
+  return TUFRG_OK;
+}
+
+}  // namespace tufrg

@@ -1,0 +1,301 @@
+// Host-side construction of the scale-independent device tables.
+//
+// * dispersion table xi(p) on the fine grid (Eq. hubb-disp);
+// * loop points: half of the fine grid, one point of each pair (p, -p) with
+//   weight 2 (weight 1 for p = -p).  The loop integrand f_m f_n w is even
+//   under p -> -p for parity-allowed pairs (pi_m pi_n = +1) and the others
+//   vanish (App. C), so the sum runs over half the zone;
+// * F[pair][k] = weight_k f_m(p_k) f_n(p_k) / Nf for the allowed pairs m <= n;
+// * half-shifts of every l on the fine grid (l/2 lands on the fine grid when
+//   nf % (2 nc) == 0 and nf % 4 == 0);
+// * position-space projection data (Sec. 2.5: the Kronecker-delta overlaps
+//   and Fourier phases are scale independent and computed once).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+#include "internal.h"
+
+namespace tufrg {
+namespace {
+
+constexpr int kKC = 16;            // loop points per chunk of the FP64 loop kernel
+constexpr int kLT = 32;            // l per CTA of the FP64 loop kernel
+constexpr int kTargetCTAs = 4 * 152;
+
+int imod(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// Cross-projection signatures.  For target channel T with projection rule
+// (k1, k2, k3)(l, k, k') of Eqs. (proj-P/C/D) and source channel S whose
+// folded bosonic momentum is l' = fold(k +- k'), put k' = s (l' - k).  The
+// fermionic arguments of Phi^S then read q = k + l/2 - l'/2 and
+// q' = sq k + bq l/2 + gq l'/2.  With f(k) = sum_R c(R) e^{ik.R} the k sum
+// forces R1 - s R2 + R3 + sq R4 = 0 (mod the coarse grid), the source enters
+// through its Fourier series at X = s R2 + (-R3 + gq R4)/2 and the result
+// carries the phase e^{i l.Y}, Y = (R3 + bq R4)/2.
+struct Sig {
+  int target, source, s, sq, bq, gq;
+};
+const Sig kSigs[6] = {
+    {0, 1, +1, -1, +1, +1},  // P <- C : q' = -k + l/2 + l'/2
+    {0, 2, -1, -1, +1, +1},  // P <- D
+    {1, 0, +1, -1, +1, +1},  // C <- P
+    {1, 2, -1, +1, -1, -1},  // C <- D : q' = k - l/2 - l'/2
+    {2, 0, +1, +1, -1, -1},  // D <- P
+    {2, 1, -1, +1, -1, -1},  // D <- C
+};
+
+template <class T>
+tufrg_status upload(T** dptr, const std::vector<T>& h, cudaStream_t st) {
+  size_t bytes = std::max<size_t>(h.size(), 1) * sizeof(T);
+  if (cudaMalloc((void**)dptr, bytes) != cudaSuccess) return TUFRG_ERR_OOM;
+  if (!h.empty()) TUFRG_CUDA(cudaMemcpyAsync(*dptr, h.data(), h.size() * sizeof(T),
+                                             cudaMemcpyHostToDevice, st));
+  return TUFRG_OK;
+}
+
+template <class T>
+tufrg_status alloc(T** dptr, size_t n) {
+  if (cudaMalloc((void**)dptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess)
+    return TUFRG_ERR_OOM;
+  return TUFRG_OK;
+}
+
+void build_proj(tufrg_ctx* c) {
+  const Basis& B = c->basis;
+  const int nb = B.nb;
+  ProjTables& P = c->proj;
+  std::map<std::array<int, 5>, int> keys;
+  std::vector<std::vector<std::array<int, 4>>> rows[3];
+  for (int t = 0; t < 3; ++t) rows[t].assign((size_t)nb * nb, {});
+  int dmax = 0;
+  for (const Sig& g : kSigs) {
+    for (int b1 = 0; b1 < nb; ++b1)
+      for (int b2 = 0; b2 < nb; ++b2)
+        for (int b3 = 0; b3 < nb; ++b3)
+          for (int b4 = 0; b4 < nb; ++b4) {
+            int kx = B.bx[b1] - g.s * B.bx[b2] + B.bx[b3] + g.sq * B.bx[b4];
+            int ky = B.by[b1] - g.s * B.by[b2] + B.by[b3] + g.sq * B.by[b4];
+            if (imod(kx, c->ncx) != 0 || imod(ky, c->ncy) != 0) continue;
+            int x2x = 2 * g.s * B.bx[b2] - B.bx[b3] + g.gq * B.bx[b4];
+            int x2y = 2 * g.s * B.by[b2] - B.by[b3] + g.gq * B.by[b4];
+            int y2x = B.bx[b3] + g.bq * B.bx[b4];
+            int y2y = B.by[b3] + g.bq * B.by[b4];
+            dmax = std::max({dmax, std::abs(x2x), std::abs(x2y), std::abs(y2x), std::abs(y2y)});
+            auto ins = keys.emplace(std::array<int, 5>{g.source, b3, b4, x2x, x2y},
+                                    (int)keys.size());
+            // V = V0 - Phi^SC + Phi^C + Phi^D (Eq. simple-deco)
+            rows[g.target][(size_t)b1 * nb + b2].push_back(
+                {ins.first->second, y2x, y2y, g.source == 0 ? -1 : 1});
+          }
+  }
+  P.dmax = dmax;
+  P.nkeys = (int)keys.size();
+  P.key_src.assign(P.nkeys, 0);
+  P.key_b3.assign(P.nkeys, 0);
+  P.key_b4.assign(P.nkeys, 0);
+  P.key_dx.assign(P.nkeys, 0);
+  P.key_dy.assign(P.nkeys, 0);
+  for (auto& kv : keys) {
+    int i = kv.second;
+    P.key_src[i] = kv.first[0];
+    P.key_b3[i] = kv.first[1];
+    P.key_b4[i] = kv.first[2];
+    P.key_dx[i] = kv.first[3];
+    P.key_dy[i] = kv.first[4];
+  }
+  for (int t = 0; t < 3; ++t) {
+    P.row_ptr[t].assign((size_t)nb * nb + 1, 0);
+    P.term_key[t].clear();
+    P.term_dx[t].clear();
+    P.term_dy[t].clear();
+    P.term_sign[t].clear();
+    for (size_t o = 0; o < rows[t].size(); ++o) {
+      for (auto& e : rows[t][o]) {
+        P.term_key[t].push_back(e[0]);
+        P.term_dx[t].push_back(e[1]);
+        P.term_dy[t].push_back(e[2]);
+        P.term_sign[t].push_back((double)e[3]);
+      }
+      P.row_ptr[t][o + 1] = (int)P.term_key[t].size();
+    }
+  }
+}
+
+}  // namespace
+
+tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
+  const Basis& B = c->basis;
+  const int nff = c->nff, nb = c->nb;
+  const double two_pi = 2.0 * M_PI;
+
+  // dispersion on the fine grid, index ix * nfy + iy, p = -pi + 2 pi i / nf
+  std::vector<double> cx(c->nfx), cy(c->nfy);
+  for (int i = 0; i < c->nfx; ++i) cx[i] = std::cos(-M_PI + two_pi * i / c->nfx);
+  for (int i = 0; i < c->nfy; ++i) cy[i] = std::cos(-M_PI + two_pi * i / c->nfy);
+  std::vector<double4_32a> tab((size_t)c->nf);
+  for (int ix = 0; ix < c->nfx; ++ix)
+    for (int iy = 0; iy < c->nfy; ++iy) {
+      double xi = -2.0 * c->p.t * (cx[ix] + cy[iy]) - 4.0 * c->p.tp * cx[ix] * cy[iy] - c->p.mu;
+      tab[(size_t)ix * c->nfy + iy] = make_double4_32a(xi, 0.0, 0.0, 0.0);
+    }
+  TUFRG_CHECK(upload(&c->d_tab, tab, st));
+
+  // loop points over half the zone
+  std::vector<int2> kp;
+  std::vector<double> kw;
+  const int hy = c->nfy / 2, hx = c->nfx / 2;
+  for (int ix = 0; ix < c->nfx; ++ix)
+    for (int iy = 1; iy < hy; ++iy) {
+      kp.push_back(make_int2(ix, iy));
+      kw.push_back(2.0);
+    }
+  for (int iy : {0, hy})
+    for (int ix = 0; ix <= hx; ++ix) {
+      kp.push_back(make_int2(ix, iy));
+      kw.push_back((ix == 0 || ix == hx) ? 1.0 : 2.0);
+    }
+  c->kdim = (int)kp.size();
+
+  // parity-allowed pairs m <= n
+  c->pair_m.clear();
+  c->pair_n.clear();
+  for (int m = 0; m < nff; ++m)
+    for (int n = m; n < nff; ++n)
+      if (B.ff[m].parity * B.ff[n].parity == 1) {
+        c->pair_m.push_back(m);
+        c->pair_n.push_back(n);
+      }
+  c->npair = (int)c->pair_m.size();
+  c->rm = c->npair <= 16 ? 1 : (c->npair <= 32 ? 2 : 4);
+  const int mt = 16 * c->rm;
+  c->mtiles = (c->npair + mt - 1) / mt;
+  c->mpad = c->mtiles * mt;
+  const int ltiles = (c->nl + kLT - 1) / kLT;
+  const int nchunks = (c->kdim + kKC - 1) / kKC;
+  int ksplit = std::max(1, (kTargetCTAs + ltiles * c->mtiles - 1) / (ltiles * c->mtiles));
+  ksplit = std::min(ksplit, nchunks);
+  c->kchunk = ((nchunks + ksplit - 1) / ksplit) * kKC;
+  c->ksplit = (c->kdim + c->kchunk - 1) / c->kchunk;
+  c->kpad = c->ksplit * c->kchunk;
+
+  std::vector<int2> kidx(c->kpad, make_int2(-1, -1));
+  for (int k = 0; k < c->kdim; ++k) kidx[k] = kp[k];
+  TUFRG_CHECK(upload(&c->d_kidx, kidx, st));
+
+  // form factors at the loop points via per-direction cos/sin tables
+  const int R = 4;
+  std::vector<double> fv((size_t)nff * c->kdim);
+  for (int k = 0; k < c->kdim; ++k) {
+    double px = -M_PI + two_pi * kp[k].x / c->nfx, py = -M_PI + two_pi * kp[k].y / c->nfy;
+    double cxr[R], sxr[R], cyr[R], syr[R];
+    for (int r = 0; r < R; ++r) {
+      cxr[r] = std::cos(r * px);
+      sxr[r] = std::sin(r * px);
+      cyr[r] = std::cos(r * py);
+      syr[r] = std::sin(r * py);
+    }
+    for (int m = 0; m < nff; ++m) {
+      double v = 0.0;
+      for (const TrigTerm& t : B.ff[m].terms) {
+        int ax = std::abs(t.rx), ay = std::abs(t.ry);
+        double ccx = cxr[ax], ssx = t.rx < 0 ? -sxr[ax] : sxr[ax];
+        double ccy = cyr[ay], ssy = t.ry < 0 ? -syr[ay] : syr[ay];
+        double val = t.is_sin ? (ssx * ccy + ccx * ssy) : (ccx * ccy - ssx * ssy);
+        v += t.coef * val;
+      }
+      fv[(size_t)m * c->kdim + k] = v;
+    }
+  }
+  std::vector<double> F((size_t)c->mpad * c->kpad, 0.0);
+  std::vector<int> pair(c->mpad, -1);
+  for (int q = 0; q < c->npair; ++q) {
+    int m = c->pair_m[q], n = c->pair_n[q];
+    pair[q] = m * nff + n;
+    for (int k = 0; k < c->kdim; ++k)
+      F[(size_t)q * c->kpad + k] =
+          kw[k] * fv[(size_t)m * c->kdim + k] * fv[(size_t)n * c->kdim + k] / c->nf;
+  }
+  TUFRG_CHECK(upload(&c->d_F, F, st));
+  TUFRG_CHECK(upload(&c->d_pair, pair, st));
+
+  // l/2 in fine-grid steps: (-pi/2 + pi j / nc) / (2 pi / nf)
+  std::vector<int2> sh(c->nl);
+  for (int jx = 0; jx < c->ncx; ++jx)
+    for (int jy = 0; jy < c->ncy; ++jy)
+      sh[(size_t)jx * c->ncy + jy] = make_int2(-c->nfx / 4 + jx * (c->nfx / (2 * c->ncx)),
+                                               -c->nfy / 4 + jy * (c->nfy / (2 * c->ncy)));
+  TUFRG_CHECK(upload(&c->d_shift, sh, st));
+
+  // bond coefficients
+  std::vector<double2> coef((size_t)nff * nb);
+  for (size_t i = 0; i < coef.size(); ++i)
+    coef[i] = make_double2(B.coef[i].real(), B.coef[i].imag());
+  TUFRG_CHECK(upload(&c->d_coef, coef, st));
+
+  // projection tables
+  build_proj(c);
+  const ProjTables& P = c->proj;
+  const int nd = 2 * P.dmax + 1;
+  std::vector<double2> phase((size_t)(c->ncx + c->ncy) * nd);
+  for (int dim = 0; dim < 2; ++dim) {
+    int n = dim == 0 ? c->ncx : c->ncy, off = dim == 0 ? 0 : c->ncx;
+    for (int i = 0; i < n; ++i)
+      for (int d = -P.dmax; d <= P.dmax; ++d) {
+        // l = pi (2i - n)/n, position d/2:  l * d/2 = pi (2i - n) d / (2n)
+        double a = M_PI * (double)((2 * i - n) * d) / (2.0 * n);
+        phase[(size_t)(off + i) * nd + d + P.dmax] = make_double2(std::cos(a), std::sin(a));
+      }
+  }
+  TUFRG_CHECK(upload(&c->d_phase, phase, st));
+  std::vector<int4> keys(P.nkeys);
+  for (int i = 0; i < P.nkeys; ++i)
+    keys[i] = make_int4(P.key_src[i], P.key_b3[i] * nb + P.key_b4[i], P.key_dx[i] + P.dmax,
+                        P.key_dy[i] + P.dmax);
+  TUFRG_CHECK(upload(&c->d_key, keys, st));
+  std::vector<int> rowp;
+  std::vector<int4> terms;
+  for (int t = 0; t < 3; ++t) {
+    c->term_off[t] = (int)terms.size();
+    for (int v : P.row_ptr[t]) rowp.push_back(v);
+    for (size_t i = 0; i < P.term_key[t].size(); ++i)
+      terms.push_back(make_int4(P.term_key[t][i], P.term_dx[t][i] + P.dmax,
+                                P.term_dy[t][i] + P.dmax, (int)P.term_sign[t][i]));
+  }
+  TUFRG_CHECK(upload(&c->d_row_ptr, rowp, st));
+  TUFRG_CHECK(upload(&c->d_terms, terms, st));
+
+  // workspace
+  TUFRG_CHECK(alloc(&c->d_lambda, 4));
+  TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nl));
+  TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
+  TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
+  TUFRG_CHECK(alloc(&c->d_bt, (size_t)3 * nb * nb * c->nl));
+  TUFRG_CHECK(alloc(&c->d_fkey, (size_t)P.nkeys));
+  TUFRG_CHECK(prepare_products(c));
+  TUFRG_CUDA(cudaStreamCreateWithFlags(&c->fstream, cudaStreamNonBlocking));
+  TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  return TUFRG_OK;
+}
+
+void free_device(tufrg_ctx* c) {
+  free_flow(c);
+  void* ptrs[] = {c->d_tab,  c->d_kidx,   c->d_F,       c->d_shift,   c->d_pair,
+                  c->d_coef, c->d_phase,  c->d_key,     c->d_row_ptr, c->d_terms,
+                  c->d_lambda, c->d_partial, c->d_chi,  c->d_V,       c->d_bt,
+                  c->d_fkey};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->fstream) cudaStreamDestroy(c->fstream);
+}
+
+}  // namespace tufrg

@@ -1,0 +1,197 @@
+"""GPU parity: each step of the right-hand side and the flow, called through the
+C ABI, against the FP64 oracle on the same seeded inputs.
+
+Bar: the FP64 path must match the oracle to a relative max-norm error of
+1e-6 per array (tests hold it to 1e-9, which FP64 sums over <= 1e6 terms
+meet with margin); flows at fixed checkpoints and Lambda_c to 1e-6.
+Sizes span several CTA tiles with ragged tails (Nl = 36, 48 not multiples
+of the 32-l tile; rectangular grids), the largest basis (Nff = 29), the
+degenerate zero state, and the full production sizes on sampled outputs.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import flow as ofl
+from oracle import loops as olo
+from oracle import projections as opj
+from oracle import rhs as orhs
+from oracle.model import Problem
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-9
+
+CASES = {
+    "cfg1": dict(shells=1, nc=8, nf=96, tp=-0.25, mu=-1.0, U=3.0),
+    "ragged": dict(shells=2, nc=6, nf=36, tp=-0.3, mu=-0.9, U=2.5),
+    "rect": dict(shells=3, nc=6, ncy=8, nf=48, tp=-0.35, mu=-1.4, U=3.0),
+    "nff29": dict(shells=6, nc=8, nf=16, tp=-0.2, mu=-0.5, U=3.0),
+}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    from paper_1604_06296_gb300 import build
+    build.build()
+    assert T.cuda.is_available()
+    return T
+
+
+def make(case, torch, feedback=True, precision="fp64"):
+    from paper_1604_06296_gb300 import Solver
+    c = dict(CASES[case]) if isinstance(case, str) else dict(case)
+    bonds = W.bonds_for_shells(c["shells"])
+    ncy, nfy = c.get("ncy", c["nc"]), c.get("nfy", c["nf"])
+    s = Solver(1.0, c["tp"], c["mu"], c["U"], bonds, c["nc"], c["nf"], precision=precision,
+               feedback=feedback, ncy=ncy, nfy=nfy)
+    p = Problem(1.0, c["tp"], c["mu"], c["U"], bonds, c["nc"], ncy, c["nf"], nfy,
+                feedback=feedback).check()
+    return s, p
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def dev(torch, x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("lam", [5.0, 0.3, 0.02])
+def test_loops(torch, case, lam):
+    s, p = make(case, torch)
+    got = s.loops(lam).cpu().numpy()
+    ref = np.stack(olo.chi_dot(p, lam))
+    assert rel(got, ref) < RTOL
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_projections(torch, case):
+    s, p = make(case, torch)
+    y = W.random_state(21, p.nl, p.nff, 0.7)
+    got = s.project(dev(torch, y)).cpu().numpy()
+    assert rel(got, opj.project(p, y)) < RTOL
+    if p.nl <= 64 and p.nff <= 13:
+        assert rel(got, opj.project_bruteforce(p, y)) < RTOL
+
+
+def test_projections_zero_state_is_bare_u(torch):
+    s, p = make("cfg1", torch)
+    got = s.project(s.zeros(3)).cpu().numpy()
+    ref = np.zeros_like(got)
+    ref[:, :, 0, 0] = p.U
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_products(torch, case):
+    s, p = make(case, torch)
+    V = W.random_state(3, p.nl, p.nff)
+    chi = W.random_state(4, p.nl, p.nff)[:2]
+    got = s.products(dev(torch, V), dev(torch, chi)).cpu().numpy()
+    assert rel(got, orhs.products(V, chi[0], chi[1])) < RTOL
+
+
+@pytest.mark.parametrize("case", ["cfg1", "ragged", "rect"])
+@pytest.mark.parametrize("feedback", [True, False])
+def test_rhs(torch, case, feedback):
+    s, p = make(case, torch, feedback=feedback)
+    y = W.random_state(8, p.nl, p.nff, 0.5)
+    got = s.rhs(0.7, dev(torch, y)).cpu().numpy()
+    assert rel(got, orhs.rhs(p, 0.7, y)) < RTOL
+
+
+def test_loops_production_size_sampled(torch):
+    c = W.config("cfg2")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.35, mu=-1.4, U=3.0)
+    s, p = make(case, torch)
+    got = s.loops(0.05).cpu().numpy()
+    sel = [0, 37, 288, 300, 575]
+    ref = np.stack(olo.chi_dot(p, 0.05, sel))
+    assert rel(got[:, sel], ref) < RTOL
+    # App. C invariants on the full output
+    assert np.array_equal(got, np.swapaxes(got, -1, -2))
+
+
+def test_projections_production_size(torch):
+    c = W.config("cfg2")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.25, mu=-1.0, U=3.0)
+    s, p = make(case, torch)
+    y = W.random_state(5, p.nl, p.nff, 0.3)
+    got = s.project(dev(torch, y)).cpu().numpy()
+    assert rel(got, opj.project(p, y)) < RTOL
+
+
+def test_large_scale_loops_sampled(torch):
+    c = W.config("cfg5")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=c["tp"], mu=c["mu"], U=c["U"])
+    s, p = make(case, torch)
+    got = s.loops(0.1).cpu().numpy()
+    sel = [0, 1176]
+    ref = np.stack(olo.chi_dot(p, 0.1, sel))
+    assert rel(got[:, sel], ref) < RTOL
+
+
+def test_flow_cfg1_against_oracle_golden(torch):
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "flow_cfg1.npz"))
+    c = W.config("cfg1")
+    s, p = make("cfg1", torch)
+    y, res, states = s.flow(lambda0=c["lambda0"], lambda_min=c["lambda_min"],
+                            threshold=c["threshold"], rtol=1e-8, atol=1e-10, h0=0.05,
+                            checkpoints=list(g["checkpoints"]))
+    assert res["diverged"] and bool(g["diverged"])
+    assert abs(res["lambda_c"] / float(g["lambda_c"]) - 1) < 1e-6
+    assert (res["channel"], res["l_index"]) == (int(g["channel"]), int(g["l_index"]))
+    yc = y.cpu().numpy()
+    # the reported element must be a maximal one (ties by symmetry are valid)
+    assert abs(abs(yc[res["channel"], res["l_index"], res["m"], res["n"]]) - np.abs(yc).max()) \
+        <= 1e-12 * np.abs(yc).max()
+    assert rel(yc, g["y_c"]) < 1e-6
+    for i in range(len(g["checkpoints"])):
+        assert rel(states[i].cpu().numpy(), g["y_checkpoints"][i]) < 1e-6
+
+
+def test_rk4_steps_match_oracle(torch):
+    s, p = make("ragged", torch)
+    lam0, lam1, steps = 10.0, 1.5, 6
+    h = (np.log(lam1) - np.log(lam0)) / steps
+    y, res, _ = s.flow(lambda0=lam0, lambda_min=lam1, threshold=1e9, h0=abs(h), method="rk4")
+    _, yref = ofl.rk4(ofl.log_rhs(p), np.log(lam0), np.zeros((3, p.nl, p.nff, p.nff)), h, steps)
+    assert res["n_accepted"] == steps and not res["diverged"]
+    assert rel(y.cpu().numpy(), yref) < RTOL
+
+
+def test_ladder_flow_closed_form_on_gpu(torch):
+    case = dict(shells=1, nc=8, nf=64, tp=-0.1, mu=-0.4, U=2.0)
+    s, p = make(case, torch, feedback=False)
+    lam0, lam1 = 10.0, 0.3
+    y, res, _ = s.flow(lambda0=lam0, lambda_min=lam1, threshold=1e9, rtol=1e-11, atol=1e-13,
+                       h0=0.02)
+    y = y.cpu().numpy()
+    c1, c0 = np.stack(olo.chi(p, lam1)), np.stack(olo.chi(p, lam0))
+    dpp, dph = (c1 - c0)[0][:, 0, 0], (c1 - c0)[1][:, 0, 0]
+    U = p.U
+    assert np.allclose(U - y[0, :, 0, 0], U / (1 + U * dpp), rtol=1e-8)
+    assert np.allclose(U + y[1, :, 0, 0], U / (1 + U * dph), rtol=1e-8)
+    assert np.allclose(U + y[2, :, 0, 0], U / (1 - U ** 2 * dph ** 2), rtol=1e-8)
+    rest = y.copy()
+    rest[:, :, 0, 0] = 0
+    assert np.abs(rest).max() == 0.0
+
+
+def test_invalid_calls_return_status(torch):
+    from paper_1604_06296_gb300 import TufrgError
+    s, p = make("cfg1", torch)
+    with pytest.raises(TufrgError):
+        s.rhs(-1.0, s.zeros(3))
+    with pytest.raises(ValueError):
+        s.rhs(1.0, s.zeros(2))
+    y = s.zeros(3)
+    y[0, 0, 0, 0] = float("nan")
+    with pytest.raises(TufrgError) as e:
+        s.flow(y=y, lambda0=10.0, lambda_min=1.0)
+    assert e.value.status == -3
