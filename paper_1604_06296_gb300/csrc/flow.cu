@@ -420,7 +420,7 @@ tufrg_status rk4_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
   const size_t n = c->state_elems();
   const int G = grid_for(n);
   for (int i = 0; i < n_steps && !f.finished; ++i) {
-    if ((f.hc->s_end - f.hc->s) * f.hc->dir >= -1e-12) {
+    if ((f.hc->s_end - f.hc->s) * f.hc->dir <= 1e-12) {  // reached ln Lambda_min
       f.finished = true;
       break;
     }
