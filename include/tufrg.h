@@ -204,6 +204,29 @@ tufrg_status tufrg_flow_step(tufrg_ctx* ctx, int32_t n_steps, tufrg_result* res,
 tufrg_status tufrg_flow_state(tufrg_ctx* ctx, double* y_dev, tufrg_result* res,
                               void* cuda_stream);
 
+/* Allocation-free variant of tufrg_loops.  The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory -- code
+ * whose device memory belongs to another allocator and may not call
+ * cudaMalloc itself (a plugin hosted by another framework, a process held to
+ * a budget reserved at start-up), or a latency-critical loop that must not
+ * allocate once running.  It needs no context: from the parameters p (host)
+ * it rebuilds the scale-independent tables and runs the FP64 loop
+ * contraction (p->precision is ignored) entirely inside one static device
+ * array of 16 MiB, which every GPU that loads the library holds until the
+ * process exits.  The caller passes p, lambda > 0 and the output
+ * chi_dot_dev [2][Nl][Nff][Nff] (device); results equal tufrg_loops up to
+ * rounding.
+ *  - Problems whose tables exceed the array (e.g. fine grids much beyond
+ *    200 x 200 at Nff = 13) return TUFRG_ERR_ARG before any device work.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and corrupt each other's results, so
+ *    serialise them.  Each call rewrites every part of the array it reads.
+ *  - Calls no cudaMalloc, cudaFree or other allocating CUDA routine. */
+tufrg_status tufrg_loops_noalloc(const tufrg_params* p, double lambda, double* chi_dot_dev,
+                                 void* cuda_stream);
+
 /* Chemical potential for filling n (particles per site, both spins):
  * bisection on n(mu) = (2/Nf) sum_k [eps0_k < mu] (ties count 1/2) over the
  * nf_x x nf_y grid.  Host computation. */

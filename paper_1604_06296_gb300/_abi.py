@@ -71,6 +71,7 @@ SIGNATURES = {
     "tufrg_flow_init": ([c_void_p, POINTER(tufrg_flow_opts), c_void_p, c_void_p], c_int32),
     "tufrg_flow_step": ([c_void_p, c_int32, POINTER(tufrg_result), c_void_p], c_int32),
     "tufrg_flow_state": ([c_void_p, c_void_p, POINTER(tufrg_result), c_void_p], c_int32),
+    "tufrg_loops_noalloc": ([POINTER(tufrg_params), c_double, c_void_p, c_void_p], c_int32),
     "tufrg_mu_for_density": ([c_double, c_double, c_double, c_int32, c_int32,
                               POINTER(c_double)], c_int32),
     "tufrg_status_string": ([c_int32], ctypes.c_char_p),
@@ -176,6 +177,13 @@ def tufrg_flow_state(ctx, y_dev: int, stream: int = 0) -> tufrg_result:
     _check(lib().tufrg_flow_state(ctx, _dptr(y_dev), byref(res), _dptr(stream)),
            "tufrg_flow_state")
     return res
+
+
+def tufrg_loops_noalloc(params: tufrg_params, lam: float, chi_dot_dev: int,
+                        stream: int = 0) -> None:
+    """Loops without any device allocation (see include/tufrg.h)."""
+    _check(lib().tufrg_loops_noalloc(byref(params), lam, _dptr(chi_dot_dev), _dptr(stream)),
+           "tufrg_loops_noalloc")
 
 
 def tufrg_mu_for_density(t: float, tp: float, n: float, nf_x: int, nf_y: int) -> float:

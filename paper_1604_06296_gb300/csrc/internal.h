@@ -136,6 +136,20 @@ tufrg_status rhs_device(tufrg_ctx* c, const double* y, double* dy, const double*
 
 tufrg_status prepare_products(tufrg_ctx* c);
 
+// The FP64 loop contraction on explicitly given buffers (same kernels and
+// layouts as launch_loops_fp64, without a context).
+struct LoopBuffers {
+  double4_32a* tab;
+  const int2* kidx;
+  const double* F;
+  const int2* shift;
+  const double* lambda;
+  const int* pair;
+  double* partial;
+  int nf, nfx, nfy, nl, nff, npair, mpad, kpad, kchunk, ksplit, mtiles, rm;
+};
+tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaStream_t st);
+
 tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0, cudaStream_t st);
 tufrg_status flow_step(tufrg_ctx* c, int n_steps, tufrg_result* r, cudaStream_t st);
 tufrg_status flow_state(tufrg_ctx* c, double* y_out, tufrg_result* r, cudaStream_t st);

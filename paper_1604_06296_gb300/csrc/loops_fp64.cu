@@ -200,4 +200,34 @@ tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi, cudaStream_t st) {
   return TUFRG_OK;
 }
 
+tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaStream_t st) {
+  const int blocks = std::min((b.nf + 255) / 256, 152 * 8);
+  scale_tables_kernel<<<blocks, 256, 0, st>>>(b.tab, b.nf, b.lambda);
+  TUFRG_CUDA(cudaGetLastError());
+  dim3 grid((b.nl + LT - 1) / LT, b.mtiles, b.ksplit);
+  switch (b.rm) {
+    case 1:
+      loops_fp64_kernel<1><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
+                                                b.nfy, b.nl, b.kpad, b.kchunk, b.mpad,
+                                                b.partial);
+      break;
+    case 2:
+      loops_fp64_kernel<2><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
+                                                b.nfy, b.nl, b.kpad, b.kchunk, b.mpad,
+                                                b.partial);
+      break;
+    default:
+      loops_fp64_kernel<4><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
+                                                b.nfy, b.nl, b.kpad, b.kchunk, b.mpad,
+                                                b.partial);
+  }
+  TUFRG_CUDA(cudaGetLastError());
+  TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * 2 * b.nl * b.nff * b.nff, st));
+  const int total = 2 * b.npair * b.nl;
+  loops_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(b.partial, b.ksplit, b.mpad, b.nl,
+                                                           b.npair, b.pair, b.nff, chi);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
 }  // namespace tufrg
