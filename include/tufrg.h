@@ -233,6 +233,12 @@ tufrg_status tufrg_loops_noalloc(const tufrg_params* p, double lambda, double* c
 tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x,
                                   int32_t nf_y, double* mu_out);
 
+/* Synchronises the stream and reports device-side failures of earlier
+ * asynchronous calls on this context: TUFRG_ERR_TIMEOUT if a bounded wait
+ * inside a kernel (tensor-core pipeline barriers) gave up; the flag is then
+ * cleared.  tufrg_flow* calls check it themselves. */
+tufrg_status tufrg_check(tufrg_ctx* ctx, void* cuda_stream);
+
 const char* tufrg_status_string(tufrg_status s);
 
 #ifdef __cplusplus

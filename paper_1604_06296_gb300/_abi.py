@@ -74,6 +74,7 @@ SIGNATURES = {
     "tufrg_loops_noalloc": ([POINTER(tufrg_params), c_double, c_void_p, c_void_p], c_int32),
     "tufrg_mu_for_density": ([c_double, c_double, c_double, c_int32, c_int32,
                               POINTER(c_double)], c_int32),
+    "tufrg_check": ([c_void_p, c_void_p], c_int32),
     "tufrg_status_string": ([c_int32], ctypes.c_char_p),
 }
 
@@ -190,6 +191,10 @@ def tufrg_mu_for_density(t: float, tp: float, n: float, nf_x: int, nf_y: int) ->
     mu = c_double()
     _check(lib().tufrg_mu_for_density(t, tp, n, nf_x, nf_y, byref(mu)), "tufrg_mu_for_density")
     return mu.value
+
+
+def tufrg_check(ctx, stream: int = 0) -> None:
+    _check(lib().tufrg_check(ctx, _dptr(stream)), "tufrg_check")
 
 
 def tufrg_status_string(status: int) -> str:

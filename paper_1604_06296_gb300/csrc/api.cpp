@@ -33,10 +33,17 @@ tufrg_status validate(const tufrg_params* p) {
 
 namespace tufrg {
 
+tufrg_status launch_loops(tufrg_ctx* c, double* chi, cudaStream_t st) {
+  if (c->p.precision == TUFRG_FP64) {
+    TUFRG_CHECK(launch_scale_tables(c, st));
+    return launch_loops_fp64(c, chi, st);
+  }
+  return launch_loops_tc(c, chi, st);
+}
+
 tufrg_status rhs_device(tufrg_ctx* c, const double* y, double* dy, const double* d_scale,
                         cudaStream_t st) {
-  TUFRG_CHECK(launch_scale_tables(c, st));
-  TUFRG_CHECK(launch_loops_fp64(c, c->d_chi, st));
+  TUFRG_CHECK(launch_loops(c, c->d_chi, st));
   TUFRG_CHECK(launch_project(c, y, c->d_V, st));
   TUFRG_CHECK(launch_products(c, c->d_V, c->d_chi, dy, d_scale, st));
   return TUFRG_OK;
@@ -113,8 +120,7 @@ tufrg_status tufrg_loops(tufrg_ctx* c, double lambda, double* chi_dot_dev, void*
   if (!c || !chi_dot_dev || !finite_pos(lambda)) return TUFRG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
-  TUFRG_CHECK(tufrg::launch_scale_tables(c, st));
-  return tufrg::launch_loops_fp64(c, chi_dot_dev, st);
+  return tufrg::launch_loops(c, chi_dot_dev, st);
 }
 
 tufrg_status tufrg_project(tufrg_ctx* c, const double* y_dev, double* v_dev, void* stream) {
@@ -234,6 +240,20 @@ tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x, i
       hi = mid;
   }
   *mu_out = 0.5 * (lo + hi);
+  return TUFRG_OK;
+}
+
+tufrg_status tufrg_check(tufrg_ctx* c, void* stream) {
+  if (!c) return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int err = 0;
+  TUFRG_CUDA(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  if (err) {
+    TUFRG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    TUFRG_CUDA(cudaStreamSynchronize(st));
+    return TUFRG_ERR_TIMEOUT;
+  }
   return TUFRG_OK;
 }
 

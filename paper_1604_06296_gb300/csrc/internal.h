@@ -90,7 +90,9 @@ struct tufrg_ctx {
   double4_32a* d_tab = nullptr;        // [nf] (xi, A, H, 0) -- A, H filled per scale
   int2* d_kidx = nullptr;          // [kpad] fine-grid (ix, iy) of each loop point (-1 pad)
   double* d_F = nullptr;           // [mpad][kpad] weight * f_m f_n / Nf
-  int2* d_shift = nullptr;         // [nl] l/2 in fine-grid steps
+  int nrow = 0;                    // l-representative rows (one per pair {l, -l})
+  int2* d_shift = nullptr;         // [nrow] l/2 of each row in fine-grid steps
+  int2* d_rowmap = nullptr;        // [nrow] (l, partner l) written by each row
   int* d_pair = nullptr;           // [mpad] m*nff+n (or -1)
   double2* d_coef = nullptr;       // [nff][nb] bond coefficients
   double2* d_phase = nullptr;      // [ncx + ncy][2*dmax+1] e^{i l d pi/(2nc)} tables
@@ -99,9 +101,17 @@ struct tufrg_ctx {
   int4* d_terms = nullptr;         // [total terms] (key, dx, dy, sign)
   int term_off[3] = {0, 0, 0};
 
+  // tensor-core loop path (precision BF16X3 / 3XTF32)
+  int tc_npad = 0, tc_kpad = 0, tc_kbps = 0, tc_ksplit = 0, tc_nrow_pad = 0, tc_tmem_cols = 0;
+  float4* d_tabf = nullptr;        // [nf] (xi, A, H, 0) in FP32 per scale
+  unsigned char* d_Fhi = nullptr;  // [tc_npad][tc_kpad] high parts of F (bf16 or tf32)
+  unsigned char* d_Flo = nullptr;  // [tc_npad][tc_kpad] low parts
+  float* d_partial_tc = nullptr;   // [tc_ksplit][2][tc_npad][tc_nrow_pad]
+  int* d_err = nullptr;            // device error word (bounded waits that gave up)
+
   // device: workspace
   double* d_lambda = nullptr;      // scalar scale used by the kernels
-  double* d_partial = nullptr;     // [ksplit][2][mpad][nl] split-K partial sums
+  double* d_partial = nullptr;     // [ksplit][2][mpad][nrow] split-K partial sums
   double* d_chi = nullptr;         // [2][nl][nff][nff]
   double* d_V = nullptr;           // [3][nl][nff][nff]
   double2* d_bt = nullptr;         // [3][nb*nb][nl] bond-space propagators
@@ -135,6 +145,11 @@ tufrg_status rhs_device(tufrg_ctx* c, const double* y, double* dy, const double*
                         cudaStream_t st);
 
 tufrg_status prepare_products(tufrg_ctx* c);
+tufrg_status prepare_loops_tc(tufrg_ctx* c);
+size_t tc_smem_bytes(int npad);
+tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi_out, cudaStream_t st);
+// loops in the context's precision
+tufrg_status launch_loops(tufrg_ctx* c, double* chi_out, cudaStream_t st);
 
 // The FP64 loop contraction on explicitly given buffers (same kernels and
 // layouts as launch_loops_fp64, without a context).
@@ -143,10 +158,11 @@ struct LoopBuffers {
   const int2* kidx;
   const double* F;
   const int2* shift;
+  const int2* rowmap;
   const double* lambda;
   const int* pair;
   double* partial;
-  int nf, nfx, nfy, nl, nff, npair, mpad, kpad, kchunk, ksplit, mtiles, rm;
+  int nf, nfx, nfy, nl, nrow, nff, npair, mpad, kpad, kchunk, ksplit, mtiles, rm;
 };
 tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaStream_t st);
 

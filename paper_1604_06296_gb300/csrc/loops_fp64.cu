@@ -57,7 +57,7 @@ template <int RM>
 __global__ void __launch_bounds__(NT)
 loops_fp64_kernel(const double4_32a* __restrict__ tab, const int2* __restrict__ kidx,
                   const double* __restrict__ F, const int2* __restrict__ shift,
-                  const double* __restrict__ lam, int nfx, int nfy, int nl, int kpad,
+                  const double* __restrict__ lam, int nfx, int nfy, int nrow, int kpad,
                   int kchunk, int mpad, double* __restrict__ partial) {
   constexpr int MT = 16 * RM;
   __shared__ double sW[2][KC][LT];
@@ -89,7 +89,7 @@ loops_fp64_kernel(const double4_32a* __restrict__ tab, const int2* __restrict__ 
       const int l = l0 + ll;
       const int2 p = kidx[k0 + kk];
       double wpp = 0.0, wph = 0.0;
-      if (l < nl && p.x >= 0) {
+      if (l < nrow && p.x >= 0) {
         const int2 s = shift[l];
         const int ax = wrap(p.x + s.x, nfx), ay = wrap(p.y + s.y, nfy);
         const int bx = wrap(p.x - s.x, nfx), by = wrap(p.y - s.y, nfy);
@@ -131,28 +131,37 @@ loops_fp64_kernel(const double4_32a* __restrict__ tab, const int2* __restrict__ 
       for (int j = 0; j < 4; ++j) {
         const int l = l0 + tx + 8 * j;
         const int m = m0 + ty + 16 * i;
-        if (l < nl) partial[((size_t)(split * 2 + c) * mpad + m) * nl + l] = acc[c][i][j];
+        if (l < nrow) partial[((size_t)(split * 2 + c) * mpad + m) * nrow + l] = acc[c][i][j];
       }
 }
 
 // Sums the split-K partials in fixed order (deterministic), applies -1/4
-// (pp) and +1/4 (ph) and scatters each allowed pair to (m, n) and (n, m).
+// (pp) and +1/4 (ph) and scatters each allowed pair to (m, n) and (n, m) of
+// the row's l and of its partner -l.
 __global__ void loops_reduce_kernel(const double* __restrict__ partial, int ksplit, int mpad,
-                                    int nl, int npair, const int* __restrict__ pair, int nff,
+                                    int nrow, const int2* __restrict__ rowmap, int nl,
+                                    int npair, const int* __restrict__ pair, int nff,
                                     double* __restrict__ chi) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2 * npair * nl) return;
-  const int l = idx % nl;
-  const int r = idx / nl;
+  if (idx >= 2 * npair * nrow) return;
+  const int row = idx % nrow;
+  const int r = idx / nrow;
   const int q = r % npair, ch = r / npair;
   double s = 0.0;
-  for (int sp = 0; sp < ksplit; ++sp) s += partial[((size_t)(sp * 2 + ch) * mpad + q) * nl + l];
+  for (int sp = 0; sp < ksplit; ++sp)
+    s += partial[((size_t)(sp * 2 + ch) * mpad + q) * nrow + row];
   s *= ch == 0 ? -0.25 : 0.25;
   const int mn = pair[q];
   const int m = mn / nff, n = mn % nff;
-  double* out = chi + ((size_t)ch * nl + l) * nff * nff;
+  const int2 lp = rowmap[row];
+  double* out = chi + ((size_t)ch * nl + lp.x) * nff * nff;
   out[m * nff + n] = s;
   out[n * nff + m] = s;
+  if (lp.y != lp.x) {
+    out = chi + ((size_t)ch * nl + lp.y) * nff * nff;
+    out[m * nff + n] = s;
+    out[n * nff + m] = s;
+  }
 }
 
 __global__ void set_scalar_kernel(double* d, double v) { d[0] = v; }
@@ -173,29 +182,29 @@ tufrg_status launch_scale_tables(tufrg_ctx* c, cudaStream_t st) {
 }
 
 tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi, cudaStream_t st) {
-  dim3 grid((c->nl + LT - 1) / LT, c->mtiles, c->ksplit);
+  dim3 grid((c->nrow + LT - 1) / LT, c->mtiles, c->ksplit);
   switch (c->rm) {
     case 1:
       loops_fp64_kernel<1><<<grid, NT, 0, st>>>(c->d_tab, c->d_kidx, c->d_F, c->d_shift,
-                                                c->d_lambda, c->nfx, c->nfy, c->nl, c->kpad,
+                                                c->d_lambda, c->nfx, c->nfy, c->nrow, c->kpad,
                                                 c->kchunk, c->mpad, c->d_partial);
       break;
     case 2:
       loops_fp64_kernel<2><<<grid, NT, 0, st>>>(c->d_tab, c->d_kidx, c->d_F, c->d_shift,
-                                                c->d_lambda, c->nfx, c->nfy, c->nl, c->kpad,
+                                                c->d_lambda, c->nfx, c->nfy, c->nrow, c->kpad,
                                                 c->kchunk, c->mpad, c->d_partial);
       break;
     default:
       loops_fp64_kernel<4><<<grid, NT, 0, st>>>(c->d_tab, c->d_kidx, c->d_F, c->d_shift,
-                                                c->d_lambda, c->nfx, c->nfy, c->nl, c->kpad,
+                                                c->d_lambda, c->nfx, c->nfy, c->nrow, c->kpad,
                                                 c->kchunk, c->mpad, c->d_partial);
   }
   TUFRG_CUDA(cudaGetLastError());
   TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * 2 * c->nl * c->nff * c->nff, st));
-  const int total = 2 * c->npair * c->nl;
+  const int total = 2 * c->npair * c->nrow;
   loops_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(c->d_partial, c->ksplit, c->mpad,
-                                                           c->nl, c->npair, c->d_pair, c->nff,
-                                                           chi);
+                                                           c->nrow, c->d_rowmap, c->nl,
+                                                           c->npair, c->d_pair, c->nff, chi);
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }
@@ -204,28 +213,29 @@ tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaSt
   const int blocks = std::min((b.nf + 255) / 256, 152 * 8);
   scale_tables_kernel<<<blocks, 256, 0, st>>>(b.tab, b.nf, b.lambda);
   TUFRG_CUDA(cudaGetLastError());
-  dim3 grid((b.nl + LT - 1) / LT, b.mtiles, b.ksplit);
+  dim3 grid((b.nrow + LT - 1) / LT, b.mtiles, b.ksplit);
   switch (b.rm) {
     case 1:
       loops_fp64_kernel<1><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
-                                                b.nfy, b.nl, b.kpad, b.kchunk, b.mpad,
+                                                b.nfy, b.nrow, b.kpad, b.kchunk, b.mpad,
                                                 b.partial);
       break;
     case 2:
       loops_fp64_kernel<2><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
-                                                b.nfy, b.nl, b.kpad, b.kchunk, b.mpad,
+                                                b.nfy, b.nrow, b.kpad, b.kchunk, b.mpad,
                                                 b.partial);
       break;
     default:
       loops_fp64_kernel<4><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
-                                                b.nfy, b.nl, b.kpad, b.kchunk, b.mpad,
+                                                b.nfy, b.nrow, b.kpad, b.kchunk, b.mpad,
                                                 b.partial);
   }
   TUFRG_CUDA(cudaGetLastError());
   TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * 2 * b.nl * b.nff * b.nff, st));
-  const int total = 2 * b.npair * b.nl;
-  loops_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(b.partial, b.ksplit, b.mpad, b.nl,
-                                                           b.npair, b.pair, b.nff, chi);
+  const int total = 2 * b.npair * b.nrow;
+  loops_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(b.partial, b.ksplit, b.mpad, b.nrow,
+                                                           b.rowmap, b.nl, b.npair, b.pair,
+                                                           b.nff, chi);
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }

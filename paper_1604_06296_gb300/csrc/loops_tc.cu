@@ -1,0 +1,470 @@
+// Step ii (Eq. chis) on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+//   chi_dot_{pair}(l) = sum_k F_{pair}(k) W(k, l)
+//
+// as D[row = l-representative][n = pair] = sum_k W[row][k] F[n][k] with the
+// operands split into high and low parts of a narrow type (BF16x3:
+// bf16 hi/lo, kind::f16; 3xTF32: tf32 hi/lo, kind::tf32) and three products
+// W_hi F_hi + W_lo F_hi + W_hi F_lo accumulated in FP32 in tensor memory;
+// the split-K partial sums of each CTA are combined in FP64 by a second
+// kernel.  The propagator operand W is generated in registers from the
+// per-scale FP32 table (xi, A = 1/(Omega + |xi|), H = |xi|(Omega + 3|xi|) A^3)
+// with the same closed-form frequency integral as the FP64 path, and written
+// straight into the 128B-swizzled K-major shared-memory layout the MMA reads;
+// F (scale independent) is staged with cp.async.  Both channels share W's
+// table reads and divisions and have their own accumulator.
+//
+// CTA: 9 warps.  Warps 0-7 produce the W tiles of a K-block (16 rows each,
+// lanes along k) and stage F, then read the accumulators out (warp w reads
+// the 32 TMEM lanes 32 (w % 4).. of channel w / 4).  Warp 8 owns TMEM and one
+// of its threads issues the MMAs.  Two pipeline stages, mbarriers full/empty;
+// every wait is bounded in time and a timeout sets an error word, stops the
+// pipeline, drains the issued MMAs and frees TMEM.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "internal.h"
+
+namespace tufrg {
+namespace {
+
+constexpr int kRows = 128;          // MMA M: l-representatives per CTA
+constexpr int kProducers = 8;       // producer warps
+constexpr int kThreads = 32 * (kProducers + 1);
+constexpr int kRowBytes = 128;      // one 128B-swizzle row per K-block
+constexpr int kWTile = kRows * kRowBytes;  // 16 KB
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase of the given parity; gives up after kWaitNs.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1 KB apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);       // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+template <int PREC>
+struct Prec;
+template <>
+struct Prec<TUFRG_BF16X3> {
+  static constexpr int kElem = 2;      // bytes
+  static constexpr int kPerLane = 2;   // k per lane per row
+  static constexpr uint32_t kFormat = 1;  // BF16
+};
+template <>
+struct Prec<TUFRG_3XTF32> {
+  static constexpr int kElem = 4;
+  static constexpr int kPerLane = 1;
+  static constexpr uint32_t kFormat = 2;  // TF32
+};
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if constexpr (PREC == TUFRG_BF16X3) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i += (i < 0) ? n : 0;
+  i -= (i >= n) ? n : 0;
+  return i;
+}
+
+// half-zone loop point k (order of the setup tables); x = -1 in the padding
+__device__ __forceinline__ int2 loop_point(int k, int nfx, int nfy, int kdim) {
+  if (k >= kdim) return make_int2(-1, -1);
+  const int hx = nfx / 2, hy = nfy / 2, main = nfx * (hy - 1);
+  if (k < main) return make_int2(k / (hy - 1), 1 + k % (hy - 1));
+  const int r = k - main;
+  return make_int2(r % (hx + 1), r < hx + 1 ? 0 : hy);
+}
+
+// Closed-form frequency integral of the two loops for one propagator pair.
+__device__ __forceinline__ void weights(const float4 ta, const float4 tb, float om, float om2,
+                                        float inv_om2, float& wpp, float& wph) {
+  const float sa = ta.y + tb.y, pa = ta.y * tb.y;
+  const float D = pa * fmaf(-2.f * om2, fmaf(sa, sa, -pa), fmaf(5.f * om, sa, -3.f));
+  const float xs = fabsf(ta.x) + fabsf(tb.x);
+  const float S = xs > 0.f ? __fdividef(ta.z + tb.z, xs) : inv_om2;
+  const bool same = ta.x * tb.x > 0.f;
+  wpp = same ? S : D;
+  wph = same ? D : S;
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+struct TcArgs {
+  const float4* tab;
+  const int2* shift;
+  const unsigned char* Fhi;
+  const unsigned char* Flo;
+  float* partial;
+  int* err;
+  const double* lam;
+  int nfx, nfy, kdim, kpad, kbps, nrow, nrow_pad, npad, tmem_cols;
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
+  using P = Prec<PREC>;
+  constexpr int KB = kRowBytes / P::kElem;  // k per K-block
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  const int npad = a.npad;
+  const uint32_t ftile = (uint32_t)npad * kRowBytes;
+  const uint32_t stage_bytes = 4u * kWTile + 2u * ftile;
+  // per stage: W pp_hi, pp_lo, ph_hi, ph_lo, F hi, F lo
+  const uint32_t ctrl = base + 2u * stage_bytes;
+  const uint32_t bar_full = ctrl, bar_empty = ctrl + 16, bar_done = ctrl + 32;
+  unsigned char* gctrl = gbase + 2u * stage_bytes;
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(gctrl + 48);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gctrl + 52);
+  int2* s_shift = reinterpret_cast<int2*>(gctrl + 64);
+  int* s_valid = reinterpret_cast<int*>(gctrl + 64 + 8 * kRows);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x, split = blockIdx.y;
+  const int row0 = tile * kRows;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(bar_full + 8 * s, kProducers);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    mbar_init(bar_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int r = threadIdx.x; r < kRows; r += kThreads) {
+    const int g = row0 + r;
+    s_shift[r] = g < a.nrow ? a.shift[g] : make_int2(0, 0);
+    s_valid[r] = g < a.nrow ? 1 : 0;
+  }
+  if (warp == kProducers) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const double omd = a.lam[0];
+  const float om = (float)omd, om2 = (float)(omd * omd), inv_om2 = (float)(1.0 / (omd * omd));
+  const int kb_begin = split * a.kbps;
+  const size_t frow = (size_t)a.kpad * P::kElem;  // bytes per F row
+
+  if (warp < kProducers) {
+    // ------------------------------------------------------------ producers
+    for (int kb = 0; kb < a.kbps; ++kb) {
+      const int s = kb & 1;
+      if (kb >= 2 && !mbar_wait(bar_empty + 8 * s, ((kb >> 1) + 1) & 1)) {
+        atomicOr(a.err, 1);
+        *abort_flag = 1;
+      }
+      if (*abort_flag) break;
+      const uint32_t st = base + s * stage_bytes;
+      const int k0 = (kb_begin + kb) * KB;
+      // F tiles (hi, lo): npad rows x 8 chunks of 16 bytes each
+      for (int c = threadIdx.x; c < 16 * npad; c += 32 * kProducers) {
+        const int t = c / (8 * npad), rem = c - t * 8 * npad, row = rem >> 3, ch = rem & 7;
+        const unsigned char* src =
+            (t ? a.Flo : a.Fhi) + (size_t)row * frow + (size_t)k0 * P::kElem + ch * 16;
+        cp_async16(st + 4u * kWTile + t * ftile + row * kRowBytes + ((ch ^ (row & 7)) << 4), src);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      // W tiles: this lane's loop points
+      int2 pk[P::kPerLane];
+#pragma unroll
+      for (int j = 0; j < P::kPerLane; ++j)
+        pk[j] = loop_point(k0 + P::kPerLane * lane + j, a.nfx, a.nfy, a.kdim);
+      const uint32_t col = (uint32_t)(P::kPerLane * lane) * P::kElem;  // byte within row
+#pragma unroll 4
+      for (int i = 0; i < kRows / kProducers; ++i) {
+        const int r = warp + kProducers * i;
+        const int2 sh = s_shift[r];
+        const bool valid = s_valid[r] != 0;
+        float wpp[P::kPerLane], wph[P::kPerLane];
+#pragma unroll
+        for (int j = 0; j < P::kPerLane; ++j) {
+          wpp[j] = 0.f;
+          wph[j] = 0.f;
+          if (valid && pk[j].x >= 0) {
+            const int ax = wrap(pk[j].x + sh.x, a.nfx), ay = wrap(pk[j].y + sh.y, a.nfy);
+            const int bx = wrap(pk[j].x - sh.x, a.nfx), by = wrap(pk[j].y - sh.y, a.nfy);
+            weights(__ldg(a.tab + ax * a.nfy + ay), __ldg(a.tab + bx * a.nfy + by), om, om2,
+                    inv_om2, wpp[j], wph[j]);
+          }
+        }
+        uint32_t v[4];
+        if constexpr (PREC == TUFRG_BF16X3) {
+          const __nv_bfloat162 ph = __floats2bfloat162_rn(wpp[0], wpp[1]);
+          const float2 bp = __bfloat1622float2(ph);
+          const __nv_bfloat162 pl = __floats2bfloat162_rn(wpp[0] - bp.x, wpp[1] - bp.y);
+          const __nv_bfloat162 hh = __floats2bfloat162_rn(wph[0], wph[1]);
+          const float2 bh = __bfloat1622float2(hh);
+          const __nv_bfloat162 hl = __floats2bfloat162_rn(wph[0] - bh.x, wph[1] - bh.y);
+          std::memcpy(&v[0], &ph, 4);
+          std::memcpy(&v[1], &pl, 4);
+          std::memcpy(&v[2], &hh, 4);
+          std::memcpy(&v[3], &hl, 4);
+        } else {
+          v[0] = tf32_rna(wpp[0]);
+          v[1] = tf32_rna(wpp[0] - __uint_as_float(v[0]));
+          v[2] = tf32_rna(wph[0]);
+          v[3] = tf32_rna(wph[0] - __uint_as_float(v[2]));
+        }
+        const uint32_t off = r * kRowBytes + ((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          asm volatile("st.shared.b32 [%0], %1;" ::"r"(st + t * kWTile + off), "r"(v[t])
+                       : "memory");
+      }
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_full + 8 * s);
+    }
+  } else if (lane == 0) {
+    // --------------------------------------------------------- MMA issuer
+    const uint32_t idesc = (1u << 4) | (P::kFormat << 7) | (P::kFormat << 10) |
+                           ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+    for (int kb = 0; kb < a.kbps; ++kb) {
+      const int s = kb & 1;
+      if (!mbar_wait(bar_full + 8 * s, (kb >> 1) & 1)) {
+        atomicOr(a.err, 2);
+        *abort_flag = 1;
+      }
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = base + s * stage_bytes;
+      const uint32_t fh = st + 4u * kWTile, fl = fh + ftile;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction
+        const uint32_t o = 32u * kk;
+        const uint64_t bh = smem_desc(fh + o), bl = smem_desc(fl + o);
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          const uint32_t d = tmem + ch * npad;
+          const uint64_t ah = smem_desc(st + (2 * ch) * kWTile + o);
+          const uint64_t al = smem_desc(st + (2 * ch + 1) * kWTile + o);
+          mma<PREC>(d, ah, bh, idesc, (kb | kk) != 0);
+          mma<PREC>(d, al, bh, idesc, 1);
+          mma<PREC>(d, ah, bl, idesc, 1);
+        }
+      }
+      mma_commit(bar_empty + 8 * s);
+    }
+    mma_commit(bar_done);  // arrives once every issued MMA has completed
+  }
+
+  // ------------------------------------------------------------- epilogue
+  if (warp < kProducers) {
+    const bool ok = mbar_wait(bar_done, 0);
+    if (!ok) {
+      atomicOr(a.err, 4);
+      *abort_flag = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && !*abort_flag) {
+      const int quad = warp & 3, ch = warp >> 2;
+      const int row = quad * 32 + lane;
+      float* out = a.partial + (size_t)(split * 2 + ch) * npad * a.nrow_pad + row0 + row;
+      for (int c0 = 0; c0 < npad; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + ch * npad + c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) out[(size_t)(c0 + j) * a.nrow_pad] = __uint_as_float(r[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == kProducers) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols)
+                 : "memory");
+  }
+}
+
+// FP32 per-scale table from the FP64 dispersion table.
+__global__ void scale_tables_f32_kernel(const double4_32a* __restrict__ tab,
+                                        float4* __restrict__ tabf, int nf,
+                                        const double* __restrict__ lam) {
+  const double om = lam[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+    const double xi = tab[i].x, x = fabs(xi), A = 1.0 / (om + x);
+    tabf[i] = make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), 0.f);
+  }
+}
+
+// FP64 combination of the split-K partials in fixed order; -1/4 (pp), +1/4
+// (ph); scatter to (m, n), (n, m) of the row's l and of its partner.
+__global__ void loops_tc_reduce_kernel(const float* __restrict__ partial, int ksplit, int npad,
+                                       int nrow, int nrow_pad, const int2* __restrict__ rowmap,
+                                       int nl, int npair, const int* __restrict__ pair, int nff,
+                                       double* __restrict__ chi) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * npair * nrow) return;
+  const int row = idx % nrow;
+  const int r = idx / nrow;
+  const int q = r % npair, ch = r / npair;
+  double s = 0.0;
+  for (int sp = 0; sp < ksplit; ++sp)
+    s += (double)partial[((size_t)(sp * 2 + ch) * npad + q) * nrow_pad + row];
+  s *= ch == 0 ? -0.25 : 0.25;
+  const int mn = pair[q];
+  const int m = mn / nff, n = mn % nff;
+  const int2 lp = rowmap[row];
+  double* out = chi + ((size_t)ch * nl + lp.x) * nff * nff;
+  out[m * nff + n] = s;
+  out[n * nff + m] = s;
+  if (lp.y != lp.x) {
+    out = chi + ((size_t)ch * nl + lp.y) * nff * nff;
+    out[m * nff + n] = s;
+    out[n * nff + m] = s;
+  }
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(int npad) {
+  return 1024 + 2 * (4 * (size_t)kWTile + 2 * (size_t)npad * kRowBytes) + 64 + 8 * kRows +
+         4 * kRows;
+}
+
+tufrg_status prepare_loops_tc(tufrg_ctx* c) {
+  const int smem = (int)tc_smem_bytes(c->tc_npad);
+  if (c->p.precision == TUFRG_BF16X3)
+    TUFRG_CUDA(cudaFuncSetAttribute(loops_tc_kernel<TUFRG_BF16X3>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  else
+    TUFRG_CUDA(cudaFuncSetAttribute(loops_tc_kernel<TUFRG_3XTF32>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return TUFRG_OK;
+}
+
+tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi, cudaStream_t st) {
+  const int blocks = std::min((c->nf + 255) / 256, 152 * 8);
+  scale_tables_f32_kernel<<<blocks, 256, 0, st>>>(c->d_tab, c->d_tabf, c->nf, c->d_lambda);
+  TUFRG_CUDA(cudaGetLastError());
+  TcArgs a;
+  a.tab = c->d_tabf;
+  a.shift = c->d_shift;
+  a.Fhi = c->d_Fhi;
+  a.Flo = c->d_Flo;
+  a.partial = c->d_partial_tc;
+  a.err = c->d_err;
+  a.lam = c->d_lambda;
+  a.nfx = c->nfx;
+  a.nfy = c->nfy;
+  a.kdim = c->kdim;
+  a.kpad = c->tc_kpad;
+  a.kbps = c->tc_kbps;
+  a.nrow = c->nrow;
+  a.nrow_pad = c->tc_nrow_pad;
+  a.npad = c->tc_npad;
+  a.tmem_cols = c->tc_tmem_cols;
+  const dim3 grid(c->tc_nrow_pad / kRows, c->tc_ksplit);
+  const size_t smem = tc_smem_bytes(c->tc_npad);
+  if (c->p.precision == TUFRG_BF16X3)
+    loops_tc_kernel<TUFRG_BF16X3><<<grid, kThreads, smem, st>>>(a);
+  else
+    loops_tc_kernel<TUFRG_3XTF32><<<grid, kThreads, smem, st>>>(a);
+  TUFRG_CUDA(cudaGetLastError());
+  TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * 2 * c->nl * c->nff * c->nff, st));
+  const int total = 2 * c->npair * c->nrow;
+  loops_tc_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(
+      c->d_partial_tc, c->tc_ksplit, c->tc_npad, c->nrow, c->tc_nrow_pad, c->d_rowmap, c->nl,
+      c->npair, c->d_pair, c->nff, chi);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+}  // namespace tufrg

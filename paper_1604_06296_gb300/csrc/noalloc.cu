@@ -121,12 +121,13 @@ __global__ void nz_kf_kernel(int2* kidx, double* F, TrigTable tt, int nfx, int n
   }
 }
 
-__global__ void nz_small_kernel(int2* shift, int* pair, TrigTable tt, int ncx, int ncy, int nfx,
-                                int nfy, int mpad, double* lam, double lambda) {
+__global__ void nz_small_kernel(int2* shift, int2* rowmap, int* pair, TrigTable tt, int ncx,
+                                int ncy, int nfx, int nfy, int mpad, double* lam, double lambda) {
   const int nl = ncx * ncy;
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
     const int jx = l / ncy, jy = l - jx * ncy;
     shift[l] = make_int2(-nfx / 4 + jx * (nfx / (2 * ncx)), -nfy / 4 + jy * (nfy / (2 * ncy)));
+    rowmap[l] = make_int2(l, l);  // every l is its own row here
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int q = 0;
@@ -193,8 +194,8 @@ extern "C" tufrg_status tufrg_loops_noalloc(const tufrg_params* p, double lambda
   const int nchunks = (kdim + kKC - 1) / kKC;
   int ksplit = std::min(nchunks, std::max(1, (kTargetCTAs + ltiles * mtiles - 1) /
                                                  (ltiles * mtiles)));
-  size_t off_tab = 0, off_kidx = 0, off_F = 0, off_shift = 0, off_pair = 0, off_part = 0,
-         total = 0;
+  size_t off_tab = 0, off_kidx = 0, off_F = 0, off_shift = 0, off_rowmap = 0, off_pair = 0,
+         off_part = 0, total = 0;
   int kchunk = 0, kpad = 0;
   for (;; --ksplit) {
     kchunk = ((nchunks + ksplit - 1) / ksplit) * kKC;
@@ -204,7 +205,8 @@ extern "C" tufrg_status tufrg_loops_noalloc(const tufrg_params* p, double lambda
     off_kidx = off_tab + align256(sizeof(double4_32a) * (size_t)nf);
     off_F = off_kidx + align256(sizeof(int2) * (size_t)kpad);
     off_shift = off_F + align256(sizeof(double) * (size_t)mpad * kpad);
-    off_pair = off_shift + align256(sizeof(int2) * (size_t)nl);
+    off_rowmap = off_shift + align256(sizeof(int2) * (size_t)nl);
+    off_pair = off_rowmap + align256(sizeof(int2) * (size_t)nl);
     off_part = off_pair + align256(sizeof(int) * (size_t)mpad);
     total = off_part + sizeof(double) * (size_t)ks * 2 * mpad * nl;
     if (total <= kNoallocBytes) {
@@ -224,12 +226,14 @@ extern "C" tufrg_status tufrg_loops_noalloc(const tufrg_params* p, double lambda
   lb.kidx = reinterpret_cast<int2*>(b + off_kidx);
   lb.F = reinterpret_cast<double*>(b + off_F);
   lb.shift = reinterpret_cast<int2*>(b + off_shift);
+  lb.rowmap = reinterpret_cast<int2*>(b + off_rowmap);
   lb.pair = reinterpret_cast<int*>(b + off_pair);
   lb.partial = reinterpret_cast<double*>(b + off_part);
   lb.nf = nf;
   lb.nfx = nfx;
   lb.nfy = nfy;
   lb.nl = nl;
+  lb.nrow = nl;
   lb.nff = nff;
   lb.npair = npair;
   lb.mpad = mpad;
@@ -247,8 +251,8 @@ extern "C" tufrg_status tufrg_loops_noalloc(const tufrg_params* p, double lambda
                                    nfx, nfy, kdim, kpad, mpad, 1.0 / nf);
   TUFRG_CUDA(cudaGetLastError());
   nz_small_kernel<<<(nl + 255) / 256, 256, 0, st>>>(
-      const_cast<int2*>(lb.shift), const_cast<int*>(lb.pair), tt, p->nc_x, p->nc_y, nfx, nfy,
-      mpad, const_cast<double*>(lb.lambda), lambda);
+      const_cast<int2*>(lb.shift), const_cast<int2*>(lb.rowmap), const_cast<int*>(lb.pair), tt,
+      p->nc_x, p->nc_y, nfx, nfy, mpad, const_cast<double*>(lb.lambda), lambda);
   TUFRG_CUDA(cudaGetLastError());
   return launch_loops_fp64_buffers(lb, chi_dot_dev, st);
 }

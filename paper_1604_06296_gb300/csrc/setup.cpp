@@ -6,13 +6,15 @@
 //   under p -> -p for parity-allowed pairs (pi_m pi_n = +1) and the others
 //   vanish (App. C), so the sum runs over half the zone;
 // * F[pair][k] = weight_k f_m(p_k) f_n(p_k) / Nf for the allowed pairs m <= n;
-// * half-shifts of every l on the fine grid (l/2 lands on the fine grid when
-//   nf % (2 nc) == 0 and nf % 4 == 0);
+// * l-representatives (one row per pair {l, -l}) with the half-shift of l on
+//   the fine grid (l/2 lands on the fine grid when nf % (2 nc) == 0 and
+//   nf % 4 == 0);
 // * position-space projection data (Sec. 2.5: the Kronecker-delta overlaps
 //   and Fourier phases are scale independent and computed once).
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <tuple>
 
@@ -24,6 +26,28 @@ namespace {
 constexpr int kKC = 16;            // loop points per chunk of the FP64 loop kernel
 constexpr int kLT = 32;            // l per CTA of the FP64 loop kernel
 constexpr int kTargetCTAs = 4 * 152;
+
+// bf16 of a float by round to nearest even (finite inputs)
+uint16_t bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// tf32 of a float: 10 explicit mantissa bits, rounded half away from zero
+uint32_t tf32_rna(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return (u + 0x1000u) & 0xFFFFE000u;
+}
 
 int imod(int a, int n) {
   int r = a % n;
@@ -172,13 +196,32 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
         c->pair_n.push_back(n);
       }
   c->npair = (int)c->pair_m.size();
+
+  // l-representatives: the loops at l and at fold(-l) are equal (the
+  // propagator pair (xi(p + l/2), xi(p - l/2)) is only swapped, and the
+  // weights are symmetric), so one row per pair {l, -l} is computed and
+  // written to both.  Rows keep the l order; self-conjugate l appear once.
+  std::vector<int2> rowmap, rowshift;
+  for (int jx = 0; jx < c->ncx; ++jx)
+    for (int jy = 0; jy < c->ncy; ++jy) {
+      const int l = jx * c->ncy + jy;
+      const int partner = ((c->ncx - jx) % c->ncx) * c->ncy + (c->ncy - jy) % c->ncy;
+      if (l > partner) continue;
+      rowmap.push_back(make_int2(l, partner));
+      // l/2 in fine-grid steps: (-pi/2 + pi j / nc) / (2 pi / nf)
+      rowshift.push_back(make_int2(-c->nfx / 4 + jx * (c->nfx / (2 * c->ncx)),
+                                   -c->nfy / 4 + jy * (c->nfy / (2 * c->ncy))));
+    }
+  c->nrow = (int)rowmap.size();
+
   c->rm = c->npair <= 16 ? 1 : (c->npair <= 32 ? 2 : 4);
   const int mt = 16 * c->rm;
   c->mtiles = (c->npair + mt - 1) / mt;
   c->mpad = c->mtiles * mt;
-  const int ltiles = (c->nl + kLT - 1) / kLT;
+  const int ltiles = (c->nrow + kLT - 1) / kLT;
   const int nchunks = (c->kdim + kKC - 1) / kKC;
-  int ksplit = std::max(1, (kTargetCTAs + ltiles * c->mtiles - 1) / (ltiles * c->mtiles));
+  // at most one wave of resident CTAs (4 per SM at 128 registers per thread)
+  int ksplit = std::max(1, kTargetCTAs / (ltiles * c->mtiles));
   ksplit = std::min(ksplit, nchunks);
   c->kchunk = ((nchunks + ksplit - 1) / ksplit) * kKC;
   c->ksplit = (c->kdim + c->kchunk - 1) / c->kchunk;
@@ -224,13 +267,56 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
   TUFRG_CHECK(upload(&c->d_F, F, st));
   TUFRG_CHECK(upload(&c->d_pair, pair, st));
 
-  // l/2 in fine-grid steps: (-pi/2 + pi j / nc) / (2 pi / nf)
-  std::vector<int2> sh(c->nl);
-  for (int jx = 0; jx < c->ncx; ++jx)
-    for (int jy = 0; jy < c->ncy; ++jy)
-      sh[(size_t)jx * c->ncy + jy] = make_int2(-c->nfx / 4 + jx * (c->nfx / (2 * c->ncx)),
-                                               -c->nfy / 4 + jy * (c->nfy / (2 * c->ncy)));
-  TUFRG_CHECK(upload(&c->d_shift, sh, st));
+  if (c->p.precision != TUFRG_FP64) {
+    // tensor-core path: M = 128 l-rows per CTA, N = pairs (multiple of 16),
+    // K-blocks of one 128-byte swizzle row; split K so that each CTA sums at
+    // most ~8192 loop points in FP32 and the grid fills whole waves
+    const bool bf16 = c->p.precision == TUFRG_BF16X3;
+    const int es = bf16 ? 2 : 4, kb = 128 / es;
+    c->tc_npad = (c->npair + 15) / 16 * 16;
+    if (c->tc_npad > 176) return TUFRG_ERR_ARG;  // two pipeline stages must fit shared memory
+    const int ltiles = (c->nrow + 127) / 128;
+    c->tc_nrow_pad = ltiles * 128;
+    const int nkb = (c->kdim + kb - 1) / kb;
+    const int waves = std::max(1, (int)std::ceil((double)c->kdim * ltiles / (8192.0 * 152)));
+    int ks = std::min(nkb, std::max(1, 152 * waves / ltiles));
+    c->tc_kbps = (nkb + ks - 1) / ks;
+    c->tc_ksplit = (nkb + c->tc_kbps - 1) / c->tc_kbps;
+    c->tc_kpad = c->tc_ksplit * c->tc_kbps * kb;
+    int cols = 32;
+    while (cols < 2 * c->tc_npad) cols *= 2;
+    c->tc_tmem_cols = cols;
+    std::vector<unsigned char> fh((size_t)c->tc_npad * c->tc_kpad * es, 0);
+    std::vector<unsigned char> fl(fh.size(), 0);
+    for (int q = 0; q < c->npair; ++q)
+      for (int k = 0; k < c->kdim; ++k) {
+        const float f = (float)F[(size_t)q * c->kpad + k];
+        const size_t off = ((size_t)q * c->tc_kpad + k) * es;
+        if (bf16) {
+          const uint16_t h = bf16_rne(f);
+          const uint16_t l = bf16_rne(f - bf16_value(h));
+          std::memcpy(&fh[off], &h, 2);
+          std::memcpy(&fl[off], &l, 2);
+        } else {
+          const uint32_t h = tf32_rna(f);
+          float hf;
+          std::memcpy(&hf, &h, 4);
+          const uint32_t l = tf32_rna(f - hf);
+          std::memcpy(&fh[off], &h, 4);
+          std::memcpy(&fl[off], &l, 4);
+        }
+      }
+    TUFRG_CHECK(upload(&c->d_Fhi, fh, st));
+    TUFRG_CHECK(upload(&c->d_Flo, fl, st));
+    TUFRG_CHECK(alloc(&c->d_tabf, (size_t)c->nf));
+    TUFRG_CHECK(alloc(&c->d_partial_tc, (size_t)c->tc_ksplit * 2 * c->tc_npad * c->tc_nrow_pad));
+    TUFRG_CHECK(prepare_loops_tc(c));
+  }
+  TUFRG_CHECK(alloc(&c->d_err, 1));
+  TUFRG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+
+  TUFRG_CHECK(upload(&c->d_shift, rowshift, st));
+  TUFRG_CHECK(upload(&c->d_rowmap, rowmap, st));
 
   // bond coefficients
   std::vector<double2> coef((size_t)nff * nb);
@@ -272,7 +358,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
 
   // workspace
   TUFRG_CHECK(alloc(&c->d_lambda, 4));
-  TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nl));
+  TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nrow));
   TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
   TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
   TUFRG_CHECK(alloc(&c->d_bt, (size_t)3 * nb * nb * c->nl));
@@ -287,7 +373,8 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
 
 void free_device(tufrg_ctx* c) {
   free_flow(c);
-  void* ptrs[] = {c->d_tab,  c->d_kidx,   c->d_F,       c->d_shift,   c->d_pair,
+  void* ptrs[] = {c->d_tabf, c->d_Fhi, c->d_Flo, c->d_partial_tc, c->d_err,
+                  c->d_rowmap, c->d_tab, c->d_kidx, c->d_F,       c->d_shift,   c->d_pair,
                   c->d_coef, c->d_phase,  c->d_key,     c->d_row_ptr, c->d_terms,
                   c->d_lambda, c->d_partial, c->d_chi,  c->d_V,       c->d_bt,
                   c->d_fkey};

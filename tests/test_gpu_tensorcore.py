@@ -1,0 +1,101 @@
+"""Tensor-core loop contraction (BF16x3 and 3xTF32 on tcgen05) against the FP64
+oracle, through the C ABI.
+
+Bar (reduced-precision paths): loops and couplings within 1e-4 relative
+max-norm of the FP64 oracle, Lambda_c within 1 %.  The tests assert tighter
+per-precision bounds derived from the split arithmetic: BF16x3 keeps ~16
+mantissa bits per operand (products ~2^-16 relative), 3xTF32 ~22 bits, FP32
+accumulation over <= 8192 loop points per CTA, FP64 across CTAs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import loops as olo
+from oracle import rhs as orhs
+from tests.test_gpu_parity import CASES, dev, make, rel
+
+pytestmark = pytest.mark.gpu
+
+BOUND = {"bf16x3": 5e-5, "3xtf32": 5e-6}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    from paper_1604_06296_gb300 import build
+    build.build()
+    assert T.cuda.is_available()
+    return T
+
+
+def check_device(s):
+    from paper_1604_06296_gb300 import _abi
+    _abi.tufrg_check(s.ctx)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "3xtf32"])
+@pytest.mark.parametrize("case", ["cfg1", "ragged", "rect"])
+@pytest.mark.parametrize("lam", [5.0, 0.3, 0.02])
+def test_loops_tensor_core(torch, precision, case, lam):
+    s, p = make(case, torch, precision=precision)
+    got = s.loops(lam).cpu().numpy()
+    check_device(s)
+    ref = np.stack(olo.chi_dot(p, lam))
+    err = rel(got, ref)
+    print(f"{precision} {case} lam={lam}: rel err {err:.2e}")
+    assert err < BOUND[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "3xtf32"])
+def test_rhs_tensor_core(torch, precision):
+    s, p = make("cfg1", torch, precision=precision)
+    y = W.random_state(8, p.nl, p.nff, 0.5)
+    got = s.rhs(0.7, dev(torch, y)).cpu().numpy()
+    check_device(s)
+    assert rel(got, orhs.rhs(p, 0.7, y)) < BOUND[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "3xtf32"])
+def test_production_size_loops_sampled(torch, precision):
+    c = W.config("cfg2")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.25, mu=-1.0, U=3.0)
+    s, p = make(case, torch, precision=precision)
+    for lam in (1.0, 0.02):
+        got = s.loops(lam).cpu().numpy()
+        check_device(s)
+        sel = [0, 37, 288, 300, 575]
+        ref = np.stack(olo.chi_dot(p, lam, sel))
+        err = rel(got[:, sel], ref)
+        print(f"cfg2 {precision} lam={lam}: rel err {err:.2e}")
+        assert err < BOUND[precision]
+        # chi(-l) = chi(l) is exact by construction, chi symmetric
+        assert np.array_equal(got, np.swapaxes(got, -1, -2))
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "3xtf32"])
+def test_flow_cfg1_tensor_core_against_oracle(torch, precision):
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "flow_cfg1.npz"))
+    c = W.config("cfg1")
+    s, p = make("cfg1", torch, precision=precision)
+    y, res, states = s.flow(lambda0=c["lambda0"], lambda_min=c["lambda_min"],
+                            threshold=c["threshold"], rtol=1e-8, atol=1e-10, h0=0.05,
+                            checkpoints=list(g["checkpoints"]))
+    check_device(s)
+    dl = abs(res["lambda_c"] / float(g["lambda_c"]) - 1)
+    print(f"{precision}: Lambda_c {res['lambda_c']:.8f} vs {float(g['lambda_c']):.8f} ({dl:.2e})")
+    assert res["diverged"] and dl < 1e-2
+    assert (res["channel"], res["l_index"]) == (int(g["channel"]), int(g["l_index"]))
+    for i, lam in enumerate(g["checkpoints"]):
+        e = rel(states[i].cpu().numpy(), g["y_checkpoints"][i])
+        print(f"  checkpoint {lam}: rel err {e:.2e}")
+        assert e < 1e-4
+
+
+def test_basis_too_large_for_tensor_core_path_rejected(torch):
+    from paper_1604_06296_gb300 import TufrgError
+    with pytest.raises(TufrgError) as e:
+        make(dict(CASES["nff29"]), torch, precision="bf16x3")
+    assert e.value.status == -1
