@@ -292,7 +292,6 @@ def main():
 
     # dominant kernel: the loop contraction, timed alone on the launching stream
     peaks, peak_src = measured_peaks()
-    f64_peak = fp64_peak_tflops(torch)
     chi = solver.empty(2)
     kms = []
     for _ in range(max(3, args.steps)):
@@ -305,21 +304,41 @@ def main():
         kms.append(e0.elapsed_time(e1))
     k_ms = statistics.median(kms)
     p = solver.params
-    nf = p.nf_x * p.nf_y
-    kdim = p.nf_x * (p.nf_y // 2 - 1) + 2 * (p.nf_x // 2 + 1)
     k = np.array([0.3, -1.1]), np.array([0.7, 0.4])
     par = np.sign(tufrg.tufrg_eval_formfactors(solver._bonds, -k[0], -k[1])[:, 0]
                   * tufrg.tufrg_eval_formfactors(solver._bonds, k[0], k[1])[:, 0])
     npair = int(sum(1 for m in range(solver.nff) for n in range(m, solver.nff)
                     if par[m] * par[n] > 0))
-    flops = 2.0 * 2 * npair * kdim * solver.nl        # 2 channels, FMA = 2 flop
+    kdim = p.nf_x * (p.nf_y // 2 - 1) + 2 * (p.nf_x // 2 + 1)
+    # rows: one l of each interior pair {l, -l} (the loops at -l equal those
+    # at l) and every l on the zone boundary
+    nrow = sum(1 for jx in range(p.nc_x) for jy in range(p.nc_y)
+               if jx == 0 or jy == 0
+               or jx * p.nc_y + jy <= (p.nc_x - jx) * p.nc_y + (p.nc_y - jy))
+    if args.precision == "fp64":
+        flops = 2.0 * 2 * npair * kdim * nrow            # 2 channels, FMA = 2 flop
+        peak = fp64_peak_tflops(torch)
+        roofline = {"bound": "alu", "peak_source":
+                    "FP64: cuBLAS DGEMM 4096^3 measured in this run (of measured)",
+                    "kernel": "loops_fp64_kernel (+ per-scale table, split-K reduce)",
+                    "traffic": profile_traffic("loops_fp64.cu", "loops_fp64_cfg2.txt")}
+    else:
+        flops = 2.0 * 3 * 2 * npair * kdim * nrow        # 3 split products issued per MAC
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 if args.precision == "bf16x3" else bf16 * 1.1 / 2.25
+        roofline = {"bound": "tensor", "peak_source":
+                    f"bf16 dense burst {bf16} TFLOP/s from {peak_src}"
+                    + ("" if args.precision == "bf16x3" else " x nominal tf32/bf16 1.1/2.25")
+                    + " (of measured)",
+                    "kernel": f"loops_tc_kernel<{args.precision}> (+ per-scale table, reduce)",
+                    "traffic": profile_traffic("loops_tc.cu",
+                                               f"loops_tc_{args.precision}_cfg2.txt")}
     achieved = flops / (k_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": f64_peak, "unit": "TFLOP/s",
-                "frac": achieved / f64_peak, "traffic": profile_traffic(
-                    "loops_fp64.cu", "loops_fp64_cfg2.txt"),
-                "kernel": "loops_fp64_kernel (+ per-scale table, split-K reduce)",
-                "kernel_ms": k_ms, "algorithmic_flop_per_launch": flops,
-                "peak_source": "FP64: cuBLAS DGEMM 4096^3 measured in this run (of measured)"}
+    roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "kernel_ms": k_ms,
+                     "algorithmic_flop_per_launch": flops,
+                     "counting": f"{npair} allowed pairs x {kdim} half-zone points x {nrow} "
+                                 "l-representatives x 2 channels"})
 
     # end to end through the C ABI with host buffers: H2D state, RHS, D2H result
     y_host = torch.from_numpy(W.random_state(1, solver.nl, solver.nff, 0.1)).pin_memory()
@@ -370,16 +389,18 @@ def main():
     # products) + error + control + accept
     launches_per_step = 6 * 8 + 3
     if rank == 0:
+        dtype = "f64" if args.precision == "fp64" else f"{args.precision} loops, f64 state"
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                "config": {"workload": workload_desc(tp), "precision": args.precision,
                           "step": "one DoPri5 step (6 RHS evaluations + stage/error/control)",
                           "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                           "parallelism": f"{world} independent phase-diagram points"
                                          if world > 1 else "single point"},
                "rhs_evals_timed": total_rhs, "wall_s": wall,
+               "step_ms": [round(t, 3) for t in step_ms],
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                "flow": flow_info, "peaks_source": peak_src}

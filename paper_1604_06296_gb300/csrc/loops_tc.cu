@@ -14,10 +14,10 @@
 // F (scale independent) is staged with cp.async.  Both channels share W's
 // table reads and divisions and have their own accumulator.
 //
-// CTA: 9 warps.  Warps 0-7 produce the W tiles of a K-block (16 rows each,
-// lanes along k) and stage F, then read the accumulators out (warp w reads
-// the 32 TMEM lanes 32 (w % 4).. of channel w / 4).  Warp 8 owns TMEM and one
-// of its threads issues the MMAs.  Two pipeline stages, mbarriers full/empty;
+// CTA: 17 warps.  Warps 0-15 produce the W tiles of a K-block (8 rows each,
+// lanes along k, table loads of 4 rows in flight) and stage F; warps 0-7 then
+// read the accumulators out (warp w reads the 32 TMEM lanes 32 (w % 4).. of
+// channel w / 4).  Warp 16 owns TMEM and one of its threads issues the MMAs.  Two pipeline stages, mbarriers full/empty;
 // every wait is bounded in time and a timeout sets an error word, stops the
 // pipeline, drains the issued MMAs and frees TMEM.
 #include <cuda_bf16.h>
@@ -30,7 +30,8 @@ namespace tufrg {
 namespace {
 
 constexpr int kRows = 128;          // MMA M: l-representatives per CTA
-constexpr int kProducers = 8;       // producer warps
+constexpr int kProducers = 16;      // producer warps
+constexpr int kBatch = 4;           // rows whose table loads are issued together
 constexpr int kThreads = 32 * (kProducers + 1);
 constexpr int kRowBytes = 128;      // one 128B-swizzle row per K-block
 constexpr int kWTile = kRows * kRowBytes;  // 16 KB
@@ -256,46 +257,62 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       for (int j = 0; j < P::kPerLane; ++j)
         pk[j] = loop_point(k0 + P::kPerLane * lane + j, a.nfx, a.nfy, a.kdim);
       const uint32_t col = (uint32_t)(P::kPerLane * lane) * P::kElem;  // byte within row
-#pragma unroll 4
-      for (int i = 0; i < kRows / kProducers; ++i) {
-        const int r = warp + kProducers * i;
-        const int2 sh = s_shift[r];
-        const bool valid = s_valid[r] != 0;
-        float wpp[P::kPerLane], wph[P::kPerLane];
+#pragma unroll 1
+      for (int i0 = 0; i0 < kRows / kProducers; i0 += kBatch) {
+        // issue the table loads of kBatch rows first (memory-level parallelism);
+        // invalid entries load index 0 and are zeroed afterwards
+        float4 ta[kBatch][P::kPerLane], tb[kBatch][P::kPerLane];
+        bool ok[kBatch][P::kPerLane];
 #pragma unroll
-        for (int j = 0; j < P::kPerLane; ++j) {
-          wpp[j] = 0.f;
-          wph[j] = 0.f;
-          if (valid && pk[j].x >= 0) {
+        for (int i = 0; i < kBatch; ++i) {
+          const int r = warp + kProducers * (i0 + i);
+          const int2 sh = s_shift[r];
+          const bool valid = s_valid[r] != 0;
+#pragma unroll
+          for (int j = 0; j < P::kPerLane; ++j) {
+            ok[i][j] = valid && pk[j].x >= 0;
             const int ax = wrap(pk[j].x + sh.x, a.nfx), ay = wrap(pk[j].y + sh.y, a.nfy);
             const int bx = wrap(pk[j].x - sh.x, a.nfx), by = wrap(pk[j].y - sh.y, a.nfy);
-            weights(__ldg(a.tab + ax * a.nfy + ay), __ldg(a.tab + bx * a.nfy + by), om, om2,
-                    inv_om2, wpp[j], wph[j]);
+            ta[i][j] = __ldg(a.tab + (ok[i][j] ? ax * a.nfy + ay : 0));
+            tb[i][j] = __ldg(a.tab + (ok[i][j] ? bx * a.nfy + by : 0));
           }
         }
-        uint32_t v[4];
-        if constexpr (PREC == TUFRG_BF16X3) {
-          const __nv_bfloat162 ph = __floats2bfloat162_rn(wpp[0], wpp[1]);
-          const float2 bp = __bfloat1622float2(ph);
-          const __nv_bfloat162 pl = __floats2bfloat162_rn(wpp[0] - bp.x, wpp[1] - bp.y);
-          const __nv_bfloat162 hh = __floats2bfloat162_rn(wph[0], wph[1]);
-          const float2 bh = __bfloat1622float2(hh);
-          const __nv_bfloat162 hl = __floats2bfloat162_rn(wph[0] - bh.x, wph[1] - bh.y);
-          std::memcpy(&v[0], &ph, 4);
-          std::memcpy(&v[1], &pl, 4);
-          std::memcpy(&v[2], &hh, 4);
-          std::memcpy(&v[3], &hl, 4);
-        } else {
-          v[0] = tf32_rna(wpp[0]);
-          v[1] = tf32_rna(wpp[0] - __uint_as_float(v[0]));
-          v[2] = tf32_rna(wph[0]);
-          v[3] = tf32_rna(wph[0] - __uint_as_float(v[2]));
-        }
-        const uint32_t off = r * kRowBytes + ((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-          asm volatile("st.shared.b32 [%0], %1;" ::"r"(st + t * kWTile + off), "r"(v[t])
-                       : "memory");
+        for (int i = 0; i < kBatch; ++i) {
+          const int r = warp + kProducers * (i0 + i);
+          float wpp[P::kPerLane], wph[P::kPerLane];
+#pragma unroll
+          for (int j = 0; j < P::kPerLane; ++j) {
+            weights(ta[i][j], tb[i][j], om, om2, inv_om2, wpp[j], wph[j]);
+            if (!ok[i][j]) {
+              wpp[j] = 0.f;
+              wph[j] = 0.f;
+            }
+          }
+          uint32_t v[4];
+          if constexpr (PREC == TUFRG_BF16X3) {
+            const __nv_bfloat162 ph = __floats2bfloat162_rn(wpp[0], wpp[1]);
+            const float2 bp = __bfloat1622float2(ph);
+            const __nv_bfloat162 pl = __floats2bfloat162_rn(wpp[0] - bp.x, wpp[1] - bp.y);
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(wph[0], wph[1]);
+            const float2 bh = __bfloat1622float2(hh);
+            const __nv_bfloat162 hl = __floats2bfloat162_rn(wph[0] - bh.x, wph[1] - bh.y);
+            std::memcpy(&v[0], &ph, 4);
+            std::memcpy(&v[1], &pl, 4);
+            std::memcpy(&v[2], &hh, 4);
+            std::memcpy(&v[3], &hl, 4);
+          } else {
+            v[0] = tf32_rna(wpp[0]);
+            v[1] = tf32_rna(wpp[0] - __uint_as_float(v[0]));
+            v[2] = tf32_rna(wph[0]);
+            v[3] = tf32_rna(wph[0] - __uint_as_float(v[2]));
+          }
+          const uint32_t off = r * kRowBytes + ((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(st + t * kWTile + off), "r"(v[t])
+                         : "memory");
+        }
       }
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       fence_proxy_async();
@@ -336,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   }
 
   // ------------------------------------------------------------- epilogue
-  if (warp < kProducers) {
+  if (warp < 8) {  // warps 0-3: pp, 4-7: ph; warp w reads TMEM lanes 32 (w % 4)..
     const bool ok = mbar_wait(bar_done, 0);
     if (!ok) {
       atomicOr(a.err, 4);

@@ -197,15 +197,19 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
       }
   c->npair = (int)c->pair_m.size();
 
-  // l-representatives: the loops at l and at fold(-l) are equal (the
-  // propagator pair (xi(p + l/2), xi(p - l/2)) is only swapped, and the
-  // weights are symmetric), so one row per pair {l, -l} is computed and
-  // written to both.  Rows keep the l order; self-conjugate l appear once.
+  // l-representatives: for l inside the zone (no component at -pi) the
+  // folded -l has half momentum -l/2, so the propagator pair
+  // (xi(p + l/2), xi(p - l/2)) is only swapped and, the weights being
+  // symmetric, the loops at l and -l are equal: one row serves both.  An l on
+  // the zone boundary keeps -pi/2 in that component after folding, so it is
+  // not paired (it gets its own row).
   std::vector<int2> rowmap, rowshift;
   for (int jx = 0; jx < c->ncx; ++jx)
     for (int jy = 0; jy < c->ncy; ++jy) {
       const int l = jx * c->ncy + jy;
-      const int partner = ((c->ncx - jx) % c->ncx) * c->ncy + (c->ncy - jy) % c->ncy;
+      const bool interior = jx != 0 && jy != 0;
+      const int partner =
+          interior ? ((c->ncx - jx) % c->ncx) * c->ncy + (c->ncy - jy) % c->ncy : l;
       if (l > partner) continue;
       rowmap.push_back(make_int2(l, partner));
       // l/2 in fine-grid steps: (-pi/2 + pi j / nc) / (2 pi / nf)
