@@ -103,7 +103,10 @@ struct tufrg_ctx {
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_kbps = 0, tc_ksplit = 0, tc_nrow_pad = 0, tc_tmem_cols = 0;
-  float4* d_tabf = nullptr;        // [nf] (xi, A, H, 0) in FP32 per scale
+  int tc_nsets = 1;                // accumulator sets per channel in TMEM
+  int tc_hx = 0, tc_hy = 0, tc_wy = 0;  // halo of the extended table, its row width
+  float4* d_ext = nullptr;         // [(nfx+2hx)*wy] (xi, A, H, 0) in FP32 per scale
+  int* d_rowoff = nullptr;         // [nrow] sx * wy + sy
   unsigned char* d_Fhi = nullptr;  // [tc_npad][tc_kpad] high parts of F (bf16 or tf32)
   unsigned char* d_Flo = nullptr;  // [tc_npad][tc_kpad] low parts
   float* d_partial_tc = nullptr;   // [tc_ksplit][2][tc_npad][tc_nrow_pad]

@@ -8,8 +8,9 @@
 // W_hi F_hi + W_lo F_hi + W_hi F_lo accumulated in FP32 in tensor memory;
 // the split-K partial sums of each CTA are combined in FP64 by a second
 // kernel.  The propagator operand W is generated in registers from the
-// per-scale FP32 table (xi, A = 1/(Omega + |xi|), H = |xi|(Omega + 3|xi|) A^3)
-// with the same closed-form frequency integral as the FP64 path, and written
+// per-scale FP32 table (xi, A = 1/(Omega + |xi|), H = |xi|(Omega + 3|xi|) A^3,
+// extended by a wrap-around halo so p +- l/2 is one add from p) with the same
+// closed-form frequency integral as the FP64 path, and written
 // straight into the 128B-swizzled K-major shared-memory layout the MMA reads;
 // F (scale independent) is staged with cp.async.  Both channels share W's
 // table reads and divisions and have their own accumulator.
@@ -167,14 +168,14 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 }
 
 struct TcArgs {
-  const float4* tab;
-  const int2* shift;
+  const float4* ext;      // per-scale table with a wrap-around halo, row width wy
+  const int* rowoff;      // [nrow] (sx * wy + sy): offset of p + l/2 from p
   const unsigned char* Fhi;
   const unsigned char* Flo;
   float* partial;
   int* err;
   const double* lam;
-  int nfx, nfy, kdim, kpad, kbps, nrow, nrow_pad, npad, tmem_cols;
+  int nfx, nfy, hx, hy, wy, kdim, kpad, kbps, nrow, nrow_pad, npad, nsets, tmem_cols;
 };
 
 template <int PREC>
@@ -194,12 +195,12 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   unsigned char* gctrl = gbase + 2u * stage_bytes;
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(gctrl + 48);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gctrl + 52);
-  int2* s_shift = reinterpret_cast<int2*>(gctrl + 64);
-  int* s_valid = reinterpret_cast<int*>(gctrl + 64 + 8 * kRows);
+  int* s_off = reinterpret_cast<int*>(gctrl + 64);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x, split = blockIdx.y;
   const int row0 = tile * kRows;
+  const int nvalid = min(kRows, a.nrow - row0);  // rows of this tile with an l
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
@@ -210,11 +211,8 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int r = threadIdx.x; r < kRows; r += kThreads) {
-    const int g = row0 + r;
-    s_shift[r] = g < a.nrow ? a.shift[g] : make_int2(0, 0);
-    s_valid[r] = g < a.nrow ? 1 : 0;
-  }
+  for (int r = threadIdx.x; r < kRows; r += kThreads)
+    s_off[r] = r < nvalid ? a.rowoff[row0 + r] : 0;
   if (warp == kProducers) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32((const void*)tmem_slot)),
@@ -234,6 +232,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 
   if (warp < kProducers) {
     // ------------------------------------------------------------ producers
+    // this lane writes bytes [col, col + 4) of rows r = warp + 16 i; all its
+    // rows have r % 8 == warp % 8, so the swizzled offset is fixed
+    const uint32_t col = (uint32_t)(P::kPerLane * lane) * P::kElem;
+    const uint32_t swz = (((col >> 4) ^ (uint32_t)(warp & 7)) << 4) | (col & 15);
+    const int center = a.hx * a.wy + a.hy;  // any in-range entry
     for (int kb = 0; kb < a.kbps; ++kb) {
       const int s = kb & 1;
       if (kb >= 2 && !mbar_wait(bar_empty + 8 * s, ((kb >> 1) + 1) & 1)) {
@@ -251,40 +254,38 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
         cp_async16(st + 4u * kWTile + t * ftile + row * kRowBytes + ((ch ^ (row & 7)) << 4), src);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
-      // W tiles: this lane's loop points
-      int2 pk[P::kPerLane];
+      // this lane's loop points as offsets into the halo table
+      int pb[P::kPerLane];
+      bool kok[P::kPerLane];
 #pragma unroll
-      for (int j = 0; j < P::kPerLane; ++j)
-        pk[j] = loop_point(k0 + P::kPerLane * lane + j, a.nfx, a.nfy, a.kdim);
-      const uint32_t col = (uint32_t)(P::kPerLane * lane) * P::kElem;  // byte within row
+      for (int j = 0; j < P::kPerLane; ++j) {
+        const int2 pk = loop_point(k0 + P::kPerLane * lane + j, a.nfx, a.nfy, a.kdim);
+        kok[j] = pk.x >= 0;
+        pb[j] = kok[j] ? (pk.x + a.hx) * a.wy + pk.y + a.hy : center;
+      }
 #pragma unroll 1
       for (int i0 = 0; i0 < kRows / kProducers; i0 += kBatch) {
-        // issue the table loads of kBatch rows first (memory-level parallelism);
-        // invalid entries load index 0 and are zeroed afterwards
+        // table loads of kBatch rows first (memory-level parallelism)
         float4 ta[kBatch][P::kPerLane], tb[kBatch][P::kPerLane];
-        bool ok[kBatch][P::kPerLane];
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
           const int r = warp + kProducers * (i0 + i);
-          const int2 sh = s_shift[r];
-          const bool valid = s_valid[r] != 0;
+          const int off = s_off[r];
 #pragma unroll
           for (int j = 0; j < P::kPerLane; ++j) {
-            ok[i][j] = valid && pk[j].x >= 0;
-            const int ax = wrap(pk[j].x + sh.x, a.nfx), ay = wrap(pk[j].y + sh.y, a.nfy);
-            const int bx = wrap(pk[j].x - sh.x, a.nfx), by = wrap(pk[j].y - sh.y, a.nfy);
-            ta[i][j] = __ldg(a.tab + (ok[i][j] ? ax * a.nfy + ay : 0));
-            tb[i][j] = __ldg(a.tab + (ok[i][j] ? bx * a.nfy + by : 0));
+            ta[i][j] = __ldg(a.ext + (pb[j] + off));
+            tb[i][j] = __ldg(a.ext + (pb[j] - off));
           }
         }
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
           const int r = warp + kProducers * (i0 + i);
           float wpp[P::kPerLane], wph[P::kPerLane];
+          const bool rv = r < nvalid;  // warp-uniform
 #pragma unroll
           for (int j = 0; j < P::kPerLane; ++j) {
             weights(ta[i][j], tb[i][j], om, om2, inv_om2, wpp[j], wph[j]);
-            if (!ok[i][j]) {
+            if (!(rv && kok[j])) {
               wpp[j] = 0.f;
               wph[j] = 0.f;
             }
@@ -307,11 +308,10 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
             v[2] = tf32_rna(wph[0]);
             v[3] = tf32_rna(wph[0] - __uint_as_float(v[2]));
           }
-          const uint32_t off = r * kRowBytes + ((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
+          const uint32_t dst = st + (uint32_t)r * kRowBytes + swz;
 #pragma unroll
           for (int t = 0; t < 4; ++t)
-            asm volatile("st.shared.b32 [%0], %1;" ::"r"(st + t * kWTile + off), "r"(v[t])
-                         : "memory");
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t]) : "memory");
         }
       }
       asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -321,6 +321,8 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     }
   } else if (lane == 0) {
     // --------------------------------------------------------- MMA issuer
+    // K-blocks go round-robin to nsets accumulator sets (shorter FP32
+    // accumulation chains); set q, channel c at TMEM columns (2 q + c) npad
     const uint32_t idesc = (1u << 4) | (P::kFormat << 7) | (P::kFormat << 10) |
                            ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
     for (int kb = 0; kb < a.kbps; ++kb) {
@@ -333,16 +335,18 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = base + s * stage_bytes;
       const uint32_t fh = st + 4u * kWTile, fl = fh + ftile;
+      const int set = kb % a.nsets;
+      const bool first = kb < a.nsets;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction
         const uint32_t o = 32u * kk;
         const uint64_t bh = smem_desc(fh + o), bl = smem_desc(fl + o);
 #pragma unroll
         for (int ch = 0; ch < 2; ++ch) {
-          const uint32_t d = tmem + ch * npad;
+          const uint32_t d = tmem + (uint32_t)((2 * set + ch) * npad);
           const uint64_t ah = smem_desc(st + (2 * ch) * kWTile + o);
           const uint64_t al = smem_desc(st + (2 * ch + 1) * kWTile + o);
-          mma<PREC>(d, ah, bh, idesc, (kb | kk) != 0);
+          mma<PREC>(d, ah, bh, idesc, !(first && kk == 0));
           mma<PREC>(d, al, bh, idesc, 1);
           mma<PREC>(d, ah, bl, idesc, 1);
         }
@@ -363,20 +367,29 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     if (ok && !*abort_flag) {
       const int quad = warp & 3, ch = warp >> 2;
       const int row = quad * 32 + lane;
+      const int sets = min(a.nsets, a.kbps);
       float* out = a.partial + (size_t)(split * 2 + ch) * npad * a.nrow_pad + row0 + row;
       for (int c0 = 0; c0 < npad; c0 += 16) {
-        uint32_t r[16];
-        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + ch * npad + c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-            "%10, %11, %12, %13, %14, %15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float acc[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) out[(size_t)(c0 + j) * a.nrow_pad] = __uint_as_float(r[j]);
+        for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+        for (int q = 0; q < sets; ++q) {
+          uint32_t r[16];
+          const uint32_t taddr =
+              tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((2 * q + ch) * npad + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+              "%10, %11, %12, %13, %14, %15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(r[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) out[(size_t)(c0 + j) * a.nrow_pad] = acc[j];
       }
     }
   }
@@ -390,14 +403,21 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   }
 }
 
-// FP32 per-scale table from the FP64 dispersion table.
-__global__ void scale_tables_f32_kernel(const double4_32a* __restrict__ tab,
-                                        float4* __restrict__ tabf, int nf,
-                                        const double* __restrict__ lam) {
+// Per-scale FP32 table (xi, A, H, 0) with a wrap-around halo of hx, hy
+// points on each side, so that p +- l/2 needs no wrapping.
+__global__ void scale_table_ext_kernel(const double4_32a* __restrict__ tab,
+                                       float4* __restrict__ ext, int nfx, int nfy, int hx,
+                                       int hy, int wy, int n_ext,
+                                       const double* __restrict__ lam) {
   const double om = lam[0];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
-    const double xi = tab[i].x, x = fabs(xi), A = 1.0 / (om + x);
-    tabf[i] = make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), 0.f);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_ext; e += gridDim.x * blockDim.x) {
+    int ix = e / wy - hx, iy = e % wy - hy;
+    ix += ix < 0 ? nfx : 0;
+    ix -= ix >= nfx ? nfx : 0;
+    iy += iy < 0 ? nfy : 0;
+    iy -= iy >= nfy ? nfy : 0;
+    const double xi = tab[ix * nfy + iy].x, x = fabs(xi), A = 1.0 / (om + x);
+    ext[e] = make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), 0.f);
   }
 }
 
@@ -432,8 +452,7 @@ __global__ void loops_tc_reduce_kernel(const float* __restrict__ partial, int ks
 }  // namespace
 
 size_t tc_smem_bytes(int npad) {
-  return 1024 + 2 * (4 * (size_t)kWTile + 2 * (size_t)npad * kRowBytes) + 64 + 8 * kRows +
-         4 * kRows;
+  return 1024 + 2 * (4 * (size_t)kWTile + 2 * (size_t)npad * kRowBytes) + 64 + 4 * kRows;
 }
 
 tufrg_status prepare_loops_tc(tufrg_ctx* c) {
@@ -448,12 +467,14 @@ tufrg_status prepare_loops_tc(tufrg_ctx* c) {
 }
 
 tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi, cudaStream_t st) {
-  const int blocks = std::min((c->nf + 255) / 256, 152 * 8);
-  scale_tables_f32_kernel<<<blocks, 256, 0, st>>>(c->d_tab, c->d_tabf, c->nf, c->d_lambda);
+  const int n_ext = (c->nfx + 2 * c->tc_hx) * c->tc_wy;
+  const int blocks = std::min((n_ext + 255) / 256, 152 * 8);
+  scale_table_ext_kernel<<<blocks, 256, 0, st>>>(c->d_tab, c->d_ext, c->nfx, c->nfy, c->tc_hx,
+                                                 c->tc_hy, c->tc_wy, n_ext, c->d_lambda);
   TUFRG_CUDA(cudaGetLastError());
   TcArgs a;
-  a.tab = c->d_tabf;
-  a.shift = c->d_shift;
+  a.ext = c->d_ext;
+  a.rowoff = c->d_rowoff;
   a.Fhi = c->d_Fhi;
   a.Flo = c->d_Flo;
   a.partial = c->d_partial_tc;
@@ -461,12 +482,16 @@ tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi, cudaStream_t st) {
   a.lam = c->d_lambda;
   a.nfx = c->nfx;
   a.nfy = c->nfy;
+  a.hx = c->tc_hx;
+  a.hy = c->tc_hy;
+  a.wy = c->tc_wy;
   a.kdim = c->kdim;
   a.kpad = c->tc_kpad;
   a.kbps = c->tc_kbps;
   a.nrow = c->nrow;
   a.nrow_pad = c->tc_nrow_pad;
   a.npad = c->tc_npad;
+  a.nsets = c->tc_nsets;
   a.tmem_cols = c->tc_tmem_cols;
   const dim3 grid(c->tc_nrow_pad / kRows, c->tc_ksplit);
   const size_t smem = tc_smem_bytes(c->tc_npad);

@@ -287,9 +287,20 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
     c->tc_kbps = (nkb + ks - 1) / ks;
     c->tc_ksplit = (nkb + c->tc_kbps - 1) / c->tc_kbps;
     c->tc_kpad = c->tc_ksplit * c->tc_kbps * kb;
+    // accumulator sets: as many (<= 4) as fit the 512 TMEM columns
+    c->tc_nsets = 1;
+    while (c->tc_nsets < 4 && 2 * c->tc_nsets * 2 * c->tc_npad <= 512) c->tc_nsets *= 2;
     int cols = 32;
-    while (cols < 2 * c->tc_npad) cols *= 2;
+    while (cols < c->tc_nsets * 2 * c->tc_npad) cols *= 2;
     c->tc_tmem_cols = cols;
+    // halo table and per-row offsets of p + l/2
+    c->tc_hx = c->nfx / 4;
+    c->tc_hy = c->nfy / 4;
+    c->tc_wy = c->nfy + 2 * c->tc_hy;
+    std::vector<int> rowoff(c->nrow);
+    for (int r = 0; r < c->nrow; ++r) rowoff[r] = rowshift[r].x * c->tc_wy + rowshift[r].y;
+    TUFRG_CHECK(upload(&c->d_rowoff, rowoff, st));
+    TUFRG_CHECK(alloc(&c->d_ext, (size_t)(c->nfx + 2 * c->tc_hx) * c->tc_wy));
     std::vector<unsigned char> fh((size_t)c->tc_npad * c->tc_kpad * es, 0);
     std::vector<unsigned char> fl(fh.size(), 0);
     for (int q = 0; q < c->npair; ++q)
@@ -312,7 +323,6 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
       }
     TUFRG_CHECK(upload(&c->d_Fhi, fh, st));
     TUFRG_CHECK(upload(&c->d_Flo, fl, st));
-    TUFRG_CHECK(alloc(&c->d_tabf, (size_t)c->nf));
     TUFRG_CHECK(alloc(&c->d_partial_tc, (size_t)c->tc_ksplit * 2 * c->tc_npad * c->tc_nrow_pad));
     TUFRG_CHECK(prepare_loops_tc(c));
   }
@@ -377,7 +387,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
 
 void free_device(tufrg_ctx* c) {
   free_flow(c);
-  void* ptrs[] = {c->d_tabf, c->d_Fhi, c->d_Flo, c->d_partial_tc, c->d_err,
+  void* ptrs[] = {c->d_ext, c->d_rowoff, c->d_Fhi, c->d_Flo, c->d_partial_tc, c->d_err,
                   c->d_rowmap, c->d_tab, c->d_kidx, c->d_F,       c->d_shift,   c->d_pair,
                   c->d_coef, c->d_phase,  c->d_key,     c->d_row_ptr, c->d_terms,
                   c->d_lambda, c->d_partial, c->d_chi,  c->d_V,       c->d_bt,
