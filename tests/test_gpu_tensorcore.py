@@ -5,7 +5,10 @@ Bar (reduced-precision paths): loops and couplings within 1e-4 relative
 max-norm of the FP64 oracle, Lambda_c within 1 %.  The tests assert tighter
 per-precision bounds derived from the split arithmetic: BF16x3 keeps ~16
 mantissa bits per operand (products ~2^-16 relative), 3xTF32 ~22 bits, FP32
-accumulation over <= 8192 loop points per CTA, FP64 across CTAs.
+FP32 accumulation in TMEM (the tensor core rounds the accumulator at every
+MMA instruction, so the error grows with the chain length: K-blocks go
+round-robin to up to four accumulator sets), FP64 across CTAs.  Measured on
+GB300: ~2e-6 (BF16x3) and ~3e-7 / 6e-6 (3xTF32, short / production chains).
 """
 import os
 
@@ -19,7 +22,7 @@ from tests.test_gpu_parity import CASES, dev, make, rel
 
 pytestmark = pytest.mark.gpu
 
-BOUND = {"bf16x3": 5e-5, "3xtf32": 5e-6}
+BOUND = {"bf16x3": 1e-5, "3xtf32": 1e-5}
 
 
 @pytest.fixture(scope="module")
