@@ -214,7 +214,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "3xtf32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "3xtf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flow-time", action="store_true")
     args = ap.parse_args()
@@ -366,17 +366,29 @@ def main():
 
     flow_info = None
     if not args.no_flow_time:
-        y0 = solver.zeros(3)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        _, res, _ = solver.flow(y0, **flow_kw)
-        e1.record()
-        e1.synchronize()
-        flow_info = {"flow_time_to_lambda_c_s": e0.elapsed_time(e1) / 1e3,
-                     "lambda_c": res["lambda_c"], "diverged": res["diverged"],
-                     "kind": res["kind"], "l_index": res["l_index"], "m": res["m"],
-                     "n": res["n"], "rhs_evals": res["n_rhs"]}
+        # full flow to Lambda_c: this precision vs the plain FP64 GPU flow
+        def timed_flow(s):
+            y0 = s.zeros(3)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record()
+            _, res, _ = s.flow(y0, **flow_kw)
+            f1.record()
+            f1.synchronize()
+            return {"flow_time_to_lambda_c_s": f0.elapsed_time(f1) / 1e3,
+                    "lambda_c": res["lambda_c"], "diverged": res["diverged"],
+                    "kind": res["kind"], "l_index": res["l_index"], "m": res["m"],
+                    "n": res["n"], "rhs_evals": res["n_rhs"]}
+        flow_info = {args.precision: timed_flow(solver)}
+        if args.precision != "fp64":
+            ref = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]),
+                               c["nc"], c["nf"], precision="fp64")
+            flow_info["fp64"] = timed_flow(ref)
+            ref.close()
+            a, b = flow_info[args.precision], flow_info["fp64"]
+            flow_info["speedup_vs_fp64_gpu"] = (b["flow_time_to_lambda_c_s"]
+                                                / a["flow_time_to_lambda_c_s"])
+            flow_info["lambda_c_rel_diff_vs_fp64_gpu"] = abs(a["lambda_c"] / b["lambda_c"] - 1)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

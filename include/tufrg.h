@@ -106,6 +106,9 @@ typedef struct {
   double* checkpoint_states_dev; /* [n_checkpoints][3][Nl][Nff][Nff]; entries of
                                     scales not reached are left untouched; must stay
                                     valid until the flow has finished */
+  double fp64_above;      /* > 0: once an accepted step has max |B| above this, the
+                             loops of the remaining steps run in FP64 (a context set up
+                             with a tensor-core precision only); 0: never switch */
 } tufrg_flow_opts;
 
 /* Result of tufrg_flow / tufrg_flow_step / tufrg_flow_state. */
@@ -118,6 +121,7 @@ typedef struct {
   int32_t l_index, m, n;  /* location of max |B| in the state (smallest flat index);
                              filled by tufrg_flow and tufrg_flow_state */
   double max_abs;         /* max |B| of the state (tufrg_flow, tufrg_flow_state) */
+  double lambda_switch;   /* scale after which the loops ran in FP64 (0: no switch) */
   int64_t n_rhs, n_accepted, n_rejected;
 } tufrg_result;
 

@@ -90,13 +90,14 @@ class Solver:
         return out
 
     def _opts(self, lambda0, lambda_min, threshold, rtol, atol, h0, method, max_steps,
-              checkpoints):
+              checkpoints, fp64_above=0.0):
         import torch
         o = _abi.tufrg_flow_opts()
         o.lambda0, o.lambda_min, o.threshold = float(lambda0), float(lambda_min), float(threshold)
         o.rtol, o.atol, o.h0 = float(rtol), float(atol), float(h0)
         o.method = TUFRG_RK4 if method == "rk4" else TUFRG_DOPRI5
         o.max_steps = int(max_steps)
+        o.fp64_above = float(fp64_above)
         cks = np.ascontiguousarray(np.asarray(checkpoints, dtype=np.float64))
         states = torch.zeros((len(cks), 3, self.nl, self.nff, self.nff), dtype=torch.float64,
                              device="cuda")
@@ -114,22 +115,23 @@ class Solver:
         return d
 
     def flow(self, y=None, lambda0=10.0, lambda_min=1e-3, threshold=50.0, rtol=1e-8,
-             atol=1e-10, h0=0.05, method="dopri5", max_steps=100000, checkpoints=()):
+             atol=1e-10, h0=0.05, method="dopri5", max_steps=100000, checkpoints=(),
+             fp64_above=0.0):
         """Integrates the flow in place of y (zeros = bare U start).
 
         Returns (y, result dict, checkpoint states [n][3][Nl][Nff][Nff])."""
         y = self.zeros(3) if y is None else y
         o, states = self._opts(lambda0, lambda_min, threshold, rtol, atol, h0, method,
-                               max_steps, checkpoints)
+                               max_steps, checkpoints, fp64_above)
         r = tufrg_flow(self.ctx, o, self._check(y, 3), _stream())
         return y, self._result(r), states
 
     def flow_init(self, y0=None, lambda0=10.0, lambda_min=1e-3, threshold=50.0, rtol=1e-8,
-                  atol=1e-10, h0=0.05, method="dopri5", checkpoints=()):
+                  atol=1e-10, h0=0.05, method="dopri5", checkpoints=(), fp64_above=0.0):
         """Starts a stepwise flow; returns the checkpoint-state tensor."""
         y0 = self.zeros(3) if y0 is None else y0
         o, states = self._opts(lambda0, lambda_min, threshold, rtol, atol, h0, method, 1,
-                               checkpoints)
+                               checkpoints, fp64_above)
         tufrg_flow_init(self.ctx, o, self._check(y0, 3), _stream())
         return states
 

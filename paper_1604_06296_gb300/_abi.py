@@ -39,13 +39,15 @@ class tufrg_flow_opts(Structure):
     _fields_ = [("lambda0", c_double), ("lambda_min", c_double), ("threshold", c_double),
                 ("rtol", c_double), ("atol", c_double), ("h0", c_double),
                 ("method", c_int32), ("max_steps", c_int32), ("n_checkpoints", c_int32),
-                ("checkpoints", POINTER(c_double)), ("checkpoint_states_dev", c_void_p)]
+                ("checkpoints", POINTER(c_double)), ("checkpoint_states_dev", c_void_p),
+                ("fp64_above", c_double)]
 
 
 class tufrg_result(Structure):
     _fields_ = [("lambda_c", c_double), ("h_next", c_double), ("diverged", c_int32),
                 ("finished", c_int32), ("channel", c_int32), ("l_index", c_int32),
                 ("m", c_int32), ("n", c_int32), ("max_abs", c_double),
+                ("lambda_switch", c_double),
                 ("n_rhs", c_int64), ("n_accepted", c_int64), ("n_rejected", c_int64)]
 
     def as_dict(self):

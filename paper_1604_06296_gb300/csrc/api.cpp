@@ -33,17 +33,17 @@ tufrg_status validate(const tufrg_params* p) {
 
 namespace tufrg {
 
-tufrg_status launch_loops(tufrg_ctx* c, double* chi, cudaStream_t st) {
-  if (c->p.precision == TUFRG_FP64) {
+tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) {
+  if (prec == TUFRG_FP64) {
     TUFRG_CHECK(launch_scale_tables(c, st));
     return launch_loops_fp64(c, chi, st);
   }
   return launch_loops_tc(c, chi, st);
 }
 
-tufrg_status rhs_device(tufrg_ctx* c, const double* y, double* dy, const double* d_scale,
-                        cudaStream_t st) {
-  TUFRG_CHECK(launch_loops(c, c->d_chi, st));
+tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy,
+                        const double* d_scale, cudaStream_t st) {
+  TUFRG_CHECK(launch_loops(c, prec, c->d_chi, st));
   TUFRG_CHECK(launch_project(c, y, c->d_V, st));
   TUFRG_CHECK(launch_products(c, c->d_V, c->d_chi, dy, d_scale, st));
   return TUFRG_OK;
@@ -78,6 +78,7 @@ tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** o
   c->nf = c->nfx * c->nfy;
   c->nff = c->basis.nff;
   c->nb = c->basis.nb;
+  c->loop_prec = p->precision;
   s = tufrg::setup_device(c, (cudaStream_t)cuda_stream);
   if (s != TUFRG_OK) {
     tufrg::free_device(c);
@@ -120,7 +121,7 @@ tufrg_status tufrg_loops(tufrg_ctx* c, double lambda, double* chi_dot_dev, void*
   if (!c || !chi_dot_dev || !finite_pos(lambda)) return TUFRG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
-  return tufrg::launch_loops(c, chi_dot_dev, st);
+  return tufrg::launch_loops(c, c->p.precision, chi_dot_dev, st);
 }
 
 tufrg_status tufrg_project(tufrg_ctx* c, const double* y_dev, double* v_dev, void* stream) {
@@ -140,7 +141,7 @@ tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double*
   if (!c || !y_dev || !dy_dev || y_dev == dy_dev || !finite_pos(lambda)) return TUFRG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
-  return tufrg::rhs_device(c, y_dev, dy_dev, nullptr, st);
+  return tufrg::rhs_device(c, c->p.precision, y_dev, dy_dev, nullptr, st);
 }
 
 namespace {
@@ -158,6 +159,7 @@ tufrg_status check_opts(const tufrg_flow_opts* o) {
     return TUFRG_ERR_ARG;
   for (int i = 0; i < o->n_checkpoints; ++i)
     if (!finite_pos(o->checkpoints[i])) return TUFRG_ERR_ARG;
+  if (!(o->fp64_above >= 0.0) || !std::isfinite(o->fp64_above)) return TUFRG_ERR_ARG;
   return TUFRG_OK;
 }
 

@@ -48,6 +48,7 @@ struct FlowCtl {
   double bis_a, bis_b;
   int nonfinite, accepted, last_rejected, crossed, done, status;
   long long n_acc, n_rej, n_rhs;
+  double ymax_last;  // max |y| after the last accepted step
 };
 
 struct Combo {
@@ -131,6 +132,7 @@ __global__ void control_kernel(FlowCtl* c) {
     c->accepted = 1;
     c->n_acc += 1;
     const double ymax = __longlong_as_double((long long)c->max_u);
+    c->ymax_last = ymax;
     c->crossed = ymax > c->thr;
     c->h = c->h * fac;
     c->last_rejected = 0;
@@ -247,7 +249,9 @@ struct FlowState {
   size_t bytes = 0;
   double *y, *k[7], *ytmp, *ynew, *yprev, *k1prev;
   FlowCtl* ctl = nullptr;
-  cudaGraphExec_t attempt = nullptr;
+  cudaGraphExec_t attempt[2] = {nullptr, nullptr};  // [loops in FP64]
+  double fp64_above = 0.0;
+  double lambda_switch = 0.0;
 };
 
 namespace {
@@ -262,8 +266,10 @@ tufrg_status ensure_buffers(tufrg_ctx* c) {
   const size_t n = c->state_elems();
   const size_t need = sizeof(double) * n * 12 + 1024;
   if (f.bytes < need) {
-    if (f.attempt) cudaGraphExecDestroy(f.attempt);
-    f.attempt = nullptr;
+    for (auto& g : f.attempt) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
     if (f.base) cudaFree(f.base);
     f.base = nullptr;
     f.bytes = 0;
@@ -295,7 +301,7 @@ tufrg_status stage(tufrg_ctx* c, const double* y, double* out,
   const size_t n = c->state_elems();
   combo_kernel<<<grid_for(n), 256, 0, st>>>(y, out, cb, f.ctl, c->d_lambda, n, 1);
   TUFRG_CUDA(cudaGetLastError());
-  return rhs_device(c, out, k_out, c->d_lambda + 1, st);
+  return rhs_device(c, c->loop_prec, out, k_out, c->d_lambda + 1, st);
 }
 
 // One DoPri5 attempt: stages 2..7, error norm, control, accept.
@@ -379,9 +385,11 @@ tufrg_status checkpoints_in_last_step(tufrg_ctx* c, cudaStream_t st) {
   return TUFRG_OK;
 }
 
-tufrg_status dopri5_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
+// The attempt graph of the current loop precision (captured on first use).
+tufrg_status attempt_graph(tufrg_ctx* c, cudaStream_t st, cudaGraphExec_t* out) {
   FlowState& f = *c->flow;
-  if (!f.attempt) {
+  const int which = c->loop_prec == TUFRG_FP64 ? 1 : 0;
+  if (!f.attempt[which]) {
     cudaGraph_t g = nullptr;
     TUFRG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     tufrg_status s = enqueue_attempt(c, st);
@@ -391,13 +399,26 @@ tufrg_status dopri5_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
       return s;
     }
     TUFRG_CUDA(e);
-    e = cudaGraphInstantiate(&f.attempt, g, 0);
+    e = cudaGraphInstantiate(&f.attempt[which], g, 0);
     cudaGraphDestroy(g);
     TUFRG_CUDA(e);
   }
+  *out = f.attempt[which];
+  return TUFRG_OK;
+}
+
+tufrg_status dopri5_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
+  FlowState& f = *c->flow;
   for (int i = 0; i < n_steps && !f.finished; ++i) {
-    TUFRG_CUDA(cudaGraphLaunch(f.attempt, st));
+    cudaGraphExec_t g = nullptr;
+    TUFRG_CHECK(attempt_graph(c, st, &g));
+    TUFRG_CUDA(cudaGraphLaunch(g, st));
     TUFRG_CHECK(read_ctl(c, st));
+    if (f.hc->accepted && f.fp64_above > 0.0 && c->loop_prec != TUFRG_FP64 &&
+        f.hc->ymax_last > f.fp64_above) {
+      c->loop_prec = TUFRG_FP64;  // near the divergence: the remaining loops in FP64
+      f.lambda_switch = std::exp(f.hc->s);
+    }
     if (f.hc->status != TUFRG_OK) {
       f.finished = true;
       return (tufrg_status)f.hc->status;
@@ -471,6 +492,7 @@ void fill_progress(tufrg_ctx* c, tufrg_result* r) {
   r->n_accepted = f.hc->n_acc;
   r->n_rejected = f.hc->n_rej;
   r->n_rhs = f.method == TUFRG_RK4 ? f.rk4_rhs : 1 + f.hc->n_rhs;
+  r->lambda_switch = f.lambda_switch;
 }
 
 }  // namespace
@@ -478,7 +500,8 @@ void fill_progress(tufrg_ctx* c, tufrg_result* r) {
 void free_flow(tufrg_ctx* c) {
   if (!c->flow) return;
   FlowState& f = *c->flow;
-  if (f.attempt) cudaGraphExecDestroy(f.attempt);
+  for (auto& g : f.attempt)
+    if (g) cudaGraphExecDestroy(g);
   if (f.base) cudaFree(f.base);
   if (f.hc) cudaFreeHost(f.hc);
   delete c->flow;
@@ -493,6 +516,9 @@ tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
   f.finished = f.crossed = false;
   f.method = o->method;
   f.threshold = o->threshold;
+  f.fp64_above = o->fp64_above;
+  f.lambda_switch = 0.0;
+  c->loop_prec = c->p.precision;  // every flow starts in the context's precision
   f.rk4_rhs = 0;
   f.cks.clear();
   for (int i = 0; i < o->n_checkpoints; ++i) f.cks.push_back({std::log(o->checkpoints[i]), i});

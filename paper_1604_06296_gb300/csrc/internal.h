@@ -104,6 +104,7 @@ struct tufrg_ctx {
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_kbps = 0, tc_ksplit = 0, tc_nrow_pad = 0, tc_tmem_cols = 0;
   int tc_nsets = 1;                // accumulator sets per channel in TMEM
+  int loop_prec = TUFRG_FP64;      // precision of the flow's next loop contractions
   int tc_hx = 0, tc_hy = 0, tc_wy = 0;  // halo of the extended table, its row width
   float4* d_ext = nullptr;         // [(nfx+2hx)*wy] (xi, A, H, 0) in FP32 per scale
   int* d_rowoff = nullptr;         // [nrow] sx * wy + sy
@@ -143,16 +144,17 @@ tufrg_status launch_products(tufrg_ctx* c, const double* v, const double* chi, d
                              const double* d_scale, cudaStream_t st);
 tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 
-// steps i-iii at the scale stored in c->d_lambda; dy scaled by *d_scale if non-null
-tufrg_status rhs_device(tufrg_ctx* c, const double* y, double* dy, const double* d_scale,
-                        cudaStream_t st);
+// steps i-iii at the scale stored in c->d_lambda with loops in precision prec;
+// dy scaled by *d_scale if non-null
+tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy,
+                        const double* d_scale, cudaStream_t st);
 
 tufrg_status prepare_products(tufrg_ctx* c);
 tufrg_status prepare_loops_tc(tufrg_ctx* c);
 size_t tc_smem_bytes(int npad);
 tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi_out, cudaStream_t st);
-// loops in the context's precision
-tufrg_status launch_loops(tufrg_ctx* c, double* chi_out, cudaStream_t st);
+// loops in the given precision (the context's, or FP64)
+tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi_out, cudaStream_t st);
 
 // The FP64 loop contraction on explicitly given buffers (same kernels and
 // layouts as launch_loops_fp64, without a context).

@@ -4,7 +4,7 @@ oracle, through the C ABI.
 Bar (reduced-precision paths): loops and couplings within 1e-4 relative
 max-norm of the FP64 oracle, Lambda_c within 1 %.  The tests assert tighter
 per-precision bounds derived from the split arithmetic: BF16x3 keeps ~16
-mantissa bits per operand (products ~2^-16 relative), 3xTF32 ~22 bits, FP32
+mantissa bits per operand (products ~2^-16 relative), 3xTF32 ~22 bits;
 FP32 accumulation in TMEM (the tensor core rounds the accumulator at every
 MMA instruction, so the error grows with the chain length: K-blocks go
 round-robin to up to four accumulator sets), FP64 across CTAs.  Measured on
@@ -95,6 +95,24 @@ def test_flow_cfg1_tensor_core_against_oracle(torch, precision):
         e = rel(states[i].cpu().numpy(), g["y_checkpoints"][i])
         print(f"  checkpoint {lam}: rel err {e:.2e}")
         assert e < 1e-4
+
+
+def test_flow_switches_to_fp64_near_the_divergence(torch):
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "flow_cfg1.npz"))
+    c = W.config("cfg1")
+    s, p = make("cfg1", torch, precision="bf16x3")
+    y, res, _ = s.flow(lambda0=c["lambda0"], lambda_min=c["lambda_min"],
+                       threshold=c["threshold"], rtol=1e-8, atol=1e-10, h0=0.05, fp64_above=5.0)
+    check_device(s)
+    dl = abs(res["lambda_c"] / float(g["lambda_c"]) - 1)
+    print(f"bf16x3 -> fp64 above |B| = 5: Lambda_c rel err {dl:.2e}, "
+          f"switch at Lambda = {res['lambda_switch']:.5f}")
+    assert res["diverged"] and dl < 1e-5
+    assert res["lambda_switch"] > res["lambda_c"]
+    # the context's own precision is untouched for later calls
+    got = s.loops(0.3).cpu().numpy()
+    ref = np.stack(olo.chi_dot(p, 0.3))
+    assert 1e-9 < rel(got, ref) < BOUND["bf16x3"]
 
 
 def test_basis_too_large_for_tensor_core_path_rejected(torch):
