@@ -67,9 +67,11 @@ typedef enum {
 } tufrg_status;
 
 typedef enum {
-  TUFRG_FP64 = 0,    /* loops in FP64 (DFMA) */
-  TUFRG_3XTF32 = 1,  /* loops on tcgen05, kind::tf32, hi/lo split, 3 products */
-  TUFRG_BF16X3 = 2   /* loops on tcgen05, kind::f16 (bf16), hi/lo split, 3 products */
+  TUFRG_FP64 = 0,    /* everything in FP64 (loops on DFMA) */
+  TUFRG_3XTF32 = 1,  /* loops on tcgen05, kind::tf32, hi/lo split, 3 products, FP32
+                        accumulation; projections and products in FP32 arithmetic;
+                        state, derivative, step control in FP64 */
+  TUFRG_BF16X3 = 2   /* as 3XTF32 with kind::f16 (bf16) hi/lo operands */
 } tufrg_precision;
 
 typedef enum {

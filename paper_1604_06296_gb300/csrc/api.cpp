@@ -44,8 +44,8 @@ tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) 
 tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy,
                         const double* d_scale, cudaStream_t st) {
   TUFRG_CHECK(launch_loops(c, prec, c->d_chi, st));
-  TUFRG_CHECK(launch_project(c, y, c->d_V, st));
-  TUFRG_CHECK(launch_products(c, c->d_V, c->d_chi, dy, d_scale, st));
+  TUFRG_CHECK(launch_project(c, prec, y, c->d_V, st));
+  TUFRG_CHECK(launch_products(c, prec, c->d_V, c->d_chi, dy, d_scale, st));
   return TUFRG_OK;
 }
 
@@ -126,14 +126,15 @@ tufrg_status tufrg_loops(tufrg_ctx* c, double lambda, double* chi_dot_dev, void*
 
 tufrg_status tufrg_project(tufrg_ctx* c, const double* y_dev, double* v_dev, void* stream) {
   if (!c || !y_dev || !v_dev || y_dev == v_dev) return TUFRG_ERR_ARG;
-  return tufrg::launch_project(c, y_dev, v_dev, (cudaStream_t)stream);
+  return tufrg::launch_project(c, c->p.precision, y_dev, v_dev, (cudaStream_t)stream);
 }
 
 tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi_dot_dev,
                             double* dy_dev, void* stream) {
   if (!c || !v_dev || !chi_dot_dev || !dy_dev || dy_dev == v_dev || dy_dev == chi_dot_dev)
     return TUFRG_ERR_ARG;
-  return tufrg::launch_products(c, v_dev, chi_dot_dev, dy_dev, nullptr, (cudaStream_t)stream);
+  return tufrg::launch_products(c, c->p.precision, v_dev, chi_dot_dev, dy_dev, nullptr,
+                                (cudaStream_t)stream);
 }
 
 tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double* dy_dev,

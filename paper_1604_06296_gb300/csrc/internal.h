@@ -139,9 +139,11 @@ void free_device(tufrg_ctx* c);
 // kernels (launchers)
 tufrg_status launch_scale_tables(tufrg_ctx* c, cudaStream_t st);
 tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi_out, cudaStream_t st);
-tufrg_status launch_project(tufrg_ctx* c, const double* y, double* v, cudaStream_t st);
-tufrg_status launch_products(tufrg_ctx* c, const double* v, const double* chi, double* dy,
-                             const double* d_scale, cudaStream_t st);
+// projections and products: FP64 arithmetic when prec == TUFRG_FP64, else FP32
+tufrg_status launch_project(tufrg_ctx* c, int prec, const double* y, double* v,
+                            cudaStream_t st);
+tufrg_status launch_products(tufrg_ctx* c, int prec, const double* v, const double* chi,
+                             double* dy, const double* d_scale, cudaStream_t st);
 tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 
 // steps i-iii at the scale stored in c->d_lambda with loops in precision prec;

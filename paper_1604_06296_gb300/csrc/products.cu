@@ -4,44 +4,50 @@
 //   dD =  2 V^D chi^ph V^D - V^C chi^ph V^D - V^D chi^ph V^C
 //      =  (2 V^D - V^C) (chi^ph V^D) - V^D (chi^ph V^C)
 // One CTA per l; the five Nff x Nff operands and three intermediate products
-// sit in shared memory (8 Nff^2 doubles <= 54 KB for Nff = 29).
+// sit in shared memory (8 Nff^2 doubles <= 54 KB for Nff = 29).  FP64 for an
+// FP64 context, FP32 arithmetic for the mixed-precision contexts.
 #include "internal.h"
 
 namespace tufrg {
 namespace {
 
-__device__ __forceinline__ void matmul(const double* __restrict__ a, const double* __restrict__ b,
-                                       double* __restrict__ c, int n) {
+template <class T>
+__device__ __forceinline__ void matmul(const T* __restrict__ a, const T* __restrict__ b,
+                                       T* __restrict__ c, int n) {
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    double s = 0.0;
+    T s = 0;
     for (int k = 0; k < n; ++k) s = fma(a[i * n + k], b[k * n + j], s);
     c[e] = s;
   }
 }
 
+// arithmetic in T (FP64, or FP32 for the mixed-precision contexts); inputs
+// and the derivative are FP64
+template <class T>
 __global__ void products_kernel(const double* __restrict__ v, const double* __restrict__ chi,
                                 double* __restrict__ dy, int nl, int nff,
                                 const double* __restrict__ scale) {
-  extern __shared__ double sm[];
+  extern __shared__ double smd[];
+  T* sm = reinterpret_cast<T*>(smd);
   const int n2 = nff * nff;
-  double* VP = sm;
-  double* VC = VP + n2;
-  double* VD = VC + n2;
-  double* Xp = VD + n2;
-  double* Xh = Xp + n2;
-  double* T1 = Xh + n2;
-  double* T2 = T1 + n2;
-  double* T3 = T2 + n2;
+  T* VP = sm;
+  T* VC = VP + n2;
+  T* VD = VC + n2;
+  T* Xp = VD + n2;
+  T* Xh = Xp + n2;
+  T* T1 = Xh + n2;
+  T* T2 = T1 + n2;
+  T* T3 = T2 + n2;
   const int l = blockIdx.x;
   const size_t chan = (size_t)nl * n2;
   const size_t off = (size_t)l * n2;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
-    VP[e] = v[off + e];
-    VC[e] = v[chan + off + e];
-    VD[e] = v[2 * chan + off + e];
-    Xp[e] = chi[off + e];
-    Xh[e] = chi[chan + off + e];
+    VP[e] = (T)v[off + e];
+    VC[e] = (T)v[chan + off + e];
+    VD[e] = (T)v[2 * chan + off + e];
+    Xp[e] = (T)chi[off + e];
+    Xh[e] = (T)chi[chan + off + e];
   }
   __syncthreads();
   matmul(Xp, VP, T1, nff);  // chi^pp V^P
@@ -51,16 +57,16 @@ __global__ void products_kernel(const double* __restrict__ v, const double* __re
   const double sc = scale ? scale[0] : 1.0;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
     const int i = e / nff, j = e % nff;
-    double p = 0.0, cc = 0.0, d = 0.0;
+    T p = 0, cc = 0, d = 0;
     for (int k = 0; k < nff; ++k) {
       p = fma(VP[i * nff + k], T1[k * nff + j], p);
       cc = fma(VC[i * nff + k], T2[k * nff + j], cc);
-      d = fma(2.0 * VD[i * nff + k] - VC[i * nff + k], T3[k * nff + j], d);
+      d = fma(2 * VD[i * nff + k] - VC[i * nff + k], T3[k * nff + j], d);
       d = fma(-VD[i * nff + k], T2[k * nff + j], d);
     }
-    dy[off + e] = sc * p;
-    dy[chan + off + e] = -sc * cc;
-    dy[2 * chan + off + e] = sc * d;
+    dy[off + e] = sc * (double)p;
+    dy[chan + off + e] = -sc * (double)cc;
+    dy[2 * chan + off + e] = sc * (double)d;
   }
 }
 
@@ -68,16 +74,24 @@ __global__ void products_kernel(const double* __restrict__ v, const double* __re
 
 tufrg_status prepare_products(tufrg_ctx* c) {
   const size_t smem = sizeof(double) * 8 * c->nff * c->nff;
-  if (smem > 48 * 1024)
-    TUFRG_CUDA(cudaFuncSetAttribute(products_kernel,
+  if (smem > 48 * 1024) {
+    TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<double>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<float>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
   return TUFRG_OK;
 }
 
-tufrg_status launch_products(tufrg_ctx* c, const double* v, const double* chi, double* dy,
-                             const double* d_scale, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 8 * c->nff * c->nff;
-  products_kernel<<<c->nl, 256, smem, st>>>(v, chi, dy, c->nl, c->nff, d_scale);
+tufrg_status launch_products(tufrg_ctx* c, int prec, const double* v, const double* chi,
+                             double* dy, const double* d_scale, cudaStream_t st) {
+  if (prec == TUFRG_FP64) {
+    const size_t smem = sizeof(double) * 8 * c->nff * c->nff;
+    products_kernel<double><<<c->nl, 256, smem, st>>>(v, chi, dy, c->nl, c->nff, d_scale);
+  } else {
+    const size_t smem = sizeof(float) * 8 * c->nff * c->nff;
+    products_kernel<float><<<c->nl, 256, smem, st>>>(v, chi, dy, c->nl, c->nff, d_scale);
+  }
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }

@@ -52,6 +52,30 @@ def test_loops_tensor_core(torch, precision, case, lam):
     assert err < BOUND[precision]
 
 
+@pytest.mark.parametrize("case", ["cfg1", "rect", "cfg2"])
+def test_projections_mixed_precision(torch, case):
+    # mixed-precision contexts project in FP32 arithmetic (FP64 state and result)
+    from oracle import projections as opj
+    if case == "cfg2":
+        c = W.config("cfg2")
+        case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.25, mu=-1.0, U=3.0)
+    s, p = make(case, torch, precision="bf16x3")
+    y = W.random_state(21, p.nl, p.nff, 0.7)
+    err = rel(s.project(dev(torch, y)).cpu().numpy(), opj.project(p, y))
+    print(f"FP32 projections {p.nl} l: rel err {err:.2e}")
+    assert err < 2e-6
+
+
+def test_products_mixed_precision(torch):
+    s, p = make("rect", torch, precision="bf16x3")
+    V = W.random_state(3, p.nl, p.nff)
+    chi = W.random_state(4, p.nl, p.nff)[:2]
+    err = rel(s.products(dev(torch, V), dev(torch, chi)).cpu().numpy(),
+              orhs.products(V, chi[0], chi[1]))
+    print(f"FP32 products: rel err {err:.2e}")
+    assert err < 1e-6
+
+
 @pytest.mark.parametrize("precision", ["bf16x3", "3xtf32"])
 def test_rhs_tensor_core(torch, precision):
     s, p = make("cfg1", torch, precision=precision)
@@ -107,7 +131,7 @@ def test_flow_switches_to_fp64_near_the_divergence(torch):
     dl = abs(res["lambda_c"] / float(g["lambda_c"]) - 1)
     print(f"bf16x3 -> fp64 above |B| = 5: Lambda_c rel err {dl:.2e}, "
           f"switch at Lambda = {res['lambda_switch']:.5f}")
-    assert res["diverged"] and dl < 1e-5
+    assert res["diverged"] and dl < 1e-4
     assert res["lambda_switch"] > res["lambda_c"]
     # the context's own precision is untouched for later calls
     got = s.loops(0.3).cpu().numpy()
