@@ -106,8 +106,9 @@ struct tufrg_ctx {
   int tc_nsets = 1;                // accumulator sets per channel in TMEM
   int loop_prec = TUFRG_FP64;      // precision of the flow's next loop contractions
   int tc_hx = 0, tc_hy = 0, tc_wy = 0;  // halo of the extended table, its row width
-  float4* d_ext = nullptr;         // [(nfx+2hx)*wy] (xi, A, H, 0) in FP32 per scale
+  float4* d_ext = nullptr;         // [(nfx+2hx)*wy] (xi, A, H, |xi|) in FP32 per scale
   int* d_rowoff = nullptr;         // [nrow] sx * wy + sy
+  int* d_kbase = nullptr;          // [tc_kpad] loop point offsets in the halo table
   unsigned char* d_Fhi = nullptr;  // [tc_npad][tc_kpad] high parts of F (bf16 or tf32)
   unsigned char* d_Flo = nullptr;  // [tc_npad][tc_kpad] low parts
   float* d_partial_tc = nullptr;   // [tc_ksplit][2][tc_npad][tc_nrow_pad]

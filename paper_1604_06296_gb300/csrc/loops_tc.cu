@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kRows = 128;          // MMA M: l-representatives per CTA
 constexpr int kProducers = 16;      // producer warps
-constexpr int kBatch = 4;           // rows whose table loads are issued together
+constexpr int kLoadsInFlight = 16;  // float4 table loads a lane issues before computing
 constexpr int kThreads = 32 * (kProducers + 1);
 constexpr int kRowBytes = 128;      // one 128B-swizzle row per K-block
 constexpr int kWTile = kRows * kRowBytes;  // 16 KB
@@ -140,25 +140,36 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i;
 }
 
-// half-zone loop point k (order of the setup tables); x = -1 in the padding
-__device__ __forceinline__ int2 loop_point(int k, int nfx, int nfy, int kdim) {
-  if (k >= kdim) return make_int2(-1, -1);
-  const int hx = nfx / 2, hy = nfy / 2, main = nfx * (hy - 1);
-  if (k < main) return make_int2(k / (hy - 1), 1 + k % (hy - 1));
-  const int r = k - main;
-  return make_int2(r % (hx + 1), r < hx + 1 ? 0 : hy);
-}
-
 // Closed-form frequency integral of the two loops for one propagator pair.
+// Table entries: (xi, A, H, |xi|).
 __device__ __forceinline__ void weights(const float4 ta, const float4 tb, float om, float om2,
                                         float inv_om2, float& wpp, float& wph) {
   const float sa = ta.y + tb.y, pa = ta.y * tb.y;
   const float D = pa * fmaf(-2.f * om2, fmaf(sa, sa, -pa), fmaf(5.f * om, sa, -3.f));
-  const float xs = fabsf(ta.x) + fabsf(tb.x);
+  const float xs = ta.w + tb.w;
   const float S = xs > 0.f ? __fdividef(ta.z + tb.z, xs) : inv_om2;
   const bool same = ta.x * tb.x > 0.f;
   wpp = same ? S : D;
   wph = same ? D : S;
+}
+
+// The same for two propagator pairs at once with paired FP32 instructions.
+__device__ __forceinline__ void weights2(const float4 a0, const float4 b0, const float4 a1,
+                                         const float4 b1, float om, float om2, float inv_om2,
+                                         float2& wpp, float2& wph) {
+  const float2 Aa = make_float2(a0.y, a1.y), Ab = make_float2(b0.y, b1.y);
+  const float2 sa = __fadd2_rn(Aa, Ab), pa = __fmul2_rn(Aa, Ab);
+  const float2 t1 = __ffma2_rn(sa, sa, make_float2(-pa.x, -pa.y));
+  const float2 t2 = __ffma2_rn(make_float2(5.f * om, 5.f * om), sa, make_float2(-3.f, -3.f));
+  const float2 br = __ffma2_rn(make_float2(-2.f * om2, -2.f * om2), t1, t2);
+  const float2 D = __fmul2_rn(pa, br);
+  const float2 xs = __fadd2_rn(make_float2(a0.w, a1.w), make_float2(b0.w, b1.w));
+  const float2 hs = __fadd2_rn(make_float2(a0.z, a1.z), make_float2(b0.z, b1.z));
+  const float2 sg = __fmul2_rn(make_float2(a0.x, a1.x), make_float2(b0.x, b1.x));
+  const float S0 = xs.x > 0.f ? hs.x * __frcp_rn(xs.x) : inv_om2;
+  const float S1 = xs.y > 0.f ? hs.y * __frcp_rn(xs.y) : inv_om2;
+  wpp = make_float2(sg.x > 0.f ? S0 : D.x, sg.y > 0.f ? S1 : D.y);
+  wph = make_float2(sg.x > 0.f ? D.x : S0, sg.y > 0.f ? D.y : S1);
 }
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -169,6 +180,7 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 
 struct TcArgs {
   const float4* ext;      // per-scale table with a wrap-around halo, row width wy
+  const int* kbase;       // [kpad] offset of each loop point in the halo table
   const int* rowoff;      // [nrow] (sx * wy + sy): offset of p + l/2 from p
   const unsigned char* Fhi;
   const unsigned char* Flo;
@@ -182,6 +194,7 @@ template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   using P = Prec<PREC>;
   constexpr int KB = kRowBytes / P::kElem;  // k per K-block
+  constexpr int kBatch = kLoadsInFlight / (4 * P::kPerLane);  // rows per load batch
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -236,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     // rows have r % 8 == warp % 8, so the swizzled offset is fixed
     const uint32_t col = (uint32_t)(P::kPerLane * lane) * P::kElem;
     const uint32_t swz = (((col >> 4) ^ (uint32_t)(warp & 7)) << 4) | (col & 15);
-    const int center = a.hx * a.wy + a.hy;  // any in-range entry
+    const int fchunks = 8 * npad;  // 16-byte chunks per F tile
     for (int kb = 0; kb < a.kbps; ++kb) {
       const int s = kb & 1;
       if (kb >= 2 && !mbar_wait(bar_empty + 8 * s, ((kb >> 1) + 1) & 1)) {
@@ -246,31 +259,40 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       if (*abort_flag) break;
       const uint32_t st = base + s * stage_bytes;
       const int k0 = (kb_begin + kb) * KB;
-      // F tiles (hi, lo): npad rows x 8 chunks of 16 bytes each
-      for (int c = threadIdx.x; c < 16 * npad; c += 32 * kProducers) {
-        const int t = c / (8 * npad), rem = c - t * 8 * npad, row = rem >> 3, ch = rem & 7;
-        const unsigned char* src =
-            (t ? a.Flo : a.Fhi) + (size_t)row * frow + (size_t)k0 * P::kElem + ch * 16;
-        cp_async16(st + 4u * kWTile + t * ftile + row * kRowBytes + ((ch ^ (row & 7)) << 4), src);
+      const size_t fk = (size_t)k0 * P::kElem;
+      for (int c = threadIdx.x; c < 2 * fchunks; c += 32 * kProducers) {
+        const int t = c >= fchunks, rem = c - t * fchunks, row = rem >> 3, ch = rem & 7;
+        cp_async16(st + 4u * kWTile + t * ftile + row * kRowBytes + ((ch ^ (row & 7)) << 4),
+                   (t ? a.Flo : a.Fhi) + (size_t)row * frow + fk + ch * 16);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
-      // this lane's loop points as offsets into the halo table
+      // this lane's loop points as offsets into the halo table (padding points
+      // use a valid entry: their F is zero)
       int pb[P::kPerLane];
-      bool kok[P::kPerLane];
-#pragma unroll
-      for (int j = 0; j < P::kPerLane; ++j) {
-        const int2 pk = loop_point(k0 + P::kPerLane * lane + j, a.nfx, a.nfy, a.kdim);
-        kok[j] = pk.x >= 0;
-        pb[j] = kok[j] ? (pk.x + a.hx) * a.wy + pk.y + a.hy : center;
+      if constexpr (P::kPerLane == 2) {
+        const int2 v = __ldg(reinterpret_cast<const int2*>(a.kbase + k0) + lane);
+        pb[0] = v.x;
+        pb[1] = v.y;
+      } else {
+        pb[0] = __ldg(a.kbase + k0 + lane);
       }
 #pragma unroll 1
       for (int i0 = 0; i0 < kRows / kProducers; i0 += kBatch) {
+        if (warp + kProducers * i0 >= nvalid) {  // rows without an l: zeros
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) {
+            const uint32_t dst = st + (uint32_t)(warp + kProducers * (i0 + i)) * kRowBytes + swz;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(0u) : "memory");
+          }
+          continue;
+        }
         // table loads of kBatch rows first (memory-level parallelism)
         float4 ta[kBatch][P::kPerLane], tb[kBatch][P::kPerLane];
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
-          const int r = warp + kProducers * (i0 + i);
-          const int off = s_off[r];
+          const int off = s_off[warp + kProducers * (i0 + i)];
 #pragma unroll
           for (int j = 0; j < P::kPerLane; ++j) {
             ta[i][j] = __ldg(a.ext + (pb[j] + off));
@@ -280,33 +302,27 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
           const int r = warp + kProducers * (i0 + i);
-          float wpp[P::kPerLane], wph[P::kPerLane];
-          const bool rv = r < nvalid;  // warp-uniform
-#pragma unroll
-          for (int j = 0; j < P::kPerLane; ++j) {
-            weights(ta[i][j], tb[i][j], om, om2, inv_om2, wpp[j], wph[j]);
-            if (!(rv && kok[j])) {
-              wpp[j] = 0.f;
-              wph[j] = 0.f;
-            }
-          }
           uint32_t v[4];
           if constexpr (PREC == TUFRG_BF16X3) {
-            const __nv_bfloat162 ph = __floats2bfloat162_rn(wpp[0], wpp[1]);
-            const float2 bp = __bfloat1622float2(ph);
-            const __nv_bfloat162 pl = __floats2bfloat162_rn(wpp[0] - bp.x, wpp[1] - bp.y);
-            const __nv_bfloat162 hh = __floats2bfloat162_rn(wph[0], wph[1]);
-            const float2 bh = __bfloat1622float2(hh);
-            const __nv_bfloat162 hl = __floats2bfloat162_rn(wph[0] - bh.x, wph[1] - bh.y);
+            float2 wpp, wph;
+            weights2(ta[i][0], tb[i][0], ta[i][1], tb[i][1], om, om2, inv_om2, wpp, wph);
+            const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
+            const __nv_bfloat162 pl = __float22bfloat162_rn(
+                __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
+            const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
+            const __nv_bfloat162 hl = __float22bfloat162_rn(
+                __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
             std::memcpy(&v[0], &ph, 4);
             std::memcpy(&v[1], &pl, 4);
             std::memcpy(&v[2], &hh, 4);
             std::memcpy(&v[3], &hl, 4);
           } else {
-            v[0] = tf32_rna(wpp[0]);
-            v[1] = tf32_rna(wpp[0] - __uint_as_float(v[0]));
-            v[2] = tf32_rna(wph[0]);
-            v[3] = tf32_rna(wph[0] - __uint_as_float(v[2]));
+            float wpp, wph;
+            weights(ta[i][0], tb[i][0], om, om2, inv_om2, wpp, wph);
+            v[0] = tf32_rna(wpp);
+            v[1] = tf32_rna(wpp - __uint_as_float(v[0]));
+            v[2] = tf32_rna(wph);
+            v[3] = tf32_rna(wph - __uint_as_float(v[2]));
           }
           const uint32_t dst = st + (uint32_t)r * kRowBytes + swz;
 #pragma unroll
@@ -403,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   }
 }
 
-// Per-scale FP32 table (xi, A, H, 0) with a wrap-around halo of hx, hy
+// Per-scale FP32 table (xi, A, H, |xi|) with a wrap-around halo of hx, hy
 // points on each side, so that p +- l/2 needs no wrapping.
 __global__ void scale_table_ext_kernel(const double4_32a* __restrict__ tab,
                                        float4* __restrict__ ext, int nfx, int nfy, int hx,
@@ -417,7 +433,7 @@ __global__ void scale_table_ext_kernel(const double4_32a* __restrict__ tab,
     iy += iy < 0 ? nfy : 0;
     iy -= iy >= nfy ? nfy : 0;
     const double xi = tab[ix * nfy + iy].x, x = fabs(xi), A = 1.0 / (om + x);
-    ext[e] = make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), 0.f);
+    ext[e] = make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), (float)x);
   }
 }
 
@@ -474,6 +490,7 @@ tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi, cudaStream_t st) {
   TUFRG_CUDA(cudaGetLastError());
   TcArgs a;
   a.ext = c->d_ext;
+  a.kbase = c->d_kbase;
   a.rowoff = c->d_rowoff;
   a.Fhi = c->d_Fhi;
   a.Flo = c->d_Flo;

@@ -300,6 +300,10 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
     std::vector<int> rowoff(c->nrow);
     for (int r = 0; r < c->nrow; ++r) rowoff[r] = rowshift[r].x * c->tc_wy + rowshift[r].y;
     TUFRG_CHECK(upload(&c->d_rowoff, rowoff, st));
+    std::vector<int> kbase(c->tc_kpad, c->tc_hx * c->tc_wy + c->tc_hy);  // padding: centre
+    for (int k = 0; k < c->kdim; ++k)
+      kbase[k] = (kp[k].x + c->tc_hx) * c->tc_wy + kp[k].y + c->tc_hy;
+    TUFRG_CHECK(upload(&c->d_kbase, kbase, st));
     TUFRG_CHECK(alloc(&c->d_ext, (size_t)(c->nfx + 2 * c->tc_hx) * c->tc_wy));
     std::vector<unsigned char> fh((size_t)c->tc_npad * c->tc_kpad * es, 0);
     std::vector<unsigned char> fl(fh.size(), 0);
@@ -387,7 +391,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
 
 void free_device(tufrg_ctx* c) {
   free_flow(c);
-  void* ptrs[] = {c->d_ext, c->d_rowoff, c->d_Fhi, c->d_Flo, c->d_partial_tc, c->d_err,
+  void* ptrs[] = {c->d_ext, c->d_rowoff, c->d_kbase, c->d_Fhi, c->d_Flo, c->d_partial_tc, c->d_err,
                   c->d_rowmap, c->d_tab, c->d_kidx, c->d_F,       c->d_shift,   c->d_pair,
                   c->d_coef, c->d_phase,  c->d_key,     c->d_row_ptr, c->d_terms,
                   c->d_lambda, c->d_partial, c->d_chi,  c->d_V,       c->d_bt,
