@@ -166,8 +166,8 @@ __device__ __forceinline__ void weights2(const float4 a0, const float4 b0, const
   const float2 xs = __fadd2_rn(make_float2(a0.w, a1.w), make_float2(b0.w, b1.w));
   const float2 hs = __fadd2_rn(make_float2(a0.z, a1.z), make_float2(b0.z, b1.z));
   const float2 sg = __fmul2_rn(make_float2(a0.x, a1.x), make_float2(b0.x, b1.x));
-  const float S0 = xs.x > 0.f ? hs.x * __frcp_rn(xs.x) : inv_om2;
-  const float S1 = xs.y > 0.f ? hs.y * __frcp_rn(xs.y) : inv_om2;
+  const float S0 = xs.x > 0.f ? __fdividef(hs.x, xs.x) : inv_om2;
+  const float S1 = xs.y > 0.f ? __fdividef(hs.y, xs.y) : inv_om2;
   wpp = make_float2(sg.x > 0.f ? S0 : D.x, sg.y > 0.f ? S1 : D.y);
   wph = make_float2(sg.x > 0.f ? D.x : S0, sg.y > 0.f ? D.y : S1);
 }
