@@ -152,6 +152,22 @@ def profile_traffic(kernel_file, profile_name):
 
 
 # --------------------------------------------------------------------------
+def loop_counts(tufrg, bonds, ncx, ncy, nfx, nfy):
+    """Algorithmic sizes of one loop contraction: parity-allowed pairs m <= n,
+    half-zone loop points, l-representative rows."""
+    k = np.array([0.3, -1.1]), np.array([0.7, 0.4])
+    par = np.sign(tufrg.tufrg_eval_formfactors(bonds, -k[0], -k[1])[:, 0]
+                  * tufrg.tufrg_eval_formfactors(bonds, k[0], k[1])[:, 0])
+    nff = len(par)
+    npair = int(sum(1 for m in range(nff) for n in range(m, nff) if par[m] * par[n] > 0))
+    kdim = nfx * (nfy // 2 - 1) + 2 * (nfx // 2 + 1)
+    # rows: one l of each interior pair {l, -l} (the loops at -l equal those
+    # at l) and every l on the zone boundary
+    nrow = sum(1 for jx in range(ncx) for jy in range(ncy)
+               if jx == 0 or jy == 0 or jx * ncy + jy <= (ncx - jx) * ncy + (ncy - jy))
+    return npair, kdim, nrow
+
+
 def cpu_oracle_rhs_sample(tp, l_sample=48):
     """One FP64 oracle right-hand side at the workload, loops on l_sample of
     the Nl points (scaled to all Nl), projections and products on all l."""
@@ -208,6 +224,118 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------
+def scan_points(n, seed=W.BATCH_SEED):
+    """The seeded phase-diagram scan with mu from each point's density."""
+    import paper_1604_06296_gb300 as tufrg
+    pts = W.batch_points(n, seed)
+    for q in pts:
+        q["mu"] = tufrg.tufrg_mu_for_density(q["t"], q["tp"], q["density"], q["nf"], q["nf"])
+        q["bonds"] = W.bonds_for_shells(q["shells"])
+    return pts
+
+
+def run_scan(args, rank, world, local):
+    """Batched phase-diagram scan: all points of this rank advance together;
+    a step is one DoPri5 attempt of every active point (one captured graph)."""
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    c = W.config("cfg1")
+    pts = scan_points(args.points, W.BATCH_SEED + rank)
+    t0 = time.perf_counter()
+    batch = tufrg.Batch(pts, precision=args.precision)
+    setup_s = time.perf_counter() - t0
+    tune = batch.autotune(0.5)
+    flow_kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
+                   rtol=1e-6, atol=1e-8, h0=0.05)
+    batch.flow(max_steps=args.warmup, **flow_kw)
+    torch.cuda.synchronize()
+    clocks = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(local).uuid))
+    clocks.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record()
+    _, res, st = batch.flow(max_steps=args.steps, **flow_kw)
+    e1.record()
+    e1.synchronize()
+    wall = time.perf_counter() - t_wall
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    rhs = float(sum(r["n_rhs"] for r in res))
+    if pg:
+        t = torch.tensor([dev_s, rhs], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        dev_s, rhs = float(tmax[0]), float(t[1])
+    value = rhs / dev_s
+    # dominant kernel: the persistent loop contraction over all points
+    chi = batch.empty(True)
+    kms = []
+    for _ in range(3):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        batch.loops(0.5, out=chi)
+        a1.record()
+        a1.synchronize()
+        kms.append(a0.elapsed_time(a1))
+    k_ms = statistics.median(kms)
+    flops = 0.0
+    for q in pts:
+        npair, kdim, nrow = loop_counts(tufrg, q["bonds"], q["nc"], q["nc"], q["nf"], q["nf"])
+        flops += 2.0 * 3 * 2 * npair * kdim * nrow
+    peaks, peak_src = measured_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    peak = bf16 if args.precision == "bf16x3" else bf16 * 1.1 / 2.25
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel_ms": k_ms,
+                "kernel": f"loops_tc_kernel<{args.precision}> over all points (+ tables, reduce)",
+                "algorithmic_flop_per_launch": flops,
+                "peak_source": f"bf16 dense burst from {peak_src} (of measured)"}
+    # kernels of the library in the timed call: first stage (combination + 7
+    # right-hand-side kernels), per attempt 6 x 8 + error, control, accept,
+    # then 100 bisection rounds of 2 and 6 more for the crossing and argmax
+    attempts = max(r["n_accepted"] + r["n_rejected"] for r in res)
+    launches = 8 + 51 * attempts + 2 * 100 + 6
+    if rank == 0:
+        sizes = sorted({(q["nc"], q["nf"], W.n_ff_for_shells(q["shells"])) for q in pts})
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": dev_s * 1e3 / max(1, max(r["n_accepted"] + r["n_rejected"]
+                                                       for r in res)),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": f"{args.precision} loops, f64 state", "data": "synthetic",
+               "config": {"workload": f"batched phase-diagram scan: {len(pts)} seeded points "
+                                      "per GPU, t'~U[-0.45,0], U~U[2,4], density~U[0.6,1], "
+                                      "coarse 16^2..32^2, Nff 5..21, fine 240^2..480^2",
+                          "step": "one DoPri5 attempt of every active point (rtol 1e-6)",
+                          "l2": "inputs larger than L2 (tables and states of all points)",
+                          "sizes": [list(x) for x in sizes]},
+               "rhs_evals_timed": rhs, "wall_s": wall, "setup_s": setup_s,
+               "diverged": int(sum(r["diverged"] for r in res)),
+               "finished": int(sum(r["finished"] for r in res)),
+               "status_nonzero": int(sum(1 for x in st if x)),
+               "autotune": tune, "roofline": roofline, "clocks": clk,
+               "gpu_launches": launches, "peaks_source": peak_src}
+        print(json.dumps(out))
+    batch.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,10 +345,15 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "3xtf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flow-time", action="store_true")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "scan"],
+                    help="cfg2: production point (default); scan: batched phase-diagram scan")
+    ap.add_argument("--points", type=int, default=256, help="scan: points per GPU")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "scan":
+        return run_scan(args, rank, world, local)
 
     import torch
     import paper_1604_06296_gb300 as tufrg
@@ -304,17 +437,7 @@ def main():
         kms.append(e0.elapsed_time(e1))
     k_ms = statistics.median(kms)
     p = solver.params
-    k = np.array([0.3, -1.1]), np.array([0.7, 0.4])
-    par = np.sign(tufrg.tufrg_eval_formfactors(solver._bonds, -k[0], -k[1])[:, 0]
-                  * tufrg.tufrg_eval_formfactors(solver._bonds, k[0], k[1])[:, 0])
-    npair = int(sum(1 for m in range(solver.nff) for n in range(m, solver.nff)
-                    if par[m] * par[n] > 0))
-    kdim = p.nf_x * (p.nf_y // 2 - 1) + 2 * (p.nf_x // 2 + 1)
-    # rows: one l of each interior pair {l, -l} (the loops at -l equal those
-    # at l) and every l on the zone boundary
-    nrow = sum(1 for jx in range(p.nc_x) for jy in range(p.nc_y)
-               if jx == 0 or jy == 0
-               or jx * p.nc_y + jy <= (p.nc_x - jx) * p.nc_y + (p.nc_y - jy))
+    npair, kdim, nrow = loop_counts(tufrg, solver._bonds, p.nc_x, p.nc_y, p.nf_x, p.nf_y)
     if args.precision == "fp64":
         flops = 2.0 * 2 * npair * kdim * nrow            # 2 channels, FMA = 2 flop
         peak = fp64_peak_tflops(torch)

@@ -245,6 +245,90 @@ tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x,
  * cleared.  tufrg_flow* calls check it themselves. */
 tufrg_status tufrg_check(tufrg_ctx* ctx, void* cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Tile autotuning.  The tensor-core loop contraction cuts each point's loop
+ * sum into work items of kbps K-blocks (64 fine-grid points per K-block for
+ * BF16X3, 32 for 3XTF32) per tile of 128 l-rows; persistent CTAs, one per
+ * SM, take the items from a queue.  Small items balance the SMs better,
+ * large ones cost fewer partial sums and pipeline restarts; an item holds at
+ * most 4096 loop points (FP32 accumulation chains).  The tuner times
+ * one loop contraction per candidate (CUDA events, after a warm-up) and
+ * keeps the fastest.  Results depend on kbps only through the FP32
+ * accumulation order (differences at the level of the precision's rounding).
+ */
+typedef struct {
+  int32_t n_candidates;   /* candidates timed (<= 16) */
+  int32_t kbps[16];       /* K-blocks per work item of each candidate */
+  double ms[16];          /* its loop-contraction time (median of the repeats) */
+  int32_t chosen;         /* index of the candidate kept */
+  int32_t kbps_default;   /* the setup's heuristic choice (also a candidate) */
+} tufrg_tune_report;
+
+/* Autotunes the context's tensor-core loop contraction at scale lambda
+ * (TUFRG_ERR_ARG for an FP64 context).  rep may be NULL.  Blocks. */
+tufrg_status tufrg_autotune(tufrg_ctx* ctx, double lambda, tufrg_tune_report* rep,
+                            void* cuda_stream);
+
+/* ---------------------------------------------------------------------
+ * Batches: many phase-diagram points (own t, t', mu, U, grids and bond
+ * shells) advanced together.  Each step of the right-hand side is one
+ * launch over all points (the loop contraction one persistent launch whose
+ * work items come from every point); a batched flow keeps step control per
+ * point on the device and runs each DoPri5 attempt of all points as one
+ * captured CUDA graph.
+ *
+ * Packed layouts: point i's state occupies elements
+ * [state_offset_i, state_offset_i + 3 Nl_i Nff_i^2) of a packed state array
+ * ([3][Nl_i][Nff_i][Nff_i] as for a context); its loops occupy
+ * [loop_offset_i, loop_offset_i + 2 Nl_i Nff_i^2) of a packed loop array.
+ */
+typedef struct tufrg_batch tufrg_batch;
+
+/* Sets up n_points points (params: host array [n_points]).  All points use
+ * the same precision.  Points with equal grids and bond lists share their
+ * scale-independent tables.  Blocks until the tables are on the device. */
+tufrg_status tufrg_batch_setup(int32_t n_points, const tufrg_params* params, void* cuda_stream,
+                               tufrg_batch** out);
+
+void tufrg_batch_destroy(tufrg_batch* b);
+
+/* Point sizes and packed offsets (any output may be NULL).  point = -1
+ * gives the totals: *state_offset = packed state elements, *loop_offset =
+ * packed loop elements, *nl = number of points. */
+tufrg_status tufrg_batch_dims(const tufrg_batch* b, int32_t point, int32_t* nl, int32_t* nff,
+                              int64_t* state_offset, int64_t* loop_offset);
+
+/* Loops (Eq. chis) of every point, point i at scale lambda[i] (host array);
+ * chi_dot_dev: packed loop array. */
+tufrg_status tufrg_batch_loops(tufrg_batch* b, const double* lambda, double* chi_dot_dev,
+                               void* cuda_stream);
+
+/* Right-hand sides dy/dLambda of every point at its scale lambda[i];
+ * y_dev, dy_dev: packed state arrays (may not alias). */
+tufrg_status tufrg_batch_rhs(tufrg_batch* b, const double* lambda, const double* y_dev,
+                             double* dy_dev, void* cuda_stream);
+
+/* Flows of every point with the options of tufrg_flow (DoPri5 only; no
+ * checkpoints; fp64_above must be 0).  Each point has its own step size,
+ * acceptance and stop; a finished point does no further work.  The loop
+ * runs until every point has finished or max_steps attempts were made.
+ * y_dev: packed state, in = initial states, out = final states (at Lambda_c
+ * for diverged points).  res: host array [n_points]; status: host array
+ * [n_points] of each point's tufrg_status (may be NULL).  The return value
+ * is the first failing point's status (TUFRG_ERR_TIMEOUT if a bounded wait
+ * of the loop kernel gave up); a point that failed (non-finite state, step
+ * underflow) stops there and the others go on.  Blocks. */
+tufrg_status tufrg_batch_flow(tufrg_batch* b, const tufrg_flow_opts* opts, double* y_dev,
+                              tufrg_result* res, int32_t* status, void* cuda_stream);
+
+/* Autotunes the batch's persistent loop contraction (see tufrg_autotune),
+ * every point at scale lambda. */
+tufrg_status tufrg_batch_autotune(tufrg_batch* b, double lambda, tufrg_tune_report* rep,
+                                  void* cuda_stream);
+
+/* As tufrg_check, for the batch's kernels. */
+tufrg_status tufrg_batch_check(tufrg_batch* b, void* cuda_stream);
+
 const char* tufrg_status_string(tufrg_status s);
 
 #ifdef __cplusplus

@@ -143,10 +143,117 @@ class Solver:
         r = tufrg_flow_state(self.ctx, self._check(out, 3), _stream())
         return out, self._result(r)
 
+    def autotune(self, lam=1.0):
+        """Tile autotuning of the tensor-core loops; returns the timing report."""
+        return _abi.tufrg_autotune(self.ctx, float(lam), _stream()).as_dict()
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             tufrg_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(t, tp, mu, U, bonds, nc, nf, precision="bf16x3", feedback=True, ncy=None,
+                nfy=None):
+    """A tufrg_params and the bond array it points to (keep both alive)."""
+    b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+    p = _abi.tufrg_params()
+    p.lattice = 0
+    p.t, p.tp, p.mu, p.U = float(t), float(tp), float(mu), float(U)
+    p.n_bonds = len(b)
+    p.bonds = b.ctypes.data_as(_abi.POINTER(_abi.c_int32))
+    p.nc_x, p.nc_y = int(nc), int(ncy or nc)
+    p.nf_x, p.nf_y = int(nf), int(nfy or nf)
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.feedback = 1 if feedback else 0
+    return p, b
+
+
+class Batch:
+    """Many phase-diagram points advanced together on the current CUDA device.
+
+    points: list of dicts with keys t, tp, mu, U, bonds, nc, nf (and
+    optionally feedback); all points share one tensor-core precision.  States
+    and loops are packed float64 CUDA tensors (1-D); ``view(x, i)`` gives
+    point i's [3 or 2][Nl][Nff][Nff] view.
+    """
+
+    def __init__(self, points, precision="bf16x3"):
+        made = [make_params(q["t"], q["tp"], q["mu"], q["U"], q["bonds"], q["nc"], q["nf"],
+                            precision, q.get("feedback", True)) for q in points]
+        arr = (_abi.tufrg_params * len(made))(*[m[0] for m in made])
+        self._keep = [m[1] for m in made]
+        self.n = len(made)
+        self.b = _abi.tufrg_batch_setup(arr, _stream())
+        self.dims = [_abi.tufrg_batch_dims(self.b, i) for i in range(self.n)]
+        _, _, self.state_elems, self.loop_elems = _abi.tufrg_batch_dims(self.b, -1)
+
+    def empty(self, loops=False):
+        import torch
+        return torch.empty(self.loop_elems if loops else self.state_elems, dtype=torch.float64,
+                           device="cuda")
+
+    def zeros(self, loops=False):
+        return self.empty(loops).zero_()
+
+    def view(self, x, i, loops=False):
+        nl, nff, so, lo = self.dims[i]
+        lead = 2 if loops else 3
+        off = lo if loops else so
+        return x[off:off + lead * nl * nff * nff].view(lead, nl, nff, nff)
+
+    def _vec(self, x, loops=False):
+        import torch
+        n = self.loop_elems if loops else self.state_elems
+        if (not isinstance(x, torch.Tensor) or x.dtype != torch.float64 or not x.is_cuda
+                or not x.is_contiguous() or x.numel() != n):
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of {n} elements")
+        return x.data_ptr()
+
+    def _lams(self, lam):
+        lam = np.broadcast_to(np.asarray(lam, dtype=np.float64), (self.n,))
+        return np.ascontiguousarray(lam)
+
+    def loops(self, lam, out=None):
+        out = self.empty(True) if out is None else out
+        _abi.tufrg_batch_loops(self.b, self._lams(lam), self._vec(out, True), _stream())
+        return out
+
+    def rhs(self, lam, y, out=None):
+        out = self.empty() if out is None else out
+        _abi.tufrg_batch_rhs(self.b, self._lams(lam), self._vec(y), self._vec(out), _stream())
+        return out
+
+    def flow(self, y=None, lambda0=10.0, lambda_min=1e-3, threshold=50.0, rtol=1e-8,
+             atol=1e-10, h0=0.05, max_steps=100000):
+        """Flows of every point (DoPri5) in place of y; returns (y, results, statuses)."""
+        y = self.zeros() if y is None else y
+        o = _abi.tufrg_flow_opts()
+        o.lambda0, o.lambda_min, o.threshold = float(lambda0), float(lambda_min), float(threshold)
+        o.rtol, o.atol, o.h0 = float(rtol), float(atol), float(h0)
+        o.method = TUFRG_DOPRI5
+        o.max_steps = int(max_steps)
+        o.n_checkpoints = 0
+        o.fp64_above = 0.0
+        _, res, st = _abi.tufrg_batch_flow(self.b, self.n, o, self._vec(y), _stream())
+        return y, [Solver._result(r) for r in res], st
+
+    def autotune(self, lam=1.0):
+        return _abi.tufrg_batch_autotune(self.b, float(lam), _stream()).as_dict()
+
+    def check(self):
+        _abi.tufrg_batch_check(self.b, _stream())
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            _abi.tufrg_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -54,6 +54,16 @@ class tufrg_result(Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class tufrg_tune_report(Structure):
+    _fields_ = [("n_candidates", c_int32), ("kbps", c_int32 * 16), ("ms", c_double * 16),
+                ("chosen", c_int32), ("kbps_default", c_int32)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"kbps": list(self.kbps[:n]), "ms": list(self.ms[:n]),
+                "chosen": self.kbps[self.chosen], "kbps_default": self.kbps_default}
+
+
 _lib = None
 
 # name -> (argtypes, restype); restype c_int32 means a tufrg_status to check
@@ -77,6 +87,19 @@ SIGNATURES = {
     "tufrg_mu_for_density": ([c_double, c_double, c_double, c_int32, c_int32,
                               POINTER(c_double)], c_int32),
     "tufrg_check": ([c_void_p, c_void_p], c_int32),
+    "tufrg_autotune": ([c_void_p, c_double, POINTER(tufrg_tune_report), c_void_p], c_int32),
+    "tufrg_batch_setup": ([c_int32, POINTER(tufrg_params), c_void_p, POINTER(c_void_p)],
+                          c_int32),
+    "tufrg_batch_destroy": ([c_void_p], None),
+    "tufrg_batch_dims": ([c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32),
+                          POINTER(c_int64), POINTER(c_int64)], c_int32),
+    "tufrg_batch_loops": ([c_void_p, POINTER(c_double), c_void_p, c_void_p], c_int32),
+    "tufrg_batch_rhs": ([c_void_p, POINTER(c_double), c_void_p, c_void_p, c_void_p], c_int32),
+    "tufrg_batch_flow": ([c_void_p, POINTER(tufrg_flow_opts), c_void_p, POINTER(tufrg_result),
+                          POINTER(c_int32), c_void_p], c_int32),
+    "tufrg_batch_autotune": ([c_void_p, c_double, POINTER(tufrg_tune_report), c_void_p],
+                             c_int32),
+    "tufrg_batch_check": ([c_void_p, c_void_p], c_int32),
     "tufrg_status_string": ([c_int32], ctypes.c_char_p),
 }
 
@@ -201,3 +224,65 @@ def tufrg_check(ctx, stream: int = 0) -> None:
 
 def tufrg_status_string(status: int) -> str:
     return lib().tufrg_status_string(status).decode()
+
+
+def tufrg_autotune(ctx, lam: float, stream: int = 0) -> tufrg_tune_report:
+    rep = tufrg_tune_report()
+    _check(lib().tufrg_autotune(ctx, lam, byref(rep), _dptr(stream)), "tufrg_autotune")
+    return rep
+
+
+def tufrg_batch_setup(params, stream: int = 0) -> c_void_p:
+    """params: a ctypes array of tufrg_params."""
+    b = c_void_p()
+    _check(lib().tufrg_batch_setup(len(params), params, _dptr(stream), byref(b)),
+           "tufrg_batch_setup")
+    return b
+
+
+def tufrg_batch_destroy(b) -> None:
+    lib().tufrg_batch_destroy(b)
+
+
+def tufrg_batch_dims(b, point: int) -> tuple[int, int, int, int]:
+    nl, nff, so, lo = c_int32(), c_int32(), c_int64(), c_int64()
+    _check(lib().tufrg_batch_dims(b, point, byref(nl), byref(nff), byref(so), byref(lo)),
+           "tufrg_batch_dims")
+    return nl.value, nff.value, so.value, lo.value
+
+
+def _doubles(x):
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a, a.ctypes.data_as(POINTER(c_double))
+
+
+def tufrg_batch_loops(b, lam, chi_dev: int, stream: int = 0) -> None:
+    a, ptr = _doubles(lam)
+    _check(lib().tufrg_batch_loops(b, ptr, _dptr(chi_dev), _dptr(stream)), "tufrg_batch_loops")
+
+
+def tufrg_batch_rhs(b, lam, y_dev: int, dy_dev: int, stream: int = 0) -> None:
+    a, ptr = _doubles(lam)
+    _check(lib().tufrg_batch_rhs(b, ptr, _dptr(y_dev), _dptr(dy_dev), _dptr(stream)),
+           "tufrg_batch_rhs")
+
+
+def tufrg_batch_flow(b, n_points: int, opts: tufrg_flow_opts, y_dev: int, stream: int = 0):
+    """Returns (status, results, per-point statuses); a failing point does not raise."""
+    res = (tufrg_result * n_points)()
+    st = (c_int32 * n_points)()
+    s = lib().tufrg_batch_flow(b, byref(opts), _dptr(y_dev), res, st, _dptr(stream))
+    if s not in (0, -3, -4):
+        _check(s, "tufrg_batch_flow")
+    return s, list(res), list(st)
+
+
+def tufrg_batch_autotune(b, lam: float, stream: int = 0) -> tufrg_tune_report:
+    rep = tufrg_tune_report()
+    _check(lib().tufrg_batch_autotune(b, lam, byref(rep), _dptr(stream)), "tufrg_batch_autotune")
+    return rep
+
+
+def tufrg_batch_check(b, stream: int = 0) -> None:
+    _check(lib().tufrg_batch_check(b, _dptr(stream)), "tufrg_batch_check")

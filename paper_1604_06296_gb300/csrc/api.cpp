@@ -38,23 +38,19 @@ tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) 
     TUFRG_CHECK(launch_scale_tables(c, st));
     return launch_loops_fp64(c, chi, st);
   }
-  return launch_loops_tc(c, chi, st);
+  return launch_loops_tc_multi(c->view, chi, chi != c->d_chi, st);
 }
 
-tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy,
-                        const double* d_scale, cudaStream_t st) {
+tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
+                        cudaStream_t st) {
   TUFRG_CHECK(launch_loops(c, prec, c->d_chi, st));
-  TUFRG_CHECK(launch_project(c, prec, y, c->d_V, st));
-  TUFRG_CHECK(launch_products(c, prec, c->d_V, c->d_chi, dy, d_scale, st));
+  TUFRG_CHECK(launch_project_multi(c->view, prec, y, c->d_V, c->d_bt, c->d_fkey, st));
+  TUFRG_CHECK(launch_products_multi(c->view, prec, c->d_V, c->d_chi, dy, scaled, st));
   return TUFRG_OK;
 }
 
-}  // namespace tufrg
-
-extern "C" {
-
-tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** out) {
-  if (!out) return TUFRG_ERR_ARG;
+tufrg_status create_context(const tufrg_params* p, cudaStream_t st, const SetupShare& share,
+                            tufrg_ctx** out) {
   *out = nullptr;
   TUFRG_CHECK(validate(p));
   tufrg_ctx* c = new (std::nothrow) tufrg_ctx();
@@ -79,14 +75,24 @@ tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** o
   c->nff = c->basis.nff;
   c->nb = c->basis.nb;
   c->loop_prec = p->precision;
-  s = tufrg::setup_device(c, (cudaStream_t)cuda_stream);
+  s = setup_device(c, st, share);
   if (s != TUFRG_OK) {
-    tufrg::free_device(c);
+    free_device(c);
     delete c;
     return s;
   }
   *out = c;
   return TUFRG_OK;
+}
+
+}  // namespace tufrg
+
+extern "C" {
+
+tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** out) {
+  if (!out) return TUFRG_ERR_ARG;
+  *out = nullptr;
+  return tufrg::create_context(p, (cudaStream_t)cuda_stream, tufrg::SetupShare(), out);
 }
 
 void tufrg_destroy(tufrg_ctx* c) {
@@ -126,15 +132,16 @@ tufrg_status tufrg_loops(tufrg_ctx* c, double lambda, double* chi_dot_dev, void*
 
 tufrg_status tufrg_project(tufrg_ctx* c, const double* y_dev, double* v_dev, void* stream) {
   if (!c || !y_dev || !v_dev || y_dev == v_dev) return TUFRG_ERR_ARG;
-  return tufrg::launch_project(c, c->p.precision, y_dev, v_dev, (cudaStream_t)stream);
+  return tufrg::launch_project_multi(c->view, c->p.precision, y_dev, v_dev, c->d_bt, c->d_fkey,
+                                     (cudaStream_t)stream);
 }
 
 tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi_dot_dev,
                             double* dy_dev, void* stream) {
   if (!c || !v_dev || !chi_dot_dev || !dy_dev || dy_dev == v_dev || dy_dev == chi_dot_dev)
     return TUFRG_ERR_ARG;
-  return tufrg::launch_products(c, c->p.precision, v_dev, chi_dot_dev, dy_dev, nullptr,
-                                (cudaStream_t)stream);
+  return tufrg::launch_products_multi(c->view, c->p.precision, v_dev, chi_dot_dev, dy_dev, false,
+                                      (cudaStream_t)stream);
 }
 
 tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double* dy_dev,
@@ -142,7 +149,7 @@ tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double*
   if (!c || !y_dev || !dy_dev || y_dev == dy_dev || !finite_pos(lambda)) return TUFRG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
-  return tufrg::rhs_device(c, c->p.precision, y_dev, dy_dev, nullptr, st);
+  return tufrg::rhs_device(c, c->p.precision, y_dev, dy_dev, false, st);
 }
 
 namespace {

@@ -70,6 +70,68 @@ struct ProjTables {
 
 struct FlowState;
 
+// One point (one set of model parameters and grids) as the multi-point
+// kernels see it.  A context is a batch of one point; a batch context
+// (tufrg_batch) holds many.  Offsets locate the point in packed buffers
+// (elements of the buffer's own type).
+struct PointDesc {
+  int nl, nff, nb, ncx, ncy, nd, nkeys, feedback;
+  double U;
+  int term_off[3];
+  int npair, nrow;
+  // tensor-core loops
+  int nfx, nfy, hx, hy, wy, n_ext, nkb, kpad_tc, nrow_pad, npad, nsets, ksplit;
+  long long off_state, off_chi, off_bt, off_fkey, off_partial;
+  const double4_32a* tab;
+  float4* ext;
+  const int* kbase;
+  const int* rowoff;
+  const unsigned char* Fhi;
+  const unsigned char* Flo;
+  const int2* rowmap;
+  const int* pair;
+  const double2* coef;
+  const double2* phase;
+  const int4* keys;
+  const int* row_ptr;
+  const int4* terms;
+  const double* lam;  // [0] scale of the loops, [1] factor applied to dy when scaled
+  const int* skip;    // nonzero: the point does no work (finished flow); may be null
+};
+
+// kinds of multi-point launches: per point, a fixed number of CTAs
+enum : int {
+  kKindTable = 0,  // per-scale FP32 halo table
+  kKindReduce,     // split-K combination of the tensor-core partial sums
+  kKindBond,       // projections: to bond space
+  kKindDft,        // projections: Fourier keys
+  kKindContract,   // projections: overlap sums and basis change
+  kKindProducts,   // V chi V
+  kKinds
+};
+
+struct MultiView {
+  int n = 0;
+  std::vector<PointDesc> h;
+  PointDesc* d = nullptr;
+  std::vector<int> prefix;  // [kKinds][n + 1] first CTA of each point, per kind
+  int* d_prefix = nullptr;
+  int nff_max = 0, nb_max = 0, nd_max = 0, nc_sum_max = 0;
+  // tensor-core loops: work items (point, l-tile, first K-block, K-blocks)
+  // taken from a queue by persistent CTAs
+  int tc_prec = TUFRG_FP64;  // TUFRG_FP64: no tensor-core loops
+  int kbps = 0, n_items = 0, ctas = 0, npad_max = 0, tmem_cols = 0;
+  int4* d_items = nullptr;
+  int* d_counter = nullptr;
+  float* d_partial = nullptr;
+  size_t partial_elems = 0;
+  int* d_err = nullptr;  // error word of the bounded waits
+  // elements of the packed buffers: state (y, V, dy), loops, bond space, keys
+  size_t state_elems = 0, chi_elems = 0, bt_elems = 0, fkey_elems = 0;
+  int total(int kind) const { return prefix[(size_t)kind * (n + 1) + n]; }
+  const int* dprefix(int kind) const { return d_prefix + (size_t)kind * (n + 1); }
+};
+
 }  // namespace tufrg
 
 // Opaque context of the C ABI.
@@ -102,7 +164,7 @@ struct tufrg_ctx {
   int term_off[3] = {0, 0, 0};
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
-  int tc_npad = 0, tc_kpad = 0, tc_kbps = 0, tc_ksplit = 0, tc_nrow_pad = 0, tc_tmem_cols = 0;
+  int tc_npad = 0, tc_kpad = 0, tc_nkb = 0, tc_nrow_pad = 0;
   int tc_nsets = 1;                // accumulator sets per channel in TMEM
   int loop_prec = TUFRG_FP64;      // precision of the flow's next loop contractions
   int tc_hx = 0, tc_hy = 0, tc_wy = 0;  // halo of the extended table, its row width
@@ -111,7 +173,6 @@ struct tufrg_ctx {
   int* d_kbase = nullptr;          // [tc_kpad] loop point offsets in the halo table
   unsigned char* d_Fhi = nullptr;  // [tc_npad][tc_kpad] high parts of F (bf16 or tf32)
   unsigned char* d_Flo = nullptr;  // [tc_npad][tc_kpad] low parts
-  float* d_partial_tc = nullptr;   // [tc_ksplit][2][tc_npad][tc_nrow_pad]
   int* d_err = nullptr;            // device error word (bounded waits that gave up)
 
   // device: workspace
@@ -126,6 +187,9 @@ struct tufrg_ctx {
   // stream: flows run there (graph capture needs a non-legacy stream) and are
   // joined to the caller's stream with events
   tufrg::FlowState* flow = nullptr;
+  tufrg::MultiView view;           // this context as a batch of one point
+  bool borrowed_loops = false;     // loop / projection tables owned by another context
+  bool borrowed_proj = false;
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
@@ -134,28 +198,71 @@ struct tufrg_ctx {
 
 namespace tufrg {
 
-tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st);
+// Tables a new context may take over from an existing one instead of
+// building them: loops (same fine and coarse grids, bonds, precision) and
+// projections (same coarse grid and bonds).  own_view: build the context's
+// batch-of-one view (contexts made for a tufrg_batch skip it).
+// workspace: allocate the context's own right-hand-side workspace, stream
+// and events (batch points use the batch's).
+struct SetupShare {
+  const tufrg_ctx* loops = nullptr;
+  const tufrg_ctx* proj = nullptr;
+  bool own_view = true;
+  bool workspace = true;
+};
+tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share = SetupShare());
+// validation, basis and setup_device (tufrg_setup with shared tables)
+tufrg_status create_context(const tufrg_params* p, cudaStream_t st, const SetupShare& share,
+                            tufrg_ctx** out);
+// drops the captured flow graphs (after a change of the tensor-core work items)
+void flow_drop_graphs(tufrg_ctx* c);
+// times candidate work-item sizes of the view's tensor-core loops; run sets
+// the scale(s) the view's points read and launches the contraction once
+tufrg_status autotune_view(MultiView& v, tufrg_status (*run)(void*, cudaStream_t), void* arg,
+                           tufrg_tune_report* rep, cudaStream_t st);
 void free_device(tufrg_ctx* c);
 
 // kernels (launchers)
 tufrg_status launch_scale_tables(tufrg_ctx* c, cudaStream_t st);
 tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi_out, cudaStream_t st);
 // projections and products: FP64 arithmetic when prec == TUFRG_FP64, else FP32
-tufrg_status launch_project(tufrg_ctx* c, int prec, const double* y, double* v,
-                            cudaStream_t st);
-tufrg_status launch_products(tufrg_ctx* c, int prec, const double* v, const double* chi,
-                             double* dy, const double* d_scale, cudaStream_t st);
 tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 
 // steps i-iii at the scale stored in c->d_lambda with loops in precision prec;
-// dy scaled by *d_scale if non-null
-tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy,
-                        const double* d_scale, cudaStream_t st);
+// dy scaled by c->d_lambda[1] if scaled
+tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
+                        cudaStream_t st);
 
-tufrg_status prepare_products(tufrg_ctx* c);
-tufrg_status prepare_loops_tc(tufrg_ctx* c);
+// multi-point views (multi.cpp): descriptors of n contexts packed one after
+// the other; lam[i], skip[i] are per-point device pointers (skip may be null)
+tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* const* lam,
+                        const int* const* skip, int* err, int tc_prec, int kbps,
+                        cudaStream_t st);
+tufrg_status view_set_kbps(MultiView& v, int kbps, cudaStream_t st);
+int view_default_kbps(const MultiView& v);
+void view_free(MultiView& v);
+int sm_count();
+// the largest dynamic shared memory a CTA may opt in to on the current device
+// (the attribute is per function and process-wide: kernels shared by
+// contexts of different sizes get the device limit once, never a
+// context's own size, which a later, smaller context would lower)
+int smem_optin();
+
+// tensor-core loops of every point (zero: clear chi first; the kernels write
+// only the parity-allowed pairs)
+tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, bool zero, cudaStream_t st);
 size_t tc_smem_bytes(int npad);
-tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi_out, cudaStream_t st);
+int tc_k_per_block(int prec);
+int table_ctas(int n_ext);
+tufrg_status prepare_loops_tc_multi(const MultiView& v);
+tufrg_status prepare_project_multi(const MultiView& v);
+tufrg_status prepare_products_multi(const MultiView& v);
+int dft_ctas(int nkeys);
+// projections and products of every point; bt, fkey: packed workspaces
+tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
+                                  void* bt, void* fkey, cudaStream_t st);
+tufrg_status launch_products_multi(const MultiView& v, int prec, const double* vin,
+                                   const double* chi, double* dy, bool scaled, cudaStream_t st);
 // loops in the given precision (the context's, or FP64)
 tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi_out, cudaStream_t st);
 

@@ -15,17 +15,21 @@
 // F (scale independent) is staged with cp.async.  Both channels share W's
 // table reads and divisions and have their own accumulator.
 //
-// CTA: 17 warps.  Warps 0-15 produce the W tiles of a K-block (8 rows each,
-// lanes along k, table loads of 4 rows in flight) and stage F; warps 0-7 then
-// read the accumulators out (warp w reads the 32 TMEM lanes 32 (w % 4).. of
-// channel w / 4).  Warp 16 owns TMEM and one of its threads issues the MMAs.  Two pipeline stages, mbarriers full/empty;
-// every wait is bounded in time and a timeout sets an error word, stops the
-// pipeline, drains the issued MMAs and frees TMEM.
+// Persistent CTAs (one per SM, 17 warps) take work items -- (point, tile of
+// 128 l-rows, range of K-blocks) of any number of points -- from a queue
+// ordered by cost.  Warps 0-15 produce the W tiles of a K-block (8 rows each,
+// lanes along k, table loads of several rows in flight) and stage F; warps
+// 0-7 then read the accumulators out (warp w reads the 32 TMEM lanes
+// 32 (w % 4).. of channel w / 4).  Warp 16 owns TMEM and one of its threads
+// issues the MMAs.  Two pipeline stages, mbarriers full/empty, whose phases
+// run on across items; every wait is bounded in time and a timeout sets an
+// error word, stops the pipeline, drains the issued MMAs and frees TMEM.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 
-#include "internal.h"
+#include "device_util.cuh"
 
 namespace tufrg {
 namespace {
@@ -134,12 +138,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-__device__ __forceinline__ int wrap(int i, int n) {
-  i += (i < 0) ? n : 0;
-  i -= (i >= n) ? n : 0;
-  return i;
-}
-
 // Closed-form frequency integral of the two loops for one propagator pair.
 // Table entries: (xi, A, H, |xi|).
 __device__ __forceinline__ void weights(const float4 ta, const float4 tb, float om, float om2,
@@ -179,15 +177,14 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 }
 
 struct TcArgs {
-  const float4* ext;      // per-scale table with a wrap-around halo, row width wy
-  const int* kbase;       // [kpad] offset of each loop point in the halo table
-  const int* rowoff;      // [nrow] (sx * wy + sy): offset of p + l/2 from p
-  const unsigned char* Fhi;
-  const unsigned char* Flo;
-  float* partial;
+  const PointDesc* pts;
+  const int4* items;  // (point, l-tile, first K-block, K-blocks), costliest first
+  int n_items;
+  int* counter;       // next item (zero before the launch)
+  float* partial;     // per point [ksplit][2][npad][nrow_pad] at off_partial
   int* err;
-  const double* lam;
-  int nfx, nfy, hx, hy, wy, kdim, kpad, kbps, nrow, nrow_pad, npad, nsets, tmem_cols;
+  int kbps;           // K-blocks per full item: split = first K-block / kbps
+  int npad_max, tmem_cols;
 };
 
 template <int PREC>
@@ -199,22 +196,18 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
-  const int npad = a.npad;
-  const uint32_t ftile = (uint32_t)npad * kRowBytes;
-  const uint32_t stage_bytes = 4u * kWTile + 2u * ftile;
+  const uint32_t fmax = (uint32_t)a.npad_max * kRowBytes;
+  const uint32_t stage_bytes = 4u * kWTile + 2u * fmax;
   // per stage: W pp_hi, pp_lo, ph_hi, ph_lo, F hi, F lo
   const uint32_t ctrl = base + 2u * stage_bytes;
   const uint32_t bar_full = ctrl, bar_empty = ctrl + 16, bar_done = ctrl + 32;
   unsigned char* gctrl = gbase + 2u * stage_bytes;
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(gctrl + 48);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gctrl + 52);
-  int* s_off = reinterpret_cast<int*>(gctrl + 64);
+  volatile int4* s_item = reinterpret_cast<volatile int4*>(gctrl + 64);
+  int* s_off = reinterpret_cast<int*>(gctrl + 128);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, split = blockIdx.y;
-  const int row0 = tile * kRows;
-  const int nvalid = min(kRows, a.nrow - row0);  // rows of this tile with an l
-
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(bar_full + 8 * s, kProducers);
@@ -224,8 +217,6 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int r = threadIdx.x; r < kRows; r += kThreads)
-    s_off[r] = r < nvalid ? a.rowoff[row0 + r] : 0;
   if (warp == kProducers) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32((const void*)tmem_slot)),
@@ -238,176 +229,218 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  const double omd = a.lam[0];
-  const float om = (float)omd, om2 = (float)(omd * omd), inv_om2 = (float)(1.0 / (omd * omd));
-  const int kb_begin = split * a.kbps;
-  const size_t frow = (size_t)a.kpad * P::kElem;  // bytes per F row
+  // this producer lane writes bytes [col, col + 4) of rows r = warp + 16 i;
+  // all its rows have r % 8 == warp % 8, so the swizzled offset is fixed
+  const uint32_t col = (uint32_t)(P::kPerLane * lane) * P::kElem;
+  const uint32_t swz = (((col >> 4) ^ (uint32_t)(warp & 7)) << 4) | (col & 15);
 
-  if (warp < kProducers) {
-    // ------------------------------------------------------------ producers
-    // this lane writes bytes [col, col + 4) of rows r = warp + 16 i; all its
-    // rows have r % 8 == warp % 8, so the swizzled offset is fixed
-    const uint32_t col = (uint32_t)(P::kPerLane * lane) * P::kElem;
-    const uint32_t swz = (((col >> 4) ^ (uint32_t)(warp & 7)) << 4) | (col & 15);
-    const int fchunks = 8 * npad;  // 16-byte chunks per F tile
-    for (int kb = 0; kb < a.kbps; ++kb) {
-      const int s = kb & 1;
-      if (kb >= 2 && !mbar_wait(bar_empty + 8 * s, ((kb >> 1) + 1) & 1)) {
-        atomicOr(a.err, 1);
-        *abort_flag = 1;
-      }
-      if (*abort_flag) break;
-      const uint32_t st = base + s * stage_bytes;
-      const int k0 = (kb_begin + kb) * KB;
-      const size_t fk = (size_t)k0 * P::kElem;
-      for (int c = threadIdx.x; c < 2 * fchunks; c += 32 * kProducers) {
-        const int t = c >= fchunks, rem = c - t * fchunks, row = rem >> 3, ch = rem & 7;
-        cp_async16(st + 4u * kWTile + t * ftile + row * kRowBytes + ((ch ^ (row & 7)) << 4),
-                   (t ? a.Flo : a.Fhi) + (size_t)row * frow + fk + ch * 16);
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      // this lane's loop points as offsets into the halo table (padding points
-      // use a valid entry: their F is zero)
-      int pb[P::kPerLane];
-      if constexpr (P::kPerLane == 2) {
-        const int2 v = __ldg(reinterpret_cast<const int2*>(a.kbase + k0) + lane);
-        pb[0] = v.x;
-        pb[1] = v.y;
-      } else {
-        pb[0] = __ldg(a.kbase + k0 + lane);
-      }
+  uint32_t g = 0;  // K-blocks this CTA has put through the pipeline
+  uint32_t j = 0;  // items this CTA has finished (phase of bar_done)
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(a.counter, 1);
+      const int4 v = it < a.n_items ? a.items[it] : make_int4(-1, 0, 0, 0);
+      s_item->x = v.x;
+      s_item->y = v.y;
+      s_item->z = v.z;
+      s_item->w = v.w;
+    }
+    __syncthreads();
+    const int pt = s_item->x, tile = s_item->y, kb0 = s_item->z, cnt = s_item->w;
+    if (pt < 0 || *abort_flag) break;
+    const PointDesc& pd = a.pts[pt];
+    if (pd.skip && *pd.skip) {  // finished point: nothing to do
+      __syncthreads();
+      continue;
+    }
+    const int row0 = tile * kRows;
+    const int nvalid = min(kRows, pd.nrow - row0);  // rows of this tile with an l
+    for (int r = threadIdx.x; r < kRows; r += kThreads)
+      s_off[r] = r < nvalid ? pd.rowoff[row0 + r] : 0;
+    __syncthreads();
+    const int npad = pd.npad, nsets = pd.nsets;
+    const double omd = pd.lam[0];
+    const float om = (float)omd, om2 = (float)(omd * omd), inv_om2 = (float)(1.0 / (omd * omd));
+
+    if (warp < kProducers) {
+      // ---------------------------------------------------------- producers
+      const float4* ext = pd.ext;
+      const unsigned char* Fhi = pd.Fhi;
+      const unsigned char* Flo = pd.Flo;
+      const size_t frow = (size_t)pd.kpad_tc * P::kElem;  // bytes per F row
+      const int fchunks = 8 * npad;  // 16-byte chunks per F tile
+      for (int kb = 0; kb < cnt; ++kb) {
+        const uint32_t gk = g + kb;
+        const uint32_t s = gk & 1;
+        if (gk >= 2 && !mbar_wait(bar_empty + 8 * s, ((gk >> 1) + 1) & 1)) {
+          atomicOr(a.err, 1);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) break;
+        const uint32_t st = base + s * stage_bytes;
+        const int k0 = (kb0 + kb) * KB;
+        const size_t fk = (size_t)k0 * P::kElem;
+        for (int c = threadIdx.x; c < 2 * fchunks; c += 32 * kProducers) {
+          const int t = c >= fchunks, rem = c - t * fchunks, row = rem >> 3, ch = rem & 7;
+          cp_async16(st + 4u * kWTile + t * fmax + row * kRowBytes + ((ch ^ (row & 7)) << 4),
+                     (t ? Flo : Fhi) + (size_t)row * frow + fk + ch * 16);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // this lane's loop points as offsets into the halo table (padding
+        // points use a valid entry: their F is zero)
+        int pb[P::kPerLane];
+        if constexpr (P::kPerLane == 2) {
+          const int2 v = __ldg(reinterpret_cast<const int2*>(pd.kbase + k0) + lane);
+          pb[0] = v.x;
+          pb[1] = v.y;
+        } else {
+          pb[0] = __ldg(pd.kbase + k0 + lane);
+        }
 #pragma unroll 1
-      for (int i0 = 0; i0 < kRows / kProducers; i0 += kBatch) {
-        if (warp + kProducers * i0 >= nvalid) {  // rows without an l: zeros
+        for (int i0 = 0; i0 < kRows / kProducers; i0 += kBatch) {
+          if (warp + kProducers * i0 >= nvalid) {  // rows without an l: zeros
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+              const uint32_t dst =
+                  st + (uint32_t)(warp + kProducers * (i0 + i)) * kRowBytes + swz;
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(0u)
+                             : "memory");
+            }
+            continue;
+          }
+          // table loads of kBatch rows first (memory-level parallelism)
+          float4 ta[kBatch][P::kPerLane], tb[kBatch][P::kPerLane];
 #pragma unroll
           for (int i = 0; i < kBatch; ++i) {
-            const uint32_t dst = st + (uint32_t)(warp + kProducers * (i0 + i)) * kRowBytes + swz;
+            const int off = s_off[warp + kProducers * (i0 + i)];
+#pragma unroll
+            for (int jj = 0; jj < P::kPerLane; ++jj) {
+              ta[i][jj] = __ldg(ext + (pb[jj] + off));
+              tb[i][jj] = __ldg(ext + (pb[jj] - off));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) {
+            const int r = warp + kProducers * (i0 + i);
+            uint32_t v[4];
+            if constexpr (PREC == TUFRG_BF16X3) {
+              float2 wpp, wph;
+              weights2(ta[i][0], tb[i][0], ta[i][1], tb[i][1], om, om2, inv_om2, wpp, wph);
+              const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
+              const __nv_bfloat162 pl = __float22bfloat162_rn(
+                  __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
+              const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
+              const __nv_bfloat162 hl = __float22bfloat162_rn(
+                  __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
+              std::memcpy(&v[0], &ph, 4);
+              std::memcpy(&v[1], &pl, 4);
+              std::memcpy(&v[2], &hh, 4);
+              std::memcpy(&v[3], &hl, 4);
+            } else {
+              float wpp, wph;
+              weights(ta[i][0], tb[i][0], om, om2, inv_om2, wpp, wph);
+              v[0] = tf32_rna(wpp);
+              v[1] = tf32_rna(wpp - __uint_as_float(v[0]));
+              v[2] = tf32_rna(wph);
+              v[3] = tf32_rna(wph - __uint_as_float(v[2]));
+            }
+            const uint32_t dst = st + (uint32_t)r * kRowBytes + swz;
 #pragma unroll
             for (int t = 0; t < 4; ++t)
-              asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(0u) : "memory");
-          }
-          continue;
-        }
-        // table loads of kBatch rows first (memory-level parallelism)
-        float4 ta[kBatch][P::kPerLane], tb[kBatch][P::kPerLane];
-#pragma unroll
-        for (int i = 0; i < kBatch; ++i) {
-          const int off = s_off[warp + kProducers * (i0 + i)];
-#pragma unroll
-          for (int j = 0; j < P::kPerLane; ++j) {
-            ta[i][j] = __ldg(a.ext + (pb[j] + off));
-            tb[i][j] = __ldg(a.ext + (pb[j] - off));
+              asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t])
+                           : "memory");
           }
         }
-#pragma unroll
-        for (int i = 0; i < kBatch; ++i) {
-          const int r = warp + kProducers * (i0 + i);
-          uint32_t v[4];
-          if constexpr (PREC == TUFRG_BF16X3) {
-            float2 wpp, wph;
-            weights2(ta[i][0], tb[i][0], ta[i][1], tb[i][1], om, om2, inv_om2, wpp, wph);
-            const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
-            const __nv_bfloat162 pl = __float22bfloat162_rn(
-                __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
-            const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
-            const __nv_bfloat162 hl = __float22bfloat162_rn(
-                __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
-            std::memcpy(&v[0], &ph, 4);
-            std::memcpy(&v[1], &pl, 4);
-            std::memcpy(&v[2], &hh, 4);
-            std::memcpy(&v[3], &hl, 4);
-          } else {
-            float wpp, wph;
-            weights(ta[i][0], tb[i][0], om, om2, inv_om2, wpp, wph);
-            v[0] = tf32_rna(wpp);
-            v[1] = tf32_rna(wpp - __uint_as_float(v[0]));
-            v[2] = tf32_rna(wph);
-            v[3] = tf32_rna(wph - __uint_as_float(v[2]));
-          }
-          const uint32_t dst = st + (uint32_t)r * kRowBytes + swz;
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-            asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t]) : "memory");
-        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_full + 8 * s);
       }
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar_full + 8 * s);
+    } else if (lane == 0) {
+      // ------------------------------------------------------- MMA issuer
+      // K-blocks go round-robin to nsets accumulator sets (shorter FP32
+      // accumulation chains); set q, channel c at TMEM columns (2 q + c) npad
+      const uint32_t idesc = (1u << 4) | (P::kFormat << 7) | (P::kFormat << 10) |
+                             ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+      for (int kb = 0; kb < cnt; ++kb) {
+        const uint32_t gk = g + kb;
+        const uint32_t s = gk & 1;
+        if (!mbar_wait(bar_full + 8 * s, (gk >> 1) & 1)) {
+          atomicOr(a.err, 2);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * stage_bytes;
+        const uint32_t fh = st + 4u * kWTile, fl = fh + fmax;
+        const int set = kb % nsets;
+        const bool first = kb < nsets;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction
+          const uint32_t o = 32u * kk;
+          const uint64_t bh = smem_desc(fh + o), bl = smem_desc(fl + o);
+#pragma unroll
+          for (int ch = 0; ch < 2; ++ch) {
+            const uint32_t d = tmem + (uint32_t)((2 * set + ch) * npad);
+            const uint64_t ah = smem_desc(st + (2 * ch) * kWTile + o);
+            const uint64_t al = smem_desc(st + (2 * ch + 1) * kWTile + o);
+            mma<PREC>(d, ah, bh, idesc, !(first && kk == 0));
+            mma<PREC>(d, al, bh, idesc, 1);
+            mma<PREC>(d, ah, bl, idesc, 1);
+          }
+        }
+        mma_commit(bar_empty + 8 * s);
+      }
+      mma_commit(bar_done);  // arrives once every issued MMA has completed
     }
-  } else if (lane == 0) {
-    // --------------------------------------------------------- MMA issuer
-    // K-blocks go round-robin to nsets accumulator sets (shorter FP32
-    // accumulation chains); set q, channel c at TMEM columns (2 q + c) npad
-    const uint32_t idesc = (1u << 4) | (P::kFormat << 7) | (P::kFormat << 10) |
-                           ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-    for (int kb = 0; kb < a.kbps; ++kb) {
-      const int s = kb & 1;
-      if (!mbar_wait(bar_full + 8 * s, (kb >> 1) & 1)) {
-        atomicOr(a.err, 2);
+
+    // ----------------------------------------------------------- epilogue
+    if (warp < 8) {  // warps 0-3: pp, 4-7: ph; warp w reads TMEM lanes 32 (w % 4)..
+      const bool ok = mbar_wait(bar_done, j & 1);
+      if (!ok) {
+        atomicOr(a.err, 4);
         *abort_flag = 1;
       }
-      if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = base + s * stage_bytes;
-      const uint32_t fh = st + 4u * kWTile, fl = fh + ftile;
-      const int set = kb % a.nsets;
-      const bool first = kb < a.nsets;
+      if (ok && !*abort_flag) {
+        const int quad = warp & 3, ch = warp >> 2;
+        const int row = quad * 32 + lane;
+        const int sets = min(nsets, cnt);
+        const int split = kb0 / a.kbps;
+        float* out = a.partial + pd.off_partial +
+                     (size_t)(split * 2 + ch) * npad * pd.nrow_pad + row0 + row;
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+          float acc[16];
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction
-        const uint32_t o = 32u * kk;
-        const uint64_t bh = smem_desc(fh + o), bl = smem_desc(fl + o);
+          for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+          for (int q = 0; q < sets; ++q) {
+            uint32_t r[16];
+            const uint32_t taddr =
+                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((2 * q + ch) * npad + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, "
+                "%9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int ch = 0; ch < 2; ++ch) {
-          const uint32_t d = tmem + (uint32_t)((2 * set + ch) * npad);
-          const uint64_t ah = smem_desc(st + (2 * ch) * kWTile + o);
-          const uint64_t al = smem_desc(st + (2 * ch + 1) * kWTile + o);
-          mma<PREC>(d, ah, bh, idesc, !(first && kk == 0));
-          mma<PREC>(d, al, bh, idesc, 1);
-          mma<PREC>(d, ah, bl, idesc, 1);
+            for (int e = 0; e < 16; ++e) acc[e] += __uint_as_float(r[e]);
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) out[(size_t)(c0 + e) * pd.nrow_pad] = acc[e];
         }
       }
-      mma_commit(bar_empty + 8 * s);
     }
-    mma_commit(bar_done);  // arrives once every issued MMA has completed
-  }
-
-  // ------------------------------------------------------------- epilogue
-  if (warp < 8) {  // warps 0-3: pp, 4-7: ph; warp w reads TMEM lanes 32 (w % 4)..
-    const bool ok = mbar_wait(bar_done, 0);
-    if (!ok) {
-      atomicOr(a.err, 4);
-      *abort_flag = 1;
-    }
+    g += cnt;
+    ++j;
+    // the accumulators are read and s_off, s_item are free for the next item
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && !*abort_flag) {
-      const int quad = warp & 3, ch = warp >> 2;
-      const int row = quad * 32 + lane;
-      const int sets = min(a.nsets, a.kbps);
-      float* out = a.partial + (size_t)(split * 2 + ch) * npad * a.nrow_pad + row0 + row;
-      for (int c0 = 0; c0 < npad; c0 += 16) {
-        float acc[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-        for (int q = 0; q < sets; ++q) {
-          uint32_t r[16];
-          const uint32_t taddr =
-              tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((2 * q + ch) * npad + c0);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-              "%10, %11, %12, %13, %14, %15}, [%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(r[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) out[(size_t)(c0 + j) * a.nrow_pad] = acc[j];
-      }
-    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -419,109 +452,117 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   }
 }
 
+constexpr int kTableBlock = 256, kTablePerThread = 4;
+
 // Per-scale FP32 table (xi, A, H, |xi|) with a wrap-around halo of hx, hy
 // points on each side, so that p +- l/2 needs no wrapping.
-__global__ void scale_table_ext_kernel(const double4_32a* __restrict__ tab,
-                                       float4* __restrict__ ext, int nfx, int nfy, int hx,
-                                       int hy, int wy, int n_ext,
-                                       const double* __restrict__ lam) {
-  const double om = lam[0];
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_ext; e += gridDim.x * blockDim.x) {
-    int ix = e / wy - hx, iy = e % wy - hy;
-    ix += ix < 0 ? nfx : 0;
-    ix -= ix >= nfx ? nfx : 0;
-    iy += iy < 0 ? nfy : 0;
-    iy -= iy >= nfy ? nfy : 0;
-    const double xi = tab[ix * nfy + iy].x, x = fabs(xi), A = 1.0 / (om + x);
-    ext[e] = make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), (float)x);
+__global__ void __launch_bounds__(kTableBlock)
+    scale_table_ext_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
+                           int n) {
+  const int p = point_of(prefix, n, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const double om = pd.lam[0];
+  const int e0 = (blockIdx.x - prefix[p]) * kTableBlock * kTablePerThread + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kTablePerThread; ++q) {
+    const int e = e0 + q * kTableBlock;
+    if (e >= pd.n_ext) break;
+    int ix = e / pd.wy - pd.hx, iy = e % pd.wy - pd.hy;
+    ix += ix < 0 ? pd.nfx : 0;
+    ix -= ix >= pd.nfx ? pd.nfx : 0;
+    iy += iy < 0 ? pd.nfy : 0;
+    iy -= iy >= pd.nfy ? pd.nfy : 0;
+    const double xi = pd.tab[ix * pd.nfy + iy].x, x = fabs(xi), A = 1.0 / (om + x);
+    pd.ext[e] =
+        make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), (float)x);
   }
 }
 
 // FP64 combination of the split-K partials in fixed order; -1/4 (pp), +1/4
 // (ph); scatter to (m, n), (n, m) of the row's l and of its partner.
-__global__ void loops_tc_reduce_kernel(const float* __restrict__ partial, int ksplit, int npad,
-                                       int nrow, int nrow_pad, const int2* __restrict__ rowmap,
-                                       int nl, int npair, const int* __restrict__ pair, int nff,
+__global__ void loops_tc_reduce_kernel(const PointDesc* __restrict__ pts,
+                                       const int* __restrict__ prefix, int n,
+                                       const float* __restrict__ partial,
                                        double* __restrict__ chi) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2 * npair * nrow) return;
-  const int row = idx % nrow;
-  const int r = idx / nrow;
-  const int q = r % npair, ch = r / npair;
+  const int p = point_of(prefix, n, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int idx = (blockIdx.x - prefix[p]) * blockDim.x + threadIdx.x;
+  if (idx >= 2 * pd.npair * pd.nrow) return;
+  const int row = idx % pd.nrow;
+  const int r = idx / pd.nrow;
+  const int q = r % pd.npair, ch = r / pd.npair;
+  const float* src = partial + pd.off_partial + ((size_t)ch * pd.npad + q) * pd.nrow_pad + row;
+  const size_t stride = (size_t)2 * pd.npad * pd.nrow_pad;
   double s = 0.0;
-  for (int sp = 0; sp < ksplit; ++sp)
-    s += (double)partial[((size_t)(sp * 2 + ch) * npad + q) * nrow_pad + row];
+  for (int sp = 0; sp < pd.ksplit; ++sp) s += (double)src[sp * stride];
   s *= ch == 0 ? -0.25 : 0.25;
-  const int mn = pair[q];
-  const int m = mn / nff, n = mn % nff;
-  const int2 lp = rowmap[row];
-  double* out = chi + ((size_t)ch * nl + lp.x) * nff * nff;
-  out[m * nff + n] = s;
-  out[n * nff + m] = s;
+  const int nff = pd.nff;
+  const int mn = pd.pair[q];
+  const int m = mn / nff, nn = mn % nff;
+  const int2 lp = pd.rowmap[row];
+  double* out = chi + pd.off_chi + ((size_t)ch * pd.nl + lp.x) * nff * nff;
+  out[m * nff + nn] = s;
+  out[nn * nff + m] = s;
   if (lp.y != lp.x) {
-    out = chi + ((size_t)ch * nl + lp.y) * nff * nff;
-    out[m * nff + n] = s;
-    out[n * nff + m] = s;
+    out = chi + pd.off_chi + ((size_t)ch * pd.nl + lp.y) * nff * nff;
+    out[m * nff + nn] = s;
+    out[nn * nff + m] = s;
   }
 }
 
 }  // namespace
 
 size_t tc_smem_bytes(int npad) {
-  return 1024 + 2 * (4 * (size_t)kWTile + 2 * (size_t)npad * kRowBytes) + 64 + 4 * kRows;
+  return 1024 + 2 * (4 * (size_t)kWTile + 2 * (size_t)npad * kRowBytes) + 128 + 4 * kRows;
 }
 
-tufrg_status prepare_loops_tc(tufrg_ctx* c) {
-  const int smem = (int)tc_smem_bytes(c->tc_npad);
-  if (c->p.precision == TUFRG_BF16X3)
+int tc_k_per_block(int prec) { return prec == TUFRG_BF16X3 ? kRowBytes / 2 : kRowBytes / 4; }
+
+int table_ctas(int n_ext) {
+  const int per = kTableBlock * kTablePerThread;
+  return (n_ext + per - 1) / per;
+}
+
+tufrg_status prepare_loops_tc_multi(const MultiView& v) {
+  const int smem = smem_optin();
+  if ((int)tc_smem_bytes(v.npad_max) > smem) return TUFRG_ERR_ARG;
+  if (v.tc_prec == TUFRG_BF16X3)
     TUFRG_CUDA(cudaFuncSetAttribute(loops_tc_kernel<TUFRG_BF16X3>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  else
+  else if (v.tc_prec == TUFRG_3XTF32)
     TUFRG_CUDA(cudaFuncSetAttribute(loops_tc_kernel<TUFRG_3XTF32>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return TUFRG_OK;
 }
 
-tufrg_status launch_loops_tc(tufrg_ctx* c, double* chi, cudaStream_t st) {
-  const int n_ext = (c->nfx + 2 * c->tc_hx) * c->tc_wy;
-  const int blocks = std::min((n_ext + 255) / 256, 152 * 8);
-  scale_table_ext_kernel<<<blocks, 256, 0, st>>>(c->d_tab, c->d_ext, c->nfx, c->nfy, c->tc_hx,
-                                                 c->tc_hy, c->tc_wy, n_ext, c->d_lambda);
+tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, bool zero, cudaStream_t st) {
+  if (v.tc_prec == TUFRG_FP64 || v.n_items == 0) return TUFRG_ERR_ARG;
+  scale_table_ext_kernel<<<v.total(kKindTable), kTableBlock, 0, st>>>(
+      v.d, v.dprefix(kKindTable), v.n);
   TUFRG_CUDA(cudaGetLastError());
+  TUFRG_CUDA(cudaMemsetAsync(v.d_counter, 0, sizeof(int), st));
   TcArgs a;
-  a.ext = c->d_ext;
-  a.kbase = c->d_kbase;
-  a.rowoff = c->d_rowoff;
-  a.Fhi = c->d_Fhi;
-  a.Flo = c->d_Flo;
-  a.partial = c->d_partial_tc;
-  a.err = c->d_err;
-  a.lam = c->d_lambda;
-  a.nfx = c->nfx;
-  a.nfy = c->nfy;
-  a.hx = c->tc_hx;
-  a.hy = c->tc_hy;
-  a.wy = c->tc_wy;
-  a.kdim = c->kdim;
-  a.kpad = c->tc_kpad;
-  a.kbps = c->tc_kbps;
-  a.nrow = c->nrow;
-  a.nrow_pad = c->tc_nrow_pad;
-  a.npad = c->tc_npad;
-  a.nsets = c->tc_nsets;
-  a.tmem_cols = c->tc_tmem_cols;
-  const dim3 grid(c->tc_nrow_pad / kRows, c->tc_ksplit);
-  const size_t smem = tc_smem_bytes(c->tc_npad);
-  if (c->p.precision == TUFRG_BF16X3)
-    loops_tc_kernel<TUFRG_BF16X3><<<grid, kThreads, smem, st>>>(a);
+  a.pts = v.d;
+  a.items = v.d_items;
+  a.n_items = v.n_items;
+  a.counter = v.d_counter;
+  a.partial = v.d_partial;
+  a.err = v.d_err;
+  a.kbps = v.kbps;
+  a.npad_max = v.npad_max;
+  a.tmem_cols = v.tmem_cols;
+  const int ctas = std::min(v.ctas, v.n_items);
+  const size_t smem = tc_smem_bytes(v.npad_max);
+  if (v.tc_prec == TUFRG_BF16X3)
+    loops_tc_kernel<TUFRG_BF16X3><<<ctas, kThreads, smem, st>>>(a);
   else
-    loops_tc_kernel<TUFRG_3XTF32><<<grid, kThreads, smem, st>>>(a);
+    loops_tc_kernel<TUFRG_3XTF32><<<ctas, kThreads, smem, st>>>(a);
   TUFRG_CUDA(cudaGetLastError());
-  TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * 2 * c->nl * c->nff * c->nff, st));
-  const int total = 2 * c->npair * c->nrow;
-  loops_tc_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(
-      c->d_partial_tc, c->tc_ksplit, c->tc_npad, c->nrow, c->tc_nrow_pad, c->d_rowmap, c->nl,
-      c->npair, c->d_pair, c->nff, chi);
+  if (zero) TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * v.chi_elems, st));
+  loops_tc_reduce_kernel<<<v.total(kKindReduce), 256, 0, st>>>(v.d, v.dprefix(kKindReduce),
+                                                               v.n, v.d_partial, chi);
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }

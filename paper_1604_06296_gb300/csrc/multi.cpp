@@ -1,0 +1,216 @@
+// Multi-point views: the per-point descriptors of n contexts, the CTA prefix
+// tables of the multi-point launches, and the work items of the persistent
+// tensor-core loop kernel.
+//
+// Work items are (point, tile of 128 l-rows, first K-block, K-blocks).  A
+// point's loop sum over its nkb K-blocks is cut into ksplit = ceil(nkb/kbps)
+// ranges; each range of each tile is one item whose FP32 partial sum is
+// combined with the others in FP64 (fixed order) by the reduction kernel.
+// The persistent CTAs take items from a queue ordered by estimated cost,
+// longest first, so the uneven points of a batch end together.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "internal.h"
+
+namespace tufrg {
+namespace {
+
+template <class T>
+tufrg_status upload_to(T** dptr, const std::vector<T>& h, cudaStream_t st) {
+  if (*dptr) cudaFree(*dptr);
+  *dptr = nullptr;
+  const size_t bytes = std::max<size_t>(h.size(), 1) * sizeof(T);
+  if (cudaMalloc((void**)dptr, bytes) != cudaSuccess) return TUFRG_ERR_OOM;
+  if (!h.empty())
+    TUFRG_CUDA(cudaMemcpyAsync(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return TUFRG_OK;
+}
+
+// accumulation chains of at most 4096 loop points per item: the tensor core
+// rounds the FP32 accumulator once per MMA instruction, so the relative error
+// of an item's partial sum grows with its number of K-blocks per
+// accumulator set (BF16x3 at 8192 points per item reached ~1e-5 at
+// production sizes, 4096 keep it near 5e-6)
+int max_kbps(int prec) { return 4096 / tc_k_per_block(prec); }
+
+}  // namespace
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return 1;
+  return n;
+}
+
+int smem_optin() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 48 * 1024;
+  return n;
+}
+
+int view_default_kbps(const MultiView& v) {
+  if (v.tc_prec == TUFRG_FP64) return 0;
+  long long work = 0;  // K-block x tile units
+  for (const PointDesc& d : v.h) work += (long long)d.nkb * (d.nrow_pad / 128);
+  const long long S = sm_count(), cap = max_kbps(v.tc_prec);
+  const long long waves = std::max(1LL, (work + S * cap - 1) / (S * cap));
+  const long long kbps = (work + S * waves - 1) / (S * waves);
+  return (int)std::max(1LL, std::min(cap, kbps));
+}
+
+tufrg_status view_set_kbps(MultiView& v, int kbps, cudaStream_t st) {
+  if (v.tc_prec == TUFRG_FP64) return TUFRG_OK;
+  if (kbps < 1 || kbps > max_kbps(v.tc_prec)) return TUFRG_ERR_ARG;
+  v.kbps = kbps;
+  struct Item {
+    int4 it;
+    long long cost;
+  };
+  std::vector<Item> items;
+  size_t off = 0;
+  v.npad_max = 16;
+  v.tmem_cols = 32;
+  for (int i = 0; i < v.n; ++i) {
+    PointDesc& d = v.h[i];
+    d.ksplit = (d.nkb + kbps - 1) / kbps;
+    d.off_partial = (long long)off;
+    off += (size_t)d.ksplit * 2 * d.npad * d.nrow_pad;
+    v.npad_max = std::max(v.npad_max, d.npad);
+    int cols = 32;
+    while (cols < d.nsets * 2 * d.npad) cols *= 2;
+    v.tmem_cols = std::max(v.tmem_cols, cols);
+    const int tiles = d.nrow_pad / 128;
+    for (int t = 0; t < tiles; ++t) {
+      const int valid = std::min(128, d.nrow - 128 * t);
+      for (int sp = 0; sp < d.ksplit; ++sp) {
+        const int kb0 = sp * kbps, cnt = std::min(kbps, d.nkb - kb0);
+        // producers: ~ valid rows per K-block; tensor cores: ~ pair columns
+        items.push_back({make_int4(i, t, kb0, cnt), (long long)cnt * (2 * valid + d.npad)});
+      }
+    }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const Item& a, const Item& b) { return a.cost > b.cost; });
+  std::vector<int4> packed(items.size());
+  for (size_t k = 0; k < items.size(); ++k) packed[k] = items[k].it;
+  v.n_items = (int)packed.size();
+  TUFRG_CHECK(upload_to(&v.d_items, packed, st));
+  if (off > v.partial_elems || !v.d_partial) {
+    if (v.d_partial) cudaFree(v.d_partial);
+    v.d_partial = nullptr;
+    v.partial_elems = 0;
+    if (cudaMalloc((void**)&v.d_partial, std::max<size_t>(off, 1) * sizeof(float)) != cudaSuccess)
+      return TUFRG_ERR_OOM;
+    v.partial_elems = off;
+  }
+  v.ctas = sm_count();
+  TUFRG_CHECK(upload_to(&v.d, v.h, st));
+  TUFRG_CHECK(prepare_loops_tc_multi(v));
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  return TUFRG_OK;
+}
+
+tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* const* lam,
+                        const int* const* skip, int* err, int tc_prec, int kbps,
+                        cudaStream_t st) {
+  view_free(v);
+  if (n < 1) return TUFRG_ERR_ARG;
+  v.n = n;
+  v.h.assign(n, PointDesc{});
+  v.d_err = err;
+  v.tc_prec = tc_prec;
+  v.prefix.assign((size_t)kKinds * (n + 1), 0);
+  size_t off_state = 0, off_chi = 0, off_bt = 0, off_fkey = 0;
+  const bool tc = tc_prec != TUFRG_FP64;
+  for (int i = 0; i < n; ++i) {
+    const tufrg_ctx* c = ctx[i];
+    if (tc && c->p.precision != tc_prec) return TUFRG_ERR_ARG;
+    PointDesc& d = v.h[i];
+    d.nl = c->nl;
+    d.nff = c->nff;
+    d.nb = c->nb;
+    d.ncx = c->ncx;
+    d.ncy = c->ncy;
+    d.nd = 2 * c->proj.dmax + 1;
+    d.nkeys = c->proj.nkeys;
+    d.feedback = c->p.feedback;
+    d.U = c->p.U;
+    for (int t = 0; t < 3; ++t) d.term_off[t] = c->term_off[t];
+    d.npair = c->npair;
+    d.nrow = c->nrow;
+    d.nfx = c->nfx;
+    d.nfy = c->nfy;
+    d.hx = c->tc_hx;
+    d.hy = c->tc_hy;
+    d.wy = c->tc_wy;
+    d.n_ext = tc ? (c->nfx + 2 * c->tc_hx) * c->tc_wy : 0;
+    d.nkb = c->tc_nkb;
+    d.kpad_tc = c->tc_kpad;
+    d.nrow_pad = c->tc_nrow_pad;
+    d.npad = c->tc_npad;
+    d.nsets = c->tc_nsets;
+    d.off_state = (long long)off_state;
+    d.off_chi = (long long)off_chi;
+    d.off_bt = (long long)off_bt;
+    d.off_fkey = (long long)off_fkey;
+    off_state += (size_t)3 * c->nl * c->nff * c->nff;
+    off_chi += (size_t)2 * c->nl * c->nff * c->nff;
+    off_bt += (size_t)3 * c->nb * c->nb * c->nl;
+    off_fkey += (size_t)c->proj.nkeys;
+    d.tab = c->d_tab;
+    d.ext = c->d_ext;
+    d.kbase = c->d_kbase;
+    d.rowoff = c->d_rowoff;
+    d.Fhi = c->d_Fhi;
+    d.Flo = c->d_Flo;
+    d.rowmap = c->d_rowmap;
+    d.pair = c->d_pair;
+    d.coef = c->d_coef;
+    d.phase = c->d_phase;
+    d.keys = c->d_key;
+    d.row_ptr = c->d_row_ptr;
+    d.terms = c->d_terms;
+    d.lam = lam[i];
+    d.skip = skip ? skip[i] : nullptr;
+    const int cnt[kKinds] = {
+        tc ? table_ctas(d.n_ext) : 0,
+        tc ? (2 * d.npair * d.nrow + 255) / 256 : 0,
+        d.feedback ? 3 * d.nl : 0,
+        d.feedback ? dft_ctas(d.nkeys) : 0,
+        3 * d.nl,
+        d.nl,
+    };
+    for (int k = 0; k < kKinds; ++k)
+      v.prefix[(size_t)k * (n + 1) + i + 1] = v.prefix[(size_t)k * (n + 1) + i] + cnt[k];
+    v.nff_max = std::max(v.nff_max, d.nff);
+    v.nb_max = std::max(v.nb_max, d.nb);
+    v.nd_max = std::max(v.nd_max, d.nd);
+    v.nc_sum_max = std::max(v.nc_sum_max, d.ncx + d.ncy);
+  }
+  v.state_elems = off_state;
+  v.chi_elems = off_chi;
+  v.bt_elems = off_bt;
+  v.fkey_elems = off_fkey;
+  TUFRG_CHECK(upload_to(&v.d_prefix, v.prefix, st));
+  if (cudaMalloc((void**)&v.d_counter, sizeof(int)) != cudaSuccess) return TUFRG_ERR_OOM;
+  TUFRG_CHECK(prepare_project_multi(v));
+  TUFRG_CHECK(prepare_products_multi(v));
+  if (tc) return view_set_kbps(v, kbps > 0 ? kbps : view_default_kbps(v), st);
+  TUFRG_CHECK(upload_to(&v.d, v.h, st));
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  return TUFRG_OK;
+}
+
+void view_free(MultiView& v) {
+  void* ptrs[] = {v.d, v.d_prefix, v.d_items, v.d_counter, v.d_partial};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  v = MultiView();
+}
+
+}  // namespace tufrg

@@ -3,10 +3,11 @@
 //   dC = -V^C chi^ph V^C
 //   dD =  2 V^D chi^ph V^D - V^C chi^ph V^D - V^D chi^ph V^C
 //      =  (2 V^D - V^C) (chi^ph V^D) - V^D (chi^ph V^C)
-// One CTA per l; the five Nff x Nff operands and three intermediate products
-// sit in shared memory (8 Nff^2 doubles <= 54 KB for Nff = 29).  FP64 for an
-// FP64 context, FP32 arithmetic for the mixed-precision contexts.
-#include "internal.h"
+// One CTA per (point, l) over all points of a batch; the five Nff x Nff
+// operands and three intermediate products sit in shared memory (8 Nff^2
+// doubles <= 54 KB for Nff = 29).  FP64 for an FP64 context, FP32 arithmetic
+// for the mixed-precision contexts.
+#include "device_util.cuh"
 
 namespace tufrg {
 namespace {
@@ -23,11 +24,18 @@ __device__ __forceinline__ void matmul(const T* __restrict__ a, const T* __restr
 }
 
 // arithmetic in T (FP64, or FP32 for the mixed-precision contexts); inputs
-// and the derivative are FP64
+// and the derivative are FP64; dy is multiplied by lam[1] when scaled
 template <class T>
-__global__ void products_kernel(const double* __restrict__ v, const double* __restrict__ chi,
-                                double* __restrict__ dy, int nl, int nff,
-                                const double* __restrict__ scale) {
+__global__ void products_kernel(const PointDesc* __restrict__ pts,
+                                const int* __restrict__ prefix, int np,
+                                const double* __restrict__ vbase,
+                                const double* __restrict__ chibase, double* __restrict__ dybase,
+                                int scaled) {
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nl = pd.nl, nff = pd.nff;
+  const int l = blockIdx.x - prefix[p];
   extern __shared__ double smd[];
   T* sm = reinterpret_cast<T*>(smd);
   const int n2 = nff * nff;
@@ -39,9 +47,11 @@ __global__ void products_kernel(const double* __restrict__ v, const double* __re
   T* T1 = Xh + n2;
   T* T2 = T1 + n2;
   T* T3 = T2 + n2;
-  const int l = blockIdx.x;
   const size_t chan = (size_t)nl * n2;
   const size_t off = (size_t)l * n2;
+  const double* v = vbase + pd.off_state;
+  const double* chi = chibase + pd.off_chi;
+  double* dy = dybase + pd.off_state;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
     VP[e] = (T)v[off + e];
     VC[e] = (T)v[chan + off + e];
@@ -54,17 +64,17 @@ __global__ void products_kernel(const double* __restrict__ v, const double* __re
   matmul(Xh, VC, T2, nff);  // chi^ph V^C
   matmul(Xh, VD, T3, nff);  // chi^ph V^D
   __syncthreads();
-  const double sc = scale ? scale[0] : 1.0;
+  const double sc = scaled ? pd.lam[1] : 1.0;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
     const int i = e / nff, j = e % nff;
-    T p = 0, cc = 0, d = 0;
+    T pp = 0, cc = 0, d = 0;
     for (int k = 0; k < nff; ++k) {
-      p = fma(VP[i * nff + k], T1[k * nff + j], p);
+      pp = fma(VP[i * nff + k], T1[k * nff + j], pp);
       cc = fma(VC[i * nff + k], T2[k * nff + j], cc);
       d = fma(2 * VD[i * nff + k] - VC[i * nff + k], T3[k * nff + j], d);
       d = fma(-VD[i * nff + k], T2[k * nff + j], d);
     }
-    dy[off + e] = sc * (double)p;
+    dy[off + e] = sc * (double)pp;
     dy[chan + off + e] = -sc * (double)cc;
     dy[2 * chan + off + e] = sc * (double)d;
   }
@@ -72,25 +82,27 @@ __global__ void products_kernel(const double* __restrict__ v, const double* __re
 
 }  // namespace
 
-tufrg_status prepare_products(tufrg_ctx* c) {
-  const size_t smem = sizeof(double) * 8 * c->nff * c->nff;
-  if (smem > 48 * 1024) {
-    TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<double>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<float>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
+tufrg_status prepare_products_multi(const MultiView& v) {
+  const int smem = smem_optin();
+  if (sizeof(double) * 8 * v.nff_max * v.nff_max > (size_t)smem) return TUFRG_ERR_ARG;
+  TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<double>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return TUFRG_OK;
 }
 
-tufrg_status launch_products(tufrg_ctx* c, int prec, const double* v, const double* chi,
-                             double* dy, const double* d_scale, cudaStream_t st) {
+tufrg_status launch_products_multi(const MultiView& v, int prec, const double* vin,
+                                   const double* chi, double* dy, bool scaled, cudaStream_t st) {
+  const int blocks = v.total(kKindProducts);
   if (prec == TUFRG_FP64) {
-    const size_t smem = sizeof(double) * 8 * c->nff * c->nff;
-    products_kernel<double><<<c->nl, 256, smem, st>>>(v, chi, dy, c->nl, c->nff, d_scale);
+    const size_t smem = sizeof(double) * 8 * v.nff_max * v.nff_max;
+    products_kernel<double><<<blocks, 256, smem, st>>>(v.d, v.dprefix(kKindProducts), v.n, vin,
+                                                       chi, dy, scaled ? 1 : 0);
   } else {
-    const size_t smem = sizeof(float) * 8 * c->nff * c->nff;
-    products_kernel<float><<<c->nl, 256, smem, st>>>(v, chi, dy, c->nl, c->nff, d_scale);
+    const size_t smem = sizeof(float) * 8 * v.nff_max * v.nff_max;
+    products_kernel<float><<<blocks, 256, smem, st>>>(v.d, v.dprefix(kKindProducts), v.n, vin,
+                                                      chi, dy, scaled ? 1 : 0);
   }
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;

@@ -9,14 +9,15 @@
 // the k integral, their half-integer Fourier position X and phase position Y)
 // are scale independent and built once at setup.  Bosonic momenta are the
 // coarse-grid points in [-pi, pi) (folding reading of the half-momentum
-// convention).  Three kernels:
-//   to_bond   -- Bt for all channels and l          (grid: Nl x 3)
+// convention).  Three kernels, each over all points of a batch (CTAs of a
+// point found from a prefix table):
+//   to_bond   -- Bt for all channels and l          (Nl x 3 CTAs per point)
 //   dft_keys  -- F for every key, one warp per key   (lanes over l')
 //   contract  -- T and the basis change, per (l, target channel)
 // The arithmetic type is FP64 for an FP64 context (this step is then bound by
 // GB300's FP64 rate) and FP32 for the mixed-precision contexts, whose loops
 // run on the tensor cores; the state and the result are FP64 in both cases.
-#include "internal.h"
+#include "device_util.cuh"
 
 namespace tufrg {
 namespace {
@@ -45,17 +46,26 @@ __device__ __forceinline__ V to_c(double2 d) {
   return {(decltype(V::x))d.x, (decltype(V::x))d.y};
 }
 
+constexpr int kDftWarps = 8;
+
 template <class T>
-__global__ void to_bond_kernel(const double* __restrict__ y, const double2* __restrict__ coef,
-                               int nl, int nff, int nb, typename C2<T>::type* __restrict__ bt) {
+__global__ void to_bond_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
+                               int np, const double* __restrict__ ybase,
+                               typename C2<T>::type* __restrict__ btbase) {
   using V = typename C2<T>::type;
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nl = pd.nl, nff = pd.nff, nb = pd.nb;
+  const int loc = blockIdx.x - prefix[p];
+  const int l = loc % nl, ch = loc / nl;
   extern __shared__ double2 sm2[];
   V* cs = reinterpret_cast<V*>(sm2);     // [nff][nb]
   V* tmp = cs + nff * nb;                // [nff][nb]
   T* Bs = reinterpret_cast<T*>(tmp + nff * nb);  // [nff][nff]
-  const int l = blockIdx.x, ch = blockIdx.y;
-  const double* B = y + ((size_t)ch * nl + l) * nff * nff;
-  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = to_c<V>(coef[e]);
+  const double* B = ybase + pd.off_state + ((size_t)ch * nl + l) * nff * nff;
+  V* bt = btbase + pd.off_bt;
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = to_c<V>(pd.coef[e]);
   for (int e = threadIdx.x; e < nff * nff; e += blockDim.x) Bs[e] = (T)B[e];
   __syncthreads();
   // tmp[a][b4] = sum_b B[a][b] c_b(b4)
@@ -81,86 +91,83 @@ __global__ void to_bond_kernel(const double* __restrict__ y, const double2* __re
 }
 
 template <class T>
-__global__ void dft_keys_kernel(const typename C2<T>::type* __restrict__ bt,
-                                const int4* __restrict__ keys, int nkeys,
-                                const double2* __restrict__ phase, int ncx, int ncy, int nd,
-                                int nb, int nl, typename C2<T>::type* __restrict__ fkey) {
+__global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
+                                int np, const typename C2<T>::type* __restrict__ btbase,
+                                typename C2<T>::type* __restrict__ fkbase) {
   using V = typename C2<T>::type;
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int ncx = pd.ncx, ncy = pd.ncy, nd = pd.nd, nb = pd.nb, nl = pd.nl;
   extern __shared__ double2 sm2[];
   V* ph = reinterpret_cast<V*>(sm2);  // [(ncx + ncy) * nd]
-  for (int e = threadIdx.x; e < (ncx + ncy) * nd; e += blockDim.x) ph[e] = to_c<V>(phase[e]);
+  for (int e = threadIdx.x; e < (ncx + ncy) * nd; e += blockDim.x) ph[e] = to_c<V>(pd.phase[e]);
   __syncthreads();
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int key = (blockIdx.x - prefix[p]) * kDftWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (warp >= nkeys) return;
-  const int4 k = keys[warp];
-  const V* src = bt + ((size_t)k.x * nb * nb + k.y) * nl;
+  if (key >= pd.nkeys) return;
+  const int4 k = pd.keys[key];
+  const V* src = btbase + pd.off_bt + ((size_t)k.x * nb * nb + k.y) * nl;
   V acc = {0, 0};
   for (int l = lane; l < nl; l += 32) {
     const int ix = l / ncy, iy = l - ix * ncy;
-    const V p = cmul(ph[ix * nd + k.z], ph[(ncx + iy) * nd + k.w]);
-    acc = cfma(p, src[l], acc);
+    const V q = cmul(ph[ix * nd + k.z], ph[(ncx + iy) * nd + k.w]);
+    acc = cfma(q, src[l], acc);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
   }
-  if (lane == 0) fkey[warp] = acc;
+  if (lane == 0) fkbase[pd.off_fkey + key] = acc;
 }
 
-struct ContractArgs {
-  const double* y;
-  const void* fkey;
-  const int* row_ptr;
-  const int4* terms;
-  int term_off[3];
-  const double2* coef;
-  const double2* phase;
-  int ncx, ncy, nd, nb, nff, nl;
-  double U;
-  int feedback;
-  double* v;
-};
-
 template <class T>
-__global__ void contract_kernel(ContractArgs a) {
+__global__ void contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
+                                int np, const double* __restrict__ ybase,
+                                const typename C2<T>::type* __restrict__ fkbase,
+                                double* __restrict__ vbase) {
   using V = typename C2<T>::type;
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nb = pd.nb, nff = pd.nff, nl = pd.nl, nd = pd.nd;
+  const int loc = blockIdx.x - prefix[p];
+  const int l = loc % nl, t = loc / nl;
   extern __shared__ double2 sm2[];
-  const int nb = a.nb, nff = a.nff;
   V* Tm = reinterpret_cast<V*>(sm2);  // [nb][nb]
   V* tmp = Tm + nb * nb;              // [nb][nff]
   V* cs = tmp + nb * nff;             // [nff][nb]
   V* qx = cs + nff * nb;              // [nd]
-  V* qy = qx + a.nd;                  // [nd]
-  const int l = blockIdx.x, t = blockIdx.y;
-  const int ix = l / a.ncy, iy = l - ix * a.ncy;
+  V* qy = qx + nd;                    // [nd]
+  const int ix = l / pd.ncy, iy = l - ix * pd.ncy;
   const size_t n2 = (size_t)nff * nff;
-  double* out = a.v + ((size_t)t * a.nl + l) * n2;
-  const double* own = a.y + ((size_t)t * a.nl + l) * n2;
+  double* out = vbase + pd.off_state + ((size_t)t * nl + l) * n2;
+  const double* own = ybase + pd.off_state + ((size_t)t * nl + l) * n2;
   const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
-  if (!a.feedback) {
+  const double U = pd.U;
+  if (!pd.feedback) {
     for (int e = threadIdx.x; e < (int)n2; e += blockDim.x)
-      out[e] = (e == 0 ? a.U : 0.0) + own_sign * own[e];
+      out[e] = (e == 0 ? U : 0.0) + own_sign * own[e];
     return;
   }
-  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = to_c<V>(a.coef[e]);
-  for (int e = threadIdx.x; e < a.nd; e += blockDim.x) {
-    qx[e] = to_c<V>(a.phase[ix * a.nd + e]);
-    qy[e] = to_c<V>(a.phase[(a.ncx + iy) * a.nd + e]);
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = to_c<V>(pd.coef[e]);
+  for (int e = threadIdx.x; e < nd; e += blockDim.x) {
+    qx[e] = to_c<V>(pd.phase[ix * nd + e]);
+    qy[e] = to_c<V>(pd.phase[(pd.ncx + iy) * nd + e]);
   }
   __syncthreads();
-  const int* rp = a.row_ptr + (size_t)t * (nb * nb + 1);
-  const int4* tm = a.terms + a.term_off[t];
-  const V* fkey = reinterpret_cast<const V*>(a.fkey);
-  const T inv_nl = (T)(1.0 / a.nl);
+  const int* rp = pd.row_ptr + (size_t)t * (nb * nb + 1);
+  const int4* tm = pd.terms + pd.term_off[t];
+  const V* fkey = fkbase + pd.off_fkey;
+  const T inv_nl = (T)(1.0 / nl);
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
     V acc = {0, 0};
     for (int j = rp[o]; j < rp[o + 1]; ++j) {
       const int4 q = tm[j];
-      V p = cmul(qx[q.y], qy[q.z]);
-      if (q.w < 0) p = {-p.x, -p.y};
-      acc = cfma(p, fkey[q.x], acc);
+      V ph = cmul(qx[q.y], qy[q.z]);
+      if (q.w < 0) ph = {-ph.x, -ph.y};
+      acc = cfma(ph, fkey[q.x], acc);
     }
     Tm[o] = {acc.x * inv_nl, acc.y * inv_nl};
   }
@@ -180,56 +187,75 @@ __global__ void contract_kernel(ContractArgs a) {
       const V c1 = cs[m * nb + b1], t1 = tmp[b1 * nff + n];
       s = fma(c1.x, t1.x, fma(-c1.y, t1.y, s));  // real part of c * tmp
     }
-    out[e] = (e == 0 ? a.U : 0.0) + own_sign * own[e] + (double)s;
+    out[e] = (e == 0 ? U : 0.0) + own_sign * own[e] + (double)s;
   }
 }
 
 template <class T>
-tufrg_status project_typed(tufrg_ctx* c, const double* y, double* v, cudaStream_t st) {
+size_t bond_smem(const MultiView& v) {
+  return sizeof(typename C2<T>::type) * 2 * v.nff_max * v.nb_max +
+         sizeof(T) * v.nff_max * v.nff_max;
+}
+template <class T>
+size_t dft_smem(const MultiView& v) {
+  return sizeof(typename C2<T>::type) * v.nc_sum_max * v.nd_max;
+}
+template <class T>
+size_t contract_smem(const MultiView& v) {
+  return sizeof(typename C2<T>::type) *
+         ((size_t)v.nb_max * v.nb_max + 2 * (size_t)v.nb_max * v.nff_max + 2 * v.nd_max);
+}
+
+template <class T>
+tufrg_status prepare_typed(const MultiView& v) {
+  const int smem = smem_optin();
+  if ((int)bond_smem<T>(v) > smem || (int)dft_smem<T>(v) > smem ||
+      (int)contract_smem<T>(v) > smem)
+    return TUFRG_ERR_ARG;
+  TUFRG_CUDA(cudaFuncSetAttribute(to_bond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem));
+  TUFRG_CUDA(cudaFuncSetAttribute(dft_keys_kernel<T>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  TUFRG_CUDA(cudaFuncSetAttribute(contract_kernel<T>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return TUFRG_OK;
+}
+
+template <class T>
+tufrg_status project_typed(const MultiView& v, const double* y, double* out, void* btv,
+                           void* fkv, cudaStream_t st) {
   using V = typename C2<T>::type;
-  const int nb = c->nb, nff = c->nff, nd = 2 * c->proj.dmax + 1;
-  V* bt = reinterpret_cast<V*>(c->d_bt);
-  V* fkey = reinterpret_cast<V*>(c->d_fkey);
-  if (c->p.feedback) {
-    const size_t sm1 = sizeof(V) * 2 * nff * nb + sizeof(T) * nff * nff;
-    to_bond_kernel<T><<<dim3(c->nl, 3), 128, sm1, st>>>(y, c->d_coef, c->nl, nff, nb, bt);
-    TUFRG_CUDA(cudaGetLastError());
-    const int warps_per_block = 8;
-    const int blocks = (c->proj.nkeys + warps_per_block - 1) / warps_per_block;
-    const size_t sm2 = sizeof(V) * (c->ncx + c->ncy) * nd;
-    dft_keys_kernel<T><<<blocks, 32 * warps_per_block, sm2, st>>>(
-        bt, c->d_key, c->proj.nkeys, c->d_phase, c->ncx, c->ncy, nd, nb, c->nl, fkey);
+  V* bt = reinterpret_cast<V*>(btv);
+  V* fkey = reinterpret_cast<V*>(fkv);
+  if (v.total(kKindBond) > 0) {
+    to_bond_kernel<T><<<v.total(kKindBond), 128, bond_smem<T>(v), st>>>(
+        v.d, v.dprefix(kKindBond), v.n, y, bt);
     TUFRG_CUDA(cudaGetLastError());
   }
-  ContractArgs a;
-  a.y = y;
-  a.fkey = fkey;
-  a.row_ptr = c->d_row_ptr;
-  a.terms = c->d_terms;
-  for (int t = 0; t < 3; ++t) a.term_off[t] = c->term_off[t];
-  a.coef = c->d_coef;
-  a.phase = c->d_phase;
-  a.ncx = c->ncx;
-  a.ncy = c->ncy;
-  a.nd = nd;
-  a.nb = nb;
-  a.nff = nff;
-  a.nl = c->nl;
-  a.U = c->p.U;
-  a.feedback = c->p.feedback;
-  a.v = v;
-  const size_t sm3 = sizeof(V) * ((size_t)nb * nb + 2 * (size_t)nb * nff + 2 * nd);
-  contract_kernel<T><<<dim3(c->nl, 3), 256, sm3, st>>>(a);
+  if (v.total(kKindDft) > 0) {
+    dft_keys_kernel<T><<<v.total(kKindDft), 32 * kDftWarps, dft_smem<T>(v), st>>>(
+        v.d, v.dprefix(kKindDft), v.n, bt, fkey);
+    TUFRG_CUDA(cudaGetLastError());
+  }
+  contract_kernel<T><<<v.total(kKindContract), 256, contract_smem<T>(v), st>>>(
+      v.d, v.dprefix(kKindContract), v.n, y, fkey, out);
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }
 
 }  // namespace
 
-tufrg_status launch_project(tufrg_ctx* c, int prec, const double* y, double* v,
-                            cudaStream_t st) {
-  return prec == TUFRG_FP64 ? project_typed<double>(c, y, v, st)
-                            : project_typed<float>(c, y, v, st);
+int dft_ctas(int nkeys) { return (nkeys + kDftWarps - 1) / kDftWarps; }
+
+tufrg_status prepare_project_multi(const MultiView& v) {
+  TUFRG_CHECK(prepare_typed<double>(v));
+  return prepare_typed<float>(v);
+}
+
+tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
+                                  void* bt, void* fkey, cudaStream_t st) {
+  return prec == TUFRG_FP64 ? project_typed<double>(v, y, out, bt, fkey, st)
+                            : project_typed<float>(v, y, out, bt, fkey, st);
 }
 
 }  // namespace tufrg

@@ -153,7 +153,9 @@ void build_proj(tufrg_ctx* c) {
 
 }  // namespace
 
-tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
+tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st);
+
+tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share) {
   const Basis& B = c->basis;
   const int nff = c->nff, nb = c->nb;
   const double two_pi = 2.0 * M_PI;
@@ -231,14 +233,27 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
   c->ksplit = (c->kdim + c->kchunk - 1) / c->kchunk;
   c->kpad = c->ksplit * c->kchunk;
 
+  const tufrg_ctx* dl = share.loops;
+  c->borrowed_loops = dl != nullptr;
+  if (dl) {  // same grids, bonds and precision: the scale-independent loop tables
+    c->d_kidx = dl->d_kidx;
+    c->d_F = dl->d_F;
+    c->d_pair = dl->d_pair;
+    c->d_rowoff = dl->d_rowoff;
+    c->d_kbase = dl->d_kbase;
+    c->d_Fhi = dl->d_Fhi;
+    c->d_Flo = dl->d_Flo;
+    c->d_shift = dl->d_shift;
+    c->d_rowmap = dl->d_rowmap;
+  }
   std::vector<int2> kidx(c->kpad, make_int2(-1, -1));
   for (int k = 0; k < c->kdim; ++k) kidx[k] = kp[k];
-  TUFRG_CHECK(upload(&c->d_kidx, kidx, st));
+  if (!dl) TUFRG_CHECK(upload(&c->d_kidx, kidx, st));
 
   // form factors at the loop points via per-direction cos/sin tables
   const int R = 4;
-  std::vector<double> fv((size_t)nff * c->kdim);
-  for (int k = 0; k < c->kdim; ++k) {
+  std::vector<double> fv(dl ? 0 : (size_t)nff * c->kdim);
+  for (int k = 0; k < (dl ? 0 : c->kdim); ++k) {
     double px = -M_PI + two_pi * kp[k].x / c->nfx, py = -M_PI + two_pi * kp[k].y / c->nfy;
     double cxr[R], sxr[R], cyr[R], syr[R];
     for (int r = 0; r < R; ++r) {
@@ -259,44 +274,42 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
       fv[(size_t)m * c->kdim + k] = v;
     }
   }
-  std::vector<double> F((size_t)c->mpad * c->kpad, 0.0);
+  std::vector<double> F(dl ? 0 : (size_t)c->mpad * c->kpad, 0.0);
   std::vector<int> pair(c->mpad, -1);
   for (int q = 0; q < c->npair; ++q) {
     int m = c->pair_m[q], n = c->pair_n[q];
     pair[q] = m * nff + n;
-    for (int k = 0; k < c->kdim; ++k)
+    for (int k = 0; k < (dl ? 0 : c->kdim); ++k)
       F[(size_t)q * c->kpad + k] =
           kw[k] * fv[(size_t)m * c->kdim + k] * fv[(size_t)n * c->kdim + k] / c->nf;
   }
-  TUFRG_CHECK(upload(&c->d_F, F, st));
-  TUFRG_CHECK(upload(&c->d_pair, pair, st));
+  if (!dl) {
+    TUFRG_CHECK(upload(&c->d_F, F, st));
+    TUFRG_CHECK(upload(&c->d_pair, pair, st));
+  }
 
   if (c->p.precision != TUFRG_FP64) {
-    // tensor-core path: M = 128 l-rows per CTA, N = pairs (multiple of 16),
-    // K-blocks of one 128-byte swizzle row; split K so that each CTA sums at
-    // most ~8192 loop points in FP32 and the grid fills whole waves
-    const bool bf16 = c->p.precision == TUFRG_BF16X3;
-    const int es = bf16 ? 2 : 4, kb = 128 / es;
+    // tensor-core path: M = 128 l-rows per tile, N = pairs (multiple of 16),
+    // K-blocks of one 128-byte swizzle row (the split of the K-blocks into
+    // work items belongs to the context's multi-point view)
+    const int kb = tc_k_per_block(c->p.precision);
     c->tc_npad = (c->npair + 15) / 16 * 16;
     if (c->tc_npad > 176) return TUFRG_ERR_ARG;  // two pipeline stages must fit shared memory
-    const int ltiles = (c->nrow + 127) / 128;
-    c->tc_nrow_pad = ltiles * 128;
-    const int nkb = (c->kdim + kb - 1) / kb;
-    const int waves = std::max(1, (int)std::ceil((double)c->kdim * ltiles / (8192.0 * 152)));
-    int ks = std::min(nkb, std::max(1, 152 * waves / ltiles));
-    c->tc_kbps = (nkb + ks - 1) / ks;
-    c->tc_ksplit = (nkb + c->tc_kbps - 1) / c->tc_kbps;
-    c->tc_kpad = c->tc_ksplit * c->tc_kbps * kb;
+    c->tc_nrow_pad = (c->nrow + 127) / 128 * 128;
+    c->tc_nkb = (c->kdim + kb - 1) / kb;
+    c->tc_kpad = c->tc_nkb * kb;
     // accumulator sets: as many (<= 4) as fit the 512 TMEM columns
     c->tc_nsets = 1;
     while (c->tc_nsets < 4 && 2 * c->tc_nsets * 2 * c->tc_npad <= 512) c->tc_nsets *= 2;
-    int cols = 32;
-    while (cols < c->tc_nsets * 2 * c->tc_npad) cols *= 2;
-    c->tc_tmem_cols = cols;
-    // halo table and per-row offsets of p + l/2
+    // halo table (offsets of p + l/2 below)
     c->tc_hx = c->nfx / 4;
     c->tc_hy = c->nfy / 4;
     c->tc_wy = c->nfy + 2 * c->tc_hy;
+    TUFRG_CHECK(alloc(&c->d_ext, (size_t)(c->nfx + 2 * c->tc_hx) * c->tc_wy));
+  }
+  if (c->p.precision != TUFRG_FP64 && !dl) {
+    const bool bf16 = c->p.precision == TUFRG_BF16X3;
+    const int es = bf16 ? 2 : 4;
     std::vector<int> rowoff(c->nrow);
     for (int r = 0; r < c->nrow; ++r) rowoff[r] = rowshift[r].x * c->tc_wy + rowshift[r].y;
     TUFRG_CHECK(upload(&c->d_rowoff, rowoff, st));
@@ -304,7 +317,6 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
     for (int k = 0; k < c->kdim; ++k)
       kbase[k] = (kp[k].x + c->tc_hx) * c->tc_wy + kp[k].y + c->tc_hy;
     TUFRG_CHECK(upload(&c->d_kbase, kbase, st));
-    TUFRG_CHECK(alloc(&c->d_ext, (size_t)(c->nfx + 2 * c->tc_hx) * c->tc_wy));
     std::vector<unsigned char> fh((size_t)c->tc_npad * c->tc_kpad * es, 0);
     std::vector<unsigned char> fl(fh.size(), 0);
     for (int q = 0; q < c->npair; ++q)
@@ -327,22 +339,62 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
       }
     TUFRG_CHECK(upload(&c->d_Fhi, fh, st));
     TUFRG_CHECK(upload(&c->d_Flo, fl, st));
-    TUFRG_CHECK(alloc(&c->d_partial_tc, (size_t)c->tc_ksplit * 2 * c->tc_npad * c->tc_nrow_pad));
-    TUFRG_CHECK(prepare_loops_tc(c));
   }
   TUFRG_CHECK(alloc(&c->d_err, 1));
   TUFRG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
 
-  TUFRG_CHECK(upload(&c->d_shift, rowshift, st));
-  TUFRG_CHECK(upload(&c->d_rowmap, rowmap, st));
+  if (!dl) {
+    TUFRG_CHECK(upload(&c->d_shift, rowshift, st));
+    TUFRG_CHECK(upload(&c->d_rowmap, rowmap, st));
+  }
 
-  // bond coefficients
+  const tufrg_ctx* dp = share.proj;
+  c->borrowed_proj = dp != nullptr;
+  if (dp) {  // same coarse grid and bonds: the projection tables
+    c->proj = dp->proj;
+    c->d_coef = dp->d_coef;
+    c->d_phase = dp->d_phase;
+    c->d_key = dp->d_key;
+    c->d_row_ptr = dp->d_row_ptr;
+    c->d_terms = dp->d_terms;
+    for (int t = 0; t < 3; ++t) c->term_off[t] = dp->term_off[t];
+  } else {
+    TUFRG_CHECK(setup_proj(c, st));
+  }
+  const ProjTables& P = c->proj;
+
+  // workspace
+  TUFRG_CHECK(alloc(&c->d_lambda, 4));
+  if (share.workspace) {
+    TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nrow));
+    TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
+    TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
+    TUFRG_CHECK(alloc(&c->d_bt, (size_t)3 * nb * nb * c->nl));
+    TUFRG_CHECK(alloc(&c->d_fkey, (size_t)P.nkeys));
+    // the loop kernels write only the parity-allowed pairs
+    TUFRG_CUDA(cudaMemsetAsync(c->d_chi, 0, sizeof(double) * 2 * c->nl * nff * nff, st));
+    TUFRG_CUDA(cudaStreamCreateWithFlags(&c->fstream, cudaStreamNonBlocking));
+    TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  }
+  if (share.own_view) {
+    double* lam[1] = {c->d_lambda};
+    tufrg_ctx* self[1] = {c};
+    TUFRG_CHECK(view_build(c->view, self, 1, lam, nullptr, c->d_err, c->p.precision, 0, st));
+  }
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  return TUFRG_OK;
+}
+
+// bond coefficients and the position-space projection tables
+tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
+  const Basis& B = c->basis;
+  const int nff = c->nff, nb = c->nb;
   std::vector<double2> coef((size_t)nff * nb);
   for (size_t i = 0; i < coef.size(); ++i)
     coef[i] = make_double2(B.coef[i].real(), B.coef[i].imag());
   TUFRG_CHECK(upload(&c->d_coef, coef, st));
 
-  // projection tables
   build_proj(c);
   const ProjTables& P = c->proj;
   const int nd = 2 * P.dmax + 1;
@@ -373,31 +425,27 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st) {
   }
   TUFRG_CHECK(upload(&c->d_row_ptr, rowp, st));
   TUFRG_CHECK(upload(&c->d_terms, terms, st));
-
-  // workspace
-  TUFRG_CHECK(alloc(&c->d_lambda, 4));
-  TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nrow));
-  TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
-  TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
-  TUFRG_CHECK(alloc(&c->d_bt, (size_t)3 * nb * nb * c->nl));
-  TUFRG_CHECK(alloc(&c->d_fkey, (size_t)P.nkeys));
-  TUFRG_CHECK(prepare_products(c));
-  TUFRG_CUDA(cudaStreamCreateWithFlags(&c->fstream, cudaStreamNonBlocking));
-  TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
-  TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
-  TUFRG_CUDA(cudaStreamSynchronize(st));
   return TUFRG_OK;
 }
 
 void free_device(tufrg_ctx* c) {
   free_flow(c);
-  void* ptrs[] = {c->d_ext, c->d_rowoff, c->d_kbase, c->d_Fhi, c->d_Flo, c->d_partial_tc, c->d_err,
-                  c->d_rowmap, c->d_tab, c->d_kidx, c->d_F,       c->d_shift,   c->d_pair,
-                  c->d_coef, c->d_phase,  c->d_key,     c->d_row_ptr, c->d_terms,
-                  c->d_lambda, c->d_partial, c->d_chi,  c->d_V,       c->d_bt,
-                  c->d_fkey};
-  for (void* p : ptrs)
+  view_free(c->view);
+  void* own[] = {c->d_ext,     c->d_err,   c->d_tab, c->d_lambda, c->d_partial,
+                 c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey};
+  for (void* p : own)
     if (p) cudaFree(p);
+  if (!c->borrowed_loops) {
+    void* loops[] = {c->d_rowoff, c->d_kbase, c->d_Fhi,  c->d_Flo,  c->d_rowmap,
+                     c->d_kidx,   c->d_F,     c->d_shift, c->d_pair};
+    for (void* p : loops)
+      if (p) cudaFree(p);
+  }
+  if (!c->borrowed_proj) {
+    void* proj[] = {c->d_coef, c->d_phase, c->d_key, c->d_row_ptr, c->d_terms};
+    for (void* p : proj)
+      if (p) cudaFree(p);
+  }
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->fstream) cudaStreamDestroy(c->fstream);
