@@ -30,9 +30,12 @@
 #include <cstring>
 
 #include "device_util.cuh"
+#include "tc_util.cuh"
 
 namespace tufrg {
 namespace {
+
+using namespace tc;
 
 constexpr int kRows = 128;          // MMA M: l-representatives per CTA
 constexpr int kProducers = 16;      // producer warps
@@ -40,66 +43,6 @@ constexpr int kLoadsInFlight = 16;  // float4 table loads a lane issues before c
 constexpr int kThreads = 32 * (kProducers + 1);
 constexpr int kRowBytes = 128;      // one 128B-swizzle row per K-block
 constexpr int kWTile = kRows * kRowBytes;  // 16 KB
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase of the given parity; gives up after kWaitNs.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (;;) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > kWaitNs) return false;
-  }
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1 KB apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);       // start address
-  d |= (uint64_t)1 << 16;                      // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
-  d |= (uint64_t)1 << 46;                      // descriptor version
-  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
-  return d;
-}
 
 template <int PREC>
 struct Prec;
@@ -132,11 +75,6 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
   }
 }
 
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
 
 // Closed-form frequency integral of the two loops for one propagator pair.
 // Table entries: (xi, A, H, |xi|).
