@@ -125,6 +125,11 @@ typedef struct {
   double max_abs;         /* max |B| of the state (tufrg_flow, tufrg_flow_state) */
   double lambda_switch;   /* scale after which the loops ran in FP64 (0: no switch) */
   int64_t n_rhs, n_accepted, n_rejected;
+  /* flows with a loop surrogate attached (tufrg_surrogate_attach): */
+  double lambda_surrogate_off; /* scale at which the judge rejected the surrogate
+                                  (0: never rejected, or no surrogate) */
+  int64_t n_rhs_surrogate;     /* right-hand sides whose loops the surrogate gave */
+  int64_t n_judges;            /* exact-loop judgements made */
 } tufrg_result;
 
 /* Sec. 2-4: build the problem (bond basis, grids, dispersion table,
@@ -328,6 +333,88 @@ tufrg_status tufrg_batch_autotune(tufrg_batch* b, double lambda, tufrg_tune_repo
 
 /* As tufrg_check, for the batch's kernels. */
 tufrg_status tufrg_batch_check(tufrg_batch* b, void* cuda_stream);
+
+/* ---------------------------------------------------------------------
+ * Learned loop surrogate (not part of the paper's method).  A multilayer
+ * perceptron predicts, per transfer momentum l of the coarse grid, the
+ * targets
+ *   Lambda (1 + Lambda) chi_dot_mn(l)
+ * of the parity-allowed pairs m <= n of both loops (pp first, then ph, each
+ * in the context's pair order; the other entries follow by symmetry or
+ * vanish): n_out = 2 Npair outputs.  Its inputs (l_x, l_y, ln Lambda,
+ * t', mu) enter scaled as
+ *   x = (l_x/pi, l_y/pi, (ln Lambda - ln 0.1)/4.6, (t' + 0.225)/0.225,
+ *        (mu + 0.9)/0.9),
+ * then a fixed embedding maps x to 25 features (x; cos and sin of k pi x_0
+ * and of k pi x_1 for k = 1..4, as the loops are periodic in l; x_2^2,
+ * x_2^3, x_2 x_3, x_2 x_4), followed by `depth` hidden layers of `width`
+ * SiLU units and a linear output layer whose outputs are standardised:
+ * the network predicts (target - shift) / scale per output, shift and scale
+ * being the mean and standard deviation of the first training set (identity
+ * before that).  Forward and backward passes run on
+ * tcgen05 tensor cores with BF16 hi/lo operand pairs (three products, as
+ * the loop contraction) and FP32 accumulation; Adam keeps FP32 master
+ * weights.  In a flow the surrogate replaces the loop contraction while an
+ * exact-loop judge, run every judge_every accepted steps (and at the
+ * start), finds its relative max-norm error at most tol; after the first
+ * rejection the flow uses the exact loops to the end.
+ *
+ * Parameters are flattened layer by layer: W ([n_out][n_in] row-major),
+ * then the bias.  x_dev: float [n][5]; t_dev, y_dev: float [n][n_out].
+ */
+typedef struct tufrg_surrogate tufrg_surrogate;
+
+/* n_out <= 512, width a multiple of 64 (<= 512), 1 <= depth <= 8; weights
+ * He-uniform from the seed, biases zero.  Blocks. */
+tufrg_status tufrg_surrogate_create(int32_t n_out, int32_t width, int32_t depth, uint64_t seed,
+                                    tufrg_surrogate** out);
+void tufrg_surrogate_destroy(tufrg_surrogate* s);
+tufrg_status tufrg_surrogate_n_params(const tufrg_surrogate* s, int64_t* n);
+/* copy the FP32 master parameters to / from host memory.  Blocks. */
+tufrg_status tufrg_surrogate_get_params(tufrg_surrogate* s, float* params, void* cuda_stream);
+tufrg_status tufrg_surrogate_set_params(tufrg_surrogate* s, const float* params,
+                                        void* cuda_stream);
+
+/* The output standardisation (host arrays [n_out]).  set: shift and scale
+ * both NULL restore the identity (the next training set then sets them);
+ * scale > 0.  Block. */
+tufrg_status tufrg_surrogate_get_scaling(tufrg_surrogate* s, float* shift, float* scale,
+                                         void* cuda_stream);
+tufrg_status tufrg_surrogate_set_scaling(tufrg_surrogate* s, const float* shift,
+                                         const float* scale, void* cuda_stream);
+
+/* Training samples of one scale: the exact loops of ctx at lambda (the
+ * context's precision) as Nl rows of inputs x_dev [Nl][5] and targets
+ * t_dev [Nl][n_out] (n_out must be 2 Npair of ctx). */
+tufrg_status tufrg_surrogate_samples(tufrg_ctx* ctx, const tufrg_surrogate* s, double lambda,
+                                     float* x_dev, float* t_dev, void* cuda_stream);
+
+/* Predicted targets y_dev [n][n_out] (standardisation undone) for inputs
+ * x_dev [n][5]. */
+tufrg_status tufrg_surrogate_predict(tufrg_surrogate* s, const float* x_dev, int64_t n,
+                                     float* y_dev, void* cuda_stream);
+
+/* Mean squared error of the standardised outputs against the standardised
+ * targets over n samples (n <= 65536) and its gradient with respect to the
+ * flattened parameters (host arrays; grad may be NULL).  Blocks. */
+tufrg_status tufrg_surrogate_loss_grad(tufrg_surrogate* s, const float* x_dev,
+                                       const float* t_dev, int64_t n, double* loss,
+                                       float* grad, void* cuda_stream);
+
+/* Adam (beta 0.9, 0.999, eps 1e-8) on mini-batches of `batch` samples
+ * drawn without replacement (seeded shuffle per epoch), learning rate lr
+ * with cosine decay to lr/100.  loss_hist (host, may be NULL) receives the
+ * mean mini-batch loss of each epoch.  Blocks. */
+tufrg_status tufrg_surrogate_train(tufrg_surrogate* s, const float* x_dev, const float* t_dev,
+                                   int64_t n, int32_t epochs, int32_t batch, double lr,
+                                   uint64_t seed, double* loss_hist, void* cuda_stream);
+
+/* Lets the DoPri5 flows of ctx use the surrogate for the loops (s = NULL
+ * detaches).  judge_every >= 1 accepted steps between exact judgements;
+ * tol > 0 the largest accepted relative max-norm error of the loops.  The
+ * surrogate's work buffers serve one flow at a time. */
+tufrg_status tufrg_surrogate_attach(tufrg_ctx* ctx, tufrg_surrogate* s, int32_t judge_every,
+                                    double tol);
 
 const char* tufrg_status_string(tufrg_status s);
 

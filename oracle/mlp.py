@@ -7,7 +7,10 @@ statement of that network, its input/target conventions, its loss and the
 gradient of the loss, against which the library's GPU training kernels are
 checked.
 
-Network (sizes = [5, H, ..., H, n_out]): h_0 = x,
+Network (sizes = [25, H, ..., H, n_out]): the five inputs x are first mapped
+to 25 fixed features (x itself; cos and sin of k pi x_0 and k pi x_1 for
+k = 1..4, since the loops are periodic in l; x_2^2, x_2^3, x_2 x_3, x_2 x_4),
+h_0 = embed(x), then
     z_i = W_i h_{i-1} + b_i,   h_i = silu(z_i) = z_i / (1 + exp(-z_i))
 for the hidden layers, and the linear output y = W_L h_{L-1} + b_L.
 Parameters flattened layer by layer: W_i ([n_i][k_i], row-major), then b_i.
@@ -47,6 +50,20 @@ def dsilu(z):
     return s * (1.0 + z * (1.0 - s))
 
 
+N_EMBED = 25
+
+
+def embed(x):
+    """The fixed feature map [N][5] -> [N][25] ahead of the first layer."""
+    x = np.asarray(x, dtype=np.float64)
+    cols = [x[:, j] for j in range(5)]
+    for k in range(1, 5):
+        a, b = k * np.pi * x[:, 0], k * np.pi * x[:, 1]
+        cols += [np.cos(a), np.sin(a), np.cos(b), np.sin(b)]
+    cols += [x[:, 2] ** 2, x[:, 2] ** 3, x[:, 2] * x[:, 3], x[:, 2] * x[:, 4]]
+    return np.stack(cols, axis=1)
+
+
 def n_params(sizes):
     return sum(n * k + n for k, n in zip(sizes[:-1], sizes[1:]))
 
@@ -72,7 +89,7 @@ def flatten(layers):
 def forward(theta, sizes, x):
     """Outputs y [N][n_out] and the per-layer (input, pre-activation) cache."""
     layers = unflatten(theta, sizes)
-    h = np.asarray(x, dtype=np.float64)
+    h = embed(x)
     cache = []
     for i, (W, b) in enumerate(layers):
         z = h @ W.T + b

@@ -143,6 +143,11 @@ class Solver:
         r = tufrg_flow_state(self.ctx, self._check(out, 3), _stream())
         return out, self._result(r)
 
+    def attach_surrogate(self, surrogate, judge_every=8, tol=1e-3):
+        """Flows use the surrogate's loops while the exact judge accepts them."""
+        _abi.tufrg_surrogate_attach(self.ctx, surrogate.s if surrogate else None,
+                                    int(judge_every), float(tol))
+
     def autotune(self, lam=1.0):
         """Tile autotuning of the tensor-core loops; returns the timing report."""
         return _abi.tufrg_autotune(self.ctx, float(lam), _stream()).as_dict()
@@ -244,6 +249,11 @@ class Batch:
         _, res, st = _abi.tufrg_batch_flow(self.b, self.n, o, self._vec(y), _stream())
         return y, [Solver._result(r) for r in res], st
 
+    def attach_surrogate(self, surrogate, judge_every=8, tol=1e-3):
+        """Flows use the surrogate's loops while the exact judge accepts them."""
+        _abi.tufrg_surrogate_attach(self.ctx, surrogate.s if surrogate else None,
+                                    int(judge_every), float(tol))
+
     def autotune(self, lam=1.0):
         return _abi.tufrg_batch_autotune(self.b, float(lam), _stream()).as_dict()
 
@@ -254,6 +264,72 @@ class Batch:
         if getattr(self, "b", None) is not None:
             _abi.tufrg_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """Learned loop surrogate (see include/tufrg.h): an MLP from
+    (l_x, l_y, ln Lambda, t', mu) to Lambda (1 + Lambda) chi_dot of the
+    parity-allowed pairs of both loops, trained on the GPU."""
+
+    def __init__(self, n_out, width=256, depth=4, seed=1604):
+        self.n_out, self.width, self.depth = int(n_out), int(width), int(depth)
+        self.s = _abi.tufrg_surrogate_create(self.n_out, self.width, self.depth, int(seed))
+        self.n_params = _abi.tufrg_surrogate_n_params(self.s)
+
+    @property
+    def sizes(self):
+        return [25] + [self.width] * self.depth + [self.n_out]  # after the fixed embedding
+
+    def params(self):
+        return _abi.tufrg_surrogate_get_params(self.s, _stream())
+
+    def set_params(self, p):
+        _abi.tufrg_surrogate_set_params(self.s, p, _stream())
+
+    def scaling(self):
+        """(shift, scale) of the output standardisation."""
+        return _abi.tufrg_surrogate_get_scaling(self.s, self.n_out, _stream())
+
+    def set_scaling(self, shift=None, scale=None):
+        _abi.tufrg_surrogate_set_scaling(self.s, shift, scale, _stream())
+
+    def samples(self, solver, lam, x=None, t=None):
+        """Training rows of one scale from the solver's exact loops:
+        (x [Nl][5], t [Nl][n_out]) float32 CUDA tensors (written in place if given)."""
+        import torch
+        x = torch.empty((solver.nl, 5), dtype=torch.float32, device="cuda") if x is None else x
+        t = (torch.empty((solver.nl, self.n_out), dtype=torch.float32, device="cuda")
+             if t is None else t)
+        _abi.tufrg_surrogate_samples(solver.ctx, self.s, float(lam), x.data_ptr(), t.data_ptr(),
+                                     _stream())
+        return x, t
+
+    def predict(self, x):
+        import torch
+        y = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device="cuda")
+        _abi.tufrg_surrogate_predict(self.s, x.data_ptr(), int(x.shape[0]), y.data_ptr(),
+                                     _stream())
+        return y
+
+    def loss_grad(self, x, t):
+        return _abi.tufrg_surrogate_loss_grad(self.s, x.data_ptr(), t.data_ptr(),
+                                              int(x.shape[0]), _stream())
+
+    def train(self, x, t, epochs=10, batch=4096, lr=1e-3, seed=0):
+        return _abi.tufrg_surrogate_train(self.s, x.data_ptr(), t.data_ptr(), int(x.shape[0]),
+                                          int(epochs), int(batch), float(lr), int(seed),
+                                          _stream())
+
+    def close(self):
+        if getattr(self, "s", None) is not None:
+            _abi.tufrg_surrogate_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

@@ -48,7 +48,9 @@ class tufrg_result(Structure):
                 ("finished", c_int32), ("channel", c_int32), ("l_index", c_int32),
                 ("m", c_int32), ("n", c_int32), ("max_abs", c_double),
                 ("lambda_switch", c_double),
-                ("n_rhs", c_int64), ("n_accepted", c_int64), ("n_rejected", c_int64)]
+                ("n_rhs", c_int64), ("n_accepted", c_int64), ("n_rejected", c_int64),
+                ("lambda_surrogate_off", c_double), ("n_rhs_surrogate", c_int64),
+                ("n_judges", c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -100,6 +102,24 @@ SIGNATURES = {
     "tufrg_batch_autotune": ([c_void_p, c_double, POINTER(tufrg_tune_report), c_void_p],
                              c_int32),
     "tufrg_batch_check": ([c_void_p, c_void_p], c_int32),
+    "tufrg_surrogate_create": ([c_int32, c_int32, c_int32, ctypes.c_uint64, POINTER(c_void_p)],
+                               c_int32),
+    "tufrg_surrogate_destroy": ([c_void_p], None),
+    "tufrg_surrogate_n_params": ([c_void_p, POINTER(c_int64)], c_int32),
+    "tufrg_surrogate_get_params": ([c_void_p, POINTER(ctypes.c_float), c_void_p], c_int32),
+    "tufrg_surrogate_set_params": ([c_void_p, POINTER(ctypes.c_float), c_void_p], c_int32),
+    "tufrg_surrogate_get_scaling": ([c_void_p, POINTER(ctypes.c_float), POINTER(ctypes.c_float),
+                                     c_void_p], c_int32),
+    "tufrg_surrogate_set_scaling": ([c_void_p, POINTER(ctypes.c_float), POINTER(ctypes.c_float),
+                                     c_void_p], c_int32),
+    "tufrg_surrogate_samples": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p],
+                                c_int32),
+    "tufrg_surrogate_predict": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
+    "tufrg_surrogate_loss_grad": ([c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_double),
+                                   POINTER(ctypes.c_float), c_void_p], c_int32),
+    "tufrg_surrogate_train": ([c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_double,
+                               ctypes.c_uint64, POINTER(c_double), c_void_p], c_int32),
+    "tufrg_surrogate_attach": ([c_void_p, c_void_p, c_int32, c_double], c_int32),
     "tufrg_status_string": ([c_int32], ctypes.c_char_p),
 }
 
@@ -286,3 +306,90 @@ def tufrg_batch_autotune(b, lam: float, stream: int = 0) -> tufrg_tune_report:
 
 def tufrg_batch_check(b, stream: int = 0) -> None:
     _check(lib().tufrg_batch_check(b, _dptr(stream)), "tufrg_batch_check")
+
+
+def tufrg_surrogate_create(n_out: int, width: int, depth: int, seed: int) -> c_void_p:
+    s = c_void_p()
+    _check(lib().tufrg_surrogate_create(n_out, width, depth, seed, byref(s)),
+           "tufrg_surrogate_create")
+    return s
+
+
+def tufrg_surrogate_destroy(s) -> None:
+    lib().tufrg_surrogate_destroy(s)
+
+
+def tufrg_surrogate_n_params(s) -> int:
+    n = c_int64()
+    _check(lib().tufrg_surrogate_n_params(s, byref(n)), "tufrg_surrogate_n_params")
+    return n.value
+
+
+def tufrg_surrogate_get_params(s, stream: int = 0):
+    import numpy as np
+    out = np.empty(tufrg_surrogate_n_params(s), dtype=np.float32)
+    _check(lib().tufrg_surrogate_get_params(s, out.ctypes.data_as(POINTER(ctypes.c_float)),
+                                            _dptr(stream)), "tufrg_surrogate_get_params")
+    return out
+
+
+def tufrg_surrogate_set_params(s, params, stream: int = 0) -> None:
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().tufrg_surrogate_set_params(s, a.ctypes.data_as(POINTER(ctypes.c_float)),
+                                            _dptr(stream)), "tufrg_surrogate_set_params")
+
+
+def tufrg_surrogate_samples(ctx, s, lam: float, x_dev: int, t_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_surrogate_samples(ctx, s, lam, _dptr(x_dev), _dptr(t_dev), _dptr(stream)),
+           "tufrg_surrogate_samples")
+
+
+def tufrg_surrogate_predict(s, x_dev: int, n: int, y_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_surrogate_predict(s, _dptr(x_dev), n, _dptr(y_dev), _dptr(stream)),
+           "tufrg_surrogate_predict")
+
+
+def tufrg_surrogate_loss_grad(s, x_dev: int, t_dev: int, n: int, stream: int = 0):
+    import numpy as np
+    loss = c_double()
+    g = np.empty(tufrg_surrogate_n_params(s), dtype=np.float32)
+    _check(lib().tufrg_surrogate_loss_grad(s, _dptr(x_dev), _dptr(t_dev), n, byref(loss),
+                                           g.ctypes.data_as(POINTER(ctypes.c_float)),
+                                           _dptr(stream)), "tufrg_surrogate_loss_grad")
+    return loss.value, g
+
+
+def tufrg_surrogate_train(s, x_dev: int, t_dev: int, n: int, epochs: int, batch: int, lr: float,
+                          seed: int, stream: int = 0):
+    hist = (c_double * epochs)()
+    _check(lib().tufrg_surrogate_train(s, _dptr(x_dev), _dptr(t_dev), n, epochs, batch, lr, seed,
+                                       hist, _dptr(stream)), "tufrg_surrogate_train")
+    return list(hist)
+
+
+def tufrg_surrogate_attach(ctx, s, judge_every: int = 8, tol: float = 1e-3) -> None:
+    _check(lib().tufrg_surrogate_attach(ctx, s, judge_every, tol), "tufrg_surrogate_attach")
+
+
+def tufrg_surrogate_get_scaling(s, n_out: int, stream: int = 0):
+    import numpy as np
+    sh = np.empty(n_out, dtype=np.float32)
+    sc = np.empty(n_out, dtype=np.float32)
+    _check(lib().tufrg_surrogate_get_scaling(s, sh.ctypes.data_as(POINTER(ctypes.c_float)),
+                                             sc.ctypes.data_as(POINTER(ctypes.c_float)),
+                                             _dptr(stream)), "tufrg_surrogate_get_scaling")
+    return sh, sc
+
+
+def tufrg_surrogate_set_scaling(s, shift, scale, stream: int = 0) -> None:
+    import numpy as np
+    if shift is None:
+        _check(lib().tufrg_surrogate_set_scaling(s, None, None, _dptr(stream)),
+               "tufrg_surrogate_set_scaling")
+        return
+    a = np.ascontiguousarray(shift, dtype=np.float32)
+    b = np.ascontiguousarray(scale, dtype=np.float32)
+    _check(lib().tufrg_surrogate_set_scaling(s, a.ctypes.data_as(POINTER(ctypes.c_float)),
+                                             b.ctypes.data_as(POINTER(ctypes.c_float)),
+                                             _dptr(stream)), "tufrg_surrogate_set_scaling")

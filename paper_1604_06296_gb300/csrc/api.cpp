@@ -34,6 +34,10 @@ tufrg_status validate(const tufrg_params* p) {
 namespace tufrg {
 
 tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) {
+  if (prec == kLoopSurrogate) {
+    if (!c->sur || chi != c->d_chi) return TUFRG_ERR_STATE;
+    return surrogate_loops(c->sur, c, chi, st);
+  }
   if (prec == TUFRG_FP64) {
     TUFRG_CHECK(launch_scale_tables(c, st));
     return launch_loops_fp64(c, chi, st);

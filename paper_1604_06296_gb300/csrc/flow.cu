@@ -154,9 +154,14 @@ struct FlowState {
   size_t bytes = 0;
   double *y, *k[7], *ytmp, *ynew, *yprev, *k1prev;
   FlowCtl* ctl = nullptr;
-  cudaGraphExec_t attempt[2] = {nullptr, nullptr};  // [loops in FP64]
+  cudaGraphExec_t attempt[3] = {nullptr, nullptr, nullptr};  // loops: context, FP64, surrogate
   double fp64_above = 0.0;
   double lambda_switch = 0.0;
+  // loop surrogate: accepted steps since the last judgement, the scale at
+  // which the judge rejected it, right-hand sides it served, judgements
+  int since_judge = 0;
+  double lambda_sur_off = 0.0;
+  long long n_rhs_sur = 0, n_judges = 0;
 };
 
 namespace {
@@ -293,7 +298,7 @@ tufrg_status checkpoints_in_last_step(tufrg_ctx* c, cudaStream_t st) {
 // The attempt graph of the current loop precision (captured on first use).
 tufrg_status attempt_graph(tufrg_ctx* c, cudaStream_t st, cudaGraphExec_t* out) {
   FlowState& f = *c->flow;
-  const int which = c->loop_prec == TUFRG_FP64 ? 1 : 0;
+  const int which = c->loop_prec == TUFRG_FP64 ? 1 : (c->loop_prec == kLoopSurrogate ? 2 : 0);
   if (!f.attempt[which]) {
     cudaGraph_t g = nullptr;
     TUFRG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -312,13 +317,42 @@ tufrg_status attempt_graph(tufrg_ctx* c, cudaStream_t st, cudaGraphExec_t* out) 
   return TUFRG_OK;
 }
 
+// Exact-loop judgement of the surrogate at the current scale; on rejection
+// the flow continues with the exact loops and k1 is recomputed with them.
+tufrg_status judge(tufrg_ctx* c, double s, bool at_start, cudaStream_t st) {
+  FlowState& f = *c->flow;
+  TUFRG_CHECK(launch_set_scalar(c->d_lambda, std::exp(s), st));
+  double rel = 0.0;
+  TUFRG_CHECK(surrogate_judge(c->sur, c, c->p.precision, &rel, st));
+  ++f.n_judges;
+  f.since_judge = 0;
+  if (rel <= c->sur_tol) {
+    c->loop_prec = kLoopSurrogate;
+    return TUFRG_OK;
+  }
+  c->loop_prec = c->p.precision;
+  f.lambda_sur_off = std::exp(s);
+  if (!at_start) {  // FSAL stage of the current point with the exact loops
+    TUFRG_CHECK(stage(c, f.y, f.ytmp, {}, 0.0, f.k[0], st));
+    TUFRG_CUDA(cudaStreamSynchronize(st));
+  }
+  return TUFRG_OK;
+}
+
 tufrg_status dopri5_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
   FlowState& f = *c->flow;
   for (int i = 0; i < n_steps && !f.finished; ++i) {
+    if (c->loop_prec == kLoopSurrogate && f.since_judge >= c->sur_every)
+      TUFRG_CHECK(judge(c, f.hc->s, false, st));
+    const bool sur = c->loop_prec == kLoopSurrogate;
     cudaGraphExec_t g = nullptr;
     TUFRG_CHECK(attempt_graph(c, st, &g));
     TUFRG_CUDA(cudaGraphLaunch(g, st));
     TUFRG_CHECK(read_ctl(c, st));
+    if (sur) {
+      f.n_rhs_sur += 6;
+      if (f.hc->accepted) ++f.since_judge;
+    }
     if (f.hc->accepted && f.fp64_above > 0.0 && c->loop_prec != TUFRG_FP64 &&
         f.hc->ymax_last > f.fp64_above) {
       c->loop_prec = TUFRG_FP64;  // near the divergence: the remaining loops in FP64
@@ -398,6 +432,9 @@ void fill_progress(tufrg_ctx* c, tufrg_result* r) {
   r->n_rejected = f.hc->n_rej;
   r->n_rhs = f.method == TUFRG_RK4 ? f.rk4_rhs : 1 + f.hc->n_rhs;
   r->lambda_switch = f.lambda_switch;
+  r->lambda_surrogate_off = f.lambda_sur_off;
+  r->n_rhs_surrogate = f.n_rhs_sur;
+  r->n_judges = f.n_judges;
 }
 
 }  // namespace
@@ -430,6 +467,9 @@ tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
   f.threshold = o->threshold;
   f.fp64_above = o->fp64_above;
   f.lambda_switch = 0.0;
+  f.since_judge = 0;
+  f.lambda_sur_off = 0.0;
+  f.n_rhs_sur = f.n_judges = 0;
   c->loop_prec = c->p.precision;  // every flow starts in the context's precision
   f.rk4_rhs = 0;
   f.cks.clear();
@@ -456,6 +496,11 @@ tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
   TUFRG_CUDA(cudaMemcpyAsync(f.y, y0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   TUFRG_CHECK(write_ctl(c, h0, st));
   if (o->method == TUFRG_DOPRI5) {
+    if (c->sur) {  // the surrogate's buffers may have moved: capture afresh
+      flow_drop_graphs(c);
+      TUFRG_CHECK(judge(c, h0.s, true, st));
+      if (c->loop_prec == kLoopSurrogate) f.n_rhs_sur = 1;  // the first stage below
+    }
     TUFRG_CHECK(stage(c, f.y, f.ytmp, {}, 0.0, f.k[0], st));  // k1 = f(s0, y0)
     TUFRG_CUDA(cudaStreamSynchronize(st));
   }

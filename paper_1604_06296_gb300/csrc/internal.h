@@ -134,6 +134,8 @@ struct MultiView {
 
 }  // namespace tufrg
 
+struct tufrg_surrogate;
+
 // Opaque context of the C ABI.
 struct tufrg_ctx {
   tufrg_params p{};
@@ -190,6 +192,9 @@ struct tufrg_ctx {
   tufrg::MultiView view;           // this context as a batch of one point
   bool borrowed_loops = false;     // loop / projection tables owned by another context
   bool borrowed_proj = false;
+  tufrg_surrogate* sur = nullptr;  // loop surrogate of the flows (tufrg_surrogate_attach)
+  int sur_every = 8;               // accepted steps between exact judgements
+  double sur_tol = 1e-3;           // largest accepted relative error of its loops
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
@@ -216,6 +221,18 @@ tufrg_status create_context(const tufrg_params* p, cudaStream_t st, const SetupS
                             tufrg_ctx** out);
 // drops the captured flow graphs (after a change of the tensor-core work items)
 void flow_drop_graphs(tufrg_ctx* c);
+
+// loop "precision" of a flow whose loops the attached surrogate gives
+constexpr int kLoopSurrogate = 3;
+// the surrogate's loops of every l at the scale in c->d_lambda (forbidden
+// pairs untouched); its work buffers must exist before a graph capture (the
+// first call makes them)
+tufrg_status surrogate_loops(tufrg_surrogate* s, tufrg_ctx* c, double* chi, cudaStream_t st);
+// relative max-norm error of the surrogate's loops against the exact ones in
+// precision exact_prec, at the scale in c->d_lambda (blocks; leaves the
+// surrogate's loops in c->d_chi)
+tufrg_status surrogate_judge(tufrg_surrogate* s, tufrg_ctx* c, int exact_prec, double* rel,
+                             cudaStream_t st);
 // times candidate work-item sizes of the view's tensor-core loops; run sets
 // the scale(s) the view's points read and launches the contraction once
 tufrg_status autotune_view(MultiView& v, tufrg_status (*run)(void*, cudaStream_t), void* arg,

@@ -4,10 +4,10 @@ import numpy as np
 from oracle import mlp
 
 
-def small(seed=0, sizes=(5, 7, 6, 4)):
+def small(seed=0, sizes=(25, 7, 6, 4)):
     rng = np.random.default_rng(seed)
-    theta = rng.standard_normal(mlp.n_params(list(sizes))) * 0.6
-    x = rng.standard_normal((11, sizes[0]))
+    theta = rng.standard_normal(mlp.n_params(list(sizes))) * 0.3
+    x = rng.uniform(-1, 1, (11, 5))
     t = rng.standard_normal((11, sizes[-1]))
     return list(sizes), theta, x, t
 
@@ -46,15 +46,15 @@ def test_output_bias_stationary_at_target_mean():
 
 def test_linear_network_reduces_to_least_squares():
     rng = np.random.default_rng(3)
-    x = rng.standard_normal((40, 5))
-    t = rng.standard_normal((40, 3))
-    A = np.hstack([x, np.ones((40, 1))])
+    x = rng.uniform(-1, 1, (60, 5))
+    t = rng.standard_normal((60, 3))
+    A = np.hstack([mlp.embed(x), np.ones((60, 1))])
     sol, *_ = np.linalg.lstsq(A, t, rcond=None)
-    W, b = sol[:5].T, sol[5]
+    W, b = sol[:25].T, sol[25]
     theta = mlp.flatten([(W, b)])
-    L, g = mlp.loss_and_grad(theta, [5, 3], x, t)
+    L, g = mlp.loss_and_grad(theta, [25, 3], x, t)
     assert np.max(np.abs(g)) < 1e-12
-    assert abs(L - np.sum((A @ sol - t) ** 2) / t.size) < 1e-14
+    assert abs(L - np.sum((A @ sol - t) ** 2) / t.size) < 1e-13
 
 
 def test_targets_and_loops_round_trip():
@@ -74,3 +74,15 @@ def test_targets_and_loops_round_trip():
 def test_features_scaling():
     f = mlp.features([np.pi, -np.pi / 2], [0.0, np.pi], 0.1, -0.225, -0.9)
     assert np.allclose(f, [[1, 0, 0, 0, 0], [-0.5, 1, 0, 0, 0]])
+
+
+def test_embedding_values():
+    x = np.array([[1.0, -0.5, 0.5, 2.0, -1.0]])
+    e = mlp.embed(x)[0]
+    assert e.shape == (25,)
+    assert np.allclose(e[:5], x[0])
+    for k in range(1, 5):
+        c0, s0, c1, s1 = e[5 + 4 * (k - 1):9 + 4 * (k - 1)]
+        assert np.isclose(c0, (-1) ** k) and abs(s0) < 1e-12          # x0 = 1: k pi
+        assert np.isclose(c1, np.cos(-k * np.pi / 2)) and np.isclose(s1, np.sin(-k * np.pi / 2))
+    assert np.allclose(e[21:], [0.25, 0.125, 1.0, -0.5])
