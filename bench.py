@@ -403,6 +403,7 @@ def run_learned(args, rank, world, local):
         timed(s, *ladder[-1])  # warm-up (graph capture)
         rungs = []
         for rtol, atol in ladder:
+            print(f"learned bench: {name} rtol {rtol}", file=sys.stderr, flush=True)
             r = timed(s, rtol, atol)
             r["lambda_c_rel_err"] = abs(r["lambda_c"] / ref["lambda_c"] - 1)
             rungs.append(r)

@@ -418,6 +418,11 @@ tufrg_status tufrg_surrogate_attach(tufrg_ctx* ctx, tufrg_surrogate* s, int32_t 
 
 const char* tufrg_status_string(tufrg_status s);
 
+/* The CUDA error behind the calling thread's last TUFRG_ERR_CUDA or
+ * TUFRG_ERR_OOM: its name and the library source location of the failing
+ * call ("" if none). */
+const char* tufrg_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -121,6 +121,7 @@ SIGNATURES = {
                                ctypes.c_uint64, POINTER(c_double), c_void_p], c_int32),
     "tufrg_surrogate_attach": ([c_void_p, c_void_p, c_int32, c_double], c_int32),
     "tufrg_status_string": ([c_int32], ctypes.c_char_p),
+    "tufrg_last_cuda_error": ([], ctypes.c_char_p),
 }
 
 
@@ -142,7 +143,8 @@ def lib():
 
 def _check(status: int, where: str):
     if status != 0:
-        raise TufrgError(status, where)
+        detail = lib().tufrg_last_cuda_error().decode() if status in (-2, -6) else ""
+        raise TufrgError(status, f"{where} ({detail})" if detail else where)
 
 
 def _dptr(p) -> c_void_p:

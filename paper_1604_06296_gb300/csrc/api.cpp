@@ -1,12 +1,29 @@
 // extern "C" entry points of include/tufrg.h.
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <new>
 
 #include "internal.h"
 
+namespace {
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+thread_local char g_last_cuda_where[160] = "";
+}
+
 tufrg_status tufrg_cuda_fail(cudaError_t e) {
+  g_last_cuda_error = e;
+  g_last_cuda_where[0] = 0;
   if (e == cudaErrorMemoryAllocation) return TUFRG_ERR_OOM;
   return TUFRG_ERR_CUDA;
+}
+
+tufrg_status tufrg_cuda_fail_at(cudaError_t e, const char* file, int line) {
+  const tufrg_status s = tufrg_cuda_fail(e);
+  const char* base = std::strrchr(file, '/');
+  std::snprintf(g_last_cuda_where, sizeof g_last_cuda_where, "%s at %s:%d", cudaGetErrorName(e),
+                base ? base + 1 : file, line);
+  return s;
 }
 
 namespace {
@@ -269,6 +286,11 @@ tufrg_status tufrg_check(tufrg_ctx* c, void* stream) {
     return TUFRG_ERR_TIMEOUT;
   }
   return TUFRG_OK;
+}
+
+const char* tufrg_last_cuda_error(void) {
+  if (g_last_cuda_error == cudaSuccess) return "";
+  return g_last_cuda_where[0] ? g_last_cuda_where : cudaGetErrorName(g_last_cuda_error);
 }
 
 const char* tufrg_status_string(tufrg_status s) {

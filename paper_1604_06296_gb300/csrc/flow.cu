@@ -441,9 +441,10 @@ void fill_progress(tufrg_ctx* c, tufrg_result* r) {
 
 void flow_drop_graphs(tufrg_ctx* c) {
   if (!c->flow) return;
-  for (auto& g : c->flow->attempt)
+  for (auto& g : c->flow->attempt) {
     if (g) cudaGraphExecDestroy(g);
-  c->flow->attempt[0] = c->flow->attempt[1] = nullptr;
+    g = nullptr;
+  }
 }
 
 void free_flow(tufrg_ctx* c) {

@@ -10,10 +10,10 @@
 
 #include "../../include/tufrg.h"
 
-#define TUFRG_CUDA(expr)                                      \
-  do {                                                        \
-    cudaError_t tufrg_e_ = (expr);                            \
-    if (tufrg_e_ != cudaSuccess) return tufrg_cuda_fail(tufrg_e_); \
+#define TUFRG_CUDA(expr)                                                              \
+  do {                                                                                \
+    cudaError_t tufrg_e_ = (expr);                                                    \
+    if (tufrg_e_ != cudaSuccess) return tufrg_cuda_fail_at(tufrg_e_, __FILE__, __LINE__); \
   } while (0)
 
 #define TUFRG_CHECK(expr)                     \
@@ -23,6 +23,8 @@
   } while (0)
 
 tufrg_status tufrg_cuda_fail(cudaError_t e);
+// records the failing call's source location for tufrg_last_cuda_error
+tufrg_status tufrg_cuda_fail_at(cudaError_t e, const char* file, int line);
 
 namespace tufrg {
 

@@ -884,7 +884,8 @@ tufrg_status tufrg_surrogate_create(int32_t n_out, int32_t width, int32_t depth,
   tufrg::free_buffers(s);
   bool ok = dalloc(&s->w, off) && dalloc(&s->m, off) && dalloc(&s->v, off) &&
             dalloc(&s->grad, off) && dalloc(&s->d_loss, 1) && dalloc(&s->d_judge, 2) &&
-            dalloc(&s->d_err, 1) && dalloc(&s->oshift, n_out) && dalloc(&s->oscale, n_out);
+            dalloc(&s->d_err, 1) && dalloc(&s->oshift, t.np[s->L - 1]) &&
+            dalloc(&s->oscale, t.np[s->L - 1]);
   for (int i = 0; ok && i < s->L; ++i) {
     const size_t e = (size_t)t.np[i] * t.kp[i];
     ok = dalloc(&s->Whi[i], e) && dalloc(&s->Wlo[i], e) && dalloc(&s->WThi[i], e) &&
@@ -904,11 +905,13 @@ tufrg_status tufrg_surrogate_create(int32_t n_out, int32_t width, int32_t depth,
       h[t.off_w[i] + j] = (float)(a * (2.0 * rng.uniform() - 1.0));
   }
   tufrg_status st = TUFRG_OK;
-  const std::vector<float> zero(n_out, 0.f), one(n_out, 1.f);
+  // standardisation over the padded outputs (identity in the padding)
+  const int np_out = t.np[s->L - 1];
+  const std::vector<float> zero(np_out, 0.f), one(np_out, 1.f);
   if (cudaMemcpy(s->w, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(s->oshift, zero.data(), sizeof(float) * n_out, cudaMemcpyHostToDevice) !=
+      cudaMemcpy(s->oshift, zero.data(), sizeof(float) * np_out, cudaMemcpyHostToDevice) !=
           cudaSuccess ||
-      cudaMemcpy(s->oscale, one.data(), sizeof(float) * n_out, cudaMemcpyHostToDevice) !=
+      cudaMemcpy(s->oscale, one.data(), sizeof(float) * np_out, cudaMemcpyHostToDevice) !=
           cudaSuccess ||
       cudaMemset(s->m, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(s->v, 0, sizeof(float) * off) != cudaSuccess ||

@@ -190,6 +190,24 @@ def test_flow_with_surrogate_gains_and_keeps_lambda_c(torch, trained):
         assert res["lambda_surrogate_off"] > res["lambda_c"]
 
 
+def test_repeated_flows_with_accepted_surrogate(torch, trained):
+    """Flows after one that switched from the surrogate to the exact loops
+    (each flow captures its graphs afresh) give the same result."""
+    s, _, _ = trained
+    sol = make_solver(HELD_OUT_TP)
+    sol.attach_surrogate(s, judge_every=8, tol=1e-2)
+    kw = dict(threshold=50.0, rtol=1e-6, atol=1e-8, h0=0.05)
+    _, a, _ = sol.flow(**kw)
+    sol.attach_surrogate(s, judge_every=8, tol=1e-2)
+    _, b, _ = sol.flow(**kw)
+    _, c, _ = sol.flow(**kw)
+    sol.close()
+    assert a["n_rhs_surrogate"] > 0
+    for r in (b, c):
+        assert r["n_rhs_surrogate"] == a["n_rhs_surrogate"] and r["n_rhs"] == a["n_rhs"]
+        assert abs(r["lambda_c"] / a["lambda_c"] - 1) < 1e-12
+
+
 def test_judge_rejects_an_untrained_network(torch):
     from paper_1604_06296_gb300 import Surrogate
     npair = len(omlp.pair_list(Basis.from_bonds(W.bonds_for_shells(1)).parity))
