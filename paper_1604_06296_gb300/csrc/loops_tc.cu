@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kTableBlock)
   const int p = point_of(prefix, n, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const double om = pd.lam[0];
+  const float omf = (float)pd.lam[0];
   const int e0 = (blockIdx.x - prefix[p]) * kTableBlock * kTablePerThread + threadIdx.x;
 #pragma unroll
   for (int q = 0; q < kTablePerThread; ++q) {
@@ -411,9 +411,11 @@ __global__ void __launch_bounds__(kTableBlock)
     ix -= ix >= pd.nfx ? pd.nfx : 0;
     iy += iy < 0 ? pd.nfy : 0;
     iy -= iy >= pd.nfy ? pd.nfy : 0;
-    const double xi = pd.tab[ix * pd.nfy + iy].x, x = fabs(xi), A = 1.0 / (om + x);
-    pd.ext[e] =
-        make_float4((float)xi, (float)A, (float)(x * (om + 3.0 * x) * A * A * A), (float)x);
+    // FP32 arithmetic (the table is FP32; GB300's FP64 division would
+    // dominate this kernel)
+    const float xi = (float)pd.tab[ix * pd.nfy + iy].x, x = fabsf(xi);
+    const float A = __frcp_rn(omf + x);
+    pd.ext[e] = make_float4(xi, A, x * fmaf(3.f, x, omf) * (A * A * A), x);
   }
 }
 
