@@ -154,15 +154,23 @@ def profile_traffic(kernel_file, profile_name):
 # --------------------------------------------------------------------------
 def loop_counts(tufrg, bonds, ncx, ncy, nfx, nfy):
     """Algorithmic sizes of one loop contraction: parity-allowed pairs m <= n,
-    half-zone loop points, l-representative rows."""
+    half-zone loop points (one of each pair {p, -p}), loop rows."""
     par = _parity(tufrg, bonds)
     nff = len(par)
     npair = int(sum(1 for m in range(nff) for n in range(m, nff) if par[m] * par[n] > 0))
-    kdim = nfx * (nfy // 2 - 1) + 2 * (nfx // 2 + 1)
-    # rows: one l of each interior pair {l, -l} (the loops at -l equal those
-    # at l) and every l on the zone boundary
-    nrow = sum(1 for jx in range(ncx) for jy in range(ncy)
-               if jx == 0 or jy == 0 or jx * ncy + jy <= (ncx - jx) * ncy + (ncy - jy))
+    kdim = nfx * nfy // 2 + 2
+    # rows: every l on the zone boundary, and one l per C4v orbit of interior
+    # l on square grids (per pair {l, -l} otherwise): the loops of the other
+    # members follow by the point-group covariance
+    boundary = ncx + ncy - 1
+    if ncx == ncy and nfx == nfy:
+        h = ncx // 2
+        orbits = {frozenset(((a, b), (-b, a), (-a, -b), (b, -a), (a, -b), (-a, b), (b, a),
+                             (-b, -a)))
+                  for a in range(-h + 1, h) for b in range(-h + 1, h)}
+        nrow = boundary + len(orbits)
+    else:
+        nrow = boundary + ((ncx - 1) * (ncy - 1) + 1) // 2
     return npair, kdim, nrow
 
 
@@ -302,11 +310,11 @@ def run_scan(args, rank, world, local):
                 "kernel": f"loops_tc_kernel<{args.precision}> over all points (+ tables, reduce)",
                 "algorithmic_flop_per_launch": flops,
                 "peak_source": f"bf16 dense burst from {peak_src} (of measured)"}
-    # kernels of the library in the timed call: first stage (combination + 7
-    # right-hand-side kernels), per attempt 6 x 8 + error, control, accept,
+    # kernels of the library in the timed call: first stage (combination + 8
+    # right-hand-side kernels), per attempt 6 x 9 + error, control, accept,
     # then 100 bisection rounds of 2 and 6 more for the crossing and argmax
     attempts = max(r["n_accepted"] + r["n_rejected"] for r in res)
-    launches = 8 + 51 * attempts + 2 * 100 + 6
+    launches = 9 + 57 * attempts + 2 * 100 + 6
     if rank == 0:
         sizes = sorted({(q["nc"], q["nf"], W.n_ff_for_shells(q["shells"])) for q in pts})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -567,7 +575,8 @@ def main():
                      "frac": achieved / peak, "kernel_ms": k_ms,
                      "algorithmic_flop_per_launch": flops,
                      "counting": f"{npair} allowed pairs x {kdim} half-zone points x {nrow} "
-                                 "l-representatives x 2 channels"})
+                                 "loop rows (C4v orbits of interior l + boundary l) x 2 "
+                                 "channels"})
 
     # end to end through the C ABI with host buffers: H2D state, RHS, D2H result
     y_host = torch.from_numpy(W.random_state(1, solver.nl, solver.nff, 0.1)).pin_memory()
@@ -646,9 +655,9 @@ def main():
                "sample": sample}
 
     # kernels of the library per timed step: 6 stages x (combination, per-scale
-    # table, loop contraction, split-K reduce, to_bond, dft_keys, contract,
-    # products) + error + control + accept
-    launches_per_step = 6 * 8 + 3
+    # table, loop contraction, split-K reduce, orbit expansion, to_bond,
+    # dft_keys, contract, products) + error + control + accept
+    launches_per_step = 6 * 9 + 3
     if rank == 0:
         dtype = "f64" if args.precision == "fp64" else f"{args.precision} loops, f64 state"
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

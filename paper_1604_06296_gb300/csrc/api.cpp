@@ -59,7 +59,7 @@ tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) 
     TUFRG_CHECK(launch_scale_tables(c, st));
     return launch_loops_fp64(c, chi, st);
   }
-  return launch_loops_tc_multi(c->view, chi, chi != c->d_chi, st);
+  return launch_loops_tc_multi(c->view, chi, st);
 }
 
 tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,

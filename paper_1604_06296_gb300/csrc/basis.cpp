@@ -113,6 +113,52 @@ tufrg_status Basis::build(int n_bonds, const int32_t* bonds) {
   return TUFRG_OK;
 }
 
+// The eight elements g of C4v as integer matrices acting on momenta k:
+// identity, rotations by 90, 180, 270 degrees, mirrors y -> -y, x -> -x,
+// the diagonal and the antidiagonal.
+const int kC4v[8][2][2] = {{{1, 0}, {0, 1}},  {{0, -1}, {1, 0}}, {{-1, 0}, {0, -1}},
+                           {{0, 1}, {-1, 0}}, {{1, 0}, {0, -1}}, {{-1, 0}, {0, 1}},
+                           {{0, 1}, {1, 0}},  {{0, -1}, {-1, 0}}};
+
+// f_m(g k) = sum_n R^g_mn f_n(k).  With f_m(k) = sum_b c_m(b) e^{i k.R_b}
+// and g orthogonal, f_m(g k) = sum_b c_m(b) e^{i k.(g^T R_b)}, so
+// R^g_mn = sum_b c_m(b) conj(c_n(b')), R_b' = g^T R_b (plane waves of distinct
+// bonds are orthonormal under the zone average).  For a basis adapted to
+// C4v every R^g is a signed permutation; returns false otherwise.
+bool Basis::point_group(std::vector<int>& perm, std::vector<int>& sign) const {
+  std::map<std::pair<int, int>, int> index;
+  for (int b = 0; b < nb; ++b) index[{bx[b], by[b]}] = b;
+  perm.assign(8 * (size_t)nff, 0);
+  sign.assign(8 * (size_t)nff, 0);
+  for (int g = 0; g < 8; ++g) {
+    std::vector<int> bmap(nb);
+    for (int b = 0; b < nb; ++b) {
+      // g^T R_b
+      const int x = kC4v[g][0][0] * bx[b] + kC4v[g][1][0] * by[b];
+      const int y = kC4v[g][0][1] * bx[b] + kC4v[g][1][1] * by[b];
+      auto it = index.find({x, y});
+      if (it == index.end()) return false;
+      bmap[b] = it->second;
+    }
+    for (int m = 0; m < nff; ++m) {
+      int found = -1;
+      for (int n = 0; n < nff; ++n) {
+        std::complex<double> r(0.0, 0.0);
+        for (int b = 0; b < nb; ++b)
+          r += coef[(size_t)m * nb + b] * std::conj(coef[(size_t)n * nb + bmap[b]]);
+        if (std::abs(r.imag()) > 1e-9) return false;
+        if (std::abs(r.real()) < 1e-9) continue;
+        if (found >= 0 || std::abs(std::abs(r.real()) - 1.0) > 1e-9) return false;
+        found = n;
+        sign[(size_t)g * nff + m] = r.real() > 0 ? 1 : -1;
+      }
+      if (found < 0) return false;
+      perm[(size_t)g * nff + m] = found;
+    }
+  }
+  return true;
+}
+
 double Basis::eval(int m, double kx, double ky) const {
   double v = 0.0;
   for (const TrigTerm& t : ff[m].terms) {

@@ -224,7 +224,7 @@ int grid_for(int n) { return (n + 127) / 128; }
 tufrg_status batch_rhs_device(tufrg_batch* b, const double* y, double* dy, bool scaled,
                               cudaStream_t st) {
   const MultiView& v = b->view;
-  TUFRG_CHECK(launch_loops_tc_multi(v, b->d_chi, false, st));
+  TUFRG_CHECK(launch_loops_tc_multi(v, b->d_chi, st));
   TUFRG_CHECK(launch_project_multi(v, b->precision, y, b->d_V, b->d_bt, b->d_fkey, st));
   return launch_products_multi(v, b->precision, b->d_V, b->d_chi, dy, scaled, st);
 }
@@ -467,12 +467,12 @@ struct CtxRun {
 tufrg_status run_ctx(void* arg, cudaStream_t st) {
   CtxRun* r = static_cast<CtxRun*>(arg);
   TUFRG_CHECK(launch_set_scalar(r->c->d_lambda, r->lambda, st));
-  return launch_loops_tc_multi(r->c->view, r->c->d_chi, false, st);
+  return launch_loops_tc_multi(r->c->view, r->c->d_chi, st);
 }
 
 tufrg_status run_batch(void* arg, cudaStream_t st) {
   tufrg_batch* b = static_cast<tufrg_batch*>(arg);
-  return launch_loops_tc_multi(b->view, b->d_chi, false, st);
+  return launch_loops_tc_multi(b->view, b->d_chi, st);
 }
 
 }  // namespace
@@ -652,7 +652,7 @@ tufrg_status tufrg_batch_loops(tufrg_batch* b, const double* lambda, double* chi
   if (!b || !lambda || !chi_dot_dev) return TUFRG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   TUFRG_CHECK(tufrg::set_lambdas(b, lambda, st));
-  return tufrg::launch_loops_tc_multi(b->view, chi_dot_dev, true, st);
+  return tufrg::launch_loops_tc_multi(b->view, chi_dot_dev, st);
 }
 
 tufrg_status tufrg_batch_rhs(tufrg_batch* b, const double* lambda, const double* y_dev,

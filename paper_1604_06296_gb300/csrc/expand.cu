@@ -1,0 +1,129 @@
+// The two stages after a loop contraction, for every point of a view:
+// * split-K combination of the partial sums into the loops of the rows
+//   (FP64, fixed order);
+// * loops of every transfer momentum from the loops of the rows (App. C): a
+//   row computed at l serves the l' = g l of its list, chi(g l) =
+//   R^g chi(l) R^g^T with f(g k) = R^g f(k).  The R^g of the C4v-adapted
+//   basis are signed permutations, so this is a gather with signs; the
+//   parity-forbidden entries (not computed) are written as zeros, so every
+//   entry of chi is written.  One CTA per (point, row).
+#include "device_util.cuh"
+
+namespace tufrg {
+namespace {
+
+constexpr int kMaxNff = 32;
+
+__global__ void expand_rows_kernel(const PointDesc* __restrict__ pts,
+                                   const int* __restrict__ prefix, int n,
+                                   const double* __restrict__ rowres, double* __restrict__ chi) {
+  const int p = point_of(prefix, n, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int row = blockIdx.x - prefix[p];
+  const int nff = pd.nff, n2 = nff * nff, nrow = pd.nrow, npair = pd.npair;
+  __shared__ double X[2][kMaxNff * kMaxNff];
+  for (int e = threadIdx.x; e < 2 * n2; e += blockDim.x) X[e / n2][e % n2] = 0.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * npair; e += blockDim.x) {
+    const int ch = e / npair, q = e % npair;
+    const int mn = pd.pair[q], m = mn / nff, nn = mn % nff;
+    const double v = rowres[pd.off_rowres + ((size_t)ch * nrow + row) * npair + q];
+    X[ch][m * nff + nn] = v;
+    X[ch][nn * nff + m] = v;
+  }
+  __syncthreads();
+  for (int i = pd.rowimg_ptr[row]; i < pd.rowimg_ptr[row + 1]; ++i) {
+    const int2 lg = pd.rowimg[i];
+    const int* perm = pd.symperm + lg.y * nff;
+    const int* sign = pd.symsign + lg.y * nff;
+    for (int e = threadIdx.x; e < 2 * n2; e += blockDim.x) {
+      const int ch = e / n2, r = e % n2, m = r / nff, nn = r % nff;
+      chi[pd.off_chi + ((size_t)ch * pd.nl + lg.x) * n2 + r] =
+          (double)(sign[m] * sign[nn]) * X[ch][perm[m] * nff + perm[nn]];
+    }
+  }
+}
+
+// Split-K combination of one (channel, pair) and 32 rows: partial sums laid
+// out as [split][2][P][R] (P pair stride, R row stride), FP64 result
+// scaled by -1/4 (pp) / +1/4 (ph) into rowres [2][nrow][npair].  Thread
+// (row lane, phase) sums the splits sp = phase (mod kPhases) -- independent
+// loads -- and the phases combine in a fixed order (deterministic).
+constexpr int kPhases = 8;
+
+template <class T>
+__device__ __forceinline__ void reduce_rows(const T* __restrict__ partial, int P, int R,
+                                            int ksplit, int npair, int nrow, int ch, int q,
+                                            int row0, double* __restrict__ rowres) {
+  __shared__ double red[kPhases][32];
+  const int lane = threadIdx.x & 31, phase = threadIdx.x >> 5;
+  const int row = row0 + lane;
+  double s = 0.0;
+  if (row < nrow) {
+    const T* src = partial + ((size_t)ch * P + q) * R + row;
+    const size_t stride = (size_t)2 * P * R;
+#pragma unroll 4
+    for (int sp = phase; sp < ksplit; sp += kPhases) s += (double)src[sp * stride];
+  }
+  red[phase][lane] = s;
+  __syncthreads();
+  if (phase == 0 && row < nrow) {
+    double t = red[0][lane];
+#pragma unroll
+    for (int k = 1; k < kPhases; ++k) t += red[k][lane];
+    rowres[((size_t)ch * nrow + row) * npair + q] = t * (ch == 0 ? -0.25 : 0.25);
+  }
+}
+
+// tensor-core partials of every point: CTA -> (point, channel, pair, 32 rows)
+__global__ void __launch_bounds__(32 * kPhases)
+    tc_rows_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int n,
+                   const float* __restrict__ partial, double* __restrict__ rowres) {
+  const int p = point_of(prefix, n, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int tiles = (pd.nrow + 31) / 32;
+  const int loc = blockIdx.x - prefix[p];
+  const int t = loc % tiles, r = loc / tiles, q = r % pd.npair, ch = r / pd.npair;
+  reduce_rows(partial + pd.off_partial, pd.npad, pd.nrow_pad, pd.ksplit, pd.npair, pd.nrow,
+              ch, q, 32 * t, rowres + pd.off_rowres);
+}
+
+// FP64-path partials of one context
+__global__ void __launch_bounds__(32 * kPhases)
+    fp64_rows_kernel(const double* __restrict__ partial, int mpad, int ksplit, int npair,
+                     int nrow, double* __restrict__ rowres) {
+  const int tiles = (nrow + 31) / 32;
+  const int t = blockIdx.x % tiles, r = blockIdx.x / tiles, q = r % npair, ch = r / npair;
+  reduce_rows(partial, mpad, nrow, ksplit, npair, nrow, ch, q, 32 * t, rowres);
+}
+
+}  // namespace
+
+int rows_reduce_ctas(int npair, int nrow) { return 2 * npair * ((nrow + 31) / 32); }
+
+tufrg_status launch_tc_rows_multi(const MultiView& v, cudaStream_t st) {
+  tc_rows_kernel<<<v.total(kKindReduce), 32 * kPhases, 0, st>>>(v.d, v.dprefix(kKindReduce), v.n,
+                                                                v.d_partial, v.d_rowres);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+tufrg_status launch_fp64_rows(const double* partial, int mpad, int ksplit, int npair, int nrow,
+                              double* rowres, cudaStream_t st) {
+  fp64_rows_kernel<<<rows_reduce_ctas(npair, nrow), 32 * kPhases, 0, st>>>(
+      partial, mpad, ksplit, npair, nrow, rowres);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+tufrg_status launch_expand_multi(const MultiView& v, double* chi, cudaStream_t st) {
+  if (v.nff_max > kMaxNff) return TUFRG_ERR_ARG;
+  expand_rows_kernel<<<v.total(kKindExpand), 128, 0, st>>>(v.d, v.dprefix(kKindExpand), v.n,
+                                                           v.d_rowres, chi);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+}  // namespace tufrg

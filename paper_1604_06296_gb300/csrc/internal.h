@@ -54,6 +54,10 @@ struct Basis {
 
   tufrg_status build(int n_bonds, const int32_t* bonds);
   double eval(int m, double kx, double ky) const;
+  // representation of C4v on the form factors as signed permutations:
+  // f_m(g k) = sign[g][m] f_{perm[g][m]}(k) for the 8 elements g (order of
+  // kC4v); false if some element is not a signed permutation
+  bool point_group(std::vector<int>& perm, std::vector<int>& sign) const;
 };
 
 // Scale-independent projection data of Eqs. (proj_VP/VC/VD) in position
@@ -71,6 +75,8 @@ struct ProjTables {
 };
 
 struct FlowState;
+
+extern const int kC4v[8][2][2];
 
 // One point (one set of model parameters and grids) as the multi-point
 // kernels see it.  A context is a batch of one point; a batch context
@@ -90,7 +96,11 @@ struct PointDesc {
   const int* rowoff;
   const unsigned char* Fhi;
   const unsigned char* Flo;
-  const int2* rowmap;
+  const int* rowimg_ptr;  // [nrow + 1] CSR of the (l, g) each row serves
+  const int2* rowimg;
+  const int* symperm;     // [8][nff] signed permutations R^g
+  const int* symsign;
+  long long off_rowres;   // offset of the point's [2][nrow][npair] row loops
   const int* pair;
   const double2* coef;
   const double2* phase;
@@ -109,6 +119,7 @@ enum : int {
   kKindDft,        // projections: Fourier keys
   kKindContract,   // projections: overlap sums and basis change
   kKindProducts,   // V chi V
+  kKindExpand,     // row loops -> loops of every l the row serves
   kKinds
 };
 
@@ -128,8 +139,9 @@ struct MultiView {
   float* d_partial = nullptr;
   size_t partial_elems = 0;
   int* d_err = nullptr;  // error word of the bounded waits
+  double* d_rowres = nullptr;  // loops of the rows, FP64, all points
   // elements of the packed buffers: state (y, V, dy), loops, bond space, keys
-  size_t state_elems = 0, chi_elems = 0, bt_elems = 0, fkey_elems = 0;
+  size_t state_elems = 0, chi_elems = 0, bt_elems = 0, fkey_elems = 0, rowres_elems = 0;
   int total(int kind) const { return prefix[(size_t)kind * (n + 1) + n]; }
   const int* dprefix(int kind) const { return d_prefix + (size_t)kind * (n + 1); }
 };
@@ -156,9 +168,13 @@ struct tufrg_ctx {
   double4_32a* d_tab = nullptr;        // [nf] (xi, A, H, 0) -- A, H filled per scale
   int2* d_kidx = nullptr;          // [kpad] fine-grid (ix, iy) of each loop point (-1 pad)
   double* d_F = nullptr;           // [mpad][kpad] weight * f_m f_n / Nf
-  int nrow = 0;                    // l-representative rows (one per pair {l, -l})
+  int nrow = 0;                    // loop rows (C4v orbits / {l, -l} pairs / boundary l)
+  bool c4v = false;                // rows serve C4v orbits
   int2* d_shift = nullptr;         // [nrow] l/2 of each row in fine-grid steps
-  int2* d_rowmap = nullptr;        // [nrow] (l, partner l) written by each row
+  int* d_rowimg_ptr = nullptr;     // [nrow + 1] CSR over d_rowimg
+  int2* d_rowimg = nullptr;        // [nl] (l, g): chi(l) = R^g chi(row) R^g^T
+  int* d_symperm = nullptr;        // [8][nff] R^g as signed permutations:
+  int* d_symsign = nullptr;        //   (R^g chi R^g^T)_mn = s_m s_n chi_{p(m) p(n)}
   int* d_pair = nullptr;           // [mpad] m*nff+n (or -1)
   double2* d_coef = nullptr;       // [nff][nb] bond coefficients
   double2* d_phase = nullptr;      // [ncx + ncy][2*dmax+1] e^{i l d pi/(2nc)} tables
@@ -269,7 +285,15 @@ int smem_optin();
 
 // tensor-core loops of every point (zero: clear chi first; the kernels write
 // only the parity-allowed pairs)
-tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, bool zero, cudaStream_t st);
+tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, cudaStream_t st);
+// loops of every l from the row loops in v.d_rowres (writes every entry)
+tufrg_status launch_expand_multi(const MultiView& v, double* chi, cudaStream_t st);
+// split-K combinations into the row loops (tensor-core partials of every
+// point of v; FP64 partials of one context)
+int rows_reduce_ctas(int npair, int nrow);
+tufrg_status launch_tc_rows_multi(const MultiView& v, cudaStream_t st);
+tufrg_status launch_fp64_rows(const double* partial, int mpad, int ksplit, int npair, int nrow,
+                              double* rowres, cudaStream_t st);
 size_t tc_smem_bytes(int npad);
 int tc_k_per_block(int prec);
 int table_ctas(int n_ext);

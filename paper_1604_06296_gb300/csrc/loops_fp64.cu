@@ -200,13 +200,9 @@ tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi, cudaStream_t st) {
                                                 c->kchunk, c->mpad, c->d_partial);
   }
   TUFRG_CUDA(cudaGetLastError());
-  TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * 2 * c->nl * c->nff * c->nff, st));
-  const int total = 2 * c->npair * c->nrow;
-  loops_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(c->d_partial, c->ksplit, c->mpad,
-                                                           c->nrow, c->d_rowmap, c->nl,
-                                                           c->npair, c->d_pair, c->nff, chi);
-  TUFRG_CUDA(cudaGetLastError());
-  return TUFRG_OK;
+  TUFRG_CHECK(launch_fp64_rows(c->d_partial, c->mpad, c->ksplit, c->npair, c->nrow,
+                               c->view.d_rowres, st));
+  return launch_expand_multi(c->view, chi, st);
 }
 
 tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaStream_t st) {

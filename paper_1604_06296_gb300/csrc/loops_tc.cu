@@ -39,7 +39,6 @@ using namespace tc;
 
 constexpr int kRows = 128;          // MMA M: l-representatives per CTA
 constexpr int kProducers = 16;      // producer warps
-constexpr int kLoadsInFlight = 16;  // float4 table loads a lane issues before computing
 constexpr int kThreads = 32 * (kProducers + 1);
 constexpr int kRowBytes = 128;      // one 128B-swizzle row per K-block
 constexpr int kWTile = kRows * kRowBytes;  // 16 KB
@@ -76,20 +75,8 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 }
 
 
-// Closed-form frequency integral of the two loops for one propagator pair.
-// Table entries: (xi, A, H, |xi|).
-__device__ __forceinline__ void weights(const float4 ta, const float4 tb, float om, float om2,
-                                        float inv_om2, float& wpp, float& wph) {
-  const float sa = ta.y + tb.y, pa = ta.y * tb.y;
-  const float D = pa * fmaf(-2.f * om2, fmaf(sa, sa, -pa), fmaf(5.f * om, sa, -3.f));
-  const float xs = ta.w + tb.w;
-  const float S = xs > 0.f ? __fdividef(ta.z + tb.z, xs) : inv_om2;
-  const bool same = ta.x * tb.x > 0.f;
-  wpp = same ? S : D;
-  wph = same ? D : S;
-}
-
-// The same for two propagator pairs at once with paired FP32 instructions.
+// Closed-form frequency integral of the two loops for two propagator pairs
+// at once, with paired FP32 instructions.  Table entries: (xi, A, H, |xi|).
 __device__ __forceinline__ void weights2(const float4 a0, const float4 b0, const float4 a1,
                                          const float4 b1, float om, float om2, float inv_om2,
                                          float2& wpp, float2& wph) {
@@ -129,7 +116,10 @@ template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   using P = Prec<PREC>;
   constexpr int KB = kRowBytes / P::kElem;  // k per K-block
-  constexpr int kBatch = kLoadsInFlight / (4 * P::kPerLane);  // rows per load batch
+  // producer pipeline unit: one row at two loop points (BF16) or two rows at
+  // one loop point (TF32) -- four table entries, one paired weight evaluation
+  constexpr int kUnitRows = P::kPerLane == 2 ? 1 : 2;
+  constexpr int kUnits = kRows / kProducers / kUnitRows;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -207,6 +197,9 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       const unsigned char* Flo = pd.Flo;
       const size_t frow = (size_t)pd.kpad_tc * P::kElem;  // bytes per F row
       const int fchunks = 8 * npad;  // 16-byte chunks per F tile
+      // this warp's rows with an l, in units of kUnitRows rows
+      const int nrw = max(0, min(kRows / kProducers, (nvalid - warp + kProducers - 1) / kProducers));
+      const int nunits = (nrw + kUnitRows - 1) / kUnitRows;
       for (int kb = 0; kb < cnt; ++kb) {
         const uint32_t gk = g + kb;
         const uint32_t s = gk & 1;
@@ -234,61 +227,75 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
         } else {
           pb[0] = __ldg(pd.kbase + k0 + lane);
         }
-#pragma unroll 1
-        for (int i0 = 0; i0 < kRows / kProducers; i0 += kBatch) {
-          if (warp + kProducers * i0 >= nvalid) {  // rows without an l: zeros
-#pragma unroll
-            for (int i = 0; i < kBatch; ++i) {
-              const uint32_t dst =
-                  st + (uint32_t)(warp + kProducers * (i0 + i)) * kRowBytes + swz;
-#pragma unroll
-              for (int t = 0; t < 4; ++t)
-                asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(0u)
-                             : "memory");
-            }
-            continue;
+        // rolling pipeline over this warp's rows: the table gathers of the
+        // next unit are in flight while the current unit is computed (two
+        // register buffers of four float4); rows without an l are skipped
+        // (their accumulator rows are never read)
+        float4 bufA[4], bufB[4];
+        auto load_unit = [&](int u, float4* b) {
+          if constexpr (P::kPerLane == 2) {  // one row, two loop points
+            const int off = s_off[warp + kProducers * u];
+            b[0] = __ldg(ext + (pb[0] + off));
+            b[1] = __ldg(ext + (pb[0] - off));
+            b[2] = __ldg(ext + (pb[1] + off));
+            b[3] = __ldg(ext + (pb[1] - off));
+          } else {  // two rows, one loop point
+            const int off0 = s_off[warp + kProducers * (2 * u)];
+            const int off1 = s_off[warp + kProducers * (2 * u + 1)];
+            b[0] = __ldg(ext + (pb[0] + off0));
+            b[1] = __ldg(ext + (pb[0] - off0));
+            b[2] = __ldg(ext + (pb[0] + off1));
+            b[3] = __ldg(ext + (pb[0] - off1));
           }
-          // table loads of kBatch rows first (memory-level parallelism)
-          float4 ta[kBatch][P::kPerLane], tb[kBatch][P::kPerLane];
-#pragma unroll
-          for (int i = 0; i < kBatch; ++i) {
-            const int off = s_off[warp + kProducers * (i0 + i)];
-#pragma unroll
-            for (int jj = 0; jj < P::kPerLane; ++jj) {
-              ta[i][jj] = __ldg(ext + (pb[jj] + off));
-              tb[i][jj] = __ldg(ext + (pb[jj] - off));
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < kBatch; ++i) {
-            const int r = warp + kProducers * (i0 + i);
+        };
+        auto do_unit = [&](int u, const float4* b) {
+          float2 wpp, wph;
+          weights2(b[0], b[1], b[2], b[3], om, om2, inv_om2, wpp, wph);
+          if constexpr (PREC == TUFRG_BF16X3) {
             uint32_t v[4];
-            if constexpr (PREC == TUFRG_BF16X3) {
-              float2 wpp, wph;
-              weights2(ta[i][0], tb[i][0], ta[i][1], tb[i][1], om, om2, inv_om2, wpp, wph);
-              const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
-              const __nv_bfloat162 pl = __float22bfloat162_rn(
-                  __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
-              const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
-              const __nv_bfloat162 hl = __float22bfloat162_rn(
-                  __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
-              std::memcpy(&v[0], &ph, 4);
-              std::memcpy(&v[1], &pl, 4);
-              std::memcpy(&v[2], &hh, 4);
-              std::memcpy(&v[3], &hl, 4);
-            } else {
-              float wpp, wph;
-              weights(ta[i][0], tb[i][0], om, om2, inv_om2, wpp, wph);
-              v[0] = tf32_rna(wpp);
-              v[1] = tf32_rna(wpp - __uint_as_float(v[0]));
-              v[2] = tf32_rna(wph);
-              v[3] = tf32_rna(wph - __uint_as_float(v[2]));
-            }
-            const uint32_t dst = st + (uint32_t)r * kRowBytes + swz;
+            const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
+            const __nv_bfloat162 pl = __float22bfloat162_rn(
+                __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
+            const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
+            const __nv_bfloat162 hl = __float22bfloat162_rn(
+                __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
+            std::memcpy(&v[0], &ph, 4);
+            std::memcpy(&v[1], &pl, 4);
+            std::memcpy(&v[2], &hh, 4);
+            std::memcpy(&v[3], &hl, 4);
+            const uint32_t dst = st + (uint32_t)(warp + kProducers * u) * kRowBytes + swz;
 #pragma unroll
             for (int t = 0; t < 4; ++t)
               asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t])
                            : "memory");
+          } else {
+            const float w[2][2] = {{wpp.x, wph.x}, {wpp.y, wph.y}};
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              uint32_t v[4];
+              v[0] = tf32_rna(w[j][0]);
+              v[1] = tf32_rna(w[j][0] - __uint_as_float(v[0]));
+              v[2] = tf32_rna(w[j][1]);
+              v[3] = tf32_rna(w[j][1] - __uint_as_float(v[2]));
+              const uint32_t dst =
+                  st + (uint32_t)(warp + kProducers * (2 * u + j)) * kRowBytes + swz;
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t])
+                             : "memory");
+            }
+          }
+        };
+        if (nunits > 0) load_unit(0, bufA);
+#pragma unroll
+        for (int u = 0; u < kUnits; u += 2) {
+          if (u < nunits) {
+            if (u + 1 < nunits) load_unit(u + 1, bufB);
+            do_unit(u, bufA);
+          }
+          if (u + 1 < nunits) {
+            if (u + 2 < nunits) load_unit(u + 2, bufA);
+            do_unit(u + 1, bufB);
           }
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -419,39 +426,6 @@ __global__ void __launch_bounds__(kTableBlock)
   }
 }
 
-// FP64 combination of the split-K partials in fixed order; -1/4 (pp), +1/4
-// (ph); scatter to (m, n), (n, m) of the row's l and of its partner.
-__global__ void loops_tc_reduce_kernel(const PointDesc* __restrict__ pts,
-                                       const int* __restrict__ prefix, int n,
-                                       const float* __restrict__ partial,
-                                       double* __restrict__ chi) {
-  const int p = point_of(prefix, n, blockIdx.x);
-  const PointDesc& pd = pts[p];
-  if (pd.skip && *pd.skip) return;
-  const int idx = (blockIdx.x - prefix[p]) * blockDim.x + threadIdx.x;
-  if (idx >= 2 * pd.npair * pd.nrow) return;
-  const int row = idx % pd.nrow;
-  const int r = idx / pd.nrow;
-  const int q = r % pd.npair, ch = r / pd.npair;
-  const float* src = partial + pd.off_partial + ((size_t)ch * pd.npad + q) * pd.nrow_pad + row;
-  const size_t stride = (size_t)2 * pd.npad * pd.nrow_pad;
-  double s = 0.0;
-  for (int sp = 0; sp < pd.ksplit; ++sp) s += (double)src[sp * stride];
-  s *= ch == 0 ? -0.25 : 0.25;
-  const int nff = pd.nff;
-  const int mn = pd.pair[q];
-  const int m = mn / nff, nn = mn % nff;
-  const int2 lp = pd.rowmap[row];
-  double* out = chi + pd.off_chi + ((size_t)ch * pd.nl + lp.x) * nff * nff;
-  out[m * nff + nn] = s;
-  out[nn * nff + m] = s;
-  if (lp.y != lp.x) {
-    out = chi + pd.off_chi + ((size_t)ch * pd.nl + lp.y) * nff * nff;
-    out[m * nff + nn] = s;
-    out[nn * nff + m] = s;
-  }
-}
-
 }  // namespace
 
 size_t tc_smem_bytes(int npad) {
@@ -477,7 +451,7 @@ tufrg_status prepare_loops_tc_multi(const MultiView& v) {
   return TUFRG_OK;
 }
 
-tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, bool zero, cudaStream_t st) {
+tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, cudaStream_t st) {
   if (v.tc_prec == TUFRG_FP64 || v.n_items == 0) return TUFRG_ERR_ARG;
   scale_table_ext_kernel<<<v.total(kKindTable), kTableBlock, 0, st>>>(
       v.d, v.dprefix(kKindTable), v.n);
@@ -500,11 +474,8 @@ tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, bool zero, c
   else
     loops_tc_kernel<TUFRG_3XTF32><<<ctas, kThreads, smem, st>>>(a);
   TUFRG_CUDA(cudaGetLastError());
-  if (zero) TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * v.chi_elems, st));
-  loops_tc_reduce_kernel<<<v.total(kKindReduce), 256, 0, st>>>(v.d, v.dprefix(kKindReduce),
-                                                               v.n, v.d_partial, chi);
-  TUFRG_CUDA(cudaGetLastError());
-  return TUFRG_OK;
+  TUFRG_CHECK(launch_tc_rows_multi(v, st));
+  return launch_expand_multi(v, chi, st);
 }
 
 }  // namespace tufrg

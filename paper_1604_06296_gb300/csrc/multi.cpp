@@ -125,7 +125,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
   v.d_err = err;
   v.tc_prec = tc_prec;
   v.prefix.assign((size_t)kKinds * (n + 1), 0);
-  size_t off_state = 0, off_chi = 0, off_bt = 0, off_fkey = 0;
+  size_t off_state = 0, off_chi = 0, off_bt = 0, off_fkey = 0, off_rowres = 0;
   const bool tc = tc_prec != TUFRG_FP64;
   for (int i = 0; i < n; ++i) {
     const tufrg_ctx* c = ctx[i];
@@ -168,7 +168,12 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.rowoff = c->d_rowoff;
     d.Fhi = c->d_Fhi;
     d.Flo = c->d_Flo;
-    d.rowmap = c->d_rowmap;
+    d.rowimg_ptr = c->d_rowimg_ptr;
+    d.rowimg = c->d_rowimg;
+    d.symperm = c->d_symperm;
+    d.symsign = c->d_symsign;
+    d.off_rowres = (long long)off_rowres;
+    off_rowres += (size_t)2 * c->nrow * c->npair;
     d.pair = c->d_pair;
     d.coef = c->d_coef;
     d.phase = c->d_phase;
@@ -179,11 +184,12 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.skip = skip ? skip[i] : nullptr;
     const int cnt[kKinds] = {
         tc ? table_ctas(d.n_ext) : 0,
-        tc ? (2 * d.npair * d.nrow + 255) / 256 : 0,
+        tc ? rows_reduce_ctas(d.npair, d.nrow) : 0,
         d.feedback ? 3 * d.nl : 0,
         d.feedback ? dft_ctas(d.nkeys) : 0,
         3 * d.nl,
         d.nl,
+        d.nrow,
     };
     for (int k = 0; k < kKinds; ++k)
       v.prefix[(size_t)k * (n + 1) + i + 1] = v.prefix[(size_t)k * (n + 1) + i] + cnt[k];
@@ -196,6 +202,10 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
   v.chi_elems = off_chi;
   v.bt_elems = off_bt;
   v.fkey_elems = off_fkey;
+  v.rowres_elems = off_rowres;
+  if (cudaMalloc((void**)&v.d_rowres, std::max<size_t>(off_rowres, 1) * sizeof(double)) !=
+      cudaSuccess)
+    return TUFRG_ERR_OOM;
   TUFRG_CHECK(upload_to(&v.d_prefix, v.prefix, st));
   if (cudaMalloc((void**)&v.d_counter, sizeof(int)) != cudaSuccess) return TUFRG_ERR_OOM;
   TUFRG_CHECK(prepare_project_multi(v));
@@ -207,7 +217,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
 }
 
 void view_free(MultiView& v) {
-  void* ptrs[] = {v.d, v.d_prefix, v.d_items, v.d_counter, v.d_partial};
+  void* ptrs[] = {v.d, v.d_prefix, v.d_items, v.d_counter, v.d_partial, v.d_rowres};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   v = MultiView();

@@ -6,9 +6,10 @@
 //   under p -> -p for parity-allowed pairs (pi_m pi_n = +1) and the others
 //   vanish (App. C), so the sum runs over half the zone;
 // * F[pair][k] = weight_k f_m(p_k) f_n(p_k) / Nf for the allowed pairs m <= n;
-// * l-representatives (one row per pair {l, -l}) with the half-shift of l on
-//   the fine grid (l/2 lands on the fine grid when nf % (2 nc) == 0 and
-//   nf % 4 == 0);
+// * loop rows: one per C4v orbit of interior l on square grids (one per
+//   pair {l, -l} otherwise, one per zone-boundary l) with the half-shift of
+//   the row's l on the fine grid (l/2 lands on the fine grid when
+//   nf % (2 nc) == 0 and nf % 4 == 0) and the list of (l, g) it serves;
 // * position-space projection data (Sec. 2.5: the Kronecker-delta overlaps
 //   and Fourier phases are scale independent and computed once).
 #include <algorithm>
@@ -172,19 +173,22 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     }
   TUFRG_CHECK(upload(&c->d_tab, tab, st));
 
-  // loop points over half the zone
+  // loop points over half the zone, one of each pair {p, -p}: the columns
+  // 0 < ix < nfx/2 whole, and the two self-partnered columns ix = 0, nfx/2
+  // for 0 <= iy <= nfy/2.  Every run of consecutive loop points is a run of
+  // consecutive iy, i.e. of consecutive entries of the [ix][iy] tables.
   std::vector<int2> kp;
   std::vector<double> kw;
   const int hy = c->nfy / 2, hx = c->nfx / 2;
-  for (int ix = 0; ix < c->nfx; ++ix)
-    for (int iy = 1; iy < hy; ++iy) {
+  for (int ix = 1; ix < hx; ++ix)
+    for (int iy = 0; iy < c->nfy; ++iy) {
       kp.push_back(make_int2(ix, iy));
       kw.push_back(2.0);
     }
-  for (int iy : {0, hy})
-    for (int ix = 0; ix <= hx; ++ix) {
+  for (int ix : {0, hx})
+    for (int iy = 0; iy <= hy; ++iy) {
       kp.push_back(make_int2(ix, iy));
-      kw.push_back((ix == 0 || ix == hx) ? 1.0 : 2.0);
+      kw.push_back((iy == 0 || iy == hy) ? 1.0 : 2.0);
     }
   c->kdim = (int)kp.size();
 
@@ -199,26 +203,50 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
       }
   c->npair = (int)c->pair_m.size();
 
-  // l-representatives: for l inside the zone (no component at -pi) the
-  // folded -l has half momentum -l/2, so the propagator pair
-  // (xi(p + l/2), xi(p - l/2)) is only swapped and, the weights being
-  // symmetric, the loops at l and -l are equal: one row serves both.  An l on
-  // the zone boundary keeps -pi/2 in that component after folding, so it is
-  // not paired (it gets its own row).
-  std::vector<int2> rowmap, rowshift;
+  // Rows of the loop contraction and the l each row serves.  For l inside
+  // the zone (no component at -pi) the loops are covariant under the point
+  // group: chi(g l) = R^g chi(l) R^g^T with f(g k) = R^g f(k) (App. C; xi is
+  // C4v symmetric and the folded g l has half momentum g l/2).  On square
+  // grids with a basis whose R^g are signed permutations, one row serves a
+  // whole C4v orbit of interior l; otherwise one row serves {l, -l}
+  // (g = inversion, R^g = diag(parity), which leaves the parity-allowed
+  // loops unchanged).  An l on the zone boundary keeps -pi/2 in a component
+  // after folding, which breaks the covariance: it gets its own row.
+  std::vector<int> symperm, symsign;
+  const bool c4v = c->ncx == c->ncy && c->nfx == c->nfy && B.point_group(symperm, symsign);
+  if (!c4v) {
+    symperm.assign(8 * (size_t)nff, 0);
+    symsign.assign(8 * (size_t)nff, 1);
+    for (int g = 0; g < 8; ++g)
+      for (int m = 0; m < nff; ++m) symperm[(size_t)g * nff + m] = m;
+  }
+  std::vector<int2> rowshift, rowimg;
+  std::vector<int> rowimg_ptr(1, 0);
+  std::vector<char> served(c->nl, 0);
+  const int hcx = c->ncx / 2, hcy = c->ncy / 2;
   for (int jx = 0; jx < c->ncx; ++jx)
     for (int jy = 0; jy < c->ncy; ++jy) {
       const int l = jx * c->ncy + jy;
+      if (served[l]) continue;
       const bool interior = jx != 0 && jy != 0;
-      const int partner =
-          interior ? ((c->ncx - jx) % c->ncx) * c->ncy + (c->ncy - jy) % c->ncy : l;
-      if (l > partner) continue;
-      rowmap.push_back(make_int2(l, partner));
+      for (int g = 0; g < (interior ? 8 : 1); ++g) {
+        if (!c4v && g != 0 && g != 2) continue;
+        // g acts on u = j - n/2 (k = 2 pi u / n); interior images stay interior
+        const int ux = jx - hcx, uy = jy - hcy;
+        const int vx = kC4v[g][0][0] * ux + kC4v[g][0][1] * uy;
+        const int vy = kC4v[g][1][0] * ux + kC4v[g][1][1] * uy;
+        const int lg = (vx + hcx) * c->ncy + (vy + hcy);
+        if (served[lg]) continue;
+        served[lg] = 1;
+        rowimg.push_back(make_int2(lg, c4v ? g : 0));
+      }
+      rowimg_ptr.push_back((int)rowimg.size());
       // l/2 in fine-grid steps: (-pi/2 + pi j / nc) / (2 pi / nf)
       rowshift.push_back(make_int2(-c->nfx / 4 + jx * (c->nfx / (2 * c->ncx)),
                                    -c->nfy / 4 + jy * (c->nfy / (2 * c->ncy))));
     }
-  c->nrow = (int)rowmap.size();
+  c->nrow = (int)rowshift.size();
+  c->c4v = c4v;
 
   c->rm = c->npair <= 16 ? 1 : (c->npair <= 32 ? 2 : 4);
   const int mt = 16 * c->rm;
@@ -244,7 +272,10 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_Fhi = dl->d_Fhi;
     c->d_Flo = dl->d_Flo;
     c->d_shift = dl->d_shift;
-    c->d_rowmap = dl->d_rowmap;
+    c->d_rowimg_ptr = dl->d_rowimg_ptr;
+    c->d_rowimg = dl->d_rowimg;
+    c->d_symperm = dl->d_symperm;
+    c->d_symsign = dl->d_symsign;
   }
   std::vector<int2> kidx(c->kpad, make_int2(-1, -1));
   for (int k = 0; k < c->kdim; ++k) kidx[k] = kp[k];
@@ -345,7 +376,10 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
 
   if (!dl) {
     TUFRG_CHECK(upload(&c->d_shift, rowshift, st));
-    TUFRG_CHECK(upload(&c->d_rowmap, rowmap, st));
+    TUFRG_CHECK(upload(&c->d_rowimg_ptr, rowimg_ptr, st));
+    TUFRG_CHECK(upload(&c->d_rowimg, rowimg, st));
+    TUFRG_CHECK(upload(&c->d_symperm, symperm, st));
+    TUFRG_CHECK(upload(&c->d_symsign, symsign, st));
   }
 
   const tufrg_ctx* dp = share.proj;
@@ -436,8 +470,9 @@ void free_device(tufrg_ctx* c) {
   for (void* p : own)
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {
-    void* loops[] = {c->d_rowoff, c->d_kbase, c->d_Fhi,  c->d_Flo,  c->d_rowmap,
-                     c->d_kidx,   c->d_F,     c->d_shift, c->d_pair};
+    void* loops[] = {c->d_rowoff,  c->d_kbase,     c->d_Fhi,    c->d_Flo,     c->d_rowimg_ptr,
+                     c->d_rowimg,  c->d_symperm,   c->d_symsign, c->d_kidx,   c->d_F,
+                     c->d_shift,   c->d_pair};
     for (void* p : loops)
       if (p) cudaFree(p);
   }
