@@ -310,11 +310,11 @@ def run_scan(args, rank, world, local):
                 "kernel": f"loops_tc_kernel<{args.precision}> over all points (+ tables, reduce)",
                 "algorithmic_flop_per_launch": flops,
                 "peak_source": f"bf16 dense burst from {peak_src} (of measured)"}
-    # kernels of the library in the timed call: first stage (combination + 8
-    # right-hand-side kernels), per attempt 6 x 9 + error, control, accept,
+    # kernels of the library in the timed call: first stage (combination + 7
+    # right-hand-side kernels), per attempt 6 x 8 + error, control, accept,
     # then 100 bisection rounds of 2 and 6 more for the crossing and argmax
     attempts = max(r["n_accepted"] + r["n_rejected"] for r in res)
-    launches = 9 + 57 * attempts + 2 * 100 + 6
+    launches = 8 + 51 * attempts + 2 * 100 + 6
     if rank == 0:
         sizes = sorted({(q["nc"], q["nf"], W.n_ff_for_shells(q["shells"])) for q in pts})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -655,9 +655,9 @@ def main():
                "sample": sample}
 
     # kernels of the library per timed step: 6 stages x (combination, per-scale
-    # table, loop contraction, split-K reduce, orbit expansion, to_bond,
-    # dft_keys, contract, products) + error + control + accept
-    launches_per_step = 6 * 9 + 3
+    # table, loop contraction, split-K reduce, to_bond, dft_keys, contract,
+    # products gathering the row loops) + error + control + accept
+    launches_per_step = 6 * 8 + 3
     if rank == 0:
         dtype = "f64" if args.precision == "fp64" else f"{args.precision} loops, f64 state"
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

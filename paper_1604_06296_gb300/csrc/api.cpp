@@ -62,12 +62,34 @@ tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) 
   return launch_loops_tc_multi(c->view, chi, st);
 }
 
+tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st) {
+  if (prec == kLoopSurrogate) return TUFRG_ERR_ARG;
+  if (prec == TUFRG_FP64) {
+    TUFRG_CHECK(launch_scale_tables(c, st));
+    return launch_loops_fp64_rows(c, st);
+  }
+  return launch_loops_tc_rows_multi(c->view, st);
+}
+
 tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
                         cudaStream_t st) {
-  TUFRG_CHECK(launch_loops(c, prec, c->d_chi, st));
-  TUFRG_CHECK(launch_project_multi(c->view, prec, y, c->d_V, c->d_bt, c->d_fkey, st));
-  TUFRG_CHECK(launch_products_multi(c->view, prec, c->d_V, c->d_chi, dy, scaled, st));
-  return TUFRG_OK;
+  // projections and products in FP32 arithmetic for a mixed-precision
+  // context, in FP64 for an FP64 context and after a switch to FP64 loops
+  const int arith =
+      (prec == TUFRG_FP64 || c->p.precision == TUFRG_FP64) ? TUFRG_FP64 : TUFRG_3XTF32;
+  // the projections (state only) beside the loops (scale only)
+  TUFRG_CUDA(cudaEventRecord(c->ev_fork, st));
+  TUFRG_CUDA(cudaStreamWaitEvent(c->pstream, c->ev_fork, 0));
+  TUFRG_CHECK(launch_project_multi(c->view, arith, y, c->d_V, c->d_bt, c->d_fkey, c->pstream));
+  TUFRG_CUDA(cudaEventRecord(c->ev_join, c->pstream));
+  // exact loops stay as row loops; the products gather each l from its row
+  const bool rows = prec != kLoopSurrogate;
+  if (rows)
+    TUFRG_CHECK(launch_loop_rows(c, prec, st));
+  else
+    TUFRG_CHECK(launch_loops(c, prec, c->d_chi, st));
+  TUFRG_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
+  return launch_products_multi(c->view, arith, c->d_V, rows ? nullptr : c->d_chi, dy, scaled, st);
 }
 
 tufrg_status create_context(const tufrg_params* p, cudaStream_t st, const SetupShare& share,

@@ -214,6 +214,8 @@ struct tufrg_batch {
   tufrg::BatchFlow flow;
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t pstream = nullptr;  // projections beside the loops
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace tufrg {
@@ -224,9 +226,14 @@ int grid_for(int n) { return (n + 127) / 128; }
 tufrg_status batch_rhs_device(tufrg_batch* b, const double* y, double* dy, bool scaled,
                               cudaStream_t st) {
   const MultiView& v = b->view;
-  TUFRG_CHECK(launch_loops_tc_multi(v, b->d_chi, st));
-  TUFRG_CHECK(launch_project_multi(v, b->precision, y, b->d_V, b->d_bt, b->d_fkey, st));
-  return launch_products_multi(v, b->precision, b->d_V, b->d_chi, dy, scaled, st);
+  // the projections (states only) beside the loops (scales only)
+  TUFRG_CUDA(cudaEventRecord(b->ev_fork, st));
+  TUFRG_CUDA(cudaStreamWaitEvent(b->pstream, b->ev_fork, 0));
+  TUFRG_CHECK(launch_project_multi(v, b->precision, y, b->d_V, b->d_bt, b->d_fkey, b->pstream));
+  TUFRG_CUDA(cudaEventRecord(b->ev_join, b->pstream));
+  TUFRG_CHECK(launch_loops_tc_rows_multi(v, st));  // row loops, gathered by the products
+  TUFRG_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
+  return launch_products_multi(v, b->precision, b->d_V, nullptr, dy, scaled, st);
 }
 
 tufrg_status set_lambdas(tufrg_batch* b, const double* lambda, cudaStream_t st) {
@@ -537,9 +544,10 @@ void batch_free(tufrg_batch* b) {
       tufrg::free_device(c);
       delete c;
     }
-  if (b->ev_in) cudaEventDestroy(b->ev_in);
-  if (b->ev_out) cudaEventDestroy(b->ev_out);
-  if (b->fstream) cudaStreamDestroy(b->fstream);
+  for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_fork, b->ev_join})
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t q : {b->fstream, b->pstream})
+    if (q) cudaStreamDestroy(q);
   delete b;
 }
 
@@ -599,6 +607,9 @@ tufrg_status batch_setup(int32_t n, const tufrg_params* params, cudaStream_t st,
   TUFRG_CUDA(cudaStreamCreateWithFlags(&b->fstream, cudaStreamNonBlocking));
   TUFRG_CUDA(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
   TUFRG_CUDA(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  TUFRG_CUDA(cudaStreamCreateWithFlags(&b->pstream, cudaStreamNonBlocking));
+  TUFRG_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  TUFRG_CUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
   TUFRG_CUDA(cudaStreamSynchronize(st));
   return TUFRG_OK;
 }

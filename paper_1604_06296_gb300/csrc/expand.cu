@@ -50,13 +50,13 @@ __global__ void expand_rows_kernel(const PointDesc* __restrict__ pts,
 // scaled by -1/4 (pp) / +1/4 (ph) into rowres [2][nrow][npair].  Thread
 // (row lane, phase) sums the splits sp = phase (mod kPhases) -- independent
 // loads -- and the phases combine in a fixed order (deterministic).
-constexpr int kPhases = 8;
+constexpr int kPhases = 32;
 
 template <class T>
 __device__ __forceinline__ void reduce_rows(const T* __restrict__ partial, int P, int R,
                                             int ksplit, int npair, int nrow, int ch, int q,
                                             int row0, double* __restrict__ rowres) {
-  __shared__ double red[kPhases][32];
+  __shared__ double red[kPhases][33];
   const int lane = threadIdx.x & 31, phase = threadIdx.x >> 5;
   const int row = row0 + lane;
   double s = 0.0;

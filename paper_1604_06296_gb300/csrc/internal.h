@@ -98,6 +98,8 @@ struct PointDesc {
   const unsigned char* Flo;
   const int* rowimg_ptr;  // [nrow + 1] CSR of the (l, g) each row serves
   const int2* rowimg;
+  const int2* lrow;       // [nl] (row, g) serving each l
+  const int* pairidx;     // [nff][nff] pair index of {m, n}, -1 if forbidden
   const int* symperm;     // [8][nff] signed permutations R^g
   const int* symsign;
   long long off_rowres;   // offset of the point's [2][nrow][npair] row loops
@@ -173,6 +175,8 @@ struct tufrg_ctx {
   int2* d_shift = nullptr;         // [nrow] l/2 of each row in fine-grid steps
   int* d_rowimg_ptr = nullptr;     // [nrow + 1] CSR over d_rowimg
   int2* d_rowimg = nullptr;        // [nl] (l, g): chi(l) = R^g chi(row) R^g^T
+  int2* d_lrow = nullptr;          // [nl] (row, g) serving each l
+  int* d_pairidx = nullptr;        // [nff][nff] index of the pair {m, n} (-1: forbidden)
   int* d_symperm = nullptr;        // [8][nff] R^g as signed permutations:
   int* d_symsign = nullptr;        //   (R^g chi R^g^T)_mn = s_m s_n chi_{p(m) p(n)}
   int* d_pair = nullptr;           // [mpad] m*nff+n (or -1)
@@ -215,6 +219,11 @@ struct tufrg_ctx {
   double sur_tol = 1e-3;           // largest accepted relative error of its loops
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // the projections of a right-hand side run on their own stream, beside the
+  // loop contraction (fork after the stage combination, join before the
+  // products; branches of the captured flow graphs)
+  cudaStream_t pstream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   size_t state_elems() const { return (size_t)3 * nl * nff * nff; }
 };
@@ -260,6 +269,7 @@ void free_device(tufrg_ctx* c);
 // kernels (launchers)
 tufrg_status launch_scale_tables(tufrg_ctx* c, cudaStream_t st);
 tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi_out, cudaStream_t st);
+tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st);
 // projections and products: FP64 arithmetic when prec == TUFRG_FP64, else FP32
 tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 
@@ -301,11 +311,18 @@ tufrg_status prepare_loops_tc_multi(const MultiView& v);
 tufrg_status prepare_project_multi(const MultiView& v);
 tufrg_status prepare_products_multi(const MultiView& v);
 int dft_ctas(int nkeys);
+int contract_ctas(int nl);
 // projections and products of every point; bt, fkey: packed workspaces
 tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
                                   void* bt, void* fkey, cudaStream_t st);
+// chi == nullptr: the loops of each l are gathered from the row loops
+// v.d_rowres (the orbit expansion fused into the products)
 tufrg_status launch_products_multi(const MultiView& v, int prec, const double* vin,
                                    const double* chi, double* dy, bool scaled, cudaStream_t st);
+// loop contraction up to the row loops in c->view.d_rowres (no expansion);
+// prec must not be the surrogate
+tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st);
+tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st);
 // loops in the given precision (the context's, or FP64)
 tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi_out, cudaStream_t st);
 

@@ -182,6 +182,11 @@ tufrg_status launch_scale_tables(tufrg_ctx* c, cudaStream_t st) {
 }
 
 tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi, cudaStream_t st) {
+  TUFRG_CHECK(launch_loops_fp64_rows(c, st));
+  return launch_expand_multi(c->view, chi, st);
+}
+
+tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st) {
   dim3 grid((c->nrow + LT - 1) / LT, c->mtiles, c->ksplit);
   switch (c->rm) {
     case 1:
@@ -200,9 +205,8 @@ tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi, cudaStream_t st) {
                                                 c->kchunk, c->mpad, c->d_partial);
   }
   TUFRG_CUDA(cudaGetLastError());
-  TUFRG_CHECK(launch_fp64_rows(c->d_partial, c->mpad, c->ksplit, c->npair, c->nrow,
-                               c->view.d_rowres, st));
-  return launch_expand_multi(c->view, chi, st);
+  return launch_fp64_rows(c->d_partial, c->mpad, c->ksplit, c->npair, c->nrow,
+                          c->view.d_rowres, st);
 }
 
 tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaStream_t st) {

@@ -452,6 +452,11 @@ tufrg_status prepare_loops_tc_multi(const MultiView& v) {
 }
 
 tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, cudaStream_t st) {
+  TUFRG_CHECK(launch_loops_tc_rows_multi(v, st));
+  return launch_expand_multi(v, chi, st);
+}
+
+tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st) {
   if (v.tc_prec == TUFRG_FP64 || v.n_items == 0) return TUFRG_ERR_ARG;
   scale_table_ext_kernel<<<v.total(kKindTable), kTableBlock, 0, st>>>(
       v.d, v.dprefix(kKindTable), v.n);
@@ -474,8 +479,7 @@ tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, cudaStream_t
   else
     loops_tc_kernel<TUFRG_3XTF32><<<ctas, kThreads, smem, st>>>(a);
   TUFRG_CUDA(cudaGetLastError());
-  TUFRG_CHECK(launch_tc_rows_multi(v, st));
-  return launch_expand_multi(v, chi, st);
+  return launch_tc_rows_multi(v, st);
 }
 
 }  // namespace tufrg

@@ -170,6 +170,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.Flo = c->d_Flo;
     d.rowimg_ptr = c->d_rowimg_ptr;
     d.rowimg = c->d_rowimg;
+    d.lrow = c->d_lrow;
+    d.pairidx = c->d_pairidx;
     d.symperm = c->d_symperm;
     d.symsign = c->d_symsign;
     d.off_rowres = (long long)off_rowres;
@@ -187,7 +189,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
         tc ? rows_reduce_ctas(d.npair, d.nrow) : 0,
         d.feedback ? 3 * d.nl : 0,
         d.feedback ? dft_ctas(d.nkeys) : 0,
-        3 * d.nl,
+        contract_ctas(d.nl),
         d.nl,
         d.nrow,
     };

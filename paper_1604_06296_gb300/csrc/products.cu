@@ -25,11 +25,15 @@ __device__ __forceinline__ void matmul(const T* __restrict__ a, const T* __restr
 
 // arithmetic in T (FP64, or FP32 for the mixed-precision contexts); inputs
 // and the derivative are FP64; dy is multiplied by lam[1] when scaled
+// chibase == nullptr: the loops of l are gathered from the loops of the row
+// serving l (rowres), chi(l)_mn = s_m s_n chi(row)_{p(m) p(n)} with the
+// signed permutation of the group element that maps the row's l to l.
 template <class T>
 __global__ void products_kernel(const PointDesc* __restrict__ pts,
                                 const int* __restrict__ prefix, int np,
                                 const double* __restrict__ vbase,
-                                const double* __restrict__ chibase, double* __restrict__ dybase,
+                                const double* __restrict__ chibase,
+                                const double* __restrict__ rowres, double* __restrict__ dybase,
                                 int scaled) {
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
@@ -50,14 +54,31 @@ __global__ void products_kernel(const PointDesc* __restrict__ pts,
   const size_t chan = (size_t)nl * n2;
   const size_t off = (size_t)l * n2;
   const double* v = vbase + pd.off_state;
-  const double* chi = chibase + pd.off_chi;
   double* dy = dybase + pd.off_state;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
     VP[e] = (T)v[off + e];
     VC[e] = (T)v[chan + off + e];
     VD[e] = (T)v[2 * chan + off + e];
-    Xp[e] = (T)chi[off + e];
-    Xh[e] = (T)chi[chan + off + e];
+  }
+  if (chibase) {
+    const double* chi = chibase + pd.off_chi;
+    for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+      Xp[e] = (T)chi[off + e];
+      Xh[e] = (T)chi[chan + off + e];
+    }
+  } else {
+    const int2 rg = pd.lrow[l];
+    const int* perm = pd.symperm + rg.y * nff;
+    const int* sign = pd.symsign + rg.y * nff;
+    const double* rp = rowres + pd.off_rowres + (size_t)rg.x * pd.npair;
+    const size_t ch1 = (size_t)pd.nrow * pd.npair;
+    for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+      const int m = e / nff, n = e % nff;
+      const int q = pd.pairidx[perm[m] * nff + perm[n]];
+      const T sg = (T)(sign[m] * sign[n]);
+      Xp[e] = q >= 0 ? sg * (T)rp[q] : (T)0;
+      Xh[e] = q >= 0 ? sg * (T)rp[ch1 + q] : (T)0;
+    }
   }
   __syncthreads();
   matmul(Xp, VP, T1, nff);  // chi^pp V^P
@@ -98,11 +119,11 @@ tufrg_status launch_products_multi(const MultiView& v, int prec, const double* v
   if (prec == TUFRG_FP64) {
     const size_t smem = sizeof(double) * 8 * v.nff_max * v.nff_max;
     products_kernel<double><<<blocks, 256, smem, st>>>(v.d, v.dprefix(kKindProducts), v.n, vin,
-                                                       chi, dy, scaled ? 1 : 0);
+                                                       chi, v.d_rowres, dy, scaled ? 1 : 0);
   } else {
     const size_t smem = sizeof(float) * 8 * v.nff_max * v.nff_max;
     products_kernel<float><<<blocks, 256, smem, st>>>(v.d, v.dprefix(kKindProducts), v.n, vin,
-                                                      chi, dy, scaled ? 1 : 0);
+                                                      chi, v.d_rowres, dy, scaled ? 1 : 0);
   }
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;

@@ -13,7 +13,7 @@
 // point found from a prefix table):
 //   to_bond   -- Bt for all channels and l          (Nl x 3 CTAs per point)
 //   dft_keys  -- F for every key, one warp per key   (lanes over l')
-//   contract  -- T and the basis change, per (l, target channel)
+//   contract  -- T and the basis change, per (target channel, 4 l)
 // The arithmetic type is FP64 for an FP64 context (this step is then bound by
 // GB300's FP64 rate) and FP32 for the mixed-precision contexts, whose loops
 // run on the tensor cores; the state and the result are FP64 in both cases.
@@ -122,39 +122,49 @@ __global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __
   if (lane == 0) fkbase[pd.off_fkey + key] = acc;
 }
 
+// kContractL transfer momenta of one target channel per CTA: each term of
+// the (scale-independent) overlap lists and its Fourier key are read once
+// and applied to all of them (only the phases e^{i l.Y} differ).
+constexpr int kContractL = 4;
+
 template <class T>
-__global__ void contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
-                                int np, const double* __restrict__ ybase,
-                                const typename C2<T>::type* __restrict__ fkbase,
-                                double* __restrict__ vbase) {
+__global__ void __launch_bounds__(256)
+    contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
+                    const double* __restrict__ ybase,
+                    const typename C2<T>::type* __restrict__ fkbase, double* __restrict__ vbase) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
   const int nb = pd.nb, nff = pd.nff, nl = pd.nl, nd = pd.nd;
+  const int groups = (nl + kContractL - 1) / kContractL;
   const int loc = blockIdx.x - prefix[p];
-  const int l = loc % nl, t = loc / nl;
+  const int t = loc / groups, l0 = (loc % groups) * kContractL;
+  const int nlb = min(kContractL, nl - l0);  // l of this CTA
   extern __shared__ double2 sm2[];
-  V* Tm = reinterpret_cast<V*>(sm2);  // [nb][nb]
-  V* tmp = Tm + nb * nb;              // [nb][nff]
-  V* cs = tmp + nb * nff;             // [nff][nb]
-  V* qx = cs + nff * nb;              // [nd]
-  V* qy = qx + nd;                    // [nd]
-  const int ix = l / pd.ncy, iy = l - ix * pd.ncy;
+  V* Tm = reinterpret_cast<V*>(sm2);       // [kContractL][nb][nb]
+  V* tmp = Tm + kContractL * nb * nb;      // [nb][nff]
+  V* cs = tmp + nb * nff;                  // [nff][nb]
+  V* qx = cs + nff * nb;                   // [kContractL][nd]
+  V* qy = qx + kContractL * nd;            // [kContractL][nd]
   const size_t n2 = (size_t)nff * nff;
-  double* out = vbase + pd.off_state + ((size_t)t * nl + l) * n2;
-  const double* own = ybase + pd.off_state + ((size_t)t * nl + l) * n2;
   const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
   const double U = pd.U;
   if (!pd.feedback) {
-    for (int e = threadIdx.x; e < (int)n2; e += blockDim.x)
-      out[e] = (e == 0 ? U : 0.0) + own_sign * own[e];
+    for (int e = threadIdx.x; e < nlb * (int)n2; e += blockDim.x) {
+      const int j = e / (int)n2, r = e % (int)n2;
+      const size_t o = ((size_t)t * nl + l0 + j) * n2 + r;
+      vbase[pd.off_state + o] = (r == 0 ? U : 0.0) + own_sign * ybase[pd.off_state + o];
+    }
     return;
   }
   for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = to_c<V>(pd.coef[e]);
-  for (int e = threadIdx.x; e < nd; e += blockDim.x) {
-    qx[e] = to_c<V>(pd.phase[ix * nd + e]);
-    qy[e] = to_c<V>(pd.phase[(pd.ncx + iy) * nd + e]);
+  for (int e = threadIdx.x; e < kContractL * nd; e += blockDim.x) {
+    const int j = e / nd, d = e % nd;
+    const int l = l0 + min(j, nlb - 1);
+    const int ix = l / pd.ncy, iy = l - ix * pd.ncy;
+    qx[e] = to_c<V>(pd.phase[ix * nd + d]);
+    qy[e] = to_c<V>(pd.phase[(pd.ncx + iy) * nd + d]);
   }
   __syncthreads();
   const int* rp = pd.row_ptr + (size_t)t * (nb * nb + 1);
@@ -162,32 +172,42 @@ __global__ void contract_kernel(const PointDesc* __restrict__ pts, const int* __
   const V* fkey = fkbase + pd.off_fkey;
   const T inv_nl = (T)(1.0 / nl);
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
-    V acc = {0, 0};
-    for (int j = rp[o]; j < rp[o + 1]; ++j) {
-      const int4 q = tm[j];
-      V ph = cmul(qx[q.y], qy[q.z]);
-      if (q.w < 0) ph = {-ph.x, -ph.y};
-      acc = cfma(ph, fkey[q.x], acc);
+    V acc[kContractL];
+#pragma unroll
+    for (int j = 0; j < kContractL; ++j) acc[j] = {0, 0};
+    for (int k = rp[o]; k < rp[o + 1]; ++k) {
+      const int4 q = tm[k];
+      V f = fkey[q.x];
+      if (q.w < 0) f = {-f.x, -f.y};
+#pragma unroll
+      for (int j = 0; j < kContractL; ++j)
+        acc[j] = cfma(cmul(qx[j * nd + q.y], qy[j * nd + q.z]), f, acc[j]);
     }
-    Tm[o] = {acc.x * inv_nl, acc.y * inv_nl};
+#pragma unroll
+    for (int j = 0; j < kContractL; ++j) Tm[j * nb * nb + o] = {acc[j].x * inv_nl, acc[j].y * inv_nl};
   }
   __syncthreads();
-  // tmp[b1][n] = sum_b2 T[b1][b2] c_n(b2)
-  for (int e = threadIdx.x; e < nb * nff; e += blockDim.x) {
-    const int b1 = e / nff, n = e % nff;
-    V s = {0, 0};
-    for (int b2 = 0; b2 < nb; ++b2) s = cfma(Tm[b1 * nb + b2], cs[n * nb + b2], s);
-    tmp[e] = s;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < (int)n2; e += blockDim.x) {
-    const int m = e / nff, n = e % nff;
-    T s = 0;
-    for (int b1 = 0; b1 < nb; ++b1) {
-      const V c1 = cs[m * nb + b1], t1 = tmp[b1 * nff + n];
-      s = fma(c1.x, t1.x, fma(-c1.y, t1.y, s));  // real part of c * tmp
+  for (int j = 0; j < nlb; ++j) {
+    const V* Tj = Tm + j * nb * nb;
+    // tmp[b1][n] = sum_b2 T[b1][b2] c_n(b2)
+    for (int e = threadIdx.x; e < nb * nff; e += blockDim.x) {
+      const int b1 = e / nff, n = e % nff;
+      V s = {0, 0};
+      for (int b2 = 0; b2 < nb; ++b2) s = cfma(Tj[b1 * nb + b2], cs[n * nb + b2], s);
+      tmp[e] = s;
     }
-    out[e] = (e == 0 ? U : 0.0) + own_sign * own[e] + (double)s;
+    __syncthreads();
+    const size_t base = pd.off_state + ((size_t)t * nl + l0 + j) * n2;
+    for (int e = threadIdx.x; e < (int)n2; e += blockDim.x) {
+      const int m = e / nff, n = e % nff;
+      T s = 0;
+      for (int b1 = 0; b1 < nb; ++b1) {
+        const V c1 = cs[m * nb + b1], t1 = tmp[b1 * nff + n];
+        s = fma(c1.x, t1.x, fma(-c1.y, t1.y, s));  // real part of c * tmp
+      }
+      vbase[base + e] = (e == 0 ? U : 0.0) + own_sign * ybase[base + e] + (double)s;
+    }
+    __syncthreads();
   }
 }
 
@@ -203,7 +223,8 @@ size_t dft_smem(const MultiView& v) {
 template <class T>
 size_t contract_smem(const MultiView& v) {
   return sizeof(typename C2<T>::type) *
-         ((size_t)v.nb_max * v.nb_max + 2 * (size_t)v.nb_max * v.nff_max + 2 * v.nd_max);
+         ((size_t)kContractL * v.nb_max * v.nb_max + 2 * (size_t)v.nb_max * v.nff_max +
+          2 * (size_t)kContractL * v.nd_max);
 }
 
 template <class T>
@@ -246,6 +267,8 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
 }  // namespace
 
 int dft_ctas(int nkeys) { return (nkeys + kDftWarps - 1) / kDftWarps; }
+
+int contract_ctas(int nl) { return 3 * ((nl + kContractL - 1) / kContractL); }
 
 tufrg_status prepare_project_multi(const MultiView& v) {
   TUFRG_CHECK(prepare_typed<double>(v));

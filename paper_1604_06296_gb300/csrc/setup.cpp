@@ -247,6 +247,10 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     }
   c->nrow = (int)rowshift.size();
   c->c4v = c4v;
+  std::vector<int2> lrow(c->nl);
+  for (int r = 0; r < c->nrow; ++r)
+    for (int i = rowimg_ptr[r]; i < rowimg_ptr[r + 1]; ++i)
+      lrow[rowimg[i].x] = make_int2(r, rowimg[i].y);
 
   c->rm = c->npair <= 16 ? 1 : (c->npair <= 32 ? 2 : 4);
   const int mt = 16 * c->rm;
@@ -267,6 +271,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_kidx = dl->d_kidx;
     c->d_F = dl->d_F;
     c->d_pair = dl->d_pair;
+    c->d_pairidx = dl->d_pairidx;
     c->d_rowoff = dl->d_rowoff;
     c->d_kbase = dl->d_kbase;
     c->d_Fhi = dl->d_Fhi;
@@ -274,6 +279,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_shift = dl->d_shift;
     c->d_rowimg_ptr = dl->d_rowimg_ptr;
     c->d_rowimg = dl->d_rowimg;
+    c->d_lrow = dl->d_lrow;
     c->d_symperm = dl->d_symperm;
     c->d_symsign = dl->d_symsign;
   }
@@ -314,9 +320,15 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
       F[(size_t)q * c->kpad + k] =
           kw[k] * fv[(size_t)m * c->kdim + k] * fv[(size_t)n * c->kdim + k] / c->nf;
   }
+  std::vector<int> pairidx((size_t)nff * nff, -1);
+  for (int q = 0; q < c->npair; ++q) {
+    pairidx[(size_t)c->pair_m[q] * nff + c->pair_n[q]] = q;
+    pairidx[(size_t)c->pair_n[q] * nff + c->pair_m[q]] = q;
+  }
   if (!dl) {
     TUFRG_CHECK(upload(&c->d_F, F, st));
     TUFRG_CHECK(upload(&c->d_pair, pair, st));
+    TUFRG_CHECK(upload(&c->d_pairidx, pairidx, st));
   }
 
   if (c->p.precision != TUFRG_FP64) {
@@ -378,6 +390,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CHECK(upload(&c->d_shift, rowshift, st));
     TUFRG_CHECK(upload(&c->d_rowimg_ptr, rowimg_ptr, st));
     TUFRG_CHECK(upload(&c->d_rowimg, rowimg, st));
+    TUFRG_CHECK(upload(&c->d_lrow, lrow, st));
     TUFRG_CHECK(upload(&c->d_symperm, symperm, st));
     TUFRG_CHECK(upload(&c->d_symsign, symsign, st));
   }
@@ -410,6 +423,9 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CUDA(cudaStreamCreateWithFlags(&c->fstream, cudaStreamNonBlocking));
     TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    TUFRG_CUDA(cudaStreamCreateWithFlags(&c->pstream, cudaStreamNonBlocking));
+    TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }
   if (share.own_view) {
     double* lam[1] = {c->d_lambda};
@@ -471,7 +487,8 @@ void free_device(tufrg_ctx* c) {
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {
     void* loops[] = {c->d_rowoff,  c->d_kbase,     c->d_Fhi,    c->d_Flo,     c->d_rowimg_ptr,
-                     c->d_rowimg,  c->d_symperm,   c->d_symsign, c->d_kidx,   c->d_F,
+                     c->d_rowimg,  c->d_lrow,      c->d_symperm, c->d_symsign, c->d_kidx,
+                     c->d_F,       c->d_pairidx,
                      c->d_shift,   c->d_pair};
     for (void* p : loops)
       if (p) cudaFree(p);
@@ -481,9 +498,10 @@ void free_device(tufrg_ctx* c) {
     for (void* p : proj)
       if (p) cudaFree(p);
   }
-  if (c->ev_in) cudaEventDestroy(c->ev_in);
-  if (c->ev_out) cudaEventDestroy(c->ev_out);
-  if (c->fstream) cudaStreamDestroy(c->fstream);
+  for (cudaEvent_t e : {c->ev_in, c->ev_out, c->ev_fork, c->ev_join})
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t q : {c->fstream, c->pstream})
+    if (q) cudaStreamDestroy(q);
 }
 
 }  // namespace tufrg
