@@ -286,17 +286,14 @@ def run_scan(args, rank, world, local):
         pg.all_reduce(t, op=pg.ReduceOp.SUM)
         dev_s, rhs = float(tmax[0]), float(t[1])
     value = rhs / dev_s
-    # dominant kernel: the persistent loop contraction over all points
-    chi = batch.empty(True)
-    kms = []
+    # dominant kernel: the persistent loop contraction over all points (CUDA
+    # events inside the library around its launch; inputs far larger than L2)
+    kms, sms = [], []
     for _ in range(3):
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        batch.loops(0.5, out=chi)
-        a1.record()
-        a1.synchronize()
-        kms.append(a0.elapsed_time(a1))
-    k_ms = statistics.median(kms)
+        k1, s1 = batch.profile_loops(0.5, 1)
+        kms.append(k1)
+        sms.append(s1)
+    k_ms, stage_ms = statistics.median(kms), statistics.median(sms)
     flops = 0.0
     for q in pts:
         npair, kdim, nrow = loop_counts(tufrg, q["bonds"], q["nc"], q["nc"], q["nf"], q["nf"])
@@ -307,7 +304,9 @@ def run_scan(args, rank, world, local):
     achieved = flops / (k_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel_ms": k_ms,
-                "kernel": f"loops_tc_kernel<{args.precision}> over all points (+ tables, reduce)",
+                "stage_ms": stage_ms,
+                "kernel": f"loops_tc_kernel<{args.precision}> over all points (stage_ms: + "
+                          "tables, split-K combination)",
                 "algorithmic_flop_per_launch": flops,
                 "peak_source": f"bf16 dense burst from {peak_src} (of measured)"}
     # kernels of the library in the timed call: first stage (combination + 7
@@ -537,19 +536,19 @@ def main():
         device_s_max, total_rhs = device_s, float(rhs_count)
     value = total_rhs / device_s_max
 
-    # dominant kernel: the loop contraction, timed alone on the launching stream
+    # dominant kernel: the loop contraction, timed by CUDA events recorded
+    # inside the library around its launch on its stream (L2 flushed before
+    # each launch); the loop stage (table + contraction + split-K
+    # combination) beside it
     peaks, peak_src = measured_peaks()
-    chi = solver.empty(2)
-    kms = []
+    kms, sms = [], []
     for _ in range(max(3, args.steps)):
         flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        solver.loops(0.5, out=chi)
-        e1.record()
-        e1.synchronize()
-        kms.append(e0.elapsed_time(e1))
+        k1, s1 = solver.profile_loops(0.5, 1)
+        kms.append(k1)
+        sms.append(s1)
     k_ms = statistics.median(kms)
+    stage_ms = statistics.median(sms)
     p = solver.params
     npair, kdim, nrow = loop_counts(tufrg, solver._bonds, p.nc_x, p.nc_y, p.nf_x, p.nf_y)
     if args.precision == "fp64":
@@ -557,7 +556,8 @@ def main():
         peak = fp64_peak_tflops(torch)
         roofline = {"bound": "alu", "peak_source":
                     "FP64: cuBLAS DGEMM 4096^3 measured in this run (of measured)",
-                    "kernel": "loops_fp64_kernel (+ per-scale table, split-K reduce)",
+                    "kernel": "loops_fp64_kernel (stage_ms: + per-scale table, split-K "
+                              "combination)",
                     "traffic": profile_traffic("loops_fp64.cu", "loops_fp64_cfg2.txt")}
     else:
         flops = 2.0 * 3 * 2 * npair * kdim * nrow        # 3 split products issued per MAC
@@ -567,12 +567,14 @@ def main():
                     f"bf16 dense burst {bf16} TFLOP/s from {peak_src}"
                     + ("" if args.precision == "bf16x3" else " x nominal tf32/bf16 1.1/2.25")
                     + " (of measured)",
-                    "kernel": f"loops_tc_kernel<{args.precision}> (+ per-scale table, reduce)",
+                    "kernel": f"loops_tc_kernel<{args.precision}> (stage_ms: + per-scale table, "
+                              "split-K combination)",
                     "traffic": profile_traffic("loops_tc.cu",
                                                f"loops_tc_{args.precision}_cfg2.txt")}
     achieved = flops / (k_ms * 1e-3) / 1e12
     roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "kernel_ms": k_ms,
+                     "frac": achieved / peak, "kernel_ms": k_ms, "stage_ms": stage_ms,
+                     "stage_frac": flops / (stage_ms * 1e-3) / 1e12 / peak,
                      "algorithmic_flop_per_launch": flops,
                      "counting": f"{npair} allowed pairs x {kdim} half-zone points x {nrow} "
                                  "loop rows (C4v orbits of interior l + boundary l) x 2 "

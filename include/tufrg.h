@@ -331,6 +331,10 @@ tufrg_status tufrg_batch_flow(tufrg_batch* b, const tufrg_flow_opts* opts, doubl
 tufrg_status tufrg_batch_autotune(tufrg_batch* b, double lambda, tufrg_tune_report* rep,
                                   void* cuda_stream);
 
+/* As tufrg_profile_loops, for the persistent contraction over all points. */
+tufrg_status tufrg_batch_profile_loops(tufrg_batch* b, double lambda, int32_t n,
+                                       double* kernel_ms, double* stage_ms, void* cuda_stream);
+
 /* As tufrg_check, for the batch's kernels. */
 tufrg_status tufrg_batch_check(tufrg_batch* b, void* cuda_stream);
 
@@ -415,6 +419,14 @@ tufrg_status tufrg_surrogate_train(tufrg_surrogate* s, const float* x_dev, const
  * surrogate's work buffers serve one flow at a time. */
 tufrg_status tufrg_surrogate_attach(tufrg_ctx* ctx, tufrg_surrogate* s, int32_t judge_every,
                                     double tol);
+
+/* Measurement: runs n loop contractions of the context at scale lambda (up
+ * to the loops of the rows, as a right-hand side does) and returns the mean
+ * duration of the contraction kernel itself (kernel_ms; CUDA events recorded
+ * around its launch on its stream) and of the whole loop stage -- per-scale
+ * table, contraction, split-K combination -- (stage_ms).  Blocks. */
+tufrg_status tufrg_profile_loops(tufrg_ctx* ctx, double lambda, int32_t n, double* kernel_ms,
+                                 double* stage_ms, void* cuda_stream);
 
 const char* tufrg_status_string(tufrg_status s);
 

@@ -148,6 +148,10 @@ class Solver:
         _abi.tufrg_surrogate_attach(self.ctx, surrogate.s if surrogate else None,
                                     int(judge_every), float(tol))
 
+    def profile_loops(self, lam=0.5, n=5):
+        """(contraction kernel ms, loop stage ms), CUDA events inside the library."""
+        return _abi.tufrg_profile_loops(self.ctx, float(lam), int(n), _stream())
+
     def autotune(self, lam=1.0):
         """Tile autotuning of the tensor-core loops; returns the timing report."""
         return _abi.tufrg_autotune(self.ctx, float(lam), _stream()).as_dict()
@@ -256,6 +260,10 @@ class Batch:
 
     def autotune(self, lam=1.0):
         return _abi.tufrg_batch_autotune(self.b, float(lam), _stream()).as_dict()
+
+    def profile_loops(self, lam=0.5, n=3):
+        """(contraction kernel ms, loop stage ms) over all points."""
+        return _abi.tufrg_batch_profile_loops(self.b, float(lam), int(n), _stream())
 
     def check(self):
         _abi.tufrg_batch_check(self.b, _stream())

@@ -120,6 +120,10 @@ SIGNATURES = {
     "tufrg_surrogate_train": ([c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_double,
                                ctypes.c_uint64, POINTER(c_double), c_void_p], c_int32),
     "tufrg_surrogate_attach": ([c_void_p, c_void_p, c_int32, c_double], c_int32),
+    "tufrg_profile_loops": ([c_void_p, c_double, c_int32, POINTER(c_double), POINTER(c_double),
+                             c_void_p], c_int32),
+    "tufrg_batch_profile_loops": ([c_void_p, c_double, c_int32, POINTER(c_double),
+                                   POINTER(c_double), c_void_p], c_int32),
     "tufrg_status_string": ([c_int32], ctypes.c_char_p),
     "tufrg_last_cuda_error": ([], ctypes.c_char_p),
 }
@@ -395,3 +399,18 @@ def tufrg_surrogate_set_scaling(s, shift, scale, stream: int = 0) -> None:
     _check(lib().tufrg_surrogate_set_scaling(s, a.ctypes.data_as(POINTER(ctypes.c_float)),
                                              b.ctypes.data_as(POINTER(ctypes.c_float)),
                                              _dptr(stream)), "tufrg_surrogate_set_scaling")
+
+
+def tufrg_profile_loops(ctx, lam: float, n: int, stream: int = 0):
+    """(kernel ms, stage ms) averaged over n loop contractions."""
+    k, g = c_double(), c_double()
+    _check(lib().tufrg_profile_loops(ctx, lam, n, byref(k), byref(g), _dptr(stream)),
+           "tufrg_profile_loops")
+    return k.value, g.value
+
+
+def tufrg_batch_profile_loops(b, lam: float, n: int, stream: int = 0):
+    k, g = c_double(), c_double()
+    _check(lib().tufrg_batch_profile_loops(b, lam, n, byref(k), byref(g), _dptr(stream)),
+           "tufrg_batch_profile_loops")
+    return k.value, g.value

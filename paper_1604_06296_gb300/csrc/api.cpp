@@ -296,6 +296,43 @@ tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x, i
   return TUFRG_OK;
 }
 
+tufrg_status tufrg_profile_loops(tufrg_ctx* c, double lambda, int32_t n, double* kernel_ms,
+                                 double* stage_ms, void* stream) {
+  if (!c || n < 1 || !finite_pos(lambda) || !kernel_ms || !stage_ms || !c->d_chi)
+    return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  tufrg_status s = TUFRG_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) s = TUFRG_ERR_CUDA;
+  double k = 0.0, g = 0.0;
+  for (int i = 0; i < n && s == TUFRG_OK; ++i) {
+    s = tufrg::launch_set_scalar(c->d_lambda, lambda, st);
+    if (s == TUFRG_OK && cudaEventRecord(ev[2], st) != cudaSuccess) s = TUFRG_ERR_CUDA;
+    if (s == TUFRG_OK && c->p.precision == TUFRG_FP64) {
+      s = tufrg::launch_scale_tables(c, st);
+      if (s == TUFRG_OK) s = tufrg::launch_loops_fp64_rows(c, st, ev);
+    } else if (s == TUFRG_OK) {
+      s = tufrg::launch_loops_tc_rows_multi(c->view, st, ev);
+    }
+    if (s == TUFRG_OK && cudaEventRecord(ev[3], st) != cudaSuccess) s = TUFRG_ERR_CUDA;
+    float a = 0.f, b = 0.f;
+    if (s == TUFRG_OK &&
+        (cudaEventSynchronize(ev[3]) != cudaSuccess ||
+         cudaEventElapsedTime(&a, ev[0], ev[1]) != cudaSuccess ||
+         cudaEventElapsedTime(&b, ev[2], ev[3]) != cudaSuccess))
+      s = TUFRG_ERR_CUDA;
+    k += a;
+    g += b;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  TUFRG_CHECK(s);
+  *kernel_ms = k / n;
+  *stage_ms = g / n;
+  return tufrg_check(c, stream);
+}
+
 tufrg_status tufrg_check(tufrg_ctx* c, void* stream) {
   if (!c) return TUFRG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;

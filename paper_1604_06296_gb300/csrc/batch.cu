@@ -56,6 +56,16 @@ __global__ void bcombo_kernel(const double* __restrict__ y, double* __restrict__
   }
 }
 
+// the scales of a stage of every active point
+__global__ void bstage_lambda_kernel(const FlowCtl* __restrict__ ctl, double cnode,
+                                     double* __restrict__ lam, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || ctl[p].done) return;
+  const double L = exp(ctl[p].s + cnode * ctl[p].h);
+  lam[2 * p] = L;
+  lam[2 * p + 1] = L;
+}
+
 __global__ void berror_kernel(const double* __restrict__ y, const double* __restrict__ ynew,
                               Combo ce, FlowCtl* __restrict__ ctl, const Seg* __restrict__ seg,
                               const int* __restrict__ prefix, int n) {
@@ -215,7 +225,7 @@ struct tufrg_batch {
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaStream_t pstream = nullptr;  // projections beside the loops
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_stage = nullptr;
 };
 
 namespace tufrg {
@@ -302,8 +312,12 @@ tufrg_status bstage(tufrg_batch* b, const double* y, double* out,
     cb.k[j] = terms[j].second;
   }
   cb.c = cnode;
-  bcombo_kernel<<<f.n_chunks, kFlowThreads, 0, st>>>(y, out, cb, f.ctl, b->d_lam, f.seg,
-                                                     f.prefix, b->n, 1);
+  // the stage's states on the projection stream, the scales on the loop stream
+  TUFRG_CUDA(cudaEventRecord(b->ev_stage, st));
+  TUFRG_CUDA(cudaStreamWaitEvent(b->pstream, b->ev_stage, 0));
+  bcombo_kernel<<<f.n_chunks, kFlowThreads, 0, b->pstream>>>(y, out, cb, f.ctl, b->d_lam, f.seg,
+                                                             f.prefix, b->n, 0);
+  bstage_lambda_kernel<<<grid_for(b->n), 128, 0, st>>>(f.ctl, cnode, b->d_lam, b->n);
   TUFRG_CUDA(cudaGetLastError());
   return batch_rhs_device(b, out, k_out, true, st);
 }
@@ -544,7 +558,7 @@ void batch_free(tufrg_batch* b) {
       tufrg::free_device(c);
       delete c;
     }
-  for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_fork, b->ev_join})
+  for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_fork, b->ev_join, b->ev_stage})
     if (e) cudaEventDestroy(e);
   for (cudaStream_t q : {b->fstream, b->pstream})
     if (q) cudaStreamDestroy(q);
@@ -610,6 +624,7 @@ tufrg_status batch_setup(int32_t n, const tufrg_params* params, cudaStream_t st,
   TUFRG_CUDA(cudaStreamCreateWithFlags(&b->pstream, cudaStreamNonBlocking));
   TUFRG_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
   TUFRG_CUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  TUFRG_CUDA(cudaEventCreateWithFlags(&b->ev_stage, cudaEventDisableTiming));
   TUFRG_CUDA(cudaStreamSynchronize(st));
   return TUFRG_OK;
 }
@@ -714,6 +729,38 @@ tufrg_status tufrg_autotune(tufrg_ctx* c, double lambda, tufrg_tune_report* rep,
   tufrg::CtxRun r{c, lambda};
   TUFRG_CHECK(tufrg::autotune_view(c->view, tufrg::run_ctx, &r, rep, st));
   return tufrg::check_err(c->d_err, st);
+}
+
+tufrg_status tufrg_batch_profile_loops(tufrg_batch* b, double lambda, int32_t n,
+                                       double* kernel_ms, double* stage_ms, void* cuda_stream) {
+  if (!b || n < 1 || !finite_pos(lambda) || !kernel_ms || !stage_ms) return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::vector<double> lam(b->n, lambda);
+  TUFRG_CHECK(tufrg::set_lambdas(b, lam.data(), st));
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  tufrg_status s = TUFRG_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) s = TUFRG_ERR_CUDA;
+  double k = 0.0, g = 0.0;
+  for (int i = 0; i < n && s == TUFRG_OK; ++i) {
+    if (cudaEventRecord(ev[2], st) != cudaSuccess) s = TUFRG_ERR_CUDA;
+    if (s == TUFRG_OK) s = tufrg::launch_loops_tc_rows_multi(b->view, st, ev);
+    if (s == TUFRG_OK && cudaEventRecord(ev[3], st) != cudaSuccess) s = TUFRG_ERR_CUDA;
+    float a = 0.f, c = 0.f;
+    if (s == TUFRG_OK &&
+        (cudaEventSynchronize(ev[3]) != cudaSuccess ||
+         cudaEventElapsedTime(&a, ev[0], ev[1]) != cudaSuccess ||
+         cudaEventElapsedTime(&c, ev[2], ev[3]) != cudaSuccess))
+      s = TUFRG_ERR_CUDA;
+    k += a;
+    g += c;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  TUFRG_CHECK(s);
+  *kernel_ms = k / n;
+  *stage_ms = g / n;
+  return tufrg::check_err(b->d_err, st);
 }
 
 tufrg_status tufrg_batch_check(tufrg_batch* b, void* cuda_stream) {

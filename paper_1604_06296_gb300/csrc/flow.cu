@@ -43,6 +43,14 @@ __global__ void combo_kernel(const double* __restrict__ y, double* __restrict__ 
   }
 }
 
+// the scale of a stage: Lambda = exp(s + c h), for the loops and for dy/ds
+__global__ void stage_lambda_kernel(const FlowCtl* __restrict__ ctl, double cnode,
+                                    double* __restrict__ lam) {
+  const double L = exp(ctl->s + cnode * ctl->h);
+  lam[0] = L;
+  lam[1] = L;
+}
+
 __global__ void error_kernel(const double* __restrict__ y, const double* __restrict__ ynew,
                              Combo e, FlowCtl* __restrict__ ctl, size_t n) {
   const double h = ctl->h, rtol = ctl->rtol, atol = ctl->atol;
@@ -209,7 +217,12 @@ tufrg_status stage(tufrg_ctx* c, const double* y, double* out,
   }
   cb.c = cnode;
   const size_t n = c->state_elems();
-  combo_kernel<<<grid_for(n), 256, 0, st>>>(y, out, cb, f.ctl, c->d_lambda, n, 1);
+  // the stage's state on the projection stream (its consumer), its scale on
+  // the loop stream: the loops start without waiting for the combination
+  TUFRG_CUDA(cudaEventRecord(c->ev_stage, st));
+  TUFRG_CUDA(cudaStreamWaitEvent(c->pstream, c->ev_stage, 0));
+  combo_kernel<<<grid_for(n), 256, 0, c->pstream>>>(y, out, cb, f.ctl, c->d_lambda, n, 0);
+  stage_lambda_kernel<<<1, 1, 0, st>>>(f.ctl, cnode, c->d_lambda);
   TUFRG_CUDA(cudaGetLastError());
   return rhs_device(c, c->loop_prec, out, k_out, true, st);
 }

@@ -224,6 +224,7 @@ struct tufrg_ctx {
   // products; branches of the captured flow graphs)
   cudaStream_t pstream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_stage = nullptr;  // flows: the stage combination joins the projection stream
 
   size_t state_elems() const { return (size_t)3 * nl * nff * nff; }
 };
@@ -269,7 +270,7 @@ void free_device(tufrg_ctx* c);
 // kernels (launchers)
 tufrg_status launch_scale_tables(tufrg_ctx* c, cudaStream_t st);
 tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi_out, cudaStream_t st);
-tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st);
+tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr);
 // projections and products: FP64 arithmetic when prec == TUFRG_FP64, else FP32
 tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 
@@ -322,7 +323,10 @@ tufrg_status launch_products_multi(const MultiView& v, int prec, const double* v
 // loop contraction up to the row loops in c->view.d_rowres (no expansion);
 // prec must not be the surrogate
 tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st);
-tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st);
+// ev (optional): events recorded just before and after the contraction
+// kernel itself, on its stream
+tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st,
+                                        cudaEvent_t* ev = nullptr);
 // loops in the given precision (the context's, or FP64)
 tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi_out, cudaStream_t st);
 

@@ -186,8 +186,9 @@ tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi, cudaStream_t st) {
   return launch_expand_multi(c->view, chi, st);
 }
 
-tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st) {
+tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st, cudaEvent_t* ev) {
   dim3 grid((c->nrow + LT - 1) / LT, c->mtiles, c->ksplit);
+  if (ev) TUFRG_CUDA(cudaEventRecord(ev[0], st));
   switch (c->rm) {
     case 1:
       loops_fp64_kernel<1><<<grid, NT, 0, st>>>(c->d_tab, c->d_kidx, c->d_F, c->d_shift,
@@ -205,6 +206,7 @@ tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st) {
                                                 c->kchunk, c->mpad, c->d_partial);
   }
   TUFRG_CUDA(cudaGetLastError());
+  if (ev) TUFRG_CUDA(cudaEventRecord(ev[1], st));
   return launch_fp64_rows(c->d_partial, c->mpad, c->ksplit, c->npair, c->nrow,
                           c->view.d_rowres, st);
 }

@@ -456,7 +456,7 @@ tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, cudaStream_t
   return launch_expand_multi(v, chi, st);
 }
 
-tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st) {
+tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st, cudaEvent_t* ev) {
   if (v.tc_prec == TUFRG_FP64 || v.n_items == 0) return TUFRG_ERR_ARG;
   scale_table_ext_kernel<<<v.total(kKindTable), kTableBlock, 0, st>>>(
       v.d, v.dprefix(kKindTable), v.n);
@@ -474,11 +474,13 @@ tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st) {
   a.tmem_cols = v.tmem_cols;
   const int ctas = std::min(v.ctas, v.n_items);
   const size_t smem = tc_smem_bytes(v.npad_max);
+  if (ev) TUFRG_CUDA(cudaEventRecord(ev[0], st));
   if (v.tc_prec == TUFRG_BF16X3)
     loops_tc_kernel<TUFRG_BF16X3><<<ctas, kThreads, smem, st>>>(a);
   else
     loops_tc_kernel<TUFRG_3XTF32><<<ctas, kThreads, smem, st>>>(a);
   TUFRG_CUDA(cudaGetLastError());
+  if (ev) TUFRG_CUDA(cudaEventRecord(ev[1], st));
   return launch_tc_rows_multi(v, st);
 }
 

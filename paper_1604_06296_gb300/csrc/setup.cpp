@@ -426,6 +426,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CUDA(cudaStreamCreateWithFlags(&c->pstream, cudaStreamNonBlocking));
     TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    TUFRG_CUDA(cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming));
   }
   if (share.own_view) {
     double* lam[1] = {c->d_lambda};
@@ -498,7 +499,7 @@ void free_device(tufrg_ctx* c) {
     for (void* p : proj)
       if (p) cudaFree(p);
   }
-  for (cudaEvent_t e : {c->ev_in, c->ev_out, c->ev_fork, c->ev_join})
+  for (cudaEvent_t e : {c->ev_in, c->ev_out, c->ev_fork, c->ev_join, c->ev_stage})
     if (e) cudaEventDestroy(e);
   for (cudaStream_t q : {c->fstream, c->pstream})
     if (q) cudaStreamDestroy(q);

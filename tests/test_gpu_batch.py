@@ -200,3 +200,8 @@ def test_batch_rejects_mixed_or_fp64_precision(torch):
     with pytest.raises(TufrgError) as e:
         _abi.tufrg_batch_setup(arr)
     assert e.value.status == -1
+
+
+def test_batch_profile_loops(torch, small):
+    k, g = small.profile_loops(0.5, 2)
+    assert 0 < k <= g

@@ -144,3 +144,14 @@ def test_basis_too_large_for_tensor_core_path_rejected(torch):
     with pytest.raises(TufrgError) as e:
         make(dict(CASES["nff29"]), torch, precision="bf16x3")
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp64"])
+def test_profile_loops(torch, precision):
+    s, p = make("cfg1", torch, precision=precision)
+    k, g = s.profile_loops(0.4, 3)
+    print(f"{precision}: contraction kernel {k * 1e3:.1f} us, loop stage {g * 1e3:.1f} us")
+    assert 0 < k <= g
+    # the profiled contractions are the real ones: the loops of the last are right
+    ref = np.stack(olo.chi_dot(p, 0.4))
+    assert rel(s.loops(0.4).cpu().numpy(), ref) < BOUND["bf16x3"]
