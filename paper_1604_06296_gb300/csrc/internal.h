@@ -192,7 +192,8 @@ struct tufrg_ctx {
   int tc_nsets = 1;                // accumulator sets per channel in TMEM
   int loop_prec = TUFRG_FP64;      // precision of the flow's next loop contractions
   int tc_hx = 0, tc_hy = 0, tc_wy = 0;  // halo of the extended table, its row width
-  float4* d_ext = nullptr;         // [(nfx+2hx)*wy] (xi, A, H, |xi|) in FP32 per scale
+  float4* d_ext = nullptr;         // halo table over [(nfx+2hx)*wy] points, FP32 per scale:
+                                   // A = 1/(Omega+|xi|), u = xi A (BF16X3: pair layout)
   int* d_rowoff = nullptr;         // [nrow] sx * wy + sy
   int* d_kbase = nullptr;          // [tc_kpad] loop point offsets in the halo table
   unsigned char* d_Fhi = nullptr;  // [tc_npad][tc_kpad] high parts of F (bf16 or tf32)

@@ -8,9 +8,9 @@
 // W_hi F_hi + W_lo F_hi + W_hi F_lo accumulated in FP32 in tensor memory;
 // the split-K partial sums of each CTA are combined in FP64 by a second
 // kernel.  The propagator operand W is generated in registers from the
-// per-scale FP32 table (xi, A = 1/(Omega + |xi|), H = |xi|(Omega + 3|xi|) A^3,
-// extended by a wrap-around halo so p +- l/2 is one add from p) with the same
-// closed-form frequency integral as the FP64 path, and written
+// per-scale FP32 table (A = 1/(Omega + |xi|), u = xi A, extended by a
+// wrap-around halo so p +- l/2 is one add from p) with the same closed-form
+// frequency integral as the FP64 path, and written
 // straight into the 128B-swizzled K-major shared-memory layout the MMA reads;
 // F (scale independent) is staged with cp.async.  Both channels share W's
 // table reads and divisions and have their own accumulator.
@@ -50,12 +50,18 @@ struct Prec<TUFRG_BF16X3> {
   static constexpr int kElem = 2;      // bytes
   static constexpr int kPerLane = 2;   // k per lane per row
   static constexpr uint32_t kFormat = 1;  // BF16
+  struct Buf {
+    float4 v[2];  // table pairs at p + l/2, p - l/2
+  };
 };
 template <>
 struct Prec<TUFRG_3XTF32> {
   static constexpr int kElem = 4;
   static constexpr int kPerLane = 1;
   static constexpr uint32_t kFormat = 2;  // TF32
+  struct Buf {
+    float2 v[4];  // table entries at p +- l/2 of two rows
+  };
 };
 
 template <int PREC>
@@ -76,21 +82,31 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 
 
 // Closed-form frequency integral of the two loops for two propagator pairs
-// at once, with paired FP32 instructions.  Table entries: (xi, A, H, |xi|).
-__device__ __forceinline__ void weights2(const float4 a0, const float4 b0, const float4 a1,
-                                         const float4 b1, float om, float om2, float inv_om2,
-                                         float2& wpp, float2& wph) {
-  const float2 Aa = make_float2(a0.y, a1.y), Ab = make_float2(b0.y, b1.y);
+// at once, with paired FP32 instructions, from the table values A and u of
+// both propagators (a at p + l/2, b at p - l/2).  With x = |xi| = |u| / A and
+// Omega A = 1 - |u|:
+//   D = A_a A_b (5 Omega (A_a + A_b) - 3 - 2 Omega^2 (A_a^2 + A_a A_b + A_b^2))
+//   S = (H_a + H_b) / (x_a + x_b),  H = x (3x + Omega) A^3 = |u| (1 + 2|u|) A,
+//     = A_a A_b (H_a + H_b) / (|u_a| A_b + |u_b| A_a)   (1/Omega^2 at x_a = x_b = 0)
+// the particle-particle weight is S for propagators of one sign, D else, and
+// the particle-hole weight the other one.
+__device__ __forceinline__ void weights_au(const float2 Aa, const float2 usa, const float2 Ab,
+                                           const float2 usb, float om, float om2,
+                                           float inv_om2, float2& wpp, float2& wph) {
   const float2 sa = __fadd2_rn(Aa, Ab), pa = __fmul2_rn(Aa, Ab);
   const float2 t1 = __ffma2_rn(sa, sa, make_float2(-pa.x, -pa.y));
   const float2 t2 = __ffma2_rn(make_float2(5.f * om, 5.f * om), sa, make_float2(-3.f, -3.f));
   const float2 br = __ffma2_rn(make_float2(-2.f * om2, -2.f * om2), t1, t2);
   const float2 D = __fmul2_rn(pa, br);
-  const float2 xs = __fadd2_rn(make_float2(a0.w, a1.w), make_float2(b0.w, b1.w));
-  const float2 hs = __fadd2_rn(make_float2(a0.z, a1.z), make_float2(b0.z, b1.z));
-  const float2 sg = __fmul2_rn(make_float2(a0.x, a1.x), make_float2(b0.x, b1.x));
-  const float S0 = xs.x > 0.f ? __fdividef(hs.x, xs.x) : inv_om2;
-  const float S1 = xs.y > 0.f ? __fdividef(hs.y, xs.y) : inv_om2;
+  const float2 ua = make_float2(fabsf(usa.x), fabsf(usa.y));
+  const float2 ub = make_float2(fabsf(usb.x), fabsf(usb.y));
+  const float2 ha = __fmul2_rn(ua, __ffma2_rn(ua, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
+  const float2 hb = __fmul2_rn(ub, __ffma2_rn(ub, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
+  const float2 num = __fmul2_rn(pa, __ffma2_rn(ha, Aa, __fmul2_rn(hb, Ab)));
+  const float2 den = __ffma2_rn(ua, Ab, __fmul2_rn(ub, Aa));
+  const float2 sg = __fmul2_rn(usa, usb);
+  const float S0 = den.x > 0.f ? __fdividef(num.x, den.x) : inv_om2;
+  const float S1 = den.y > 0.f ? __fdividef(num.y, den.y) : inv_om2;
   wpp = make_float2(sg.x > 0.f ? S0 : D.x, sg.y > 0.f ? S1 : D.y);
   wph = make_float2(sg.x > 0.f ? D.x : S0, sg.y > 0.f ? D.y : S1);
 }
@@ -192,7 +208,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 
     if (warp < kProducers) {
       // ---------------------------------------------------------- producers
+      // BF16X3: pairs (A_q, A_q+1, u_q, u_q+1) of even q at ext, of odd q at
+      // ext + (n_ext + 1) / 2; 3xTF32: (A_q, u_q) per point
       const float4* ext = pd.ext;
+      const float4* ext_odd = pd.ext + (pd.n_ext + 1) / 2;
+      const float2* ext2 = reinterpret_cast<const float2*>(pd.ext);
       const unsigned char* Fhi = pd.Fhi;
       const unsigned char* Flo = pd.Flo;
       const size_t frow = (size_t)pd.kpad_tc * P::kElem;  // bytes per F row
@@ -217,40 +237,43 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
                      (t ? Flo : Fhi) + (size_t)row * frow + fk + ch * 16);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        // this lane's loop points as offsets into the halo table (padding
-        // points use a valid entry: their F is zero)
-        int pb[P::kPerLane];
-        if constexpr (P::kPerLane == 2) {
-          const int2 v = __ldg(reinterpret_cast<const int2*>(pd.kbase + k0) + lane);
-          pb[0] = v.x;
-          pb[1] = v.y;
-        } else {
-          pb[0] = __ldg(pd.kbase + k0 + lane);
-        }
+        // this lane's first loop point as an offset into the halo table
+        // (padding points use a valid entry: their F is zero); BF16X3 lanes
+        // take loop points 2 lane, 2 lane + 1 of the K-block, neighbours iy,
+        // iy + 1 of one column, i.e. table entries pb, pb + 1
+        const int pb = __ldg(pd.kbase + k0 + P::kPerLane * lane);
         // rolling pipeline over this warp's rows: the table gathers of the
         // next unit are in flight while the current unit is computed (two
-        // register buffers of four float4); rows without an l are skipped
-        // (their accumulator rows are never read)
-        float4 bufA[4], bufB[4];
-        auto load_unit = [&](int u, float4* b) {
-          if constexpr (P::kPerLane == 2) {  // one row, two loop points
+        // register buffers); rows without an l are skipped (their
+        // accumulator rows are never read)
+        using Buf = typename P::Buf;
+        Buf bufA, bufB;
+        auto load_unit = [&](int u, Buf& b) {
+          if constexpr (P::kPerLane == 2) {  // one row, two loop points: one pair each side
             const int off = s_off[warp + kProducers * u];
-            b[0] = __ldg(ext + (pb[0] + off));
-            b[1] = __ldg(ext + (pb[0] - off));
-            b[2] = __ldg(ext + (pb[1] + off));
-            b[3] = __ldg(ext + (pb[1] - off));
+            const int qa = pb + off, qb = pb - off;  // of one parity
+            const float4* t = (qa & 1) ? ext_odd : ext;
+            b.v[0] = __ldg(t + (qa >> 1));
+            b.v[1] = __ldg(t + (qb >> 1));
           } else {  // two rows, one loop point
             const int off0 = s_off[warp + kProducers * (2 * u)];
             const int off1 = s_off[warp + kProducers * (2 * u + 1)];
-            b[0] = __ldg(ext + (pb[0] + off0));
-            b[1] = __ldg(ext + (pb[0] - off0));
-            b[2] = __ldg(ext + (pb[0] + off1));
-            b[3] = __ldg(ext + (pb[0] - off1));
+            b.v[0] = __ldg(ext2 + (pb + off0));
+            b.v[1] = __ldg(ext2 + (pb - off0));
+            b.v[2] = __ldg(ext2 + (pb + off1));
+            b.v[3] = __ldg(ext2 + (pb - off1));
           }
         };
-        auto do_unit = [&](int u, const float4* b) {
+        auto do_unit = [&](int u, const Buf& b) {
           float2 wpp, wph;
-          weights2(b[0], b[1], b[2], b[3], om, om2, inv_om2, wpp, wph);
+          if constexpr (P::kPerLane == 2)
+            weights_au(make_float2(b.v[0].x, b.v[0].y), make_float2(b.v[0].z, b.v[0].w),
+                       make_float2(b.v[1].x, b.v[1].y), make_float2(b.v[1].z, b.v[1].w), om, om2,
+                       inv_om2, wpp, wph);
+          else
+            weights_au(make_float2(b.v[0].x, b.v[2].x), make_float2(b.v[0].y, b.v[2].y),
+                       make_float2(b.v[1].x, b.v[3].x), make_float2(b.v[1].y, b.v[3].y), om, om2,
+                       inv_om2, wpp, wph);
           if constexpr (PREC == TUFRG_BF16X3) {
             uint32_t v[4];
             const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
@@ -399,8 +422,13 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 
 constexpr int kTableBlock = 256, kTablePerThread = 4;
 
-// Per-scale FP32 table (xi, A, H, |xi|) with a wrap-around halo of hx, hy
-// points on each side, so that p +- l/2 needs no wrapping.
+// Per-scale FP32 table (A, u) = (1/(Omega + |xi|), xi A) with a wrap-around
+// halo of hx, hy points on each side, so that p +- l/2 needs no wrapping
+// (FP32 arithmetic: the table is FP32, and GB300's FP64 division would
+// dominate this kernel).  BF16X3 layout: float4 (A_q, A_q+1, u_q, u_q+1) for
+// even q in the first half, for odd q in the second (the last entry
+// repeated past the end); 3xTF32: float2 (A_q, u_q).
+template <int PREC>
 __global__ void __launch_bounds__(kTableBlock)
     scale_table_ext_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
                            int n) {
@@ -409,20 +437,35 @@ __global__ void __launch_bounds__(kTableBlock)
   if (pd.skip && *pd.skip) return;
   const float omf = (float)pd.lam[0];
   const int e0 = (blockIdx.x - prefix[p]) * kTableBlock * kTablePerThread + threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < kTablePerThread; ++q) {
-    const int e = e0 + q * kTableBlock;
-    if (e >= pd.n_ext) break;
+  auto entry = [&](int e) {
+    e = min(e, pd.n_ext - 1);
     int ix = e / pd.wy - pd.hx, iy = e % pd.wy - pd.hy;
     ix += ix < 0 ? pd.nfx : 0;
     ix -= ix >= pd.nfx ? pd.nfx : 0;
     iy += iy < 0 ? pd.nfy : 0;
     iy -= iy >= pd.nfy ? pd.nfy : 0;
-    // FP32 arithmetic (the table is FP32; GB300's FP64 division would
-    // dominate this kernel)
-    const float xi = (float)pd.tab[ix * pd.nfy + iy].x, x = fabsf(xi);
-    const float A = __frcp_rn(omf + x);
-    pd.ext[e] = make_float4(xi, A, x * fmaf(3.f, x, omf) * (A * A * A), x);
+    const float xi = (float)pd.tab[ix * pd.nfy + iy].x;
+    const float A = __frcp_rn(omf + fabsf(xi));
+    return make_float2(A, xi * A);
+  };
+  if constexpr (PREC == TUFRG_BF16X3) {
+    const int half = (pd.n_ext + 1) / 2;
+#pragma unroll
+    for (int q = 0; q < kTablePerThread; ++q) {
+      const int j = e0 + q * kTableBlock;
+      if (j >= half) break;
+      const float2 a = entry(2 * j), b = entry(2 * j + 1), c = entry(2 * j + 2);
+      pd.ext[j] = make_float4(a.x, b.x, a.y, b.y);
+      pd.ext[half + j] = make_float4(b.x, c.x, b.y, c.y);
+    }
+  } else {
+    float2* t = reinterpret_cast<float2*>(pd.ext);
+#pragma unroll
+    for (int q = 0; q < kTablePerThread; ++q) {
+      const int e = e0 + q * kTableBlock;
+      if (e >= pd.n_ext) break;
+      t[e] = entry(e);
+    }
   }
 }
 
@@ -458,8 +501,12 @@ tufrg_status launch_loops_tc_multi(const MultiView& v, double* chi, cudaStream_t
 
 tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st, cudaEvent_t* ev) {
   if (v.tc_prec == TUFRG_FP64 || v.n_items == 0) return TUFRG_ERR_ARG;
-  scale_table_ext_kernel<<<v.total(kKindTable), kTableBlock, 0, st>>>(
-      v.d, v.dprefix(kKindTable), v.n);
+  if (v.tc_prec == TUFRG_BF16X3)
+    scale_table_ext_kernel<TUFRG_BF16X3><<<v.total(kKindTable), kTableBlock, 0, st>>>(
+        v.d, v.dprefix(kKindTable), v.n);
+  else
+    scale_table_ext_kernel<TUFRG_3XTF32><<<v.total(kKindTable), kTableBlock, 0, st>>>(
+        v.d, v.dprefix(kKindTable), v.n);
   TUFRG_CUDA(cudaGetLastError());
   TUFRG_CUDA(cudaMemsetAsync(v.d_counter, 0, sizeof(int), st));
   TcArgs a;

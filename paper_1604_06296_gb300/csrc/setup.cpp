@@ -185,11 +185,19 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
       kp.push_back(make_int2(ix, iy));
       kw.push_back(2.0);
     }
-  for (int ix : {0, hx})
+  for (int ix : {0, hx}) {
     for (int iy = 0; iy <= hy; ++iy) {
       kp.push_back(make_int2(ix, iy));
       kw.push_back((iy == 0 || iy == hy) ? 1.0 : 2.0);
     }
+    // columns of even length, so that loop points 2j, 2j + 1 are always
+    // neighbours iy, iy + 1 of one column (the BF16X3 producers read them as
+    // a pair): a padding point of weight 0
+    if ((hy + 1) % 2) {
+      kp.push_back(make_int2(ix, hy + 1));
+      kw.push_back(0.0);
+    }
+  }
   c->kdim = (int)kp.size();
 
   // parity-allowed pairs m <= n
@@ -348,7 +356,10 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->tc_hx = c->nfx / 4;
     c->tc_hy = c->nfy / 4;
     c->tc_wy = c->nfy + 2 * c->tc_hy;
-    TUFRG_CHECK(alloc(&c->d_ext, (size_t)(c->nfx + 2 * c->tc_hx) * c->tc_wy));
+    // (A, xi A) per point: BF16X3 as two float4 arrays of point pairs
+    // (2j, 2j + 1) and (2j + 1, 2j + 2), 3xTF32 as one float2 per point
+    const size_t n_ext = (size_t)(c->nfx + 2 * c->tc_hx) * c->tc_wy;
+    TUFRG_CHECK(alloc(&c->d_ext, 2 * ((n_ext + 1) / 2)));
   }
   if (c->p.precision != TUFRG_FP64 && !dl) {
     const bool bf16 = c->p.precision == TUFRG_BF16X3;
