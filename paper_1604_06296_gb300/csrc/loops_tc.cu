@@ -42,6 +42,7 @@ constexpr int kProducers = 16;      // producer warps
 constexpr int kThreads = 32 * (kProducers + 1);
 constexpr int kRowBytes = 128;      // one 128B-swizzle row per K-block
 constexpr int kWTile = kRows * kRowBytes;  // 16 KB
+constexpr int kDepth = 4;           // producer units in flight (table gathers ahead)
 
 template <int PREC>
 struct Prec;
@@ -87,26 +88,27 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 // Omega A = 1 - |u|:
 //   D = A_a A_b (5 Omega (A_a + A_b) - 3 - 2 Omega^2 (A_a^2 + A_a A_b + A_b^2))
 //   S = (H_a + H_b) / (x_a + x_b),  H = x (3x + Omega) A^3 = |u| (1 + 2|u|) A,
-//     = A_a A_b (H_a + H_b) / (|u_a| A_b + |u_b| A_a)   (1/Omega^2 at x_a = x_b = 0)
+//     = A_a A_b (H_a + H_b) / (|u_a| A_b + |u_b| A_a)
 // the particle-particle weight is S for propagators of one sign, D else, and
-// the particle-hole weight the other one.
+// the particle-hole weight the other one.  |u| is taken no smaller than
+// 1e-30: at x_a = x_b = 0 S is then A_a A_b = 1/Omega^2, its limit, and
+// elsewhere the floor is far below FP32 resolution.
 __device__ __forceinline__ void weights_au(const float2 Aa, const float2 usa, const float2 Ab,
-                                           const float2 usb, float om, float om2,
-                                           float inv_om2, float2& wpp, float2& wph) {
+                                           const float2 usb, float om, float om2, float2& wpp,
+                                           float2& wph) {
   const float2 sa = __fadd2_rn(Aa, Ab), pa = __fmul2_rn(Aa, Ab);
   const float2 t1 = __ffma2_rn(sa, sa, make_float2(-pa.x, -pa.y));
   const float2 t2 = __ffma2_rn(make_float2(5.f * om, 5.f * om), sa, make_float2(-3.f, -3.f));
   const float2 br = __ffma2_rn(make_float2(-2.f * om2, -2.f * om2), t1, t2);
   const float2 D = __fmul2_rn(pa, br);
-  const float2 ua = make_float2(fabsf(usa.x), fabsf(usa.y));
-  const float2 ub = make_float2(fabsf(usb.x), fabsf(usb.y));
+  const float2 ua = make_float2(fmaxf(fabsf(usa.x), 1e-30f), fmaxf(fabsf(usa.y), 1e-30f));
+  const float2 ub = make_float2(fmaxf(fabsf(usb.x), 1e-30f), fmaxf(fabsf(usb.y), 1e-30f));
   const float2 ha = __fmul2_rn(ua, __ffma2_rn(ua, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
   const float2 hb = __fmul2_rn(ub, __ffma2_rn(ub, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
   const float2 num = __fmul2_rn(pa, __ffma2_rn(ha, Aa, __fmul2_rn(hb, Ab)));
   const float2 den = __ffma2_rn(ua, Ab, __fmul2_rn(ub, Aa));
   const float2 sg = __fmul2_rn(usa, usb);
-  const float S0 = den.x > 0.f ? __fdividef(num.x, den.x) : inv_om2;
-  const float S1 = den.y > 0.f ? __fdividef(num.y, den.y) : inv_om2;
+  const float S0 = __fdividef(num.x, den.x), S1 = __fdividef(num.y, den.y);
   wpp = make_float2(sg.x > 0.f ? S0 : D.x, sg.y > 0.f ? S1 : D.y);
   wph = make_float2(sg.x > 0.f ? D.x : S0, sg.y > 0.f ? D.y : S1);
 }
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     __syncthreads();
     const int npad = pd.npad, nsets = pd.nsets;
     const double omd = pd.lam[0];
-    const float om = (float)omd, om2 = (float)(omd * omd), inv_om2 = (float)(1.0 / (omd * omd));
+    const float om = (float)omd, om2 = (float)(omd * omd);
 
     if (warp < kProducers) {
       // ---------------------------------------------------------- producers
@@ -220,6 +222,82 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       // this warp's rows with an l, in units of kUnitRows rows
       const int nrw = max(0, min(kRows / kProducers, (nvalid - warp + kProducers - 1) / kProducers));
       const int nunits = (nrw + kUnitRows - 1) / kUnitRows;
+      // The table gathers run kDepth - 1 units ahead of the arithmetic, in a
+      // ring of register buffers, across K-block boundaries too (the gathers
+      // of the next K-block's first units are issued while the last units of
+      // this one are computed).  Every warp gathers all kUnits units of a
+      // K-block (rows without an l read offset 0) and computes only those
+      // with an l (the accumulator rows of the others are never read).
+      using Buf = typename P::Buf;
+      auto load_unit = [&](int u, int pb, Buf& b) {
+        if constexpr (P::kPerLane == 2) {  // one row, two loop points: one pair each side
+          const int off = s_off[warp + kProducers * u];
+          const int qa = pb + off, qb = pb - off;  // of one parity
+          const float4* t = (qa & 1) ? ext_odd : ext;
+          b.v[0] = __ldg(t + (qa >> 1));
+          b.v[1] = __ldg(t + (qb >> 1));
+        } else {  // two rows, one loop point
+          const int off0 = s_off[warp + kProducers * (2 * u)];
+          const int off1 = s_off[warp + kProducers * (2 * u + 1)];
+          b.v[0] = __ldg(ext2 + (pb + off0));
+          b.v[1] = __ldg(ext2 + (pb - off0));
+          b.v[2] = __ldg(ext2 + (pb + off1));
+          b.v[3] = __ldg(ext2 + (pb - off1));
+        }
+      };
+      auto do_unit = [&](int u, uint32_t st, const Buf& b) {
+        float2 wpp, wph;
+        if constexpr (P::kPerLane == 2)
+          weights_au(make_float2(b.v[0].x, b.v[0].y), make_float2(b.v[0].z, b.v[0].w),
+                     make_float2(b.v[1].x, b.v[1].y), make_float2(b.v[1].z, b.v[1].w), om, om2,
+                     wpp, wph);
+        else
+          weights_au(make_float2(b.v[0].x, b.v[2].x), make_float2(b.v[0].y, b.v[2].y),
+                     make_float2(b.v[1].x, b.v[3].x), make_float2(b.v[1].y, b.v[3].y), om, om2,
+                     wpp, wph);
+        if constexpr (PREC == TUFRG_BF16X3) {
+          uint32_t v[4];
+          const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
+          const __nv_bfloat162 pl = __float22bfloat162_rn(
+              __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
+          const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
+          const __nv_bfloat162 hl = __float22bfloat162_rn(
+              __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
+          std::memcpy(&v[0], &ph, 4);
+          std::memcpy(&v[1], &pl, 4);
+          std::memcpy(&v[2], &hh, 4);
+          std::memcpy(&v[3], &hl, 4);
+          const uint32_t dst = st + (uint32_t)(warp + kProducers * u) * kRowBytes + swz;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t]) : "memory");
+        } else {
+          const float w[2][2] = {{wpp.x, wph.x}, {wpp.y, wph.y}};
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            uint32_t v[4];
+            v[0] = tf32_rna(w[j][0]);
+            v[1] = tf32_rna(w[j][0] - __uint_as_float(v[0]));
+            v[2] = tf32_rna(w[j][1]);
+            v[3] = tf32_rna(w[j][1] - __uint_as_float(v[2]));
+            const uint32_t dst = st + (uint32_t)(warp + kProducers * (2 * u + j)) * kRowBytes + swz;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t])
+                           : "memory");
+          }
+        }
+      };
+      static_assert(kUnits % kDepth == 0, "the ring continues across K-blocks");
+      Buf buf[kDepth];
+      // this lane's first loop point of a K-block as an offset into the halo
+      // table (padding points use a valid entry: their F is zero); BF16X3
+      // lanes take loop points 2 lane, 2 lane + 1 of the K-block, neighbours
+      // iy, iy + 1 of one column, i.e. table entries pb, pb + 1
+      int pb = cnt > 0 ? __ldg(pd.kbase + kb0 * KB + P::kPerLane * lane) : 0;
+#pragma unroll
+      for (int t = 0; t < kDepth - 1; ++t)
+        if (cnt > 0) load_unit(t, pb, buf[t]);
       for (int kb = 0; kb < cnt; ++kb) {
         const uint32_t gk = g + kb;
         const uint32_t s = gk & 1;
@@ -237,90 +315,18 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
                      (t ? Flo : Fhi) + (size_t)row * frow + fk + ch * 16);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        // this lane's first loop point as an offset into the halo table
-        // (padding points use a valid entry: their F is zero); BF16X3 lanes
-        // take loop points 2 lane, 2 lane + 1 of the K-block, neighbours iy,
-        // iy + 1 of one column, i.e. table entries pb, pb + 1
-        const int pb = __ldg(pd.kbase + k0 + P::kPerLane * lane);
-        // rolling pipeline over this warp's rows: the table gathers of the
-        // next unit are in flight while the current unit is computed (two
-        // register buffers); rows without an l are skipped (their
-        // accumulator rows are never read)
-        using Buf = typename P::Buf;
-        Buf bufA, bufB;
-        auto load_unit = [&](int u, Buf& b) {
-          if constexpr (P::kPerLane == 2) {  // one row, two loop points: one pair each side
-            const int off = s_off[warp + kProducers * u];
-            const int qa = pb + off, qb = pb - off;  // of one parity
-            const float4* t = (qa & 1) ? ext_odd : ext;
-            b.v[0] = __ldg(t + (qa >> 1));
-            b.v[1] = __ldg(t + (qb >> 1));
-          } else {  // two rows, one loop point
-            const int off0 = s_off[warp + kProducers * (2 * u)];
-            const int off1 = s_off[warp + kProducers * (2 * u + 1)];
-            b.v[0] = __ldg(ext2 + (pb + off0));
-            b.v[1] = __ldg(ext2 + (pb - off0));
-            b.v[2] = __ldg(ext2 + (pb + off1));
-            b.v[3] = __ldg(ext2 + (pb - off1));
-          }
-        };
-        auto do_unit = [&](int u, const Buf& b) {
-          float2 wpp, wph;
-          if constexpr (P::kPerLane == 2)
-            weights_au(make_float2(b.v[0].x, b.v[0].y), make_float2(b.v[0].z, b.v[0].w),
-                       make_float2(b.v[1].x, b.v[1].y), make_float2(b.v[1].z, b.v[1].w), om, om2,
-                       inv_om2, wpp, wph);
-          else
-            weights_au(make_float2(b.v[0].x, b.v[2].x), make_float2(b.v[0].y, b.v[2].y),
-                       make_float2(b.v[1].x, b.v[3].x), make_float2(b.v[1].y, b.v[3].y), om, om2,
-                       inv_om2, wpp, wph);
-          if constexpr (PREC == TUFRG_BF16X3) {
-            uint32_t v[4];
-            const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
-            const __nv_bfloat162 pl = __float22bfloat162_rn(
-                __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
-            const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
-            const __nv_bfloat162 hl = __float22bfloat162_rn(
-                __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
-            std::memcpy(&v[0], &ph, 4);
-            std::memcpy(&v[1], &pl, 4);
-            std::memcpy(&v[2], &hh, 4);
-            std::memcpy(&v[3], &hl, 4);
-            const uint32_t dst = st + (uint32_t)(warp + kProducers * u) * kRowBytes + swz;
+        const bool more = kb + 1 < cnt;
+        const int pbn = more ? __ldg(pd.kbase + k0 + KB + P::kPerLane * lane) : pb;
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-              asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t])
-                           : "memory");
-          } else {
-            const float w[2][2] = {{wpp.x, wph.x}, {wpp.y, wph.y}};
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              uint32_t v[4];
-              v[0] = tf32_rna(w[j][0]);
-              v[1] = tf32_rna(w[j][0] - __uint_as_float(v[0]));
-              v[2] = tf32_rna(w[j][1]);
-              v[3] = tf32_rna(w[j][1] - __uint_as_float(v[2]));
-              const uint32_t dst =
-                  st + (uint32_t)(warp + kProducers * (2 * u + j)) * kRowBytes + swz;
-#pragma unroll
-              for (int t = 0; t < 4; ++t)
-                asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t])
-                             : "memory");
-            }
-          }
-        };
-        if (nunits > 0) load_unit(0, bufA);
-#pragma unroll
-        for (int u = 0; u < kUnits; u += 2) {
-          if (u < nunits) {
-            if (u + 1 < nunits) load_unit(u + 1, bufB);
-            do_unit(u, bufA);
-          }
-          if (u + 1 < nunits) {
-            if (u + 2 < nunits) load_unit(u + 2, bufA);
-            do_unit(u + 1, bufB);
-          }
+        for (int u = 0; u < kUnits; ++u) {
+          const int t = u + kDepth - 1;  // unit gathered now, into the slot unit u - 1 freed
+          if (t < kUnits)
+            load_unit(t, pb, buf[t % kDepth]);
+          else if (more)
+            load_unit(t - kUnits, pbn, buf[t % kDepth]);
+          if (u < nunits) do_unit(u, st, buf[u % kDepth]);
         }
+        pb = pbn;
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         fence_proxy_async();
         __syncwarp();
