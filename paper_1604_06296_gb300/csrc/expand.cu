@@ -1,6 +1,7 @@
 // The two stages after a loop contraction, for every point of a view:
 // * split-K combination of the partial sums into the loops of the rows
-//   (FP64, fixed order);
+//   (fixed order; FP32 partials in compensated FP32 pairs, FP64 partials in
+//   FP64);
 // * loops of every transfer momentum from the loops of the rows (App. C): a
 //   row computed at l serves the l' = g l of its list, chi(g l) =
 //   R^g chi(l) R^g^T with f(g k) = R^g f(k).  The R^g of the C4v-adapted
@@ -50,29 +51,72 @@ __global__ void expand_rows_kernel(const PointDesc* __restrict__ pts,
 // scaled by -1/4 (pp) / +1/4 (ph) into rowres [2][nrow][npair].  Thread
 // (row lane, phase) sums the splits sp = phase (mod kPhases) -- independent
 // loads -- and the phases combine in a fixed order (deterministic).
+//
+// FP32 partials are summed as unevaluated pairs hi + lo of FP32 numbers
+// (error-free transformation of each addition, Knuth's TwoSum), which carry
+// ~44 significant bits -- far beyond the FP32 partials themselves -- at FP32
+// speed; only the result is converted to FP64 (FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this GPU).  FP64 partials are summed in
+// FP64.
 constexpr int kPhases = 32;
+
+// (a.x + a.y) + b as a renormalised pair (TwoSum of the high parts, the low
+// parts and the rounding error added, then a Fast2Sum)
+__device__ __forceinline__ float2 pair_add(float2 a, float b) {
+  const float s = a.x + b;
+  const float bv = s - a.x;
+  const float e = ((a.x - (s - bv)) + (b - bv)) + a.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bv = s - a.x;
+  const float e = ((a.x - (s - bv)) + (b.x - bv)) + (a.y + b.y);
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
 
 template <class T>
 __device__ __forceinline__ void reduce_rows(const T* __restrict__ partial, int P, int R,
                                             int ksplit, int npair, int nrow, int ch, int q,
                                             int row0, double* __restrict__ rowres) {
-  __shared__ double red[kPhases][33];
   const int lane = threadIdx.x & 31, phase = threadIdx.x >> 5;
   const int row = row0 + lane;
-  double s = 0.0;
-  if (row < nrow) {
-    const T* src = partial + ((size_t)ch * P + q) * R + row;
-    const size_t stride = (size_t)2 * P * R;
+  const T* src = partial + ((size_t)ch * P + q) * R + row;
+  const size_t stride = (size_t)2 * P * R;
+  const double scale = ch == 0 ? -0.25 : 0.25;
+  if constexpr (sizeof(T) == 4) {
+    __shared__ float2 red[kPhases][33];
+    float2 s = make_float2(0.f, 0.f);
+    if (row < nrow) {
 #pragma unroll 4
-    for (int sp = phase; sp < ksplit; sp += kPhases) s += (double)src[sp * stride];
-  }
-  red[phase][lane] = s;
-  __syncthreads();
-  if (phase == 0 && row < nrow) {
-    double t = red[0][lane];
+      for (int sp = phase; sp < ksplit; sp += kPhases) s = pair_add(s, src[sp * stride]);
+    }
+    red[phase][lane] = s;
+    __syncthreads();
+    if (phase == 0 && row < nrow) {
+      float2 t = red[0][lane];
 #pragma unroll
-    for (int k = 1; k < kPhases; ++k) t += red[k][lane];
-    rowres[((size_t)ch * nrow + row) * npair + q] = t * (ch == 0 ? -0.25 : 0.25);
+      for (int k = 1; k < kPhases; ++k) t = pair_add(t, red[k][lane]);
+      rowres[((size_t)ch * nrow + row) * npair + q] = ((double)t.x + (double)t.y) * scale;
+    }
+  } else {
+    __shared__ double red[kPhases][33];
+    double s = 0.0;
+    if (row < nrow) {
+#pragma unroll 4
+      for (int sp = phase; sp < ksplit; sp += kPhases) s += src[sp * stride];
+    }
+    red[phase][lane] = s;
+    __syncthreads();
+    if (phase == 0 && row < nrow) {
+      double t = red[0][lane];
+#pragma unroll
+      for (int k = 1; k < kPhases; ++k) t += red[k][lane];
+      rowres[((size_t)ch * nrow + row) * npair + q] = t * scale;
+    }
   }
 }
 

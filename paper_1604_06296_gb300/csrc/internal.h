@@ -91,6 +91,7 @@ struct PointDesc {
   int nfx, nfy, hx, hy, wy, n_ext, nkb, kpad_tc, nrow_pad, npad, nsets, ksplit;
   long long off_state, off_chi, off_bt, off_fkey, off_partial;
   const double4_32a* tab;
+  const float* xiext;  // [n_ext] xi over the halo table's points (FP32)
   float4* ext;
   const int* kbase;
   const int* rowoff;
@@ -194,6 +195,7 @@ struct tufrg_ctx {
   int tc_hx = 0, tc_hy = 0, tc_wy = 0;  // halo of the extended table, its row width
   float4* d_ext = nullptr;         // halo table over [(nfx+2hx)*wy] points, FP32 per scale:
                                    // A = 1/(Omega+|xi|), u = xi A (BF16X3: pair layout)
+  float* d_xiext = nullptr;        // [(nfx+2hx)*wy] xi at the halo table's points, FP32
   int* d_rowoff = nullptr;         // [nrow] sx * wy + sy
   int* d_kbase = nullptr;          // [tc_kpad] loop point offsets in the halo table
   unsigned char* d_Fhi = nullptr;  // [tc_npad][tc_kpad] high parts of F (bf16 or tf32)

@@ -6,8 +6,8 @@
 // operands split into high and low parts of a narrow type (BF16x3:
 // bf16 hi/lo, kind::f16; 3xTF32: tf32 hi/lo, kind::tf32) and three products
 // W_hi F_hi + W_lo F_hi + W_hi F_lo accumulated in FP32 in tensor memory;
-// the split-K partial sums of each CTA are combined in FP64 by a second
-// kernel.  The propagator operand W is generated in registers from the
+// the split-K partial sums of each CTA are combined (fixed order, compensated
+// FP32 pairs, FP64 result) by a second kernel.  The propagator operand W is generated in registers from the
 // per-scale FP32 table (A = 1/(Omega + |xi|), u = xi A, extended by a
 // wrap-around halo so p +- l/2 is one add from p) with the same closed-form
 // frequency integral as the FP64 path, and written
@@ -444,13 +444,7 @@ __global__ void __launch_bounds__(kTableBlock)
   const float omf = (float)pd.lam[0];
   const int e0 = (blockIdx.x - prefix[p]) * kTableBlock * kTablePerThread + threadIdx.x;
   auto entry = [&](int e) {
-    e = min(e, pd.n_ext - 1);
-    int ix = e / pd.wy - pd.hx, iy = e % pd.wy - pd.hy;
-    ix += ix < 0 ? pd.nfx : 0;
-    ix -= ix >= pd.nfx ? pd.nfx : 0;
-    iy += iy < 0 ? pd.nfy : 0;
-    iy -= iy >= pd.nfy ? pd.nfy : 0;
-    const float xi = (float)pd.tab[ix * pd.nfy + iy].x;
+    const float xi = __ldg(pd.xiext + min(e, pd.n_ext - 1));
     const float A = __frcp_rn(omf + fabsf(xi));
     return make_float2(A, xi * A);
   };

@@ -5,7 +5,8 @@
 // Work items are (point, tile of 128 l-rows, first K-block, K-blocks).  A
 // point's loop sum over its nkb K-blocks is cut into ksplit = ceil(nkb/kbps)
 // ranges; each range of each tile is one item whose FP32 partial sum is
-// combined with the others in FP64 (fixed order) by the reduction kernel.
+// combined with the others (fixed order, compensated FP32 pairs, FP64
+// result) by the reduction kernel.
 // The persistent CTAs take items from a queue ordered by estimated cost,
 // longest first, so the uneven points of a batch end together.
 #include <algorithm>
@@ -164,6 +165,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     off_fkey += (size_t)c->proj.nkeys;
     d.tab = c->d_tab;
     d.ext = c->d_ext;
+    d.xiext = c->d_xiext;
     d.kbase = c->d_kbase;
     d.rowoff = c->d_rowoff;
     d.Fhi = c->d_Fhi;

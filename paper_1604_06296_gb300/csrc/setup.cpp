@@ -360,6 +360,14 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     // (2j, 2j + 1) and (2j + 1, 2j + 2), 3xTF32 as one float2 per point
     const size_t n_ext = (size_t)(c->nfx + 2 * c->tc_hx) * c->tc_wy;
     TUFRG_CHECK(alloc(&c->d_ext, 2 * ((n_ext + 1) / 2)));
+    // the scale-independent xi at every point of the halo table (wrapped)
+    std::vector<float> xiext(n_ext);
+    for (size_t e = 0; e < n_ext; ++e) {
+      const int ix = imod((int)(e / c->tc_wy) - c->tc_hx, c->nfx);
+      const int iy = imod((int)(e % c->tc_wy) - c->tc_hy, c->nfy);
+      xiext[e] = (float)tab[(size_t)ix * c->nfy + iy].x;
+    }
+    TUFRG_CHECK(upload(&c->d_xiext, xiext, st));
   }
   if (c->p.precision != TUFRG_FP64 && !dl) {
     const bool bf16 = c->p.precision == TUFRG_BF16X3;
@@ -493,7 +501,7 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
 void free_device(tufrg_ctx* c) {
   free_flow(c);
   view_free(c->view);
-  void* own[] = {c->d_ext,     c->d_err,   c->d_tab, c->d_lambda, c->d_partial,
+  void* own[] = {c->d_ext,     c->d_xiext, c->d_err, c->d_tab, c->d_lambda, c->d_partial,
                  c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey};
   for (void* p : own)
     if (p) cudaFree(p);
