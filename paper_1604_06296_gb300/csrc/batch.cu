@@ -50,8 +50,7 @@ __global__ void bcombo_kernel(const double* __restrict__ y, double* __restrict__
   const long long b = seg[p].off + (long long)chunk * kChunk;
   const long long e = min(b + kChunk, seg[p].off + seg[p].len);
   for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
-    double acc = 0.0;
-    for (int j = 0; j < cb.nk; ++j) acc = fma(cb.a[j], cb.k[j][i], acc);
+    const double acc = combo_sum(cb, i);
     out[i] = y[i] + h * acc;
   }
 }
@@ -78,8 +77,7 @@ __global__ void berror_kernel(const double* __restrict__ y, const double* __rest
   unsigned long long emax = 0, ymax = 0;
   int bad = 0;
   for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
-    double acc = 0.0;
-    for (int j = 0; j < ce.nk; ++j) acc = fma(ce.a[j], ce.k[j][i], acc);
+    const double acc = combo_sum(ce, i);
     const double yn = ynew[i];
     const double sc = atol + rtol * fmax(fabs(y[i]), fabs(yn));
     const double r = fabs(h * acc) / sc;

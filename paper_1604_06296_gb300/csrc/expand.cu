@@ -58,7 +58,7 @@ __global__ void expand_rows_kernel(const PointDesc* __restrict__ pts,
 // speed; only the result is converted to FP64 (FP64 arithmetic runs at a
 // small fraction of the FP32 rate on this GPU).  FP64 partials are summed in
 // FP64.
-constexpr int kPhases = 32;
+constexpr int kPhases = 8;  // 256 threads: the whole grid resident in one wave
 
 // (a.x + a.y) + b as a renormalised pair (TwoSum of the high parts, the low
 // parts and the rounding error added, then a Fast2Sum)
@@ -92,7 +92,7 @@ __device__ __forceinline__ void reduce_rows(const T* __restrict__ partial, int P
     float2 s = make_float2(0.f, 0.f);
     if (row < nrow) {
 #pragma unroll 4
-      for (int sp = phase; sp < ksplit; sp += kPhases) s = pair_add(s, src[sp * stride]);
+      for (int sp = phase; sp < ksplit; sp += kPhases) s = pair_add(s, __ldg(src + sp * stride));
     }
     red[phase][lane] = s;
     __syncthreads();

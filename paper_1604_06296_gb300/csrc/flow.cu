@@ -37,8 +37,7 @@ __global__ void combo_kernel(const double* __restrict__ y, double* __restrict__ 
   }
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int j = 0; j < cb.nk; ++j) acc = fma(cb.a[j], cb.k[j][i], acc);
+    const double acc = combo_sum(cb, i);
     out[i] = y[i] + h * acc;
   }
 }
@@ -58,8 +57,7 @@ __global__ void error_kernel(const double* __restrict__ y, const double* __restr
   int bad = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int j = 0; j < e.nk; ++j) acc = fma(e.a[j], e.k[j][i], acc);
+    const double acc = combo_sum(e, i);
     const double yn = ynew[i];
     const double sc = atol + rtol * fmax(fabs(y[i]), fabs(yn));
     const double r = fabs(h * acc) / sc;

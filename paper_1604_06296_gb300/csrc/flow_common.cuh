@@ -59,6 +59,17 @@ struct Combo {
   double c;  // stage node: Lambda = exp(s + c h)
 };
 
+// sum_j a_j k_j[i] over the nk terms, in the order of j.  The loop has
+// constant bounds so that the kernel parameter is indexed with constants (a
+// runtime index makes every thread copy it to local memory first).
+__device__ __forceinline__ double combo_sum(const Combo& cb, size_t i) {
+  double acc = 0.0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j)
+    if (j < cb.nk) acc = fma(cb.a[j], cb.k[j][i], acc);
+  return acc;
+}
+
 // Step-size control after the error norm of an attempt (see the file header).
 __device__ __forceinline__ void control_update(FlowCtl* c) {
   const double err = __longlong_as_double((long long)c->err_u);

@@ -107,6 +107,8 @@ struct PointDesc {
   const int* pair;
   const double2* coef;
   const double2* phase;
+  const float2* coef_f;   // the same in FP32 (FP32-arithmetic kernels)
+  const float2* phase_f;
   const int4* keys;
   const int* row_ptr;
   const int4* terms;
@@ -183,6 +185,8 @@ struct tufrg_ctx {
   int* d_pair = nullptr;           // [mpad] m*nff+n (or -1)
   double2* d_coef = nullptr;       // [nff][nb] bond coefficients
   double2* d_phase = nullptr;      // [ncx + ncy][2*dmax+1] e^{i l d pi/(2nc)} tables
+  float2* d_coef_f = nullptr;      // d_coef, d_phase rounded to FP32
+  float2* d_phase_f = nullptr;
   int4* d_key = nullptr;           // [nkeys] (src, b3*nb+b4, dx, dy)
   int* d_row_ptr = nullptr;        // [3][nb*nb+1]
   int4* d_terms = nullptr;         // [total terms] (key, dx, dy, sign)

@@ -181,6 +181,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.pair = c->d_pair;
     d.coef = c->d_coef;
     d.phase = c->d_phase;
+    d.coef_f = c->d_coef_f;
+    d.phase_f = c->d_phase_f;
     d.keys = c->d_key;
     d.row_ptr = c->d_row_ptr;
     d.terms = c->d_terms;

@@ -46,6 +46,21 @@ __device__ __forceinline__ V to_c(double2 d) {
   return {(decltype(V::x))d.x, (decltype(V::x))d.y};
 }
 
+// bond coefficients and phase tables in the arithmetic type (FP32 copies
+// made at setup: no FP64 conversions in the FP32 kernels)
+__device__ __forceinline__ double2 coef_at(const PointDesc& pd, int e, double) {
+  return pd.coef[e];
+}
+__device__ __forceinline__ float2 coef_at(const PointDesc& pd, int e, float) {
+  return pd.coef_f[e];
+}
+__device__ __forceinline__ double2 phase_at(const PointDesc& pd, int e, double) {
+  return pd.phase[e];
+}
+__device__ __forceinline__ float2 phase_at(const PointDesc& pd, int e, float) {
+  return pd.phase_f[e];
+}
+
 constexpr int kDftWarps = 8;
 
 template <class T>
@@ -65,7 +80,7 @@ __global__ void to_bond_kernel(const PointDesc* __restrict__ pts, const int* __r
   T* Bs = reinterpret_cast<T*>(tmp + nff * nb);  // [nff][nff]
   const double* B = ybase + pd.off_state + ((size_t)ch * nl + l) * nff * nff;
   V* bt = btbase + pd.off_bt;
-  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = to_c<V>(pd.coef[e]);
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
   for (int e = threadIdx.x; e < nff * nff; e += blockDim.x) Bs[e] = (T)B[e];
   __syncthreads();
   // tmp[a][b4] = sum_b B[a][b] c_b(b4)
@@ -101,7 +116,7 @@ __global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __
   const int ncx = pd.ncx, ncy = pd.ncy, nd = pd.nd, nb = pd.nb, nl = pd.nl;
   extern __shared__ double2 sm2[];
   V* ph = reinterpret_cast<V*>(sm2);  // [(ncx + ncy) * nd]
-  for (int e = threadIdx.x; e < (ncx + ncy) * nd; e += blockDim.x) ph[e] = to_c<V>(pd.phase[e]);
+  for (int e = threadIdx.x; e < (ncx + ncy) * nd; e += blockDim.x) ph[e] = phase_at(pd, e, T());
   __syncthreads();
   const int key = (blockIdx.x - prefix[p]) * kDftWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -109,10 +124,12 @@ __global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __
   const int4 k = pd.keys[key];
   const V* src = btbase + pd.off_bt + ((size_t)k.x * nb * nb + k.y) * nl;
   V acc = {0, 0};
+  // unrolled so that several loads of Bt are in flight per lane
+#pragma unroll 6
   for (int l = lane; l < nl; l += 32) {
     const int ix = l / ncy, iy = l - ix * ncy;
     const V q = cmul(ph[ix * nd + k.z], ph[(ncx + iy) * nd + k.w]);
-    acc = cfma(q, src[l], acc);
+    acc = cfma(q, __ldg(src + l), acc);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -158,19 +175,19 @@ __global__ void __launch_bounds__(256)
     }
     return;
   }
-  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = to_c<V>(pd.coef[e]);
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
   for (int e = threadIdx.x; e < kContractL * nd; e += blockDim.x) {
     const int j = e / nd, d = e % nd;
     const int l = l0 + min(j, nlb - 1);
     const int ix = l / pd.ncy, iy = l - ix * pd.ncy;
-    qx[e] = to_c<V>(pd.phase[ix * nd + d]);
-    qy[e] = to_c<V>(pd.phase[(pd.ncx + iy) * nd + d]);
+    qx[e] = phase_at(pd, ix * nd + d, T());
+    qy[e] = phase_at(pd, (pd.ncx + iy) * nd + d, T());
   }
   __syncthreads();
   const int* rp = pd.row_ptr + (size_t)t * (nb * nb + 1);
   const int4* tm = pd.terms + pd.term_off[t];
   const V* fkey = fkbase + pd.off_fkey;
-  const T inv_nl = (T)(1.0 / nl);
+  const T inv_nl = T(1) / T(nl);
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
     V acc[kContractL];
 #pragma unroll

@@ -420,6 +420,8 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->proj = dp->proj;
     c->d_coef = dp->d_coef;
     c->d_phase = dp->d_phase;
+    c->d_coef_f = dp->d_coef_f;
+    c->d_phase_f = dp->d_phase_f;
     c->d_key = dp->d_key;
     c->d_row_ptr = dp->d_row_ptr;
     c->d_terms = dp->d_terms;
@@ -464,6 +466,10 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
   for (size_t i = 0; i < coef.size(); ++i)
     coef[i] = make_double2(B.coef[i].real(), B.coef[i].imag());
   TUFRG_CHECK(upload(&c->d_coef, coef, st));
+  std::vector<float2> coef_f(coef.size());
+  for (size_t i = 0; i < coef.size(); ++i)
+    coef_f[i] = make_float2((float)coef[i].x, (float)coef[i].y);
+  TUFRG_CHECK(upload(&c->d_coef_f, coef_f, st));
 
   build_proj(c);
   const ProjTables& P = c->proj;
@@ -479,6 +485,10 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
       }
   }
   TUFRG_CHECK(upload(&c->d_phase, phase, st));
+  std::vector<float2> phase_f(phase.size());
+  for (size_t i = 0; i < phase.size(); ++i)
+    phase_f[i] = make_float2((float)phase[i].x, (float)phase[i].y);
+  TUFRG_CHECK(upload(&c->d_phase_f, phase_f, st));
   std::vector<int4> keys(P.nkeys);
   for (int i = 0; i < P.nkeys; ++i)
     keys[i] = make_int4(P.key_src[i], P.key_b3[i] * nb + P.key_b4[i], P.key_dx[i] + P.dmax,
@@ -514,7 +524,8 @@ void free_device(tufrg_ctx* c) {
       if (p) cudaFree(p);
   }
   if (!c->borrowed_proj) {
-    void* proj[] = {c->d_coef, c->d_phase, c->d_key, c->d_row_ptr, c->d_terms};
+    void* proj[] = {c->d_coef,  c->d_phase,   c->d_key,  c->d_row_ptr,
+                    c->d_terms, c->d_coef_f, c->d_phase_f};
     for (void* p : proj)
       if (p) cudaFree(p);
   }
