@@ -7,10 +7,10 @@
 // bf16 hi/lo, kind::f16; 3xTF32: tf32 hi/lo, kind::tf32) and three products
 // W_hi F_hi + W_lo F_hi + W_hi F_lo accumulated in FP32 in tensor memory;
 // the split-K partial sums of each CTA are combined (fixed order, compensated
-// FP32 pairs, FP64 result) by a second kernel.  The propagator operand W is generated in registers from the
-// per-scale FP32 table (A = 1/(Omega + |xi|), u = xi A, extended by a
-// wrap-around halo so p +- l/2 is one add from p) with the same closed-form
-// frequency integral as the FP64 path, and written
+// FP32 pairs, FP64 result) by a second kernel.  The propagator operand W is
+// generated in registers from the per-scale FP32 table (A = 1/(Omega + |xi|),
+// u = xi A, extended by a wrap-around halo so p +- l/2 is one add from p)
+// with the same closed-form frequency integral as the FP64 path, and written
 // straight into the 128B-swizzled K-major shared-memory layout the MMA reads;
 // F (scale independent) is staged with cp.async.  Both channels share W's
 // table reads and divisions and have their own accumulator.
@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(gctrl + 48);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gctrl + 52);
   volatile int4* s_item = reinterpret_cast<volatile int4*>(gctrl + 64);
-  int* s_off = reinterpret_cast<int*>(gctrl + 128);
+  int* s_off = reinterpret_cast<int*>(gctrl + 128);     // 3xTF32: row offsets
+  int2* s_idx = reinterpret_cast<int2*>(gctrl + 128);   // BF16X3: row gather indices
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -201,8 +202,23 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     }
     const int row0 = tile * kRows;
     const int nvalid = min(kRows, pd.nrow - row0);  // rows of this tile with an l
-    for (int r = threadIdx.x; r < kRows; r += kThreads)
-      s_off[r] = r < nvalid ? pd.rowoff[row0 + r] : 0;
+    if constexpr (P::kPerLane == 2) {
+      // every lane's first loop point has the parity pib of the first loop
+      // point (neighbour pairs iy, iy + 1 with iy even, even row width), so
+      // the pair of p + l/2 is entry (pb >> 1) + a of the even or odd pair
+      // array, with a fixed per row: (idx_a, idx_b) into [even | odd] for
+      // p + l/2 and p - l/2
+      const int pib = pd.kbase[0] & 1, half = (pd.n_ext + 1) / 2;
+      for (int r = threadIdx.x; r < kRows; r += kThreads) {
+        const int off = r < nvalid ? pd.rowoff[row0 + r] : 0;
+        const int qa = pib + off, qb = pib - off;  // of one parity
+        const int odd = (qa & 1) * half;
+        s_idx[r] = make_int2((qa >> 1) + odd, (qb >> 1) + odd);
+      }
+    } else {
+      for (int r = threadIdx.x; r < kRows; r += kThreads)
+        s_off[r] = r < nvalid ? pd.rowoff[row0 + r] : 0;
+    }
     __syncthreads();
     const int npad = pd.npad, nsets = pd.nsets;
     const double omd = pd.lam[0];
@@ -211,9 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     if (warp < kProducers) {
       // ---------------------------------------------------------- producers
       // BF16X3: pairs (A_q, A_q+1, u_q, u_q+1) of even q at ext, of odd q at
-      // ext + (n_ext + 1) / 2; 3xTF32: (A_q, u_q) per point
+      // ext + (n_ext + 1) / 2, read at the row's s_idx; 3xTF32: (A_q, u_q)
+      // per point
       const float4* ext = pd.ext;
-      const float4* ext_odd = pd.ext + (pd.n_ext + 1) / 2;
       const float2* ext2 = reinterpret_cast<const float2*>(pd.ext);
       const unsigned char* Fhi = pd.Fhi;
       const unsigned char* Flo = pd.Flo;
@@ -231,11 +247,10 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       using Buf = typename P::Buf;
       auto load_unit = [&](int u, int pb, Buf& b) {
         if constexpr (P::kPerLane == 2) {  // one row, two loop points: one pair each side
-          const int off = s_off[warp + kProducers * u];
-          const int qa = pb + off, qb = pb - off;  // of one parity
-          const float4* t = (qa & 1) ? ext_odd : ext;
-          b.v[0] = __ldg(t + (qa >> 1));
-          b.v[1] = __ldg(t + (qb >> 1));
+          const int2 ix = s_idx[warp + kProducers * u];
+          const int hb = pb >> 1;
+          b.v[0] = __ldg(ext + (hb + ix.x));
+          b.v[1] = __ldg(ext + (hb + ix.y));
         } else {  // two rows, one loop point
           const int off0 = s_off[warp + kProducers * (2 * u)];
           const int off1 = s_off[warp + kProducers * (2 * u + 1)];
@@ -472,7 +487,7 @@ __global__ void __launch_bounds__(kTableBlock)
 }  // namespace
 
 size_t tc_smem_bytes(int npad) {
-  return 1024 + 2 * (4 * (size_t)kWTile + 2 * (size_t)npad * kRowBytes) + 128 + 4 * kRows;
+  return 1024 + 2 * (4 * (size_t)kWTile + 2 * (size_t)npad * kRowBytes) + 128 + 8 * kRows;
 }
 
 int tc_k_per_block(int prec) { return prec == TUFRG_BF16X3 ? kRowBytes / 2 : kRowBytes / 4; }
