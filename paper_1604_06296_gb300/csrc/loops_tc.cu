@@ -90,9 +90,9 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 //   S = (H_a + H_b) / (x_a + x_b),  H = x (3x + Omega) A^3 = |u| (1 + 2|u|) A,
 //     = A_a A_b (H_a + H_b) / (|u_a| A_b + |u_b| A_a)
 // the particle-particle weight is S for propagators of one sign, D else, and
-// the particle-hole weight the other one.  |u| is taken no smaller than
-// 1e-30: at x_a = x_b = 0 S is then A_a A_b = 1/Omega^2, its limit, and
-// elsewhere the floor is far below FP32 resolution.
+// the particle-hole weight the other one.  The table holds |u| no smaller
+// than 1e-30 (with the sign of xi): at x_a = x_b = 0 S is then A_a A_b =
+// 1/Omega^2, its limit, and elsewhere the floor is far below FP32 resolution.
 __device__ __forceinline__ void weights_au(const float2 Aa, const float2 usa, const float2 Ab,
                                            const float2 usb, float om, float om2, float2& wpp,
                                            float2& wph) {
@@ -101,8 +101,8 @@ __device__ __forceinline__ void weights_au(const float2 Aa, const float2 usa, co
   const float2 t2 = __ffma2_rn(make_float2(5.f * om, 5.f * om), sa, make_float2(-3.f, -3.f));
   const float2 br = __ffma2_rn(make_float2(-2.f * om2, -2.f * om2), t1, t2);
   const float2 D = __fmul2_rn(pa, br);
-  const float2 ua = make_float2(fmaxf(fabsf(usa.x), 1e-30f), fmaxf(fabsf(usa.y), 1e-30f));
-  const float2 ub = make_float2(fmaxf(fabsf(usb.x), 1e-30f), fmaxf(fabsf(usb.y), 1e-30f));
+  const float2 ua = make_float2(fabsf(usa.x), fabsf(usa.y));
+  const float2 ub = make_float2(fabsf(usb.x), fabsf(usb.y));
   const float2 ha = __fmul2_rn(ua, __ffma2_rn(ua, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
   const float2 hb = __fmul2_rn(ub, __ffma2_rn(ub, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
   const float2 num = __fmul2_rn(pa, __ffma2_rn(ha, Aa, __fmul2_rn(hb, Ab)));
@@ -282,10 +282,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
           std::memcpy(&v[1], &pl, 4);
           std::memcpy(&v[2], &hh, 4);
           std::memcpy(&v[3], &hl, 4);
-          const uint32_t dst = st + (uint32_t)(warp + kProducers * u) * kRowBytes + swz;
+          // plain stores (the compiler may interleave the units around them);
+          // the proxy fence before the stage's arrive orders them for the MMA
+          unsigned char* dst = gbase + (st - base) + (warp + kProducers * u) * kRowBytes + swz;
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t]) : "memory");
+          for (int t = 0; t < 4; ++t) *reinterpret_cast<uint32_t*>(dst + t * kWTile) = v[t];
         } else {
           const float w[2][2] = {{wpp.x, wph.x}, {wpp.y, wph.y}};
 #pragma unroll
@@ -295,11 +296,10 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
             v[1] = tf32_rna(w[j][0] - __uint_as_float(v[0]));
             v[2] = tf32_rna(w[j][1]);
             v[3] = tf32_rna(w[j][1] - __uint_as_float(v[2]));
-            const uint32_t dst = st + (uint32_t)(warp + kProducers * (2 * u + j)) * kRowBytes + swz;
+            unsigned char* dst =
+                gbase + (st - base) + (warp + kProducers * (2 * u + j)) * kRowBytes + swz;
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-              asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst + t * kWTile), "r"(v[t])
-                           : "memory");
+            for (int t = 0; t < 4; ++t) *reinterpret_cast<uint32_t*>(dst + t * kWTile) = v[t];
           }
         }
       };
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kTableBlock)
   auto entry = [&](int e) {
     const float xi = __ldg(pd.xiext + min(e, pd.n_ext - 1));
     const float A = __frcp_rn(omf + fabsf(xi));
-    return make_float2(A, xi * A);
+    return make_float2(A, copysignf(fmaxf(fabsf(xi * A), 1e-30f), xi));
   };
   if constexpr (PREC == TUFRG_BF16X3) {
     const int half = (pd.n_ext + 1) / 2;
