@@ -441,46 +441,43 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   }
 }
 
-constexpr int kTableBlock = 256, kTablePerThread = 4;
+constexpr int kTableBlock = 256;
 
 // Per-scale FP32 table (A, u) = (1/(Omega + |xi|), xi A) with a wrap-around
 // halo of hx, hy points on each side, so that p +- l/2 needs no wrapping
 // (FP32 arithmetic: the table is FP32, and GB300's FP64 division would
-// dominate this kernel).  BF16X3 layout: float4 (A_q, A_q+1, u_q, u_q+1) for
-// even q in the first half, for odd q in the second (the last entry
-// repeated past the end); 3xTF32: float2 (A_q, u_q).
+// dominate this kernel).  |u| is floored at 1e-30 (sign of xi kept).  BF16X3
+// layout: float4 (A_q, A_q+1, u_q, u_q+1) for even q in the first half, for
+// odd q in the second (the last entry repeated past the end); 3xTF32: float2
+// (A_q, u_q).  One thread per entry q, the neighbour's values by a shuffle.
+// Block 0 also resets the work-item counter of the contraction that follows.
 template <int PREC>
 __global__ void __launch_bounds__(kTableBlock)
     scale_table_ext_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
-                           int n) {
+                           int n, int* __restrict__ counter) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
   const int p = point_of(prefix, n, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
   const float omf = (float)pd.lam[0];
-  const int e0 = (blockIdx.x - prefix[p]) * kTableBlock * kTablePerThread + threadIdx.x;
+  const int n_ext = pd.n_ext;
+  const int q = (blockIdx.x - prefix[p]) * kTableBlock + threadIdx.x;
   auto entry = [&](int e) {
-    const float xi = __ldg(pd.xiext + min(e, pd.n_ext - 1));
+    const float xi = __ldg(pd.xiext + min(e, n_ext - 1));
     const float A = __frcp_rn(omf + fabsf(xi));
     return make_float2(A, copysignf(fmaxf(fabsf(xi * A), 1e-30f), xi));
   };
+  const float2 a = entry(q);
   if constexpr (PREC == TUFRG_BF16X3) {
-    const int half = (pd.n_ext + 1) / 2;
-#pragma unroll
-    for (int q = 0; q < kTablePerThread; ++q) {
-      const int j = e0 + q * kTableBlock;
-      if (j >= half) break;
-      const float2 a = entry(2 * j), b = entry(2 * j + 1), c = entry(2 * j + 2);
-      pd.ext[j] = make_float4(a.x, b.x, a.y, b.y);
-      pd.ext[half + j] = make_float4(b.x, c.x, b.y, c.y);
-    }
+    const int half = (n_ext + 1) / 2;
+    // the CTA's threads cover consecutive q, every warp a run of 32
+    float2 b;
+    b.x = __shfl_down_sync(0xffffffffu, a.x, 1);
+    b.y = __shfl_down_sync(0xffffffffu, a.y, 1);
+    if ((threadIdx.x & 31) == 31) b = entry(q + 1);
+    if (q < 2 * half) pd.ext[(q & 1) * half + (q >> 1)] = make_float4(a.x, b.x, a.y, b.y);
   } else {
-    float2* t = reinterpret_cast<float2*>(pd.ext);
-#pragma unroll
-    for (int q = 0; q < kTablePerThread; ++q) {
-      const int e = e0 + q * kTableBlock;
-      if (e >= pd.n_ext) break;
-      t[e] = entry(e);
-    }
+    if (q < n_ext) reinterpret_cast<float2*>(pd.ext)[q] = a;
   }
 }
 
@@ -492,10 +489,7 @@ size_t tc_smem_bytes(int npad) {
 
 int tc_k_per_block(int prec) { return prec == TUFRG_BF16X3 ? kRowBytes / 2 : kRowBytes / 4; }
 
-int table_ctas(int n_ext) {
-  const int per = kTableBlock * kTablePerThread;
-  return (n_ext + per - 1) / per;
-}
+int table_ctas(int n_ext) { return (n_ext + 1 + kTableBlock - 1) / kTableBlock; }
 
 tufrg_status prepare_loops_tc_multi(const MultiView& v) {
   const int smem = smem_optin();
@@ -518,12 +512,11 @@ tufrg_status launch_loops_tc_rows_multi(const MultiView& v, cudaStream_t st, cud
   if (v.tc_prec == TUFRG_FP64 || v.n_items == 0) return TUFRG_ERR_ARG;
   if (v.tc_prec == TUFRG_BF16X3)
     scale_table_ext_kernel<TUFRG_BF16X3><<<v.total(kKindTable), kTableBlock, 0, st>>>(
-        v.d, v.dprefix(kKindTable), v.n);
+        v.d, v.dprefix(kKindTable), v.n, v.d_counter);
   else
     scale_table_ext_kernel<TUFRG_3XTF32><<<v.total(kKindTable), kTableBlock, 0, st>>>(
-        v.d, v.dprefix(kKindTable), v.n);
+        v.d, v.dprefix(kKindTable), v.n, v.d_counter);
   TUFRG_CUDA(cudaGetLastError());
-  TUFRG_CUDA(cudaMemsetAsync(v.d_counter, 0, sizeof(int), st));
   TcArgs a;
   a.pts = v.d;
   a.items = v.d_items;
