@@ -309,11 +309,12 @@ def run_scan(args, rank, world, local):
                           "tables, split-K combination)",
                 "algorithmic_flop_per_launch": flops,
                 "peak_source": f"bf16 dense burst from {peak_src} (of measured)"}
-    # kernels of the library in the timed call: first stage (combination + 7
-    # right-hand-side kernels), per attempt 6 x 8 + error, control, accept,
-    # then 100 bisection rounds of 2 and 6 more for the crossing and argmax
+    # kernels of the library in the timed call: first stage (combination,
+    # stage scales + 7 right-hand-side kernels), per attempt 6 x 9 + error,
+    # control, accept, then 100 bisection rounds of 2 and 6 more for the
+    # crossing and argmax
     attempts = max(r["n_accepted"] + r["n_rejected"] for r in res)
-    launches = 8 + 51 * attempts + 2 * 100 + 6
+    launches = 9 + 57 * attempts + 2 * 100 + 6
     if rank == 0:
         sizes = sorted({(q["nc"], q["nf"], W.n_ff_for_shells(q["shells"])) for q in pts})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -656,10 +657,11 @@ def main():
         cpu = {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": sample}
 
-    # kernels of the library per timed step: 6 stages x (combination, per-scale
-    # table, loop contraction, split-K reduce, to_bond, dft_keys, contract,
-    # products gathering the row loops) + error + control + accept
-    launches_per_step = 6 * 8 + 3
+    # kernels of the library per timed step: 6 stages x (combination, stage
+    # scale, per-scale table, loop contraction, split-K reduce, to_bond,
+    # dft_keys, contract, products gathering the row loops) + error + control
+    # + accept
+    launches_per_step = 6 * 9 + 3
     if rank == 0:
         dtype = "f64" if args.precision == "fp64" else f"{args.precision} loops, f64 state"
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
