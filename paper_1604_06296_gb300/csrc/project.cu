@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(256)
   const int nlb = min(kContractL, nl - l0);  // l of this CTA
   extern __shared__ double2 sm2[];
   V* Tm = reinterpret_cast<V*>(sm2);       // [kContractL][nb][nb]
-  V* tmp = Tm + kContractL * nb * nb;      // [nb][nff]
-  V* cs = tmp + nb * nff;                  // [nff][nb]
+  V* tmp = Tm + kContractL * nb * nb;      // [kContractL][nb][nff]
+  V* cs = tmp + kContractL * nb * nff;     // [nff][nb]
   V* qx = cs + nff * nb;                   // [kContractL][nd]
   V* qy = qx + kContractL * nd;            // [kContractL][nd]
   const size_t n2 = (size_t)nff * nff;
@@ -204,27 +204,51 @@ __global__ void __launch_bounds__(256)
     for (int j = 0; j < kContractL; ++j) Tm[j * nb * nb + o] = {acc[j].x * inv_nl, acc[j].y * inv_nl};
   }
   __syncthreads();
-  for (int j = 0; j < nlb; ++j) {
-    const V* Tj = Tm + j * nb * nb;
-    // tmp[b1][n] = sum_b2 T[b1][b2] c_n(b2)
-    for (int e = threadIdx.x; e < nb * nff; e += blockDim.x) {
-      const int b1 = e / nff, n = e % nff;
-      V s = {0, 0};
-      for (int b2 = 0; b2 < nb; ++b2) s = cfma(Tj[b1 * nb + b2], cs[n * nb + b2], s);
-      tmp[e] = s;
+  // basis change for all l of the CTA at once: rows of cw lanes (lane n <
+  // nff is column n), 32 / cw rows per warp, the kContractL l of a row in
+  // one thread (independent chains, each coefficient read once)
+  const int cw = nff <= 16 ? 16 : 32, rpw = 32 / cw;
+  const int lane = threadIdx.x & 31, n = lane & (cw - 1);
+  const int r0 = (threadIdx.x >> 5) * rpw + lane / cw, rstep = (blockDim.x >> 5) * rpw;
+  // tmp[j][b1][n] = sum_b2 T_j[b1][b2] c_n(b2)
+  for (int b1 = r0; b1 < nb; b1 += rstep) {
+    if (n >= nff) continue;
+    V acc[kContractL];
+#pragma unroll
+    for (int jj = 0; jj < kContractL; ++jj) acc[jj] = {0, 0};
+    for (int b2 = 0; b2 < nb; ++b2) {
+      const V c = cs[n * nb + b2];
+#pragma unroll
+      for (int jj = 0; jj < kContractL; ++jj)
+        acc[jj] = cfma(Tm[jj * nb * nb + b1 * nb + b2], c, acc[jj]);
     }
-    __syncthreads();
-    const size_t base = pd.off_state + ((size_t)t * nl + l0 + j) * n2;
-    for (int e = threadIdx.x; e < (int)n2; e += blockDim.x) {
-      const int m = e / nff, n = e % nff;
-      T s = 0;
-      for (int b1 = 0; b1 < nb; ++b1) {
-        const V c1 = cs[m * nb + b1], t1 = tmp[b1 * nff + n];
-        s = fma(c1.x, t1.x, fma(-c1.y, t1.y, s));  // real part of c * tmp
+#pragma unroll
+    for (int jj = 0; jj < kContractL; ++jj) tmp[(jj * nb + b1) * nff + n] = acc[jj];
+  }
+  __syncthreads();
+  // V_mn = V0 + own + Re sum_b1 c_m(b1) tmp[b1][n]
+  const size_t base = pd.off_state + ((size_t)t * nl + l0) * n2;
+  for (int m = r0; m < nff; m += rstep) {
+    if (n >= nff) continue;
+    const int mn = m * nff + n;
+    double yv[kContractL];
+#pragma unroll
+    for (int jj = 0; jj < kContractL; ++jj) yv[jj] = jj < nlb ? ybase[base + jj * n2 + mn] : 0.0;
+    T acc[kContractL];
+#pragma unroll
+    for (int jj = 0; jj < kContractL; ++jj) acc[jj] = 0;
+    for (int b1 = 0; b1 < nb; ++b1) {
+      const V c1 = cs[m * nb + b1];
+#pragma unroll
+      for (int jj = 0; jj < kContractL; ++jj) {
+        const V t1 = tmp[(jj * nb + b1) * nff + n];
+        acc[jj] = fma(c1.x, t1.x, fma(-c1.y, t1.y, acc[jj]));  // real part of c * tmp
       }
-      vbase[base + e] = (e == 0 ? U : 0.0) + own_sign * ybase[base + e] + (double)s;
     }
-    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < kContractL; ++jj)
+      if (jj < nlb)
+        vbase[base + jj * n2 + mn] = (mn == 0 ? U : 0.0) + own_sign * yv[jj] + (double)acc[jj];
   }
 }
 
@@ -240,7 +264,7 @@ size_t dft_smem(const MultiView& v) {
 template <class T>
 size_t contract_smem(const MultiView& v) {
   return sizeof(typename C2<T>::type) *
-         ((size_t)kContractL * v.nb_max * v.nb_max + 2 * (size_t)v.nb_max * v.nff_max +
+         ((size_t)kContractL * v.nb_max * v.nb_max + (kContractL + 1) * (size_t)v.nb_max * v.nff_max +
           2 * (size_t)kContractL * v.nd_max);
 }
 
