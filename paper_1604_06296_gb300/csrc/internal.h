@@ -135,6 +135,7 @@ struct MultiView {
   std::vector<int> prefix;  // [kKinds][n + 1] first CTA of each point, per kind
   int* d_prefix = nullptr;
   int nff_max = 0, nb_max = 0, nd_max = 0, nc_sum_max = 0;
+  int nf_uniform = 0;  // Nff = Nb, the same for every point (else 0)
   // tensor-core loops: work items (point, l-tile, first K-block, K-blocks)
   // taken from a queue by persistent CTAs
   int tc_prec = TUFRG_FP64;  // TUFRG_FP64: no tensor-core loops

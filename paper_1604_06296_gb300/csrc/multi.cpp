@@ -203,6 +203,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     v.nb_max = std::max(v.nb_max, d.nb);
     v.nd_max = std::max(v.nd_max, d.nd);
     v.nc_sum_max = std::max(v.nc_sum_max, d.ncx + d.ncy);
+    const int nf = d.nff == d.nb ? d.nff : 0;
+    v.nf_uniform = i == 0 ? nf : (v.nf_uniform == nf ? nf : 0);
   }
   v.state_elems = off_state;
   v.chi_elems = off_chi;

@@ -28,7 +28,7 @@ __device__ __forceinline__ void matmul(const T* __restrict__ a, const T* __restr
 // chibase == nullptr: the loops of l are gathered from the loops of the row
 // serving l (rowres), chi(l)_mn = s_m s_n chi(row)_{p(m) p(n)} with the
 // signed permutation of the group element that maps the row's l to l.
-template <class T>
+template <class T, int NF>
 __global__ void products_kernel(const PointDesc* __restrict__ pts,
                                 const int* __restrict__ prefix, int np,
                                 const double* __restrict__ vbase,
@@ -38,7 +38,7 @@ __global__ void products_kernel(const PointDesc* __restrict__ pts,
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int nl = pd.nl, nff = pd.nff;
+  const int nl = pd.nl, nff = NF ? NF : pd.nff;
   const int l = blockIdx.x - prefix[p];
   extern __shared__ double smd[];
   T* sm = reinterpret_cast<T*>(smd);
@@ -106,25 +106,35 @@ __global__ void products_kernel(const PointDesc* __restrict__ pts,
 tufrg_status prepare_products_multi(const MultiView& v) {
   const int smem = smem_optin();
   if (sizeof(double) * 8 * v.nff_max * v.nff_max > (size_t)smem) return TUFRG_ERR_ARG;
-  TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<double>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  TUFRG_CUDA(cudaFuncSetAttribute(products_kernel<float>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  cudaError_t e = cudaSuccess;
+  for_each_nf([&](auto nf) {
+    constexpr int NF = decltype(nf)::value;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(products_kernel<double, NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(products_kernel<float, NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  TUFRG_CUDA(e);
   return TUFRG_OK;
 }
 
 tufrg_status launch_products_multi(const MultiView& v, int prec, const double* vin,
                                    const double* chi, double* dy, bool scaled, cudaStream_t st) {
   const int blocks = v.total(kKindProducts);
-  if (prec == TUFRG_FP64) {
-    const size_t smem = sizeof(double) * 8 * v.nff_max * v.nff_max;
-    products_kernel<double><<<blocks, 256, smem, st>>>(v.d, v.dprefix(kKindProducts), v.n, vin,
-                                                       chi, v.d_rowres, dy, scaled ? 1 : 0);
-  } else {
-    const size_t smem = sizeof(float) * 8 * v.nff_max * v.nff_max;
-    products_kernel<float><<<blocks, 256, smem, st>>>(v.d, v.dprefix(kKindProducts), v.n, vin,
-                                                      chi, v.d_rowres, dy, scaled ? 1 : 0);
-  }
+  with_nf(v.nf_uniform, [&](auto nf) {
+    constexpr int NF = decltype(nf)::value;
+    if (prec == TUFRG_FP64) {
+      const size_t smem = sizeof(double) * 8 * v.nff_max * v.nff_max;
+      products_kernel<double, NF><<<blocks, 256, smem, st>>>(
+          v.d, v.dprefix(kKindProducts), v.n, vin, chi, v.d_rowres, dy, scaled ? 1 : 0);
+    } else {
+      const size_t smem = sizeof(float) * 8 * v.nff_max * v.nff_max;
+      products_kernel<float, NF><<<blocks, 256, smem, st>>>(
+          v.d, v.dprefix(kKindProducts), v.n, vin, chi, v.d_rowres, dy, scaled ? 1 : 0);
+    }
+  });
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }

@@ -63,7 +63,7 @@ __device__ __forceinline__ float2 phase_at(const PointDesc& pd, int e, float) {
 
 constexpr int kDftWarps = 8;
 
-template <class T>
+template <class T, int NF>
 __global__ void to_bond_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
                                int np, const double* __restrict__ ybase,
                                typename C2<T>::type* __restrict__ btbase) {
@@ -71,7 +71,7 @@ __global__ void to_bond_kernel(const PointDesc* __restrict__ pts, const int* __r
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int nl = pd.nl, nff = pd.nff, nb = pd.nb;
+  const int nl = pd.nl, nff = NF ? NF : pd.nff, nb = NF ? NF : pd.nb;
   const int loc = blockIdx.x - prefix[p];
   const int l = loc % nl, ch = loc / nl;
   extern __shared__ double2 sm2[];
@@ -144,7 +144,7 @@ __global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __
 // and applied to all of them (only the phases e^{i l.Y} differ).
 constexpr int kContractL = 4;
 
-template <class T>
+template <class T, int NF>
 __global__ void __launch_bounds__(256)
     contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
                     const double* __restrict__ ybase,
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256)
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int nb = pd.nb, nff = pd.nff, nl = pd.nl, nd = pd.nd;
+  const int nb = NF ? NF : pd.nb, nff = NF ? NF : pd.nff, nl = pd.nl, nd = pd.nd;
   const int groups = (nl + kContractL - 1) / kContractL;
   const int loc = blockIdx.x - prefix[p];
   const int t = loc / groups, l0 = (loc % groups) * kContractL;
@@ -274,12 +274,19 @@ tufrg_status prepare_typed(const MultiView& v) {
   if ((int)bond_smem<T>(v) > smem || (int)dft_smem<T>(v) > smem ||
       (int)contract_smem<T>(v) > smem)
     return TUFRG_ERR_ARG;
-  TUFRG_CUDA(cudaFuncSetAttribute(to_bond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  smem));
   TUFRG_CUDA(cudaFuncSetAttribute(dft_keys_kernel<T>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  TUFRG_CUDA(cudaFuncSetAttribute(contract_kernel<T>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  cudaError_t e = cudaSuccess;
+  for_each_nf([&](auto nf) {
+    constexpr int NF = decltype(nf)::value;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(to_bond_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(contract_kernel<T, NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  TUFRG_CUDA(e);
   return TUFRG_OK;
 }
 
@@ -290,8 +297,10 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
   V* bt = reinterpret_cast<V*>(btv);
   V* fkey = reinterpret_cast<V*>(fkv);
   if (v.total(kKindBond) > 0) {
-    to_bond_kernel<T><<<v.total(kKindBond), 128, bond_smem<T>(v), st>>>(
-        v.d, v.dprefix(kKindBond), v.n, y, bt);
+    with_nf(v.nf_uniform, [&](auto nf) {
+      to_bond_kernel<T, decltype(nf)::value><<<v.total(kKindBond), 128, bond_smem<T>(v), st>>>(
+          v.d, v.dprefix(kKindBond), v.n, y, bt);
+    });
     TUFRG_CUDA(cudaGetLastError());
   }
   if (v.total(kKindDft) > 0) {
@@ -299,8 +308,11 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
         v.d, v.dprefix(kKindDft), v.n, bt, fkey);
     TUFRG_CUDA(cudaGetLastError());
   }
-  contract_kernel<T><<<v.total(kKindContract), 256, contract_smem<T>(v), st>>>(
-      v.d, v.dprefix(kKindContract), v.n, y, fkey, out);
+  with_nf(v.nf_uniform, [&](auto nf) {
+    contract_kernel<T, decltype(nf)::value>
+        <<<v.total(kKindContract), 256, contract_smem<T>(v), st>>>(
+            v.d, v.dprefix(kKindContract), v.n, y, fkey, out);
+  });
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }
