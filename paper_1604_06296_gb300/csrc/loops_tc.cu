@@ -18,10 +18,10 @@
 // Persistent CTAs (one per SM, 17 warps) take work items -- (point, tile of
 // 128 l-rows, range of K-blocks) of any number of points -- from a queue
 // ordered by cost.  Warps 0-15 produce the W tiles of a K-block (8 rows each,
-// lanes along k, table loads of several rows in flight) and stage F; warps
-// 0-7 then read the accumulators out (warp w reads the 32 TMEM lanes
-// 32 (w % 4).. of channel w / 4).  Warp 16 owns TMEM and one of its threads
-// issues the MMAs.  Two pipeline stages, mbarriers full/empty, whose phases
+// lanes along k, table loads of several rows in flight) and stage F, then
+// read the accumulators out (warp w reads the 32 TMEM lanes 32 (w % 4).. of
+// channel (w / 4) % 2, half of the columns).  Warp 16 owns TMEM and one of
+// its threads issues the MMAs.  Two pipeline stages, mbarriers full/empty, whose phases
 // run on across items; every wait is bounded in time and a timeout sets an
 // error word, stops the pipeline, drains the issued MMAs and frees TMEM.
 #include <cuda_bf16.h>
@@ -386,7 +386,9 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     }
 
     // ----------------------------------------------------------- epilogue
-    if (warp < 8) {  // warps 0-3: pp, 4-7: ph; warp w reads TMEM lanes 32 (w % 4)..
+    if (warp < kProducers) {
+      // all producer warps: warp w reads TMEM lanes 32 (w % 4).. of channel
+      // (w / 4) % 2, the 16-column blocks w / 8, w / 8 + 2, ...
       const bool ok = mbar_wait(bar_done, j & 1);
       if (!ok) {
         atomicOr(a.err, 4);
@@ -394,13 +396,13 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok && !*abort_flag) {
-        const int quad = warp & 3, ch = warp >> 2;
+        const int quad = warp & 3, ch = (warp >> 2) & 1, half = warp >> 3;
         const int row = quad * 32 + lane;
         const int sets = min(nsets, cnt);
         const int split = kb0 / a.kbps;
         float* out = a.partial + pd.off_partial +
                      (size_t)(split * 2 + ch) * npad * pd.nrow_pad + row0 + row;
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+        for (int c0 = 16 * half; c0 < npad; c0 += 32) {
           float acc[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) acc[q] = 0.f;
