@@ -100,6 +100,7 @@ struct PointDesc {
   const int* rowimg_ptr;  // [nrow + 1] CSR of the (l, g) each row serves
   const int2* rowimg;
   const int2* lrow;       // [nl] (row, g) serving each l
+  const int* lgather;     // [nl][nff][nff] signed row-loop index + 1 of each entry (0: none)
   const int* pairidx;     // [nff][nff] pair index of {m, n}, -1 if forbidden
   const int* symperm;     // [8][nff] signed permutations R^g
   const int* symsign;
@@ -180,6 +181,8 @@ struct tufrg_ctx {
   int* d_rowimg_ptr = nullptr;     // [nrow + 1] CSR over d_rowimg
   int2* d_rowimg = nullptr;        // [nl] (l, g): chi(l) = R^g chi(row) R^g^T
   int2* d_lrow = nullptr;          // [nl] (row, g) serving each l
+  int* d_lgather = nullptr;        // [nl][nff][nff] +-(row npair + pair + 1): entry (m, n)
+                                   // of l's loops in the row loops, signed; 0: forbidden
   int* d_pairidx = nullptr;        // [nff][nff] index of the pair {m, n} (-1: forbidden)
   int* d_symperm = nullptr;        // [8][nff] R^g as signed permutations:
   int* d_symsign = nullptr;        //   (R^g chi R^g^T)_mn = s_m s_n chi_{p(m) p(n)}

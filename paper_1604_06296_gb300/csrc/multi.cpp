@@ -173,6 +173,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.rowimg_ptr = c->d_rowimg_ptr;
     d.rowimg = c->d_rowimg;
     d.lrow = c->d_lrow;
+    d.lgather = c->d_lgather;
     d.pairidx = c->d_pairidx;
     d.symperm = c->d_symperm;
     d.symsign = c->d_symsign;

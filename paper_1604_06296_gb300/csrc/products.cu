@@ -67,17 +67,16 @@ __global__ void products_kernel(const PointDesc* __restrict__ pts,
       Xh[e] = (T)chi[chan + off + e];
     }
   } else {
-    const int2 rg = pd.lrow[l];
-    const int* perm = pd.symperm + rg.y * nff;
-    const int* sign = pd.symsign + rg.y * nff;
-    const double* rp = rowres + pd.off_rowres + (size_t)rg.x * pd.npair;
+    // one gather table entry per (m, n): the signed index into the row loops
+    const int* gi = pd.lgather + (size_t)l * n2;
+    const double* rp = rowres + pd.off_rowres;
     const size_t ch1 = (size_t)pd.nrow * pd.npair;
     for (int e = threadIdx.x; e < n2; e += blockDim.x) {
-      const int m = e / nff, n = e % nff;
-      const int q = pd.pairidx[perm[m] * nff + perm[n]];
-      const T sg = (T)(sign[m] * sign[n]);
-      Xp[e] = q >= 0 ? sg * (T)rp[q] : (T)0;
-      Xh[e] = q >= 0 ? sg * (T)rp[ch1 + q] : (T)0;
+      const int v = __ldg(gi + e);
+      const int q = abs(v) - 1;
+      const T sg = v > 0 ? (T)1 : (T)-1;
+      Xp[e] = v != 0 ? sg * (T)rp[q] : (T)0;
+      Xh[e] = v != 0 ? sg * (T)rp[ch1 + q] : (T)0;
     }
   }
   __syncthreads();

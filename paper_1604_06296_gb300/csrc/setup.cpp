@@ -288,6 +288,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_rowimg_ptr = dl->d_rowimg_ptr;
     c->d_rowimg = dl->d_rowimg;
     c->d_lrow = dl->d_lrow;
+    c->d_lgather = dl->d_lgather;
     c->d_symperm = dl->d_symperm;
     c->d_symsign = dl->d_symsign;
   }
@@ -410,6 +411,21 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CHECK(upload(&c->d_rowimg_ptr, rowimg_ptr, st));
     TUFRG_CHECK(upload(&c->d_rowimg, rowimg, st));
     TUFRG_CHECK(upload(&c->d_lrow, lrow, st));
+    // entry (m, n) of the loops of l = s_m s_n chi(row)_{p(m) p(n)} for the
+    // row serving l and its group element's signed permutation
+    std::vector<int> lgather((size_t)c->nl * nff * nff, 0);
+    for (int l = 0; l < c->nl; ++l) {
+      const int r = lrow[l].x, g = lrow[l].y;
+      for (int m = 0; m < nff; ++m)
+        for (int n = 0; n < nff; ++n) {
+          const int q = pairidx[(size_t)symperm[(size_t)g * nff + m] * nff +
+                                symperm[(size_t)g * nff + n]];
+          if (q < 0) continue;
+          const int sg = symsign[(size_t)g * nff + m] * symsign[(size_t)g * nff + n];
+          lgather[((size_t)l * nff + m) * nff + n] = sg * (r * c->npair + q + 1);
+        }
+    }
+    TUFRG_CHECK(upload(&c->d_lgather, lgather, st));
     TUFRG_CHECK(upload(&c->d_symperm, symperm, st));
     TUFRG_CHECK(upload(&c->d_symsign, symsign, st));
   }
@@ -518,6 +534,7 @@ void free_device(tufrg_ctx* c) {
   if (!c->borrowed_loops) {
     void* loops[] = {c->d_rowoff,  c->d_kbase,     c->d_Fhi,    c->d_Flo,     c->d_rowimg_ptr,
                      c->d_rowimg,  c->d_lrow,      c->d_symperm, c->d_symsign, c->d_kidx,
+                     c->d_lgather,
                      c->d_F,       c->d_pairidx,
                      c->d_shift,   c->d_pair};
     for (void* p : loops)
