@@ -12,17 +12,6 @@
 namespace tufrg {
 namespace {
 
-template <class T>
-__device__ __forceinline__ void matmul(const T* __restrict__ a, const T* __restrict__ b,
-                                       T* __restrict__ c, int n) {
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    T s = 0;
-    for (int k = 0; k < n; ++k) s = fma(a[i * n + k], b[k * n + j], s);
-    c[e] = s;
-  }
-}
-
 // arithmetic in T (FP64, or FP32 for the mixed-precision contexts); inputs
 // and the derivative are FP64; dy is multiplied by lam[1] when scaled
 // chibase == nullptr: the loops of l are gathered from the loops of the row
@@ -80,9 +69,15 @@ __global__ void products_kernel(const PointDesc* __restrict__ pts,
     }
   }
   __syncthreads();
-  matmul(Xp, VP, T1, nff);  // chi^pp V^P
-  matmul(Xh, VC, T2, nff);  // chi^ph V^C
-  matmul(Xh, VD, T3, nff);  // chi^ph V^D
+  // chi^pp V^P, chi^ph V^C, chi^ph V^D as one loop over their 3 Nff^2 entries
+  for (int e = threadIdx.x; e < 3 * n2; e += blockDim.x) {
+    const int w = e / n2, ij = e - w * n2, i = ij / nff, j = ij - i * nff;
+    const T* a = (w == 0 ? Xp : Xh) + i * nff;
+    const T* b = (w == 0 ? VP : (w == 1 ? VC : VD)) + j;
+    T s = 0;
+    for (int k = 0; k < nff; ++k) s = fma(a[k], b[k * nff], s);
+    (w == 0 ? T1 : (w == 1 ? T2 : T3))[ij] = s;
+  }
   __syncthreads();
   const double sc = scaled ? pd.lam[1] : 1.0;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
