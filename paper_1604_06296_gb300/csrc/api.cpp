@@ -187,12 +187,53 @@ tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi
                                       (cudaStream_t)stream);
 }
 
+namespace {
+
+// The right-hand side as a graph on the context's stream: captured for the
+// (y, dy) pair of the call, reused while the pair repeats.
+tufrg_status rhs_graph(tufrg_ctx* c, const double* y_dev, double* dy_dev) {
+  if (c->rhs_graph && c->rhs_y == y_dev && c->rhs_dy == dy_dev) return TUFRG_OK;
+  if (c->rhs_graph) cudaGraphExecDestroy(c->rhs_graph);
+  c->rhs_graph = nullptr;
+  cudaGraph_t g = nullptr;
+  TUFRG_CUDA(cudaStreamBeginCapture(c->fstream, cudaStreamCaptureModeThreadLocal));
+  const tufrg_status s = tufrg::rhs_device(c, c->p.precision, y_dev, dy_dev, false, c->fstream);
+  cudaError_t e = cudaStreamEndCapture(c->fstream, &g);
+  if (s != TUFRG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  TUFRG_CUDA(e);
+  e = cudaGraphInstantiate(&c->rhs_graph, g, 0);
+  cudaGraphDestroy(g);
+  TUFRG_CUDA(e);
+  c->rhs_y = y_dev;
+  c->rhs_dy = dy_dev;
+  return TUFRG_OK;
+}
+
+}  // namespace
+
 tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double* dy_dev,
                        void* stream) {
   if (!c || !y_dev || !dy_dev || y_dev == dy_dev || !finite_pos(lambda)) return TUFRG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
-  return tufrg::rhs_device(c, c->p.precision, y_dev, dy_dev, false, st);
+  if (!c->fstream) {
+    TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
+    return tufrg::rhs_device(c, c->p.precision, y_dev, dy_dev, false, st);
+  }
+  TUFRG_CUDA(cudaEventRecord(c->ev_in, st));
+  TUFRG_CUDA(cudaStreamWaitEvent(c->fstream, c->ev_in, 0));
+  tufrg_status s = rhs_graph(c, y_dev, dy_dev);
+  if (s == TUFRG_OK) s = tufrg::launch_set_scalar(c->d_lambda, lambda, c->fstream);
+  if (s == TUFRG_OK) {
+    const cudaError_t e = cudaGraphLaunch(c->rhs_graph, c->fstream);
+    if (e != cudaSuccess) s = tufrg_cuda_fail_at(e, __FILE__, __LINE__);
+  }
+  if (cudaEventRecord(c->ev_out, c->fstream) != cudaSuccess ||
+      cudaStreamWaitEvent(st, c->ev_out, 0) != cudaSuccess)
+    return s == TUFRG_OK ? TUFRG_ERR_CUDA : s;
+  return s;
 }
 
 namespace {

@@ -230,6 +230,11 @@ struct tufrg_ctx {
   double sur_tol = 1e-3;           // largest accepted relative error of its loops
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // tufrg_rhs: the right-hand side captured as a graph for the last (y, dy)
+  // pair it was called with (launched on fstream after the scale is set)
+  cudaGraphExec_t rhs_graph = nullptr;
+  const double* rhs_y = nullptr;
+  double* rhs_dy = nullptr;
   // the projections of a right-hand side run on their own stream, beside the
   // loop contraction (fork after the stage combination, join before the
   // products; branches of the captured flow graphs)
@@ -259,6 +264,8 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
 tufrg_status create_context(const tufrg_params* p, cudaStream_t st, const SetupShare& share,
                             tufrg_ctx** out);
 // drops the captured flow graphs (after a change of the tensor-core work items)
+// drops the captured graphs (flow attempts, tufrg_rhs) after a change of
+// the launch configuration (autotuning, surrogate)
 void flow_drop_graphs(tufrg_ctx* c);
 
 // loop "precision" of a flow whose loops the attached surrogate gives

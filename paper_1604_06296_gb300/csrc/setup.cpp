@@ -525,6 +525,7 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
 }
 
 void free_device(tufrg_ctx* c) {
+  flow_drop_graphs(c);
   free_flow(c);
   view_free(c->view);
   void* own[] = {c->d_ext,     c->d_xiext, c->d_err, c->d_tab, c->d_lambda, c->d_partial,
