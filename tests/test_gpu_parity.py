@@ -104,6 +104,24 @@ def test_rhs(torch, case, feedback):
     assert rel(got, orhs.rhs(p, 0.7, y)) < RTOL
 
 
+@pytest.mark.parametrize("precision,bar", [("fp64", RTOL), ("bf16x3", 1e-5)])
+def test_rhs_repeated_with_alternating_buffers(torch, precision, bar):
+    """tufrg_rhs replays a graph captured for its (y, dy) pair: alternating
+    pairs, new scales and a flow in between all give the oracle's RHS."""
+    s, p = make("ragged", torch, precision=precision)
+    ys = [W.random_state(30 + i, p.nl, p.nff, 0.5) for i in range(2)]
+    yd = [dev(torch, y) for y in ys]
+    outs = [s.empty(3), s.empty(3)]
+    calls = [(0, 0.7), (1, 0.3), (0, 0.3), (1, 2.0), (0, 0.7)]
+    for i, lam in calls:
+        got = s.rhs(lam, yd[i], out=outs[i]).cpu().numpy()
+        assert rel(got, orhs.rhs(p, lam, ys[i])) < bar
+    s.flow(threshold=50.0, rtol=1e-6, atol=1e-8, h0=0.05, max_steps=5)
+    got = s.rhs(0.5, yd[1], out=outs[1]).cpu().numpy()
+    assert rel(got, orhs.rhs(p, 0.5, ys[1])) < bar
+    s.close()
+
+
 def test_loops_production_size_sampled(torch):
     c = W.config("cfg2")
     case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.35, mu=-1.4, U=3.0)
