@@ -50,6 +50,30 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def aggregate_ranks(pg, device_s, units, device="cuda"):
+    """Weak scaling: each rank times its own independent points; the job's
+    time is the slowest rank's and its units are the sum over ranks (the only
+    collective).  Returns (max seconds, total units)."""
+    if pg is None:
+        return device_s, float(units)
+    import torch
+    t = torch.tensor([device_s, float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
+def rank_tprime(rank):
+    """t' of the production point a rank runs (ranks cycle over the three)."""
+    return W.CFG2_TPRIME[(1 + rank) % len(W.CFG2_TPRIME)]
+
+
+def rank_scan_seed(rank):
+    """Seed of the scan points of a rank (disjoint draws per rank)."""
+    return W.BATCH_SEED + rank
+
+
 # --------------------------------------------------------------------------
 # clocks sampled during the timed region
 class ClockSampler:
@@ -252,7 +276,7 @@ def run_scan(args, rank, world, local):
         dist.init_process_group("nccl")
         pg = dist
     c = W.config("cfg1")
-    pts = scan_points(args.points, W.BATCH_SEED + rank)
+    pts = scan_points(args.points, rank_scan_seed(rank))
     t0 = time.perf_counter()
     batch = tufrg.Batch(pts, precision=args.precision)
     setup_s = time.perf_counter() - t0
@@ -279,12 +303,7 @@ def run_scan(args, rank, world, local):
     clk = clocks.stop()
     dev_s = e0.elapsed_time(e1) / 1e3
     rhs = float(sum(r["n_rhs"] for r in res))
-    if pg:
-        t = torch.tensor([dev_s, rhs], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        dev_s, rhs = float(tmax[0]), float(t[1])
+    dev_s, rhs = aggregate_ranks(pg, dev_s, rhs)
     value = rhs / dev_s
     # dominant kernel: the persistent loop contraction over all points (CUDA
     # events inside the library around its launch; inputs far larger than L2)
@@ -481,7 +500,7 @@ def main():
         pg = dist
 
     c = W.config(WORKLOAD)
-    tp = W.CFG2_TPRIME[(1 + rank) % len(W.CFG2_TPRIME)]
+    tp = rank_tprime(rank)
     solver = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"],
                           c["nf"], precision=args.precision)
     flow_kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
@@ -527,14 +546,7 @@ def main():
     clk = clocks.stop()
 
     device_s = sum(step_ms) / 1e3
-    if pg:
-        t = torch.tensor([device_s, float(rhs_count)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        device_s_max, total_rhs = float(tmax[0]), float(t[1])
-    else:
-        device_s_max, total_rhs = device_s, float(rhs_count)
+    device_s_max, total_rhs = aggregate_ranks(pg, device_s, rhs_count)
     value = total_rhs / device_s_max
 
     # dominant kernel: the loop contraction, timed by CUDA events recorded
