@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "tc_util.cuh"
@@ -330,17 +331,26 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
                      (t ? Flo : Fhi) + (size_t)row * frow + fk + ch * 16);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        const bool more = kb + 1 < cnt;
-        const int pbn = more ? __ldg(pd.kbase + k0 + KB + P::kPerLane * lane) : pb;
+        // (after the item's last K-block the ring gathers this one's first
+        // units again: valid addresses, no branch)
+        const int pbn = kb + 1 < cnt ? __ldg(pd.kbase + k0 + KB + P::kPerLane * lane) : pb;
+        // warps with all kUnits units run the K-block without a branch, so
+        // the compiler can interleave the units' arithmetic
+        auto kblock = [&](auto full) {
 #pragma unroll
-        for (int u = 0; u < kUnits; ++u) {
-          const int t = u + kDepth - 1;  // unit gathered now, into the slot unit u - 1 freed
-          if (t < kUnits)
-            load_unit(t, pb, buf[t % kDepth]);
-          else if (more)
-            load_unit(t - kUnits, pbn, buf[t % kDepth]);
-          if (u < nunits) do_unit(u, st, buf[u % kDepth]);
-        }
+          for (int u = 0; u < kUnits; ++u) {
+            const int t = u + kDepth - 1;  // unit gathered now, into the slot unit u - 1 freed
+            if (t < kUnits)
+              load_unit(t, pb, buf[t % kDepth]);
+            else
+              load_unit(t - kUnits, pbn, buf[t % kDepth]);
+            if (decltype(full)::value || u < nunits) do_unit(u, st, buf[u % kDepth]);
+          }
+        };
+        if (nunits == kUnits)
+          kblock(std::true_type{});
+        else
+          kblock(std::false_type{});
         pb = pbn;
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         fence_proxy_async();
