@@ -249,6 +249,15 @@ tufrg_status tufrg_loops_noalloc(const tufrg_params* p, double lambda, double* c
 tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x,
                                   int32_t nf_y, double* mu_out);
 
+/* Diagnostic of the failure path (no counterpart in the paper): enqueues
+ * one bounded device wait of wait_us microseconds (1..100000) on a barrier
+ * that nothing completes.  It runs out, sets the context's error word the
+ * way a stalled tensor-core pipeline would, and returns; the next
+ * tufrg_check then reports TUFRG_ERR_TIMEOUT and clears it, and the context
+ * stays usable.  TUFRG_ERR_ARG for a null context, one without a workspace
+ * or wait_us out of range. */
+tufrg_status tufrg_selftest_wait(tufrg_ctx* ctx, int32_t wait_us, void* cuda_stream);
+
 /* Synchronises the stream and reports device-side failures of earlier
  * asynchronous calls on this context: TUFRG_ERR_TIMEOUT if a bounded wait
  * inside a kernel (tensor-core pipeline barriers) gave up; the flag is then

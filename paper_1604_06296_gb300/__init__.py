@@ -156,6 +156,14 @@ class Solver:
         """Tile autotuning of the tensor-core loops; returns the timing report."""
         return _abi.tufrg_autotune(self.ctx, float(lam), _stream()).as_dict()
 
+    def check(self):
+        """Raise TufrgError if a device wait gave up since the last check."""
+        _abi.tufrg_check(self.ctx, _stream())
+
+    def selftest_wait(self, wait_us=20000):
+        """Launch one bounded wait that nothing completes (diagnostic)."""
+        _abi.tufrg_selftest_wait(self.ctx, int(wait_us), _stream())
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             tufrg_destroy(self.ctx)

@@ -89,6 +89,7 @@ SIGNATURES = {
     "tufrg_mu_for_density": ([c_double, c_double, c_double, c_int32, c_int32,
                               POINTER(c_double)], c_int32),
     "tufrg_check": ([c_void_p, c_void_p], c_int32),
+    "tufrg_selftest_wait": ([c_void_p, c_int32, c_void_p], c_int32),
     "tufrg_autotune": ([c_void_p, c_double, POINTER(tufrg_tune_report), c_void_p], c_int32),
     "tufrg_batch_setup": ([c_int32, POINTER(tufrg_params), c_void_p, POINTER(c_void_p)],
                           c_int32),
@@ -246,6 +247,10 @@ def tufrg_mu_for_density(t: float, tp: float, n: float, nf_x: int, nf_y: int) ->
 
 def tufrg_check(ctx, stream: int = 0) -> None:
     _check(lib().tufrg_check(ctx, _dptr(stream)), "tufrg_check")
+
+
+def tufrg_selftest_wait(ctx, wait_us: int, stream: int = 0) -> None:
+    _check(lib().tufrg_selftest_wait(ctx, int(wait_us), _dptr(stream)), "tufrg_selftest_wait")
 
 
 def tufrg_status_string(status: int) -> str:

@@ -40,15 +40,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for the phase of the given parity; gives up after kWaitNs.
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Waits for the phase of the given parity; gives up after limit_ns.
+__device__ inline bool mbar_wait_for(uint32_t bar, uint32_t parity,
+                                     unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (;;) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
+}
+
+// Waits for the phase of the given parity; gives up after kWaitNs.
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, kWaitNs);
 }
 
 __device__ __forceinline__ void fence_proxy_async() {

@@ -201,6 +201,26 @@ def test_ladder_flow_closed_form_on_gpu(torch):
     assert np.abs(rest).max() == 0.0
 
 
+def test_bounded_wait_times_out_and_context_stays_usable(torch):
+    """A device wait on an mbarrier that nothing arrives on gives up after
+    its limit, records the error word, and leaves the context usable."""
+    from paper_1604_06296_gb300 import TufrgError
+    s, p = make("cfg1", torch)
+    s.check()
+    s.selftest_wait(20000)
+    with pytest.raises(TufrgError) as e:
+        s.check()
+    assert e.value.status == -5
+    s.check()  # the error word was cleared
+    y = W.random_state(41, p.nl, p.nff, 0.5)
+    got = s.rhs(0.7, dev(torch, y)).cpu().numpy()
+    assert rel(got, orhs.rhs(p, 0.7, y)) < RTOL
+    s.check()
+    with pytest.raises(TufrgError):
+        s.selftest_wait(0)
+    s.close()
+
+
 def test_invalid_calls_return_status(torch):
     from paper_1604_06296_gb300 import TufrgError
     s, p = make("cfg1", torch)
