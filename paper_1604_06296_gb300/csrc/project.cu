@@ -143,6 +143,7 @@ __global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __
 // the (scale-independent) overlap lists and its Fourier key are read once
 // and applied to all of them (only the phases e^{i l.Y} differ).
 constexpr int kContractL = 4;
+constexpr int kTermBatch = 8;
 
 template <class T, int NF>
 __global__ void __launch_bounds__(256)
@@ -192,13 +193,25 @@ __global__ void __launch_bounds__(256)
     V acc[kContractL];
 #pragma unroll
     for (int j = 0; j < kContractL; ++j) acc[j] = {0, 0};
-    for (int k = rp[o]; k < rp[o + 1]; ++k) {
-      const int4 q = tm[k];
-      V f = fkey[q.x];
-      if (q.w < 0) f = {-f.x, -f.y};
+    // terms in batches of kTermBatch: all terms of a batch, then all their
+    // keys, are loaded before any is used (rows hold up to ~26 terms, and the
+    // key loads depend on the term loads)
+    const int ke = rp[o + 1];
+    for (int k = rp[o]; k < ke; k += kTermBatch) {
+      int4 q[kTermBatch];
+      V f[kTermBatch];
 #pragma unroll
-      for (int j = 0; j < kContractL; ++j)
-        acc[j] = cfma(cmul(qx[j * nd + q.y], qy[j * nd + q.z]), f, acc[j]);
+      for (int i = 0; i < kTermBatch; ++i) q[i] = k + i < ke ? tm[k + i] : make_int4(0, 0, 0, 0);
+#pragma unroll
+      for (int i = 0; i < kTermBatch; ++i) {
+        f[i] = k + i < ke ? fkey[q[i].x] : V{0, 0};
+        if (q[i].w < 0) f[i] = {-f[i].x, -f[i].y};
+      }
+#pragma unroll
+      for (int i = 0; i < kTermBatch; ++i)
+#pragma unroll
+        for (int j = 0; j < kContractL; ++j)
+          acc[j] = cfma(cmul(qx[j * nd + q[i].y], qy[j * nd + q[i].z]), f[i], acc[j]);
     }
 #pragma unroll
     for (int j = 0; j < kContractL; ++j) Tm[j * nb * nb + o] = {acc[j].x * inv_nl, acc[j].y * inv_nl};
