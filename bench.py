@@ -38,11 +38,14 @@ WORKLOAD = "cfg2"
 L2_FLUSH_BYTES = 512 << 20
 
 
-def workload_desc(tp):
-    c = W.config(WORKLOAD)
+def workload_desc(tp, name=WORKLOAD):
+    c = W.config(name)
+    r2 = int(max((b ** 2).sum() for b in np.asarray(W.bonds_for_shells(c["shells"]))))
+    rad = f"{int(r2 ** 0.5)}" if int(r2 ** 0.5) ** 2 == r2 else f"sqrt({r2})"
     return (f"t-t' Hubbard square lattice, t'={tp}, mu=4t', U={c['U']}; coarse "
             f"{c['nc']}x{c['nc']} ({c['nc'] ** 2} l), Nff={W.n_ff_for_shells(c['shells'])} "
-            f"(bonds <= 2), fine {c['nf']}x{c['nf']}; DoPri5 steps from Lambda0={c['lambda0']}")
+            f"(bonds <= {rad}), fine {c['nf']}x{c['nf']}; DoPri5 steps from "
+            f"Lambda0={c['lambda0']}")
 
 
 def dist_env():
@@ -64,8 +67,11 @@ def aggregate_ranks(pg, device_s, units, device="cuda"):
     return float(tmax[0]), float(t[1])
 
 
-def rank_tprime(rank):
-    """t' of the production point a rank runs (ranks cycle over the three)."""
+def rank_tprime(rank, name=WORKLOAD):
+    """t' of the point a rank runs: the production workload cycles over its
+    three t'; the large workload steps down from its t' by 0.02 per rank."""
+    if name == "cfg5":
+        return round(W.config(name)["tp"] - 0.02 * rank, 4)
     return W.CFG2_TPRIME[(1 + rank) % len(W.CFG2_TPRIME)]
 
 
@@ -474,9 +480,11 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "3xtf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flow-time", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "scan", "learned"],
-                    help="cfg2: production point (default); scan: batched phase-diagram scan; "
-                         "learned: loop surrogate trained and used in flows")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg5", "scan", "learned"],
+                    help="cfg2: production point (default); cfg5: large point (coarse 48x48, "
+                         "Nff 25, fine 960x960; no flow ladder or CPU baseline: the FP64 "
+                         "reference flow takes tens of minutes there); scan: batched "
+                         "phase-diagram scan; learned: loop surrogate trained and used in flows")
     ap.add_argument("--points", type=int, default=256, help="scan: points per GPU")
     ap.add_argument("--epochs", type=int, default=40, help="learned: training epochs")
     args = ap.parse_args()
@@ -499,8 +507,11 @@ def main():
         dist.init_process_group("nccl")
         pg = dist
 
-    c = W.config(WORKLOAD)
-    tp = rank_tprime(rank)
+    name = args.workload
+    c = W.config(name)
+    tp = rank_tprime(rank, name)
+    if name == "cfg5":
+        args.no_flow_time = args.no_cpu_baseline = True
     solver = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"],
                           c["nf"], precision=args.precision)
     flow_kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
@@ -571,7 +582,7 @@ def main():
                     "FP64: cuBLAS DGEMM 4096^3 measured in this run (of measured)",
                     "kernel": "loops_fp64_kernel (stage_ms: + per-scale table, split-K "
                               "combination)",
-                    "traffic": profile_traffic("loops_fp64.cu", "loops_fp64_cfg2.txt")}
+                    "traffic": profile_traffic("loops_fp64.cu", f"loops_fp64_{name}.txt")}
     else:
         flops = 2.0 * 3 * 2 * npair * kdim * nrow        # 3 split products issued per MAC
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
@@ -583,7 +594,7 @@ def main():
                     "kernel": f"loops_tc_kernel<{args.precision}> (stage_ms: + per-scale table, "
                               "split-K combination)",
                     "traffic": profile_traffic("loops_tc.cu",
-                                               f"loops_tc_{args.precision}_cfg2.txt")}
+                                               f"loops_tc_{args.precision}_{name}.txt")}
     achieved = flops / (k_ms * 1e-3) / 1e12
     roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "kernel_ms": k_ms, "stage_ms": stage_ms,
@@ -680,7 +691,7 @@ def main():
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-               "config": {"workload": workload_desc(tp), "precision": args.precision,
+               "config": {"workload": workload_desc(tp, name), "precision": args.precision,
                           "step": "one DoPri5 step (6 RHS evaluations + stage/error/control)",
                           "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                           "parallelism": f"{world} independent phase-diagram points"

@@ -8,7 +8,9 @@
 // combined with the others (fixed order, compensated FP32 pairs, FP64
 // result) by the reduction kernel.
 // The persistent CTAs take items from a queue ordered by estimated cost,
-// longest first, so the uneven points of a batch end together.
+// longest first, so the uneven points of a batch end together; the tiles of
+// one K range stay next to each other in the queue, so that F is read from
+// HBM about once however many tiles a point has.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -70,7 +72,7 @@ tufrg_status view_set_kbps(MultiView& v, int kbps, cudaStream_t st) {
   v.kbps = kbps;
   struct Item {
     int4 it;
-    long long cost;
+    long long cost;  // of the item's K range over all tiles of its point
   };
   std::vector<Item> items;
   size_t off = 0;
@@ -86,13 +88,14 @@ tufrg_status view_set_kbps(MultiView& v, int kbps, cudaStream_t st) {
     while (cols < d.nsets * 2 * d.npad) cols *= 2;
     v.tmem_cols = std::max(v.tmem_cols, cols);
     const int tiles = d.nrow_pad / 128;
-    for (int t = 0; t < tiles; ++t) {
-      const int valid = std::min(128, d.nrow - 128 * t);
-      for (int sp = 0; sp < d.ksplit; ++sp) {
-        const int kb0 = sp * kbps, cnt = std::min(kbps, d.nkb - kb0);
-        // producers: ~ valid rows per K-block; tensor cores: ~ pair columns
-        items.push_back({make_int4(i, t, kb0, cnt), (long long)cnt * (2 * valid + d.npad)});
-      }
+    // the tiles of one K range one after the other (and ordered as a group):
+    // CTAs running at the same time then read the same F columns, from L2
+    // after the first
+    for (int sp = 0; sp < d.ksplit; ++sp) {
+      const int kb0 = sp * kbps, cnt = std::min(kbps, d.nkb - kb0);
+      long long cost = 0;  // producers: ~ valid rows per K-block; tensor cores: ~ pair columns
+      for (int t = 0; t < tiles; ++t) cost += (long long)cnt * (2 * std::min(128, d.nrow - 128 * t) + d.npad);
+      for (int t = 0; t < tiles; ++t) items.push_back({make_int4(i, t, kb0, cnt), cost});
     }
   }
   std::stable_sort(items.begin(), items.end(),

@@ -9,6 +9,8 @@ FP32 accumulation in TMEM (the tensor core rounds the accumulator at every
 MMA instruction, so the error grows with the chain length: K-blocks go
 round-robin to up to four accumulator sets), FP64 across CTAs.  Measured on
 GB300: ~2e-6 (BF16x3) and ~3e-7 / 6e-6 (3xTF32, short / production chains).
+At the large size (Nff = 25) the BF16x3 loops are checked entry by entry
+against the bound the split arithmetic gives, 4 * 2^-16 (1/Nf) sum |f f w|.
 """
 import os
 
@@ -100,6 +102,42 @@ def test_production_size_loops_sampled(torch, precision):
         assert err < BOUND[precision]
         # chi(-l) = chi(l) is exact by construction, chi symmetric
         assert np.array_equal(got, np.swapaxes(got, -1, -2))
+
+
+def test_large_size_loops_sampled_bf16x3(torch):
+    """The large workload (coarse 48x48, Nff = 25: 169 allowed pairs, the
+    widest N the two pipeline stages hold; fine 960x960) on the tensor cores,
+    sampled l against the oracle: an interior l, its C4v image, a zone-boundary
+    l and a general one."""
+    c = W.config("cfg5")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=c["tp"], mu=c["mu"], U=c["U"])
+    s, p = make(case, torch, precision="bf16x3")
+    got = s.loops(0.1).cpu().numpy()
+    check_device(s)
+    ix, iy = 30, 17
+    sel = [ix * 48 + iy, iy * 48 + ix, 0 * 48 + 31, 1176]
+    ref = np.stack(olo.chi_dot(p, 0.1, sel))
+    err = rel(got[:, sel], ref)
+    print(f"cfg5 bf16x3: rel err {err:.2e}")
+    assert err < 1e-4  # the bar on couplings of the mixed-precision forms
+    # Element-wise bound from the arithmetic.  The hi/lo split leaves a
+    # relative residual of at most 2^-16 on each of W and F and drops
+    # W_lo F_lo (at most 2^-16 |W F|); the FP32 chains and the compensated
+    # combination add far less.  So |error_mn| <= 4 * 2^-16 * A_mn with
+    # A_mn = (1/Nf) sum_p |f_m(p) f_n(p) w(p)|: with Nff = 25 the sums cancel
+    # more than at Nff = 13, and the max-norm error relative to max |chi|
+    # grows with them.
+    P, F = p.p_values, np.abs(p.f_fine)
+    for j, l in enumerate(sel):
+        half = 0.5 * p.l_values[l]
+        ws = olo.weights(p.xi(P[:, 0] + half[0], P[:, 1] + half[1]),
+                         p.xi(P[:, 0] - half[0], P[:, 1] - half[1]), 0.1, True)
+        for ch, w in enumerate(ws):
+            A = (F * np.abs(w)) @ F.T / p.nf
+            d = np.abs(got[ch, l] - ref[ch, j])
+            print(f"  l={l} ch={ch}: max |error| / A = {np.max(d / A) * 2 ** 16:.2f} x 2^-16")
+            assert np.all(d <= 2.0 ** -14 * A)
+    assert np.array_equal(got, np.swapaxes(got, -1, -2))
 
 
 @pytest.mark.parametrize("precision", ["bf16x3", "3xtf32"])
