@@ -72,6 +72,14 @@ struct ProjTables {
   std::vector<int> row_ptr[3];
   std::vector<int> term_key[3], term_dy[3], term_dx[3];
   std::vector<double> term_sign[3];
+  // the same terms grouped by phase position: the distinct Y of target t
+  // are entries gy_off[t] .. gy_off[t + 1] - 1 of gy = (2Y_x, 2Y_y); the
+  // terms of position g fill slots g * gmaxt .. of gslot as (b1*nb+b2, key,
+  // sign, 0), ordered by output pair, unused slots (-1, -1, 0, 0)
+  int gy_off[4] = {0, 0, 0, 0};
+  int gmaxt = 0;
+  std::vector<int2> gy;
+  std::vector<int4> gslot;
 };
 
 struct FlowState;
@@ -85,7 +93,8 @@ extern const int kC4v[8][2][2];
 struct PointDesc {
   int nl, nff, nb, ncx, ncy, nd, nkeys, feedback;
   double U;
-  int term_off[3];
+  int term_off[3];  // term form: first term of target t
+  int gy_off[4];    // grouped form: positions Y of target t are gy_off[t] .. gy_off[t + 1] - 1
   int npair, nrow;
   // tensor-core loops
   int nfx, nfy, hx, hy, wy, n_ext, nkb, kpad_tc, nrow_pad, npad, nsets, ksplit;
@@ -110,9 +119,13 @@ struct PointDesc {
   const double2* phase;
   const float2* coef_f;   // the same in FP32 (FP32-arithmetic kernels)
   const float2* phase_f;
+  const double2* yphase;  // [phase positions Y][nl] e^{i l.Y}
+  const float2* yphase_f;
   const int4* keys;
-  const int* row_ptr;
-  const int4* terms;
+  const int* row_ptr;  // term form: [3][nb*nb+1] CSR over output pairs
+  const int4* terms;   //   (key, 2Y_x + dmax, 2Y_y + dmax, sign)
+  const int4* gslot;   // grouped form: [positions Y][gmaxt] (b1*nb+b2, key, sign, 0)
+  int gmaxt;
   const double* lam;  // [0] scale of the loops, [1] factor applied to dy when scaled
   const int* skip;    // nonzero: the point does no work (finished flow); may be null
 };
@@ -123,7 +136,8 @@ enum : int {
   kKindReduce,     // split-K combination of the tensor-core partial sums
   kKindBond,       // projections: to bond space
   kKindDft,        // projections: Fourier keys
-  kKindContract,   // projections: overlap sums and basis change
+  kKindOverlap,    // projections: key sums and basis change per phase position
+  kKindContract,   // projections: phase sums over the positions, per l
   kKindProducts,   // V chi V
   kKindExpand,     // row loops -> loops of every l the row serves
   kKinds
@@ -135,8 +149,11 @@ struct MultiView {
   PointDesc* d = nullptr;
   std::vector<int> prefix;  // [kKinds][n + 1] first CTA of each point, per kind
   int* d_prefix = nullptr;
-  int nff_max = 0, nb_max = 0, nd_max = 0, nc_sum_max = 0;
+  int nff_max = 0, nb_max = 0, nd_max = 0, nc_sum_max = 0, ny_max = 0;
   int nf_uniform = 0;  // Nff = Nb, the same for every point (else 0)
+  // projections in the grouped form (some point has Nff >= kGroupedNff), else
+  // in the term form
+  bool proj_grouped = false;
   // tensor-core loops: work items (point, l-tile, first K-block, K-blocks)
   // taken from a queue by persistent CTAs
   int tc_prec = TUFRG_FP64;  // TUFRG_FP64: no tensor-core loops
@@ -191,10 +208,13 @@ struct tufrg_ctx {
   double2* d_phase = nullptr;      // [ncx + ncy][2*dmax+1] e^{i l d pi/(2nc)} tables
   float2* d_coef_f = nullptr;      // d_coef, d_phase rounded to FP32
   float2* d_phase_f = nullptr;
+  double2* d_yphase = nullptr;     // [ProjTables::gy][nl] e^{i l.Y}, FP64 and FP32
+  float2* d_yphase_f = nullptr;
   int4* d_key = nullptr;           // [nkeys] (src, b3*nb+b4, dx, dy)
-  int* d_row_ptr = nullptr;        // [3][nb*nb+1]
-  int4* d_terms = nullptr;         // [total terms] (key, dx, dy, sign)
+  int* d_row_ptr = nullptr;        // term form: [3][nb*nb+1]
+  int4* d_terms = nullptr;         //   [total terms] (key, dx, dy, sign)
   int term_off[3] = {0, 0, 0};
+  int4* d_gslot = nullptr;         // grouped form: ProjTables::gslot
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_nkb = 0, tc_nrow_pad = 0;
@@ -215,7 +235,8 @@ struct tufrg_ctx {
   double* d_partial = nullptr;     // [ksplit][2][mpad][nrow] split-K partial sums
   double* d_chi = nullptr;         // [2][nl][nff][nff]
   double* d_V = nullptr;           // [3][nl][nff][nff]
-  double2* d_bt = nullptr;         // [3][nb*nb][nl] bond-space propagators
+  double2* d_bt = nullptr;         // [3][nb*nb][nl] bond-space propagators, then the
+                                   // overlap sums H [positions Y][nff][nff] (bt_region)
   double2* d_fkey = nullptr;       // [nkeys] Fourier values
 
   // integrator of tufrg_flow_* (allocated on first use) and the library's own
@@ -330,7 +351,12 @@ tufrg_status prepare_loops_tc_multi(const MultiView& v);
 tufrg_status prepare_project_multi(const MultiView& v);
 tufrg_status prepare_products_multi(const MultiView& v);
 int dft_ctas(int nkeys);
-int contract_ctas(int nl);
+int contract_ctas(int nl, bool grouped);
+// the projections of a view take the grouped form from this form-factor count on
+constexpr int kGroupedNff = 21;
+// elements of a point's bond-space workspace: the bond-space propagators
+// [3][nb*nb][nl], later reused for the overlap sums [positions Y][nff][nff]
+size_t bt_region(int nb, int nl, int nff, int ny_total);
 // projections and products of every point; bt, fkey: packed workspaces
 tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
                                   void* bt, void* fkey, cudaStream_t st);

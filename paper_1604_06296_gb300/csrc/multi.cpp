@@ -131,6 +131,10 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
   v.prefix.assign((size_t)kKinds * (n + 1), 0);
   size_t off_state = 0, off_chi = 0, off_bt = 0, off_fkey = 0, off_rowres = 0;
   const bool tc = tc_prec != TUFRG_FP64;
+  // the projection form of the whole view (one launch sequence for all points)
+  bool grouped = false;
+  for (int i = 0; i < n; ++i) grouped = grouped || ctx[i]->nff >= kGroupedNff;
+  v.proj_grouped = grouped;
   for (int i = 0; i < n; ++i) {
     const tufrg_ctx* c = ctx[i];
     if (tc && c->p.precision != tc_prec) return TUFRG_ERR_ARG;
@@ -145,6 +149,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.feedback = c->p.feedback;
     d.U = c->p.U;
     for (int t = 0; t < 3; ++t) d.term_off[t] = c->term_off[t];
+    for (int t = 0; t < 4; ++t) d.gy_off[t] = c->proj.gy_off[t];
     d.npair = c->npair;
     d.nrow = c->nrow;
     d.nfx = c->nfx;
@@ -164,7 +169,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.off_fkey = (long long)off_fkey;
     off_state += (size_t)3 * c->nl * c->nff * c->nff;
     off_chi += (size_t)2 * c->nl * c->nff * c->nff;
-    off_bt += (size_t)3 * c->nb * c->nb * c->nl;
+    off_bt += bt_region(c->nb, c->nl, c->nff, c->proj.gy_off[3]);
     off_fkey += (size_t)c->proj.nkeys;
     d.tab = c->d_tab;
     d.ext = c->d_ext;
@@ -187,9 +192,13 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.phase = c->d_phase;
     d.coef_f = c->d_coef_f;
     d.phase_f = c->d_phase_f;
+    d.yphase = c->d_yphase;
+    d.yphase_f = c->d_yphase_f;
     d.keys = c->d_key;
     d.row_ptr = c->d_row_ptr;
     d.terms = c->d_terms;
+    d.gslot = c->d_gslot;
+    d.gmaxt = c->proj.gmaxt;
     d.lam = lam[i];
     d.skip = skip ? skip[i] : nullptr;
     const int cnt[kKinds] = {
@@ -197,7 +206,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
         tc ? rows_reduce_ctas(d.npair, d.nrow) : 0,
         d.feedback ? 3 * d.nl : 0,
         d.feedback ? dft_ctas(d.nkeys) : 0,
-        contract_ctas(d.nl),
+        grouped && d.feedback ? d.gy_off[3] : 0,
+        contract_ctas(d.nl, grouped),
         d.nl,
         d.nrow,
     };
@@ -207,6 +217,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     v.nb_max = std::max(v.nb_max, d.nb);
     v.nd_max = std::max(v.nd_max, d.nd);
     v.nc_sum_max = std::max(v.nc_sum_max, d.ncx + d.ncy);
+    for (int t = 0; t < 3; ++t) v.ny_max = std::max(v.ny_max, d.gy_off[t + 1] - d.gy_off[t]);
     const int nf = d.nff == d.nb ? d.nff : 0;
     v.nf_uniform = i == 0 ? nf : (v.nf_uniform == nf ? nf : 0);
   }

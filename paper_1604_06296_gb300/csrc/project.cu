@@ -9,11 +9,24 @@
 // the k integral, their half-integer Fourier position X and phase position Y)
 // are scale independent and built once at setup.  Bosonic momenta are the
 // coarse-grid points in [-pi, pi) (folding reading of the half-momentum
-// convention).  Three kernels, each over all points of a batch (CTAs of a
-// point found from a prefix table):
-//   to_bond   -- Bt for all channels and l          (Nl x 3 CTAs per point)
-//   dft_keys  -- F for every key, one warp per key   (lanes over l')
-//   contract  -- T and the basis change, per (target channel, 4 l)
+// convention).  Three kernels compute the keys and the terms (term form):
+//   to_bond   -- Bt for all channels and l              (Nl x 3 CTAs per point)
+//   dft_keys  -- F for every key, one warp per key       (lanes over l')
+//   contract_terms -- T and the basis change, per (target channel, 4 l)
+// The phase e^{i l.Y} is the only l dependence of a term, and the terms of a
+// target channel take few distinct Y (41 at Nb = 13, 81 at Nb = 25), so the
+// sums regroup (exactly, by linearity) as
+//
+//   V^T_mn(l) = V0_T + own_T + (1/Nl) Re sum_Y e^{i l.Y} H^T_mn(Y),
+//   H^T_mn(Y) = sum_{b1,b2} c_m(b1) c_n(b2) G^T_{b1 b2}(Y),
+//   G^T_{b1 b2}(Y) = sum_{terms of (b1, b2) at Y} sign * F_key,
+//
+// with G and H independent of l (grouped form).  It replaces contract_terms by
+//   overlap   -- G and the basis change to H, per (target channel, Y)
+//   contract  -- the phase sum over Y, per (target channel, 8 l)
+// and needs about half the arithmetic.  Views with a point of Nff >= 21 use
+// it (there the sums bound the step); for Nff <= 13 its extra dependent
+// launch costs more than the arithmetic it saves.
 // The arithmetic type is FP64 for an FP64 context (this step is then bound by
 // GB300's FP64 rate) and FP32 for the mixed-precision contexts, whose loops
 // run on the tensor cores; the state and the result are FP64 in both cases.
@@ -59,6 +72,23 @@ __device__ __forceinline__ double2 phase_at(const PointDesc& pd, int e, double) 
 }
 __device__ __forceinline__ float2 phase_at(const PointDesc& pd, int e, float) {
   return pd.phase_f[e];
+}
+__device__ __forceinline__ double2 yphase_at(const PointDesc& pd, size_t e, double) {
+  return pd.yphase[e];
+}
+__device__ __forceinline__ float2 yphase_at(const PointDesc& pd, size_t e, float) {
+  return pd.yphase_f[e];
+}
+
+// H(Y) rows [nff * nff] are stored with an even stride, so that every row
+// starts on a 16-byte boundary (16-byte asynchronous copies)
+__host__ __device__ constexpr int hstride(int nff) { return (nff * nff + 1) & ~1; }
+
+// Y positions of H staged in shared memory per pass of the phase sum (all
+// of them at Nb = 13 in FP32, within 56 KB)
+__host__ __device__ inline int contract_ychunk(int ny, int nff, int vbytes) {
+  const int c = 56 * 1024 / (hstride(nff) * vbytes);
+  return ny < c ? (ny > 0 ? ny : 1) : (c > 0 ? c : 1);
 }
 
 constexpr int kDftWarps = 8;
@@ -139,15 +169,16 @@ __global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __
   if (lane == 0) fkbase[pd.off_fkey + key] = acc;
 }
 
-// kContractL transfer momenta of one target channel per CTA: each term of
+// Term form (Nff <= 13).  kTermsL transfer momenta of one target channel per
+// CTA: each term of
 // the (scale-independent) overlap lists and its Fourier key are read once
 // and applied to all of them (only the phases e^{i l.Y} differ).
-constexpr int kContractL = 4;
+constexpr int kTermsL = 4;
 constexpr int kTermBatch = 8;
 
 template <class T, int NF>
 __global__ void __launch_bounds__(256)
-    contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
+    contract_terms_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
                     const double* __restrict__ ybase,
                     const typename C2<T>::type* __restrict__ fkbase, double* __restrict__ vbase) {
   using V = typename C2<T>::type;
@@ -155,16 +186,16 @@ __global__ void __launch_bounds__(256)
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
   const int nb = NF ? NF : pd.nb, nff = NF ? NF : pd.nff, nl = pd.nl, nd = pd.nd;
-  const int groups = (nl + kContractL - 1) / kContractL;
+  const int groups = (nl + kTermsL - 1) / kTermsL;
   const int loc = blockIdx.x - prefix[p];
-  const int t = loc / groups, l0 = (loc % groups) * kContractL;
-  const int nlb = min(kContractL, nl - l0);  // l of this CTA
+  const int t = loc / groups, l0 = (loc % groups) * kTermsL;
+  const int nlb = min(kTermsL, nl - l0);  // l of this CTA
   extern __shared__ double2 sm2[];
-  V* Tm = reinterpret_cast<V*>(sm2);       // [kContractL][nb][nb]
-  V* tmp = Tm + kContractL * nb * nb;      // [kContractL][nb][nff]
-  V* cs = tmp + kContractL * nb * nff;     // [nff][nb]
-  V* qx = cs + nff * nb;                   // [kContractL][nd]
-  V* qy = qx + kContractL * nd;            // [kContractL][nd]
+  V* Tm = reinterpret_cast<V*>(sm2);       // [kTermsL][nb][nb]
+  V* tmp = Tm + kTermsL * nb * nb;      // [kTermsL][nb][nff]
+  V* cs = tmp + kTermsL * nb * nff;     // [nff][nb]
+  V* qx = cs + nff * nb;                   // [kTermsL][nd]
+  V* qy = qx + kTermsL * nd;            // [kTermsL][nd]
   const size_t n2 = (size_t)nff * nff;
   const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
   const double U = pd.U;
@@ -177,7 +208,7 @@ __global__ void __launch_bounds__(256)
     return;
   }
   for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
-  for (int e = threadIdx.x; e < kContractL * nd; e += blockDim.x) {
+  for (int e = threadIdx.x; e < kTermsL * nd; e += blockDim.x) {
     const int j = e / nd, d = e % nd;
     const int l = l0 + min(j, nlb - 1);
     const int ix = l / pd.ncy, iy = l - ix * pd.ncy;
@@ -190,9 +221,9 @@ __global__ void __launch_bounds__(256)
   const V* fkey = fkbase + pd.off_fkey;
   const T inv_nl = T(1) / T(nl);
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
-    V acc[kContractL];
+    V acc[kTermsL];
 #pragma unroll
-    for (int j = 0; j < kContractL; ++j) acc[j] = {0, 0};
+    for (int j = 0; j < kTermsL; ++j) acc[j] = {0, 0};
     // terms in batches of kTermBatch: all terms of a batch, then all their
     // keys, are loaded before any is used (rows hold up to ~26 terms, and the
     // key loads depend on the term loads)
@@ -210,15 +241,15 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int i = 0; i < kTermBatch; ++i)
 #pragma unroll
-        for (int j = 0; j < kContractL; ++j)
+        for (int j = 0; j < kTermsL; ++j)
           acc[j] = cfma(cmul(qx[j * nd + q[i].y], qy[j * nd + q[i].z]), f[i], acc[j]);
     }
 #pragma unroll
-    for (int j = 0; j < kContractL; ++j) Tm[j * nb * nb + o] = {acc[j].x * inv_nl, acc[j].y * inv_nl};
+    for (int j = 0; j < kTermsL; ++j) Tm[j * nb * nb + o] = {acc[j].x * inv_nl, acc[j].y * inv_nl};
   }
   __syncthreads();
   // basis change for all l of the CTA at once: rows of cw lanes (lane n <
-  // nff is column n), 32 / cw rows per warp, the kContractL l of a row in
+  // nff is column n), 32 / cw rows per warp, the kTermsL l of a row in
   // one thread (independent chains, each coefficient read once)
   const int cw = nff <= 16 ? 16 : 32, rpw = 32 / cw;
   const int lane = threadIdx.x & 31, n = lane & (cw - 1);
@@ -226,17 +257,17 @@ __global__ void __launch_bounds__(256)
   // tmp[j][b1][n] = sum_b2 T_j[b1][b2] c_n(b2)
   for (int b1 = r0; b1 < nb; b1 += rstep) {
     if (n >= nff) continue;
-    V acc[kContractL];
+    V acc[kTermsL];
 #pragma unroll
-    for (int jj = 0; jj < kContractL; ++jj) acc[jj] = {0, 0};
+    for (int jj = 0; jj < kTermsL; ++jj) acc[jj] = {0, 0};
     for (int b2 = 0; b2 < nb; ++b2) {
       const V c = cs[n * nb + b2];
 #pragma unroll
-      for (int jj = 0; jj < kContractL; ++jj)
+      for (int jj = 0; jj < kTermsL; ++jj)
         acc[jj] = cfma(Tm[jj * nb * nb + b1 * nb + b2], c, acc[jj]);
     }
 #pragma unroll
-    for (int jj = 0; jj < kContractL; ++jj) tmp[(jj * nb + b1) * nff + n] = acc[jj];
+    for (int jj = 0; jj < kTermsL; ++jj) tmp[(jj * nb + b1) * nff + n] = acc[jj];
   }
   __syncthreads();
   // V_mn = V0 + own + Re sum_b1 c_m(b1) tmp[b1][n]
@@ -244,24 +275,197 @@ __global__ void __launch_bounds__(256)
   for (int m = r0; m < nff; m += rstep) {
     if (n >= nff) continue;
     const int mn = m * nff + n;
-    double yv[kContractL];
+    double yv[kTermsL];
 #pragma unroll
-    for (int jj = 0; jj < kContractL; ++jj) yv[jj] = jj < nlb ? ybase[base + jj * n2 + mn] : 0.0;
-    T acc[kContractL];
+    for (int jj = 0; jj < kTermsL; ++jj) yv[jj] = jj < nlb ? ybase[base + jj * n2 + mn] : 0.0;
+    T acc[kTermsL];
 #pragma unroll
-    for (int jj = 0; jj < kContractL; ++jj) acc[jj] = 0;
+    for (int jj = 0; jj < kTermsL; ++jj) acc[jj] = 0;
     for (int b1 = 0; b1 < nb; ++b1) {
       const V c1 = cs[m * nb + b1];
 #pragma unroll
-      for (int jj = 0; jj < kContractL; ++jj) {
+      for (int jj = 0; jj < kTermsL; ++jj) {
         const V t1 = tmp[(jj * nb + b1) * nff + n];
         acc[jj] = fma(c1.x, t1.x, fma(-c1.y, t1.y, acc[jj]));  // real part of c * tmp
       }
     }
 #pragma unroll
-    for (int jj = 0; jj < kContractL; ++jj)
+    for (int jj = 0; jj < kTermsL; ++jj)
       if (jj < nlb)
         vbase[base + jj * n2 + mn] = (mn == 0 ? U : 0.0) + own_sign * yv[jj] + (double)acc[jj];
+  }
+}
+
+// Grouped form (Nff >= 21).  One CTA per (target channel, phase position Y):
+// G(Y) from the keys of its
+// terms, then H(Y) = c^T G(Y) c, written over the point's bond-space
+// workspace (the bond-space propagators are no longer needed once the keys
+// exist).  Every thread loads one term slot and its key at once (two round
+// trips); the first term of each output pair then adds its pair's terms in
+// slot order.
+template <class T, int NF>
+__global__ void __launch_bounds__(256)
+    overlap_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
+                   const typename C2<T>::type* __restrict__ fkbase,
+                   typename C2<T>::type* __restrict__ hbase) {
+  using V = typename C2<T>::type;
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nb = NF ? NF : pd.nb, nff = NF ? NF : pd.nff;
+  const int g = blockIdx.x - prefix[p];  // over the positions of all three targets
+  const int nt = pd.gmaxt;
+  extern __shared__ double2 sm2[];
+  V* G = reinterpret_cast<V*>(sm2);  // [nb][nb]
+  V* tmp = G + nb * nb;              // [nb][nff]
+  V* cs = tmp + nb * nff;            // [nff][nb]
+  V* tv = cs + nff * nb;             // [nt] signed key values
+  int* to = reinterpret_cast<int*>(tv + nt);  // [nt] output pair of each slot (-1: unused)
+  const int4* slot = pd.gslot + (size_t)g * nt;
+  const V* fkey = fkbase + pd.off_fkey;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const int4 q = slot[k];
+    V f = {0, 0};
+    if (q.y >= 0) f = fkey[q.y];
+    tv[k] = q.z < 0 ? V{-f.x, -f.y} : f;
+    to[k] = q.x;
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) G[e] = {0, 0};
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
+  __syncthreads();
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const int o = to[k];
+    if (o < 0 || (k > 0 && to[k - 1] == o)) continue;
+    V acc = tv[k];
+    for (int k2 = k + 1; k2 < nt && to[k2] == o; ++k2) {
+      acc.x += tv[k2].x;
+      acc.y += tv[k2].y;
+    }
+    G[o] = acc;
+  }
+  __syncthreads();
+  // tmp[b1][n] = sum_b2 G[b1][b2] c_n(b2)
+  for (int e = threadIdx.x; e < nb * nff; e += blockDim.x) {
+    const int b1 = e / nff, n = e - b1 * nff;
+    V acc = {0, 0};
+    for (int b2 = 0; b2 < nb; ++b2) acc = cfma(G[b1 * nb + b2], cs[n * nb + b2], acc);
+    tmp[e] = acc;
+  }
+  __syncthreads();
+  // H[m][n] = sum_b1 c_m(b1) tmp[b1][n]
+  V* H = hbase + pd.off_bt + (size_t)g * hstride(nff);
+  for (int e = threadIdx.x; e < nff * nff; e += blockDim.x) {
+    const int m = e / nff, n = e - m * nff;
+    V acc = {0, 0};
+    for (int b1 = 0; b1 < nb; ++b1) acc = cfma(cs[m * nb + b1], tmp[b1 * nff + n], acc);
+    H[e] = acc;
+  }
+}
+
+// kContractL transfer momenta of one target channel per CTA:
+// V = V0 + own + (1/Nl) Re sum_Y e^{i l.Y} H(Y).  H of the target is staged
+// in shared memory by 16-byte asynchronous copies (in passes of
+// contract_ychunk positions), together with the precomputed phases of the
+// CTA's l, so that a pass costs one round trip to L2.  The positions are
+// split over contract_groups groups of threads, one thread of a group per
+// output entry (m, n) holding all kContractL l; the groups' partial sums are
+// then added in a fixed order.
+constexpr int kContractL = 8;
+
+__host__ __device__ inline int contract_tpg(int nff) { return (nff * nff + 31) / 32 * 32; }
+__host__ __device__ inline int contract_groups(int nff) {
+  const int g = 1024 / contract_tpg(nff);
+  return g < 1 ? 1 : (g > 4 ? 4 : g);
+}
+
+template <class T, int NF>
+__global__ void __launch_bounds__(1024)
+    contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
+                    const double* __restrict__ ybase,
+                    const typename C2<T>::type* __restrict__ hbase, double* __restrict__ vbase) {
+  using V = typename C2<T>::type;
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nff = NF ? NF : pd.nff, nl = pd.nl;
+  const int groups = (nl + kContractL - 1) / kContractL;
+  const int loc = blockIdx.x - prefix[p];
+  const int t = loc / groups, l0 = (loc % groups) * kContractL;
+  const int nlb = min(kContractL, nl - l0);  // l of this CTA
+  const int n2 = nff * nff, n2p = hstride(nff);
+  const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
+  const double U = pd.U;
+  const size_t base = pd.off_state + ((size_t)t * nl + l0) * n2;
+  if (!pd.feedback) {
+    for (int e = threadIdx.x; e < nlb * n2; e += blockDim.x) {
+      const int r = e % n2;
+      vbase[base + e] = (r == 0 ? U : 0.0) + own_sign * ybase[base + e];
+    }
+    return;
+  }
+  // (a batch of mixed Nff launches for the largest: fewer groups may fit)
+  const int tpg = contract_tpg(nff), ng = min(contract_groups(nff), (int)blockDim.x / tpg);
+  const int grp = threadIdx.x / tpg, mn = threadIdx.x - grp * tpg;
+  const bool active = grp < ng && mn < n2;
+  const int y0 = pd.gy_off[t], ny = pd.gy_off[t + 1] - y0;
+  const int ych = contract_ychunk(ny, nff, (int)sizeof(V));
+  extern __shared__ double2 sm2[];
+  V* Hs = reinterpret_cast<V*>(sm2);  // [ych][n2p]
+  V* ph = Hs + (size_t)ych * n2p;     // [ych][kContractL] e^{i l.Y}
+  const uint32_t hs = (uint32_t)__cvta_generic_to_shared(Hs);
+  const char* H = reinterpret_cast<const char*>(hbase + pd.off_bt + (size_t)y0 * n2p);
+  double yv[kContractL];  // the state entries group 0 adds to
+#pragma unroll
+  for (int j = 0; j < kContractL; ++j)
+    yv[j] = grp == 0 && mn < n2 && j < nlb ? ybase[base + (size_t)j * n2 + mn] : 0.0;
+  T acc[kContractL];
+#pragma unroll
+  for (int j = 0; j < kContractL; ++j) acc[j] = 0;
+  for (int c0 = 0; c0 < ny; c0 += ych) {
+    const int cn = min(ych, ny - c0);
+    if (c0 > 0) __syncthreads();  // the previous pass is consumed
+    const int chunks = cn * n2p * (int)sizeof(V) / 16;
+    const char* src = H + (size_t)c0 * n2p * sizeof(V);
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(hs + 16u * i),
+                   "l"(src + 16 * (size_t)i)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int e = threadIdx.x; e < cn * kContractL; e += blockDim.x) {
+      const int yi = e / kContractL, j = e - yi * kContractL;
+      ph[e] = yphase_at(pd, (size_t)(y0 + c0 + yi) * nl + l0 + min(j, nlb - 1), T());
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if (active) {
+#pragma unroll 2
+      for (int yi = grp; yi < cn; yi += ng) {
+        const V h = Hs[yi * n2p + mn];
+        const V* e = ph + yi * kContractL;
+#pragma unroll
+        for (int j = 0; j < kContractL; ++j)
+          acc[j] = fma(e[j].x, h.x, fma(-e[j].y, h.y, acc[j]));  // real part of e * h
+      }
+    }
+  }
+  // partial sums of the groups, added by group 0 in group order
+  __syncthreads();  // the staging area is free
+  T* red = reinterpret_cast<T*>(sm2);  // [ng][kContractL][tpg]
+  if (active && grp > 0) {
+#pragma unroll
+    for (int j = 0; j < kContractL; ++j) red[((size_t)grp * kContractL + j) * tpg + mn] = acc[j];
+  }
+  __syncthreads();
+  if (active && grp == 0) {
+    const T inv_nl = T(1) / T(nl);
+#pragma unroll
+    for (int j = 0; j < kContractL; ++j) {
+      T a = acc[j];
+      for (int g = 1; g < ng; ++g) a += red[((size_t)g * kContractL + j) * tpg + mn];
+      if (j < nlb)
+        vbase[base + (size_t)j * n2 + mn] =
+            (mn == 0 ? U : 0.0) + own_sign * yv[j] + (double)(a * inv_nl);
+    }
   }
 }
 
@@ -275,17 +479,42 @@ size_t dft_smem(const MultiView& v) {
   return sizeof(typename C2<T>::type) * v.nc_sum_max * v.nd_max;
 }
 template <class T>
-size_t contract_smem(const MultiView& v) {
+size_t overlap_smem(const MultiView& v) {
+  int nt = 1;
+  for (const PointDesc& d : v.h) nt = std::max(nt, d.gmaxt);
   return sizeof(typename C2<T>::type) *
-         ((size_t)kContractL * v.nb_max * v.nb_max + (kContractL + 1) * (size_t)v.nb_max * v.nff_max +
-          2 * (size_t)kContractL * v.nd_max);
+             ((size_t)v.nb_max * v.nb_max + 2 * (size_t)v.nb_max * v.nff_max + nt) +
+         sizeof(int) * (size_t)nt;
+}
+
+template <class T>
+size_t contract_terms_smem(const MultiView& v) {
+  return sizeof(typename C2<T>::type) *
+         ((size_t)kTermsL * v.nb_max * v.nb_max + (kTermsL + 1) * (size_t)v.nb_max * v.nff_max +
+          2 * (size_t)kTermsL * v.nd_max);
+}
+
+template <class T>
+size_t contract_smem(const MultiView& v) {
+  const int vb = (int)sizeof(typename C2<T>::type);
+  size_t m = 0;
+  for (const PointDesc& d : v.h) {
+    for (int t = 0; t < 3; ++t) {
+      const int ych = contract_ychunk(d.gy_off[t + 1] - d.gy_off[t], d.nff, vb);
+      m = std::max(m, (size_t)vb * ych * (hstride(d.nff) + kContractL));
+    }
+    // the groups' partial sums reuse the staging area
+    m = std::max(m, sizeof(T) * contract_groups(d.nff) * kContractL * contract_tpg(d.nff));
+  }
+  return m;
 }
 
 template <class T>
 tufrg_status prepare_typed(const MultiView& v) {
   const int smem = smem_optin();
   if ((int)bond_smem<T>(v) > smem || (int)dft_smem<T>(v) > smem ||
-      (int)contract_smem<T>(v) > smem)
+      (int)overlap_smem<T>(v) > smem || (int)contract_smem<T>(v) > smem ||
+      (int)contract_terms_smem<T>(v) > smem)
     return TUFRG_ERR_ARG;
   TUFRG_CUDA(cudaFuncSetAttribute(dft_keys_kernel<T>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -295,6 +524,12 @@ tufrg_status prepare_typed(const MultiView& v) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(to_bond_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(contract_terms_kernel<T, NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(overlap_kernel<T, NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(contract_kernel<T, NF>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -321,10 +556,29 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
         v.d, v.dprefix(kKindDft), v.n, bt, fkey);
     TUFRG_CUDA(cudaGetLastError());
   }
+  if (!v.proj_grouped) {
+    with_nf(v.nf_uniform, [&](auto nf) {
+      contract_terms_kernel<T, decltype(nf)::value>
+          <<<v.total(kKindContract), 256, contract_terms_smem<T>(v), st>>>(
+              v.d, v.dprefix(kKindContract), v.n, y, fkey, out);
+    });
+    TUFRG_CUDA(cudaGetLastError());
+    return TUFRG_OK;
+  }
+  if (v.total(kKindOverlap) > 0) {
+    with_nf(v.nf_uniform, [&](auto nf) {
+      overlap_kernel<T, decltype(nf)::value><<<v.total(kKindOverlap), 256, overlap_smem<T>(v), st>>>(
+          v.d, v.dprefix(kKindOverlap), v.n, fkey, bt);
+    });
+    TUFRG_CUDA(cudaGetLastError());
+  }
+  // groups of one thread per output entry (m, n); Nff <= 29: at most 1024
+  // threads (a batch has one Nff when nf_uniform, else the largest decides)
+  const int cthreads = contract_groups(v.nff_max) * contract_tpg(v.nff_max);
   with_nf(v.nf_uniform, [&](auto nf) {
     contract_kernel<T, decltype(nf)::value>
-        <<<v.total(kKindContract), 256, contract_smem<T>(v), st>>>(
-            v.d, v.dprefix(kKindContract), v.n, y, fkey, out);
+        <<<v.total(kKindContract), cthreads, contract_smem<T>(v), st>>>(
+            v.d, v.dprefix(kKindContract), v.n, y, bt, out);
   });
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
@@ -334,7 +588,14 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
 
 int dft_ctas(int nkeys) { return (nkeys + kDftWarps - 1) / kDftWarps; }
 
-int contract_ctas(int nl) { return 3 * ((nl + kContractL - 1) / kContractL); }
+int contract_ctas(int nl, bool grouped) {
+  const int L = grouped ? kContractL : kTermsL;
+  return 3 * ((nl + L - 1) / L);
+}
+
+size_t bt_region(int nb, int nl, int nff, int ny_total) {
+  return std::max((size_t)3 * nb * nb * nl, (size_t)ny_total * hstride(nff));
+}
 
 tufrg_status prepare_project_multi(const MultiView& v) {
   TUFRG_CHECK(prepare_typed<double>(v));

@@ -150,6 +150,29 @@ void build_proj(tufrg_ctx* c) {
       P.row_ptr[t][o + 1] = (int)P.term_key[t].size();
     }
   }
+  // the terms of each target grouped by phase position Y (in the order of
+  // (2Y_x, 2Y_y)), within a position by output pair, within a pair in the
+  // order above; padded to the same number of slots per position
+  std::vector<std::vector<int4>> groups;
+  P.gy.clear();
+  for (int t = 0; t < 3; ++t) {
+    P.gy_off[t] = (int)P.gy.size();
+    std::map<std::pair<int, int>, std::vector<int4>> by_y;  // (o, key, sign, 0)
+    for (int o = 0; o < nb * nb; ++o)
+      for (int k = P.row_ptr[t][o]; k < P.row_ptr[t][o + 1]; ++k)
+        by_y[{P.term_dx[t][k], P.term_dy[t][k]}].push_back(
+            make_int4(o, P.term_key[t][k], P.term_sign[t][k] < 0 ? -1 : 1, 0));
+    for (auto& kv : by_y) {
+      P.gy.push_back(make_int2(kv.first.first, kv.first.second));
+      groups.push_back(kv.second);
+    }
+  }
+  P.gy_off[3] = (int)P.gy.size();
+  P.gmaxt = 1;
+  for (const auto& g : groups) P.gmaxt = std::max(P.gmaxt, (int)g.size());
+  P.gslot.assign(groups.size() * P.gmaxt, make_int4(-1, -1, 0, 0));
+  for (size_t g = 0; g < groups.size(); ++g)
+    for (size_t k = 0; k < groups[g].size(); ++k) P.gslot[g * P.gmaxt + k] = groups[g][k];
 }
 
 }  // namespace
@@ -438,10 +461,13 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_phase = dp->d_phase;
     c->d_coef_f = dp->d_coef_f;
     c->d_phase_f = dp->d_phase_f;
+    c->d_yphase = dp->d_yphase;
+    c->d_yphase_f = dp->d_yphase_f;
     c->d_key = dp->d_key;
     c->d_row_ptr = dp->d_row_ptr;
     c->d_terms = dp->d_terms;
     for (int t = 0; t < 3; ++t) c->term_off[t] = dp->term_off[t];
+    c->d_gslot = dp->d_gslot;
   } else {
     TUFRG_CHECK(setup_proj(c, st));
   }
@@ -453,7 +479,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nrow));
     TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
     TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
-    TUFRG_CHECK(alloc(&c->d_bt, (size_t)3 * nb * nb * c->nl));
+    TUFRG_CHECK(alloc(&c->d_bt, bt_region(nb, c->nl, nff, P.gy_off[3])));
     TUFRG_CHECK(alloc(&c->d_fkey, (size_t)P.nkeys));
     // the loop kernels write only the parity-allowed pairs
     TUFRG_CUDA(cudaMemsetAsync(c->d_chi, 0, sizeof(double) * 2 * c->nl * nff * nff, st));
@@ -521,6 +547,23 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
   }
   TUFRG_CHECK(upload(&c->d_row_ptr, rowp, st));
   TUFRG_CHECK(upload(&c->d_terms, terms, st));
+  TUFRG_CHECK(upload(&c->d_gslot, P.gslot, st));
+  // e^{i l.Y} for every phase position Y and every l = (ix, iy)
+  std::vector<double2> yph((size_t)P.gy.size() * c->nl);
+  std::vector<float2> yph_f(yph.size());
+  for (size_t g = 0; g < P.gy.size(); ++g) {
+    const int dx = P.gy[g].x, dy = P.gy[g].y;
+    for (int ix = 0; ix < c->ncx; ++ix)
+      for (int iy = 0; iy < c->ncy; ++iy) {
+        const double a = M_PI * (double)((2 * ix - c->ncx) * dx) / (2.0 * c->ncx) +
+                         M_PI * (double)((2 * iy - c->ncy) * dy) / (2.0 * c->ncy);
+        const size_t e = g * c->nl + (size_t)ix * c->ncy + iy;
+        yph[e] = make_double2(std::cos(a), std::sin(a));
+        yph_f[e] = make_float2((float)yph[e].x, (float)yph[e].y);
+      }
+  }
+  TUFRG_CHECK(upload(&c->d_yphase, yph, st));
+  TUFRG_CHECK(upload(&c->d_yphase_f, yph_f, st));
   return TUFRG_OK;
 }
 
@@ -542,8 +585,8 @@ void free_device(tufrg_ctx* c) {
       if (p) cudaFree(p);
   }
   if (!c->borrowed_proj) {
-    void* proj[] = {c->d_coef,  c->d_phase,   c->d_key,  c->d_row_ptr,
-                    c->d_terms, c->d_coef_f, c->d_phase_f};
+    void* proj[] = {c->d_coef,   c->d_phase,   c->d_key,    c->d_row_ptr, c->d_terms,
+                    c->d_gslot,  c->d_coef_f,  c->d_phase_f, c->d_yphase, c->d_yphase_f};
     for (void* p : proj)
       if (p) cudaFree(p);
   }

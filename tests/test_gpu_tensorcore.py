@@ -54,13 +54,16 @@ def test_loops_tensor_core(torch, precision, case, lam):
     assert err < BOUND[precision]
 
 
-@pytest.mark.parametrize("case", ["cfg1", "rect", "cfg2"])
+@pytest.mark.parametrize("case", ["cfg1", "rect", "cfg2", "nff25"])
 def test_projections_mixed_precision(torch, case):
-    # mixed-precision contexts project in FP32 arithmetic (FP64 state and result)
+    # mixed-precision contexts project in FP32 arithmetic (FP64 state and result);
+    # Nff = 25 takes the grouped form of the projections, the others the term form
     from oracle import projections as opj
     if case == "cfg2":
         c = W.config("cfg2")
         case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.25, mu=-1.0, U=3.0)
+    elif case == "nff25":
+        case = dict(shells=5, nc=8, nf=16, tp=-0.3, mu=-1.2, U=3.5)
     s, p = make(case, torch, precision="bf16x3")
     y = W.random_state(21, p.nl, p.nff, 0.7)
     err = rel(s.project(dev(torch, y)).cpu().numpy(), opj.project(p, y))
