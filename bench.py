@@ -507,10 +507,10 @@ def main():
         dist.init_process_group("nccl")
         pg = dist
 
-    name = args.workload
-    c = W.config(name)
-    tp = rank_tprime(rank, name)
-    if name == "cfg5":
+    wl = args.workload
+    c = W.config(wl)
+    tp = rank_tprime(rank, wl)
+    if wl == "cfg5":
         args.no_flow_time = args.no_cpu_baseline = True
     solver = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"],
                           c["nf"], precision=args.precision)
@@ -582,7 +582,7 @@ def main():
                     "FP64: cuBLAS DGEMM 4096^3 measured in this run (of measured)",
                     "kernel": "loops_fp64_kernel (stage_ms: + per-scale table, split-K "
                               "combination)",
-                    "traffic": profile_traffic("loops_fp64.cu", f"loops_fp64_{name}.txt")}
+                    "traffic": profile_traffic("loops_fp64.cu", f"loops_fp64_{wl}.txt")}
     else:
         flops = 2.0 * 3 * 2 * npair * kdim * nrow        # 3 split products issued per MAC
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
@@ -594,7 +594,7 @@ def main():
                     "kernel": f"loops_tc_kernel<{args.precision}> (stage_ms: + per-scale table, "
                               "split-K combination)",
                     "traffic": profile_traffic("loops_tc.cu",
-                                               f"loops_tc_{args.precision}_{name}.txt")}
+                                               f"loops_tc_{args.precision}_{wl}.txt")}
     achieved = flops / (k_ms * 1e-3) / 1e12
     roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "kernel_ms": k_ms, "stage_ms": stage_ms,
@@ -691,7 +691,7 @@ def main():
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-               "config": {"workload": workload_desc(tp, name), "precision": args.precision,
+               "config": {"workload": workload_desc(tp, wl), "precision": args.precision,
                           "step": "one DoPri5 step (6 RHS evaluations + stage/error/control)",
                           "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                           "parallelism": f"{world} independent phase-diagram points"
