@@ -36,6 +36,9 @@ METRIC = "fRG RHS evals/s & flow time to Λ_c (mixed/learned vs FP64 GPU, same a
 UNIT = "RHS evals/s"
 WORKLOAD = "cfg2"
 L2_FLUSH_BYTES = 512 << 20
+# the library computes the projections of a view in the grouped form (one more
+# kernel per right-hand side) when one of its points has this many form factors
+GROUPED_NFF = 21
 
 
 def workload_desc(tp, name=WORKLOAD):
@@ -335,11 +338,12 @@ def run_scan(args, rank, world, local):
                 "algorithmic_flop_per_launch": flops,
                 "peak_source": f"bf16 dense burst from {peak_src} (of measured)"}
     # kernels of the library in the timed call: first stage (combination,
-    # stage scales + 7 right-hand-side kernels), per attempt 6 x 9 + error,
-    # control, accept, then 100 bisection rounds of 2 and 6 more for the
-    # crossing and argmax
+    # stage scales + 7 right-hand-side kernels, 8 in the grouped form), per
+    # attempt 6 stages of as many + error, control, accept, then 100 bisection
+    # rounds of 2 and 6 more for the crossing and argmax
     attempts = max(r["n_accepted"] + r["n_rejected"] for r in res)
-    launches = 9 + 57 * attempts + 2 * 100 + 6
+    per_stage = 9 + (max(W.n_ff_for_shells(q["shells"]) for q in pts) >= GROUPED_NFF)
+    launches = per_stage + (6 * per_stage + 3) * attempts + 2 * 100 + 6
     if rank == 0:
         sizes = sorted({(q["nc"], q["nf"], W.n_ff_for_shells(q["shells"])) for q in pts})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -682,9 +686,10 @@ def main():
 
     # kernels of the library per timed step: 6 stages x (combination, stage
     # scale, per-scale table, loop contraction, split-K reduce, to_bond,
-    # dft_keys, contract, products gathering the row loops) + error + control
-    # + accept
-    launches_per_step = 6 * 9 + 3
+    # dft_keys, contract (+ overlap in the grouped form), products gathering
+    # the row loops) + error + control + accept
+    per_stage = 9 + (solver.nff >= GROUPED_NFF)
+    launches_per_step = 6 * per_stage + 3
     if rank == 0:
         dtype = "f64" if args.precision == "fp64" else f"{args.precision} loops, f64 state"
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
