@@ -149,7 +149,7 @@ struct MultiView {
   PointDesc* d = nullptr;
   std::vector<int> prefix;  // [kKinds][n + 1] first CTA of each point, per kind
   int* d_prefix = nullptr;
-  int nff_max = 0, nb_max = 0, nd_max = 0, nc_sum_max = 0, ny_max = 0;
+  int nff_max = 0, nb_max = 0, nd_max = 0, nc_sum_max = 0;
   int nf_uniform = 0;  // Nff = Nb, the same for every point (else 0)
   // projections in the grouped form (some point has Nff >= kGroupedNff), else
   // in the term form

@@ -217,7 +217,6 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     v.nb_max = std::max(v.nb_max, d.nb);
     v.nd_max = std::max(v.nd_max, d.nd);
     v.nc_sum_max = std::max(v.nc_sum_max, d.ncx + d.ncy);
-    for (int t = 0; t < 3; ++t) v.ny_max = std::max(v.ny_max, d.gy_off[t + 1] - d.gy_off[t]);
     const int nf = d.nff == d.nb ? d.nff : 0;
     v.nf_uniform = i == 0 ? nf : (v.nf_uniform == nf ? nf : 0);
   }
