@@ -107,6 +107,27 @@ def test_production_size_loops_sampled(torch, precision):
         assert np.array_equal(got, np.swapaxes(got, -1, -2))
 
 
+def test_production_size_rhs_sampled_bf16x3(torch):
+    """One whole right-hand side at the production size in the precision the
+    bench times (tufrg_rhs: loops on the tensor cores, FP32 projections and
+    products), sampled l against the oracle: the projections over all l, the
+    loops and products at the sampled l."""
+    from oracle import projections as opj
+    c = W.config("cfg2")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.25, mu=-1.0, U=3.0)
+    s, p = make(case, torch, precision="bf16x3")
+    y = W.random_state(11, p.nl, p.nff, 0.5)
+    got = s.rhs(0.4, dev(torch, y)).cpu().numpy()
+    check_device(s)
+    sel = [0, 37, 288, 300, 575]
+    V = opj.project(p, y)
+    chi = olo.chi_dot(p, 0.4, sel)
+    ref = orhs.products(V[:, sel], chi[0], chi[1])
+    err = rel(got[:, sel], ref)
+    print(f"cfg2 bf16x3 RHS (sampled l): rel err {err:.2e}")
+    assert err < BOUND["bf16x3"]
+
+
 def test_large_size_loops_sampled_bf16x3(torch):
     """The large workload (coarse 48x48, Nff = 25: 169 allowed pairs, the
     widest N the two pipeline stages hold; fine 960x960) on the tensor cores,
