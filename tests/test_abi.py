@@ -108,4 +108,6 @@ def test_null_arguments_rejected(abi):
     assert L.tufrg_rhs(None, 1.0, None, None, None) == -1
     assert L.tufrg_loops(None, 1.0, None, None) == -1
     assert L.tufrg_flow(None, None, None, None, None) == -1
+    assert L.tufrg_check(None, None) == -1
+    assert L.tufrg_selftest_wait(None, 1000, None) == -1
     assert abi.tufrg_status_string(-3) == "non-finite state"
