@@ -68,3 +68,11 @@ def test_ranks_draw_disjoint_scan_points():
     key = lambda q: (q["tp"], q["density"], q["U"], q["shells"], q["nf"])
     assert not set(map(key, a)) & set(map(key, b))
     assert np.all(np.isfinite([q["tp"] for q in a + b]))
+
+
+def test_ranks_run_different_points_of_the_large_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    tps = [bench.rank_tprime(r, "cfg5") for r in range(8)]
+    assert len(set(tps)) == 8 and tps[0] == W.config("cfg5")["tp"]
