@@ -170,9 +170,8 @@ __global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __
 }
 
 // Term form (Nff <= 13).  kTermsL transfer momenta of one target channel per
-// CTA: each term of
-// the (scale-independent) overlap lists and its Fourier key are read once
-// and applied to all of them (only the phases e^{i l.Y} differ).
+// CTA: each term of the (scale-independent) overlap lists and its Fourier key
+// are read once and applied to all of them (only the phases e^{i l.Y} differ).
 constexpr int kTermsL = 4;
 constexpr int kTermBatch = 8;
 
@@ -297,12 +296,11 @@ __global__ void __launch_bounds__(256)
 }
 
 // Grouped form (Nff >= 21).  One CTA per (target channel, phase position Y):
-// G(Y) from the keys of its
-// terms, then H(Y) = c^T G(Y) c, written over the point's bond-space
-// workspace (the bond-space propagators are no longer needed once the keys
-// exist).  Every thread loads one term slot and its key at once (two round
-// trips); the first term of each output pair then adds its pair's terms in
-// slot order.
+// G(Y) from the keys of its terms, then H(Y) = c^T G(Y) c, written over the
+// point's bond-space workspace (the bond-space propagators are no longer
+// needed once the keys exist).  Every thread loads one term slot and its key
+// at once (two round trips); the first term of each output pair then adds
+// its pair's terms in slot order.
 template <class T, int NF>
 __global__ void __launch_bounds__(256)
     overlap_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
