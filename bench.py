@@ -192,19 +192,29 @@ def loop_counts(tufrg, bonds, ncx, ncy, nfx, nfy):
     nff = len(par)
     npair = int(sum(1 for m in range(nff) for n in range(m, nff) if par[m] * par[n] > 0))
     kdim = nfx * nfy // 2 + 2
-    # rows: every l on the zone boundary, and one l per C4v orbit of interior
-    # l on square grids (per pair {l, -l} otherwise): the loops of the other
-    # members follow by the point-group covariance
-    boundary = ncx + ncy - 1
-    if ncx == ncy and nfx == nfy:
-        h = ncx // 2
-        orbits = {frozenset(((a, b), (-b, a), (-a, -b), (b, -a), (a, -b), (-a, b), (b, a),
-                             (-b, -a)))
-                  for a in range(-h + 1, h) for b in range(-h + 1, h)}
-        nrow = boundary + len(orbits)
-    else:
-        nrow = boundary + ((ncx - 1) * (ncy - 1) + 1) // 2
-    return npair, kdim, nrow
+    return npair, kdim, loop_rows(ncx, ncy, nfx, nfy)
+
+
+def loop_rows(ncx, ncy, nfx, nfy):
+    """Loop rows: one per class of l under the point-group elements g that map
+    l into the zone [-pi, pi)^2 without a fold (the loops of g l follow from
+    those of l by covariance); C4v on square grids, {e, -1} otherwise."""
+    square = ncx == ncy and nfx == nfy
+    group = ([(1, 0, 0, 1), (0, -1, 1, 0), (-1, 0, 0, -1), (0, 1, -1, 0), (1, 0, 0, -1),
+              (-1, 0, 0, 1), (0, 1, 1, 0), (0, -1, -1, 0)] if square
+             else [(1, 0, 0, 1), (-1, 0, 0, -1)])
+    hx, hy = ncx // 2, ncy // 2
+    served, rows = set(), 0
+    for ux in range(-hx, ncx - hx):
+        for uy in range(-hy, ncy - hy):
+            if (ux, uy) in served:
+                continue
+            rows += 1
+            for a, b, c, d in group:
+                vx, vy = a * ux + b * uy, c * ux + d * uy
+                if -hx <= vx < ncx - hx and -hy <= vy < ncy - hy:
+                    served.add((vx, vy))
+    return rows
 
 
 def cpu_oracle_rhs_sample(tp, l_sample=48, name=WORKLOAD):

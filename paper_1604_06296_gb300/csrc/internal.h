@@ -106,6 +106,7 @@ struct PointDesc {
   const int* rowoff;
   const unsigned char* Fhi;
   const unsigned char* Flo;
+  const void* tmap;       // two TMA tensor maps (F hi, F lo), 128 bytes each
   const int* rowimg_ptr;  // [nrow + 1] CSR of the (l, g) each row serves
   const int2* rowimg;
   const int2* lrow;       // [nl] (row, g) serving each l
@@ -222,12 +223,13 @@ struct tufrg_ctx {
   int loop_prec = TUFRG_FP64;      // precision of the flow's next loop contractions
   int tc_hx = 0, tc_hy = 0, tc_wy = 0;  // halo of the extended table, its row width
   float4* d_ext = nullptr;         // halo table over [(nfx+2hx)*wy] points, FP32 per scale:
-                                   // A = 1/(Omega+|xi|), u = xi A (BF16X3: pair layout)
+                                   // A = 1/(Omega+|xi|), xi (BF16X3: pair layout)
   float* d_xiext = nullptr;        // [(nfx+2hx)*wy] xi at the halo table's points, FP32
   int* d_rowoff = nullptr;         // [nrow] sx * wy + sy
   int* d_kbase = nullptr;          // [tc_kpad] loop point offsets in the halo table
   unsigned char* d_Fhi = nullptr;  // [tc_npad][tc_kpad] high parts of F (bf16 or tf32)
   unsigned char* d_Flo = nullptr;  // [tc_npad][tc_kpad] low parts
+  void* d_tmap = nullptr;          // TMA tensor maps of d_Fhi, d_Flo (2 x 128 bytes)
   int* d_err = nullptr;            // device error word (bounded waits that gave up)
 
   // device: workspace
@@ -345,6 +347,8 @@ tufrg_status launch_tc_rows_multi(const MultiView& v, cudaStream_t st);
 tufrg_status launch_fp64_rows(const double* partial, int mpad, int ksplit, int npair, int nrow,
                               double* rowres, cudaStream_t st);
 size_t tc_smem_bytes(int npad);
+// TMA tensor maps of a context's F parts into c->d_tmap
+tufrg_status make_f_tensor_maps(tufrg_ctx* c, cudaStream_t st);
 int tc_k_per_block(int prec);
 int table_ctas(int n_ext);
 tufrg_status prepare_loops_tc_multi(const MultiView& v);

@@ -1,4 +1,4 @@
-// Step ii (Eq. chis) on the 5th-generation tensor cores (tcgen05, TMEM).
+// Step ii (Eq. chis) on the 5th-generation tensor cores (tcgen05, TMEM, TMA).
 //
 //   chi_dot_{pair}(l) = sum_k F_{pair}(k) W(k, l)
 //
@@ -8,22 +8,28 @@
 // W_hi F_hi + W_lo F_hi + W_hi F_lo accumulated in FP32 in tensor memory;
 // the split-K partial sums of each CTA are combined (fixed order, compensated
 // FP32 pairs, FP64 result) by a second kernel.  The propagator operand W is
-// generated in registers from the per-scale FP32 table (A = 1/(Omega + |xi|),
-// u = xi A, extended by a wrap-around halo so p +- l/2 is one add from p)
-// with the same closed-form frequency integral as the FP64 path, and written
+// generated in registers from the per-scale FP32 table (A = 1/(Omega + |xi|)
+// and xi, extended by a wrap-around halo so p +- l/2 is one add from p) with
+// the same closed-form frequency integral as the FP64 path, and written
 // straight into the 128B-swizzled K-major shared-memory layout the MMA reads;
-// F (scale independent) is staged with cp.async.  Both channels share W's
-// table reads and divisions and have their own accumulator.
+// F (scale independent) arrives by TMA (one 2-D box per K-block and part).
+// Both channels share W's table reads and divisions and have their own
+// accumulator.
 //
 // Persistent CTAs (one per SM, 17 warps) take work items -- (point, tile of
-// 128 l-rows, range of K-blocks) of any number of points -- from a queue
-// ordered by cost.  Warps 0-15 produce the W tiles of a K-block (8 rows each,
-// lanes along k, table loads of several rows in flight) and stage F, then
-// read the accumulators out (warp w reads the 32 TMEM lanes 32 (w % 4).. of
-// channel (w / 4) % 2, half of the columns).  Warp 16 owns TMEM and one of
-// its threads issues the MMAs.  Two pipeline stages, mbarriers full/empty, whose phases
-// run on across items; every wait is bounded in time and a timeout sets an
-// error word, stops the pipeline, drains the issued MMAs and frees TMEM.
+// up to 128 l-rows, range of K-blocks) of any number of points -- from a
+// queue ordered by cost.  The rows of a point are spread evenly over its
+// tiles.  Warps 0-15 produce the W tiles of a K-block (8 rows each, lanes
+// along k, table loads of several rows in flight; one thread of warp 0 also
+// starts the F copies), then read the accumulators out (warp w reads the 32
+// TMEM lanes 32 (w % 4).. of channel (w / 4) % 2, half of the columns).
+// Warp 16 owns TMEM and one of its threads issues the MMAs.  Two pipeline
+// stages, mbarriers full (producers), tma (F bytes) and empty (MMAs done),
+// whose phases run on across items; every wait is bounded in time and a
+// timeout sets an error word, stops the pipeline, waits for the copies in
+// flight, drains the issued MMAs and frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -82,36 +88,78 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
   }
 }
 
+// paired FP32 arithmetic (one instruction for both lanes of a float2)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+      " sub.rn.f32x2 z, x, y;\n mov.b64 {%0, %1}, z;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// approximate reciprocal (PTX rcp.approx: relative error below 2^-22)
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Constants of the weight formulas at one scale Omega.
+struct WConst {
+  float2 c5om, cm2om2, cm3, c2om2, cm2om, c3;
+  __device__ explicit WConst(float om)
+      : c5om{5.f * om, 5.f * om},
+        cm2om2{-2.f * om * om, -2.f * om * om},
+        cm3{-3.f, -3.f},
+        c2om2{2.f * om * om, 2.f * om * om},
+        cm2om{-2.f * om, -2.f * om},
+        c3{3.f, 3.f} {}
+};
 
 // Closed-form frequency integral of the two loops for two propagator pairs
-// at once, with paired FP32 instructions, from the table values A and u of
-// both propagators (a at p + l/2, b at p - l/2).  With x = |xi| = |u| / A and
-// Omega A = 1 - |u|:
-//   D = A_a A_b (5 Omega (A_a + A_b) - 3 - 2 Omega^2 (A_a^2 + A_a A_b + A_b^2))
-//   S = (H_a + H_b) / (x_a + x_b),  H = x (3x + Omega) A^3 = |u| (1 + 2|u|) A,
-//     = A_a A_b (H_a + H_b) / (|u_a| A_b + |u_b| A_a)
-// the particle-particle weight is S for propagators of one sign, D else, and
-// the particle-hole weight the other one.  The table holds |u| no smaller
-// than 1e-30 (with the sign of xi): at x_a = x_b = 0 S is then A_a A_b =
-// 1/Omega^2, its limit, and elsewhere the floor is far below FP32 resolution.
-__device__ __forceinline__ void weights_au(const float2 Aa, const float2 usa, const float2 Ab,
-                                           const float2 usb, float om, float om2, float2& wpp,
-                                           float2& wph) {
-  const float2 sa = __fadd2_rn(Aa, Ab), pa = __fmul2_rn(Aa, Ab);
-  const float2 t1 = __ffma2_rn(sa, sa, make_float2(-pa.x, -pa.y));
-  const float2 t2 = __ffma2_rn(make_float2(5.f * om, 5.f * om), sa, make_float2(-3.f, -3.f));
-  const float2 br = __ffma2_rn(make_float2(-2.f * om2, -2.f * om2), t1, t2);
-  const float2 D = __fmul2_rn(pa, br);
-  const float2 ua = make_float2(fabsf(usa.x), fabsf(usa.y));
-  const float2 ub = make_float2(fabsf(usb.x), fabsf(usb.y));
-  const float2 ha = __fmul2_rn(ua, __ffma2_rn(ua, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
-  const float2 hb = __fmul2_rn(ub, __ffma2_rn(ub, make_float2(2.f, 2.f), make_float2(1.f, 1.f)));
-  const float2 num = __fmul2_rn(pa, __ffma2_rn(ha, Aa, __fmul2_rn(hb, Ab)));
-  const float2 den = __ffma2_rn(ua, Ab, __fmul2_rn(ub, Aa));
-  const float2 sg = __fmul2_rn(usa, usb);
-  const float S0 = __fdividef(num.x, den.x), S1 = __fdividef(num.y, den.y);
-  wpp = make_float2(sg.x > 0.f ? S0 : D.x, sg.y > 0.f ? S1 : D.y);
-  wph = make_float2(sg.x > 0.f ? D.x : S0, sg.y > 0.f ? D.y : S1);
+// at once, from the table values A = 1/(Omega + |xi|) and the signed xi of
+// both propagators (a at p + l/2, b at p - l/2).  With h(x) = x (Omega + 3x)
+// / (Omega + x)^3 (so that J = -sgn(xi) h(|xi|) / 4):
+//   D = h[|xi_a|, |xi_b|]
+//     = A_a A_b (5 Omega (A_a + A_b) - 3 - 2 Omega^2 (A_a^2 + A_a A_b + A_b^2)),
+//   S = (h_a + h_b) / (|xi_a| + |xi_b|) = (Hs_a + Hs_b') / (xi_a + xi_b'),
+// with Hs = sgn(xi) h(|xi|) = xi A^2 (3 - 2 Omega A) (Omega + 3|xi| = 3/A -
+// 2 Omega) and xi_b' = xi_b carried over to the sign of xi_a (Hs is linear
+// in the sign): numerator and denominator of S are sums of two terms of one
+// sign, and 3 - 2 Omega A lies in [1, 3).  The particle-particle weight is S
+// for propagators of one sign, D else, and the particle-hole weight the
+// other one (the -1/4 and +1/4 are applied in the combination of the partial
+// sums).  The table holds |xi| no smaller than 1e-30 (sign kept): at xi_a =
+// xi_b = 0 S is then 1/Omega^2, its limit.
+__device__ __forceinline__ void weights(const float2 Aa, const float2 xa, const float2 Ab,
+                                        const float2 xb, const WConst& k, float2& wpp,
+                                        float2& wph) {
+  const float2 sa = add2(Aa, Ab), pa = mul2(Aa, Ab);
+  const float2 q = fma2(sa, k.cm2om2, k.c5om);   // 5 Omega - 2 Omega^2 sa
+  const float2 r = fma2(sa, q, k.cm3);           // -3 + 5 Omega sa - 2 Omega^2 sa^2
+  const float2 D = mul2(pa, fma2(pa, k.c2om2, r));
+  const float2 va = mul2(Aa, fma2(Aa, k.cm2om, k.c3));  // A (3 - 2 Omega A)
+  const float2 vb = mul2(Ab, fma2(Ab, k.cm2om, k.c3));
+  const float2 xs = make_float2(copysignf(xb.x, xa.x), copysignf(xb.y, xa.y));
+  const float2 num = fma2(mul2(xa, Aa), va, mul2(mul2(xs, Ab), vb));
+  const float2 den = add2(xa, xs);
+  const float2 S = mul2(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+  const float2 sg = mul2(xa, xb);
+  const bool s0 = sg.x > 0.f, s1 = sg.y > 0.f;
+  wpp = make_float2(s0 ? S.x : D.x, s1 ? S.y : D.y);
+  wph = make_float2(s0 ? D.x : S.x, s1 ? D.y : S.y);
+}
+
+// bf16x2 high parts (round to nearest) and low parts (the remainders,
+// rounded) of two floats
+__device__ __forceinline__ void split_bf16(float2 w, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __float22bfloat162_rn(w);
+  const __nv_bfloat162 l = __float22bfloat162_rn(sub2(w, __bfloat1622float2(h)));
+  std::memcpy(&hi, &h, 4);
+  std::memcpy(&lo, &l, 4);
 }
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -147,10 +195,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   const uint32_t stage_bytes = 4u * kWTile + 2u * fmax;
   // per stage: W pp_hi, pp_lo, ph_hi, ph_lo, F hi, F lo
   const uint32_t ctrl = base + 2u * stage_bytes;
-  const uint32_t bar_full = ctrl, bar_empty = ctrl + 16, bar_done = ctrl + 32;
+  const uint32_t bar_full = ctrl, bar_tma = ctrl + 16, bar_empty = ctrl + 32,
+                 bar_done = ctrl + 48;
   unsigned char* gctrl = gbase + 2u * stage_bytes;
-  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(gctrl + 48);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gctrl + 52);
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(gctrl + 56);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gctrl + 60);
   volatile int4* s_item = reinterpret_cast<volatile int4*>(gctrl + 64);
   int* s_off = reinterpret_cast<int*>(gctrl + 128);     // 3xTF32: row offsets
   int2* s_idx = reinterpret_cast<int2*>(gctrl + 128);   // BF16X3: row gather indices
@@ -159,6 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(bar_full + 8 * s, kProducers);
+      mbar_init(bar_tma + 8 * s, 1);
       mbar_init(bar_empty + 8 * s, 1);
     }
     mbar_init(bar_done, 1);
@@ -184,6 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 
   uint32_t g = 0;  // K-blocks this CTA has put through the pipeline
   uint32_t j = 0;  // items this CTA has finished (phase of bar_done)
+  int tma_last = -1;  // warp 0, lane 0: last K-block (count g) whose F it requested
   for (;;) {
     if (threadIdx.x == 0) {
       const int it = atomicAdd(a.counter, 1);
@@ -201,8 +252,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       __syncthreads();
       continue;
     }
-    const int row0 = tile * kRows;
-    const int nvalid = min(kRows, pd.nrow - row0);  // rows of this tile with an l
+    // rows [row0, row0 + nvalid) of the point: its rows spread evenly over
+    // its tiles (at most 128 each)
+    const int tiles = pd.nrow_pad / kRows;
+    const int row0 = (tile * pd.nrow) / tiles;
+    const int nvalid = ((tile + 1) * pd.nrow) / tiles - row0;
     if constexpr (P::kPerLane == 2) {
       // every lane's first loop point has the parity pib of the first loop
       // point (neighbour pairs iy, iy + 1 with iy even, even row width), so
@@ -222,20 +276,16 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     }
     __syncthreads();
     const int npad = pd.npad, nsets = pd.nsets;
-    const double omd = pd.lam[0];
-    const float om = (float)omd, om2 = (float)(omd * omd);
 
     if (warp < kProducers) {
       // ---------------------------------------------------------- producers
-      // BF16X3: pairs (A_q, A_q+1, u_q, u_q+1) of even q at ext, of odd q at
-      // ext + (n_ext + 1) / 2, read at the row's s_idx; 3xTF32: (A_q, u_q)
-      // per point
+      // BF16X3: pairs (A_q, A_q+1, xi_q, xi_q+1) of even q at ext, of odd q
+      // at ext + (n_ext + 1) / 2, read at the row's s_idx; 3xTF32: (A_q,
+      // xi_q) per point
       const float4* ext = pd.ext;
       const float2* ext2 = reinterpret_cast<const float2*>(pd.ext);
-      const unsigned char* Fhi = pd.Fhi;
-      const unsigned char* Flo = pd.Flo;
-      const size_t frow = (size_t)pd.kpad_tc * P::kElem;  // bytes per F row
-      const int fchunks = 8 * npad;  // 16-byte chunks per F tile
+      const WConst wk((float)pd.lam[0]);
+      const uint32_t fbytes = (uint32_t)npad * kRowBytes;  // one F part per K-block
       // this warp's rows with an l, in units of kUnitRows rows
       const int nrw = max(0, min(kRows / kProducers, (nvalid - warp + kProducers - 1) / kProducers));
       const int nunits = (nrw + kUnitRows - 1) / kUnitRows;
@@ -249,9 +299,9 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       auto load_unit = [&](int u, int pb, Buf& b) {
         if constexpr (P::kPerLane == 2) {  // one row, two loop points: one pair each side
           const int2 ix = s_idx[warp + kProducers * u];
-          const int hb = pb >> 1;
-          b.v[0] = __ldg(ext + (hb + ix.x));
-          b.v[1] = __ldg(ext + (hb + ix.y));
+          const float4* lb = ext + (pb >> 1);
+          b.v[0] = __ldg(lb + ix.x);
+          b.v[1] = __ldg(lb + ix.y);
         } else {  // two rows, one loop point
           const int off0 = s_off[warp + kProducers * (2 * u)];
           const int off1 = s_off[warp + kProducers * (2 * u + 1)];
@@ -261,44 +311,35 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
           b.v[3] = __ldg(ext2 + (pb - off1));
         }
       };
-      auto do_unit = [&](int u, uint32_t st, const Buf& b) {
+      auto do_unit = [&](int u, unsigned char* stg, const Buf& b) {
         float2 wpp, wph;
         if constexpr (P::kPerLane == 2)
-          weights_au(make_float2(b.v[0].x, b.v[0].y), make_float2(b.v[0].z, b.v[0].w),
-                     make_float2(b.v[1].x, b.v[1].y), make_float2(b.v[1].z, b.v[1].w), om, om2,
-                     wpp, wph);
+          weights(make_float2(b.v[0].x, b.v[0].y), make_float2(b.v[0].z, b.v[0].w),
+                  make_float2(b.v[1].x, b.v[1].y), make_float2(b.v[1].z, b.v[1].w), wk, wpp,
+                  wph);
         else
-          weights_au(make_float2(b.v[0].x, b.v[2].x), make_float2(b.v[0].y, b.v[2].y),
-                     make_float2(b.v[1].x, b.v[3].x), make_float2(b.v[1].y, b.v[3].y), om, om2,
-                     wpp, wph);
+          weights(make_float2(b.v[0].x, b.v[2].x), make_float2(b.v[0].y, b.v[2].y),
+                  make_float2(b.v[1].x, b.v[3].x), make_float2(b.v[1].y, b.v[3].y), wk, wpp,
+                  wph);
         if constexpr (PREC == TUFRG_BF16X3) {
           uint32_t v[4];
-          const __nv_bfloat162 ph = __float22bfloat162_rn(wpp);
-          const __nv_bfloat162 pl = __float22bfloat162_rn(
-              __fadd2_rn(wpp, make_float2(-__low2float(ph), -__high2float(ph))));
-          const __nv_bfloat162 hh = __float22bfloat162_rn(wph);
-          const __nv_bfloat162 hl = __float22bfloat162_rn(
-              __fadd2_rn(wph, make_float2(-__low2float(hh), -__high2float(hh))));
-          std::memcpy(&v[0], &ph, 4);
-          std::memcpy(&v[1], &pl, 4);
-          std::memcpy(&v[2], &hh, 4);
-          std::memcpy(&v[3], &hl, 4);
+          split_bf16(wpp, v[0], v[1]);
+          split_bf16(wph, v[2], v[3]);
           // plain stores (the compiler may interleave the units around them);
           // the proxy fence before the stage's arrive orders them for the MMA
-          unsigned char* dst = gbase + (st - base) + (warp + kProducers * u) * kRowBytes + swz;
+          unsigned char* dst = stg + (warp + kProducers * u) * kRowBytes + swz;
 #pragma unroll
           for (int t = 0; t < 4; ++t) *reinterpret_cast<uint32_t*>(dst + t * kWTile) = v[t];
         } else {
           const float w[2][2] = {{wpp.x, wph.x}, {wpp.y, wph.y}};
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
+          for (int r = 0; r < 2; ++r) {
             uint32_t v[4];
-            v[0] = tf32_rna(w[j][0]);
-            v[1] = tf32_rna(w[j][0] - __uint_as_float(v[0]));
-            v[2] = tf32_rna(w[j][1]);
-            v[3] = tf32_rna(w[j][1] - __uint_as_float(v[2]));
-            unsigned char* dst =
-                gbase + (st - base) + (warp + kProducers * (2 * u + j)) * kRowBytes + swz;
+            v[0] = tf32_rna(w[r][0]);
+            v[1] = tf32_rna(w[r][0] - __uint_as_float(v[0]));
+            v[2] = tf32_rna(w[r][1]);
+            v[3] = tf32_rna(w[r][1] - __uint_as_float(v[2]));
+            unsigned char* dst = stg + (warp + kProducers * (2 * u + r)) * kRowBytes + swz;
 #pragma unroll
             for (int t = 0; t < 4; ++t) *reinterpret_cast<uint32_t*>(dst + t * kWTile) = v[t];
           }
@@ -317,20 +358,21 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       for (int kb = 0; kb < cnt; ++kb) {
         const uint32_t gk = g + kb;
         const uint32_t s = gk & 1;
-        if (gk >= 2 && !mbar_wait(bar_empty + 8 * s, ((gk >> 1) + 1) & 1)) {
+        if (gk >= 2 && !mbar_wait_sleep(bar_empty + 8 * s, ((gk >> 1) + 1) & 1)) {
           atomicOr(a.err, 1);
           *abort_flag = 1;
         }
         if (*abort_flag) break;
         const uint32_t st = base + s * stage_bytes;
         const int k0 = (kb0 + kb) * KB;
-        const size_t fk = (size_t)k0 * P::kElem;
-        for (int c = threadIdx.x; c < 2 * fchunks; c += 32 * kProducers) {
-          const int t = c >= fchunks, rem = c - t * fchunks, row = rem >> 3, ch = rem & 7;
-          cp_async16(st + 4u * kWTile + t * fmax + row * kRowBytes + ((ch ^ (row & 7)) << 4),
-                     (t ? Flo : Fhi) + (size_t)row * frow + fk + ch * 16);
+        if (warp == 0 && lane == 0) {  // F of this K-block, both parts, by TMA
+          mbar_arrive_expect_tx(bar_tma + 8 * s, 2u * fbytes);
+          tma_load_2d(st + 4u * kWTile, pd.tmap, k0, 0, bar_tma + 8 * s);
+          tma_load_2d(st + 4u * kWTile + fmax, static_cast<const unsigned char*>(pd.tmap) + 128,
+                      k0, 0, bar_tma + 8 * s);
+          tma_last = (int)gk;
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        unsigned char* stg = gbase + (st - base);
         // (after the item's last K-block the ring gathers this one's first
         // units again: valid addresses, no branch)
         const int pbn = kb + 1 < cnt ? __ldg(pd.kbase + k0 + KB + P::kPerLane * lane) : pb;
@@ -344,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
               load_unit(t, pb, buf[t % kDepth]);
             else
               load_unit(t - kUnits, pbn, buf[t % kDepth]);
-            if (decltype(full)::value || u < nunits) do_unit(u, st, buf[u % kDepth]);
+            if (decltype(full)::value || u < nunits) do_unit(u, stg, buf[u % kDepth]);
           }
         };
         if (nunits == kUnits)
@@ -352,7 +394,6 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
         else
           kblock(std::false_type{});
         pb = pbn;
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar_full + 8 * s);
@@ -366,7 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       for (int kb = 0; kb < cnt; ++kb) {
         const uint32_t gk = g + kb;
         const uint32_t s = gk & 1;
-        if (!mbar_wait(bar_full + 8 * s, (gk >> 1) & 1)) {
+        if (!mbar_wait_sleep(bar_full + 8 * s, (gk >> 1) & 1) ||
+            !mbar_wait_sleep(bar_tma + 8 * s, (gk >> 1) & 1)) {
           atomicOr(a.err, 2);
           *abort_flag = 1;
         }
@@ -399,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     if (warp < kProducers) {
       // all producer warps: warp w reads TMEM lanes 32 (w % 4).. of channel
       // (w / 4) % 2, the 16-column blocks w / 8, w / 8 + 2, ...
-      const bool ok = mbar_wait(bar_done, j & 1);
+      const bool ok = mbar_wait_sleep(bar_done, j & 1);
       if (!ok) {
         atomicOr(a.err, 4);
         *abort_flag = 1;
@@ -431,8 +473,10 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) acc[e] += __uint_as_float(r[e]);
           }
+          if (row < nvalid) {  // the next tile's rows follow directly
 #pragma unroll
-          for (int e = 0; e < 16; ++e) out[(size_t)(c0 + e) * pd.nrow_pad] = acc[e];
+            for (int e = 0; e < 16; ++e) out[(size_t)(c0 + e) * pd.nrow_pad] = acc[e];
+          }
         }
       }
     }
@@ -442,6 +486,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  // after a timeout: the F copies this CTA started land before it exits
+  if (threadIdx.x == 0 && tma_last >= 0 && *abort_flag) {
+    const uint32_t gk = (uint32_t)tma_last;
+    if (!mbar_wait(bar_tma + 8 * (gk & 1), (gk >> 1) & 1)) atomicOr(a.err, 8);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -455,14 +504,15 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 
 constexpr int kTableBlock = 256;
 
-// Per-scale FP32 table (A, u) = (1/(Omega + |xi|), xi A) with a wrap-around
+// Per-scale FP32 table (A, xi) = (1/(Omega + |xi|), xi) with a wrap-around
 // halo of hx, hy points on each side, so that p +- l/2 needs no wrapping
 // (FP32 arithmetic: the table is FP32, and GB300's FP64 division would
-// dominate this kernel).  |u| is floored at 1e-30 (sign of xi kept).  BF16X3
-// layout: float4 (A_q, A_q+1, u_q, u_q+1) for even q in the first half, for
-// odd q in the second (the last entry repeated past the end); 3xTF32: float2
-// (A_q, u_q).  One thread per entry q, the neighbour's values by a shuffle.
-// Block 0 also resets the work-item counter of the contraction that follows.
+// dominate this kernel).  |xi| is floored at 1e-30 (sign kept).  BF16X3
+// layout: float4 (A_q, A_q+1, xi_q, xi_q+1) for even q in the first half,
+// for odd q in the second (the last entry repeated past the end); 3xTF32:
+// float2 (A_q, xi_q).  One thread per entry q, the neighbour's values by a
+// shuffle.  Block 0 also resets the work-item counter of the contraction
+// that follows.
 template <int PREC>
 __global__ void __launch_bounds__(kTableBlock)
     scale_table_ext_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
@@ -476,8 +526,7 @@ __global__ void __launch_bounds__(kTableBlock)
   const int q = (blockIdx.x - prefix[p]) * kTableBlock + threadIdx.x;
   auto entry = [&](int e) {
     const float xi = __ldg(pd.xiext + min(e, n_ext - 1));
-    const float A = __frcp_rn(omf + fabsf(xi));
-    return make_float2(A, copysignf(fmaxf(fabsf(xi * A), 1e-30f), xi));
+    return make_float2(__frcp_rn(omf + fabsf(xi)), copysignf(fmaxf(fabsf(xi), 1e-30f), xi));
   };
   const float2 a = entry(q);
   if constexpr (PREC == TUFRG_BF16X3) {
@@ -502,6 +551,43 @@ size_t tc_smem_bytes(int npad) {
 int tc_k_per_block(int prec) { return prec == TUFRG_BF16X3 ? kRowBytes / 2 : kRowBytes / 4; }
 
 int table_ctas(int n_ext) { return (n_ext + 1 + kTableBlock - 1) / kTableBlock; }
+
+// Tensor maps of the two parts of F ([npad rows][kpad] elements, k
+// contiguous): boxes of one K-block (128 bytes) by all npad rows, written
+// with the 128-byte swizzle of the MMA's K-major operand layout.  The two
+// 128-byte maps are stored one after the other in device memory.
+tufrg_status make_f_tensor_maps(tufrg_ctx* c, cudaStream_t st) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return TUFRG_ERR_CUDA;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int es = c->p.precision == TUFRG_BF16X3 ? 2 : 4;
+  CUtensorMap maps[2];
+  const cuuint64_t dims[2] = {(cuuint64_t)c->tc_kpad, (cuuint64_t)c->tc_npad};
+  const cuuint64_t strides[1] = {(cuuint64_t)c->tc_kpad * es};
+  const cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / es), (cuuint32_t)c->tc_npad};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  unsigned char* parts[2] = {c->d_Fhi, c->d_Flo};
+  for (int t = 0; t < 2; ++t)
+    if (encode(&maps[t], dt, 2, parts[t], dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return TUFRG_ERR_ARG;
+  static_assert(sizeof(CUtensorMap) == 128, "two maps of 128 bytes");
+  if (cudaMalloc(&c->d_tmap, sizeof(maps)) != cudaSuccess) return TUFRG_ERR_OOM;
+  TUFRG_CUDA(cudaMemcpyAsync(c->d_tmap, maps, sizeof(maps), cudaMemcpyHostToDevice, st));
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  return TUFRG_OK;
+}
 
 tufrg_status prepare_loops_tc_multi(const MultiView& v) {
   const int smem = smem_optin();

@@ -2,7 +2,8 @@
 // tables of the multi-point launches, and the work items of the persistent
 // tensor-core loop kernel.
 //
-// Work items are (point, tile of 128 l-rows, first K-block, K-blocks).  A
+// Work items are (point, tile of l-rows, first K-block, K-blocks); a point's
+// rows are spread evenly over ceil(nrow / 128) tiles.  A
 // point's loop sum over its nkb K-blocks is cut into ksplit = ceil(nkb/kbps)
 // ranges; each range of each tile is one item whose FP32 partial sum is
 // combined with the others (fixed order, compensated FP32 pairs, FP64
@@ -94,7 +95,8 @@ tufrg_status view_set_kbps(MultiView& v, int kbps, cudaStream_t st) {
     for (int sp = 0; sp < d.ksplit; ++sp) {
       const int kb0 = sp * kbps, cnt = std::min(kbps, d.nkb - kb0);
       long long cost = 0;  // producers: ~ valid rows per K-block; tensor cores: ~ pair columns
-      for (int t = 0; t < tiles; ++t) cost += (long long)cnt * (2 * std::min(128, d.nrow - 128 * t) + d.npad);
+      for (int t = 0; t < tiles; ++t)
+        cost += (long long)cnt * (2 * ((t + 1) * d.nrow / tiles - t * d.nrow / tiles) + d.npad);
       for (int t = 0; t < tiles; ++t) items.push_back({make_int4(i, t, kb0, cnt), cost});
     }
   }
@@ -178,6 +180,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.rowoff = c->d_rowoff;
     d.Fhi = c->d_Fhi;
     d.Flo = c->d_Flo;
+    d.tmap = c->d_tmap;
     d.rowimg_ptr = c->d_rowimg_ptr;
     d.rowimg = c->d_rowimg;
     d.lrow = c->d_lrow;

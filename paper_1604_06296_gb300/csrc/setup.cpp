@@ -6,8 +6,9 @@
 //   under p -> -p for parity-allowed pairs (pi_m pi_n = +1) and the others
 //   vanish (App. C), so the sum runs over half the zone;
 // * F[pair][k] = weight_k f_m(p_k) f_n(p_k) / Nf for the allowed pairs m <= n;
-// * loop rows: one per C4v orbit of interior l on square grids (one per
-//   pair {l, -l} otherwise, one per zone-boundary l) with the half-shift of
+// * loop rows: one per class of l under the point-group elements that map l
+//   into the zone without a fold (C4v orbits of interior l, classes of up to
+//   four zone-boundary l; {l, -l} off square grids) with the half-shift of
 //   the row's l on the fine grid (l/2 lands on the fine grid when
 //   nf % (2 nc) == 0 and nf % 4 == 0) and the list of (l, g) it serves;
 // * position-space projection data (Sec. 2.5: the Kronecker-delta overlaps
@@ -234,15 +235,18 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
       }
   c->npair = (int)c->pair_m.size();
 
-  // Rows of the loop contraction and the l each row serves.  For l inside
-  // the zone (no component at -pi) the loops are covariant under the point
-  // group: chi(g l) = R^g chi(l) R^g^T with f(g k) = R^g f(k) (App. C; xi is
-  // C4v symmetric and the folded g l has half momentum g l/2).  On square
-  // grids with a basis whose R^g are signed permutations, one row serves a
-  // whole C4v orbit of interior l; otherwise one row serves {l, -l}
-  // (g = inversion, R^g = diag(parity), which leaves the parity-allowed
-  // loops unchanged).  An l on the zone boundary keeps -pi/2 in a component
-  // after folding, which breaks the covariance: it gets its own row.
+  // Rows of the loop contraction and the l each row serves.  The loops are
+  // covariant, chi(g l) = R^g chi(l) R^g^T with f(g k) = R^g f(k) (App. C;
+  // xi is C4v symmetric), for every point-group element g that maps l into
+  // the zone [-pi, pi)^2 without a fold: the folded g l then has the half
+  // momentum g l/2.  For l inside the zone that is every g.  For l on the
+  // zone boundary (a component at -pi) it is the elements that keep each -pi
+  // component at -pi (four of eight for one such component, two for l =
+  // (-pi, -pi)); the others send it to +pi, whose fold moves the half
+  // momentum by pi.  These relations are closed under inverse and product,
+  // so one row serves each class.  On square grids with a basis whose R^g
+  // are signed permutations g ranges over C4v; otherwise over {e, -1}
+  // (R^g = diag(parity), which leaves the parity-allowed loops unchanged).
   std::vector<int> symperm, symsign;
   const bool c4v = c->ncx == c->ncy && c->nfx == c->nfy && B.point_group(symperm, symsign);
   if (!c4v) {
@@ -259,13 +263,14 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     for (int jy = 0; jy < c->ncy; ++jy) {
       const int l = jx * c->ncy + jy;
       if (served[l]) continue;
-      const bool interior = jx != 0 && jy != 0;
-      for (int g = 0; g < (interior ? 8 : 1); ++g) {
+      for (int g = 0; g < 8; ++g) {
         if (!c4v && g != 0 && g != 2) continue;
-        // g acts on u = j - n/2 (k = 2 pi u / n); interior images stay interior
+        // g acts on u = j - n/2 (k = 2 pi u / n, u in [-n/2, n/2)); an image
+        // outside that range would need a fold
         const int ux = jx - hcx, uy = jy - hcy;
         const int vx = kC4v[g][0][0] * ux + kC4v[g][0][1] * uy;
         const int vy = kC4v[g][1][0] * ux + kC4v[g][1][1] * uy;
+        if (vx < -hcx || vx >= c->ncx - hcx || vy < -hcy || vy >= c->ncy - hcy) continue;
         const int lg = (vx + hcx) * c->ncy + (vy + hcy);
         if (served[lg]) continue;
         served[lg] = 1;
@@ -307,6 +312,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_kbase = dl->d_kbase;
     c->d_Fhi = dl->d_Fhi;
     c->d_Flo = dl->d_Flo;
+    c->d_tmap = dl->d_tmap;
     c->d_shift = dl->d_shift;
     c->d_rowimg_ptr = dl->d_rowimg_ptr;
     c->d_rowimg = dl->d_rowimg;
@@ -425,6 +431,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
       }
     TUFRG_CHECK(upload(&c->d_Fhi, fh, st));
     TUFRG_CHECK(upload(&c->d_Flo, fl, st));
+    TUFRG_CHECK(make_f_tensor_maps(c, st));
   }
   TUFRG_CHECK(alloc(&c->d_err, 1));
   TUFRG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
@@ -576,7 +583,8 @@ void free_device(tufrg_ctx* c) {
   for (void* p : own)
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {
-    void* loops[] = {c->d_rowoff,  c->d_kbase,     c->d_Fhi,    c->d_Flo,     c->d_rowimg_ptr,
+    void* loops[] = {c->d_rowoff,  c->d_kbase,     c->d_Fhi,    c->d_Flo,     c->d_tmap,
+                     c->d_rowimg_ptr,
                      c->d_rowimg,  c->d_lrow,      c->d_symperm, c->d_symsign, c->d_kidx,
                      c->d_lgather,
                      c->d_F,       c->d_pairidx,

@@ -1,4 +1,4 @@
-// tcgen05 / mbarrier / cp.async helpers shared by the tensor-core kernels
+// tcgen05 / mbarrier / cp.async / TMA helpers shared by the tensor-core kernels
 // (loop contraction, surrogate network GEMMs).  Every wait is bounded in
 // time (%globaltimer) so that a stalled pipeline returns an error instead of
 // hanging the GPU.
@@ -38,6 +38,50 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
+}
+
+// As mbar_try_wait, but the thread may sleep up to hint_ns for the phase
+// (the instruction returns as soon as the phase completes).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Sleeping wait for the phase of the given parity (pipeline waits whose
+// other side may take long); gives up after kWaitNs.
+__device__ inline bool mbar_wait_sleep(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+}
+
+// Arrival that also announces bytes an asynchronous copy will complete on
+// the barrier.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// TMA: the box at (x, y) of a 2-D tensor map (in global memory) into shared
+// memory at dst; completes its bytes on bar.  x * element size must be a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 
 // Waits for the phase of the given parity; gives up after limit_ns.

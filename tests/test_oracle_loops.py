@@ -148,3 +148,32 @@ def test_point_group_covariance_interior_l():
             lj = index[tuple(S @ lu[li])]
             for chi in (pp, ph):
                 assert np.allclose(chi[lj], C @ chi[li] @ C.T, atol=1e-13 * np.abs(chi).max())
+
+
+def test_point_group_covariance_boundary_l():
+    """App. C covariance on the zone boundary: chi(g l) = C chi(l) C^T holds
+    for the elements g that map l into [-pi, pi)^2 without a fold (those
+    that keep a -pi component at -pi), and fails for the others (the fold
+    of +pi to -pi moves the half momentum l/2 by pi)."""
+    prob = make_problem(shells=3, nc=6, nf=24, tp=-0.3)
+    pp, ph = loops.chi_dot(prob, 0.3)
+    lu = prob.l_units
+    n = prob.ncx
+    index = {tuple(u): i for i, u in enumerate(lu)}
+    boundary = np.nonzero(np.any(lu == -n, axis=1))[0]
+    held, broken = 0, 0
+    for S in ffm.POINT_GROUP:
+        C = prob.basis.rep_matrix(S)
+        for li in boundary:
+            v = S @ lu[li]
+            lj = index[tuple(((v + n) % (2 * n)) - n)]
+            err = max(np.abs(chi[lj] - C @ chi[li] @ C.T).max() / np.abs(chi).max()
+                      for chi in (pp, ph))
+            if np.all((v >= -n) & (v < n)):
+                assert err <= 1e-13
+                held += 1
+            else:
+                broken += err > 1e-3
+    # (-pi, q): 4 elements each; (-pi, -pi): 2 (e and the diagonal mirror)
+    assert held == 4 * (2 * n - 2) + 2
+    assert broken > 0

@@ -103,3 +103,23 @@ def batch_points(n: int, seed: int = BATCH_SEED) -> list[dict]:
         pts.append(dict(t=1.0, tp=tp, U=U, density=dens, nc=nc, nf=nf,
                         shells=shells))
     return pts
+
+
+# Large-scale batch: (t', mu) points around the large single point, all on
+# its grids (coarse 48x48, Nff = 25, fine 960x960) and with its U.
+LARGE_BATCH_SEED = 1604062961
+
+
+def large_batch_points(n: int = 16, seed: int = LARGE_BATCH_SEED) -> list[dict]:
+    """n seeded (t', mu) points: t' ~ U[-0.4, -0.2], mu = 4 t' + d with
+    d ~ U[-0.1, 0.1] (near van Hove filling); the other parameters and the
+    grids are those of the large workload."""
+    c = CONFIGS["cfg5"]
+    rng = np.random.default_rng(seed)
+    pts = []
+    for _ in range(n):
+        tp = float(rng.uniform(-0.4, -0.2))
+        mu = 4.0 * tp + float(rng.uniform(-0.1, 0.1))
+        pts.append(dict(t=c["t"], tp=tp, mu=mu, U=c["U"], nc=c["nc"], nf=c["nf"],
+                        shells=c["shells"]))
+    return pts
