@@ -3,15 +3,21 @@
 A step is one adaptive Dormand-Prince step of the flow (six right-hand-side
 evaluations -- per-scale tables, loop contraction, projections, products --
 plus the stage combinations, error norm, step control and accept), run by
-tufrg_flow_step on the production workload (t-t' Hubbard, t' = -0.25,
-mu = 4t', U = 3, coarse 24x24, Nff = 13, fine 480x480) starting at
-Lambda0 = 10 from the bare interaction.  value = right-hand-side evaluations
-per second over exactly K timed steps (CUDA events per step on the calling
-stream; L2 flushed between steps).  Under torchrun every rank runs its own
+tufrg_flow_step.  The default workload is the large single point (t-t'
+Hubbard, t' = -0.3, mu = 4t', U = 3.5, coarse 48x48, Nff = 25, fine 960x960)
+in BF16x3, starting at Lambda0 = 10 from the bare interaction.  value =
+right-hand-side evaluations per second over exactly K timed steps (CUDA
+events per step on the calling stream; the tables and states of the step are
+larger than L2 and L2 is flushed between steps as well).  The line also
+carries the FP64 and 3xTF32 paths on the same point, a flow to Lambda_c at
+the point, the flow-time comparison at equal Lambda_c accuracy on the
+production point, the end-to-end rate through the C ABI with host buffers,
+and the oracle on the host cores.  Under torchrun every rank runs its own
 phase-diagram point (independent problems, no collective): weak scaling.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload on this machine's host cores.
+workload on this machine's host cores (one single-threaded worker process
+per core).
 """
 from __future__ import annotations
 
@@ -34,7 +40,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "fRG RHS evals/s & flow time to Λ_c (mixed/learned vs FP64 GPU, same acc.)"
 UNIT = "RHS evals/s"
-WORKLOAD = "cfg2"
+WORKLOAD = "cfg5"
 L2_FLUSH_BYTES = 512 << 20
 # the library computes the projections of a view in the grouped form (one more
 # kernel per right-hand side) when one of its points has this many form factors
@@ -217,64 +223,136 @@ def loop_rows(ncx, ncy, nfx, nfy):
     return rows
 
 
-def cpu_oracle_rhs_sample(tp, l_sample=48, name=WORKLOAD):
-    """One FP64 oracle right-hand side at the workload, loops on l_sample of
-    the Nl points (scaled to all Nl), projections and products on all l.  At
-    the large workload the projections are timed on one of their six
-    (target, source) pairs and scaled by six (the full set takes ~50 s)."""
-    from oracle import loops, projections, rhs
+# --------------------------------------------------------------------------
+# The FP64 oracle on the host cores: one single-threaded worker process per
+# core (spawned: the parent may hold a CUDA context), each with the workload's
+# problem and a seeded state.  A sample is the loops and products of some l
+# (one l per task) and the six cross projections (one pair per task).
+_ORACLE = {}
+
+
+def _oracle_init(name, tp):
     from oracle.model import Problem
     c = W.config(name)
     p = Problem(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"], c["nc"],
                 c["nf"], c["nf"]).check()
-    y = W.random_state(0, p.nl, p.nff, 0.1)
-    sel = np.linspace(0, p.nl - 1, l_sample).astype(int)
+    _ORACLE["p"] = p
+    _ORACLE["y"] = W.random_state(0, p.nl, p.nff, 0.1)
+    p.f_fine  # noqa: B018 -- the scale-independent form factors, built once
+
+
+def _oracle_loops_products(ls, lam):
+    from oracle import loops, rhs
+    p, y = _ORACLE["p"], _ORACLE["y"]
+    ls = np.asarray(ls)
     t0 = time.perf_counter()
-    chi = loops.chi_dot(p, 0.5, sel)
-    t_loops = time.perf_counter() - t0
+    chi = loops.chi_dot(p, lam, ls)
+    rhs.products(y[:, ls], *chi)  # V stands in for the projected couplings: same cost
+    return time.perf_counter() - t0
+
+
+def _oracle_pair(target, source):
+    from oracle import projections
+    p, y = _ORACLE["p"], _ORACLE["y"]
     t0 = time.perf_counter()
-    if name == "cfg5":
-        projections.project_pair(p, "P", "C", y[1])
-        t_proj = 6.0 * (time.perf_counter() - t0)
-        V = y  # the products' cost does not depend on the values
-        proj = "projections: one of the six (target, source) pairs on all l (x6)"
-    else:
-        V = projections.project(p, y)
-        t_proj = time.perf_counter() - t0
-        proj = "projections on all l"
-    t0 = time.perf_counter()
-    rhs.products(V[:, sel], *chi)
-    t_prod = time.perf_counter() - t0
-    scale = p.nl / l_sample
-    est = t_loops * scale + t_proj + t_prod * scale
-    sample = (f"oracle RHS at the workload: loops on {l_sample} of {p.nl} l "
-              f"(x{scale:g}), {proj}, products on the sampled l (x{scale:g})")
-    return est, sample
+    projections.project_pair(p, target, source, y["PCD".index(source)])
+    return time.perf_counter() - t0
+
+
+class OracleSample:
+    """Timed samples of the oracle right-hand side on the host cores."""
+
+    PAIRS = (("P", "C"), ("P", "D"), ("C", "P"), ("C", "D"), ("D", "P"), ("D", "C"))
+
+    def __init__(self, name, tp, workers=None):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"  # read by the workers' numpy at import
+        self.workers = int(workers or os.cpu_count() or 1)
+        self.nl = W.config(name)["nc"] ** 2
+        self.pool = ProcessPoolExecutor(self.workers, mp_context=mp.get_context("spawn"),
+                                        initializer=_oracle_init, initargs=(name, tp))
+        self.next_l = 0
+
+    def loops(self, lam=0.5):
+        """Wall seconds of the loops and products of one l per worker (the
+        next l of the grid in turn)."""
+        ls = [(self.next_l + i) % self.nl for i in range(self.workers)]
+        self.next_l = (self.next_l + self.workers) % self.nl
+        t0 = time.perf_counter()
+        list(self.pool.map(_oracle_loops_products, [[q] for q in ls], [lam] * len(ls)))
+        return time.perf_counter() - t0
+
+    def projections(self):
+        """Wall seconds of the six cross projections, one per worker."""
+        t0 = time.perf_counter()
+        list(self.pool.map(_oracle_pair, *zip(*self.PAIRS)))
+        return time.perf_counter() - t0
+
+    def rhs_seconds(self, t_loops, t_proj):
+        """Wall seconds of one oracle RHS over all l on these workers: the
+        loops and products of `workers` l take t_loops, the projections t_proj."""
+        return t_loops * self.nl / self.workers + t_proj
+
+    def close(self):
+        self.pool.shutdown()
+
+
+def cpu_baseline(name, tp):
+    """The oracle RHS at the workload on the host cores, from a bounded sample."""
+    o = OracleSample(name, tp)
+    try:
+        o.loops()                      # workers start, problem built
+        t_loops = o.loops()
+        t_proj = o.projections()
+    finally:
+        o.close()
+    est = o.rhs_seconds(t_loops, t_proj)
+    return {"value": 1.0 / est, "unit": UNIT, "cores": o.workers, "kind": "oracle",
+            "extrapolated": True, "rhs_seconds_extrapolated": est,
+            "measured": {"loops_products_s": t_loops, "l_per_sample": o.workers,
+                         "projections_s": t_proj},
+            "sample": (f"FP64 oracle, {o.workers} single-threaded worker processes: loops and "
+                       f"products of {o.workers} of {o.nl} l (one per worker) and the six cross "
+                       "projections (one per worker) timed; the RHS over all l extrapolated")}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only."""
+    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only.
+    Each step is a measured sample: the loops and products of one l per
+    worker.  The projections (independent of the number of l) are timed once,
+    after the warm-up; value is the extrapolated RHS rate."""
     if rank != 0:
         return 0
-    tp = W.CFG2_TPRIME[1]
-    for _ in range(args.warmup):
-        cpu_oracle_rhs_sample(tp, l_sample=24)
-    times = []
-    sample = ""
-    t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        est, sample = cpu_oracle_rhs_sample(tp, l_sample=24)
-        times.append(est)
-    wall = time.perf_counter() - t_wall
-    value = len(times) / sum(times)
+    name = args.workload if args.workload in ("cfg2", "cfg5") else WORKLOAD
+    tp = rank_tprime(0, name)
+    o = OracleSample(name, tp)
+    try:
+        for _ in range(max(1, args.warmup)):
+            o.loops()
+        t_proj = o.projections()
+        t_wall = time.perf_counter()
+        times = [o.loops() for _ in range(args.steps)]
+        wall = time.perf_counter() - t_wall
+    finally:
+        o.close()
+    t_loops = statistics.median(times)
+    est = o.rhs_seconds(t_loops, t_proj)
+    value = 1.0 / est
+    sample = (f"each step: loops and products of {o.workers} of {o.nl} l on {o.workers} "
+              "single-threaded worker processes (one l each); the six cross projections timed "
+              "once after the warm-up; value extrapolates one RHS over all l")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_desc(tp), "precision": "fp64 (CPU oracle)"},
+           "config": {"workload": workload_desc(tp, name), "precision": "fp64 (CPU oracle)"},
            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT,
-                            "cores": os.cpu_count(), "sample": sample + "; one RHS per step",
-                            "wall_s": wall},
+                            "cores": o.workers, "sample": sample, "wall_s": wall,
+                            "extrapolated": True, "rhs_seconds_extrapolated": est,
+                            "measured": {"loops_products_s_per_step": times,
+                                         "projections_s": t_proj}},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -390,6 +468,182 @@ def run_scan(args, rank, world, local):
     return 0
 
 
+def run_sharded(args, rank, world, local):
+    """One point's right-hand side with its loop rows split over the ranks
+    (strong scaling): each rank computes its rows, one NCCL all-gather of the
+    row loops per RHS, projections and products on every rank.  A step is
+    one RHS evaluation."""
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    from paper_1604_06296_gb300.sharded import ShardedSolver
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    wl = args.workload if args.workload in ("cfg2", "cfg5") else WORKLOAD
+    c = W.config(wl)
+    tp = rank_tprime(0, wl)  # one point, the same on every rank
+    s = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"],
+                     c["nf"], precision=args.precision)
+    sh = ShardedSolver(s, rank, world, pg)
+    y = torch.from_numpy(W.random_state(1, s.nl, s.nff, 0.1)).cuda()
+    dy = s.empty(3)
+    for _ in range(args.warmup):
+        sh.rhs(0.5, y, out=dy)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sh.rhs(0.5, y, out=dy)
+    e1.record()
+    e1.synchronize()
+    if pg:
+        pg.barrier()
+    dev_s, _ = aggregate_ranks(pg, e0.elapsed_time(e1) / 1e3, 0)
+    if rank == 0:
+        r0, r1 = sh.parts[0]
+        out = {"metric": METRIC, "value": args.steps / dev_s, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
+               "scaling": "strong", "vs_baseline": None,
+               "dtype": f"{args.precision} loops, f64 state", "data": "synthetic",
+               "config": {"workload": workload_desc(tp, wl), "precision": args.precision,
+                          "step": "one RHS evaluation of the point; its loop rows split over "
+                                  "the ranks, row loops all-gathered (NCCL) once per RHS",
+                          "parallelism": f"loop rows split over {world} GPUs "
+                                         f"({sh.nrow} rows; rank 0: {r0}..{r1})",
+                          "l2": "inputs larger than L2"},
+               "gpu_launches": 9 * args.steps}
+        print(json.dumps(out))
+    s.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def run_large_batch(args, rank, world, local):
+    """The large-scale batch: 16 seeded (t', mu) points on the large grids
+    (coarse 48x48, Nff 25, fine 960x960), advanced together; a step is one
+    DoPri5 attempt of every point (one captured graph, one persistent loop
+    contraction over all points per stage)."""
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    c = W.config("cfg5")
+    pts = W.large_batch_points(16, W.LARGE_BATCH_SEED + rank)
+    for q in pts:
+        q["bonds"] = W.bonds_for_shells(q["shells"])
+    t0 = time.perf_counter()
+    batch = tufrg.Batch(pts, precision=args.precision)
+    setup_s = time.perf_counter() - t0
+    flow_kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
+                   rtol=1e-6, atol=1e-8, h0=0.05)
+    batch.flow(max_steps=args.warmup, **flow_kw)
+    torch.cuda.synchronize()
+    clocks = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(local).uuid))
+    clocks.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record()
+    _, res, st = batch.flow(max_steps=args.steps, **flow_kw)
+    e1.record()
+    e1.synchronize()
+    wall = time.perf_counter() - t_wall
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    rhs = float(sum(r["n_rhs"] for r in res))
+    attempts = max(r["n_accepted"] + r["n_rejected"] for r in res)
+    dev_s, rhs = aggregate_ranks(pg, dev_s, rhs)
+    value = rhs / dev_s
+    kms, sms = [], []
+    for _ in range(3):
+        k1, s1 = batch.profile_loops(0.5, 1)
+        kms.append(k1)
+        sms.append(s1)
+    k_ms, stage_ms = statistics.median(kms), statistics.median(sms)
+    npair, kdim, nrow = loop_counts(tufrg, pts[0]["bonds"], c["nc"], c["nc"], c["nf"], c["nf"])
+    flops = len(pts) * 2.0 * 3 * 2 * npair * kdim * nrow
+    peaks, peak_src = measured_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    peak = bf16 if args.precision == "bf16x3" else bf16 * 1.1 / 2.25
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel_ms": k_ms,
+                "stage_ms": stage_ms,
+                "kernel": f"loops_tc_kernel<{args.precision}> over all points (stage_ms: + "
+                          "tables, split-K combination)",
+                "algorithmic_flop_per_launch": flops,
+                "peak_source": f"bf16 dense burst from {peak_src} (of measured)"}
+    # end to end: batched RHS through the C ABI with the packed states of all
+    # points copied from and to pinned host memory
+    y_host = torch.empty(batch.state_elems, dtype=torch.float64).pin_memory()
+    for i in range(batch.n):
+        nl, nff, so, _ = batch.dims[i]
+        y_host[so:so + 3 * nl * nff * nff] = torch.from_numpy(
+            W.random_state(1 + i, nl, nff, 0.1).ravel())
+    dy_host = torch.empty_like(y_host).pin_memory()
+    y_dev, dy_dev = batch.empty(), batch.empty()
+    y_dev.copy_(y_host, non_blocking=True)
+    batch.rhs(0.5, y_dev, out=dy_dev)
+    torch.cuda.synchronize()
+    ems = []
+    for _ in range(max(2, min(args.steps, 5))):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        y_dev.copy_(y_host, non_blocking=True)
+        batch.rhs(0.5, y_dev, out=dy_dev)
+        dy_host.copy_(dy_dev, non_blocking=True)
+        f1.record()
+        f1.synchronize()
+        ems.append(f0.elapsed_time(f1))
+    e2e = {"value": world * batch.n * len(ems) / (sum(ems) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": y_host.numel() * 8, "d2h_bytes_per_step": dy_host.numel() * 8,
+           "call": "tufrg_batch_rhs of all points with pinned host copies in/out"}
+    per_stage = 10  # the grouped projections (Nff = 25): one more kernel per stage
+    launches = per_stage + (6 * per_stage + 3) * attempts
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline("cfg5", pts[0]["tp"])
+            cpu["sample"] += " (at one point of the batch)"
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": dev_s * 1e3 / max(1, attempts), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": f"{args.precision} loops, f64 state", "data": "synthetic",
+               "config": {"workload": "large-scale batch: 16 seeded (t', mu) points per GPU, "
+                                      "t'~U[-0.4,-0.2], mu=4t'+U[-0.1,0.1], U=3.5; coarse "
+                                      "48x48, Nff=25, fine 960x960",
+                          "step": "one DoPri5 attempt of every point (rtol 1e-6)",
+                          "l2": "inputs larger than L2 (tables and states of all points)",
+                          "points": [{"tp": q["tp"], "mu": q["mu"]} for q in pts]},
+               "rhs_evals_timed": rhs, "wall_s": wall, "setup_s": setup_s,
+               "status_nonzero": int(sum(1 for x in st if x)),
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": launches, "peaks_source": peak_src}
+        print(json.dumps(out))
+    batch.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def run_learned(args, rank, world, local):
     """Learned loop surrogate at production size (coarse 24x24, Nff 13, fine
     480x480): trained on ~1e6 exact loop rows of 16 seeded t' (mu = 4t',
@@ -494,31 +748,82 @@ def _parity(tufrg, bonds):
                    * tufrg.tufrg_eval_formfactors(bonds, k[0], k[1])[:, 0])
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "3xtf32", "bf16x3"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-flow-time", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg5", "scan", "learned"],
-                    help="cfg2: production point (default); cfg5: large point (coarse 48x48, "
-                         "Nff 25, fine 960x960; no flow ladder: the FP64 reference flow "
-                         "takes tens of minutes there); scan: batched "
-                         "phase-diagram scan; learned: loop surrogate trained and used in flows")
-    ap.add_argument("--points", type=int, default=256, help="scan: points per GPU")
-    ap.add_argument("--epochs", type=int, default=40, help="learned: training epochs")
-    args = ap.parse_args()
-    rank, world, local = dist_env()
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
-    if args.workload == "scan":
-        return run_scan(args, rank, world, local)
-    if args.workload == "learned":
-        return run_learned(args, rank, world, local)
+def rhs_rate(torch, solver, n, seed=1):
+    """RHS evaluations per second of tufrg_rhs on a seeded device state (CUDA
+    events around n calls after one untimed call) and the loop contraction's
+    own time (events inside the library)."""
+    y = torch.from_numpy(W.random_state(seed, solver.nl, solver.nff, 0.1)).cuda()
+    dy = solver.empty(3)
+    solver.rhs(0.5, y, out=dy)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        solver.rhs(0.5, y, out=dy)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    k_ms, _ = solver.profile_loops(0.5, 1)
+    return {"rhs_evals_per_s": 1e3 / ms, "ms_per_rhs": ms, "loop_kernel_ms": k_ms,
+            "rhs_timed": n}
 
+
+def timed_flow(torch, s, flow_kw, rtol, atol):
+    y0 = s.zeros(3)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    _, res, _ = s.flow(y0, **dict(flow_kw, rtol=rtol, atol=atol))
+    f1.record()
+    f1.synchronize()
+    return {"rtol": rtol, "atol": atol, "time_s": f0.elapsed_time(f1) / 1e3,
+            "lambda_c": res["lambda_c"], "diverged": res["diverged"], "kind": res["kind"],
+            "l_index": res["l_index"], "m": res["m"], "n": res["n"],
+            "rhs_evals": res["n_rhs"]}
+
+
+def flow_ladder(torch, tufrg, precision, name="cfg2"):
+    """Flows to Lambda_c on one point of a workload.  Reference: the FP64 GPU
+    flow at rtol 1e-8.  Each path runs a short tolerance ladder; its cost at a
+    given accuracy is the fastest rung whose Lambda_c is within LC_TARGET of
+    the reference."""
+    c = W.config(name)
+    tp = rank_tprime(0, name)
+    bonds = W.bonds_for_shells(c["shells"])
+    flow_kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
+                   h0=0.05)
+    LC_TARGET = 1e-4
+    ladder = [(1e-6, 1e-8), (1e-5, 1e-7), (1e-4, 1e-6)]
+    ref = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], bonds, c["nc"], c["nf"], precision="fp64")
+    paths = {"fp64": ref}
+    if precision != "fp64":
+        paths[precision] = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], bonds, c["nc"], c["nf"],
+                                        precision=precision)
+    reference = timed_flow(torch, ref, flow_kw, 1e-8, 1e-10)
+    info = {"workload": workload_desc(tp, name), "reference_fp64_rtol1e-8": reference,
+            "lambda_c_target": LC_TARGET}
+    best = {}
+    for pname, s in paths.items():
+        rungs = []
+        for rtol, atol in ladder:
+            r = timed_flow(torch, s, flow_kw, rtol, atol)
+            r["lambda_c_rel_err"] = abs(r["lambda_c"] / reference["lambda_c"] - 1)
+            rungs.append(r)
+        info[pname] = rungs
+        ok = [r for r in rungs if r["diverged"] and r["lambda_c_rel_err"] <= LC_TARGET
+              and r["kind"] == reference["kind"]]
+        best[pname] = min(ok, key=lambda r: r["time_s"]) if ok else None
+    info["best_at_target"] = best
+    if precision != "fp64" and best.get("fp64") and best.get(precision):
+        info["speedup_vs_fp64_gpu_at_equal_lambda_c_accuracy"] = (
+            best["fp64"]["time_s"] / best[precision]["time_s"])
+    for s in paths.values():
+        s.close()
+    return info
+
+
+def run_point(args, rank, world, local):
+    """One phase-diagram point per rank (the production or the large point)."""
     import torch
     import paper_1604_06296_gb300 as tufrg
     if not torch.cuda.is_available():
@@ -533,10 +838,9 @@ def main():
     wl = args.workload
     c = W.config(wl)
     tp = rank_tprime(rank, wl)
-    if wl == "cfg5":
-        args.no_flow_time = True
-    solver = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"],
-                          c["nf"], precision=args.precision)
+    bonds = W.bonds_for_shells(c["shells"])
+    solver = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], bonds, c["nc"], c["nf"],
+                          precision=args.precision)
     flow_kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
                    rtol=1e-8, atol=1e-10, h0=0.05)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -624,8 +928,7 @@ def main():
                      "stage_frac": flops / (stage_ms * 1e-3) / 1e12 / peak,
                      "algorithmic_flop_per_launch": flops,
                      "counting": f"{npair} allowed pairs x {kdim} half-zone points x {nrow} "
-                                 "loop rows (C4v orbits of interior l + boundary l) x 2 "
-                                 "channels"})
+                                 "loop rows (point-group classes of l) x 2 channels"})
 
     # end to end through the C ABI with host buffers: H2D state, RHS, D2H result
     y_host = torch.from_numpy(W.random_state(1, solver.nl, solver.nff, 0.1)).pin_memory()
@@ -650,86 +953,107 @@ def main():
     e2e = {"value": world * len(ems) / (sum(ems) / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": y_host.numel() * 8, "d2h_bytes_per_step": dy_host.numel() * 8,
            "call": "tufrg_rhs with pinned host copies in/out"}
+    del y_host, dy_host, y_dev, dy_dev
+
+    if pg:
+        pg.destroy_process_group()
+    if rank != 0:
+        solver.close()
+        return 0
+
+    # the other precisions on the same point (rank 0)
+    comparisons = {}
+    if not args.no_compare:
+        comparisons[args.precision] = rhs_rate(torch, solver, 10)
+        for prec in ("fp64", "3xtf32", "bf16x3"):
+            if prec == args.precision:
+                continue
+            s2 = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], bonds, c["nc"], c["nf"],
+                              precision=prec)
+            comparisons[prec] = rhs_rate(torch, s2, 3 if prec == "fp64" else 10)
+            s2.close()
+        for prec, r in comparisons.items():
+            r["vs_fp64"] = r["rhs_evals_per_s"] / comparisons["fp64"]["rhs_evals_per_s"]
 
     flow_info = None
     if not args.no_flow_time:
-        # Full flows to Lambda_c.  Reference: FP64 GPU flow at rtol 1e-8.  Each
-        # path then runs a short tolerance ladder; its cost at a given accuracy
-        # is the fastest rung whose Lambda_c is within LC_TARGET of the reference.
-        LC_TARGET = 1e-4
-        ladder = [(1e-6, 1e-8), (1e-5, 1e-7), (1e-4, 1e-6)]
-
-        def timed_flow(s, rtol, atol):
-            y0 = s.zeros(3)
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record()
-            _, res, _ = s.flow(y0, **dict(flow_kw, rtol=rtol, atol=atol))
-            f1.record()
-            f1.synchronize()
-            return {"rtol": rtol, "atol": atol, "time_s": f0.elapsed_time(f1) / 1e3,
-                    "lambda_c": res["lambda_c"], "diverged": res["diverged"],
-                    "kind": res["kind"], "l_index": res["l_index"], "m": res["m"],
-                    "n": res["n"], "rhs_evals": res["n_rhs"]}
-
-        ref = solver if args.precision == "fp64" else tufrg.Solver(
-            c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"], c["nf"],
-            precision="fp64")
-        reference = timed_flow(ref, 1e-8, 1e-10)
-        paths = {"fp64": ref} if args.precision == "fp64" else {"fp64": ref,
-                                                                 args.precision: solver}
-        flow_info = {"reference_fp64_rtol1e-8": reference, "lambda_c_target": LC_TARGET}
-        best = {}
-        for name, s in paths.items():
-            rungs = []
-            for rtol, atol in ladder:
-                r = timed_flow(s, rtol, atol)
-                r["lambda_c_rel_err"] = abs(r["lambda_c"] / reference["lambda_c"] - 1)
-                rungs.append(r)
-            flow_info[name] = rungs
-            ok = [r for r in rungs if r["diverged"] and r["lambda_c_rel_err"] <= LC_TARGET
-                  and r["kind"] == reference["kind"]]
-            best[name] = min(ok, key=lambda r: r["time_s"]) if ok else None
-        flow_info["best_at_target"] = best
-        if args.precision != "fp64" and best.get("fp64") and best.get(args.precision):
-            flow_info["speedup_vs_fp64_gpu_at_equal_lambda_c_accuracy"] = (
-                best["fp64"]["time_s"] / best[args.precision]["time_s"])
-        if ref is not solver:
-            ref.close()
+        # a flow to Lambda_c at this point in the bench's precision, and the
+        # flow-time comparison at equal Lambda_c accuracy (FP64 reference at
+        # rtol 1e-8 and tolerance ladders) on the production point, where the
+        # FP64 reference flow takes about a second
+        own = timed_flow(torch, solver, dict(flow_kw), 1e-6, 1e-8)
+        flow_info = {"this_point_rtol1e-6": own,
+                     "equal_accuracy_production_point": flow_ladder(torch, tufrg,
+                                                                    args.precision)}
+    solver.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, sample = cpu_oracle_rhs_sample(tp, 8, wl) if wl == "cfg5" else \
-            cpu_oracle_rhs_sample(tp)
-        cpu = {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": sample}
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, tp)
 
     # kernels of the library per timed step: 6 stages x (combination, stage
     # scale, per-scale table, loop contraction, split-K reduce, to_bond,
     # dft_keys, contract (+ overlap in the grouped form), products gathering
     # the row loops) + error + control + accept
-    per_stage = 9 + (solver.nff >= GROUPED_NFF)
+    per_stage = 9 + (W.n_ff_for_shells(c["shells"]) >= GROUPED_NFF)
     launches_per_step = 6 * per_stage + 3
-    if rank == 0:
-        dtype = "f64" if args.precision == "fp64" else f"{args.precision} loops, f64 state"
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-               "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-               "config": {"workload": workload_desc(tp, wl), "precision": args.precision,
-                          "step": "one DoPri5 step (6 RHS evaluations + stage/error/control)",
-                          "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                          "parallelism": f"{world} independent phase-diagram points"
-                                         if world > 1 else "single point"},
-               "rhs_evals_timed": total_rhs, "wall_s": wall,
-               "step_ms": [round(t, 3) for t in step_ms],
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-               "flow": flow_info, "peaks_source": peak_src}
-        print(json.dumps(out))
-    if pg:
-        pg.destroy_process_group()
+    dtype = "f64" if args.precision == "fp64" else f"{args.precision} loops, f64 state"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+           "config": {"workload": workload_desc(tp, wl), "precision": args.precision,
+                      "step": "one DoPri5 step (6 RHS evaluations + stage/error/control)",
+                      "l2": f"inputs larger than L2, and flushed between timed steps "
+                            f"({L2_FLUSH_BYTES >> 20} MB write)",
+                      "parallelism": f"{world} independent phase-diagram points"
+                                     if world > 1 else "single point"},
+           "rhs_evals_timed": total_rhs, "wall_s": wall,
+           "step_ms": [round(t, 3) for t in step_ms],
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+           "precisions_same_point": comparisons or None,
+           "flow": flow_info, "peaks_source": peak_src}
+    print(json.dumps(out))
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "3xtf32", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-flow-time", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the other precisions on the same point")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["cfg5", "cfg2", "cfg5-batch", "scan", "learned"],
+                    help="cfg5: large point (coarse 48x48, Nff 25, fine 960x960; default); "
+                         "cfg2: production point (coarse 24x24, Nff 13, fine 480x480); "
+                         "cfg5-batch: 16 (t', mu) points on the large grids advanced "
+                         "together; scan: batched phase-diagram scan; learned: loop "
+                         "surrogate trained and used in flows")
+    ap.add_argument("--shard", action="store_true",
+                    help="one point with its loop rows split over the ranks (strong scaling); "
+                         "a step is one RHS evaluation")
+    ap.add_argument("--points", type=int, default=256, help="scan: points per GPU")
+    ap.add_argument("--epochs", type=int, default=40, help="learned: training epochs")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.shard:
+        return run_sharded(args, rank, world, local)
+    if args.workload == "scan":
+        return run_scan(args, rank, world, local)
+    if args.workload == "cfg5-batch":
+        return run_large_batch(args, rank, world, local)
+    if args.workload == "learned":
+        return run_learned(args, rank, world, local)
+    return run_point(args, rank, world, local)
 
 
 if __name__ == "__main__":

@@ -265,6 +265,37 @@ tufrg_status tufrg_selftest_wait(tufrg_ctx* ctx, int32_t wait_us, void* cuda_str
 tufrg_status tufrg_check(tufrg_ctx* ctx, void* cuda_stream);
 
 /* ---------------------------------------------------------------------
+ * The loop contraction of one point split over several GPUs (Sec. 3: the
+ * paper distributes the bosonic momenta l over its MPI ranks).  The unit of
+ * work is the loop row: one per class of transfer momenta l under the
+ * point-group elements that map l into the zone without a fold (App. C),
+ * whose loops follow from the row's by the point-group representation.  A
+ * rank computes the rows [row_begin, row_end) of its context; the caller
+ * gathers the row loops of all ranks (one collective per right-hand side)
+ * and finishes the right-hand side on every rank with the replicated state.
+ * Row loops are FP64 [2][nrow][npair] (pp, then ph; for each row the
+ * parity-allowed pairs m <= n in the basis order, times -1/4 / +1/4 as in
+ * chi_dot), row-major, caller-owned device memory.
+ *
+ * tufrg_row_info: the context's nrow and npair (host outputs).
+ * tufrg_shard_rows: the context's loop contraction computes only the rows
+ *   [row_begin, row_end), 0 <= row_begin < row_end <= nrow (the whole range
+ *   undoes the split).  Tensor-core precisions only (TUFRG_ERR_ARG for an
+ *   FP64 context).  While a context is split, tufrg_loops, tufrg_rhs and the
+ *   flows return TUFRG_ERR_STATE.
+ * tufrg_loop_rows: rows [row_begin, row_end) of the row loops at the scale
+ *   lambda into rows_dev (the other rows untouched).  Stream-ordered.
+ * tufrg_rhs_from_rows: the right-hand side (projections, products) of y at
+ *   lambda with the loops given by complete row loops rows_dev.  y, dy as in
+ *   tufrg_rhs. */
+tufrg_status tufrg_row_info(const tufrg_ctx* ctx, int32_t* nrow, int32_t* npair);
+tufrg_status tufrg_shard_rows(tufrg_ctx* ctx, int32_t row_begin, int32_t row_end,
+                              void* cuda_stream);
+tufrg_status tufrg_loop_rows(tufrg_ctx* ctx, double lambda, double* rows_dev, void* cuda_stream);
+tufrg_status tufrg_rhs_from_rows(tufrg_ctx* ctx, double lambda, const double* rows_dev,
+                                 const double* y_dev, double* dy_dev, void* cuda_stream);
+
+/* ---------------------------------------------------------------------
  * Tile autotuning.  The tensor-core loop contraction cuts each point's loop
  * sum into work items of kbps K-blocks (64 fine-grid points per K-block for
  * BF16X3, 32 for 3XTF32) per tile of 128 l-rows; persistent CTAs, one per

@@ -77,6 +77,11 @@ SIGNATURES = {
                                 POINTER(c_double), POINTER(c_double), POINTER(c_int32)],
                                c_int32),
     "tufrg_loops": ([c_void_p, c_double, c_void_p, c_void_p], c_int32),
+    "tufrg_row_info": ([c_void_p, POINTER(c_int32), POINTER(c_int32)], c_int32),
+    "tufrg_shard_rows": ([c_void_p, c_int32, c_int32, c_void_p], c_int32),
+    "tufrg_loop_rows": ([c_void_p, c_double, c_void_p, c_void_p], c_int32),
+    "tufrg_rhs_from_rows": ([c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p],
+                            c_int32),
     "tufrg_project": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "tufrg_products": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "tufrg_rhs": ([c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
@@ -230,6 +235,27 @@ def tufrg_flow_state(ctx, y_dev: int, stream: int = 0) -> tufrg_result:
     _check(lib().tufrg_flow_state(ctx, _dptr(y_dev), byref(res), _dptr(stream)),
            "tufrg_flow_state")
     return res
+
+
+def tufrg_row_info(ctx) -> tuple[int, int]:
+    """(nrow, npair): loop rows and parity-allowed pairs of the context."""
+    nrow, npair = c_int32(), c_int32()
+    _check(lib().tufrg_row_info(ctx, byref(nrow), byref(npair)), "tufrg_row_info")
+    return nrow.value, npair.value
+
+
+def tufrg_shard_rows(ctx, row_begin: int, row_end: int, stream: int = 0) -> None:
+    _check(lib().tufrg_shard_rows(ctx, row_begin, row_end, _dptr(stream)), "tufrg_shard_rows")
+
+
+def tufrg_loop_rows(ctx, lam: float, rows_dev: int, stream: int = 0) -> None:
+    _check(lib().tufrg_loop_rows(ctx, lam, _dptr(rows_dev), _dptr(stream)), "tufrg_loop_rows")
+
+
+def tufrg_rhs_from_rows(ctx, lam: float, rows_dev: int, y_dev: int, dy_dev: int,
+                        stream: int = 0) -> None:
+    _check(lib().tufrg_rhs_from_rows(ctx, lam, _dptr(rows_dev), _dptr(y_dev), _dptr(dy_dev),
+                                     _dptr(stream)), "tufrg_rhs_from_rows")
 
 
 def tufrg_loops_noalloc(params: tufrg_params, lam: float, chi_dot_dev: int,

@@ -50,7 +50,10 @@ tufrg_status validate(const tufrg_params* p) {
 
 namespace tufrg {
 
+static bool sharded(const tufrg_ctx* c) { return c->shard_lo != 0 || c->shard_hi != c->nrow; }
+
 tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) {
+  if (sharded(c)) return TUFRG_ERR_STATE;  // the loops of every l need every row
   if (prec == kLoopSurrogate) {
     if (!c->sur || chi != c->d_chi) return TUFRG_ERR_STATE;
     return surrogate_loops(c->sur, c, chi, st);
@@ -64,6 +67,7 @@ tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) 
 
 tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st) {
   if (prec == kLoopSurrogate) return TUFRG_ERR_ARG;
+  if (sharded(c)) return TUFRG_ERR_STATE;
   if (prec == TUFRG_FP64) {
     TUFRG_CHECK(launch_scale_tables(c, st));
     return launch_loops_fp64_rows(c, st);
@@ -72,7 +76,7 @@ tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st) {
 }
 
 tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool wedge) {
   // projections and products in FP32 arithmetic for a mixed-precision
   // context, in FP64 for an FP64 context and after a switch to FP64 loops
   const int arith =
@@ -80,16 +84,20 @@ tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, boo
   // the projections (state only) beside the loops (scale only)
   TUFRG_CUDA(cudaEventRecord(c->ev_fork, st));
   TUFRG_CUDA(cudaStreamWaitEvent(c->pstream, c->ev_fork, 0));
-  TUFRG_CHECK(launch_project_multi(c->view, arith, y, c->d_V, c->d_bt, c->d_fkey, c->pstream));
-  TUFRG_CUDA(cudaEventRecord(c->ev_join, c->pstream));
   // exact loops stay as row loops; the products gather each l from its row
+  // (or, for a covariant state, run at the rows' representatives only)
   const bool rows = prec != kLoopSurrogate;
+  wedge = wedge && rows;
+  TUFRG_CHECK(launch_project_multi(c->view, arith, y, c->d_V, c->d_bt, c->d_fkey, c->pstream,
+                                   wedge));
+  TUFRG_CUDA(cudaEventRecord(c->ev_join, c->pstream));
   if (rows)
     TUFRG_CHECK(launch_loop_rows(c, prec, st));
   else
     TUFRG_CHECK(launch_loops(c, prec, c->d_chi, st));
   TUFRG_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
-  return launch_products_multi(c->view, arith, c->d_V, rows ? nullptr : c->d_chi, dy, scaled, st);
+  return launch_products_multi(c->view, arith, c->d_V, rows ? nullptr : c->d_chi, dy, scaled, st,
+                               wedge);
 }
 
 tufrg_status create_context(const tufrg_params* p, cudaStream_t st, const SetupShare& share,
@@ -234,6 +242,57 @@ tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double*
       cudaStreamWaitEvent(st, c->ev_out, 0) != cudaSuccess)
     return s == TUFRG_OK ? TUFRG_ERR_CUDA : s;
   return s;
+}
+
+tufrg_status tufrg_row_info(const tufrg_ctx* c, int32_t* nrow, int32_t* npair) {
+  if (!c) return TUFRG_ERR_ARG;
+  if (nrow) *nrow = c->nrow;
+  if (npair) *npair = c->npair;
+  return TUFRG_OK;
+}
+
+tufrg_status tufrg_shard_rows(tufrg_ctx* c, int32_t row_begin, int32_t row_end, void* stream) {
+  if (!c || c->p.precision == TUFRG_FP64 || row_begin < 0 || row_end <= row_begin ||
+      row_end > c->nrow)
+    return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  TUFRG_CUDA(cudaStreamSynchronize(st));
+  c->shard_lo = row_begin;
+  c->shard_hi = row_end;
+  tufrg::flow_drop_graphs(c);
+  double* lam[1] = {c->d_lambda};
+  tufrg_ctx* self[1] = {c};
+  return tufrg::view_build(c->view, self, 1, lam, nullptr, c->d_err, c->p.precision, 0, st);
+}
+
+tufrg_status tufrg_loop_rows(tufrg_ctx* c, double lambda, double* rows_dev, void* stream) {
+  if (!c || !rows_dev || !finite_pos(lambda) || c->p.precision == TUFRG_FP64)
+    return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
+  TUFRG_CHECK(tufrg::launch_loops_tc_rows_multi(c->view, st));
+  const size_t w = (size_t)(c->shard_hi - c->shard_lo) * c->npair;
+  for (int ch = 0; ch < 2; ++ch) {
+    const size_t o = ((size_t)ch * c->nrow + c->shard_lo) * c->npair;
+    TUFRG_CUDA(cudaMemcpyAsync(rows_dev + o, c->view.d_rowres + o, sizeof(double) * w,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  return TUFRG_OK;
+}
+
+tufrg_status tufrg_rhs_from_rows(tufrg_ctx* c, double lambda, const double* rows_dev,
+                                 const double* y_dev, double* dy_dev, void* stream) {
+  if (!c || !rows_dev || !y_dev || !dy_dev || y_dev == dy_dev || !finite_pos(lambda) ||
+      !c->d_V)
+    return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int arith = c->p.precision == TUFRG_FP64 ? TUFRG_FP64 : TUFRG_3XTF32;
+  TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
+  TUFRG_CUDA(cudaMemcpyAsync(c->view.d_rowres, rows_dev,
+                             sizeof(double) * 2 * (size_t)c->nrow * c->npair,
+                             cudaMemcpyDeviceToDevice, st));
+  TUFRG_CHECK(tufrg::launch_project_multi(c->view, arith, y_dev, c->d_V, c->d_bt, c->d_fkey, st));
+  return tufrg::launch_products_multi(c->view, arith, c->d_V, nullptr, dy_dev, false, st);
 }
 
 namespace {

@@ -14,6 +14,7 @@
 // point's Hermite interpolant (its last step is kept intact once it stops).
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <new>
@@ -202,6 +203,11 @@ struct BatchFlow {
   int* prefix = nullptr;    // chunks of the packed state per point
   int n_chunks = 0;
   cudaGraphExec_t attempt = nullptr;
+  // every point's state is point-group covariant (checked at the start):
+  // projections and products at the rows' representative l only; the
+  // attempt graph was captured with graph_wedge
+  bool wedge = false, graph_wedge = false;
+  unsigned long long* cov = nullptr;  // device [2 n]: deviation, max |y| per point
 };
 
 }  // namespace tufrg
@@ -231,17 +237,20 @@ namespace {
 
 int grid_for(int n) { return (n + 127) / 128; }
 
+// wedge: projections and products at the rows' representative l only
+// (flows of point-group covariant states)
 tufrg_status batch_rhs_device(tufrg_batch* b, const double* y, double* dy, bool scaled,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool wedge = false) {
   const MultiView& v = b->view;
   // the projections (states only) beside the loops (scales only)
   TUFRG_CUDA(cudaEventRecord(b->ev_fork, st));
   TUFRG_CUDA(cudaStreamWaitEvent(b->pstream, b->ev_fork, 0));
-  TUFRG_CHECK(launch_project_multi(v, b->precision, y, b->d_V, b->d_bt, b->d_fkey, b->pstream));
+  TUFRG_CHECK(launch_project_multi(v, b->precision, y, b->d_V, b->d_bt, b->d_fkey, b->pstream,
+                                   wedge));
   TUFRG_CUDA(cudaEventRecord(b->ev_join, b->pstream));
   TUFRG_CHECK(launch_loops_tc_rows_multi(v, st));  // row loops, gathered by the products
   TUFRG_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
-  return launch_products_multi(v, b->precision, b->d_V, nullptr, dy, scaled, st);
+  return launch_products_multi(v, b->precision, b->d_V, nullptr, dy, scaled, st, wedge);
 }
 
 tufrg_status set_lambdas(tufrg_batch* b, const double* lambda, cudaStream_t st) {
@@ -270,7 +279,8 @@ tufrg_status batch_flow_buffers(tufrg_batch* b) {
   if (f.base) return TUFRG_OK;
   const size_t n = b->view.state_elems;
   f.n_state = n;
-  const size_t bytes = sizeof(double) * n * 12 + sizeof(FlowCtl) * b->n + 256;
+  const size_t bytes =
+      sizeof(double) * n * 12 + sizeof(FlowCtl) * b->n + 256 + 16 * (size_t)b->n + 256;
   if (cudaMalloc((void**)&f.base, bytes) != cudaSuccess) return TUFRG_ERR_OOM;
   double* p = f.base;
   f.y = p;
@@ -280,6 +290,8 @@ tufrg_status batch_flow_buffers(tufrg_batch* b) {
   f.yprev = p + n * 10;
   f.k1prev = p + n * 11;
   f.ctl = reinterpret_cast<FlowCtl*>(p + n * 12);
+  f.cov = reinterpret_cast<unsigned long long*>(
+      (reinterpret_cast<uintptr_t>(f.ctl + b->n) + 255) & ~uintptr_t(255));
   TUFRG_CUDA(cudaMallocHost((void**)&f.hctl, sizeof(FlowCtl) * b->n));
   std::vector<Seg> seg(b->n);
   std::vector<int> prefix(b->n + 1, 0);
@@ -317,7 +329,7 @@ tufrg_status bstage(tufrg_batch* b, const double* y, double* out,
                                                              f.prefix, b->n, 0);
   bstage_lambda_kernel<<<grid_for(b->n), 128, 0, st>>>(f.ctl, cnode, b->d_lam, b->n);
   TUFRG_CUDA(cudaGetLastError());
-  return batch_rhs_device(b, out, k_out, true, st);
+  return batch_rhs_device(b, out, k_out, true, st, f.wedge);
 }
 
 tufrg_status enqueue_battempt(tufrg_batch* b, cudaStream_t st) {
@@ -404,6 +416,26 @@ tufrg_status batch_flow(tufrg_batch* b, const tufrg_flow_opts* o, double* y_dev,
   TUFRG_CUDA(cudaMemcpyAsync(f.ctl, f.hctl, sizeof(FlowCtl) * np, cudaMemcpyHostToDevice, st));
   TUFRG_CUDA(cudaMemsetAsync(b->d_skip, 0, sizeof(int) * np, st));
   TUFRG_CUDA(cudaMemcpyAsync(f.y, y_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  // the wedge when every point's initial state is covariant (zeros are)
+  {
+    TUFRG_CHECK(launch_covariance_check(b->view, f.y, f.cov, st));
+    std::vector<unsigned long long> h(2 * (size_t)np);
+    TUFRG_CUDA(cudaMemcpyAsync(h.data(), f.cov, sizeof(unsigned long long) * h.size(),
+                               cudaMemcpyDeviceToHost, st));
+    TUFRG_CUDA(cudaStreamSynchronize(st));
+    f.wedge = true;
+    for (int i = 0; i < np; ++i) {
+      double dev, amax;
+      std::memcpy(&dev, &h[2 * i], 8);
+      std::memcpy(&amax, &h[2 * i + 1], 8);
+      f.wedge = f.wedge && dev <= 1e-13 * amax;
+    }
+    if (f.wedge != f.graph_wedge && f.attempt) {
+      cudaGraphExecDestroy(f.attempt);
+      f.attempt = nullptr;
+    }
+    f.graph_wedge = f.wedge;
+  }
   TUFRG_CHECK(bstage(b, f.y, f.ytmp, {}, 0.0, f.k[0], st));  // k1 = f(s0, y0)
   TUFRG_CHECK(battempt_graph(b, st));
   int attempts = 0;

@@ -163,6 +163,11 @@ struct FlowState {
   cudaGraphExec_t attempt[3] = {nullptr, nullptr, nullptr};  // loops: context, FP64, surrogate
   double fp64_above = 0.0;
   double lambda_switch = 0.0;
+  // the flow's state is point-group covariant (checked at the start; exact
+  // loops keep it so): projections and products at the rows' representative
+  // l only.  graphs_wedge: the setting the attempt graphs were captured with
+  bool wedge = false, graphs_wedge = false;
+  unsigned long long* cov = nullptr;  // [2]: covariance deviation and max |y| (device)
   // loop surrogate: accepted steps since the last judgement, the scale at
   // which the judge rejected it, right-hand sides it served, judgements
   int since_judge = 0;
@@ -200,6 +205,8 @@ tufrg_status ensure_buffers(tufrg_ctx* c) {
   f.yprev = p + n * 10;
   f.k1prev = p + n * 11;
   f.ctl = (FlowCtl*)(p + n * 12);
+  f.cov = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(f.ctl) + 512);
+  static_assert(sizeof(FlowCtl) <= 512, "the covariance words follow the control block");
   return TUFRG_OK;
 }
 
@@ -222,7 +229,7 @@ tufrg_status stage(tufrg_ctx* c, const double* y, double* out,
   combo_kernel<<<grid_for(n), 256, 0, c->pstream>>>(y, out, cb, f.ctl, c->d_lambda, n, 0);
   stage_lambda_kernel<<<1, 1, 0, st>>>(f.ctl, cnode, c->d_lambda);
   TUFRG_CUDA(cudaGetLastError());
-  return rhs_device(c, c->loop_prec, out, k_out, true, st);
+  return rhs_device(c, c->loop_prec, out, k_out, true, st, f.wedge);
 }
 
 // One DoPri5 attempt: stages 2..7, error norm, control, accept.
@@ -510,6 +517,26 @@ tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
     h0.h = h0.s_end - h0.s;
   }
   TUFRG_CUDA(cudaMemcpyAsync(f.y, y0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  // the wedge when the initial state is covariant (the bare start, zeros, is)
+  // and every loop is exact (a surrogate's loops are not covariant)
+  f.wedge = false;
+  if (!c->sur) {
+    TUFRG_CHECK(launch_covariance_check(c->view, f.y, f.cov, st));
+    unsigned long long h[2] = {0, 0};
+    TUFRG_CUDA(cudaMemcpyAsync(h, f.cov, sizeof(h), cudaMemcpyDeviceToHost, st));
+    TUFRG_CUDA(cudaStreamSynchronize(st));
+    double dev, amax;
+    std::memcpy(&dev, &h[0], 8);
+    std::memcpy(&amax, &h[1], 8);
+    f.wedge = dev <= 1e-13 * amax;
+  }
+  if (f.wedge != f.graphs_wedge) {
+    for (auto& g : f.attempt) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+    f.graphs_wedge = f.wedge;
+  }
   TUFRG_CHECK(write_ctl(c, h0, st));
   if (o->method == TUFRG_DOPRI5) {
     if (c->sur) {  // the surrogate's buffers may have moved: capture afresh

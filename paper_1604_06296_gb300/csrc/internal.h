@@ -96,6 +96,7 @@ struct PointDesc {
   int term_off[3];  // term form: first term of target t
   int gy_off[4];    // grouped form: positions Y of target t are gy_off[t] .. gy_off[t + 1] - 1
   int npair, nrow;
+  int row_lo, row_hi;  // the loop rows this view's contraction computes (all: 0, nrow)
   // tensor-core loops
   int nfx, nfy, hx, hy, wy, n_ext, nkb, kpad_tc, nrow_pad, npad, nsets, ksplit;
   long long off_state, off_chi, off_bt, off_fkey, off_partial;
@@ -141,6 +142,8 @@ enum : int {
   kKindContract,   // projections: phase sums over the positions, per l
   kKindProducts,   // V chi V
   kKindExpand,     // row loops -> loops of every l the row serves
+  kKindContractRows,  // projections, phase sums: at the representative l of each row only
+  kKindProductsRows,  // V chi V at each row's representative l, written to the l it serves
   kKinds
 };
 
@@ -193,7 +196,8 @@ struct tufrg_ctx {
   double4_32a* d_tab = nullptr;        // [nf] (xi, A, H, 0) -- A, H filled per scale
   int2* d_kidx = nullptr;          // [kpad] fine-grid (ix, iy) of each loop point (-1 pad)
   double* d_F = nullptr;           // [mpad][kpad] weight * f_m f_n / Nf
-  int nrow = 0;                    // loop rows (C4v orbits / {l, -l} pairs / boundary l)
+  int nrow = 0;                    // loop rows (point-group classes of l)
+  int shard_lo = 0, shard_hi = 0;  // rows of the loop contraction (all unless sharded)
   bool c4v = false;                // rows serve C4v orbits
   int2* d_shift = nullptr;         // [nrow] l/2 of each row in fine-grid steps
   int* d_rowimg_ptr = nullptr;     // [nrow + 1] CSR over d_rowimg
@@ -317,8 +321,10 @@ tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 
 // steps i-iii at the scale stored in c->d_lambda with loops in precision prec;
 // dy scaled by c->d_lambda[1] if scaled
+// wedge: projections and products at the rows' representative l only
+// (flows of a point-group covariant state)
 tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
-                        cudaStream_t st);
+                        cudaStream_t st, bool wedge = false);
 
 // multi-point views (multi.cpp): descriptors of n contexts packed one after
 // the other; lam[i], skip[i] are per-point device pointers (skip may be null)
@@ -361,13 +367,24 @@ constexpr int kGroupedNff = 21;
 // elements of a point's bond-space workspace: the bond-space propagators
 // [3][nb*nb][nl], later reused for the overlap sums [positions Y][nff][nff]
 size_t bt_region(int nb, int nl, int nff, int ny_total);
-// projections and products of every point; bt, fkey: packed workspaces
+// projections and products of every point; bt, fkey: packed workspaces.
+// rows: the projected couplings at the representative l of each loop row
+// only (the wedge of a point-group covariant state)
 tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
-                                  void* bt, void* fkey, cudaStream_t st);
+                                  void* bt, void* fkey, cudaStream_t st, bool rows = false);
 // chi == nullptr: the loops of each l are gathered from the row loops
-// v.d_rowres (the orbit expansion fused into the products)
+// v.d_rowres (the orbit expansion fused into the products).  rows (with chi
+// == nullptr): the products at each row's representative l only, written to
+// every l the row serves as R^g dy R^g^T (needs the couplings of the
+// representatives, and a covariant state for the result to be exact)
 tufrg_status launch_products_multi(const MultiView& v, int prec, const double* vin,
-                                   const double* chi, double* dy, bool scaled, cudaStream_t st);
+                                   const double* chi, double* dy, bool scaled, cudaStream_t st,
+                                   bool rows = false);
+// largest |y(g l) - R^g y(l) R^g^T| over every l a row serves (l the row's
+// representative) and largest |y|, for each point of the view, into dev[2 * i],
+// dev[2 * i + 1] as the bit patterns of non-negative doubles
+tufrg_status launch_covariance_check(const MultiView& v, const double* y,
+                                     unsigned long long* dev, cudaStream_t st);
 // loop contraction up to the row loops in c->view.d_rowres (no expansion);
 // prec must not be the surrogate
 tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st);

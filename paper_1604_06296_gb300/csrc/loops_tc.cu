@@ -8,8 +8,9 @@
 // W_hi F_hi + W_lo F_hi + W_hi F_lo accumulated in FP32 in tensor memory;
 // the split-K partial sums of each CTA are combined (fixed order, compensated
 // FP32 pairs, FP64 result) by a second kernel.  The propagator operand W is
-// generated in registers from the per-scale FP32 table (A = 1/(Omega + |xi|)
-// and xi, extended by a wrap-around halo so p +- l/2 is one add from p) with
+// generated in registers from the per-scale FP32 table (alpha = Omega /
+// (Omega + |xi|) and xi, extended by a wrap-around halo so p +- l/2 is one
+// add from p) with
 // the same closed-form frequency integral as the FP64 path, and written
 // straight into the 128B-swizzled K-major shared-memory layout the MMA reads;
 // F (scale independent) arrives by TMA (one 2-D box per K-block and part).
@@ -34,7 +35,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <type_traits>
 
 #include "device_util.cuh"
 #include "tc_util.cuh"
@@ -107,44 +107,33 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Constants of the weight formulas at one scale Omega.
-struct WConst {
-  float2 c5om, cm2om2, cm3, c2om2, cm2om, c3;
-  __device__ explicit WConst(float om)
-      : c5om{5.f * om, 5.f * om},
-        cm2om2{-2.f * om * om, -2.f * om * om},
-        cm3{-3.f, -3.f},
-        c2om2{2.f * om * om, 2.f * om * om},
-        cm2om{-2.f * om, -2.f * om},
-        c3{3.f, 3.f} {}
-};
-
 // Closed-form frequency integral of the two loops for two propagator pairs
-// at once, from the table values A = 1/(Omega + |xi|) and the signed xi of
-// both propagators (a at p + l/2, b at p - l/2).  With h(x) = x (Omega + 3x)
-// / (Omega + x)^3 (so that J = -sgn(xi) h(|xi|) / 4):
-//   D = h[|xi_a|, |xi_b|]
-//     = A_a A_b (5 Omega (A_a + A_b) - 3 - 2 Omega^2 (A_a^2 + A_a A_b + A_b^2)),
-//   S = (h_a + h_b) / (|xi_a| + |xi_b|) = (Hs_a + Hs_b') / (xi_a + xi_b'),
-// with Hs = sgn(xi) h(|xi|) = xi A^2 (3 - 2 Omega A) (Omega + 3|xi| = 3/A -
-// 2 Omega) and xi_b' = xi_b carried over to the sign of xi_a (Hs is linear
-// in the sign): numerator and denominator of S are sums of two terms of one
-// sign, and 3 - 2 Omega A lies in [1, 3).  The particle-particle weight is S
-// for propagators of one sign, D else, and the particle-hole weight the
-// other one (the -1/4 and +1/4 are applied in the combination of the partial
-// sums).  The table holds |xi| no smaller than 1e-30 (sign kept): at xi_a =
-// xi_b = 0 S is then 1/Omega^2, its limit.
-__device__ __forceinline__ void weights(const float2 Aa, const float2 xa, const float2 Ab,
-                                        const float2 xb, const WConst& k, float2& wpp,
-                                        float2& wph) {
-  const float2 sa = add2(Aa, Ab), pa = mul2(Aa, Ab);
-  const float2 q = fma2(sa, k.cm2om2, k.c5om);   // 5 Omega - 2 Omega^2 sa
-  const float2 r = fma2(sa, q, k.cm3);           // -3 + 5 Omega sa - 2 Omega^2 sa^2
-  const float2 D = mul2(pa, fma2(pa, k.c2om2, r));
-  const float2 va = mul2(Aa, fma2(Aa, k.cm2om, k.c3));  // A (3 - 2 Omega A)
-  const float2 vb = mul2(Ab, fma2(Ab, k.cm2om, k.c3));
+// at once, from the table values alpha = Omega A = Omega / (Omega + |xi|)
+// and the signed xi of both propagators (a at p + l/2, b at p - l/2).  With
+// h(x) = x (Omega + 3x) / (Omega + x)^3 (so that J = -sgn(xi) h(|xi|) / 4)
+// the weights are, times Omega^2 (the factor 1/Omega^2 is applied in the
+// combination of the partial sums, with the -1/4 and +1/4):
+//   Omega^2 D = Omega^2 h[|xi_a|, |xi_b|]
+//     = a_a a_b (5 (a_a + a_b) - 3 - 2 (a_a^2 + a_a a_b + a_b^2)),  a = alpha,
+//   Omega^2 S = Omega^2 (h_a + h_b) / (|xi_a| + |xi_b|)
+//     = (xi_a a_a^2 (3 - 2 a_a) + xi_b' a_b^2 (3 - 2 a_b)) / (xi_a + xi_b'),
+// from Omega^2 h(x) = x a^2 (3 - 2a) (Omega + 3x = (3 - 2a) (Omega + x)) and
+// xi_b' = xi_b carried over to the sign of xi_a: numerator and denominator
+// of S are sums of two terms of one sign, 3 - 2a lies in [1, 3), and the
+// constants are plain numbers.  The particle-particle weight is S for
+// propagators of one sign, D else, and the particle-hole weight the other
+// one.  The table holds |xi| no smaller than 1e-30 (sign kept): at xi_a =
+// xi_b = 0 both are 1, the common limit.
+__device__ __forceinline__ void weights(const float2 aa, const float2 xa, const float2 ab,
+                                        const float2 xb, float2& wpp, float2& wph) {
+  const float2 sa = add2(aa, ab), pa = mul2(aa, ab);
+  const float2 q = fma2(sa, make_float2(-2.f, -2.f), make_float2(5.f, 5.f));
+  const float2 r = fma2(sa, q, make_float2(-3.f, -3.f));  // -3 + 5 sa - 2 sa^2
+  const float2 D = mul2(pa, fma2(pa, make_float2(2.f, 2.f), r));
+  const float2 va = mul2(aa, fma2(aa, make_float2(-2.f, -2.f), make_float2(3.f, 3.f)));
+  const float2 vb = mul2(ab, fma2(ab, make_float2(-2.f, -2.f), make_float2(3.f, 3.f)));
   const float2 xs = make_float2(copysignf(xb.x, xa.x), copysignf(xb.y, xa.y));
-  const float2 num = fma2(mul2(xa, Aa), va, mul2(mul2(xs, Ab), vb));
+  const float2 num = fma2(mul2(xa, aa), va, mul2(mul2(xs, ab), vb));
   const float2 den = add2(xa, xs);
   const float2 S = mul2(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
   const float2 sg = mul2(xa, xb);
@@ -252,11 +241,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       __syncthreads();
       continue;
     }
-    // rows [row0, row0 + nvalid) of the point: its rows spread evenly over
-    // its tiles (at most 128 each)
-    const int tiles = pd.nrow_pad / kRows;
-    const int row0 = (tile * pd.nrow) / tiles;
-    const int nvalid = ((tile + 1) * pd.nrow) / tiles - row0;
+    // rows [row0, row0 + nvalid) of the point: the rows [row_lo, row_hi) the
+    // view computes spread evenly over their tiles (at most 128 each)
+    const int nr = pd.row_hi - pd.row_lo, tiles = (nr + kRows - 1) / kRows;
+    const int row0 = pd.row_lo + (tile * nr) / tiles;
+    const int nvalid = pd.row_lo + ((tile + 1) * nr) / tiles - row0;
     if constexpr (P::kPerLane == 2) {
       // every lane's first loop point has the parity pib of the first loop
       // point (neighbour pairs iy, iy + 1 with iy even, even row width), so
@@ -279,22 +268,20 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 
     if (warp < kProducers) {
       // ---------------------------------------------------------- producers
-      // BF16X3: pairs (A_q, A_q+1, xi_q, xi_q+1) of even q at ext, of odd q
-      // at ext + (n_ext + 1) / 2, read at the row's s_idx; 3xTF32: (A_q,
-      // xi_q) per point
+      // BF16X3: pairs (alpha_q, alpha_q+1, xi_q, xi_q+1) of even q at ext, of
+      // odd q at ext + (n_ext + 1) / 2, read at the row's s_idx; 3xTF32:
+      // (alpha_q, xi_q) per point
       const float4* ext = pd.ext;
       const float2* ext2 = reinterpret_cast<const float2*>(pd.ext);
-      const WConst wk((float)pd.lam[0]);
       const uint32_t fbytes = (uint32_t)npad * kRowBytes;  // one F part per K-block
-      // this warp's rows with an l, in units of kUnitRows rows
-      const int nrw = max(0, min(kRows / kProducers, (nvalid - warp + kProducers - 1) / kProducers));
-      const int nunits = (nrw + kUnitRows - 1) / kUnitRows;
       // The table gathers run kDepth - 1 units ahead of the arithmetic, in a
       // ring of register buffers, across K-block boundaries too (the gathers
       // of the next K-block's first units are issued while the last units of
-      // this one are computed).  Every warp gathers all kUnits units of a
-      // K-block (rows without an l read offset 0) and computes only those
-      // with an l (the accumulator rows of the others are never read).
+      // this one are computed).  Every warp gathers and computes all kUnits
+      // units of a K-block: rows without an l read offset 0 and their
+      // accumulator rows are never read.  A branch-free K-block lets the
+      // compiler interleave the units, which costs less than the work on
+      // the rows without an l (at most 127 of a tile).
       using Buf = typename P::Buf;
       auto load_unit = [&](int u, int pb, Buf& b) {
         if constexpr (P::kPerLane == 2) {  // one row, two loop points: one pair each side
@@ -315,12 +302,10 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
         float2 wpp, wph;
         if constexpr (P::kPerLane == 2)
           weights(make_float2(b.v[0].x, b.v[0].y), make_float2(b.v[0].z, b.v[0].w),
-                  make_float2(b.v[1].x, b.v[1].y), make_float2(b.v[1].z, b.v[1].w), wk, wpp,
-                  wph);
+                  make_float2(b.v[1].x, b.v[1].y), make_float2(b.v[1].z, b.v[1].w), wpp, wph);
         else
           weights(make_float2(b.v[0].x, b.v[2].x), make_float2(b.v[0].y, b.v[2].y),
-                  make_float2(b.v[1].x, b.v[3].x), make_float2(b.v[1].y, b.v[3].y), wk, wpp,
-                  wph);
+                  make_float2(b.v[1].x, b.v[3].x), make_float2(b.v[1].y, b.v[3].y), wpp, wph);
         if constexpr (PREC == TUFRG_BF16X3) {
           uint32_t v[4];
           split_bf16(wpp, v[0], v[1]);
@@ -376,23 +361,15 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
         // (after the item's last K-block the ring gathers this one's first
         // units again: valid addresses, no branch)
         const int pbn = kb + 1 < cnt ? __ldg(pd.kbase + k0 + KB + P::kPerLane * lane) : pb;
-        // warps with all kUnits units run the K-block without a branch, so
-        // the compiler can interleave the units' arithmetic
-        auto kblock = [&](auto full) {
 #pragma unroll
-          for (int u = 0; u < kUnits; ++u) {
-            const int t = u + kDepth - 1;  // unit gathered now, into the slot unit u - 1 freed
-            if (t < kUnits)
-              load_unit(t, pb, buf[t % kDepth]);
-            else
-              load_unit(t - kUnits, pbn, buf[t % kDepth]);
-            if (decltype(full)::value || u < nunits) do_unit(u, stg, buf[u % kDepth]);
-          }
-        };
-        if (nunits == kUnits)
-          kblock(std::true_type{});
-        else
-          kblock(std::false_type{});
+        for (int u = 0; u < kUnits; ++u) {
+          const int t = u + kDepth - 1;  // unit gathered now, into the slot unit u - 1 freed
+          if (t < kUnits)
+            load_unit(t, pb, buf[t % kDepth]);
+          else
+            load_unit(t - kUnits, pbn, buf[t % kDepth]);
+          do_unit(u, stg, buf[u % kDepth]);
+        }
         pb = pbn;
         fence_proxy_async();
         __syncwarp();
@@ -504,13 +481,13 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
 
 constexpr int kTableBlock = 256;
 
-// Per-scale FP32 table (A, xi) = (1/(Omega + |xi|), xi) with a wrap-around
-// halo of hx, hy points on each side, so that p +- l/2 needs no wrapping
-// (FP32 arithmetic: the table is FP32, and GB300's FP64 division would
-// dominate this kernel).  |xi| is floored at 1e-30 (sign kept).  BF16X3
-// layout: float4 (A_q, A_q+1, xi_q, xi_q+1) for even q in the first half,
-// for odd q in the second (the last entry repeated past the end); 3xTF32:
-// float2 (A_q, xi_q).  One thread per entry q, the neighbour's values by a
+// Per-scale FP32 table (alpha, xi) = (Omega / (Omega + |xi|), xi) with a
+// wrap-around halo of hx, hy points on each side, so that p +- l/2 needs no
+// wrapping (FP32 arithmetic: the table is FP32, and GB300's FP64 division
+// would dominate this kernel).  |xi| is floored at 1e-30 (sign kept).
+// BF16X3 layout: float4 (alpha_q, alpha_q+1, xi_q, xi_q+1) for even q in the
+// first half, for odd q in the second (the last entry repeated past the
+// end); 3xTF32: float2 (alpha_q, xi_q).  One thread per entry q, the neighbour's values by a
 // shuffle.  Block 0 also resets the work-item counter of the contraction
 // that follows.
 template <int PREC>
@@ -526,7 +503,8 @@ __global__ void __launch_bounds__(kTableBlock)
   const int q = (blockIdx.x - prefix[p]) * kTableBlock + threadIdx.x;
   auto entry = [&](int e) {
     const float xi = __ldg(pd.xiext + min(e, n_ext - 1));
-    return make_float2(__frcp_rn(omf + fabsf(xi)), copysignf(fmaxf(fabsf(xi), 1e-30f), xi));
+    const float x = fmaxf(fabsf(xi), 1e-30f);
+    return make_float2(__fdiv_rn(omf, omf + x), copysignf(x, xi));
   };
   const float2 a = entry(q);
   if constexpr (PREC == TUFRG_BF16X3) {

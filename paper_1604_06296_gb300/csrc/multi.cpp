@@ -60,7 +60,7 @@ int smem_optin() {
 int view_default_kbps(const MultiView& v) {
   if (v.tc_prec == TUFRG_FP64) return 0;
   long long work = 0;  // K-block x tile units
-  for (const PointDesc& d : v.h) work += (long long)d.nkb * (d.nrow_pad / 128);
+  for (const PointDesc& d : v.h) work += (long long)d.nkb * ((d.row_hi - d.row_lo + 127) / 128);
   const long long S = sm_count(), cap = max_kbps(v.tc_prec);
   const long long waves = std::max(1LL, (work + S * cap - 1) / (S * cap));
   const long long kbps = (work + S * waves - 1) / (S * waves);
@@ -88,7 +88,7 @@ tufrg_status view_set_kbps(MultiView& v, int kbps, cudaStream_t st) {
     int cols = 32;
     while (cols < d.nsets * 2 * d.npad) cols *= 2;
     v.tmem_cols = std::max(v.tmem_cols, cols);
-    const int tiles = d.nrow_pad / 128;
+    const int nr = d.row_hi - d.row_lo, tiles = (nr + 127) / 128;
     // the tiles of one K range one after the other (and ordered as a group):
     // CTAs running at the same time then read the same F columns, from L2
     // after the first
@@ -96,7 +96,7 @@ tufrg_status view_set_kbps(MultiView& v, int kbps, cudaStream_t st) {
       const int kb0 = sp * kbps, cnt = std::min(kbps, d.nkb - kb0);
       long long cost = 0;  // producers: ~ valid rows per K-block; tensor cores: ~ pair columns
       for (int t = 0; t < tiles; ++t)
-        cost += (long long)cnt * (2 * ((t + 1) * d.nrow / tiles - t * d.nrow / tiles) + d.npad);
+        cost += (long long)cnt * (2 * ((t + 1) * nr / tiles - t * nr / tiles) + d.npad);
       for (int t = 0; t < tiles; ++t) items.push_back({make_int4(i, t, kb0, cnt), cost});
     }
   }
@@ -154,6 +154,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     for (int t = 0; t < 4; ++t) d.gy_off[t] = c->proj.gy_off[t];
     d.npair = c->npair;
     d.nrow = c->nrow;
+    d.row_lo = c->shard_lo;
+    d.row_hi = c->shard_hi;
     d.nfx = c->nfx;
     d.nfy = c->nfy;
     d.hx = c->tc_hx;
@@ -206,12 +208,14 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.skip = skip ? skip[i] : nullptr;
     const int cnt[kKinds] = {
         tc ? table_ctas(d.n_ext) : 0,
-        tc ? rows_reduce_ctas(d.npair, d.nrow) : 0,
+        tc ? rows_reduce_ctas(d.npair, d.row_hi - d.row_lo) : 0,
         d.feedback ? 3 * d.nl : 0,
         d.feedback ? dft_ctas(d.nkeys) : 0,
         grouped && d.feedback ? d.gy_off[3] : 0,
         contract_ctas(d.nl, grouped),
         d.nl,
+        d.nrow,
+        contract_ctas(d.nrow, grouped),
         d.nrow,
     };
     for (int k = 0; k < kKinds; ++k)

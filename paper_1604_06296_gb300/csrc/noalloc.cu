@@ -13,14 +13,19 @@
 // The array is kNoallocBytes (16 MiB) large; every GPU that loads the
 // library holds it until the process exits.  Problems whose tables do not
 // fit are rejected with TUFRG_ERR_ARG before any device work.  In host code
-// the array's name is only a stand-in: its device address is looked up once
-// per device with cudaGetSymbolAddress (on the first call made with that
-// device current) and passed to the kernels.  All calls share the array, so
+// the array's name is only a stand-in: its device address is looked up with
+// cudaGetSymbolAddress on the first call in each CUDA context (the first call
+// on a device, and again after a reset of the device) and passed to the
+// kernels; that first call should come before any stream capture.  All calls share the array, so
 // calls that overlap on the GPU race; every call rewrites each region of the
 // array before reading it, so nothing left by an earlier call reaches a
 // result.  No cudaMalloc, cudaFree or other allocating CUDA routine is used.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -30,23 +35,46 @@ namespace {
 constexpr size_t kNoallocBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
+// The array's device address per CUDA context (a device reset makes a new
+// context, whose module, and array, live at a new address).
+struct ScratchEntry {
+  CUcontext ctx;
+  void* addr;
+};
+std::vector<ScratchEntry> g_scratch_addr;
 std::mutex g_scratch_mutex;
+PFN_cuCtxGetCurrent_v4000 g_ctx_get_current = nullptr;
 
-// Device address of the static array on the current device.
+// Device address of the static array in the current context.
 tufrg_status scratch_address(void** out) {
-  int dev = 0;
-  TUFRG_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return TUFRG_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) return tufrg_cuda_fail(e);
-    g_scratch_addr[dev] = p;
+  if (!g_ctx_get_current) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return TUFRG_ERR_CUDA;
+    g_ctx_get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
   }
-  *out = g_scratch_addr[dev];
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return TUFRG_ERR_CUDA;
+  if (!ctx) {  // no context bound yet: the runtime's primary context of the current device
+    int dev = 0;
+    TUFRG_CUDA(cudaGetDevice(&dev));
+    TUFRG_CUDA(cudaSetDevice(dev));
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return TUFRG_ERR_CUDA;
+  }
+  for (const ScratchEntry& e : g_scratch_addr)
+    if (e.ctx == ctx) {
+      *out = e.addr;
+      return TUFRG_OK;
+    }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) return tufrg_cuda_fail(e);
+  g_scratch_addr.push_back({ctx, p});
+  *out = p;
   return TUFRG_OK;
 }
 

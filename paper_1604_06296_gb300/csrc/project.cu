@@ -13,6 +13,9 @@
 //   to_bond   -- Bt for all channels and l              (Nl x 3 CTAs per point)
 //   dft_keys  -- F for every key, one warp per key       (lanes over l')
 //   contract_terms -- T and the basis change, per (target channel, 4 l)
+// In a flow of a point-group covariant state the last step runs only at the
+// representative l of the loop rows (the products then write every l a row
+// serves); the Fourier keys still sum over every l.
 // The phase e^{i l.Y} is the only l dependence of a term, and the terms of a
 // target channel take few distinct Y (41 at Nb = 13, 81 at Nb = 25), so the
 // sums regroup (exactly, by linearity) as
@@ -179,16 +182,25 @@ template <class T, int NF>
 __global__ void __launch_bounds__(256)
     contract_terms_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
                     const double* __restrict__ ybase,
-                    const typename C2<T>::type* __restrict__ fkbase, double* __restrict__ vbase) {
+                    const typename C2<T>::type* __restrict__ fkbase, double* __restrict__ vbase,
+                    int rows) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
   const int nb = NF ? NF : pd.nb, nff = NF ? NF : pd.nff, nl = pd.nl, nd = pd.nd;
-  const int groups = (nl + kTermsL - 1) / kTermsL;
+  // output slots: every l, or the representative l of every loop row
+  const int nout = rows ? pd.nrow : nl;
+  const int groups = (nout + kTermsL - 1) / kTermsL;
   const int loc = blockIdx.x - prefix[p];
-  const int t = loc / groups, l0 = (loc % groups) * kTermsL;
-  const int nlb = min(kTermsL, nl - l0);  // l of this CTA
+  const int t = loc / groups, q0 = (loc % groups) * kTermsL;
+  const int nlb = min(kTermsL, nout - q0);  // slots of this CTA
+  __shared__ int sl[kTermsL];               // l of each slot (the last one repeated)
+  if (threadIdx.x < kTermsL) {
+    const int q = q0 + min((int)threadIdx.x, nlb - 1);
+    sl[threadIdx.x] = rows ? pd.rowimg[pd.rowimg_ptr[q]].x : q;
+  }
+  __syncthreads();
   extern __shared__ double2 sm2[];
   V* Tm = reinterpret_cast<V*>(sm2);       // [kTermsL][nb][nb]
   V* tmp = Tm + kTermsL * nb * nb;      // [kTermsL][nb][nff]
@@ -201,7 +213,7 @@ __global__ void __launch_bounds__(256)
   if (!pd.feedback) {
     for (int e = threadIdx.x; e < nlb * (int)n2; e += blockDim.x) {
       const int j = e / (int)n2, r = e % (int)n2;
-      const size_t o = ((size_t)t * nl + l0 + j) * n2 + r;
+      const size_t o = ((size_t)t * nl + sl[j]) * n2 + r;
       vbase[pd.off_state + o] = (r == 0 ? U : 0.0) + own_sign * ybase[pd.off_state + o];
     }
     return;
@@ -209,7 +221,7 @@ __global__ void __launch_bounds__(256)
   for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
   for (int e = threadIdx.x; e < kTermsL * nd; e += blockDim.x) {
     const int j = e / nd, d = e % nd;
-    const int l = l0 + min(j, nlb - 1);
+    const int l = sl[j];
     const int ix = l / pd.ncy, iy = l - ix * pd.ncy;
     qx[e] = phase_at(pd, ix * nd + d, T());
     qy[e] = phase_at(pd, (pd.ncx + iy) * nd + d, T());
@@ -270,13 +282,14 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   // V_mn = V0 + own + Re sum_b1 c_m(b1) tmp[b1][n]
-  const size_t base = pd.off_state + ((size_t)t * nl + l0) * n2;
+  const size_t base = pd.off_state + (size_t)t * nl * n2;
   for (int m = r0; m < nff; m += rstep) {
     if (n >= nff) continue;
     const int mn = m * nff + n;
     double yv[kTermsL];
 #pragma unroll
-    for (int jj = 0; jj < kTermsL; ++jj) yv[jj] = jj < nlb ? ybase[base + jj * n2 + mn] : 0.0;
+    for (int jj = 0; jj < kTermsL; ++jj)
+      yv[jj] = jj < nlb ? ybase[base + (size_t)sl[jj] * n2 + mn] : 0.0;
     T acc[kTermsL];
 #pragma unroll
     for (int jj = 0; jj < kTermsL; ++jj) acc[jj] = 0;
@@ -291,7 +304,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int jj = 0; jj < kTermsL; ++jj)
       if (jj < nlb)
-        vbase[base + jj * n2 + mn] = (mn == 0 ? U : 0.0) + own_sign * yv[jj] + (double)acc[jj];
+        vbase[base + (size_t)sl[jj] * n2 + mn] =
+            (mn == 0 ? U : 0.0) + own_sign * yv[jj] + (double)acc[jj];
   }
 }
 
@@ -380,24 +394,34 @@ template <class T, int NF>
 __global__ void __launch_bounds__(1024)
     contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
                     const double* __restrict__ ybase,
-                    const typename C2<T>::type* __restrict__ hbase, double* __restrict__ vbase) {
+                    const typename C2<T>::type* __restrict__ hbase, double* __restrict__ vbase,
+                    int rows) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
   const int nff = NF ? NF : pd.nff, nl = pd.nl;
-  const int groups = (nl + kContractL - 1) / kContractL;
+  // output slots: every l, or the representative l of every loop row
+  const int nout = rows ? pd.nrow : nl;
+  const int groups = (nout + kContractL - 1) / kContractL;
   const int loc = blockIdx.x - prefix[p];
-  const int t = loc / groups, l0 = (loc % groups) * kContractL;
-  const int nlb = min(kContractL, nl - l0);  // l of this CTA
+  const int t = loc / groups, q0 = (loc % groups) * kContractL;
+  const int nlb = min(kContractL, nout - q0);  // slots of this CTA
+  __shared__ int sl[kContractL];               // l of each slot (the last one repeated)
+  if (threadIdx.x < kContractL) {
+    const int q = q0 + min((int)threadIdx.x, nlb - 1);
+    sl[threadIdx.x] = rows ? pd.rowimg[pd.rowimg_ptr[q]].x : q;
+  }
+  __syncthreads();
   const int n2 = nff * nff, n2p = hstride(nff);
   const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
   const double U = pd.U;
-  const size_t base = pd.off_state + ((size_t)t * nl + l0) * n2;
+  const size_t base = pd.off_state + (size_t)t * nl * n2;  // l = sl[j] at base + sl[j] n2
   if (!pd.feedback) {
     for (int e = threadIdx.x; e < nlb * n2; e += blockDim.x) {
-      const int r = e % n2;
-      vbase[base + e] = (r == 0 ? U : 0.0) + own_sign * ybase[base + e];
+      const int j = e / n2, r = e % n2;
+      const size_t o = base + (size_t)sl[j] * n2 + r;
+      vbase[o] = (r == 0 ? U : 0.0) + own_sign * ybase[o];
     }
     return;
   }
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(1024)
   double yv[kContractL];  // the state entries group 0 adds to
 #pragma unroll
   for (int j = 0; j < kContractL; ++j)
-    yv[j] = grp == 0 && mn < n2 && j < nlb ? ybase[base + (size_t)j * n2 + mn] : 0.0;
+    yv[j] = grp == 0 && mn < n2 && j < nlb ? ybase[base + (size_t)sl[j] * n2 + mn] : 0.0;
   T acc[kContractL];
 #pragma unroll
   for (int j = 0; j < kContractL; ++j) acc[j] = 0;
@@ -431,7 +455,7 @@ __global__ void __launch_bounds__(1024)
     asm volatile("cp.async.commit_group;" ::: "memory");
     for (int e = threadIdx.x; e < cn * kContractL; e += blockDim.x) {
       const int yi = e / kContractL, j = e - yi * kContractL;
-      ph[e] = yphase_at(pd, (size_t)(y0 + c0 + yi) * nl + l0 + min(j, nlb - 1), T());
+      ph[e] = yphase_at(pd, (size_t)(y0 + c0 + yi) * nl + sl[j], T());
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
@@ -461,7 +485,7 @@ __global__ void __launch_bounds__(1024)
       T a = acc[j];
       for (int g = 1; g < ng; ++g) a += red[((size_t)g * kContractL + j) * tpg + mn];
       if (j < nlb)
-        vbase[base + (size_t)j * n2 + mn] =
+        vbase[base + (size_t)sl[j] * n2 + mn] =
             (mn == 0 ? U : 0.0) + own_sign * yv[j] + (double)(a * inv_nl);
     }
   }
@@ -507,12 +531,24 @@ size_t contract_smem(const MultiView& v) {
   return m;
 }
 
+// the largest dynamic shared memory a kernel may take: the device limit less
+// its static shared memory
+template <class K>
+cudaError_t allow_dynamic_smem(K* kernel, int optin) {
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)a.sharedSizeBytes);
+}
+
 template <class T>
 tufrg_status prepare_typed(const MultiView& v) {
   const int smem = smem_optin();
+  // (the two contract kernels also hold a few bytes of static shared memory)
   if ((int)bond_smem<T>(v) > smem || (int)dft_smem<T>(v) > smem ||
-      (int)overlap_smem<T>(v) > smem || (int)contract_smem<T>(v) > smem ||
-      (int)contract_terms_smem<T>(v) > smem)
+      (int)overlap_smem<T>(v) > smem || (int)contract_smem<T>(v) + 64 > smem ||
+      (int)contract_terms_smem<T>(v) + 64 > smem)
     return TUFRG_ERR_ARG;
   TUFRG_CUDA(cudaFuncSetAttribute(dft_keys_kernel<T>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -522,15 +558,11 @@ tufrg_status prepare_typed(const MultiView& v) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(to_bond_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(contract_terms_kernel<T, NF>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(contract_terms_kernel<T, NF>, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(overlap_kernel<T, NF>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(contract_kernel<T, NF>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(contract_kernel<T, NF>, smem);
   });
   TUFRG_CUDA(e);
   return TUFRG_OK;
@@ -538,7 +570,8 @@ tufrg_status prepare_typed(const MultiView& v) {
 
 template <class T>
 tufrg_status project_typed(const MultiView& v, const double* y, double* out, void* btv,
-                           void* fkv, cudaStream_t st) {
+                           void* fkv, cudaStream_t st, bool rows) {
+  const int kind = rows ? kKindContractRows : kKindContract;
   using V = typename C2<T>::type;
   V* bt = reinterpret_cast<V*>(btv);
   V* fkey = reinterpret_cast<V*>(fkv);
@@ -557,8 +590,8 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
   if (!v.proj_grouped) {
     with_nf(v.nf_uniform, [&](auto nf) {
       contract_terms_kernel<T, decltype(nf)::value>
-          <<<v.total(kKindContract), 256, contract_terms_smem<T>(v), st>>>(
-              v.d, v.dprefix(kKindContract), v.n, y, fkey, out);
+          <<<v.total(kind), 256, contract_terms_smem<T>(v), st>>>(
+              v.d, v.dprefix(kind), v.n, y, fkey, out, rows ? 1 : 0);
     });
     TUFRG_CUDA(cudaGetLastError());
     return TUFRG_OK;
@@ -575,8 +608,8 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
   const int cthreads = contract_groups(v.nff_max) * contract_tpg(v.nff_max);
   with_nf(v.nf_uniform, [&](auto nf) {
     contract_kernel<T, decltype(nf)::value>
-        <<<v.total(kKindContract), cthreads, contract_smem<T>(v), st>>>(
-            v.d, v.dprefix(kKindContract), v.n, y, bt, out);
+        <<<v.total(kind), cthreads, contract_smem<T>(v), st>>>(
+            v.d, v.dprefix(kind), v.n, y, bt, out, rows ? 1 : 0);
   });
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
@@ -601,9 +634,9 @@ tufrg_status prepare_project_multi(const MultiView& v) {
 }
 
 tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
-                                  void* bt, void* fkey, cudaStream_t st) {
-  return prec == TUFRG_FP64 ? project_typed<double>(v, y, out, bt, fkey, st)
-                            : project_typed<float>(v, y, out, bt, fkey, st);
+                                  void* bt, void* fkey, cudaStream_t st, bool rows) {
+  return prec == TUFRG_FP64 ? project_typed<double>(v, y, out, bt, fkey, st, rows)
+                            : project_typed<float>(v, y, out, bt, fkey, st, rows);
 }
 
 }  // namespace tufrg

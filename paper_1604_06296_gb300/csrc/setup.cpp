@@ -282,6 +282,8 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
                                    -c->nfy / 4 + jy * (c->nfy / (2 * c->ncy))));
     }
   c->nrow = (int)rowshift.size();
+  c->shard_lo = 0;
+  c->shard_hi = c->nrow;
   c->c4v = c4v;
   std::vector<int2> lrow(c->nl);
   for (int r = 0; r < c->nrow; ++r)
