@@ -468,6 +468,29 @@ def run_scan(args, rank, world, local):
     return 0
 
 
+def run_profile_loops(args, local):
+    """The workload's loop stage launched args.profile_loops times (for a
+    profiler capture of the contraction kernel); prints the event-timed
+    kernel and stage milliseconds."""
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    torch.cuda.set_device(local)
+    wl = args.workload if args.workload in ("cfg2", "cfg5") else WORKLOAD
+    c = W.config(wl)
+    tp = rank_tprime(0, wl)
+    s = tufrg.Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"],
+                     c["nf"], precision=args.precision)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = []
+    for _ in range(args.profile_loops):
+        flush.zero_()
+        out.append(s.profile_loops(0.5, 1))
+    s.close()
+    print(json.dumps({"workload": workload_desc(tp, wl), "precision": args.precision,
+                      "kernel_ms_stage_ms": out}))
+    return 0
+
+
 def run_sharded(args, rank, world, local):
     """One point's right-hand side with its loop rows split over the ranks
     (strong scaling): each rank computes its rows, one NCCL all-gather of the
@@ -1039,12 +1062,17 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="one point with its loop rows split over the ranks (strong scaling); "
                          "a step is one RHS evaluation")
+    ap.add_argument("--profile-loops", type=int, default=0, metavar="N",
+                    help="only set up the workload's point and launch its loop stage N times "
+                         "(table, contraction, split-K combination), for a profiler")
     ap.add_argument("--points", type=int, default=256, help="scan: points per GPU")
     ap.add_argument("--epochs", type=int, default=40, help="learned: training epochs")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.profile_loops:
+        return run_profile_loops(args, local)
     if args.shard:
         return run_sharded(args, rank, world, local)
     if args.workload == "scan":

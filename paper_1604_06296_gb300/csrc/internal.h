@@ -123,7 +123,6 @@ struct PointDesc {
   const float2* phase_f;
   const double2* yphase;  // [phase positions Y][nl] e^{i l.Y}
   const float2* yphase_f;
-  const int4* keys;
   const int* row_ptr;  // term form: [3][nb*nb+1] CSR over output pairs
   const int4* terms;   //   (key, 2Y_x + dmax, 2Y_y + dmax, sign)
   const int4* gslot;   // grouped form: [positions Y][gmaxt] (b1*nb+b2, key, sign, 0)
@@ -136,8 +135,8 @@ struct PointDesc {
 enum : int {
   kKindTable = 0,  // per-scale FP32 halo table
   kKindReduce,     // split-K combination of the tensor-core partial sums
-  kKindBond,       // projections: to bond space
-  kKindDft,        // projections: Fourier keys
+  kKindBond,       // projections: DFT of the state along y at the Fourier positions
+  kKindDft,        // projections: DFT along x and bond space, the keys of a position
   kKindOverlap,    // projections: key sums and basis change per phase position
   kKindContract,   // projections: phase sums over the positions, per l
   kKindProducts,   // V chi V
@@ -215,7 +214,6 @@ struct tufrg_ctx {
   float2* d_phase_f = nullptr;
   double2* d_yphase = nullptr;     // [ProjTables::gy][nl] e^{i l.Y}, FP64 and FP32
   float2* d_yphase_f = nullptr;
-  int4* d_key = nullptr;           // [nkeys] (src, b3*nb+b4, dx, dy)
   int* d_row_ptr = nullptr;        // term form: [3][nb*nb+1]
   int4* d_terms = nullptr;         //   [total terms] (key, dx, dy, sign)
   int term_off[3] = {0, 0, 0};
@@ -241,9 +239,9 @@ struct tufrg_ctx {
   double* d_partial = nullptr;     // [ksplit][2][mpad][nrow] split-K partial sums
   double* d_chi = nullptr;         // [2][nl][nff][nff]
   double* d_V = nullptr;           // [3][nl][nff][nff]
-  double2* d_bt = nullptr;         // [3][nb*nb][nl] bond-space propagators, then the
-                                   // overlap sums H [positions Y][nff][nff] (bt_region)
-  double2* d_fkey = nullptr;       // [nkeys] Fourier values
+  double2* d_bt = nullptr;         // the state's DFT along y, then the overlap sums
+                                   // H [positions Y][nff][nff] (bt_region)
+  double2* d_fkey = nullptr;       // Fourier values of the keys, dense (fkey_elems)
 
   // integrator of tufrg_flow_* (allocated on first use) and the library's own
   // stream: flows run there (graph capture needs a non-legacy stream) and are
@@ -360,13 +358,16 @@ int table_ctas(int n_ext);
 tufrg_status prepare_loops_tc_multi(const MultiView& v);
 tufrg_status prepare_project_multi(const MultiView& v);
 tufrg_status prepare_products_multi(const MultiView& v);
-int dft_ctas(int nkeys);
+int bond_ctas(int ncx, int nff);
+int dft_ctas(int nd);
+// Fourier values of the keys, numbered densely over (source, 2X_x, 2X_y, b3, b4)
+size_t fkey_elems(int nd, int nb);
 int contract_ctas(int nl, bool grouped);
 // the projections of a view take the grouped form from this form-factor count on
 constexpr int kGroupedNff = 21;
-// elements of a point's bond-space workspace: the bond-space propagators
-// [3][nb*nb][nl], later reused for the overlap sums [positions Y][nff][nff]
-size_t bt_region(int nb, int nl, int nff, int ny_total);
+// elements of a point's projection workspace: the state's DFT along y
+// [3][ncx][nd][nff*nff], later reused for the overlap sums [positions Y][nff][nff]
+size_t bt_region(int ncx, int nd, int nff, int ny_total);
 // projections and products of every point; bt, fkey: packed workspaces.
 // rows: the projected couplings at the representative l of each loop row
 // only (the wedge of a point-group covariant state)

@@ -173,8 +173,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.off_fkey = (long long)off_fkey;
     off_state += (size_t)3 * c->nl * c->nff * c->nff;
     off_chi += (size_t)2 * c->nl * c->nff * c->nff;
-    off_bt += bt_region(c->nb, c->nl, c->nff, c->proj.gy_off[3]);
-    off_fkey += (size_t)c->proj.nkeys;
+    off_bt += bt_region(c->ncx, 2 * c->proj.dmax + 1, c->nff, c->proj.gy_off[3]);
+    off_fkey += fkey_elems(2 * c->proj.dmax + 1, c->nb);
     d.tab = c->d_tab;
     d.ext = c->d_ext;
     d.xiext = c->d_xiext;
@@ -199,7 +199,6 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.phase_f = c->d_phase_f;
     d.yphase = c->d_yphase;
     d.yphase_f = c->d_yphase_f;
-    d.keys = c->d_key;
     d.row_ptr = c->d_row_ptr;
     d.terms = c->d_terms;
     d.gslot = c->d_gslot;
@@ -209,8 +208,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     const int cnt[kKinds] = {
         tc ? table_ctas(d.n_ext) : 0,
         tc ? rows_reduce_ctas(d.npair, d.row_hi - d.row_lo) : 0,
-        d.feedback ? 3 * d.nl : 0,
-        d.feedback ? dft_ctas(d.nkeys) : 0,
+        d.feedback ? bond_ctas(d.ncx, d.nff) : 0,
+        d.feedback ? dft_ctas(d.nd) : 0,
         grouped && d.feedback ? d.gy_off[3] : 0,
         contract_ctas(d.nl, grouped),
         d.nl,

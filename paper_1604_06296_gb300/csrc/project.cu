@@ -10,8 +10,7 @@
 // are scale independent and built once at setup.  Bosonic momenta are the
 // coarse-grid points in [-pi, pi) (folding reading of the half-momentum
 // convention).  Three kernels compute the keys and the terms (term form):
-//   to_bond   -- Bt for all channels and l              (Nl x 3 CTAs per point)
-//   dft_keys  -- F for every key, one warp per key       (lanes over l')
+//   bond_dft1, bond_dft2 -- F for every key (below)
 //   contract_terms -- T and the basis change, per (target channel, 4 l)
 // In a flow of a point-group covariant state the last step runs only at the
 // representative l of the loop rows (the products then write every l a row
@@ -94,82 +93,112 @@ __host__ __device__ inline int contract_ychunk(int ny, int nff, int vbytes) {
   return ny < c ? (ny > 0 ? ny : 1) : (c > 0 ? c : 1);
 }
 
-constexpr int kDftWarps = 8;
 
-template <class T, int NF>
-__global__ void to_bond_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
-                               int np, const double* __restrict__ ybase,
-                               typename C2<T>::type* __restrict__ btbase) {
+// Fourier values of the keys, in two passes (each key (source S, bonds b3,
+// b4, position X) is F = sum_l' e^{i l'.X} Bt^S_{b3 b4}(l') with
+// Bt = C^T B C, C[a][b] = c_a(b); by linearity F = (C^T Bh^S(X) C)_{b3 b4}
+// with the state's own Fourier value Bh^S_ab(X) = sum_l' e^{i l'.X} B^S_ab(l'),
+// and e^{i l'.X} = e^{i l'_x X_x} e^{i l'_y X_y} on the coarse grid):
+//   bond_dft1 -- P1[S][ix][dy][ab] = sum_iy e^{i l_y(iy) Y_dy} B^S_ab(ix, iy)
+//   bond_dft2 -- Bh(X) = sum_ix e^{i l_x(ix) X_dx} P1[S][ix][dy][.], then
+//                F[S][dx][dy][b3 b4] = (C^T Bh(X) C)_{b3 b4}
+// The keys are numbered densely over (S, dx, dy, b3 b4): the X of all keys
+// lie on a grid of nd x nd half-integer positions (nd = 9 for Nff = 13..25
+// on grids of 16 or more points per direction).
+constexpr int kDft1Threads = 128;
+constexpr int kNdPass = 9;
+
+template <class T>
+__global__ void __launch_bounds__(kDft1Threads)
+    bond_dft1_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
+                     const double* __restrict__ ybase, typename C2<T>::type* __restrict__ p1base) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int nl = pd.nl, nff = NF ? NF : pd.nff, nb = NF ? NF : pd.nb;
+  const int nff2 = pd.nff * pd.nff, nd = pd.nd, ncx = pd.ncx, ncy = pd.ncy;
+  const int chunks = (nff2 + kDft1Threads - 1) / kDft1Threads;
   const int loc = blockIdx.x - prefix[p];
-  const int l = loc % nl, ch = loc / nl;
+  const int chunk = loc % chunks, rest = loc / chunks, ix = rest % ncx, src = rest / ncx;
   extern __shared__ double2 sm2[];
-  V* cs = reinterpret_cast<V*>(sm2);     // [nff][nb]
-  V* tmp = cs + nff * nb;                // [nff][nb]
-  T* Bs = reinterpret_cast<T*>(tmp + nff * nb);  // [nff][nff]
-  const double* B = ybase + pd.off_state + ((size_t)ch * nl + l) * nff * nff;
-  V* bt = btbase + pd.off_bt;
-  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
-  for (int e = threadIdx.x; e < nff * nff; e += blockDim.x) Bs[e] = (T)B[e];
+  V* ph = reinterpret_cast<V*>(sm2);  // [ncy][nd] e^{i l_y Y}
+  for (int e = threadIdx.x; e < ncy * nd; e += blockDim.x)
+    ph[e] = phase_at(pd, (ncx + e / nd) * nd + e % nd, T());
   __syncthreads();
-  // tmp[a][b4] = sum_b B[a][b] c_b(b4)
-  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) {
-    const int a = e / nb, b4 = e % nb;
-    V s = {0, 0};
-    for (int b = 0; b < nff; ++b) {
-      const T v = Bs[a * nff + b];
-      const V cc = cs[b * nb + b4];
-      s.x = fma(v, cc.x, s.x);
-      s.y = fma(v, cc.y, s.y);
+  const int ab = chunk * kDft1Threads + threadIdx.x;
+  if (ab >= nff2) return;
+  const double* B = ybase + pd.off_state + ((size_t)src * pd.nl + (size_t)ix * ncy) * nff2 + ab;
+  V* out = p1base + pd.off_bt + ((size_t)(src * ncx + ix) * nd) * nff2 + ab;
+  // positions in passes of kNdPass (one pass for the bases of complete shells
+  // on grids that resolve them; small grids alias more bond sums to more X)
+  for (int d0 = 0; d0 < nd; d0 += kNdPass) {
+    V acc[kNdPass];
+#pragma unroll
+    for (int d = 0; d < kNdPass; ++d) acc[d] = {0, 0};
+#pragma unroll 4
+    for (int iy = 0; iy < ncy; ++iy) {
+      const T b = (T)__ldg(B + (size_t)iy * nff2);
+      const V* q = ph + iy * nd + d0;
+#pragma unroll
+      for (int d = 0; d < kNdPass; ++d)
+        if (d0 + d < nd) {
+          acc[d].x = fma(q[d].x, b, acc[d].x);
+          acc[d].y = fma(q[d].y, b, acc[d].y);
+        }
     }
-    tmp[e] = s;
-  }
-  __syncthreads();
-  // Bt[b3][b4] = sum_a c_a(b3) tmp[a][b4]
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int b3 = e / nb, b4 = e % nb;
-    V s = {0, 0};
-    for (int a = 0; a < nff; ++a) s = cfma(cs[a * nb + b3], tmp[a * nb + b4], s);
-    bt[((size_t)ch * nb * nb + e) * nl + l] = s;
+#pragma unroll
+    for (int d = 0; d < kNdPass; ++d)
+      if (d0 + d < nd) out[(size_t)(d0 + d) * nff2] = acc[d];
   }
 }
 
-template <class T>
-__global__ void dft_keys_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
-                                int np, const typename C2<T>::type* __restrict__ btbase,
-                                typename C2<T>::type* __restrict__ fkbase) {
+template <class T, int NF>
+__global__ void __launch_bounds__(256)
+    bond_dft2_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
+                     const typename C2<T>::type* __restrict__ p1base,
+                     typename C2<T>::type* __restrict__ fkbase) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int ncx = pd.ncx, ncy = pd.ncy, nd = pd.nd, nb = pd.nb, nl = pd.nl;
+  const int nff = NF ? NF : pd.nff, nb = NF ? NF : pd.nb, nff2 = nff * nff;
+  const int nd = pd.nd, ncx = pd.ncx;
+  const int loc = blockIdx.x - prefix[p];
+  const int dy = loc % nd, dx = (loc / nd) % nd, src = loc / (nd * nd);
   extern __shared__ double2 sm2[];
-  V* ph = reinterpret_cast<V*>(sm2);  // [(ncx + ncy) * nd]
-  for (int e = threadIdx.x; e < (ncx + ncy) * nd; e += blockDim.x) ph[e] = phase_at(pd, e, T());
+  V* cs = reinterpret_cast<V*>(sm2);  // [nff][nb]
+  V* Bh = cs + nff * nb;              // [nff][nff]
+  V* tmp = Bh + nff2;                 // [nff][nb]
+  V* phx = tmp + nff * nb;            // [ncx] e^{i l_x X}
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
+  for (int e = threadIdx.x; e < ncx; e += blockDim.x) phx[e] = phase_at(pd, e * nd + dx, T());
   __syncthreads();
-  const int key = (blockIdx.x - prefix[p]) * kDftWarps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (key >= pd.nkeys) return;
-  const int4 k = pd.keys[key];
-  const V* src = btbase + pd.off_bt + ((size_t)k.x * nb * nb + k.y) * nl;
-  V acc = {0, 0};
-  // unrolled so that several loads of Bt are in flight per lane
-#pragma unroll 6
-  for (int l = lane; l < nl; l += 32) {
-    const int ix = l / ncy, iy = l - ix * ncy;
-    const V q = cmul(ph[ix * nd + k.z], ph[(ncx + iy) * nd + k.w]);
-    acc = cfma(q, __ldg(src + l), acc);
+  const V* P1 = p1base + pd.off_bt + (size_t)dy * nff2;
+  const size_t xstride = (size_t)nd * nff2;
+  for (int ab = threadIdx.x; ab < nff2; ab += blockDim.x) {
+    V acc = {0, 0};
+    const V* q = P1 + (size_t)src * ncx * xstride + ab;
+#pragma unroll 4
+    for (int ix = 0; ix < ncx; ++ix) acc = cfma(phx[ix], q[ix * xstride], acc);
+    Bh[ab] = acc;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  __syncthreads();
+  // tmp[a][b4] = sum_b Bh[a][b] c_b(b4)
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) {
+    const int a = e / nb, b4 = e - a * nb;
+    V acc = {0, 0};
+    for (int b = 0; b < nff; ++b) acc = cfma(Bh[a * nff + b], cs[b * nb + b4], acc);
+    tmp[e] = acc;
   }
-  if (lane == 0) fkbase[pd.off_fkey + key] = acc;
+  __syncthreads();
+  // F[b3][b4] = sum_a c_a(b3) tmp[a][b4]
+  V* F = fkbase + pd.off_fkey + ((size_t)(src * nd + dx) * nd + dy) * nb * nb;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int b3 = e / nb, b4 = e - b3 * nb;
+    V acc = {0, 0};
+    for (int a = 0; a < nff; ++a) acc = cfma(cs[a * nb + b3], tmp[a * nb + b4], acc);
+    F[e] = acc;
+  }
 }
 
 // Term form (Nff <= 13).  kTermsL transfer momenta of one target channel per
@@ -492,13 +521,17 @@ __global__ void __launch_bounds__(1024)
 }
 
 template <class T>
-size_t bond_smem(const MultiView& v) {
-  return sizeof(typename C2<T>::type) * 2 * v.nff_max * v.nb_max +
-         sizeof(T) * v.nff_max * v.nff_max;
+size_t dft1_smem(const MultiView& v) {
+  int m = 1;
+  for (const PointDesc& d : v.h) m = std::max(m, d.ncy * d.nd);
+  return sizeof(typename C2<T>::type) * m;
 }
 template <class T>
-size_t dft_smem(const MultiView& v) {
-  return sizeof(typename C2<T>::type) * v.nc_sum_max * v.nd_max;
+size_t dft2_smem(const MultiView& v) {
+  int m = 1;
+  for (const PointDesc& d : v.h) m = std::max(m, d.ncx);
+  return sizeof(typename C2<T>::type) *
+         (2 * (size_t)v.nff_max * v.nb_max + (size_t)v.nff_max * v.nff_max + m);
 }
 template <class T>
 size_t overlap_smem(const MultiView& v) {
@@ -546,18 +579,18 @@ template <class T>
 tufrg_status prepare_typed(const MultiView& v) {
   const int smem = smem_optin();
   // (the two contract kernels also hold a few bytes of static shared memory)
-  if ((int)bond_smem<T>(v) > smem || (int)dft_smem<T>(v) > smem ||
+  if ((int)dft1_smem<T>(v) > smem || (int)dft2_smem<T>(v) > smem ||
       (int)overlap_smem<T>(v) > smem || (int)contract_smem<T>(v) + 64 > smem ||
       (int)contract_terms_smem<T>(v) + 64 > smem)
     return TUFRG_ERR_ARG;
-  TUFRG_CUDA(cudaFuncSetAttribute(dft_keys_kernel<T>,
+  TUFRG_CUDA(cudaFuncSetAttribute(bond_dft1_kernel<T>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaError_t e = cudaSuccess;
   for_each_nf([&](auto nf) {
     constexpr int NF = decltype(nf)::value;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(to_bond_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem);
+      e = cudaFuncSetAttribute(bond_dft2_kernel<T, NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(contract_terms_kernel<T, NF>, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(overlap_kernel<T, NF>,
@@ -576,15 +609,15 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
   V* bt = reinterpret_cast<V*>(btv);
   V* fkey = reinterpret_cast<V*>(fkv);
   if (v.total(kKindBond) > 0) {
-    with_nf(v.nf_uniform, [&](auto nf) {
-      to_bond_kernel<T, decltype(nf)::value><<<v.total(kKindBond), 128, bond_smem<T>(v), st>>>(
-          v.d, v.dprefix(kKindBond), v.n, y, bt);
-    });
+    bond_dft1_kernel<T><<<v.total(kKindBond), kDft1Threads, dft1_smem<T>(v), st>>>(
+        v.d, v.dprefix(kKindBond), v.n, y, bt);
     TUFRG_CUDA(cudaGetLastError());
   }
   if (v.total(kKindDft) > 0) {
-    dft_keys_kernel<T><<<v.total(kKindDft), 32 * kDftWarps, dft_smem<T>(v), st>>>(
-        v.d, v.dprefix(kKindDft), v.n, bt, fkey);
+    with_nf(v.nf_uniform, [&](auto nf) {
+      bond_dft2_kernel<T, decltype(nf)::value><<<v.total(kKindDft), 256, dft2_smem<T>(v), st>>>(
+          v.d, v.dprefix(kKindDft), v.n, bt, fkey);
+    });
     TUFRG_CUDA(cudaGetLastError());
   }
   if (!v.proj_grouped) {
@@ -617,15 +650,21 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
 
 }  // namespace
 
-int dft_ctas(int nkeys) { return (nkeys + kDftWarps - 1) / kDftWarps; }
+int bond_ctas(int ncx, int nff) {
+  return 3 * ncx * ((nff * nff + kDft1Threads - 1) / kDft1Threads);
+}
+
+int dft_ctas(int nd) { return 3 * nd * nd; }
+
+size_t fkey_elems(int nd, int nb) { return (size_t)3 * nd * nd * nb * nb; }
 
 int contract_ctas(int nl, bool grouped) {
   const int L = grouped ? kContractL : kTermsL;
   return 3 * ((nl + L - 1) / L);
 }
 
-size_t bt_region(int nb, int nl, int nff, int ny_total) {
-  return std::max((size_t)3 * nb * nb * nl, (size_t)ny_total * hstride(nff));
+size_t bt_region(int ncx, int nd, int nff, int ny_total) {
+  return std::max((size_t)3 * ncx * nd * nff * nff, (size_t)ny_total * hstride(nff));
 }
 
 tufrg_status prepare_project_multi(const MultiView& v) {

@@ -472,7 +472,6 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_phase_f = dp->d_phase_f;
     c->d_yphase = dp->d_yphase;
     c->d_yphase_f = dp->d_yphase_f;
-    c->d_key = dp->d_key;
     c->d_row_ptr = dp->d_row_ptr;
     c->d_terms = dp->d_terms;
     for (int t = 0; t < 3; ++t) c->term_off[t] = dp->term_off[t];
@@ -488,8 +487,8 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nrow));
     TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
     TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
-    TUFRG_CHECK(alloc(&c->d_bt, bt_region(nb, c->nl, nff, P.gy_off[3])));
-    TUFRG_CHECK(alloc(&c->d_fkey, (size_t)P.nkeys));
+    TUFRG_CHECK(alloc(&c->d_bt, bt_region(c->ncx, 2 * P.dmax + 1, nff, P.gy_off[3])));
+    TUFRG_CHECK(alloc(&c->d_fkey, fkey_elems(2 * P.dmax + 1, nb)));
     // the loop kernels write only the parity-allowed pairs
     TUFRG_CUDA(cudaMemsetAsync(c->d_chi, 0, sizeof(double) * 2 * c->nl * nff * nff, st));
     TUFRG_CUDA(cudaStreamCreateWithFlags(&c->fstream, cudaStreamNonBlocking));
@@ -540,23 +539,28 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
   for (size_t i = 0; i < phase.size(); ++i)
     phase_f[i] = make_float2((float)phase[i].x, (float)phase[i].y);
   TUFRG_CHECK(upload(&c->d_phase_f, phase_f, st));
-  std::vector<int4> keys(P.nkeys);
+  // keys numbered densely over (source, 2X_x, 2X_y, b3, b4): the Fourier
+  // values of all keys at a position X come from one DFT of the state
+  std::vector<int> dense(P.nkeys);
   for (int i = 0; i < P.nkeys; ++i)
-    keys[i] = make_int4(P.key_src[i], P.key_b3[i] * nb + P.key_b4[i], P.key_dx[i] + P.dmax,
-                        P.key_dy[i] + P.dmax);
-  TUFRG_CHECK(upload(&c->d_key, keys, st));
+    dense[i] = ((P.key_src[i] * nd + P.key_dx[i] + P.dmax) * nd + P.key_dy[i] + P.dmax) * nb *
+                   nb +
+               P.key_b3[i] * nb + P.key_b4[i];
   std::vector<int> rowp;
   std::vector<int4> terms;
   for (int t = 0; t < 3; ++t) {
     c->term_off[t] = (int)terms.size();
     for (int v : P.row_ptr[t]) rowp.push_back(v);
     for (size_t i = 0; i < P.term_key[t].size(); ++i)
-      terms.push_back(make_int4(P.term_key[t][i], P.term_dx[t][i] + P.dmax,
+      terms.push_back(make_int4(dense[P.term_key[t][i]], P.term_dx[t][i] + P.dmax,
                                 P.term_dy[t][i] + P.dmax, (int)P.term_sign[t][i]));
   }
+  std::vector<int4> gslot = P.gslot;
+  for (int4& g : gslot)
+    if (g.y >= 0) g.y = dense[g.y];
   TUFRG_CHECK(upload(&c->d_row_ptr, rowp, st));
   TUFRG_CHECK(upload(&c->d_terms, terms, st));
-  TUFRG_CHECK(upload(&c->d_gslot, P.gslot, st));
+  TUFRG_CHECK(upload(&c->d_gslot, gslot, st));
   // e^{i l.Y} for every phase position Y and every l = (ix, iy)
   std::vector<double2> yph((size_t)P.gy.size() * c->nl);
   std::vector<float2> yph_f(yph.size());
@@ -595,7 +599,7 @@ void free_device(tufrg_ctx* c) {
       if (p) cudaFree(p);
   }
   if (!c->borrowed_proj) {
-    void* proj[] = {c->d_coef,   c->d_phase,   c->d_key,    c->d_row_ptr, c->d_terms,
+    void* proj[] = {c->d_coef,   c->d_phase,   c->d_row_ptr, c->d_terms,
                     c->d_gslot,  c->d_coef_f,  c->d_phase_f, c->d_yphase, c->d_yphase_f};
     for (void* p : proj)
       if (p) cudaFree(p);
