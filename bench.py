@@ -169,6 +169,39 @@ def fp64_peak_tflops(torch):
     return best
 
 
+def gemm_peak_tflops(torch, dtype, tf32=False, n=8192, reps=5):
+    """Measured dense matmul rate of this GPU (cuBLAS through torch, best of
+    reps, CUDA events): FP32 with or without TF32 tensor cores, or FP64."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        a = torch.randn(n, n, dtype=dtype, device="cuda")
+        b = torch.randn(n, n, dtype=dtype, device="cuda")
+        torch.matmul(a, b)
+        best = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = max(best, 2 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        del a, b
+        return best
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def other_peaks(torch):
+    """TF32 tensor, FP32 (CUDA cores) and FP64 matmul rates measured here."""
+    return {"tf32_tflops": gemm_peak_tflops(torch, torch.float32, tf32=True),
+            "fp32_tflops": gemm_peak_tflops(torch, torch.float32, tf32=False, n=4096, reps=3),
+            "fp64_tflops": gemm_peak_tflops(torch, torch.float64, n=4096, reps=3),
+            "how": "torch.matmul (cuBLAS), best of several, CUDA events; tf32: FP32 operands "
+                   "with TF32 tensor cores allowed, 8192^3; fp32: TF32 not allowed, 4096^3; "
+                   "fp64: 4096^3"}
+
+
 def profile_traffic(kernel_file, profile_name):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
     the current source of the kernel (sha256 recorded in the summary)."""
@@ -1013,6 +1046,7 @@ def run_point(args, rank, world, local):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, tp)
+    peaks_here = None if args.no_compare else other_peaks(torch)
 
     # kernels of the library per timed step: 6 stages x (combination, stage
     # scale, per-scale table, loop contraction, split-K reduce, to_bond,
@@ -1035,7 +1069,7 @@ def run_point(args, rank, world, local):
            "step_ms": [round(t, 3) for t in step_ms],
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-           "precisions_same_point": comparisons or None,
+           "precisions_same_point": comparisons or None, "peaks_measured_here": peaks_here,
            "flow": flow_info, "peaks_source": peak_src}
     print(json.dumps(out))
     return 0

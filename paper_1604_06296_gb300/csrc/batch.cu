@@ -50,7 +50,10 @@ __global__ void bcombo_kernel(const double* __restrict__ y, double* __restrict__
   }
   const long long b = seg[p].off + (long long)chunk * kChunk;
   const long long e = min(b + kChunk, seg[p].off + seg[p].len);
-  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < kChunk / kFlowThreads; ++u) {
+    const long long i = b + u * kFlowThreads + threadIdx.x;
+    if (i >= e) break;
     const double acc = combo_sum(cb, i);
     out[i] = y[i] + h * acc;
   }
@@ -77,11 +80,16 @@ __global__ void berror_kernel(const double* __restrict__ y, const double* __rest
   const long long e = min(b + kChunk, seg[p].off + seg[p].len);
   unsigned long long emax = 0, ymax = 0;
   int bad = 0;
-  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < kChunk / kFlowThreads; ++u) {
+    const long long i = b + u * kFlowThreads + threadIdx.x;
+    if (i >= e) break;
     const double acc = combo_sum(ce, i);
     const double yn = ynew[i];
     const double sc = atol + rtol * fmax(fabs(y[i]), fabs(yn));
-    const double r = fabs(h * acc) / sc;
+    // the ratio in FP32 (the step control needs a few digits of it; GB300's
+    // FP64 division costs more than the rest of the kernel)
+    const double r = (double)__fdiv_rn((float)fabs(h * acc), (float)sc);
     if (!isfinite(yn) || !isfinite(r)) bad = 1;
     emax = max(emax, abs_bits(r));
     ymax = max(ymax, abs_bits(yn));
@@ -113,7 +121,10 @@ __global__ void baccept_kernel(double* __restrict__ y, const double* __restrict_
   if (!ctl[p].accepted) return;
   const long long b = seg[p].off + (long long)(blockIdx.x - prefix[p]) * kChunk;
   const long long e = min(b + kChunk, seg[p].off + seg[p].len);
-  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < kChunk / kFlowThreads; ++u) {
+    const long long i = b + u * kFlowThreads + threadIdx.x;
+    if (i >= e) break;
     yprev[i] = y[i];
     y[i] = ynew[i];
     k1prev[i] = k1[i];
@@ -135,7 +146,10 @@ __global__ void bhermite_kernel(const double* __restrict__ y0, const double* __r
   const long long b = seg[p].off + (long long)(blockIdx.x - prefix[p]) * kChunk;
   const long long e = min(b + kChunk, seg[p].off + seg[p].len);
   unsigned long long m = 0;
-  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < kChunk / kFlowThreads; ++u) {
+    const long long i = b + u * kFlowThreads + threadIdx.x;
+    if (i >= e) break;
     const double v = hermite(s0, y0[i], f0[i], s1, y1[i], f1[i], s);
     if (final_write)
       y1[i] = v;
@@ -180,13 +194,21 @@ __global__ void bmax_kernel(const double* __restrict__ y, FlowCtl* __restrict__ 
   const long long e = min(b + kChunk, seg[p].off + seg[p].len);
   if (arg) {
     const unsigned long long target = c.max_u;
-    for (long long i = b + threadIdx.x; i < e; i += blockDim.x)
-      if (abs_bits(y[i]) == target)
-        atomicMin(&c.arg_u, (unsigned long long)(i - seg[p].off));
+#pragma unroll
+    for (int u = 0; u < kChunk / kFlowThreads; ++u) {
+      const long long i = b + u * kFlowThreads + threadIdx.x;
+      if (i >= e) break;
+      if (abs_bits(y[i]) == target) atomicMin(&c.arg_u, (unsigned long long)(i - seg[p].off));
+    }
     return;
   }
   unsigned long long m = 0;
-  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) m = max(m, abs_bits(y[i]));
+#pragma unroll
+  for (int u = 0; u < kChunk / kFlowThreads; ++u) {
+    const long long i = b + u * kFlowThreads + threadIdx.x;
+    if (i >= e) break;
+    m = max(m, abs_bits(y[i]));
+  }
   block_max_u(m, &c.max_u);
 }
 

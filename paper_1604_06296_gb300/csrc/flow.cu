@@ -25,6 +25,16 @@
 namespace tufrg {
 namespace {
 
+// Element-wise kernels: 256 threads, up to kPer elements per thread with all
+// their loads in flight -- as many as keep ~8 CTAs per SM busy, so a small
+// state still spreads over every SM.
+constexpr int kPer = 8;
+
+__host__ __device__ inline int per_thread(size_t n) {
+  const size_t p = n / (256 * 152 * 8);
+  return p < 1 ? 1 : (p > kPer ? kPer : (int)p);
+}
+
 // out = y + h * sum_j a_j k_j ; one thread also publishes Lambda for the RHS
 __global__ void combo_kernel(const double* __restrict__ y, double* __restrict__ out, Combo cb,
                              const FlowCtl* __restrict__ ctl, double* __restrict__ lam,
@@ -35,8 +45,11 @@ __global__ void combo_kernel(const double* __restrict__ y, double* __restrict__ 
     lam[0] = L;
     lam[1] = L;
   }
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const int per = per_thread(n);
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const size_t i = ((size_t)blockIdx.x * per + u) * blockDim.x + threadIdx.x;
+    if (u >= per || i >= n) break;
     const double acc = combo_sum(cb, i);
     out[i] = y[i] + h * acc;
   }
@@ -55,12 +68,17 @@ __global__ void error_kernel(const double* __restrict__ y, const double* __restr
   const double h = ctl->h, rtol = ctl->rtol, atol = ctl->atol;
   unsigned long long emax = 0, ymax = 0;
   int bad = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const int per = per_thread(n);
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const size_t i = ((size_t)blockIdx.x * per + u) * blockDim.x + threadIdx.x;
+    if (u >= per || i >= n) break;
     const double acc = combo_sum(e, i);
     const double yn = ynew[i];
     const double sc = atol + rtol * fmax(fabs(y[i]), fabs(yn));
-    const double r = fabs(h * acc) / sc;
+    // the ratio in FP32 (the step control needs a few digits of it; GB300's
+    // FP64 division costs more than the rest of the kernel)
+    const double r = (double)__fdiv_rn((float)fabs(h * acc), (float)sc);
     if (!isfinite(yn) || !isfinite(r)) bad = 1;
     emax = max(emax, abs_bits(r));
     ymax = max(ymax, abs_bits(yn));
@@ -78,8 +96,11 @@ __global__ void accept_kernel(double* __restrict__ y, const double* __restrict__
                               const double* __restrict__ k7, double* __restrict__ k1prev,
                               const FlowCtl* __restrict__ ctl, size_t n) {
   if (!ctl->accepted) return;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const int per = per_thread(n);
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const size_t i = ((size_t)blockIdx.x * per + u) * blockDim.x + threadIdx.x;
+    if (u >= per || i >= n) break;
     yprev[i] = y[i];
     y[i] = ynew[i];
     k1prev[i] = k1[i];
@@ -97,8 +118,11 @@ __global__ void hermite_kernel(const double* __restrict__ y0, const double* __re
   const double s0 = ctl->s_prev, s1 = ctl->s;
   const double s = use_mid ? 0.5 * (ctl->bis_a + ctl->bis_b) : s_fixed;
   unsigned long long m = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const int per = per_thread(n);
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const size_t i = ((size_t)blockIdx.x * per + u) * blockDim.x + threadIdx.x;
+    if (u >= per || i >= n) break;
     const double v = hermite(s0, y0[i], f0[i], s1, y1[i], f1[i], s);
     if (out) out[i] = v;
     m = max(m, abs_bits(v));
@@ -120,8 +144,11 @@ __global__ void max_kernel(const double* __restrict__ y, FlowCtl* __restrict__ c
                            int check_finite) {
   unsigned long long m = 0;
   int bad = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const int per = per_thread(n);
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const size_t i = ((size_t)blockIdx.x * per + u) * blockDim.x + threadIdx.x;
+    if (u >= per || i >= n) break;
     m = max(m, abs_bits(y[i]));
     if (check_finite && !isfinite(y[i])) bad = 1;
   }
@@ -131,9 +158,13 @@ __global__ void max_kernel(const double* __restrict__ y, FlowCtl* __restrict__ c
 
 __global__ void argmax_kernel(const double* __restrict__ y, FlowCtl* __restrict__ ctl, size_t n) {
   const unsigned long long target = ctl->max_u;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
+  const int per = per_thread(n);
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const size_t i = ((size_t)blockIdx.x * per + u) * blockDim.x + threadIdx.x;
+    if (u >= per || i >= n) break;
     if (abs_bits(y[i]) == target) atomicMin(&ctl->arg_u, (unsigned long long)i);
+  }
 }
 
 double bits_to_double(unsigned long long u) {
@@ -142,7 +173,11 @@ double bits_to_double(unsigned long long u) {
   return d;
 }
 
-int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+// CTAs of the element-wise kernels for n elements
+int grid_for(size_t n) {
+  const size_t per = (size_t)256 * per_thread(n);
+  return (int)((n + per - 1) / per);
+}
 
 }  // namespace
 

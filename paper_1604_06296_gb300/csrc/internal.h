@@ -362,7 +362,7 @@ int bond_ctas(int ncx, int nff);
 int dft_ctas(int nd);
 // Fourier values of the keys, numbered densely over (source, 2X_x, 2X_y, b3, b4)
 size_t fkey_elems(int nd, int nb);
-int contract_ctas(int nl, bool grouped);
+int contract_ctas(int nl, int nff, bool grouped);
 // the projections of a view take the grouped form from this form-factor count on
 constexpr int kGroupedNff = 21;
 // elements of a point's projection workspace: the state's DFT along y

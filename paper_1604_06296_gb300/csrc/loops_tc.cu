@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "tc_util.cuh"
@@ -277,11 +278,10 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
       // The table gathers run kDepth - 1 units ahead of the arithmetic, in a
       // ring of register buffers, across K-block boundaries too (the gathers
       // of the next K-block's first units are issued while the last units of
-      // this one are computed).  Every warp gathers and computes all kUnits
-      // units of a K-block: rows without an l read offset 0 and their
-      // accumulator rows are never read.  A branch-free K-block lets the
-      // compiler interleave the units, which costs less than the work on
-      // the rows without an l (at most 127 of a tile).
+      // this one are computed).  Every warp gathers and computes the same
+      // number of units per K-block, without a branch per unit (the compiler
+      // interleaves the units): rows without an l (fewer than 16 per tile)
+      // read offset 0 and their accumulator rows are never read.
       using Buf = typename P::Buf;
       auto load_unit = [&](int u, int pb, Buf& b) {
         if constexpr (P::kPerLane == 2) {  // one row, two loop points: one pair each side
@@ -330,50 +330,81 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
           }
         }
       };
-      static_assert(kUnits % kDepth == 0, "the ring continues across K-blocks");
-      Buf buf[kDepth];
-      // this lane's first loop point of a K-block as an offset into the halo
-      // table (padding points use a valid entry: their F is zero); BF16X3
-      // lanes take loop points 2 lane, 2 lane + 1 of the K-block, neighbours
-      // iy, iy + 1 of one column, i.e. table entries pb, pb + 1
-      int pb = cnt > 0 ? __ldg(pd.kbase + kb0 * KB + P::kPerLane * lane) : 0;
+      // The K-blocks of the item with NU units per warp (rows warp + 16 u, u <
+      // NU: the tile's rows need ceil(nvalid / 16) of the kUnits, BF16X3).
+      // Unit u uses ring slot u % kDepth; when NU is not a multiple of
+      // kDepth the slots of the next K-block's first units are moved to 0..
+      // after each K-block (register moves instead of a second copy of the
+      // code per ring phase).
+      auto produce = [&](auto nu) {
+        constexpr int NU = decltype(nu)::value;
+        Buf buf[kDepth];
+        // this lane's first loop point of a K-block as an offset into the halo
+        // table (padding points use a valid entry: their F is zero); BF16X3
+        // lanes take loop points 2 lane, 2 lane + 1 of the K-block, neighbours
+        // iy, iy + 1 of one column, i.e. table entries pb, pb + 1
+        int pb = cnt > 0 ? __ldg(pd.kbase + kb0 * KB + P::kPerLane * lane) : 0;
 #pragma unroll
-      for (int t = 0; t < kDepth - 1; ++t)
-        if (cnt > 0) load_unit(t, pb, buf[t]);
-      for (int kb = 0; kb < cnt; ++kb) {
-        const uint32_t gk = g + kb;
-        const uint32_t s = gk & 1;
-        if (gk >= 2 && !mbar_wait_sleep(bar_empty + 8 * s, ((gk >> 1) + 1) & 1)) {
-          atomicOr(a.err, 1);
-          *abort_flag = 1;
-        }
-        if (*abort_flag) break;
-        const uint32_t st = base + s * stage_bytes;
-        const int k0 = (kb0 + kb) * KB;
-        if (warp == 0 && lane == 0) {  // F of this K-block, both parts, by TMA
-          mbar_arrive_expect_tx(bar_tma + 8 * s, 2u * fbytes);
-          tma_load_2d(st + 4u * kWTile, pd.tmap, k0, 0, bar_tma + 8 * s);
-          tma_load_2d(st + 4u * kWTile + fmax, static_cast<const unsigned char*>(pd.tmap) + 128,
-                      k0, 0, bar_tma + 8 * s);
-          tma_last = (int)gk;
-        }
-        unsigned char* stg = gbase + (st - base);
-        // (after the item's last K-block the ring gathers this one's first
-        // units again: valid addresses, no branch)
-        const int pbn = kb + 1 < cnt ? __ldg(pd.kbase + k0 + KB + P::kPerLane * lane) : pb;
+        for (int t = 0; t < kDepth - 1; ++t)
+          if (cnt > 0 && t < NU) load_unit(t, pb, buf[t]);
+        for (int kb = 0; kb < cnt; ++kb) {
+          const uint32_t gk = g + kb;
+          const uint32_t s = gk & 1;
+          if (gk >= 2 && !mbar_wait_sleep(bar_empty + 8 * s, ((gk >> 1) + 1) & 1)) {
+            atomicOr(a.err, 1);
+            *abort_flag = 1;
+          }
+          if (*abort_flag) break;
+          const uint32_t st = base + s * stage_bytes;
+          const int k0 = (kb0 + kb) * KB;
+          if (warp == 0 && lane == 0) {  // F of this K-block, both parts, by TMA
+            mbar_arrive_expect_tx(bar_tma + 8 * s, 2u * fbytes);
+            tma_load_2d(st + 4u * kWTile, pd.tmap, k0, 0, bar_tma + 8 * s);
+            tma_load_2d(st + 4u * kWTile + fmax,
+                        static_cast<const unsigned char*>(pd.tmap) + 128, k0, 0,
+                        bar_tma + 8 * s);
+            tma_last = (int)gk;
+          }
+          unsigned char* stg = gbase + (st - base);
+          // (after the item's last K-block the ring gathers this one's first
+          // units again: valid addresses, no branch)
+          const int pbn = kb + 1 < cnt ? __ldg(pd.kbase + k0 + KB + P::kPerLane * lane) : pb;
 #pragma unroll
-        for (int u = 0; u < kUnits; ++u) {
-          const int t = u + kDepth - 1;  // unit gathered now, into the slot unit u - 1 freed
-          if (t < kUnits)
-            load_unit(t, pb, buf[t % kDepth]);
-          else
-            load_unit(t - kUnits, pbn, buf[t % kDepth]);
-          do_unit(u, stg, buf[u % kDepth]);
+          for (int u = 0; u < NU; ++u) {
+            const int t = u + kDepth - 1;  // unit gathered now, into the slot unit u - 1 freed
+            if (t < NU)
+              load_unit(t, pb, buf[t % kDepth]);
+            else if (t - NU < NU)
+              load_unit(t - NU, pbn, buf[t % kDepth]);
+            do_unit(u, stg, buf[u % kDepth]);
+          }
+          if constexpr (NU % kDepth != 0) {
+            Buf nxt[kDepth - 1];
+#pragma unroll
+            for (int j = 0; j < kDepth - 1; ++j) nxt[j] = buf[(NU + j) % kDepth];
+#pragma unroll
+            for (int j = 0; j < kDepth - 1; ++j) buf[j] = nxt[j];
+          }
+          pb = pbn;
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar_full + 8 * s);
         }
-        pb = pbn;
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar_full + 8 * s);
+      };
+      if constexpr (P::kPerLane == 2) {
+        const int need = (nvalid + kProducers - 1) / kProducers;  // units of this tile
+        if (need <= 4)
+          produce(std::integral_constant<int, 4>{});
+        else if (need == 5)
+          produce(std::integral_constant<int, 5>{});
+        else if (need == 6)
+          produce(std::integral_constant<int, 6>{});
+        else if (need == 7)
+          produce(std::integral_constant<int, 7>{});
+        else
+          produce(std::integral_constant<int, kUnits>{});
+      } else {
+        produce(std::integral_constant<int, kUnits>{});
       }
     } else if (lane == 0) {
       // ------------------------------------------------------- MMA issuer

@@ -211,10 +211,10 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
         d.feedback ? bond_ctas(d.ncx, d.nff) : 0,
         d.feedback ? dft_ctas(d.nd) : 0,
         grouped && d.feedback ? d.gy_off[3] : 0,
-        contract_ctas(d.nl, grouped),
+        contract_ctas(d.nl, d.nff, grouped),
         d.nl,
         d.nrow,
-        contract_ctas(d.nrow, grouped),
+        contract_ctas(d.nrow, d.nff, grouped),
         d.nrow,
     };
     for (int k = 0; k < kKinds; ++k)

@@ -25,7 +25,7 @@
 //
 // with G and H independent of l (grouped form).  It replaces contract_terms by
 //   overlap   -- G and the basis change to H, per (target channel, Y)
-//   contract  -- the phase sum over Y, per (target channel, 8 l)
+//   contract  -- the phase sum over Y, a tiled complex matrix product
 // and needs about half the arithmetic.  Views with a point of Nff >= 21 use
 // it (there the sums bound the step); for Nff <= 13 its extra dependent
 // launch costs more than the arithmetic it saves.
@@ -85,14 +85,6 @@ __device__ __forceinline__ float2 yphase_at(const PointDesc& pd, size_t e, float
 // H(Y) rows [nff * nff] are stored with an even stride, so that every row
 // starts on a 16-byte boundary (16-byte asynchronous copies)
 __host__ __device__ constexpr int hstride(int nff) { return (nff * nff + 1) & ~1; }
-
-// Y positions of H staged in shared memory per pass of the phase sum (all
-// of them at Nb = 13 in FP32, within 56 KB)
-__host__ __device__ inline int contract_ychunk(int ny, int nff, int vbytes) {
-  const int c = 56 * 1024 / (hstride(nff) * vbytes);
-  return ny < c ? (ny > 0 ? ny : 1) : (c > 0 ? c : 1);
-}
-
 
 // Fourier values of the keys, in two passes (each key (source S, bonds b3,
 // b4, position X) is F = sum_l' e^{i l'.X} Bt^S_{b3 b4}(l') with
@@ -403,121 +395,91 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// kContractL transfer momenta of one target channel per CTA:
-// V = V0 + own + (1/Nl) Re sum_Y e^{i l.Y} H(Y).  H of the target is staged
-// in shared memory by 16-byte asynchronous copies (in passes of
-// contract_ychunk positions), together with the precomputed phases of the
-// CTA's l, so that a pass costs one round trip to L2.  The positions are
-// split over contract_groups groups of threads, one thread of a group per
-// output entry (m, n) holding all kContractL l; the groups' partial sums are
-// then added in a fixed order.
-constexpr int kContractL = 8;
+// The phase sums of the grouped form as a tiled complex matrix product:
+//   V(l)_mn = V0 + own + (1/Nl) Re sum_Y E[l][Y] H[Y][mn],  E[l][Y] = e^{i l.Y}
+// over the output slots (every l, or the rows' representatives) and the
+// Nff^2 entries, the positions Y of the target as the contraction index.
+// CTA: (point, target, kCL slots, kCM entries); positions in passes (32 in
+// FP32, 16 in FP64: 37 KB of static shared memory), staged with E in shared
+// memory; thread: one entry, kCR slots.
+constexpr int kCL = 16;      // output slots per CTA
+constexpr int kCM = 128;     // entries (m, n) per CTA
+constexpr int kCYBytes = 32 * 8;  // positions per pass x bytes per complex value
+constexpr int kCThreads = 256;
+constexpr int kCR = kCL * kCM / kCThreads;  // slots per thread (8)
 
-__host__ __device__ inline int contract_tpg(int nff) { return (nff * nff + 31) / 32 * 32; }
-__host__ __device__ inline int contract_groups(int nff) {
-  const int g = 1024 / contract_tpg(nff);
-  return g < 1 ? 1 : (g > 4 ? 4 : g);
+__host__ __device__ inline int contract_ctiles(int nout, int nff) {
+  return ((nout + kCL - 1) / kCL) * ((nff * nff + kCM - 1) / kCM);
 }
 
 template <class T, int NF>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kCThreads)
     contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
                     const double* __restrict__ ybase,
                     const typename C2<T>::type* __restrict__ hbase, double* __restrict__ vbase,
                     int rows) {
   using V = typename C2<T>::type;
+  constexpr int kCY = kCYBytes / (int)sizeof(V);
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int nff = NF ? NF : pd.nff, nl = pd.nl;
-  // output slots: every l, or the representative l of every loop row
+  const int nff = NF ? NF : pd.nff, nl = pd.nl, n2 = nff * nff, n2p = hstride(nff);
   const int nout = rows ? pd.nrow : nl;
-  const int groups = (nout + kContractL - 1) / kContractL;
+  const int tiles = contract_ctiles(nout, nff), mtiles = (n2 + kCM - 1) / kCM;
   const int loc = blockIdx.x - prefix[p];
-  const int t = loc / groups, q0 = (loc % groups) * kContractL;
-  const int nlb = min(kContractL, nout - q0);  // slots of this CTA
-  __shared__ int sl[kContractL];               // l of each slot (the last one repeated)
-  if (threadIdx.x < kContractL) {
+  const int t = loc / tiles, r = loc % tiles;
+  const int q0 = (r / mtiles) * kCL, mn0 = (r % mtiles) * kCM;
+  const int nlb = min(kCL, nout - q0);  // slots of this CTA
+  __shared__ int sl[kCL];               // l of each slot (the last one repeated)
+  __shared__ V Es[kCY][kCL];            // e^{i l.Y} of a pass
+  __shared__ V Hs[kCY][kCM];            // H of a pass
+  if (threadIdx.x < kCL) {
     const int q = q0 + min((int)threadIdx.x, nlb - 1);
     sl[threadIdx.x] = rows ? pd.rowimg[pd.rowimg_ptr[q]].x : q;
   }
   __syncthreads();
-  const int n2 = nff * nff, n2p = hstride(nff);
   const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
   const double U = pd.U;
-  const size_t base = pd.off_state + (size_t)t * nl * n2;  // l = sl[j] at base + sl[j] n2
-  if (!pd.feedback) {
-    for (int e = threadIdx.x; e < nlb * n2; e += blockDim.x) {
-      const int j = e / n2, r = e % n2;
-      const size_t o = base + (size_t)sl[j] * n2 + r;
-      vbase[o] = (r == 0 ? U : 0.0) + own_sign * ybase[o];
-    }
-    return;
-  }
-  // (a batch of mixed Nff launches for the largest: fewer groups may fit)
-  const int tpg = contract_tpg(nff), ng = min(contract_groups(nff), (int)blockDim.x / tpg);
-  const int grp = threadIdx.x / tpg, mn = threadIdx.x - grp * tpg;
-  const bool active = grp < ng && mn < n2;
-  const int y0 = pd.gy_off[t], ny = pd.gy_off[t + 1] - y0;
-  const int ych = contract_ychunk(ny, nff, (int)sizeof(V));
-  extern __shared__ double2 sm2[];
-  V* Hs = reinterpret_cast<V*>(sm2);  // [ych][n2p]
-  V* ph = Hs + (size_t)ych * n2p;     // [ych][kContractL] e^{i l.Y}
-  const uint32_t hs = (uint32_t)__cvta_generic_to_shared(Hs);
-  const char* H = reinterpret_cast<const char*>(hbase + pd.off_bt + (size_t)y0 * n2p);
-  double yv[kContractL];  // the state entries group 0 adds to
+  const size_t base = pd.off_state + (size_t)t * nl * n2;  // l at base + l n2
+  const int c = threadIdx.x % kCM, j0 = (threadIdx.x / kCM) * kCR;  // entry, first slot
+  const int mn = mn0 + c;
+  T acc[kCR];
 #pragma unroll
-  for (int j = 0; j < kContractL; ++j)
-    yv[j] = grp == 0 && mn < n2 && j < nlb ? ybase[base + (size_t)sl[j] * n2 + mn] : 0.0;
-  T acc[kContractL];
+  for (int j = 0; j < kCR; ++j) acc[j] = 0;
+  if (pd.feedback) {
+    const int y0 = pd.gy_off[t], ny = pd.gy_off[t + 1] - y0;
+    const V* H = hbase + pd.off_bt + (size_t)y0 * n2p;
+    for (int c0 = 0; c0 < ny; c0 += kCY) {
+      const int cn = min(kCY, ny - c0);
+      __syncthreads();  // the previous pass is consumed
+      for (int e = threadIdx.x; e < kCY * kCM; e += kCThreads) {
+        const int yi = e / kCM, cc = e % kCM;
+        Hs[yi][cc] = yi < cn && mn0 + cc < n2 ? H[(size_t)(c0 + yi) * n2p + mn0 + cc] : V{0, 0};
+      }
+      for (int e = threadIdx.x; e < kCY * kCL; e += kCThreads) {
+        const int yi = e / kCL, j = e % kCL;
+        Es[yi][j] = yi < cn ? yphase_at(pd, (size_t)(y0 + c0 + yi) * nl + sl[j], T()) : V{0, 0};
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int yi = 0; yi < kCY; ++yi) {
+        const V h = Hs[yi][c];
 #pragma unroll
-  for (int j = 0; j < kContractL; ++j) acc[j] = 0;
-  for (int c0 = 0; c0 < ny; c0 += ych) {
-    const int cn = min(ych, ny - c0);
-    if (c0 > 0) __syncthreads();  // the previous pass is consumed
-    const int chunks = cn * n2p * (int)sizeof(V) / 16;
-    const char* src = H + (size_t)c0 * n2p * sizeof(V);
-    for (int i = threadIdx.x; i < chunks; i += blockDim.x)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(hs + 16u * i),
-                   "l"(src + 16 * (size_t)i)
-                   : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int e = threadIdx.x; e < cn * kContractL; e += blockDim.x) {
-      const int yi = e / kContractL, j = e - yi * kContractL;
-      ph[e] = yphase_at(pd, (size_t)(y0 + c0 + yi) * nl + sl[j], T());
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    if (active) {
-#pragma unroll 2
-      for (int yi = grp; yi < cn; yi += ng) {
-        const V h = Hs[yi * n2p + mn];
-        const V* e = ph + yi * kContractL;
-#pragma unroll
-        for (int j = 0; j < kContractL; ++j)
-          acc[j] = fma(e[j].x, h.x, fma(-e[j].y, h.y, acc[j]));  // real part of e * h
+        for (int j = 0; j < kCR; ++j) {
+          const V e = Es[yi][j0 + j];
+          acc[j] = fma(e.x, h.x, fma(-e.y, h.y, acc[j]));  // real part of e * h
+        }
       }
     }
   }
-  // partial sums of the groups, added by group 0 in group order
-  __syncthreads();  // the staging area is free
-  T* red = reinterpret_cast<T*>(sm2);  // [ng][kContractL][tpg]
-  if (active && grp > 0) {
+  if (mn >= n2) return;
+  const T inv_nl = T(1) / T(nl);
 #pragma unroll
-    for (int j = 0; j < kContractL; ++j) red[((size_t)grp * kContractL + j) * tpg + mn] = acc[j];
-  }
-  __syncthreads();
-  if (active && grp == 0) {
-    const T inv_nl = T(1) / T(nl);
-#pragma unroll
-    for (int j = 0; j < kContractL; ++j) {
-      T a = acc[j];
-      for (int g = 1; g < ng; ++g) a += red[((size_t)g * kContractL + j) * tpg + mn];
-      if (j < nlb)
-        vbase[base + (size_t)sl[j] * n2 + mn] =
-            (mn == 0 ? U : 0.0) + own_sign * yv[j] + (double)(a * inv_nl);
+  for (int j = 0; j < kCR; ++j)
+    if (j0 + j < nlb) {
+      const size_t o = base + (size_t)sl[j0 + j] * n2 + mn;
+      vbase[o] = (mn == 0 ? U : 0.0) + own_sign * ybase[o] + (double)(acc[j] * inv_nl);
     }
-  }
 }
 
 template <class T>
@@ -549,21 +511,6 @@ size_t contract_terms_smem(const MultiView& v) {
           2 * (size_t)kTermsL * v.nd_max);
 }
 
-template <class T>
-size_t contract_smem(const MultiView& v) {
-  const int vb = (int)sizeof(typename C2<T>::type);
-  size_t m = 0;
-  for (const PointDesc& d : v.h) {
-    for (int t = 0; t < 3; ++t) {
-      const int ych = contract_ychunk(d.gy_off[t + 1] - d.gy_off[t], d.nff, vb);
-      m = std::max(m, (size_t)vb * ych * (hstride(d.nff) + kContractL));
-    }
-    // the groups' partial sums reuse the staging area
-    m = std::max(m, sizeof(T) * contract_groups(d.nff) * kContractL * contract_tpg(d.nff));
-  }
-  return m;
-}
-
 // the largest dynamic shared memory a kernel may take: the device limit less
 // its static shared memory
 template <class K>
@@ -580,7 +527,7 @@ tufrg_status prepare_typed(const MultiView& v) {
   const int smem = smem_optin();
   // (the two contract kernels also hold a few bytes of static shared memory)
   if ((int)dft1_smem<T>(v) > smem || (int)dft2_smem<T>(v) > smem ||
-      (int)overlap_smem<T>(v) > smem || (int)contract_smem<T>(v) + 64 > smem ||
+      (int)overlap_smem<T>(v) > smem ||
       (int)contract_terms_smem<T>(v) + 64 > smem)
     return TUFRG_ERR_ARG;
   TUFRG_CUDA(cudaFuncSetAttribute(bond_dft1_kernel<T>,
@@ -595,7 +542,6 @@ tufrg_status prepare_typed(const MultiView& v) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(overlap_kernel<T, NF>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = allow_dynamic_smem(contract_kernel<T, NF>, smem);
   });
   TUFRG_CUDA(e);
   return TUFRG_OK;
@@ -636,13 +582,9 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
     });
     TUFRG_CUDA(cudaGetLastError());
   }
-  // groups of one thread per output entry (m, n); Nff <= 29: at most 1024
-  // threads (a batch has one Nff when nf_uniform, else the largest decides)
-  const int cthreads = contract_groups(v.nff_max) * contract_tpg(v.nff_max);
   with_nf(v.nf_uniform, [&](auto nf) {
-    contract_kernel<T, decltype(nf)::value>
-        <<<v.total(kind), cthreads, contract_smem<T>(v), st>>>(
-            v.d, v.dprefix(kind), v.n, y, bt, out, rows ? 1 : 0);
+    contract_kernel<T, decltype(nf)::value><<<v.total(kind), kCThreads, 0, st>>>(
+        v.d, v.dprefix(kind), v.n, y, bt, out, rows ? 1 : 0);
   });
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
@@ -658,9 +600,8 @@ int dft_ctas(int nd) { return 3 * nd * nd; }
 
 size_t fkey_elems(int nd, int nb) { return (size_t)3 * nd * nd * nb * nb; }
 
-int contract_ctas(int nl, bool grouped) {
-  const int L = grouped ? kContractL : kTermsL;
-  return 3 * ((nl + L - 1) / L);
+int contract_ctas(int nl, int nff, bool grouped) {
+  return grouped ? 3 * contract_ctiles(nl, nff) : 3 * ((nl + kTermsL - 1) / kTermsL);
 }
 
 size_t bt_region(int ncx, int nd, int nff, int ny_total) {

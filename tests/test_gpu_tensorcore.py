@@ -217,3 +217,48 @@ def test_profile_loops(torch, precision):
     # the profiled contractions are the real ones: the loops of the last are right
     ref = np.stack(olo.chi_dot(p, 0.4))
     assert rel(s.loops(0.4).cpu().numpy(), ref) < BOUND["bf16x3"]
+
+
+def test_production_size_loops_every_l_bf16x3(torch):
+    """Every l of one production-size loop call (BF16x3, the bench's
+    precision): the rows cover every l through the point-group expansion,
+    so a tile, queue-order or expansion error at any row shows here."""
+    c = W.config("cfg2")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=-0.25, mu=-1.0, U=3.0)
+    s, p = make(case, torch, precision="bf16x3")
+    got = s.loops(0.05).cpu().numpy()
+    check_device(s)
+    ref = np.stack(olo.chi_dot(p, 0.05))
+    err = rel(got, ref)
+    worst = np.abs(got - ref).max(axis=(0, 2, 3)) / np.abs(ref).max()
+    print(f"cfg2 bf16x3 every l: rel err {err:.2e}, worst l {int(worst.argmax())}")
+    assert err < BOUND["bf16x3"]
+
+
+def test_large_size_rhs_sampled_bf16x3(torch):
+    """One whole right-hand side at the large size (coarse 48x48, Nff = 25:
+    the grouped projections, tufrg_rhs as the e2e line calls it) on 16
+    sampled l: interior l, their C4v images, zone-boundary l of both kinds
+    and (-pi, -pi); the oracle's projections over all l, loops and products
+    at the sampled l."""
+    from oracle import projections as opj
+    c = W.config("cfg5")
+    case = dict(shells=c["shells"], nc=c["nc"], nf=c["nf"], tp=c["tp"], mu=c["mu"], U=c["U"])
+    s, p = make(case, torch, precision="bf16x3")
+    y = W.random_state(12, p.nl, p.nff, 0.3)
+    got = s.rhs(0.3, dev(torch, y)).cpu().numpy()
+    check_device(s)
+    n = p.ncx
+
+    def L(ix, iy):
+        return ix * n + iy
+    sel = [L(30, 17), L(17, 30), L(18, 31), L(31, 18),      # an interior orbit
+           L(24, 24), L(5, 40), L(40, 43), L(12, 12),       # l = 0, general, diagonal
+           L(0, 31), L(0, 17), L(31, 0), L(17, 0),          # a boundary class
+           L(0, 0), L(0, 24), L(24, 0), L(47, 1)]
+    V = opj.project(p, y)
+    chi = olo.chi_dot(p, 0.3, sel)
+    ref = orhs.products(V[:, sel], chi[0], chi[1])
+    err = rel(got[:, sel], ref)
+    print(f"cfg5 bf16x3 RHS (16 sampled l): rel err {err:.2e}")
+    assert err < 1e-4  # the bar on couplings of the mixed-precision forms
