@@ -87,7 +87,7 @@ tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, boo
   // exact loops stay as row loops; the products gather each l from its row
   // (or, for a covariant state, run at the rows' representatives only)
   const bool rows = prec != kLoopSurrogate;
-  wedge = wedge && rows;
+  if (wedge && !rows) return TUFRG_ERR_STATE;  // a wedge-layout state needs exact loops
   TUFRG_CHECK(launch_project_multi(c->view, arith, y, c->d_V, c->d_bt, c->d_fkey, c->pstream,
                                    wedge));
   TUFRG_CUDA(cudaEventRecord(c->ev_join, c->pstream));

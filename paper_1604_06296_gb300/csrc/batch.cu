@@ -221,13 +221,19 @@ struct BatchFlow {
   double *y, *k[7], *ytmp, *ynew, *yprev, *k1prev;
   FlowCtl* ctl = nullptr;   // device [n]
   FlowCtl* hctl = nullptr;  // pinned host mirror
+  // segments of the packed vectors and chunks per point, for the full
+  // states [0] and the wedge layout [1]; seg, prefix, n_chunks: the layout
+  // the flow integrates
+  Seg* seg_lay[2] = {nullptr, nullptr};
+  int* prefix_lay[2] = {nullptr, nullptr};
+  int n_chunks_lay[2] = {0, 0};
   Seg* seg = nullptr;
-  int* prefix = nullptr;    // chunks of the packed state per point
+  int* prefix = nullptr;
   int n_chunks = 0;
   cudaGraphExec_t attempt = nullptr;
   // every point's state is point-group covariant (checked at the start):
-  // projections and products at the rows' representative l only; the
-  // attempt graph was captured with graph_wedge
+  // the flow integrates the states at the rows' representative l only
+  // (wedge layout); the attempt graph was captured with graph_wedge
   bool wedge = false, graph_wedge = false;
   unsigned long long* cov = nullptr;  // device [2 n]: deviation, max |y| per point
 };
@@ -259,8 +265,8 @@ namespace {
 
 int grid_for(int n) { return (n + 127) / 128; }
 
-// wedge: projections and products at the rows' representative l only
-// (flows of point-group covariant states)
+// wedge: y and dy in the wedge layout (flows of point-group covariant
+// states), projections and products at the rows' representative l only
 tufrg_status batch_rhs_device(tufrg_batch* b, const double* y, double* dy, bool scaled,
                               cudaStream_t st, bool wedge = false) {
   const MultiView& v = b->view;
@@ -289,7 +295,7 @@ tufrg_status set_lambdas(tufrg_batch* b, const double* lambda, cudaStream_t st) 
 
 void free_batch_flow(BatchFlow& f) {
   if (f.attempt) cudaGraphExecDestroy(f.attempt);
-  void* ptrs[] = {f.base, f.seg, f.prefix};
+  void* ptrs[] = {f.base, f.seg_lay[0], f.prefix_lay[0]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (f.hctl) cudaFreeHost(f.hctl);
@@ -315,20 +321,26 @@ tufrg_status batch_flow_buffers(tufrg_batch* b) {
   f.cov = reinterpret_cast<unsigned long long*>(
       (reinterpret_cast<uintptr_t>(f.ctl + b->n) + 255) & ~uintptr_t(255));
   TUFRG_CUDA(cudaMallocHost((void**)&f.hctl, sizeof(FlowCtl) * b->n));
-  std::vector<Seg> seg(b->n);
-  std::vector<int> prefix(b->n + 1, 0);
-  for (int i = 0; i < b->n; ++i) {
-    const PointDesc& d = b->view.h[i];
-    seg[i].off = d.off_state;
-    seg[i].len = 3LL * d.nl * d.nff * d.nff;
-    prefix[i + 1] = prefix[i] + (int)((seg[i].len + kChunk - 1) / kChunk);
-  }
-  f.n_chunks = prefix[b->n];
-  if (cudaMalloc((void**)&f.seg, sizeof(Seg) * b->n) != cudaSuccess ||
-      cudaMalloc((void**)&f.prefix, sizeof(int) * (b->n + 1)) != cudaSuccess)
+  std::vector<Seg> seg(2 * (size_t)b->n);
+  std::vector<int> prefix(2 * (size_t)(b->n + 1), 0);
+  for (int w = 0; w < 2; ++w)
+    for (int i = 0; i < b->n; ++i) {
+      const PointDesc& d = b->view.h[i];
+      Seg& g = seg[(size_t)w * b->n + i];
+      g.off = w ? d.off_wstate : d.off_state;
+      g.len = 3LL * (w ? d.nrow : d.nl) * d.nff * d.nff;
+      int* pf = prefix.data() + (size_t)w * (b->n + 1);
+      pf[i + 1] = pf[i] + (int)((g.len + kChunk - 1) / kChunk);
+    }
+  if (cudaMalloc((void**)&f.seg_lay[0], sizeof(Seg) * seg.size()) != cudaSuccess ||
+      cudaMalloc((void**)&f.prefix_lay[0], sizeof(int) * prefix.size()) != cudaSuccess)
     return TUFRG_ERR_OOM;
-  TUFRG_CUDA(cudaMemcpy(f.seg, seg.data(), sizeof(Seg) * b->n, cudaMemcpyHostToDevice));
-  TUFRG_CUDA(cudaMemcpy(f.prefix, prefix.data(), sizeof(int) * (b->n + 1),
+  f.seg_lay[1] = f.seg_lay[0] + b->n;
+  f.prefix_lay[1] = f.prefix_lay[0] + (b->n + 1);
+  for (int w = 0; w < 2; ++w) f.n_chunks_lay[w] = prefix[(size_t)w * (b->n + 1) + b->n];
+  TUFRG_CUDA(cudaMemcpy(f.seg_lay[0], seg.data(), sizeof(Seg) * seg.size(),
+                        cudaMemcpyHostToDevice));
+  TUFRG_CUDA(cudaMemcpy(f.prefix_lay[0], prefix.data(), sizeof(int) * prefix.size(),
                         cudaMemcpyHostToDevice));
   return TUFRG_OK;
 }
@@ -458,6 +470,15 @@ tufrg_status batch_flow(tufrg_batch* b, const tufrg_flow_opts* o, double* y_dev,
     }
     f.graph_wedge = f.wedge;
   }
+  const int lay = f.wedge ? 1 : 0;
+  f.seg = f.seg_lay[lay];
+  f.prefix = f.prefix_lay[lay];
+  f.n_chunks = f.n_chunks_lay[lay];
+  if (f.wedge) {
+    TUFRG_CHECK(launch_wedge_compress(b->view, f.y, f.ynew, st));
+    TUFRG_CUDA(cudaMemcpyAsync(f.y, f.ynew, sizeof(double) * b->view.wstate_elems,
+                               cudaMemcpyDeviceToDevice, st));
+  }
   TUFRG_CHECK(bstage(b, f.y, f.ytmp, {}, 0.0, f.k[0], st));  // k1 = f(s0, y0)
   TUFRG_CHECK(battempt_graph(b, st));
   int attempts = 0;
@@ -480,10 +501,17 @@ tufrg_status batch_flow(tufrg_batch* b, const tufrg_flow_opts* o, double* y_dev,
                                                        f.seg, f.prefix, np, 1);
   bbisect_kernel<<<G, 128, 0, st>>>(f.ctl, np, 2);
   bbisect_kernel<<<G, 128, 0, st>>>(f.ctl, np, 3);
-  bmax_kernel<<<f.n_chunks, kFlowThreads, 0, st>>>(f.y, f.ctl, f.seg, f.prefix, np, 0);
-  bmax_kernel<<<f.n_chunks, kFlowThreads, 0, st>>>(f.y, f.ctl, f.seg, f.prefix, np, 1);
+  // the final states in full (wedge layouts expanded to every l), then their
+  // largest elements
+  if (f.wedge)
+    TUFRG_CHECK(launch_wedge_expand(b->view, f.y, y_dev, st));
+  else
+    TUFRG_CUDA(cudaMemcpyAsync(y_dev, f.y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  bmax_kernel<<<f.n_chunks_lay[0], kFlowThreads, 0, st>>>(y_dev, f.ctl, f.seg_lay[0],
+                                                          f.prefix_lay[0], np, 0);
+  bmax_kernel<<<f.n_chunks_lay[0], kFlowThreads, 0, st>>>(y_dev, f.ctl, f.seg_lay[0],
+                                                          f.prefix_lay[0], np, 1);
   TUFRG_CUDA(cudaGetLastError());
-  TUFRG_CUDA(cudaMemcpyAsync(y_dev, f.y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   TUFRG_CHECK(read_ctls(b, st));
   tufrg_status first = TUFRG_OK;
   for (int i = 0; i < np; ++i) {

@@ -85,6 +85,47 @@ __global__ void covariance_check_kernel(const PointDesc* __restrict__ pts,
   }
 }
 
+// Wedge layout of a point-group covariant state: its values at the
+// representative l of each loop row, [3][nrow][nff][nff].  compress takes
+// them from the full state; expand writes every l a row serves as
+// y(g l) = R^g y(l) R^g^T.  One CTA per (point, row).
+__global__ void wedge_compress_kernel(const PointDesc* __restrict__ pts,
+                                      const int* __restrict__ prefix, int n,
+                                      const double* __restrict__ y, double* __restrict__ w) {
+  const int p = point_of(prefix, n, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  const int row = blockIdx.x - prefix[p];
+  const int n2 = pd.nff * pd.nff;
+  const size_t rep = (size_t)pd.rowimg[pd.rowimg_ptr[row]].x * n2;
+  for (int e = threadIdx.x; e < 3 * n2; e += blockDim.x) {
+    const int ch = e / n2, r = e - ch * n2;
+    w[pd.off_wstate + ((size_t)ch * pd.nrow + row) * n2 + r] =
+        y[pd.off_state + (size_t)ch * pd.nl * n2 + rep + r];
+  }
+}
+
+__global__ void wedge_expand_kernel(const PointDesc* __restrict__ pts,
+                                    const int* __restrict__ prefix, int n,
+                                    const double* __restrict__ w, double* __restrict__ y) {
+  const int p = point_of(prefix, n, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  const int row = blockIdx.x - prefix[p];
+  const int nff = pd.nff, n2 = nff * nff;
+  const double* src = w + pd.off_wstate + (size_t)row * n2;
+  const size_t wch = (size_t)pd.nrow * n2, ych = (size_t)pd.nl * n2;
+  for (int i = pd.rowimg_ptr[row]; i < pd.rowimg_ptr[row + 1]; ++i) {
+    const int2 lg = pd.rowimg[i];
+    const int* perm = pd.symperm + lg.y * nff;
+    const int* sign = pd.symsign + lg.y * nff;
+    double* dst = y + pd.off_state + (size_t)lg.x * n2;
+    for (int e = threadIdx.x; e < 3 * n2; e += blockDim.x) {
+      const int ch = e / n2, r = e - ch * n2, m = r / nff, nn = r - m * nff;
+      const double v = src[ch * wch + perm[m] * nff + perm[nn]];
+      dst[ch * ych + r] = sign[m] * sign[nn] > 0 ? v : -v;
+    }
+  }
+}
+
 // Split-K combination of one (channel, pair) and 32 rows: partial sums laid
 // out as [split][2][P][R] (P pair stride, R row stride), FP64 result
 // scaled by -1/4 (pp) / +1/4 (ph) (and 1/Omega^2 for the tensor-core
@@ -162,21 +203,75 @@ __device__ __forceinline__ void reduce_rows(const T* __restrict__ partial, int P
   }
 }
 
-// tensor-core partials of every point: CTA -> (point, channel, pair, 32 rows
-// of the rows the view computes)
+// Tensor-core partials of every point, laid out [split][2][npad][nrow_pad]
+// (nrow_pad a multiple of 128): CTA -> (point, channel, pair, 128 rows of
+// the rows the view computes, from row_lo rounded down to a multiple of 4).
+// Each lane sums 4 adjacent rows with one 16-byte load per split (a warp
+// reads 512 contiguous bytes), four splits in flight; the splits and the
+// phases are combined in the order of reduce_rows (same result).  Rows of a
+// 4-row group outside [row_lo, row_hi) are read (inside the point's
+// nrow_pad rows) but not stored.
+constexpr int kTcRowsPerCta = 128;
+
+__host__ __device__ inline int tc_rows_start(int row_lo) { return row_lo & ~3; }
+__host__ __device__ inline int tc_rows_groups(int row_lo, int row_hi) {
+  return (row_hi - tc_rows_start(row_lo) + kTcRowsPerCta - 1) / kTcRowsPerCta;
+}
+
+__device__ __forceinline__ void pair_add4(float2 (&s)[4], float4 v) {
+  s[0] = pair_add(s[0], v.x);
+  s[1] = pair_add(s[1], v.y);
+  s[2] = pair_add(s[2], v.z);
+  s[3] = pair_add(s[3], v.w);
+}
+
 __global__ void __launch_bounds__(32 * kPhases)
     tc_rows_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int n,
                    const float* __restrict__ partial, double* __restrict__ rowres) {
   const int p = point_of(prefix, n, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int tiles = (pd.row_hi - pd.row_lo + 31) / 32;
+  const int groups = tc_rows_groups(pd.row_lo, pd.row_hi);
   const int loc = blockIdx.x - prefix[p];
-  const int t = loc % tiles, r = loc / tiles, q = r % pd.npair, ch = r / pd.npair;
+  const int g = loc % groups, r = loc / groups, q = r % pd.npair, ch = r / pd.npair;
+  const int lane = threadIdx.x & 31, phase = threadIdx.x >> 5;
+  const int row = tc_rows_start(pd.row_lo) + kTcRowsPerCta * g + 4 * lane;  // first of 4
+  const bool live = row < pd.row_hi;
+  const float4* src = reinterpret_cast<const float4*>(
+      partial + pd.off_partial + ((size_t)ch * pd.npad + q) * pd.nrow_pad + row);
+  const size_t stride = (size_t)2 * pd.npad * pd.nrow_pad / 4;  // float4 per split
+  const int ksplit = pd.ksplit;
+  float2 s[4] = {};
+  if (live) {
+    for (int sp = phase; sp < ksplit; sp += 4 * kPhases) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        v[u] = sp + u * kPhases < ksplit ? __ldg(src + (size_t)(sp + u * kPhases) * stride)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (sp + u * kPhases < ksplit) pair_add4(s, v[u]);
+    }
+  }
+  __shared__ float2 red[kPhases][4][33];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) red[phase][j][lane] = s[j];
+  __syncthreads();
+  if (phase != 0 || !live) return;
   // the tensor-core weights carry a factor Omega^2
   const double om = pd.lam[0];
-  reduce_rows(partial + pd.off_partial, pd.npad, pd.nrow_pad, pd.ksplit, pd.npair, pd.nrow,
-              pd.row_hi, ch, q, pd.row_lo + 32 * t, rowres + pd.off_rowres, 1.0 / (om * om));
+  const double scale = (ch == 0 ? -0.25 : 0.25) / (om * om);
+  double* out = rowres + pd.off_rowres + (size_t)ch * pd.nrow * pd.npair + q;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 t = red[0][j][lane];
+#pragma unroll
+    for (int k = 1; k < kPhases; ++k) t = pair_add(t, red[k][j][lane]);
+    const int rj = row + j;
+    if (rj >= pd.row_lo && rj < pd.row_hi)
+      out[(size_t)rj * pd.npair] = ((double)t.x + (double)t.y) * scale;
+  }
 }
 
 // FP64-path partials of one context
@@ -191,6 +286,10 @@ __global__ void __launch_bounds__(32 * kPhases)
 }  // namespace
 
 int rows_reduce_ctas(int npair, int nrow) { return 2 * npair * ((nrow + 31) / 32); }
+
+int tc_rows_ctas(int npair, int row_lo, int row_hi) {
+  return 2 * npair * tc_rows_groups(row_lo, row_hi);
+}
 
 tufrg_status launch_tc_rows_multi(const MultiView& v, cudaStream_t st) {
   tc_rows_kernel<<<v.total(kKindReduce), 32 * kPhases, 0, st>>>(v.d, v.dprefix(kKindReduce), v.n,
@@ -212,6 +311,22 @@ tufrg_status launch_covariance_check(const MultiView& v, const double* y,
   TUFRG_CUDA(cudaMemsetAsync(dev, 0, sizeof(unsigned long long) * 2 * v.n, st));
   covariance_check_kernel<<<v.total(kKindExpand), 128, 0, st>>>(v.d, v.dprefix(kKindExpand), v.n,
                                                                 y, dev);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+tufrg_status launch_wedge_compress(const MultiView& v, const double* y, double* w,
+                                   cudaStream_t st) {
+  wedge_compress_kernel<<<v.total(kKindExpand), 128, 0, st>>>(v.d, v.dprefix(kKindExpand), v.n,
+                                                              y, w);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+tufrg_status launch_wedge_expand(const MultiView& v, const double* w, double* y,
+                                 cudaStream_t st) {
+  wedge_expand_kernel<<<v.total(kKindExpand), 128, 0, st>>>(v.d, v.dprefix(kKindExpand), v.n, w,
+                                                            y);
   TUFRG_CUDA(cudaGetLastError());
   return TUFRG_OK;
 }

@@ -203,6 +203,9 @@ struct FlowState {
   // l only.  graphs_wedge: the setting the attempt graphs were captured with
   bool wedge = false, graphs_wedge = false;
   unsigned long long* cov = nullptr;  // [2]: covariance deviation and max |y| (device)
+  // elements of the flow's vectors: the wedge layout [3][nrow][nff][nff]
+  // (the state at the rows' representatives), or the full state
+  size_t nflow = 0;
   // loop surrogate: accepted steps since the last judgement, the scale at
   // which the judge rejected it, right-hand sides it served, judgements
   int since_judge = 0;
@@ -256,7 +259,7 @@ tufrg_status stage(tufrg_ctx* c, const double* y, double* out,
     cb.k[j] = terms[j].second;
   }
   cb.c = cnode;
-  const size_t n = c->state_elems();
+  const size_t n = f.nflow;
   // the stage's state on the projection stream (its consumer), its scale on
   // the loop stream: the loops start without waiting for the combination
   TUFRG_CUDA(cudaEventRecord(c->ev_stage, st));
@@ -270,7 +273,7 @@ tufrg_status stage(tufrg_ctx* c, const double* y, double* out,
 // One DoPri5 attempt: stages 2..7, error norm, control, accept.
 tufrg_status enqueue_attempt(tufrg_ctx* c, cudaStream_t st) {
   FlowState& f = *c->flow;
-  const size_t n = c->state_elems();
+  const size_t n = f.nflow;
   for (int i = 1; i < 7; ++i) {
     std::vector<std::pair<double, const double*>> t;
     for (int j = 0; j < i; ++j)
@@ -311,7 +314,7 @@ tufrg_status write_ctl(tufrg_ctx* c, const FlowCtl& v, cudaStream_t st) {
 // interpolant, then the state at the crossing replaces y.
 tufrg_status resolve_crossing(tufrg_ctx* c, cudaStream_t st) {
   FlowState& f = *c->flow;
-  const size_t n = c->state_elems();
+  const size_t n = f.nflow;
   const int G = grid_for(n);
   FlowCtl cur = *f.hc;
   cur.bis_a = cur.s_prev;
@@ -336,13 +339,16 @@ tufrg_status resolve_crossing(tufrg_ctx* c, cudaStream_t st) {
 
 tufrg_status checkpoints_in_last_step(tufrg_ctx* c, cudaStream_t st) {
   FlowState& f = *c->flow;
-  const size_t n = c->state_elems();
+  const size_t n = f.nflow;
   while (f.next_ck < f.cks.size() && f.cks[f.next_ck].first >= f.hc->s &&
          f.cks[f.next_ck].first <= f.hc->s_prev) {
-    double* dst = f.ck_out + n * f.cks[f.next_ck].second;
+    // the full state of the checkpoint (a wedge-layout interpolant expanded)
+    double* dst = f.ck_out + c->state_elems() * f.cks[f.next_ck].second;
     hermite_kernel<<<grid_for(n), 256, 0, st>>>(f.yprev, f.k1prev, f.y, f.k[0], f.ctl,
-                                                f.cks[f.next_ck].first, 0, dst, n, 0);
+                                                f.cks[f.next_ck].first, 0,
+                                                f.wedge ? f.ytmp : dst, n, 0);
     TUFRG_CUDA(cudaGetLastError());
+    if (f.wedge) TUFRG_CHECK(launch_wedge_expand(c->view, f.ytmp, dst, st));
     ++f.next_ck;
   }
   return TUFRG_OK;
@@ -430,7 +436,7 @@ tufrg_status dopri5_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
 // Classic RK4 with equal steps; stops early when max |y| exceeds the threshold.
 tufrg_status rk4_steps(tufrg_ctx* c, int n_steps, cudaStream_t st) {
   FlowState& f = *c->flow;
-  const size_t n = c->state_elems();
+  const size_t n = f.nflow;
   const int G = grid_for(n);
   for (int i = 0; i < n_steps && !f.finished; ++i) {
     if ((f.hc->s_end - f.hc->s) * f.hc->dir <= 1e-12) {  // reached ln Lambda_min
@@ -553,7 +559,8 @@ tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
   }
   TUFRG_CUDA(cudaMemcpyAsync(f.y, y0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   // the wedge when the initial state is covariant (the bare start, zeros, is)
-  // and every loop is exact (a surrogate's loops are not covariant)
+  // and every loop is exact (a surrogate's loops are not covariant): the
+  // flow then integrates the state at the rows' representatives only
   f.wedge = false;
   if (!c->sur) {
     TUFRG_CHECK(launch_covariance_check(c->view, f.y, f.cov, st));
@@ -564,6 +571,13 @@ tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
     std::memcpy(&dev, &h[0], 8);
     std::memcpy(&amax, &h[1], 8);
     f.wedge = dev <= 1e-13 * amax;
+  }
+  f.nflow = n;
+  if (f.wedge) {
+    TUFRG_CHECK(launch_wedge_compress(c->view, f.y, f.ynew, st));
+    f.nflow = c->view.wstate_elems;
+    TUFRG_CUDA(cudaMemcpyAsync(f.y, f.ynew, sizeof(double) * f.nflow, cudaMemcpyDeviceToDevice,
+                               st));
   }
   if (f.wedge != f.graphs_wedge) {
     for (auto& g : f.attempt) {
@@ -607,11 +621,17 @@ tufrg_status flow_state(tufrg_ctx* c, double* y_out, tufrg_result* r, cudaStream
   cur.max_u = 0;
   cur.arg_u = ~0ull;
   TUFRG_CHECK(write_ctl(c, cur, st));
-  max_kernel<<<G, 256, 0, st>>>(f.y, f.ctl, n, 0);
-  argmax_kernel<<<G, 256, 0, st>>>(f.y, f.ctl, n);
+  // the full state (a wedge-layout state expanded to every l)
+  const double* yfull = f.y;
+  if (f.wedge) {
+    TUFRG_CHECK(launch_wedge_expand(c->view, f.y, f.ytmp, st));
+    yfull = f.ytmp;
+  }
+  max_kernel<<<G, 256, 0, st>>>(yfull, f.ctl, n, 0);
+  argmax_kernel<<<G, 256, 0, st>>>(yfull, f.ctl, n);
   TUFRG_CUDA(cudaGetLastError());
   if (y_out)
-    TUFRG_CUDA(cudaMemcpyAsync(y_out, f.y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    TUFRG_CUDA(cudaMemcpyAsync(y_out, yfull, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   TUFRG_CHECK(read_ctl(c, st));
   if (r) {
     fill_progress(c, r);

@@ -100,6 +100,9 @@ struct PointDesc {
   // tensor-core loops
   int nfx, nfy, hx, hy, wy, n_ext, nkb, kpad_tc, nrow_pad, npad, nsets, ksplit;
   long long off_state, off_chi, off_bt, off_fkey, off_partial;
+  // offset of the point's wedge state [3][nrow][nff][nff]: the state at the
+  // representative l of each loop row (flows of a point-group covariant state)
+  long long off_wstate;
   const double4_32a* tab;
   const float* xiext;  // [n_ext] xi over the halo table's points (FP32)
   float4* ext;
@@ -169,6 +172,7 @@ struct MultiView {
   double* d_rowres = nullptr;  // loops of the rows, FP64, all points
   // elements of the packed buffers: state (y, V, dy), loops, bond space, keys
   size_t state_elems = 0, chi_elems = 0, bt_elems = 0, fkey_elems = 0, rowres_elems = 0;
+  size_t wstate_elems = 0;
   int total(int kind) const { return prefix[(size_t)kind * (n + 1) + n]; }
   const int* dprefix(int kind) const { return d_prefix + (size_t)kind * (n + 1); }
 };
@@ -319,8 +323,9 @@ tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 
 // steps i-iii at the scale stored in c->d_lambda with loops in precision prec;
 // dy scaled by c->d_lambda[1] if scaled
-// wedge: projections and products at the rows' representative l only
-// (flows of a point-group covariant state)
+// wedge: y and dy in the wedge layout [3][nrow][nff][nff] of a point-group
+// covariant state (flows), projections and products at the rows'
+// representative l only
 tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
                         cudaStream_t st, bool wedge = false);
 
@@ -347,6 +352,7 @@ tufrg_status launch_expand_multi(const MultiView& v, double* chi, cudaStream_t s
 // split-K combinations into the row loops (tensor-core partials of every
 // point of v; FP64 partials of one context)
 int rows_reduce_ctas(int npair, int nrow);
+int tc_rows_ctas(int npair, int row_lo, int row_hi);
 tufrg_status launch_tc_rows_multi(const MultiView& v, cudaStream_t st);
 tufrg_status launch_fp64_rows(const double* partial, int mpad, int ksplit, int npair, int nrow,
                               double* rowres, cudaStream_t st);
@@ -369,15 +375,15 @@ constexpr int kGroupedNff = 21;
 // [3][ncx][nd][nff*nff], later reused for the overlap sums [positions Y][nff][nff]
 size_t bt_region(int ncx, int nd, int nff, int ny_total);
 // projections and products of every point; bt, fkey: packed workspaces.
-// rows: the projected couplings at the representative l of each loop row
-// only (the wedge of a point-group covariant state)
+// rows: the state in the wedge layout (a point-group covariant state at the
+// representative l of each loop row), the projected couplings at the
+// representatives, in the wedge layout
 tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
                                   void* bt, void* fkey, cudaStream_t st, bool rows = false);
 // chi == nullptr: the loops of each l are gathered from the row loops
 // v.d_rowres (the orbit expansion fused into the products).  rows (with chi
-// == nullptr): the products at each row's representative l only, written to
-// every l the row serves as R^g dy R^g^T (needs the couplings of the
-// representatives, and a covariant state for the result to be exact)
+// == nullptr): couplings and dy in the wedge layout, the products at each
+// row's representative l only (a covariant state's right-hand side)
 tufrg_status launch_products_multi(const MultiView& v, int prec, const double* vin,
                                    const double* chi, double* dy, bool scaled, cudaStream_t st,
                                    bool rows = false);
@@ -386,6 +392,13 @@ tufrg_status launch_products_multi(const MultiView& v, int prec, const double* v
 // dev[2 * i + 1] as the bit patterns of non-negative doubles
 tufrg_status launch_covariance_check(const MultiView& v, const double* y,
                                      unsigned long long* dev, cudaStream_t st);
+// the wedge layout [3][nrow][nff][nff] of each point's state (its values at
+// the rows' representatives) from the full state, and back: expand writes
+// every l a row serves as y(g l) = R^g y(l) R^g^T
+tufrg_status launch_wedge_compress(const MultiView& v, const double* y, double* w,
+                                   cudaStream_t st);
+tufrg_status launch_wedge_expand(const MultiView& v, const double* w, double* y,
+                                 cudaStream_t st);
 // loop contraction up to the row loops in c->view.d_rowres (no expansion);
 // prec must not be the surrogate
 tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st);

@@ -131,7 +131,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
   v.d_err = err;
   v.tc_prec = tc_prec;
   v.prefix.assign((size_t)kKinds * (n + 1), 0);
-  size_t off_state = 0, off_chi = 0, off_bt = 0, off_fkey = 0, off_rowres = 0;
+  size_t off_state = 0, off_chi = 0, off_bt = 0, off_fkey = 0, off_rowres = 0, off_wstate = 0;
   const bool tc = tc_prec != TUFRG_FP64;
   // the projection form of the whole view (one launch sequence for all points)
   bool grouped = false;
@@ -171,6 +171,8 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.off_chi = (long long)off_chi;
     d.off_bt = (long long)off_bt;
     d.off_fkey = (long long)off_fkey;
+    d.off_wstate = (long long)off_wstate;
+    off_wstate += (size_t)3 * c->nrow * c->nff * c->nff;
     off_state += (size_t)3 * c->nl * c->nff * c->nff;
     off_chi += (size_t)2 * c->nl * c->nff * c->nff;
     off_bt += bt_region(c->ncx, 2 * c->proj.dmax + 1, c->nff, c->proj.gy_off[3]);
@@ -207,7 +209,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.skip = skip ? skip[i] : nullptr;
     const int cnt[kKinds] = {
         tc ? table_ctas(d.n_ext) : 0,
-        tc ? rows_reduce_ctas(d.npair, d.row_hi - d.row_lo) : 0,
+        tc ? tc_rows_ctas(d.npair, d.row_lo, d.row_hi) : 0,
         d.feedback ? bond_ctas(d.ncx, d.nff) : 0,
         d.feedback ? dft_ctas(d.nd) : 0,
         grouped && d.feedback ? d.gy_off[3] : 0,
@@ -227,6 +229,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     v.nf_uniform = i == 0 ? nf : (v.nf_uniform == nf ? nf : 0);
   }
   v.state_elems = off_state;
+  v.wstate_elems = off_wstate;
   v.chi_elems = off_chi;
   v.bt_elems = off_bt;
   v.fkey_elems = off_fkey;

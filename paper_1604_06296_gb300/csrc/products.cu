@@ -5,7 +5,7 @@
 //      =  (2 V^D - V^C) (chi^ph V^D) - V^D (chi^ph V^C)
 // One CTA per (point, l) over all points of a batch; the five Nff x Nff
 // operands and three intermediate products sit in shared memory (8 Nff^2
-// doubles <= 54 KB for Nff = 29; one more for the row form below).  FP64 for an FP64 context, FP32 arithmetic
+// doubles <= 54 KB for Nff = 29).  FP64 for an FP64 context, FP32 arithmetic
 // for the mixed-precision contexts.
 #include "device_util.cuh"
 
@@ -95,12 +95,13 @@ __global__ void products_kernel(const PointDesc* __restrict__ pts,
   }
 }
 
-// The products at the representative l of one loop row (its loops are the
-// row loops themselves), written to every l' = g l the row serves as
-// dy(g l) = R^g dy(l) R^g^T, (R^g X R^g^T)_mn = s_m s_n X_{p(m) p(n)}: the
-// right-hand side of a state that is point-group covariant (B(g l) =
-// R^g B(l) R^g^T for every g that maps l into the zone without a fold, App. C)
-// is covariant in the same way.  One CTA per (point, row).
+// The products of a point-group covariant state (wedge layout: state,
+// couplings and derivative at the representative l of each loop row only,
+// [3][nrow][nff][nff]).  The loops of a representative are its row loops
+// themselves; the right-hand side of a covariant state (B(g l) =
+// R^g B(l) R^g^T for every g that maps l into the zone without a fold,
+// App. C) is covariant in the same way, so the representatives determine it.
+// One CTA per (point, row).
 template <class T, int NF>
 __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
                                      const int* __restrict__ prefix, int np,
@@ -110,10 +111,8 @@ __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int nl = pd.nl, nff = NF ? NF : pd.nff;
+  const int nff = NF ? NF : pd.nff;
   const int row = blockIdx.x - prefix[p];
-  const int i0 = pd.rowimg_ptr[row], i1 = pd.rowimg_ptr[row + 1];
-  const int l = pd.rowimg[i0].x;  // the representative (g = identity)
   extern __shared__ double smd[];
   T* sm = reinterpret_cast<T*>(smd);
   const int n2 = nff * nff;
@@ -125,13 +124,12 @@ __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
   T* T1 = Xh + n2;
   T* T2 = T1 + n2;
   T* T3 = T2 + n2;
-  const size_t chan = (size_t)nl * n2;
-  const size_t off = (size_t)l * n2;
-  const double* v = vbase + pd.off_state;
+  const size_t chan = (size_t)pd.nrow * n2;
+  const size_t off = pd.off_wstate + (size_t)row * n2;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
-    VP[e] = (T)v[off + e];
-    VC[e] = (T)v[chan + off + e];
-    VD[e] = (T)v[2 * chan + off + e];
+    VP[e] = (T)vbase[off + e];
+    VC[e] = (T)vbase[chan + off + e];
+    VD[e] = (T)vbase[2 * chan + off + e];
   }
   const double* rp = rowres + pd.off_rowres + (size_t)row * pd.npair;
   const size_t ch1 = (size_t)pd.nrow * pd.npair;
@@ -150,11 +148,8 @@ __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
     (w == 0 ? T1 : (w == 1 ? T2 : T3))[ij] = s;
   }
   __syncthreads();
-  // dy of the representative, over the loops (read only by the products
-  // above, before the barrier) and a ninth buffer
-  T* dP = Xp;
-  T* dC = Xh;
-  T* dD = T3 + n2;
+  const double sc = scaled ? pd.lam[1] : 1.0;
+  double* dy = dybase + off;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) {
     const int i = e / nff, j = e % nff;
     T a = 0, c = 0, d = 0;
@@ -164,26 +159,9 @@ __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
       d = fma(2 * VD[i * nff + k] - VC[i * nff + k], T3[k * nff + j], d);
       d = fma(-VD[i * nff + k], T2[k * nff + j], d);
     }
-    dP[e] = a;
-    dC[e] = c;
-    dD[e] = d;
-  }
-  __syncthreads();
-  const double sc = scaled ? pd.lam[1] : 1.0;
-  double* dy = dybase + pd.off_state;
-  for (int i = i0; i < i1; ++i) {
-    const int2 lg = pd.rowimg[i];
-    const int* perm = pd.symperm + lg.y * nff;
-    const int* sign = pd.symsign + lg.y * nff;
-    const size_t o = (size_t)lg.x * n2;
-    for (int e = threadIdx.x; e < n2; e += blockDim.x) {
-      const int m = e / nff, n = e % nff;
-      const int src = perm[m] * nff + perm[n];
-      const double sg = sc * (double)(sign[m] * sign[n]);
-      dy[o + e] = sg * (double)dP[src];
-      dy[chan + o + e] = -sg * (double)dC[src];
-      dy[2 * chan + o + e] = sg * (double)dD[src];
-    }
+    dy[e] = sc * (double)a;
+    dy[chan + e] = -sc * (double)c;
+    dy[2 * chan + e] = sc * (double)d;
   }
 }
 
@@ -191,7 +169,7 @@ __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
 
 tufrg_status prepare_products_multi(const MultiView& v) {
   const int smem = smem_optin();
-  if (sizeof(double) * 9 * v.nff_max * v.nff_max > (size_t)smem) return TUFRG_ERR_ARG;
+  if (sizeof(double) * 8 * v.nff_max * v.nff_max > (size_t)smem) return TUFRG_ERR_ARG;
   cudaError_t e = cudaSuccess;
   for_each_nf([&](auto nf) {
     constexpr int NF = decltype(nf)::value;
@@ -220,11 +198,11 @@ tufrg_status launch_products_multi(const MultiView& v, int prec, const double* v
     with_nf(v.nf_uniform, [&](auto nf) {
       constexpr int NF = decltype(nf)::value;
       if (prec == TUFRG_FP64)
-        products_rows_kernel<double, NF><<<blocks, 256, sizeof(double) * 9 * v.nff_max *
+        products_rows_kernel<double, NF><<<blocks, 256, sizeof(double) * 8 * v.nff_max *
                                                             v.nff_max, st>>>(
             v.d, v.dprefix(kKindProductsRows), v.n, vin, v.d_rowres, dy, scaled ? 1 : 0);
       else
-        products_rows_kernel<float, NF><<<blocks, 256, sizeof(float) * 9 * v.nff_max *
+        products_rows_kernel<float, NF><<<blocks, 256, sizeof(float) * 8 * v.nff_max *
                                                            v.nff_max, st>>>(
             v.d, v.dprefix(kKindProductsRows), v.n, vin, v.d_rowres, dy, scaled ? 1 : 0);
     });

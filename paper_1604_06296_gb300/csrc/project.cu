@@ -12,9 +12,11 @@
 // convention).  Three kernels compute the keys and the terms (term form):
 //   bond_dft1, bond_dft2 -- F for every key (below)
 //   contract_terms -- T and the basis change, per (target channel, 4 l)
-// In a flow of a point-group covariant state the last step runs only at the
-// representative l of the loop rows (the products then write every l a row
-// serves); the Fourier keys still sum over every l.
+// In a flow of a point-group covariant state the state is kept at the
+// representative l of the loop rows only (wedge layout [3][nrow][nff][nff]):
+// the Fourier keys still sum over every l, read through the signed
+// permutation that maps each l to its row, and the last step runs at the
+// representatives, writing the couplings in the wedge layout.
 // The phase e^{i l.Y} is the only l dependence of a term, and the terms of a
 // target channel take few distinct Y (41 at Nb = 13, 81 at Nb = 25), so the
 // sums regroup (exactly, by linearity) as
@@ -100,7 +102,10 @@ __host__ __device__ constexpr int hstride(int nff) { return (nff * nff + 1) & ~1
 constexpr int kDft1Threads = 128;
 constexpr int kNdPass = 9;
 
-template <class T>
+// kWedge: the state is given at the rows' representatives only (wedge
+// layout [3][nrow][nff][nff]); B(l) = R^g B(l0) R^g^T is read through the
+// (row, g) serving l, (R^g X R^g^T)_ab = s_a s_b X_{p(a) p(b)}.
+template <class T, bool kWedge>
 __global__ void __launch_bounds__(kDft1Threads)
     bond_dft1_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
                      const double* __restrict__ ybase, typename C2<T>::type* __restrict__ p1base) {
@@ -116,10 +121,30 @@ __global__ void __launch_bounds__(kDft1Threads)
   V* ph = reinterpret_cast<V*>(sm2);  // [ncy][nd] e^{i l_y Y}
   for (int e = threadIdx.x; e < ncy * nd; e += blockDim.x)
     ph[e] = phase_at(pd, (ncx + e / nd) * nd + e % nd, T());
+  // wedge: per iy the element offset of the serving row and its g; the
+  // signed permutations of the 8 elements
+  int* wrow = reinterpret_cast<int*>(ph + ncy * nd);  // [ncy]
+  int* wg = wrow + ncy;                               // [ncy]
+  int* wp = wg + ncy;                                 // [8][nff]
+  int* ws = wp + 8 * pd.nff;                          // [8][nff]
+  if (kWedge) {
+    for (int iy = threadIdx.x; iy < ncy; iy += blockDim.x) {
+      const int2 rg = pd.lrow[ix * ncy + iy];
+      wrow[iy] = (src * pd.nrow + rg.x) * nff2;
+      wg[iy] = rg.y * pd.nff;
+    }
+    for (int e = threadIdx.x; e < 8 * pd.nff; e += blockDim.x) {
+      wp[e] = pd.symperm[e];
+      ws[e] = pd.symsign[e];
+    }
+  }
   __syncthreads();
   const int ab = chunk * kDft1Threads + threadIdx.x;
   if (ab >= nff2) return;
-  const double* B = ybase + pd.off_state + ((size_t)src * pd.nl + (size_t)ix * ncy) * nff2 + ab;
+  const int a = ab / pd.nff, b = ab - a * pd.nff;
+  const double* B = kWedge ? ybase + pd.off_wstate
+                           : ybase + pd.off_state +
+                                 ((size_t)src * pd.nl + (size_t)ix * ncy) * nff2 + ab;
   V* out = p1base + pd.off_bt + ((size_t)(src * ncx + ix) * nd) * nff2 + ab;
   // positions in passes of kNdPass (one pass for the bases of complete shells
   // on grids that resolve them; small grids alias more bond sums to more X)
@@ -129,13 +154,20 @@ __global__ void __launch_bounds__(kDft1Threads)
     for (int d = 0; d < kNdPass; ++d) acc[d] = {0, 0};
 #pragma unroll 4
     for (int iy = 0; iy < ncy; ++iy) {
-      const T b = (T)__ldg(B + (size_t)iy * nff2);
+      T bv;
+      if (kWedge) {
+        const int g = wg[iy];
+        const double w = __ldg(B + wrow[iy] + wp[g + a] * pd.nff + wp[g + b]);
+        bv = (T)(ws[g + a] * ws[g + b] > 0 ? w : -w);
+      } else {
+        bv = (T)__ldg(B + (size_t)iy * nff2);
+      }
       const V* q = ph + iy * nd + d0;
 #pragma unroll
       for (int d = 0; d < kNdPass; ++d)
         if (d0 + d < nd) {
-          acc[d].x = fma(q[d].x, b, acc[d].x);
-          acc[d].y = fma(q[d].y, b, acc[d].y);
+          acc[d].x = fma(q[d].x, bv, acc[d].x);
+          acc[d].y = fma(q[d].y, bv, acc[d].y);
         }
     }
 #pragma unroll
@@ -193,6 +225,14 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Element offset of the state and couplings of channel t at output slot q
+// (transfer momentum l): l in the full layout, or row q in the wedge layout.
+__device__ __forceinline__ size_t slot_offset(const PointDesc& pd, int rows, int t, int q, int l,
+                                              int n2) {
+  return rows ? pd.off_wstate + ((size_t)t * pd.nrow + q) * n2
+              : pd.off_state + ((size_t)t * pd.nl + l) * n2;
+}
+
 // Term form (Nff <= 13).  kTermsL transfer momenta of one target channel per
 // CTA: each term of the (scale-independent) overlap lists and its Fourier key
 // are read once and applied to all of them (only the phases e^{i l.Y} differ).
@@ -234,8 +274,8 @@ __global__ void __launch_bounds__(256)
   if (!pd.feedback) {
     for (int e = threadIdx.x; e < nlb * (int)n2; e += blockDim.x) {
       const int j = e / (int)n2, r = e % (int)n2;
-      const size_t o = ((size_t)t * nl + sl[j]) * n2 + r;
-      vbase[pd.off_state + o] = (r == 0 ? U : 0.0) + own_sign * ybase[pd.off_state + o];
+      const size_t o = slot_offset(pd, rows, t, q0 + j, sl[j], (int)n2) + r;
+      vbase[o] = (r == 0 ? U : 0.0) + own_sign * ybase[o];
     }
     return;
   }
@@ -303,14 +343,13 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   // V_mn = V0 + own + Re sum_b1 c_m(b1) tmp[b1][n]
-  const size_t base = pd.off_state + (size_t)t * nl * n2;
   for (int m = r0; m < nff; m += rstep) {
     if (n >= nff) continue;
     const int mn = m * nff + n;
     double yv[kTermsL];
 #pragma unroll
     for (int jj = 0; jj < kTermsL; ++jj)
-      yv[jj] = jj < nlb ? ybase[base + (size_t)sl[jj] * n2 + mn] : 0.0;
+      yv[jj] = jj < nlb ? ybase[slot_offset(pd, rows, t, q0 + jj, sl[jj], n2) + mn] : 0.0;
     T acc[kTermsL];
 #pragma unroll
     for (int jj = 0; jj < kTermsL; ++jj) acc[jj] = 0;
@@ -325,7 +364,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int jj = 0; jj < kTermsL; ++jj)
       if (jj < nlb)
-        vbase[base + (size_t)sl[jj] * n2 + mn] =
+        vbase[slot_offset(pd, rows, t, q0 + jj, sl[jj], n2) + mn] =
             (mn == 0 ? U : 0.0) + own_sign * yv[jj] + (double)acc[jj];
   }
 }
@@ -440,7 +479,6 @@ __global__ void __launch_bounds__(kCThreads)
   __syncthreads();
   const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
   const double U = pd.U;
-  const size_t base = pd.off_state + (size_t)t * nl * n2;  // l at base + l n2
   const int c = threadIdx.x % kCM, j0 = (threadIdx.x / kCM) * kCR;  // entry, first slot
   const int mn = mn0 + c;
   T acc[kCR];
@@ -477,16 +515,18 @@ __global__ void __launch_bounds__(kCThreads)
 #pragma unroll
   for (int j = 0; j < kCR; ++j)
     if (j0 + j < nlb) {
-      const size_t o = base + (size_t)sl[j0 + j] * n2 + mn;
+      const size_t o = slot_offset(pd, rows, t, q0 + j0 + j, sl[j0 + j], n2) + mn;
       vbase[o] = (mn == 0 ? U : 0.0) + own_sign * ybase[o] + (double)(acc[j] * inv_nl);
     }
 }
 
 template <class T>
 size_t dft1_smem(const MultiView& v) {
-  int m = 1;
-  for (const PointDesc& d : v.h) m = std::max(m, d.ncy * d.nd);
-  return sizeof(typename C2<T>::type) * m;
+  size_t m = 1;
+  for (const PointDesc& d : v.h)
+    m = std::max(m, sizeof(typename C2<T>::type) * d.ncy * d.nd +
+                        sizeof(int) * (2 * (size_t)d.ncy + 16 * (size_t)d.nff));
+  return m;
 }
 template <class T>
 size_t dft2_smem(const MultiView& v) {
@@ -530,7 +570,9 @@ tufrg_status prepare_typed(const MultiView& v) {
       (int)overlap_smem<T>(v) > smem ||
       (int)contract_terms_smem<T>(v) + 64 > smem)
     return TUFRG_ERR_ARG;
-  TUFRG_CUDA(cudaFuncSetAttribute(bond_dft1_kernel<T>,
+  TUFRG_CUDA(cudaFuncSetAttribute(bond_dft1_kernel<T, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  TUFRG_CUDA(cudaFuncSetAttribute(bond_dft1_kernel<T, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaError_t e = cudaSuccess;
   for_each_nf([&](auto nf) {
@@ -555,8 +597,12 @@ tufrg_status project_typed(const MultiView& v, const double* y, double* out, voi
   V* bt = reinterpret_cast<V*>(btv);
   V* fkey = reinterpret_cast<V*>(fkv);
   if (v.total(kKindBond) > 0) {
-    bond_dft1_kernel<T><<<v.total(kKindBond), kDft1Threads, dft1_smem<T>(v), st>>>(
-        v.d, v.dprefix(kKindBond), v.n, y, bt);
+    if (rows)
+      bond_dft1_kernel<T, true><<<v.total(kKindBond), kDft1Threads, dft1_smem<T>(v), st>>>(
+          v.d, v.dprefix(kKindBond), v.n, y, bt);
+    else
+      bond_dft1_kernel<T, false><<<v.total(kKindBond), kDft1Threads, dft1_smem<T>(v), st>>>(
+          v.d, v.dprefix(kKindBond), v.n, y, bt);
     TUFRG_CUDA(cudaGetLastError());
   }
   if (v.total(kKindDft) > 0) {
