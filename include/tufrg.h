@@ -258,6 +258,14 @@ tufrg_status tufrg_mu_for_density(double t, double tp, double n, int32_t nf_x,
  * or wait_us out of range. */
 tufrg_status tufrg_selftest_wait(tufrg_ctx* ctx, int32_t wait_us, void* cuda_stream);
 
+/* Diagnostic of the library's own FP64 <-> FP32 conversions (no counterpart
+ * in the paper; the FP32 projections read an FP32 copy of the state made by
+ * them): x_dev [n] doubles -> y32_dev [n] floats rounded to nearest even,
+ * then y32_dev -> back_dev [n] doubles (exact).  Device pointers, enqueued
+ * on cuda_stream.  TUFRG_ERR_ARG for null pointers or n < 0. */
+tufrg_status tufrg_selftest_convert(const double* x_dev, float* y32_dev, double* back_dev,
+                                    int64_t n, void* cuda_stream);
+
 /* Synchronises the stream and reports device-side failures of earlier
  * asynchronous calls on this context: TUFRG_ERR_TIMEOUT if a bounded wait
  * inside a kernel (tensor-core pipeline barriers) gave up; the flag is then

@@ -95,6 +95,7 @@ SIGNATURES = {
                               POINTER(c_double)], c_int32),
     "tufrg_check": ([c_void_p, c_void_p], c_int32),
     "tufrg_selftest_wait": ([c_void_p, c_int32, c_void_p], c_int32),
+    "tufrg_selftest_convert": ([c_void_p, c_void_p, c_void_p, c_int64, c_void_p], c_int32),
     "tufrg_autotune": ([c_void_p, c_double, POINTER(tufrg_tune_report), c_void_p], c_int32),
     "tufrg_batch_setup": ([c_int32, POINTER(tufrg_params), c_void_p, POINTER(c_void_p)],
                           c_int32),
@@ -277,6 +278,12 @@ def tufrg_check(ctx, stream: int = 0) -> None:
 
 def tufrg_selftest_wait(ctx, wait_us: int, stream: int = 0) -> None:
     _check(lib().tufrg_selftest_wait(ctx, int(wait_us), _dptr(stream)), "tufrg_selftest_wait")
+
+
+def tufrg_selftest_convert(x_ptr: int, y32_ptr: int, back_ptr: int, n: int,
+                           stream: int = 0) -> None:
+    _check(lib().tufrg_selftest_convert(_dptr(x_ptr), _dptr(y32_ptr), _dptr(back_ptr), int(n),
+                                        _dptr(stream)), "tufrg_selftest_convert")
 
 
 def tufrg_status_string(status: int) -> str:

@@ -75,12 +75,15 @@ tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st) {
   return launch_loops_tc_rows_multi(c->view, st);
 }
 
-tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
-                        cudaStream_t st, bool wedge) {
+int rhs_arith(const tufrg_ctx* c, int prec) {
   // projections and products in FP32 arithmetic for a mixed-precision
   // context, in FP64 for an FP64 context and after a switch to FP64 loops
-  const int arith =
-      (prec == TUFRG_FP64 || c->p.precision == TUFRG_FP64) ? TUFRG_FP64 : TUFRG_3XTF32;
+  return (prec == TUFRG_FP64 || c->p.precision == TUFRG_FP64) ? TUFRG_FP64 : TUFRG_3XTF32;
+}
+
+tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
+                        cudaStream_t st, bool wedge, const float* y32) {
+  const int arith = rhs_arith(c, prec);
   // the projections (state only) beside the loops (scale only)
   TUFRG_CUDA(cudaEventRecord(c->ev_fork, st));
   TUFRG_CUDA(cudaStreamWaitEvent(c->pstream, c->ev_fork, 0));
@@ -88,7 +91,16 @@ tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, boo
   // (or, for a covariant state, run at the rows' representatives only)
   const bool rows = prec != kLoopSurrogate;
   if (wedge && !rows) return TUFRG_ERR_STATE;  // a wedge-layout state needs exact loops
-  TUFRG_CHECK(launch_project_multi(c->view, arith, y, c->d_V, c->d_bt, c->d_fkey, c->pstream,
+  const void* yin = y;
+  if (arith != TUFRG_FP64) {  // the FP32 kernels read an FP32 copy of the state
+    if (!y32) {
+      TUFRG_CHECK(launch_to_f32(y, c->d_y32, wedge ? c->view.wstate_elems : c->view.state_elems,
+                                c->pstream));
+      y32 = c->d_y32;
+    }
+    yin = y32;
+  }
+  TUFRG_CHECK(launch_project_multi(c->view, arith, yin, c->d_V, c->d_bt, c->d_fkey, c->pstream,
                                    wedge));
   TUFRG_CUDA(cudaEventRecord(c->ev_join, c->pstream));
   if (rows)
@@ -183,16 +195,30 @@ tufrg_status tufrg_loops(tufrg_ctx* c, double lambda, double* chi_dot_dev, void*
 
 tufrg_status tufrg_project(tufrg_ctx* c, const double* y_dev, double* v_dev, void* stream) {
   if (!c || !y_dev || !v_dev || y_dev == v_dev) return TUFRG_ERR_ARG;
-  return tufrg::launch_project_multi(c->view, c->p.precision, y_dev, v_dev, c->d_bt, c->d_fkey,
-                                     (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->p.precision == TUFRG_FP64)
+    return tufrg::launch_project_multi(c->view, TUFRG_FP64, y_dev, v_dev, c->d_bt, c->d_fkey, st);
+  // FP32 arithmetic on an FP32 copy of the state; the couplings returned in FP64
+  const size_t n = c->view.state_elems;
+  float* v32 = reinterpret_cast<float*>(c->d_V);
+  TUFRG_CHECK(tufrg::launch_to_f32(y_dev, c->d_y32, n, st));
+  TUFRG_CHECK(tufrg::launch_project_multi(c->view, c->p.precision, c->d_y32, v32, c->d_bt,
+                                          c->d_fkey, st));
+  return tufrg::launch_to_f64(v32, v_dev, n, st);
 }
 
 tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi_dot_dev,
                             double* dy_dev, void* stream) {
   if (!c || !v_dev || !chi_dot_dev || !dy_dev || dy_dev == v_dev || dy_dev == chi_dot_dev)
     return TUFRG_ERR_ARG;
-  return tufrg::launch_products_multi(c->view, c->p.precision, v_dev, chi_dot_dev, dy_dev, false,
-                                      (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->p.precision == TUFRG_FP64)
+    return tufrg::launch_products_multi(c->view, TUFRG_FP64, v_dev, chi_dot_dev, dy_dev, false, st);
+  // FP32 arithmetic on an FP32 copy of the couplings
+  float* v32 = reinterpret_cast<float*>(c->d_V);
+  TUFRG_CHECK(tufrg::launch_to_f32(v_dev, v32, c->view.state_elems, st));
+  return tufrg::launch_products_multi(c->view, c->p.precision, v32, chi_dot_dev, dy_dev, false,
+                                      st);
 }
 
 namespace {
@@ -291,7 +317,12 @@ tufrg_status tufrg_rhs_from_rows(tufrg_ctx* c, double lambda, const double* rows
   TUFRG_CUDA(cudaMemcpyAsync(c->view.d_rowres, rows_dev,
                              sizeof(double) * 2 * (size_t)c->nrow * c->npair,
                              cudaMemcpyDeviceToDevice, st));
-  TUFRG_CHECK(tufrg::launch_project_multi(c->view, arith, y_dev, c->d_V, c->d_bt, c->d_fkey, st));
+  const void* yin = y_dev;
+  if (arith != TUFRG_FP64) {
+    TUFRG_CHECK(tufrg::launch_to_f32(y_dev, c->d_y32, c->view.state_elems, st));
+    yin = c->d_y32;
+  }
+  TUFRG_CHECK(tufrg::launch_project_multi(c->view, arith, yin, c->d_V, c->d_bt, c->d_fkey, st));
   return tufrg::launch_products_multi(c->view, arith, c->d_V, nullptr, dy_dev, false, st);
 }
 

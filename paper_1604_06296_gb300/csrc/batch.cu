@@ -34,10 +34,12 @@ struct Seg {
   long long off, len;  // the point's elements in the packed state
 };
 
+// out = y + h sum_j a_j k_j and its FP32 copy out32 (the FP32 projections'
+// input) for every active point
 __global__ void bcombo_kernel(const double* __restrict__ y, double* __restrict__ out, Combo cb,
                               const FlowCtl* __restrict__ ctl, double* __restrict__ lam,
                               const Seg* __restrict__ seg, const int* __restrict__ prefix, int n,
-                              int set_lambda) {
+                              int set_lambda, float* __restrict__ out32) {
   const int p = point_of(prefix, n, blockIdx.x);
   const FlowCtl& c = ctl[p];
   if (c.done) return;
@@ -55,7 +57,9 @@ __global__ void bcombo_kernel(const double* __restrict__ y, double* __restrict__
     const long long i = b + u * kFlowThreads + threadIdx.x;
     if (i >= e) break;
     const double acc = combo_sum(cb, i);
-    out[i] = y[i] + h * acc;
+    const double v = y[i] + h * acc;
+    out[i] = v;
+    out32[i] = d2f(v);
   }
 }
 
@@ -249,7 +253,8 @@ struct tufrg_batch {
   int* d_skip = nullptr;    // [n]
   int* d_err = nullptr;
   double* d_chi = nullptr;
-  double* d_V = nullptr;
+  double* d_V = nullptr;    // couplings (FP32, the batch's arithmetic)
+  float* d_y32 = nullptr;   // FP32 copy of the state for the projections
   double2* d_bt = nullptr;
   double2* d_fkey = nullptr;
   std::vector<long long> loop_off;
@@ -267,13 +272,18 @@ int grid_for(int n) { return (n + 127) / 128; }
 
 // wedge: y and dy in the wedge layout (flows of point-group covariant
 // states), projections and products at the rows' representative l only
+// y32: the FP32 copy of y already written on b->pstream, or null (made here)
 tufrg_status batch_rhs_device(tufrg_batch* b, const double* y, double* dy, bool scaled,
-                              cudaStream_t st, bool wedge = false) {
+                              cudaStream_t st, bool wedge = false, const float* y32 = nullptr) {
   const MultiView& v = b->view;
   // the projections (states only) beside the loops (scales only)
   TUFRG_CUDA(cudaEventRecord(b->ev_fork, st));
   TUFRG_CUDA(cudaStreamWaitEvent(b->pstream, b->ev_fork, 0));
-  TUFRG_CHECK(launch_project_multi(v, b->precision, y, b->d_V, b->d_bt, b->d_fkey, b->pstream,
+  if (!y32) {
+    TUFRG_CHECK(launch_to_f32(y, b->d_y32, wedge ? v.wstate_elems : v.state_elems, b->pstream));
+    y32 = b->d_y32;
+  }
+  TUFRG_CHECK(launch_project_multi(v, b->precision, y32, b->d_V, b->d_bt, b->d_fkey, b->pstream,
                                    wedge));
   TUFRG_CUDA(cudaEventRecord(b->ev_join, b->pstream));
   TUFRG_CHECK(launch_loops_tc_rows_multi(v, st));  // row loops, gathered by the products
@@ -360,10 +370,10 @@ tufrg_status bstage(tufrg_batch* b, const double* y, double* out,
   TUFRG_CUDA(cudaEventRecord(b->ev_stage, st));
   TUFRG_CUDA(cudaStreamWaitEvent(b->pstream, b->ev_stage, 0));
   bcombo_kernel<<<f.n_chunks, kFlowThreads, 0, b->pstream>>>(y, out, cb, f.ctl, b->d_lam, f.seg,
-                                                             f.prefix, b->n, 0);
+                                                             f.prefix, b->n, 0, b->d_y32);
   bstage_lambda_kernel<<<grid_for(b->n), 128, 0, st>>>(f.ctl, cnode, b->d_lam, b->n);
   TUFRG_CUDA(cudaGetLastError());
-  return batch_rhs_device(b, out, k_out, true, st, f.wedge);
+  return batch_rhs_device(b, out, k_out, true, st, f.wedge, b->d_y32);
 }
 
 tufrg_status enqueue_battempt(tufrg_batch* b, cudaStream_t st) {
@@ -630,7 +640,7 @@ void batch_free(tufrg_batch* b) {
   cudaDeviceSynchronize();
   tufrg::free_batch_flow(b->flow);
   tufrg::view_free(b->view);
-  void* ptrs[] = {b->d_lam, b->d_skip, b->d_err, b->d_chi, b->d_V, b->d_bt, b->d_fkey};
+  void* ptrs[] = {b->d_lam, b->d_skip, b->d_err, b->d_chi, b->d_V, b->d_bt, b->d_fkey, b->d_y32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (tufrg_ctx* c : b->pts)
@@ -691,6 +701,8 @@ tufrg_status batch_setup(int32_t n, const tufrg_params* params, cudaStream_t st,
   if (cudaMalloc((void**)&b->d_chi, sizeof(double) * std::max<size_t>(v.chi_elems, 1)) !=
           cudaSuccess ||
       cudaMalloc((void**)&b->d_V, sizeof(double) * std::max<size_t>(v.state_elems, 1)) !=
+          cudaSuccess ||
+      cudaMalloc((void**)&b->d_y32, sizeof(float) * std::max<size_t>(v.state_elems, 1)) !=
           cudaSuccess ||
       cudaMalloc((void**)&b->d_bt, sizeof(double2) * std::max<size_t>(v.bt_elems, 1)) !=
           cudaSuccess ||

@@ -8,12 +8,12 @@
 //   basis are signed permutations, so this is a gather with signs; the
 //   parity-forbidden entries (not computed) are written as zeros, so every
 //   entry of chi is written.  One CTA per (point, row).
+#include <algorithm>
+
 #include "device_util.cuh"
 
 namespace tufrg {
 namespace {
-
-constexpr int kMaxNff = 32;
 
 __global__ void expand_rows_kernel(const PointDesc* __restrict__ pts,
                                    const int* __restrict__ prefix, int n,
@@ -23,7 +23,7 @@ __global__ void expand_rows_kernel(const PointDesc* __restrict__ pts,
   if (pd.skip && *pd.skip) return;
   const int row = blockIdx.x - prefix[p];
   const int nff = pd.nff, n2 = nff * nff, nrow = pd.nrow, npair = pd.npair;
-  __shared__ double X[2][kMaxNff * kMaxNff];
+  __shared__ double X[2][kMaxNf * kMaxNf];
   for (int e = threadIdx.x; e < 2 * n2; e += blockDim.x) X[e / n2][e % n2] = 0.0;
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * npair; e += blockDim.x) {
@@ -126,6 +126,19 @@ __global__ void wedge_expand_kernel(const PointDesc* __restrict__ pts,
   }
 }
 
+// Element-wise FP64 <-> FP32 copies (the FP32 state copy of the FP32
+// projections, FP32 couplings returned as FP64), on the integer pipe.
+__global__ void to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = d2f(x[i]);
+}
+__global__ void to_f64_kernel(const float* __restrict__ x, double* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = f2d(x[i]);
+}
+
 // Split-K combination of one (channel, pair) and 32 rows: partial sums laid
 // out as [split][2][P][R] (P pair stride, R row stride), FP64 result
 // scaled by -1/4 (pp) / +1/4 (ph) (and 1/Omega^2 for the tensor-core
@@ -141,16 +154,8 @@ __global__ void wedge_expand_kernel(const PointDesc* __restrict__ pts,
 // FP64.
 constexpr int kPhases = 8;  // 256 threads: the whole grid resident in one wave
 
-// (a.x + a.y) + b as a renormalised pair (TwoSum of the high parts, the low
-// parts and the rounding error added, then a Fast2Sum)
-__device__ __forceinline__ float2 pair_add(float2 a, float b) {
-  const float s = a.x + b;
-  const float bv = s - a.x;
-  const float e = ((a.x - (s - bv)) + (b - bv)) + a.y;
-  const float hi = s + e;
-  return make_float2(hi, e - (hi - s));
-}
-
+// (a.x + a.y) + (b.x + b.y) as a renormalised pair (TwoSum of the high parts,
+// the low parts and the rounding error added, then a Fast2Sum)
 __device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
   const float s = a.x + b.x;
   const float bv = s - a.x;
@@ -159,47 +164,32 @@ __device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
   return make_float2(hi, e - (hi - s));
 }
 
-template <class T>
-__device__ __forceinline__ void reduce_rows(const T* __restrict__ partial, int P, int R,
+// FP64 partials of one (channel, pair) and 32 rows, laid out as
+// [split][2][P][R] (P pair stride, R row stride), summed in FP64 and scaled
+// by -1/4 (pp) / +1/4 (ph) into rowres [2][nrow][npair]
+__device__ __forceinline__ void reduce_rows(const double* __restrict__ partial, int P, int R,
                                             int ksplit, int npair, int nrow, int row_end,
                                             int ch, int q, int row0,
                                             double* __restrict__ rowres, double factor) {
   const int lane = threadIdx.x & 31, phase = threadIdx.x >> 5;
   const int row = row0 + lane;
   const bool live = row < row_end;
-  const T* src = partial + ((size_t)ch * P + q) * R + row;
+  const double* src = partial + ((size_t)ch * P + q) * R + row;
   const size_t stride = (size_t)2 * P * R;
   const double scale = (ch == 0 ? -0.25 : 0.25) * factor;
-  if constexpr (sizeof(T) == 4) {
-    __shared__ float2 red[kPhases][33];
-    float2 s = make_float2(0.f, 0.f);
-    if (live) {
+  __shared__ double red[kPhases][33];
+  double s = 0.0;
+  if (live) {
 #pragma unroll 4
-      for (int sp = phase; sp < ksplit; sp += kPhases) s = pair_add(s, __ldg(src + sp * stride));
-    }
-    red[phase][lane] = s;
-    __syncthreads();
-    if (phase == 0 && live) {
-      float2 t = red[0][lane];
+    for (int sp = phase; sp < ksplit; sp += kPhases) s += src[sp * stride];
+  }
+  red[phase][lane] = s;
+  __syncthreads();
+  if (phase == 0 && live) {
+    double t = red[0][lane];
 #pragma unroll
-      for (int k = 1; k < kPhases; ++k) t = pair_add(t, red[k][lane]);
-      rowres[((size_t)ch * nrow + row) * npair + q] = ((double)t.x + (double)t.y) * scale;
-    }
-  } else {
-    __shared__ double red[kPhases][33];
-    double s = 0.0;
-    if (live) {
-#pragma unroll 4
-      for (int sp = phase; sp < ksplit; sp += kPhases) s += src[sp * stride];
-    }
-    red[phase][lane] = s;
-    __syncthreads();
-    if (phase == 0 && live) {
-      double t = red[0][lane];
-#pragma unroll
-      for (int k = 1; k < kPhases; ++k) t += red[k][lane];
-      rowres[((size_t)ch * nrow + row) * npair + q] = t * scale;
-    }
+    for (int k = 1; k < kPhases; ++k) t += red[k][lane];
+    rowres[((size_t)ch * nrow + row) * npair + q] = t * scale;
   }
 }
 
@@ -218,11 +208,15 @@ __host__ __device__ inline int tc_rows_groups(int row_lo, int row_hi) {
   return (row_hi - tc_rows_start(row_lo) + kTcRowsPerCta - 1) / kTcRowsPerCta;
 }
 
-__device__ __forceinline__ void pair_add4(float2 (&s)[4], float4 v) {
-  s[0] = pair_add(s[0], v.x);
-  s[1] = pair_add(s[1], v.y);
-  s[2] = pair_add(s[2], v.z);
-  s[3] = pair_add(s[3], v.w);
+// pair_add of two rows at once: hi = (hi of row 0, hi of row 1), lo the
+// same, b the rows' new terms; every lane takes the operations of pair_add
+// (same result, half the instructions)
+__device__ __forceinline__ void pair_add_x2(float2& hi, float2& lo, float2 b) {
+  const float2 s = add2(hi, b);
+  const float2 bv = sub2(s, hi);
+  const float2 e = add2(add2(sub2(hi, sub2(s, bv)), sub2(b, bv)), lo);
+  hi = add2(s, e);
+  lo = sub2(e, sub2(hi, s));
 }
 
 __global__ void __launch_bounds__(32 * kPhases)
@@ -241,7 +235,8 @@ __global__ void __launch_bounds__(32 * kPhases)
       partial + pd.off_partial + ((size_t)ch * pd.npad + q) * pd.nrow_pad + row);
   const size_t stride = (size_t)2 * pd.npad * pd.nrow_pad / 4;  // float4 per split
   const int ksplit = pd.ksplit;
-  float2 s[4] = {};
+  // rows (0, 1) and (2, 3) as paired sums: hi and lo parts
+  float2 h01 = make_float2(0.f, 0.f), l01 = h01, h23 = h01, l23 = h01;
   if (live) {
     for (int sp = phase; sp < ksplit; sp += 4 * kPhases) {
       float4 v[4];
@@ -251,12 +246,17 @@ __global__ void __launch_bounds__(32 * kPhases)
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (sp + u * kPhases < ksplit) pair_add4(s, v[u]);
+        if (sp + u * kPhases < ksplit) {
+          pair_add_x2(h01, l01, make_float2(v[u].x, v[u].y));
+          pair_add_x2(h23, l23, make_float2(v[u].z, v[u].w));
+        }
     }
   }
   __shared__ float2 red[kPhases][4][33];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) red[phase][j][lane] = s[j];
+  red[phase][0][lane] = make_float2(h01.x, l01.x);
+  red[phase][1][lane] = make_float2(h01.y, l01.y);
+  red[phase][2][lane] = make_float2(h23.x, l23.x);
+  red[phase][3][lane] = make_float2(h23.y, l23.y);
   __syncthreads();
   if (phase != 0 || !live) return;
   // the tensor-core weights carry a factor Omega^2
@@ -315,6 +315,27 @@ tufrg_status launch_covariance_check(const MultiView& v, const double* y,
   return TUFRG_OK;
 }
 
+namespace {
+int copy_ctas(size_t n) {
+  const size_t c = (n + 255) / 256;
+  return (int)std::min<size_t>(std::max<size_t>(c, 1), (size_t)sm_count() * 8);
+}
+}  // namespace
+
+tufrg_status launch_to_f32(const double* x, float* y, size_t n, cudaStream_t st) {
+  if (n == 0) return TUFRG_OK;
+  to_f32_kernel<<<copy_ctas(n), 256, 0, st>>>(x, y, n);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
+tufrg_status launch_to_f64(const float* x, double* y, size_t n, cudaStream_t st) {
+  if (n == 0) return TUFRG_OK;
+  to_f64_kernel<<<copy_ctas(n), 256, 0, st>>>(x, y, n);
+  TUFRG_CUDA(cudaGetLastError());
+  return TUFRG_OK;
+}
+
 tufrg_status launch_wedge_compress(const MultiView& v, const double* y, double* w,
                                    cudaStream_t st) {
   wedge_compress_kernel<<<v.total(kKindExpand), 128, 0, st>>>(v.d, v.dprefix(kKindExpand), v.n,
@@ -332,7 +353,7 @@ tufrg_status launch_wedge_expand(const MultiView& v, const double* w, double* y,
 }
 
 tufrg_status launch_expand_multi(const MultiView& v, double* chi, cudaStream_t st) {
-  if (v.nff_max > kMaxNff) return TUFRG_ERR_ARG;
+  if (v.nff_max > kMaxNf) return TUFRG_ERR_ARG;
   expand_rows_kernel<<<v.total(kKindExpand), 128, 0, st>>>(v.d, v.dprefix(kKindExpand), v.n,
                                                            v.d_rowres, chi);
   TUFRG_CUDA(cudaGetLastError());

@@ -20,6 +20,7 @@
 #include <new>
 #include <vector>
 
+#include "device_util.cuh"
 #include "flow_common.cuh"
 
 namespace tufrg {
@@ -35,10 +36,11 @@ __host__ __device__ inline int per_thread(size_t n) {
   return p < 1 ? 1 : (p > kPer ? kPer : (int)p);
 }
 
-// out = y + h * sum_j a_j k_j ; one thread also publishes Lambda for the RHS
+// out = y + h * sum_j a_j k_j (and, when out32 is given, its FP32 copy for
+// the FP32 projections); one thread also publishes Lambda for the RHS
 __global__ void combo_kernel(const double* __restrict__ y, double* __restrict__ out, Combo cb,
                              const FlowCtl* __restrict__ ctl, double* __restrict__ lam,
-                             size_t n, int set_lambda) {
+                             size_t n, int set_lambda, float* __restrict__ out32 = nullptr) {
   const double h = ctl->h;
   if (set_lambda && blockIdx.x == 0 && threadIdx.x == 0) {
     const double L = exp(ctl->s + cb.c * h);
@@ -51,7 +53,9 @@ __global__ void combo_kernel(const double* __restrict__ y, double* __restrict__ 
     const size_t i = ((size_t)blockIdx.x * per + u) * blockDim.x + threadIdx.x;
     if (u >= per || i >= n) break;
     const double acc = combo_sum(cb, i);
-    out[i] = y[i] + h * acc;
+    const double v = y[i] + h * acc;
+    out[i] = v;
+    if (out32) out32[i] = d2f(v);
   }
 }
 
@@ -264,10 +268,12 @@ tufrg_status stage(tufrg_ctx* c, const double* y, double* out,
   // the loop stream: the loops start without waiting for the combination
   TUFRG_CUDA(cudaEventRecord(c->ev_stage, st));
   TUFRG_CUDA(cudaStreamWaitEvent(c->pstream, c->ev_stage, 0));
-  combo_kernel<<<grid_for(n), 256, 0, c->pstream>>>(y, out, cb, f.ctl, c->d_lambda, n, 0);
+  // the FP32 projections' copy of the stage state, written by the combination
+  float* y32 = rhs_arith(c, c->loop_prec) == TUFRG_FP64 ? nullptr : c->d_y32;
+  combo_kernel<<<grid_for(n), 256, 0, c->pstream>>>(y, out, cb, f.ctl, c->d_lambda, n, 0, y32);
   stage_lambda_kernel<<<1, 1, 0, st>>>(f.ctl, cnode, c->d_lambda);
   TUFRG_CUDA(cudaGetLastError());
-  return rhs_device(c, c->loop_prec, out, k_out, true, st, f.wedge);
+  return rhs_device(c, c->loop_prec, out, k_out, true, st, f.wedge, y32);
 }
 
 // One DoPri5 attempt: stages 2..7, error norm, control, accept.

@@ -242,7 +242,8 @@ struct tufrg_ctx {
   double* d_lambda = nullptr;      // scalar scale used by the kernels
   double* d_partial = nullptr;     // [ksplit][2][mpad][nrow] split-K partial sums
   double* d_chi = nullptr;         // [2][nl][nff][nff]
-  double* d_V = nullptr;           // [3][nl][nff][nff]
+  double* d_V = nullptr;           // [3][nl][nff][nff] (FP32 couplings in its first half)
+  float* d_y32 = nullptr;          // FP32 copy of a state (mixed-precision contexts)
   double2* d_bt = nullptr;         // the state's DFT along y, then the overlap sums
                                    // H [positions Y][nff][nff] (bt_region)
   double2* d_fkey = nullptr;       // Fourier values of the keys, dense (fkey_elems)
@@ -326,8 +327,16 @@ tufrg_status launch_set_scalar(double* d, double value, cudaStream_t st);
 // wedge: y and dy in the wedge layout [3][nrow][nff][nff] of a point-group
 // covariant state (flows), projections and products at the rows'
 // representative l only
+// y32: an FP32 copy of y already on the way (made by the caller on c->pstream,
+// before the call), or null
 tufrg_status rhs_device(tufrg_ctx* c, int prec, const double* y, double* dy, bool scaled,
-                        cudaStream_t st, bool wedge = false);
+                        cudaStream_t st, bool wedge = false, const float* y32 = nullptr);
+// arithmetic of the projections and products for loops in precision prec:
+// FP64 for an FP64 context and for FP64 loops, else FP32
+int rhs_arith(const tufrg_ctx* c, int prec);
+// element-wise copies FP64 -> FP32 (rounded to nearest) and FP32 -> FP64
+tufrg_status launch_to_f32(const double* x, float* y, size_t n, cudaStream_t st);
+tufrg_status launch_to_f64(const float* x, double* y, size_t n, cudaStream_t st);
 
 // multi-point views (multi.cpp): descriptors of n contexts packed one after
 // the other; lam[i], skip[i] are per-point device pointers (skip may be null)
@@ -371,6 +380,8 @@ size_t fkey_elems(int nd, int nb);
 int contract_ctas(int nl, int nff, bool grouped);
 // the projections of a view take the grouped form from this form-factor count on
 constexpr int kGroupedNff = 21;
+// the largest form-factor count the kernels accept (complete shells up to 29)
+constexpr int kMaxNf = 32;
 // elements of a point's projection workspace: the state's DFT along y
 // [3][ncx][nd][nff*nff], later reused for the overlap sums [positions Y][nff][nff]
 size_t bt_region(int ncx, int nd, int nff, int ny_total);
@@ -378,13 +389,15 @@ size_t bt_region(int ncx, int nd, int nff, int ny_total);
 // rows: the state in the wedge layout (a point-group covariant state at the
 // representative l of each loop row), the projected couplings at the
 // representatives, in the wedge layout
-tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
+// y and out hold doubles for prec == TUFRG_FP64, else floats (FP32 arithmetic)
+tufrg_status launch_project_multi(const MultiView& v, int prec, const void* y, void* out,
                                   void* bt, void* fkey, cudaStream_t st, bool rows = false);
 // chi == nullptr: the loops of each l are gathered from the row loops
 // v.d_rowres (the orbit expansion fused into the products).  rows (with chi
 // == nullptr): couplings and dy in the wedge layout, the products at each
 // row's representative l only (a covariant state's right-hand side)
-tufrg_status launch_products_multi(const MultiView& v, int prec, const double* vin,
+// vin: the couplings, doubles for prec == TUFRG_FP64, else floats
+tufrg_status launch_products_multi(const MultiView& v, int prec, const void* vin,
                                    const double* chi, double* dy, bool scaled, cudaStream_t st,
                                    bool rows = false);
 // largest |y(g l) - R^g y(l) R^g^T| over every l a row serves (l the row's

@@ -33,7 +33,11 @@
 // launch costs more than the arithmetic it saves.
 // The arithmetic type is FP64 for an FP64 context (this step is then bound by
 // GB300's FP64 rate) and FP32 for the mixed-precision contexts, whose loops
-// run on the tensor cores; the state and the result are FP64 in both cases.
+// run on the tensor cores.  State and couplings are read and written in the
+// arithmetic type: the FP32 kernels take an FP32 copy of the FP64 state (made
+// by the flow's stage combination, or converted once per call) and write
+// FP32 couplings (no FP64 conversion in them: GB300 converts between FP64
+// and FP32 on its FP64 pipe, at a small fraction of the FP32 rate).
 #include "device_util.cuh"
 
 namespace tufrg {
@@ -57,6 +61,13 @@ __device__ __forceinline__ V cmul(V a, V b) {
 template <class V>
 __device__ __forceinline__ V cfma(V a, V b, V c) {
   return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+}
+// acc + q * b for a complex q and a real b (paired FP32: one instruction)
+__device__ __forceinline__ float2 cfma_real(float2 q, float b, float2 acc) {
+  return fma2(q, make_float2(b, b), acc);
+}
+__device__ __forceinline__ double2 cfma_real(double2 q, double b, double2 acc) {
+  return {fma(q.x, b, acc.x), fma(q.y, b, acc.y)};
 }
 template <class V>
 __device__ __forceinline__ V to_c(double2 d) {
@@ -108,12 +119,12 @@ constexpr int kNdPass = 9;
 template <class T, bool kWedge>
 __global__ void __launch_bounds__(kDft1Threads)
     bond_dft1_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
-                     const double* __restrict__ ybase, typename C2<T>::type* __restrict__ p1base) {
+                     const T* __restrict__ ybase, typename C2<T>::type* __restrict__ p1base) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
-  const int nff2 = pd.nff * pd.nff, nd = pd.nd, ncx = pd.ncx, ncy = pd.ncy;
+  const int nff = pd.nff, nff2 = nff * nff, nd = pd.nd, ncx = pd.ncx, ncy = pd.ncy;
   const int chunks = (nff2 + kDft1Threads - 1) / kDft1Threads;
   const int loc = blockIdx.x - prefix[p];
   const int chunk = loc % chunks, rest = loc / chunks, ix = rest % ncx, src = rest / ncx;
@@ -121,54 +132,66 @@ __global__ void __launch_bounds__(kDft1Threads)
   V* ph = reinterpret_cast<V*>(sm2);  // [ncy][nd] e^{i l_y Y}
   for (int e = threadIdx.x; e < ncy * nd; e += blockDim.x)
     ph[e] = phase_at(pd, (ncx + e / nd) * nd + e % nd, T());
-  // wedge: per iy the element offset of the serving row and its g; the
-  // signed permutations of the 8 elements
-  int* wrow = reinterpret_cast<int*>(ph + ncy * nd);  // [ncy]
-  int* wg = wrow + ncy;                               // [ncy]
-  int* wp = wg + ncy;                                 // [8][nff]
-  int* ws = wp + 8 * pd.nff;                          // [8][nff]
+  // wedge: per iy the element offset of the serving row and its g; per g
+  // and thread the signed offset + 1 of the thread's entry in the row
+  int2* wr = reinterpret_cast<int2*>(ph + ncy * nd);  // [ncy]
+  int* toff = reinterpret_cast<int*>(wr + ncy);       // [8][kDft1Threads]
+  const int ab = chunk * kDft1Threads + threadIdx.x;
   if (kWedge) {
     for (int iy = threadIdx.x; iy < ncy; iy += blockDim.x) {
       const int2 rg = pd.lrow[ix * ncy + iy];
-      wrow[iy] = (src * pd.nrow + rg.x) * nff2;
-      wg[iy] = rg.y * pd.nff;
+      wr[iy] = make_int2((src * pd.nrow + rg.x) * nff2, rg.y);
     }
-    for (int e = threadIdx.x; e < 8 * pd.nff; e += blockDim.x) {
-      wp[e] = pd.symperm[e];
-      ws[e] = pd.symsign[e];
+    if (ab < nff2) {  // read back by this thread only
+      const int a = ab / nff, b = ab - a * nff;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const int o = __ldg(pd.symperm + g * nff + a) * nff + __ldg(pd.symperm + g * nff + b) + 1;
+        const int sg = __ldg(pd.symsign + g * nff + a) * __ldg(pd.symsign + g * nff + b);
+        toff[g * kDft1Threads + threadIdx.x] = sg > 0 ? o : -o;
+      }
     }
   }
   __syncthreads();
-  const int ab = chunk * kDft1Threads + threadIdx.x;
   if (ab >= nff2) return;
-  const int a = ab / pd.nff, b = ab - a * pd.nff;
-  const double* B = kWedge ? ybase + pd.off_wstate
+  const T* B = kWedge ? ybase + pd.off_wstate
                            : ybase + pd.off_state +
                                  ((size_t)src * pd.nl + (size_t)ix * ncy) * nff2 + ab;
   V* out = p1base + pd.off_bt + ((size_t)(src * ncx + ix) * nd) * nff2 + ab;
   // positions in passes of kNdPass (one pass for the bases of complete shells
-  // on grids that resolve them; small grids alias more bond sums to more X)
+  // on grids that resolve them; small grids alias more bond sums to more X);
+  // the state in batches of kIyBatch rows, all loads of a batch in flight
+  // before its arithmetic
+  constexpr int kIyBatch = 16;
   for (int d0 = 0; d0 < nd; d0 += kNdPass) {
     V acc[kNdPass];
 #pragma unroll
     for (int d = 0; d < kNdPass; ++d) acc[d] = {0, 0};
-#pragma unroll 4
-    for (int iy = 0; iy < ncy; ++iy) {
-      T bv;
-      if (kWedge) {
-        const int g = wg[iy];
-        const double w = __ldg(B + wrow[iy] + wp[g + a] * pd.nff + wp[g + b]);
-        bv = (T)(ws[g + a] * ws[g + b] > 0 ? w : -w);
-      } else {
-        bv = (T)__ldg(B + (size_t)iy * nff2);
-      }
-      const V* q = ph + iy * nd + d0;
+    for (int iy0 = 0; iy0 < ncy; iy0 += kIyBatch) {
+      T bv[kIyBatch];
 #pragma unroll
-      for (int d = 0; d < kNdPass; ++d)
-        if (d0 + d < nd) {
-          acc[d].x = fma(q[d].x, bv, acc[d].x);
-          acc[d].y = fma(q[d].y, bv, acc[d].y);
+      for (int u = 0; u < kIyBatch; ++u) {
+        const int iy = iy0 + u;
+        bv[u] = 0;
+        if (iy < ncy) {
+          if (kWedge) {
+            const int2 rg = wr[iy];
+            const int o = toff[rg.y * kDft1Threads + threadIdx.x];
+            const T w = __ldg(B + rg.x + abs(o) - 1);
+            bv[u] = o > 0 ? w : -w;
+          } else {
+            bv[u] = __ldg(B + (size_t)iy * nff2);
+          }
         }
+      }
+#pragma unroll
+      for (int u = 0; u < kIyBatch; ++u) {
+        if (iy0 + u >= ncy) break;
+        const V* q = ph + (iy0 + u) * nd + d0;
+#pragma unroll
+        for (int d = 0; d < kNdPass; ++d)
+          if (d0 + d < nd) acc[d] = cfma_real(q[d], bv[u], acc[d]);
+      }
     }
 #pragma unroll
     for (int d = 0; d < kNdPass; ++d)
@@ -197,14 +220,36 @@ __global__ void __launch_bounds__(256)
   for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
   for (int e = threadIdx.x; e < ncx; e += blockDim.x) phx[e] = phase_at(pd, e * nd + dx, T());
   __syncthreads();
-  const V* P1 = p1base + pd.off_bt + (size_t)dy * nff2;
   const size_t xstride = (size_t)nd * nff2;
-  for (int ab = threadIdx.x; ab < nff2; ab += blockDim.x) {
-    V acc = {0, 0};
-    const V* q = P1 + (size_t)src * ncx * xstride + ab;
-#pragma unroll 4
-    for (int ix = 0; ix < ncx; ++ix) acc = cfma(phx[ix], q[ix * xstride], acc);
-    Bh[ab] = acc;
+  const V* P1 = p1base + pd.off_bt + (size_t)dy * nff2 + (size_t)src * ncx * xstride;
+  // the entries ab = threadIdx.x + r * 256 of this thread, in batches of kXB
+  // positions ix with all kR * kXB loads in flight before the arithmetic
+  {
+    constexpr int kR = (kMaxNf * kMaxNf + 255) / 256;
+    constexpr int kXB = sizeof(T) == 4 ? 8 : 4;
+    V acc[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) acc[r] = {0, 0};
+    for (int ix0 = 0; ix0 < ncx; ix0 += kXB) {
+      V q[kR][kXB];
+#pragma unroll
+      for (int r = 0; r < kR; ++r)
+#pragma unroll
+        for (int u = 0; u < kXB; ++u) {
+          const int ab = threadIdx.x + 256 * r, ix = ix0 + u;
+          q[r][u] = ab < nff2 && ix < ncx ? P1[(size_t)ix * xstride + ab] : V{0, 0};
+        }
+#pragma unroll
+      for (int u = 0; u < kXB; ++u) {
+        if (ix0 + u >= ncx) break;
+        const V e = phx[ix0 + u];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) acc[r] = cfma(e, q[r][u], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+      if (threadIdx.x + 256 * r < nff2) Bh[threadIdx.x + 256 * r] = acc[r];
   }
   __syncthreads();
   // tmp[a][b4] = sum_b Bh[a][b] c_b(b4)
@@ -242,8 +287,8 @@ constexpr int kTermBatch = 8;
 template <class T, int NF>
 __global__ void __launch_bounds__(256)
     contract_terms_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
-                    const double* __restrict__ ybase,
-                    const typename C2<T>::type* __restrict__ fkbase, double* __restrict__ vbase,
+                    const T* __restrict__ ybase,
+                    const typename C2<T>::type* __restrict__ fkbase, T* __restrict__ vbase,
                     int rows) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
@@ -269,13 +314,13 @@ __global__ void __launch_bounds__(256)
   V* qx = cs + nff * nb;                   // [kTermsL][nd]
   V* qy = qx + kTermsL * nd;            // [kTermsL][nd]
   const size_t n2 = (size_t)nff * nff;
-  const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
-  const double U = pd.U;
+  const T own_sign = t == 0 ? -1 : 1;  // V^P = V0 - P + ...; V^C = V0 + C + ...
+  const T U = (T)pd.U;
   if (!pd.feedback) {
     for (int e = threadIdx.x; e < nlb * (int)n2; e += blockDim.x) {
       const int j = e / (int)n2, r = e % (int)n2;
       const size_t o = slot_offset(pd, rows, t, q0 + j, sl[j], (int)n2) + r;
-      vbase[o] = (r == 0 ? U : 0.0) + own_sign * ybase[o];
+      vbase[o] = (r == 0 ? U : T(0)) + own_sign * ybase[o];
     }
     return;
   }
@@ -346,10 +391,10 @@ __global__ void __launch_bounds__(256)
   for (int m = r0; m < nff; m += rstep) {
     if (n >= nff) continue;
     const int mn = m * nff + n;
-    double yv[kTermsL];
+    T yv[kTermsL];
 #pragma unroll
     for (int jj = 0; jj < kTermsL; ++jj)
-      yv[jj] = jj < nlb ? ybase[slot_offset(pd, rows, t, q0 + jj, sl[jj], n2) + mn] : 0.0;
+      yv[jj] = jj < nlb ? ybase[slot_offset(pd, rows, t, q0 + jj, sl[jj], n2) + mn] : T(0);
     T acc[kTermsL];
 #pragma unroll
     for (int jj = 0; jj < kTermsL; ++jj) acc[jj] = 0;
@@ -365,7 +410,7 @@ __global__ void __launch_bounds__(256)
     for (int jj = 0; jj < kTermsL; ++jj)
       if (jj < nlb)
         vbase[slot_offset(pd, rows, t, q0 + jj, sl[jj], n2) + mn] =
-            (mn == 0 ? U : 0.0) + own_sign * yv[jj] + (double)acc[jj];
+            (mn == 0 ? U : T(0)) + own_sign * yv[jj] + acc[jj];
   }
 }
 
@@ -454,8 +499,8 @@ __host__ __device__ inline int contract_ctiles(int nout, int nff) {
 template <class T, int NF>
 __global__ void __launch_bounds__(kCThreads)
     contract_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
-                    const double* __restrict__ ybase,
-                    const typename C2<T>::type* __restrict__ hbase, double* __restrict__ vbase,
+                    const T* __restrict__ ybase,
+                    const typename C2<T>::type* __restrict__ hbase, T* __restrict__ vbase,
                     int rows) {
   using V = typename C2<T>::type;
   constexpr int kCY = kCYBytes / (int)sizeof(V);
@@ -469,16 +514,18 @@ __global__ void __launch_bounds__(kCThreads)
   const int t = loc / tiles, r = loc % tiles;
   const int q0 = (r / mtiles) * kCL, mn0 = (r % mtiles) * kCM;
   const int nlb = min(kCL, nout - q0);  // slots of this CTA
-  __shared__ int sl[kCL];               // l of each slot (the last one repeated)
-  __shared__ V Es[kCY][kCL];            // e^{i l.Y} of a pass
-  __shared__ V Hs[kCY][kCM];            // H of a pass
+  __shared__ int sl[kCL];  // l of each slot (the last one repeated)
+  // e^{i l.Y} of a pass: FP32 as two planes per position (Re, then -Im) for
+  // the paired arithmetic; FP64 as complex values
+  __shared__ __align__(16) V Es[kCY][kCL];
+  __shared__ __align__(16) V Hs[kCY][kCM];  // H of a pass
   if (threadIdx.x < kCL) {
     const int q = q0 + min((int)threadIdx.x, nlb - 1);
     sl[threadIdx.x] = rows ? pd.rowimg[pd.rowimg_ptr[q]].x : q;
   }
   __syncthreads();
-  const double own_sign = t == 0 ? -1.0 : 1.0;  // V^P = V0 - P + ...; V^C = V0 + C + ...
-  const double U = pd.U;
+  const T own_sign = t == 0 ? -1 : 1;  // V^P = V0 - P + ...; V^C = V0 + C + ...
+  const T U = (T)pd.U;
   const int c = threadIdx.x % kCM, j0 = (threadIdx.x / kCM) * kCR;  // entry, first slot
   const int mn = mn0 + c;
   T acc[kCR];
@@ -487,25 +534,83 @@ __global__ void __launch_bounds__(kCThreads)
   if (pd.feedback) {
     const int y0 = pd.gy_off[t], ny = pd.gy_off[t + 1] - y0;
     const V* H = hbase + pd.off_bt + (size_t)y0 * n2p;
-    for (int c0 = 0; c0 < ny; c0 += kCY) {
+    // a pass's operands are loaded into registers during the previous pass's
+    // arithmetic, then stored to shared memory
+    constexpr int kHPer = kCY * kCM / kCThreads, kEPer = (kCY * kCL + kCThreads - 1) / kCThreads;
+    V hreg[kHPer], ereg[kEPer];
+    auto fetch = [&](int c0) {
       const int cn = min(kCY, ny - c0);
-      __syncthreads();  // the previous pass is consumed
-      for (int e = threadIdx.x; e < kCY * kCM; e += kCThreads) {
-        const int yi = e / kCM, cc = e % kCM;
-        Hs[yi][cc] = yi < cn && mn0 + cc < n2 ? H[(size_t)(c0 + yi) * n2p + mn0 + cc] : V{0, 0};
+#pragma unroll
+      for (int u = 0; u < kHPer; ++u) {
+        const int e = threadIdx.x + u * kCThreads, yi = e / kCM, cc = e % kCM;
+        hreg[u] = yi < cn && mn0 + cc < n2 ? H[(size_t)(c0 + yi) * n2p + mn0 + cc] : V{0, 0};
       }
-      for (int e = threadIdx.x; e < kCY * kCL; e += kCThreads) {
-        const int yi = e / kCL, j = e % kCL;
-        Es[yi][j] = yi < cn ? yphase_at(pd, (size_t)(y0 + c0 + yi) * nl + sl[j], T()) : V{0, 0};
+#pragma unroll
+      for (int u = 0; u < kEPer; ++u) {
+        const int e = threadIdx.x + u * kCThreads, yi = e / kCL, j = e % kCL;
+        ereg[u] = e < kCY * kCL && yi < cn
+                      ? yphase_at(pd, (size_t)(y0 + c0 + yi) * nl + sl[j], T())
+                      : V{0, 0};
+      }
+    };
+    if (ny > 0) fetch(0);
+    for (int c0 = 0; c0 < ny; c0 += kCY) {
+      __syncthreads();  // the previous pass is consumed
+#pragma unroll
+      for (int u = 0; u < kHPer; ++u) {
+        const int e = threadIdx.x + u * kCThreads;
+        Hs[e / kCM][e % kCM] = hreg[u];
+      }
+#pragma unroll
+      for (int u = 0; u < kEPer; ++u) {
+        const int e = threadIdx.x + u * kCThreads, yi = e / kCL, j = e % kCL;
+        if (e < kCY * kCL) {
+          if constexpr (sizeof(T) == 4) {
+            float* row = reinterpret_cast<float*>(&Es[yi][0]);
+            row[j] = ereg[u].x;
+            row[kCL + j] = -ereg[u].y;
+          } else {
+            Es[yi][j] = ereg[u];
+          }
+        }
       }
       __syncthreads();
-#pragma unroll 4
-      for (int yi = 0; yi < kCY; ++yi) {
-        const V h = Hs[yi][c];
+      if (c0 + kCY < ny) fetch(c0 + kCY);
+      if constexpr (sizeof(T) == 4) {
+        // slots in pairs: acc(j, j + 1) += (-Im e) Im h, then += (Re e) Re h
+        // (each lane takes the two roundings of the scalar form)
+        float2 a2[kCR / 2];
 #pragma unroll
-        for (int j = 0; j < kCR; ++j) {
-          const V e = Es[yi][j0 + j];
-          acc[j] = fma(e.x, h.x, fma(-e.y, h.y, acc[j]));  // real part of e * h
+        for (int j = 0; j < kCR / 2; ++j) a2[j] = make_float2(acc[2 * j], acc[2 * j + 1]);
+#pragma unroll 4
+        for (int yi = 0; yi < kCY; ++yi) {
+          const V h = Hs[yi][c];
+          const float2 hx = make_float2(h.x, h.x), hy = make_float2(h.y, h.y);
+          const float* row = reinterpret_cast<const float*>(&Es[yi][0]);
+#pragma unroll
+          for (int j = 0; j < kCR; j += 4) {
+            const float4 ex = *reinterpret_cast<const float4*>(row + j0 + j);
+            const float4 ey = *reinterpret_cast<const float4*>(row + kCL + j0 + j);
+            a2[j / 2] = fma2(make_float2(ey.x, ey.y), hy, a2[j / 2]);
+            a2[j / 2] = fma2(make_float2(ex.x, ex.y), hx, a2[j / 2]);
+            a2[j / 2 + 1] = fma2(make_float2(ey.z, ey.w), hy, a2[j / 2 + 1]);
+            a2[j / 2 + 1] = fma2(make_float2(ex.z, ex.w), hx, a2[j / 2 + 1]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kCR / 2; ++j) {
+          acc[2 * j] = a2[j].x;
+          acc[2 * j + 1] = a2[j].y;
+        }
+      } else {
+#pragma unroll 4
+        for (int yi = 0; yi < kCY; ++yi) {
+          const V h = Hs[yi][c];
+#pragma unroll
+          for (int j = 0; j < kCR; ++j) {
+            const V e = Es[yi][j0 + j];
+            acc[j] = fma(e.x, h.x, fma(-e.y, h.y, acc[j]));  // real part of e * h
+          }
         }
       }
     }
@@ -516,7 +621,7 @@ __global__ void __launch_bounds__(kCThreads)
   for (int j = 0; j < kCR; ++j)
     if (j0 + j < nlb) {
       const size_t o = slot_offset(pd, rows, t, q0 + j0 + j, sl[j0 + j], n2) + mn;
-      vbase[o] = (mn == 0 ? U : 0.0) + own_sign * ybase[o] + (double)(acc[j] * inv_nl);
+      vbase[o] = (mn == 0 ? U : T(0)) + own_sign * ybase[o] + acc[j] * inv_nl;
     }
 }
 
@@ -524,8 +629,8 @@ template <class T>
 size_t dft1_smem(const MultiView& v) {
   size_t m = 1;
   for (const PointDesc& d : v.h)
-    m = std::max(m, sizeof(typename C2<T>::type) * d.ncy * d.nd +
-                        sizeof(int) * (2 * (size_t)d.ncy + 16 * (size_t)d.nff));
+    m = std::max(m, sizeof(typename C2<T>::type) * d.ncy * d.nd + sizeof(int2) * d.ncy +
+                        sizeof(int) * 8 * kDft1Threads);
   return m;
 }
 template <class T>
@@ -590,7 +695,7 @@ tufrg_status prepare_typed(const MultiView& v) {
 }
 
 template <class T>
-tufrg_status project_typed(const MultiView& v, const double* y, double* out, void* btv,
+tufrg_status project_typed(const MultiView& v, const T* y, T* out, void* btv,
                            void* fkv, cudaStream_t st, bool rows) {
   const int kind = rows ? kKindContractRows : kKindContract;
   using V = typename C2<T>::type;
@@ -655,14 +760,18 @@ size_t bt_region(int ncx, int nd, int nff, int ny_total) {
 }
 
 tufrg_status prepare_project_multi(const MultiView& v) {
+  if (v.nff_max > kMaxNf) return TUFRG_ERR_ARG;
   TUFRG_CHECK(prepare_typed<double>(v));
   return prepare_typed<float>(v);
 }
 
-tufrg_status launch_project_multi(const MultiView& v, int prec, const double* y, double* out,
+tufrg_status launch_project_multi(const MultiView& v, int prec, const void* y, void* out,
                                   void* bt, void* fkey, cudaStream_t st, bool rows) {
-  return prec == TUFRG_FP64 ? project_typed<double>(v, y, out, bt, fkey, st, rows)
-                            : project_typed<float>(v, y, out, bt, fkey, st, rows);
+  return prec == TUFRG_FP64
+             ? project_typed<double>(v, static_cast<const double*>(y), static_cast<double*>(out),
+                                     bt, fkey, st, rows)
+             : project_typed<float>(v, static_cast<const float*>(y), static_cast<float*>(out), bt,
+                                    fkey, st, rows);
 }
 
 }  // namespace tufrg

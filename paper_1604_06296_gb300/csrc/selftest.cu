@@ -1,4 +1,5 @@
-// Self-test of the bounded device waits (no counterpart in the paper).
+// Self-tests (no counterpart in the paper): the bounded device waits and the
+// library's FP64 <-> FP32 conversions.
 //
 // The tensor-core kernels wait on shared-memory mbarriers with a time limit;
 // a wait that runs out sets the context's error word (reported by
@@ -25,6 +26,14 @@ __global__ void wait_selftest_kernel(int* __restrict__ err, unsigned long long l
 
 }  // namespace
 }  // namespace tufrg
+
+extern "C" tufrg_status tufrg_selftest_convert(const double* x_dev, float* y32_dev,
+                                               double* back_dev, int64_t n, void* stream) {
+  if (!x_dev || !y32_dev || !back_dev || n < 0) return TUFRG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  TUFRG_CHECK(tufrg::launch_to_f32(x_dev, y32_dev, (size_t)n, st));
+  return tufrg::launch_to_f64(y32_dev, back_dev, (size_t)n, st);
+}
 
 extern "C" tufrg_status tufrg_selftest_wait(tufrg_ctx* c, int32_t wait_us, void* stream) {
   if (!c || !c->d_err || wait_us < 1 || wait_us > 100000) return TUFRG_ERR_ARG;

@@ -487,6 +487,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CHECK(alloc(&c->d_partial, (size_t)c->ksplit * 2 * c->mpad * c->nrow));
     TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
     TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
+    if (c->p.precision != TUFRG_FP64) TUFRG_CHECK(alloc(&c->d_y32, (size_t)3 * c->nl * nff * nff));
     TUFRG_CHECK(alloc(&c->d_bt, bt_region(c->ncx, 2 * P.dmax + 1, nff, P.gy_off[3])));
     TUFRG_CHECK(alloc(&c->d_fkey, fkey_elems(2 * P.dmax + 1, nb)));
     // the loop kernels write only the parity-allowed pairs
@@ -585,7 +586,7 @@ void free_device(tufrg_ctx* c) {
   free_flow(c);
   view_free(c->view);
   void* own[] = {c->d_ext,     c->d_xiext, c->d_err, c->d_tab, c->d_lambda, c->d_partial,
-                 c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey};
+                 c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey, c->d_y32};
   for (void* p : own)
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {
