@@ -878,6 +878,89 @@ def flow_ladder(torch, tufrg, precision, name="cfg2"):
     return info
 
 
+ATENSOR_CASES = [  # (label, shells, coarse nc, fine nf, precision)
+    ("coarse 8x8, Nff 5, fine 96x96, FP64", 1, 8, 96, "fp64"),
+    ("coarse 8x8, Nff 5, fine 96x96, BF16x3 context (FP32 projections)", 1, 8, 96, "bf16x3"),
+    ("coarse 16x16, Nff 9, fine 192x192, BF16x3 context (FP32 projections)", 2, 16, 192,
+     "bf16x3"),
+]
+
+
+def run_atensor(args, rank, world, local):
+    """Step i from the precomputed projection tensors A^{B,B'} (App. C,
+    Sec. 2.5) against the on-the-fly projections, per case: the tensors'
+    bytes and build time, both paths' time per call (CUDA events, L2 flushed
+    before each call), the products with the tensors as an HBM-bound read
+    (their bytes / time against the measured copy bandwidth), and the
+    largest difference between the two paths.  value: on-the-fly time over
+    tensor time at the first case (above 1: the stored tensors are faster,
+    as the paper found for small bases)."""
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def timed(fn, n):
+        ms = []
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    cases = []
+    for label, shells, nc, nf, prec in ATENSOR_CASES:
+        s = tufrg.Solver(1.0, -0.25, -1.0, 3.0, W.bonds_for_shells(shells), nc, nf,
+                         precision=prec)
+        nbytes = s.atensor_bytes()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.atensor_build()
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        y = torch.from_numpy(W.random_state(5, s.nl, s.nff, 0.3)).cuda()
+        va, vf = s.empty(3), s.empty(3)
+        s.project_atensor(y, out=va)
+        s.project(y, out=vf)
+        torch.cuda.synchronize()
+        diff = float((va - vf).abs().max() / vf.abs().max())
+        n = max(5, args.steps)
+        t_at = timed(lambda: s.project_atensor(y, out=va), n)
+        t_fly = timed(lambda: s.project(y, out=vf), n)
+        cols = s.nl * s.nff * s.nff
+        elem = 8 if prec == "fp64" else 4
+        read = 3 * cols * cols * elem
+        cases.append({"case": label, "tensor_bytes": nbytes, "build_s": build_s,
+                      "atensor_us": t_at * 1e3, "on_the_fly_us": t_fly * 1e3,
+                      "speedup_of_tensors": t_fly / t_at, "max_rel_diff": diff,
+                      "tensor_read_gbs": read / (t_at * 1e-3) / 1e9,
+                      "tensor_read_frac_of_hbm": read / (t_at * 1e-3) / 1e9 / hbm})
+        s.close()
+    first = cases[0]
+    big = max(cases, key=lambda c: c["tensor_bytes"])
+    out = {"metric": "step i: on-the-fly projections vs precomputed tensors (time ratio)",
+           "value": first["speedup_of_tensors"], "unit": "x", "n_gpus": 1,
+           "steps": max(5, args.steps), "warmup": 1, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 / f32", "data": "synthetic",
+           "config": {"workload": "projection tensors (App. C)",
+                      "l2": "flushed before every timed call (512 MB write)"},
+           "roofline": {"bound": "hbm", "kernel": "atensor_project_kernel (" + big["case"] + ")",
+                        "achieved": big["tensor_read_gbs"], "peak": hbm, "unit": "GB/s",
+                        "frac": big["tensor_read_frac_of_hbm"], "traffic": None,
+                        "peak_source": peak_src + " (of measured)"},
+           "cases": cases}
+    print(json.dumps(out))
+    return 0
+
+
 def run_point(args, rank, world, local):
     """One phase-diagram point per rank (the production or the large point)."""
     import torch
@@ -1087,12 +1170,13 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other precisions on the same point")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=["cfg5", "cfg2", "cfg5-batch", "scan", "learned"],
+                    choices=["cfg5", "cfg2", "cfg5-batch", "scan", "learned", "atensor"],
                     help="cfg5: large point (coarse 48x48, Nff 25, fine 960x960; default); "
                          "cfg2: production point (coarse 24x24, Nff 13, fine 480x480); "
                          "cfg5-batch: 16 (t', mu) points on the large grids advanced "
                          "together; scan: batched phase-diagram scan; learned: loop "
-                         "surrogate trained and used in flows")
+                         "surrogate trained and used in flows; atensor: projections from "
+                         "the precomputed tensors of App. C against the on-the-fly path")
     ap.add_argument("--shard", action="store_true",
                     help="one point with its loop rows split over the ranks (strong scaling); "
                          "a step is one RHS evaluation")
@@ -1115,6 +1199,8 @@ def main():
         return run_large_batch(args, rank, world, local)
     if args.workload == "learned":
         return run_learned(args, rank, world, local)
+    if args.workload == "atensor":
+        return run_atensor(args, rank, world, local)
     return run_point(args, rank, world, local)
 
 

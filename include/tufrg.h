@@ -167,6 +167,28 @@ tufrg_status tufrg_loops(tufrg_ctx* ctx, double lambda, double* chi_dot_dev,
 tufrg_status tufrg_project(tufrg_ctx* ctx, const double* y_dev, double* v_dev,
                            void* cuda_stream);
 
+/* Step i from precomputed projection tensors (App. C; Sec. 2.5: the
+ * scale-independent parts of the projections computed once and reused at
+ * every scale).  Every cross projection is a linear map of the source
+ * channel's propagator, B[Phi^B']_mn(l) = sum_{q,m',n'} A^{B,B'}_{mn,m'n'}(q, l)
+ * B'_m'n'(q); three of the six tensors are stored, (P,C), (C,P), (D,C), the
+ * others follow from the pair relations of App. C.  The tensors hold
+ * 3 (Nl Nff^2)^2 numbers in the context's arithmetic type (FP64, or FP32 for
+ * the mixed-precision contexts): bases of up to 9 form factors only.
+ *
+ * tufrg_atensor_bytes: device bytes the tensors take (host computation);
+ *   TUFRG_ERR_ARG for more than 9 form factors.
+ * tufrg_atensor_build: allocates (once) and computes the tensors from the
+ *   projection terms, enqueued on cuda_stream; TUFRG_ERR_ARG if they would
+ *   exceed 48 GiB, TUFRG_ERR_OOM if the device has no room.
+ * tufrg_project_atensor: as tufrg_project (same layouts and result up to
+ *   rounding), V = V0 + own + A y; TUFRG_ERR_STATE before
+ *   tufrg_atensor_build.  The tensors are read once per call (HBM bound). */
+tufrg_status tufrg_atensor_bytes(const tufrg_ctx* ctx, int64_t* bytes);
+tufrg_status tufrg_atensor_build(tufrg_ctx* ctx, void* cuda_stream);
+tufrg_status tufrg_project_atensor(tufrg_ctx* ctx, const double* y_dev, double* v_dev,
+                                   void* cuda_stream);
+
 /* Step iii, Eqs. (matmul-P/C/D), per l:
  *   dP = V^P chi^pp V^P, dC = -V^C chi^ph V^C,
  *   dD = 2 V^D chi^ph V^D - V^C chi^ph V^D - V^D chi^ph V^C.

@@ -78,6 +78,19 @@ class Solver:
         tufrg_project(self.ctx, self._check(y, 3), self._check(out, 3), _stream())
         return out
 
+    def atensor_bytes(self):
+        """Device bytes of the precomputed projection tensors (App. C)."""
+        return _abi.tufrg_atensor_bytes(self.ctx)
+
+    def atensor_build(self):
+        _abi.tufrg_atensor_build(self.ctx, _stream())
+
+    def project_atensor(self, y, out=None):
+        """Step i from the precomputed tensors (after atensor_build)."""
+        out = self.empty(3) if out is None else out
+        _abi.tufrg_project_atensor(self.ctx, self._check(y, 3), self._check(out, 3), _stream())
+        return out
+
     def products(self, v, chi, out=None):
         out = self.empty(3) if out is None else out
         tufrg_products(self.ctx, self._check(v, 3), self._check(chi, 2), self._check(out, 3),

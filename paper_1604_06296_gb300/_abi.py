@@ -96,6 +96,9 @@ SIGNATURES = {
     "tufrg_check": ([c_void_p, c_void_p], c_int32),
     "tufrg_selftest_wait": ([c_void_p, c_int32, c_void_p], c_int32),
     "tufrg_selftest_convert": ([c_void_p, c_void_p, c_void_p, c_int64, c_void_p], c_int32),
+    "tufrg_atensor_bytes": ([c_void_p, POINTER(c_int64)], c_int32),
+    "tufrg_atensor_build": ([c_void_p, c_void_p], c_int32),
+    "tufrg_project_atensor": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "tufrg_autotune": ([c_void_p, c_double, POINTER(tufrg_tune_report), c_void_p], c_int32),
     "tufrg_batch_setup": ([c_int32, POINTER(tufrg_params), c_void_p, POINTER(c_void_p)],
                           c_int32),
@@ -284,6 +287,21 @@ def tufrg_selftest_convert(x_ptr: int, y32_ptr: int, back_ptr: int, n: int,
                            stream: int = 0) -> None:
     _check(lib().tufrg_selftest_convert(_dptr(x_ptr), _dptr(y32_ptr), _dptr(back_ptr), int(n),
                                         _dptr(stream)), "tufrg_selftest_convert")
+
+
+def tufrg_atensor_bytes(ctx) -> int:
+    b = c_int64()
+    _check(lib().tufrg_atensor_bytes(ctx, byref(b)), "tufrg_atensor_bytes")
+    return b.value
+
+
+def tufrg_atensor_build(ctx, stream: int = 0) -> None:
+    _check(lib().tufrg_atensor_build(ctx, _dptr(stream)), "tufrg_atensor_build")
+
+
+def tufrg_project_atensor(ctx, y_ptr: int, v_ptr: int, stream: int = 0) -> None:
+    _check(lib().tufrg_project_atensor(ctx, _dptr(y_ptr), _dptr(v_ptr), _dptr(stream)),
+           "tufrg_project_atensor")
 
 
 def tufrg_status_string(status: int) -> str:

@@ -221,6 +221,25 @@ tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi
                                       st);
 }
 
+tufrg_status tufrg_atensor_bytes(const tufrg_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return TUFRG_ERR_ARG;
+  size_t b = 0;
+  const tufrg_status s = tufrg::atensor_bytes(c, &b);
+  *bytes = (int64_t)b;
+  return s;
+}
+
+tufrg_status tufrg_atensor_build(tufrg_ctx* c, void* stream) {
+  if (!c || !c->d_V) return TUFRG_ERR_ARG;
+  return tufrg::atensor_build(c, (cudaStream_t)stream);
+}
+
+tufrg_status tufrg_project_atensor(tufrg_ctx* c, const double* y_dev, double* v_dev,
+                                   void* stream) {
+  if (!c || !y_dev || !v_dev || y_dev == v_dev) return TUFRG_ERR_ARG;
+  return tufrg::atensor_project(c, y_dev, v_dev, (cudaStream_t)stream);
+}
+
 namespace {
 
 // The right-hand side as a graph on the context's stream: captured for the

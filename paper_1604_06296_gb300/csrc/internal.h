@@ -221,7 +221,13 @@ struct tufrg_ctx {
   int* d_row_ptr = nullptr;        // term form: [3][nb*nb+1]
   int4* d_terms = nullptr;         //   [total terms] (key, dx, dy, sign)
   int term_off[3] = {0, 0, 0};
+  int n_terms = 0;                 //   all targets
   int4* d_gslot = nullptr;         // grouped form: ProjTables::gslot
+  // precomputed projection tensors (tufrg_atensor_build): three stored
+  // pairs and four state vectors in the context's arithmetic type
+  void* d_atensor = nullptr;
+  bool atensor_ready = false;
+  int* d_par = nullptr;            // [nff] parity of each form factor
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_nkb = 0, tc_nrow_pad = 0;
@@ -436,6 +442,12 @@ struct LoopBuffers {
   int nf, nfx, nfy, nl, nrow, nff, npair, mpad, kpad, kchunk, ksplit, mtiles, rm;
 };
 tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaStream_t st);
+
+// precomputed projection tensors: bytes they take (TUFRG_ERR_ARG when the
+// basis is too large), their construction, and V from them
+tufrg_status atensor_bytes(const tufrg_ctx* c, size_t* bytes);
+tufrg_status atensor_build(tufrg_ctx* c, cudaStream_t st);
+tufrg_status atensor_project(tufrg_ctx* c, const double* y, double* v, cudaStream_t st);
 
 tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0, cudaStream_t st);
 tufrg_status flow_step(tufrg_ctx* c, int n_steps, tufrg_result* r, cudaStream_t st);

@@ -50,7 +50,7 @@ constexpr int kProducers = 16;      // producer warps
 constexpr int kThreads = 32 * (kProducers + 1);
 constexpr int kRowBytes = 128;      // one 128B-swizzle row per K-block
 constexpr int kWTile = kRows * kRowBytes;  // 16 KB
-constexpr int kDepth = 4;           // producer units in flight (table gathers ahead)
+constexpr int kDepth = 3;           // producer units in flight (table gathers ahead)
 
 template <int PREC>
 struct Prec;

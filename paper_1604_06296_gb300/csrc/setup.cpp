@@ -475,6 +475,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     c->d_row_ptr = dp->d_row_ptr;
     c->d_terms = dp->d_terms;
     for (int t = 0; t < 3; ++t) c->term_off[t] = dp->term_off[t];
+    c->n_terms = dp->n_terms;
     c->d_gslot = dp->d_gslot;
   } else {
     TUFRG_CHECK(setup_proj(c, st));
@@ -556,6 +557,7 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
       terms.push_back(make_int4(dense[P.term_key[t][i]], P.term_dx[t][i] + P.dmax,
                                 P.term_dy[t][i] + P.dmax, (int)P.term_sign[t][i]));
   }
+  c->n_terms = (int)terms.size();
   std::vector<int4> gslot = P.gslot;
   for (int4& g : gslot)
     if (g.y >= 0) g.y = dense[g.y];
@@ -586,7 +588,8 @@ void free_device(tufrg_ctx* c) {
   free_flow(c);
   view_free(c->view);
   void* own[] = {c->d_ext,     c->d_xiext, c->d_err, c->d_tab, c->d_lambda, c->d_partial,
-                 c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey, c->d_y32};
+                 c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey, c->d_y32,
+                 c->d_atensor, c->d_par};
   for (void* p : own)
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {
