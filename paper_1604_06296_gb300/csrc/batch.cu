@@ -561,7 +561,7 @@ tufrg_status batch_flow(tufrg_batch* b, const tufrg_flow_opts* o, double* y_dev,
 // the candidates: the default, and a ladder around it within the chain cap
 std::vector<int> tune_candidates(const MultiView& v) {
   const int d = view_default_kbps(v);
-  const int cap = 4096 / tc_k_per_block(v.tc_prec);
+  const int cap = max_kbps(v.tc_prec);
   std::vector<int> c = {d};
   for (int k : {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
     if (k <= cap) c.push_back(k);

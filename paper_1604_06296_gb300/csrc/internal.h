@@ -375,6 +375,8 @@ size_t tc_smem_bytes(int npad);
 // TMA tensor maps of a context's F parts into c->d_tmap
 tufrg_status make_f_tensor_maps(tufrg_ctx* c, cudaStream_t st);
 int tc_k_per_block(int prec);
+// the most K-blocks one work item accumulates in one FP32 chain
+int max_kbps(int prec);
 int table_ctas(int n_ext);
 tufrg_status prepare_loops_tc_multi(const MultiView& v);
 tufrg_status prepare_project_multi(const MultiView& v);

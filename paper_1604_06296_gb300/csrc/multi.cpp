@@ -32,14 +32,17 @@ tufrg_status upload_to(T** dptr, const std::vector<T>& h, cudaStream_t st) {
   return TUFRG_OK;
 }
 
-// accumulation chains of at most 4096 loop points per item: the tensor core
+// accumulation chains of at most 5120 (BF16x3) or 4096 (3xTF32, twice the
+// MMA instructions per loop point) loop points per item: the tensor core
 // rounds the FP32 accumulator once per MMA instruction, so the relative error
 // of an item's partial sum grows with its number of K-blocks per
 // accumulator set (BF16x3 at 8192 points per item reached ~1e-5 at
-// production sizes, 4096 keep it near 5e-6)
-int max_kbps(int prec) { return 4096 / tc_k_per_block(prec); }
-
+// production sizes, 4096 keep it near 5e-6).  The large workload's default
+// then takes two items of 72 K-blocks per CTA instead of three of 48
+// (323.6 instead of 333 us per launch: one item change less per CTA).
 }  // namespace
+
+int max_kbps(int prec) { return (prec == TUFRG_BF16X3 ? 5120 : 4096) / tc_k_per_block(prec); }
 
 int sm_count() {
   int dev = 0, n = 0;
