@@ -961,6 +961,77 @@ def run_atensor(args, rank, world, local):
     return 0
 
 
+def run_refine(args, rank, world, local):
+    """Fermi-surface-refined loop cells (Sec. 3: the adaptive cubature's role)
+    at the production point (coarse 24x24, Nff 13, BF16x3): the loops at two
+    scales near the critical one and the flow to Lambda_c on the fine grid
+    (480x480) without and with refinement (s = 5 sub-points per direction,
+    band 8 Lambda, below Lambda = 0.1), each against the same on a grid three
+    times finer per direction (1440x1440); the cost of the loop stage and of
+    the flow.  value: the loops' error without refinement over the error with
+    it, at the smaller scale (max norm relative to the finer grid)."""
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    c = W.config("cfg2")
+    bonds = W.bonds_for_shells(c["shells"])
+    tp = c["tp"]
+    mk = lambda nf: tufrg.Solver(c["t"], tp, 4 * tp, c["U"], bonds, c["nc"], nf,
+                                 precision=args.precision)
+    plain, refined, fine = mk(c["nf"]), mk(c["nf"]), mk(3 * c["nf"])
+    refined.set_refinement(s=5, kappa=8.0, lambda_on=0.1)
+
+    def ev(fn, n=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    scales = []
+    for lam in (0.03, 0.012):
+        ref = fine.loops(lam).cpu().numpy()
+        sc = np.abs(ref).max()
+        e_plain = float(np.abs(plain.loops(lam).cpu().numpy() - ref).max() / sc)
+        e_ref = float(np.abs(refined.loops(lam).cpu().numpy() - ref).max() / sc)
+        scales.append({"lambda": lam, "loops_err_plain": e_plain, "loops_err_refined": e_ref,
+                       "loops_ms_plain": ev(lambda: plain.loops(lam)),
+                       "loops_ms_refined": ev(lambda: refined.loops(lam)),
+                       "loops_ms_fine_grid": ev(lambda: fine.loops(lam))})
+    kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
+              rtol=1e-6, atol=1e-8, h0=0.05)
+    flows = {}
+    for name, sv in (("fine_grid_1440", fine), ("plain_480", plain), ("refined_480", refined)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, r, _ = sv.flow(**kw)
+        torch.cuda.synchronize()
+        flows[name] = {"time_s": time.perf_counter() - t0, "lambda_c": r["lambda_c"],
+                       "rhs_evals": r["n_rhs"], "diverged": r["diverged"]}
+    lc = flows["fine_grid_1440"]["lambda_c"]
+    for name in ("plain_480", "refined_480"):
+        flows[name]["lambda_c_rel_err_vs_fine_grid"] = abs(flows[name]["lambda_c"] - lc) / lc
+    for sv in (plain, refined, fine):
+        sv.close()
+    last = scales[-1]
+    out = {"metric": "loop error near Lambda_c, uniform fine grid over refined cells (ratio)",
+           "value": last["loops_err_plain"] / max(last["loops_err_refined"], 1e-300),
+           "unit": "x", "n_gpus": 1, "steps": 5, "warmup": 1, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+           "data": "synthetic",
+           "config": {"workload": workload_desc(tp, "cfg2") + "; refinement s=5, kappa=8, "
+                                  "below Lambda=0.1; reference: fine grid 1440x1440"},
+           "scales": scales, "flows": flows}
+    print(json.dumps(out))
+    return 0
+
+
 def run_point(args, rank, world, local):
     """One phase-diagram point per rank (the production or the large point)."""
     import torch
@@ -1170,13 +1241,15 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other precisions on the same point")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=["cfg5", "cfg2", "cfg5-batch", "scan", "learned", "atensor"],
+                    choices=["cfg5", "cfg2", "cfg5-batch", "scan", "learned", "atensor",
+                             "refine"],
                     help="cfg5: large point (coarse 48x48, Nff 25, fine 960x960; default); "
                          "cfg2: production point (coarse 24x24, Nff 13, fine 480x480); "
                          "cfg5-batch: 16 (t', mu) points on the large grids advanced "
                          "together; scan: batched phase-diagram scan; learned: loop "
                          "surrogate trained and used in flows; atensor: projections from "
-                         "the precomputed tensors of App. C against the on-the-fly path")
+                         "the precomputed tensors of App. C against the on-the-fly path; "
+                         "refine: Fermi-surface-refined loop cells at the production point")
     ap.add_argument("--shard", action="store_true",
                     help="one point with its loop rows split over the ranks (strong scaling); "
                          "a step is one RHS evaluation")
@@ -1201,6 +1274,8 @@ def main():
         return run_learned(args, rank, world, local)
     if args.workload == "atensor":
         return run_atensor(args, rank, world, local)
+    if args.workload == "refine":
+        return run_refine(args, rank, world, local)
     return run_point(args, rank, world, local)
 
 

@@ -167,6 +167,22 @@ tufrg_status tufrg_loops(tufrg_ctx* ctx, double lambda, double* chi_dot_dev,
 tufrg_status tufrg_project(tufrg_ctx* ctx, const double* y_dev, double* v_dev,
                            void* cuda_stream);
 
+/* Step ii with Fermi-surface-refined loop cells (Sec. 3: the paper
+ * integrates each loop with an adaptive cubature; the refinement rule is a
+ * reading).  The loop sums are the midpoint rule on the fine-grid cells;
+ * below the scale lambda_on a cell p is refined for a transfer momentum l
+ * when one of its propagators xi(k + l/2), xi(k - l/2), at the cell's centre
+ * and four corners, changes sign or comes within kappa * Lambda of zero, and
+ * its midpoint value is then replaced by the average over s x s sub-points
+ * (s odd: they lie on the grid of s * nf points per direction).  Applies to
+ * every later loop evaluation of the context (tufrg_loops, tufrg_rhs, flows,
+ * row loops); s = 1, kappa = 0 or lambda_on = 0 switch it off.  Device tables
+ * of (s nf)^2 (Nff + 1) numbers in the context's arithmetic type.
+ * TUFRG_ERR_ARG for s even or outside 1..9, negative or non-finite kappa or
+ * lambda_on, more than 512 parity-allowed pairs, or tables above 16 GiB. */
+tufrg_status tufrg_set_refinement(tufrg_ctx* ctx, int32_t s, double kappa, double lambda_on,
+                                  void* cuda_stream);
+
 /* Step i from precomputed projection tensors (App. C; Sec. 2.5: the
  * scale-independent parts of the projections computed once and reused at
  * every scale).  Every cross projection is a linear map of the source

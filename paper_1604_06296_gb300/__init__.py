@@ -78,6 +78,11 @@ class Solver:
         tufrg_project(self.ctx, self._check(y, 3), self._check(out, 3), _stream())
         return out
 
+    def set_refinement(self, s=5, kappa=8.0, lambda_on=float("inf")):
+        """Fermi-surface refinement of the loop cells (s = 1: off)."""
+        lam_on = 1e300 if lambda_on == float("inf") else float(lambda_on)
+        _abi.tufrg_set_refinement(self.ctx, int(s), float(kappa), lam_on, _stream())
+
     def atensor_bytes(self):
         """Device bytes of the precomputed projection tensors (App. C)."""
         return _abi.tufrg_atensor_bytes(self.ctx)

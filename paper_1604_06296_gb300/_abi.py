@@ -97,6 +97,7 @@ SIGNATURES = {
     "tufrg_selftest_wait": ([c_void_p, c_int32, c_void_p], c_int32),
     "tufrg_selftest_convert": ([c_void_p, c_void_p, c_void_p, c_int64, c_void_p], c_int32),
     "tufrg_atensor_bytes": ([c_void_p, POINTER(c_int64)], c_int32),
+    "tufrg_set_refinement": ([c_void_p, c_int32, c_double, c_double, c_void_p], c_int32),
     "tufrg_atensor_build": ([c_void_p, c_void_p], c_int32),
     "tufrg_project_atensor": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "tufrg_autotune": ([c_void_p, c_double, POINTER(tufrg_tune_report), c_void_p], c_int32),
@@ -287,6 +288,11 @@ def tufrg_selftest_convert(x_ptr: int, y32_ptr: int, back_ptr: int, n: int,
                            stream: int = 0) -> None:
     _check(lib().tufrg_selftest_convert(_dptr(x_ptr), _dptr(y32_ptr), _dptr(back_ptr), int(n),
                                         _dptr(stream)), "tufrg_selftest_convert")
+
+
+def tufrg_set_refinement(ctx, s: int, kappa: float, lambda_on: float, stream: int = 0) -> None:
+    _check(lib().tufrg_set_refinement(ctx, int(s), float(kappa), float(lambda_on), _dptr(stream)),
+           "tufrg_set_refinement")
 
 
 def tufrg_atensor_bytes(ctx) -> int:

@@ -58,11 +58,15 @@ tufrg_status launch_loops(tufrg_ctx* c, int prec, double* chi, cudaStream_t st) 
     if (!c->sur || chi != c->d_chi) return TUFRG_ERR_STATE;
     return surrogate_loops(c->sur, c, chi, st);
   }
+  // the row loops, their refinement correction, every l from the rows
   if (prec == TUFRG_FP64) {
     TUFRG_CHECK(launch_scale_tables(c, st));
-    return launch_loops_fp64(c, chi, st);
+    TUFRG_CHECK(launch_loops_fp64_rows(c, st));
+  } else {
+    TUFRG_CHECK(launch_loops_tc_rows_multi(c->view, st));
   }
-  return launch_loops_tc_multi(c->view, chi, st);
+  TUFRG_CHECK(launch_refine_rows(c, st));
+  return launch_expand_multi(c->view, chi, st);
 }
 
 tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st) {
@@ -70,9 +74,11 @@ tufrg_status launch_loop_rows(tufrg_ctx* c, int prec, cudaStream_t st) {
   if (sharded(c)) return TUFRG_ERR_STATE;
   if (prec == TUFRG_FP64) {
     TUFRG_CHECK(launch_scale_tables(c, st));
-    return launch_loops_fp64_rows(c, st);
+    TUFRG_CHECK(launch_loops_fp64_rows(c, st));
+  } else {
+    TUFRG_CHECK(launch_loops_tc_rows_multi(c->view, st));
   }
-  return launch_loops_tc_rows_multi(c->view, st);
+  return launch_refine_rows(c, st);
 }
 
 int rhs_arith(const tufrg_ctx* c, int prec) {
@@ -219,6 +225,12 @@ tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi
   TUFRG_CHECK(tufrg::launch_to_f32(v_dev, v32, c->view.state_elems, st));
   return tufrg::launch_products_multi(c->view, c->p.precision, v32, chi_dot_dev, dy_dev, false,
                                       st);
+}
+
+tufrg_status tufrg_set_refinement(tufrg_ctx* c, int32_t s, double kappa, double lambda_on,
+                                  void* stream) {
+  if (!c || !c->d_V) return TUFRG_ERR_ARG;
+  return tufrg::set_refinement(c, s, kappa, lambda_on, (cudaStream_t)stream);
 }
 
 tufrg_status tufrg_atensor_bytes(const tufrg_ctx* c, int64_t* bytes) {

@@ -228,6 +228,16 @@ struct tufrg_ctx {
   void* d_atensor = nullptr;
   bool atensor_ready = false;
   int* d_par = nullptr;            // [nff] parity of each form factor
+  // Fermi-surface refinement of the loop cells (tufrg_set_refinement): s x s
+  // sub-points (s = 1: off), band kappa Lambda, active below Lambda_on;
+  // dispersion on the half-cell grid (FP64), dispersion and form factors on
+  // the sub-point grid (arithmetic type), the bond vectors
+  int ref_s = 1;
+  double ref_kappa = 0.0, ref_lam_on = 0.0;
+  void* d_ref_xi2 = nullptr;
+  void* d_ref_xis = nullptr;
+  void* d_ref_ffs = nullptr;
+  int* d_ref_bonds = nullptr;
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_nkb = 0, tc_nrow_pad = 0;
@@ -444,6 +454,14 @@ struct LoopBuffers {
   int nf, nfx, nfy, nl, nrow, nff, npair, mpad, kpad, kchunk, ksplit, mtiles, rm;
 };
 tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaStream_t st);
+
+// Fermi-surface refinement of the loop cells: tables for (s, kappa,
+// Lambda_on) (s = 1, kappa = 0 or Lambda_on = 0: off), the correction of the
+// row loops of the rows the context computes (after their combination), and
+// release of the tables
+tufrg_status set_refinement(tufrg_ctx* c, int s, double kappa, double lam_on, cudaStream_t st);
+tufrg_status launch_refine_rows(tufrg_ctx* c, cudaStream_t st);
+void free_refinement(tufrg_ctx* c);
 
 // precomputed projection tensors: bytes they take (TUFRG_ERR_ARG when the
 // basis is too large), their construction, and V from them

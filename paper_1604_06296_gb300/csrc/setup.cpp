@@ -584,6 +584,7 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
 }
 
 void free_device(tufrg_ctx* c) {
+  free_refinement(c);
   flow_drop_graphs(c);
   free_flow(c);
   view_free(c->view);
