@@ -1032,6 +1032,85 @@ def run_refine(args, rank, world, local):
     return 0
 
 
+def run_mesh(args, rank, world, local):
+    """Channel-specific non-uniform bosonic meshes (Sec. 4) at the production
+    point (coarse 24x24, Nff 13, fine 480x480): P on a mesh refined 5x5 around
+    l = 0 (1080 points), C and D on one refined around l = 0 and (pi, pi)
+    (6384 points, the union), against the uniform coarse grid (576 points)
+    and the uniform grid of the meshes' finest spacing (120x120, 14400
+    points): RHS evaluations per second of each (the same seeded state
+    drawn per context), the loop kernel's share and roofline on the mesh,
+    and the flow to Lambda_c on each.  value: RHS evaluations per second on
+    the meshes."""
+    import torch
+    import paper_1604_06296_gb300 as tufrg
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    c = W.config("cfg2")
+    M = W.PRODUCTION_MESH
+    bonds = W.bonds_for_shells(c["shells"])
+    tp = c["tp"]
+    pts, wp, wc = W.channel_mesh(M["nc"], M["m"], M["p"], M["cd"])
+    mk = lambda nc, mesh=None: tufrg.Solver(c["t"], tp, 4 * tp, c["U"], bonds, nc, c["nf"],
+                                            precision=args.precision, mesh=mesh)
+    sv = {"meshes": mk(M["nc"], (M["m"], pts, wp, wc)), "coarse_24": mk(M["nc"]),
+          "uniform_120": mk(M["nc"] * M["m"])}
+    n = max(5, args.steps)
+    rates = {k: dict(rhs_rate(torch, s, n), nl=s.nl, loop_rows=tufrg._abi.tufrg_row_info(s.ctx)[0])
+             for k, s in sv.items()}
+    peaks, peak_src = measured_peaks()
+    s = sv["meshes"]
+    nrow, npair = tufrg._abi.tufrg_row_info(s.ctx)
+    kdim = c["nf"] * c["nf"] // 2 + 2
+    k_ms = rates["meshes"]["loop_kernel_ms"]
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    peak = bf16 if args.precision == "bf16x3" else bf16 * 1.1 / 2.25
+    flops = 2.0 * 3 * 2 * npair * kdim * nrow
+    roofline = {"bound": "tensor", "kernel": f"loops_tc_kernel<{args.precision}> on the meshes",
+                "achieved": flops / (k_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / (k_ms * 1e-3) / 1e12 / peak, "traffic": None,
+                "algorithmic_flop_per_launch": flops,
+                "counting": f"{npair} allowed pairs x {kdim} half-zone points x {nrow} loop "
+                            "rows (one per mesh point) x 2 channels x 3 split products",
+                "peak_source": f"bf16 dense burst {bf16} TFLOP/s from {peak_src} (of measured)"}
+    flows = {}
+    if not args.no_flow_time:
+        kw = dict(lambda0=c["lambda0"], lambda_min=c["lambda_min"], threshold=c["threshold"],
+                  rtol=1e-6, atol=1e-8, h0=0.05)
+        for name, so in sv.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, r, _ = so.flow(**kw)
+            torch.cuda.synchronize()
+            li = r["l_index"]
+            if name == "meshes":
+                j = pts[li]
+                lv = (-np.pi + 2 * np.pi * j / (M["nc"] * M["m"])).tolist()
+            else:
+                nc = so.params.nc_x
+                lv = [-np.pi + 2 * np.pi * (li // nc) / nc, -np.pi + 2 * np.pi * (li % nc) / nc]
+            flows[name] = {"time_s": time.perf_counter() - t0, "lambda_c": r["lambda_c"],
+                           "kind": r["kind"], "l_c": lv, "rhs_evals": r["n_rhs"],
+                           "diverged": r["diverged"]}
+        lc = flows["uniform_120"]["lambda_c"]
+        for name in ("meshes", "coarse_24"):
+            flows[name]["lambda_c_rel_diff_vs_uniform_120"] = abs(flows[name]["lambda_c"] - lc) / lc
+    for so in sv.values():
+        so.close()
+    out = {"metric": "RHS evaluations per second on channel-specific meshes", "unit": "RHS/s",
+           "value": rates["meshes"]["rhs_evals_per_s"], "n_gpus": 1, "steps": n, "warmup": 1,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.precision, "data": "synthetic",
+           "config": {"workload": workload_desc(tp, "cfg2") + "; mesh_P 1080 points (5x5 "
+                                  "refinement within 0.6 of l=0), mesh_CD 6384 points (within "
+                                  "1.6 of l=0 and (pi,pi)); nf 480",
+                      "l2": "inputs resident, not flushed (RHS rate of repeated calls)"},
+           "roofline": roofline, "rhs": rates, "flows": flows}
+    print(json.dumps(out))
+    return 0
+
+
 def run_point(args, rank, world, local):
     """One phase-diagram point per rank (the production or the large point)."""
     import torch
@@ -1242,14 +1321,16 @@ def main():
                     help="skip the other precisions on the same point")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["cfg5", "cfg2", "cfg5-batch", "scan", "learned", "atensor",
-                             "refine"],
+                             "refine", "mesh"],
                     help="cfg5: large point (coarse 48x48, Nff 25, fine 960x960; default); "
                          "cfg2: production point (coarse 24x24, Nff 13, fine 480x480); "
                          "cfg5-batch: 16 (t', mu) points on the large grids advanced "
                          "together; scan: batched phase-diagram scan; learned: loop "
                          "surrogate trained and used in flows; atensor: projections from "
                          "the precomputed tensors of App. C against the on-the-fly path; "
-                         "refine: Fermi-surface-refined loop cells at the production point")
+                         "refine: Fermi-surface-refined loop cells at the production point; "
+                         "mesh: channel-specific non-uniform bosonic meshes at the production "
+                         "point")
     ap.add_argument("--shard", action="store_true",
                     help="one point with its loop rows split over the ranks (strong scaling); "
                          "a step is one RHS evaluation")
@@ -1276,6 +1357,8 @@ def main():
         return run_atensor(args, rank, world, local)
     if args.workload == "refine":
         return run_refine(args, rank, world, local)
+    if args.workload == "mesh":
+        return run_mesh(args, rank, world, local)
     return run_point(args, rank, world, local)
 
 

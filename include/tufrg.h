@@ -139,6 +139,27 @@ typedef struct {
  * released by tufrg_destroy.  Blocks until the tables are on the device. */
 tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** out);
 
+/* Sec. 4 (the channel meshes): a context whose bosonic momenta are the
+ * points of a non-uniform mesh instead of the coarse grid.  The points are
+ * host integer pairs points[i][2] = (jx, jy), 0 <= j < nc m, for
+ * l = -pi + 2 pi j / (nc m); m is odd (the refinement of a coarse cell into
+ * m x m sub-cells), nc_x = nc_y = nc, and nf_x, nf_y are multiples of
+ * 2 nc m (l/2 on the fine grid).  w_p[i] and w_cd[i] are the quadrature
+ * weights of point i in mesh_P and mesh_CD (zero off that mesh; each set
+ * non-negative and summing to one within 1e-9; every point in at least one
+ * mesh; no point twice).  The state, couplings, loops and derivative of the
+ * context are [3][n_points][Nff][Nff] in the order of the points: the
+ * Fourier values of a source channel at the projections' key positions are
+ * quadratures over its own mesh (Eqs. proj_VP/VC/VD), the k and k'
+ * averages stay those of the coarse grid, and the derivative of P vanishes
+ * where w_p = 0, that of C and D where w_cd = 0.  The arrays are copied.
+ * Returns TUFRG_ERR_ARG for anything above not met; otherwise as
+ * tufrg_setup.  Loop refinement, projection tensors, row sharding and
+ * surrogates refuse a mesh context with TUFRG_ERR_STATE. */
+tufrg_status tufrg_setup_mesh(const tufrg_params* p, int32_t m, int32_t n_points,
+                              const int32_t* points, const double* w_p, const double* w_cd,
+                              void* cuda_stream, tufrg_ctx** out);
+
 /* Releases all device and host memory of the context (synchronises). */
 void tufrg_destroy(tufrg_ctx* ctx);
 

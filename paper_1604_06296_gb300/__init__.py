@@ -34,7 +34,10 @@ class Solver:
     """
 
     def __init__(self, t, tp, mu, U, bonds, nc, nf, precision="fp64", feedback=True,
-                 ncy=None, nfy=None):
+                 ncy=None, nfy=None, mesh=None):
+        """mesh: None (the coarse grid) or (m, points [n][2], w_p [n], w_cd [n]),
+        a non-uniform mesh of lattice points l = -pi + 2 pi j / (nc m) with the
+        quadrature weights of mesh_P and mesh_CD (Sec. 4)."""
         self._bonds = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p = _abi.tufrg_params()
@@ -47,7 +50,11 @@ class Solver:
         p.precision = prec
         p.feedback = 1 if feedback else 0
         self.params = p
-        self.ctx = tufrg_setup(p, _stream())
+        if mesh is None:
+            self.ctx = tufrg_setup(p, _stream())
+        else:
+            m, points, w_p, w_cd = mesh
+            self.ctx = _abi.tufrg_setup_mesh(p, int(m), points, w_p, w_cd, _stream())
         self.nl, self.nff, self.nb = tufrg_dims(self.ctx)
 
     # -- helpers -------------------------------------------------------------

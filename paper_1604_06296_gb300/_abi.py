@@ -12,6 +12,8 @@ import ctypes
 import os
 from ctypes import POINTER, Structure, byref, c_double, c_int32, c_int64, c_void_p
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtufrg.so")
 
@@ -71,6 +73,9 @@ _lib = None
 # name -> (argtypes, restype); restype c_int32 means a tufrg_status to check
 SIGNATURES = {
     "tufrg_setup": ([POINTER(tufrg_params), c_void_p, POINTER(c_void_p)], c_int32),
+    "tufrg_setup_mesh": ([POINTER(tufrg_params), c_int32, c_int32, POINTER(c_int32),
+                          POINTER(c_double), POINTER(c_double), c_void_p, POINTER(c_void_p)],
+                         c_int32),
     "tufrg_destroy": ([c_void_p], None),
     "tufrg_dims": ([c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)], c_int32),
     "tufrg_eval_formfactors": ([c_int32, POINTER(c_int32), c_int32, POINTER(c_double),
@@ -172,6 +177,23 @@ def tufrg_setup(params: tufrg_params, stream: int = 0) -> c_void_p:
     return ctx
 
 
+def tufrg_setup_mesh(params: tufrg_params, m: int, points, w_p, w_cd,
+                     stream: int = 0) -> c_void_p:
+    """points: int32 [n][2] lattice coordinates; w_p, w_cd: float64 [n] (host)."""
+    pts = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 2)
+    wp = np.ascontiguousarray(w_p, dtype=np.float64).reshape(-1)
+    wc = np.ascontiguousarray(w_cd, dtype=np.float64).reshape(-1)
+    if len(wp) != len(pts) or len(wc) != len(pts):
+        raise ValueError("points, w_p and w_cd must have the same length")
+    ctx = c_void_p()
+    _check(lib().tufrg_setup_mesh(byref(params), int(m), len(pts),
+                                  pts.ctypes.data_as(POINTER(c_int32)),
+                                  wp.ctypes.data_as(POINTER(c_double)),
+                                  wc.ctypes.data_as(POINTER(c_double)), _dptr(stream),
+                                  byref(ctx)), "tufrg_setup_mesh")
+    return ctx
+
+
 def tufrg_destroy(ctx: c_void_p) -> None:
     lib().tufrg_destroy(ctx)
 
@@ -184,7 +206,6 @@ def tufrg_dims(ctx: c_void_p) -> tuple[int, int, int]:
 
 def tufrg_eval_formfactors(bonds, kx, ky):
     """bonds: int32 array [n][2]; kx, ky: float64 arrays [n]. Returns [Nff][n]."""
-    import numpy as np
     b = np.ascontiguousarray(bonds, dtype=np.int32)
     kx = np.ascontiguousarray(kx, dtype=np.float64)
     ky = np.ascontiguousarray(ky, dtype=np.float64)
@@ -340,7 +361,6 @@ def tufrg_batch_dims(b, point: int) -> tuple[int, int, int, int]:
 
 
 def _doubles(x):
-    import numpy as np
     a = np.ascontiguousarray(x, dtype=np.float64)
     return a, a.ctypes.data_as(POINTER(c_double))
 
@@ -394,7 +414,6 @@ def tufrg_surrogate_n_params(s) -> int:
 
 
 def tufrg_surrogate_get_params(s, stream: int = 0):
-    import numpy as np
     out = np.empty(tufrg_surrogate_n_params(s), dtype=np.float32)
     _check(lib().tufrg_surrogate_get_params(s, out.ctypes.data_as(POINTER(ctypes.c_float)),
                                             _dptr(stream)), "tufrg_surrogate_get_params")
@@ -402,7 +421,6 @@ def tufrg_surrogate_get_params(s, stream: int = 0):
 
 
 def tufrg_surrogate_set_params(s, params, stream: int = 0) -> None:
-    import numpy as np
     a = np.ascontiguousarray(params, dtype=np.float32)
     _check(lib().tufrg_surrogate_set_params(s, a.ctypes.data_as(POINTER(ctypes.c_float)),
                                             _dptr(stream)), "tufrg_surrogate_set_params")
@@ -419,7 +437,6 @@ def tufrg_surrogate_predict(s, x_dev: int, n: int, y_dev: int, stream: int = 0) 
 
 
 def tufrg_surrogate_loss_grad(s, x_dev: int, t_dev: int, n: int, stream: int = 0):
-    import numpy as np
     loss = c_double()
     g = np.empty(tufrg_surrogate_n_params(s), dtype=np.float32)
     _check(lib().tufrg_surrogate_loss_grad(s, _dptr(x_dev), _dptr(t_dev), n, byref(loss),
@@ -441,7 +458,6 @@ def tufrg_surrogate_attach(ctx, s, judge_every: int = 8, tol: float = 1e-3) -> N
 
 
 def tufrg_surrogate_get_scaling(s, n_out: int, stream: int = 0):
-    import numpy as np
     sh = np.empty(n_out, dtype=np.float32)
     sc = np.empty(n_out, dtype=np.float32)
     _check(lib().tufrg_surrogate_get_scaling(s, sh.ctypes.data_as(POINTER(ctypes.c_float)),
@@ -451,7 +467,6 @@ def tufrg_surrogate_get_scaling(s, n_out: int, stream: int = 0):
 
 
 def tufrg_surrogate_set_scaling(s, shift, scale, stream: int = 0) -> None:
-    import numpy as np
     if shift is None:
         _check(lib().tufrg_surrogate_set_scaling(s, None, None, _dptr(stream)),
                "tufrg_surrogate_set_scaling")

@@ -1,4 +1,5 @@
 // extern "C" entry points of include/tufrg.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -138,6 +139,13 @@ tufrg_status create_context(const tufrg_params* p, cudaStream_t st, const SetupS
   c->ncx = p->nc_x;
   c->ncy = p->nc_y;
   c->nl = c->ncx * c->ncy;
+  if (share.mesh) {
+    c->mesh = true;
+    c->mesh_m = share.mesh->m;
+    c->mesh_pts = share.mesh->pts;
+    c->mesh_w = share.mesh->w;
+    c->nl = (int)c->mesh_pts.size();
+  }
   c->nfx = p->nf_x;
   c->nfy = p->nf_y;
   c->nf = c->nfx * c->nfy;
@@ -162,6 +170,43 @@ tufrg_status tufrg_setup(const tufrg_params* p, void* cuda_stream, tufrg_ctx** o
   if (!out) return TUFRG_ERR_ARG;
   *out = nullptr;
   return tufrg::create_context(p, (cudaStream_t)cuda_stream, tufrg::SetupShare(), out);
+}
+
+tufrg_status tufrg_setup_mesh(const tufrg_params* p, int32_t m, int32_t n_points,
+                              const int32_t* points, const double* w_p, const double* w_cd,
+                              void* cuda_stream, tufrg_ctx** out) {
+  if (!out) return TUFRG_ERR_ARG;
+  *out = nullptr;
+  if (!p || !points || !w_p || !w_cd || p->nc_x != p->nc_y || m < 1 || m > 1023 || !(m & 1) ||
+      n_points < 1 || n_points > (1 << 16))
+    return TUFRG_ERR_ARG;
+  const long long div = (long long)p->nc_x * m;
+  if (div <= 0 || p->nf_x % (2 * div) || p->nf_y % (2 * div)) return TUFRG_ERR_ARG;
+  tufrg::MeshSpec mesh;
+  mesh.m = m;
+  mesh.pts.resize(n_points);
+  mesh.w.resize(2 * (size_t)n_points);
+  double sum_p = 0.0, sum_cd = 0.0;
+  std::vector<long long> keys(n_points);
+  for (int i = 0; i < n_points; ++i) {
+    const int jx = points[2 * i], jy = points[2 * i + 1];
+    if (jx < 0 || jy < 0 || jx >= div || jy >= div) return TUFRG_ERR_ARG;
+    const double a = w_p[i], b = w_cd[i];
+    if (!std::isfinite(a) || !std::isfinite(b) || a < 0.0 || b < 0.0 || (a == 0.0 && b == 0.0))
+      return TUFRG_ERR_ARG;  // every point belongs to one of the two meshes
+    mesh.pts[i] = make_int2(jx, jy);
+    mesh.w[i] = a;
+    mesh.w[n_points + i] = b;
+    sum_p += a;
+    sum_cd += b;
+    keys[i] = (long long)jx * div + jy;
+  }
+  if (std::fabs(sum_p - 1.0) > 1e-9 || std::fabs(sum_cd - 1.0) > 1e-9) return TUFRG_ERR_ARG;
+  std::sort(keys.begin(), keys.end());
+  if (std::adjacent_find(keys.begin(), keys.end()) != keys.end()) return TUFRG_ERR_ARG;
+  tufrg::SetupShare share;
+  share.mesh = &mesh;
+  return tufrg::create_context(p, (cudaStream_t)cuda_stream, share, out);
 }
 
 void tufrg_destroy(tufrg_ctx* c) {
@@ -230,6 +275,7 @@ tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi
 tufrg_status tufrg_set_refinement(tufrg_ctx* c, int32_t s, double kappa, double lambda_on,
                                   void* stream) {
   if (!c || !c->d_V) return TUFRG_ERR_ARG;
+  if (c->mesh) return TUFRG_ERR_STATE;  // refinement of the coarse grid's loop rows only
   return tufrg::set_refinement(c, s, kappa, lambda_on, (cudaStream_t)stream);
 }
 
@@ -243,6 +289,7 @@ tufrg_status tufrg_atensor_bytes(const tufrg_ctx* c, int64_t* bytes) {
 
 tufrg_status tufrg_atensor_build(tufrg_ctx* c, void* stream) {
   if (!c || !c->d_V) return TUFRG_ERR_ARG;
+  if (c->mesh) return TUFRG_ERR_STATE;  // the tensors of the coarse grid only
   return tufrg::atensor_build(c, (cudaStream_t)stream);
 }
 
@@ -312,6 +359,7 @@ tufrg_status tufrg_shard_rows(tufrg_ctx* c, int32_t row_begin, int32_t row_end, 
   if (!c || c->p.precision == TUFRG_FP64 || row_begin < 0 || row_end <= row_begin ||
       row_end > c->nrow)
     return TUFRG_ERR_ARG;
+  if (c->mesh) return TUFRG_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
   TUFRG_CUDA(cudaStreamSynchronize(st));
   c->shard_lo = row_begin;

@@ -132,6 +132,11 @@ struct PointDesc {
   int gmaxt;
   const double* lam;  // [0] scale of the loops, [1] factor applied to dy when scaled
   const int* skip;    // nonzero: the point does no work (finished flow); may be null
+  // non-uniform meshes: [2][nl] quadrature weights of mesh_P and mesh_CD and
+  // the lattice coordinates of the points (null on the coarse grid)
+  const double* mesh_w;
+  const int2* mesh_pts;
+  int mesh_div;       // nc m: the lattice of the mesh points
 };
 
 // kinds of multi-point launches: per point, a fixed number of CTAs
@@ -157,9 +162,10 @@ struct MultiView {
   int* d_prefix = nullptr;
   int nff_max = 0, nb_max = 0, nd_max = 0, nc_sum_max = 0;
   int nf_uniform = 0;  // Nff = Nb, the same for every point (else 0)
-  // projections in the grouped form (some point has Nff >= kGroupedNff), else
-  // in the term form
+  // projections in the grouped form (some point has Nff >= kGroupedNff, or a
+  // non-uniform mesh), else in the term form
   bool proj_grouped = false;
+  bool mesh = false;  // the (single) point lives on a non-uniform mesh
   // tensor-core loops: work items (point, l-tile, first K-block, K-blocks)
   // taken from a queue by persistent CTAs
   int tc_prec = TUFRG_FP64;  // TUFRG_FP64: no tensor-core loops
@@ -238,6 +244,15 @@ struct tufrg_ctx {
   void* d_ref_xis = nullptr;
   void* d_ref_ffs = nullptr;
   int* d_ref_bonds = nullptr;
+  // non-uniform bosonic meshes (tufrg_setup_mesh): the l are mesh points
+  // l = -pi + 2 pi j / (nc m) of the union of mesh_P and mesh_CD, with each
+  // channel's quadrature weights (zero off its mesh)
+  bool mesh = false;
+  int mesh_m = 1;
+  std::vector<int2> mesh_pts;
+  std::vector<double> mesh_w;      // [2][nl]: weights of mesh_P, of mesh_CD
+  double* d_mesh_w = nullptr;
+  int2* d_mesh_pts = nullptr;
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_nkb = 0, tc_nrow_pad = 0;
@@ -299,11 +314,19 @@ namespace tufrg {
 // batch-of-one view (contexts made for a tufrg_batch skip it).
 // workspace: allocate the context's own right-hand-side workspace, stream
 // and events (batch points use the batch's).
+// A non-uniform mesh: refinement factor m, lattice points and the
+// quadrature weights of mesh_P and mesh_CD ([2][points]).
+struct MeshSpec {
+  int m = 1;
+  std::vector<int2> pts;
+  std::vector<double> w;
+};
 struct SetupShare {
   const tufrg_ctx* loops = nullptr;
   const tufrg_ctx* proj = nullptr;
   bool own_view = true;
   bool workspace = true;
+  const MeshSpec* mesh = nullptr;  // the context's l are this mesh's points
 };
 tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share = SetupShare());
 // validation, basis and setup_device (tufrg_setup with shared tables)

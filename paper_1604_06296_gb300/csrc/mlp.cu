@@ -997,6 +997,7 @@ tufrg_status tufrg_surrogate_samples(tufrg_ctx* c, const tufrg_surrogate* s, dou
   if (!c || !s || !x_dev || !t_dev || !(std::isfinite(lambda) && lambda > 0.0) ||
       s->n_out != 2 * c->npair || !c->d_chi)
     return TUFRG_ERR_ARG;
+  if (c->mesh) return TUFRG_ERR_STATE;  // the surrogate's inputs are coarse-grid momenta
   cudaStream_t st = (cudaStream_t)stream;
   TUFRG_CHECK(tufrg::launch_set_scalar(c->d_lambda, lambda, st));
   TUFRG_CHECK(tufrg::launch_loops(c, c->p.precision, c->d_chi, st));
@@ -1121,6 +1122,7 @@ tufrg_status tufrg_surrogate_attach(tufrg_ctx* c, tufrg_surrogate* s, int32_t ju
   }
   if (s->n_out != 2 * c->npair || judge_every < 1 || !(tol > 0.0) || !c->d_chi)
     return TUFRG_ERR_ARG;
+  if (c->mesh) return TUFRG_ERR_STATE;
   c->sur = s;
   c->sur_every = judge_every;
   c->sur_tol = tol;

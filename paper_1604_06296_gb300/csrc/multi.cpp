@@ -138,7 +138,9 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
   const bool tc = tc_prec != TUFRG_FP64;
   // the projection form of the whole view (one launch sequence for all points)
   bool grouped = false;
-  for (int i = 0; i < n; ++i) grouped = grouped || ctx[i]->nff >= kGroupedNff;
+  for (int i = 0; i < n; ++i) grouped = grouped || ctx[i]->nff >= kGroupedNff || ctx[i]->mesh;
+  for (int i = 0; i < n; ++i) v.mesh = v.mesh || ctx[i]->mesh;
+  if (v.mesh && n != 1) return TUFRG_ERR_ARG;  // a mesh context is a view of its own
   v.proj_grouped = grouped;
   for (int i = 0; i < n; ++i) {
     const tufrg_ctx* c = ctx[i];
@@ -210,10 +212,13 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.gmaxt = c->proj.gmaxt;
     d.lam = lam[i];
     d.skip = skip ? skip[i] : nullptr;
+    d.mesh_w = c->d_mesh_w;
+    d.mesh_pts = c->d_mesh_pts;
+    d.mesh_div = c->ncx * c->mesh_m;
     const int cnt[kKinds] = {
         tc ? table_ctas(d.n_ext) : 0,
         tc ? tc_rows_ctas(d.npair, d.row_lo, d.row_hi) : 0,
-        d.feedback ? bond_ctas(d.ncx, d.nff) : 0,
+        d.feedback && !c->mesh ? bond_ctas(d.ncx, d.nff) : 0,
         d.feedback ? dft_ctas(d.nd) : 0,
         grouped && d.feedback ? d.gy_off[3] : 0,
         contract_ctas(d.nl, d.nff, grouped),

@@ -58,17 +58,18 @@ size_t products_smem(int nff) {
 
 // The products of one l from VP, VC, VD, Xp (= chi^pp), Xh (= chi^ph) in
 // shared memory (stride pstride(nff), padding columns zero); writes
-// dy[ch * chan + m * nff + n] for the three channels, scaled by sc.  Each
+// dy[ch * chan + m * nff + n] for the three channels, P scaled by sc_p, C and
+// D by sc_cd.  Each
 // thread computes a pair of adjacent entries of a row (two lanes of one
 // paired FP32 instruction; every lane takes the scalar form's roundings in
 // the scalar form's order).
 template <class T, int NF>
-__device__ __forceinline__ void products_in_smem(T* sm, int nff_rt, double sc,
+__device__ __forceinline__ void products_in_smem(T* sm, int nff_rt, double sc_p, double sc_cd,
                                                  double* __restrict__ dy, size_t chan) {
   using P = typename Pair<T>::type;
   const int nff = NF ? NF : nff_rt;
   const int S = pstride(nff), hp = S / 2, m2 = nff * S;
-  const T sct = to_t<T>(sc);
+  const T sct = to_t<T>(sc_p), scd = to_t<T>(sc_cd);
   T* VP = sm;
   T* VC = VP + m2;
   T* VD = VC + m2;
@@ -104,12 +105,12 @@ __device__ __forceinline__ void products_in_smem(T* sm, int nff_rt, double sc,
     }
     const int o = i * nff + j;
     dy[o] = to_out(sct, pp.x);
-    dy[chan + o] = to_out(-sct, cc.x);
-    dy[2 * chan + o] = to_out(sct, d.x);
+    dy[chan + o] = to_out(-scd, cc.x);
+    dy[2 * chan + o] = to_out(scd, d.x);
     if (j + 1 < nff) {
       dy[o + 1] = to_out(sct, pp.y);
-      dy[chan + o + 1] = to_out(-sct, cc.y);
-      dy[2 * chan + o + 1] = to_out(sct, d.y);
+      dy[chan + o + 1] = to_out(-scd, cc.y);
+      dy[2 * chan + o + 1] = to_out(scd, d.y);
     }
   }
 }
@@ -177,7 +178,11 @@ __global__ void products_kernel(const PointDesc* __restrict__ pts,
     }
   }
   __syncthreads();
-  products_in_smem<T, NF>(sm, nff, scaled ? pd.lam[1] : 1.0, dybase + pd.off_state + off, chan);
+  // on a non-uniform mesh a channel's derivative vanishes off its own mesh
+  const double sc = scaled ? pd.lam[1] : 1.0;
+  const double sc_p = pd.mesh_w && pd.mesh_w[l] == 0.0 ? 0.0 : sc;
+  const double sc_cd = pd.mesh_w && pd.mesh_w[nl + l] == 0.0 ? 0.0 : sc;
+  products_in_smem<T, NF>(sm, nff, sc_p, sc_cd, dybase + pd.off_state + off, chan);
 }
 
 // The products of a point-group covariant state (wedge layout: state,
@@ -221,7 +226,8 @@ __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
     put(Xh, e, nff, S, q >= 0 ? to_t<T>(rp[ch1 + q]) : (T)0);
   }
   __syncthreads();
-  products_in_smem<T, NF>(sm, nff, scaled ? pd.lam[1] : 1.0, dybase + off, chan);
+  const double sc = scaled ? pd.lam[1] : 1.0;
+  products_in_smem<T, NF>(sm, nff, sc, sc, dybase + off, chan);
 }
 
 }  // namespace

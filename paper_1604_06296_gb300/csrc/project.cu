@@ -199,6 +199,29 @@ __global__ void __launch_bounds__(kDft1Threads)
   }
 }
 
+// Fourier values of the keys of one (source, X) from the state's DFT Bh(X)
+// (after a barrier): F = C^T Bh C, C[a][b] = c_a(b), through tmp [nff][nb]
+// (a barrier in between).
+template <class V>
+__device__ __forceinline__ void keys_from_bh(const V* cs, const V* Bh, V* tmp, int nff, int nb,
+                                             V* F) {
+  // tmp[a][b4] = sum_b Bh[a][b] c_b(b4)
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) {
+    const int a = e / nb, b4 = e - a * nb;
+    V acc = {0, 0};
+    for (int b = 0; b < nff; ++b) acc = cfma(Bh[a * nff + b], cs[b * nb + b4], acc);
+    tmp[e] = acc;
+  }
+  __syncthreads();
+  // F[b3][b4] = sum_a c_a(b3) tmp[a][b4]
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int b3 = e / nb, b4 = e - b3 * nb;
+    V acc = {0, 0};
+    for (int a = 0; a < nff; ++a) acc = cfma(cs[a * nb + b3], tmp[a * nb + b4], acc);
+    F[e] = acc;
+  }
+}
+
 template <class T, int NF>
 __global__ void __launch_bounds__(256)
     bond_dft2_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
@@ -252,22 +275,75 @@ __global__ void __launch_bounds__(256)
       if (threadIdx.x + 256 * r < nff2) Bh[threadIdx.x + 256 * r] = acc[r];
   }
   __syncthreads();
-  // tmp[a][b4] = sum_b Bh[a][b] c_b(b4)
-  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) {
-    const int a = e / nb, b4 = e - a * nb;
-    V acc = {0, 0};
-    for (int b = 0; b < nff; ++b) acc = cfma(Bh[a * nff + b], cs[b * nb + b4], acc);
-    tmp[e] = acc;
+  keys_from_bh(cs, Bh, tmp, nff, nb,
+               fkbase + pd.off_fkey + ((size_t)(src * nd + dx) * nd + dy) * nb * nb);
+}
+
+// Non-uniform meshes: the Fourier values of the keys as quadratures over the
+// source channel's mesh, Bh(X) = nl sum_{l'} w_S(l') e^{i l'.X} B^S(l') (the
+// factor nl undoes the phase sums' 1/nl), then F = C^T Bh(X) C.  One CTA per
+// (source, X); the mesh in chunks of kMeshChunk points whose weighted phases
+// sit in shared memory (l = -pi + 2 pi j / (nc m)).
+constexpr int kMeshChunk = 512;
+
+template <class T, int NF>
+__global__ void __launch_bounds__(256)
+    mesh_dft_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
+                    const T* __restrict__ ybase, typename C2<T>::type* __restrict__ fkbase) {
+  using V = typename C2<T>::type;
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nff = NF ? NF : pd.nff, nb = NF ? NF : pd.nb, nff2 = nff * nff;
+  const int nd = pd.nd, nl = pd.nl, div = pd.mesh_div, dmax = (nd - 1) / 2;
+  const int loc = blockIdx.x - prefix[p];
+  const int dy = loc % nd, dx = (loc / nd) % nd, src = loc / (nd * nd);
+  extern __shared__ double2 sm2[];
+  V* cs = reinterpret_cast<V*>(sm2);  // [nff][nb]
+  V* Bh = cs + nff * nb;              // [nff][nff]
+  V* tmp = Bh + nff2;                 // [nff][nb]
+  V* ph = tmp + nff * nb;             // [kMeshChunk] weighted phases
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
+  const double* w = pd.mesh_w + (src == 0 ? 0 : nl);
+  const T* B = ybase + pd.off_state + (size_t)src * nl * nff2;
+  constexpr int kR = (kMaxNf * kMaxNf + 255) / 256;
+  V acc[kR];
+#pragma unroll
+  for (int r = 0; r < kR; ++r) acc[r] = {0, 0};
+  for (int l0 = 0; l0 < nl; l0 += kMeshChunk) {
+    const int cn = min(kMeshChunk, nl - l0);
+    __syncthreads();  // the previous chunk is consumed
+    for (int j = threadIdx.x; j < cn; j += blockDim.x) {
+      const int2 q = pd.mesh_pts[l0 + j];
+      // l.X / pi with 2X = (dx - dmax, dy - dmax)
+      const double t = ((double)((2 * q.x - div) * (dx - dmax)) +
+                        (double)((2 * q.y - div) * (dy - dmax))) / (2.0 * div);
+      double sn, c;
+      sincospi(t, &sn, &c);
+      const double wt = w[l0 + j] * nl;
+      ph[j] = {(T)(wt * c), (T)(wt * sn)};
+    }
+    __syncthreads();
+    for (int j = 0; j < cn; ++j) {
+      const V e = ph[j];
+      const T* Bl = B + (size_t)(l0 + j) * nff2;
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        const int ab = threadIdx.x + 256 * r;
+        if (ab < nff2) {
+          const T b = Bl[ab];
+          acc[r].x = fma(e.x, b, acc[r].x);
+          acc[r].y = fma(e.y, b, acc[r].y);
+        }
+      }
+    }
   }
+#pragma unroll
+  for (int r = 0; r < kR; ++r)
+    if (threadIdx.x + 256 * r < nff2) Bh[threadIdx.x + 256 * r] = acc[r];
   __syncthreads();
-  // F[b3][b4] = sum_a c_a(b3) tmp[a][b4]
-  V* F = fkbase + pd.off_fkey + ((size_t)(src * nd + dx) * nd + dy) * nb * nb;
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int b3 = e / nb, b4 = e - b3 * nb;
-    V acc = {0, 0};
-    for (int a = 0; a < nff; ++a) acc = cfma(cs[a * nb + b3], tmp[a * nb + b4], acc);
-    F[e] = acc;
-  }
+  keys_from_bh(cs, Bh, tmp, nff, nb,
+               fkbase + pd.off_fkey + ((size_t)(src * nd + dx) * nd + dy) * nb * nb);
 }
 
 // Element offset of the state and couplings of channel t at output slot q
@@ -641,6 +717,11 @@ size_t dft2_smem(const MultiView& v) {
          (2 * (size_t)v.nff_max * v.nb_max + (size_t)v.nff_max * v.nff_max + m);
 }
 template <class T>
+size_t mesh_dft_smem(const MultiView& v) {
+  return sizeof(typename C2<T>::type) *
+         (2 * (size_t)v.nff_max * v.nb_max + (size_t)v.nff_max * v.nff_max + kMeshChunk);
+}
+template <class T>
 size_t overlap_smem(const MultiView& v) {
   int nt = 1;
   for (const PointDesc& d : v.h) nt = std::max(nt, d.gmaxt);
@@ -672,6 +753,7 @@ tufrg_status prepare_typed(const MultiView& v) {
   const int smem = smem_optin();
   // (the two contract kernels also hold a few bytes of static shared memory)
   if ((int)dft1_smem<T>(v) > smem || (int)dft2_smem<T>(v) > smem ||
+      (int)mesh_dft_smem<T>(v) > smem ||
       (int)overlap_smem<T>(v) > smem ||
       (int)contract_terms_smem<T>(v) + 64 > smem)
     return TUFRG_ERR_ARG;
@@ -684,6 +766,9 @@ tufrg_status prepare_typed(const MultiView& v) {
     constexpr int NF = decltype(nf)::value;
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(bond_dft2_kernel<T, NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mesh_dft_kernel<T, NF>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(contract_terms_kernel<T, NF>, smem);
     if (e == cudaSuccess)
@@ -710,7 +795,13 @@ tufrg_status project_typed(const MultiView& v, const T* y, T* out, void* btv,
           v.d, v.dprefix(kKindBond), v.n, y, bt);
     TUFRG_CUDA(cudaGetLastError());
   }
-  if (v.total(kKindDft) > 0) {
+  if (v.total(kKindDft) > 0 && v.mesh) {
+    with_nf(v.nf_uniform, [&](auto nf) {
+      mesh_dft_kernel<T, decltype(nf)::value><<<v.total(kKindDft), 256, mesh_dft_smem<T>(v),
+                                                 st>>>(v.d, v.dprefix(kKindDft), v.n, y, fkey);
+    });
+    TUFRG_CUDA(cudaGetLastError());
+  } else if (v.total(kKindDft) > 0) {
     with_nf(v.nf_uniform, [&](auto nf) {
       bond_dft2_kernel<T, decltype(nf)::value><<<v.total(kKindDft), 256, dft2_smem<T>(v), st>>>(
           v.d, v.dprefix(kKindDft), v.n, bt, fkey);

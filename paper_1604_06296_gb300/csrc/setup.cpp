@@ -248,7 +248,8 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
   // are signed permutations g ranges over C4v; otherwise over {e, -1}
   // (R^g = diag(parity), which leaves the parity-allowed loops unchanged).
   std::vector<int> symperm, symsign;
-  const bool c4v = c->ncx == c->ncy && c->nfx == c->nfy && B.point_group(symperm, symsign);
+  const bool c4v =
+      !c->mesh && c->ncx == c->ncy && c->nfx == c->nfy && B.point_group(symperm, symsign);
   if (!c4v) {
     symperm.assign(8 * (size_t)nff, 0);
     symsign.assign(8 * (size_t)nff, 1);
@@ -259,7 +260,16 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
   std::vector<int> rowimg_ptr(1, 0);
   std::vector<char> served(c->nl, 0);
   const int hcx = c->ncx / 2, hcy = c->ncy / 2;
-  for (int jx = 0; jx < c->ncx; ++jx)
+  // a non-uniform mesh: one row per mesh point, l/2 in fine-grid steps
+  // (-pi/2 + pi j / (nc m)) / (2 pi / nf)
+  for (int l = 0; c->mesh && l < c->nl; ++l) {
+    const int div = c->ncx * c->mesh_m;
+    rowimg.push_back(make_int2(l, 0));
+    rowimg_ptr.push_back((int)rowimg.size());
+    rowshift.push_back(make_int2(-c->nfx / 4 + c->mesh_pts[l].x * (c->nfx / (2 * div)),
+                                 -c->nfy / 4 + c->mesh_pts[l].y * (c->nfy / (2 * div))));
+  }
+  for (int jx = 0; !c->mesh && jx < c->ncx; ++jx)
     for (int jy = 0; jy < c->ncy; ++jy) {
       const int l = jx * c->ncy + jy;
       if (served[l]) continue;
@@ -567,7 +577,7 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
   // e^{i l.Y} for every phase position Y and every l = (ix, iy)
   std::vector<double2> yph((size_t)P.gy.size() * c->nl);
   std::vector<float2> yph_f(yph.size());
-  for (size_t g = 0; g < P.gy.size(); ++g) {
+  for (size_t g = 0; !c->mesh && g < P.gy.size(); ++g) {
     const int dx = P.gy[g].x, dy = P.gy[g].y;
     for (int ix = 0; ix < c->ncx; ++ix)
       for (int iy = 0; iy < c->ncy; ++iy) {
@@ -577,6 +587,20 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
         yph[e] = make_double2(std::cos(a), std::sin(a));
         yph_f[e] = make_float2((float)yph[e].x, (float)yph[e].y);
       }
+  }
+  if (c->mesh) {  // e^{i l.Y} at the mesh points, l = -pi + 2 pi j / (nc m)
+    const int div = c->ncx * c->mesh_m;
+    for (size_t g = 0; g < P.gy.size(); ++g)
+      for (int l = 0; l < c->nl; ++l) {
+        const int2 j = c->mesh_pts[l];
+        const double a = M_PI * (double)((2 * j.x - div) * P.gy[g].x) / (2.0 * div) +
+                         M_PI * (double)((2 * j.y - div) * P.gy[g].y) / (2.0 * div);
+        const size_t e = g * c->nl + l;
+        yph[e] = make_double2(std::cos(a), std::sin(a));
+        yph_f[e] = make_float2((float)yph[e].x, (float)yph[e].y);
+      }
+    TUFRG_CHECK(upload(&c->d_mesh_w, c->mesh_w, st));
+    TUFRG_CHECK(upload(&c->d_mesh_pts, c->mesh_pts, st));
   }
   TUFRG_CHECK(upload(&c->d_yphase, yph, st));
   TUFRG_CHECK(upload(&c->d_yphase_f, yph_f, st));
@@ -590,7 +614,7 @@ void free_device(tufrg_ctx* c) {
   view_free(c->view);
   void* own[] = {c->d_ext,     c->d_xiext, c->d_err, c->d_tab, c->d_lambda, c->d_partial,
                  c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey, c->d_y32,
-                 c->d_atensor, c->d_par};
+                 c->d_atensor, c->d_par,   c->d_mesh_w, c->d_mesh_pts};
   for (void* p : own)
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {

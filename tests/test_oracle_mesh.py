@@ -89,3 +89,20 @@ def test_loops_at_mesh_points_equal_grid_loops():
     rpp, rph = lp.chi_dot(prob, 0.2, gi)
     assert np.abs(pp - rpp).max() <= 1e-14 * np.abs(rpp).max()
     assert np.abs(ph - rph).max() <= 1e-14 * np.abs(rph).max()
+
+
+@pytest.mark.parametrize("nc,m,radius", [(8, 3, 0.9), (6, 5, 1.2), (24, 5, 0.6)])
+def test_workload_mesh_generator_agrees_with_the_oracle(nc, m, radius):
+    cp, ccd = [(0.0, 0.0)], [(PI, PI), (0.0, 0.0)]
+    mesh = ms.refined_mesh(nc, m, cp, ccd, radius)
+    pts, wp, wc = W.channel_mesh(nc, m, (cp, radius), (ccd, radius))
+    assert np.array_equal(pts, mesh.points)
+    assert np.abs(wp - mesh.w_p).max() <= 1e-18 and np.abs(wc - mesh.w_cd).max() <= 1e-18
+
+
+def test_production_mesh_sizes():
+    M = W.PRODUCTION_MESH
+    pts, wp, wc = W.channel_mesh(M["nc"], M["m"], M["p"], M["cd"])
+    # about the paper's 992 (P) and 6632 (C, D) points
+    assert (wp > 0).sum() == 1080 and (wc > 0).sum() == 6384 and len(pts) == 6384
+    assert abs(wp.sum() - 1) < 1e-13 and abs(wc.sum() - 1) < 1e-13

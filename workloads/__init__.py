@@ -123,3 +123,49 @@ def large_batch_points(n: int = 16, seed: int = LARGE_BATCH_SEED) -> list[dict]:
         pts.append(dict(t=c["t"], tp=tp, mu=mu, U=c["U"], nc=c["nc"], nf=c["nf"],
                         shells=c["shells"]))
     return pts
+
+
+# Channel-specific bosonic meshes (Sec. 4): nested refinements of the coarse
+# grid.  A coarse cell (centre 2 pi i / nc - pi per direction) whose centre lies
+# within a channel's radius of one of its centres (periodic distance) is split
+# into m x m sub-cells (m odd), each a lattice point j on l = -pi + 2 pi j /
+# (nc m) carrying the sub-cell's area as weight; an unsplit cell keeps its
+# coarse point with the whole cell's area.  The production-sized meshes below
+# hold about as many points as the paper's (992 for P, 6632 for C and D) on the
+# production coarse grid: P refined around l = 0 (pairing), C and D around
+# l = 0 and (pi, pi) (ferromagnetic and antiferromagnetic peaks).
+PRODUCTION_MESH = dict(nc=24, m=5, p=([(0.0, 0.0)], 0.6),
+                       cd=([(0.0, 0.0), (-np.pi, -np.pi)], 1.6))
+
+
+def channel_mesh(nc: int, m: int, p, cd):
+    """(points [n][2] int32, w_p [n], w_cd [n]) of the union of mesh_P and
+    mesh_CD; p and cd are (centres [(lx, ly)], radius).  Points in
+    lexicographic order of (jx, jy)."""
+    if m < 1 or m % 2 == 0:
+        raise ValueError("m must be odd")
+    div, half = nc * m, (m - 1) // 2
+    centre = -np.pi + 2.0 * np.pi * np.arange(nc) / nc
+
+    def weights(spec):
+        centres, radius = spec
+        w = {}
+        for ix in range(nc):
+            for iy in range(nc):
+                split = False
+                for cx, cy in centres:
+                    d = np.angle(np.exp(1j * (centre[ix] - cx))), \
+                        np.angle(np.exp(1j * (centre[iy] - cy)))
+                    split = split or np.hypot(*d) <= radius
+                if not split:
+                    w[(m * ix, m * iy)] = 1.0 / (nc * nc)
+                    continue
+                for a in range(-half, half + 1):
+                    for b in range(-half, half + 1):
+                        w[((m * ix + a) % div, (m * iy + b) % div)] = 1.0 / (div * div)
+        return w
+
+    wp, wc = weights(p), weights(cd)
+    keys = sorted(set(wp) | set(wc))
+    return (np.array(keys, dtype=np.int32).reshape(-1, 2),
+            np.array([wp.get(k, 0.0) for k in keys]), np.array([wc.get(k, 0.0) for k in keys]))
