@@ -566,10 +566,9 @@ tufrg_status flow_init(tufrg_ctx* c, const tufrg_flow_opts* o, const double* y0,
   TUFRG_CUDA(cudaMemcpyAsync(f.y, y0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   // the wedge when the initial state is covariant (the bare start, zeros, is)
   // and every loop is exact (a surrogate's loops are not covariant): the
-  // flow then integrates the state at the rows' representatives only (a
-  // non-uniform mesh has one row per point: nothing to compress)
+  // flow then integrates the state at the rows' representatives only
   f.wedge = false;
-  if (!c->sur && !c->mesh) {
+  if (!c->sur) {
     TUFRG_CHECK(launch_covariance_check(c->view, f.y, f.cov, st));
     unsigned long long h[2] = {0, 0};
     TUFRG_CUDA(cudaMemcpyAsync(h, f.cov, sizeof(h), cudaMemcpyDeviceToHost, st));

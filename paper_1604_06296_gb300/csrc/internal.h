@@ -137,6 +137,11 @@ struct PointDesc {
   const double* mesh_w;
   const int2* mesh_pts;
   int mesh_div;       // nc m: the lattice of the mesh points
+  // [2][nd^2][nl] nl w(l) e^{i l.X} of mesh_P and mesh_CD at the key positions
+  // X; the key DFT sums mesh points in mesh_chunks chunks of mesh_lc
+  const double2* mesh_e;
+  const float2* mesh_e_f;
+  int mesh_lc, mesh_chunks;
 };
 
 // kinds of multi-point launches: per point, a fixed number of CTAs
@@ -144,7 +149,9 @@ enum : int {
   kKindTable = 0,  // per-scale FP32 halo table
   kKindReduce,     // split-K combination of the tensor-core partial sums
   kKindBond,       // projections: DFT of the state along y at the Fourier positions
-  kKindDft,        // projections: DFT along x and bond space, the keys of a position
+                   // (non-uniform meshes: partial quadrature sums over chunks of points)
+  kKindDft,        // projections: DFT along x (meshes: the chunks' sum) and bond
+                   // space, the keys of a position
   kKindOverlap,    // projections: key sums and basis change per phase position
   kKindContract,   // projections: phase sums over the positions, per l
   kKindProducts,   // V chi V
@@ -253,6 +260,9 @@ struct tufrg_ctx {
   std::vector<double> mesh_w;      // [2][nl]: weights of mesh_P, of mesh_CD
   double* d_mesh_w = nullptr;
   int2* d_mesh_pts = nullptr;
+  double2* d_mesh_e = nullptr;  // [2][nd^2][nl] nl w e^{i l.X} (FP64, FP32 copy)
+  float2* d_mesh_e_f = nullptr;
+  int mesh_lc = 0, mesh_chunks = 0;
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_nkb = 0, tc_nrow_pad = 0;
@@ -426,6 +436,13 @@ constexpr int kMaxNf = 32;
 // elements of a point's projection workspace: the state's DFT along y
 // [3][ncx][nd][nff*nff], later reused for the overlap sums [positions Y][nff][nff]
 size_t bt_region(int ncx, int nd, int nff, int ny_total);
+// mesh key DFT: CTAs of the partial sums over chunks of mesh points, and the
+// partial sums' elements [3][chunks][nd^2][nff^2] (complex; in the bt region)
+constexpr int kMeshAB = 64;  // entries (a, b) per CTA of the partial sums
+int mesh_partial_ctas(int chunks, int nff);
+size_t mesh_partial_elems(int chunks, int nd, int nff);
+// projection workspace of a context (complex elements)
+size_t ctx_bt_elems(const tufrg_ctx* c);
 // projections and products of every point; bt, fkey: packed workspaces.
 // rows: the state in the wedge layout (a point-group covariant state at the
 // representative l of each loop row), the projected couplings at the

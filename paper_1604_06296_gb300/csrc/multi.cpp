@@ -180,7 +180,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     off_wstate += (size_t)3 * c->nrow * c->nff * c->nff;
     off_state += (size_t)3 * c->nl * c->nff * c->nff;
     off_chi += (size_t)2 * c->nl * c->nff * c->nff;
-    off_bt += bt_region(c->ncx, 2 * c->proj.dmax + 1, c->nff, c->proj.gy_off[3]);
+    off_bt += ctx_bt_elems(c);
     off_fkey += fkey_elems(2 * c->proj.dmax + 1, c->nb);
     d.tab = c->d_tab;
     d.ext = c->d_ext;
@@ -215,10 +215,16 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.mesh_w = c->d_mesh_w;
     d.mesh_pts = c->d_mesh_pts;
     d.mesh_div = c->ncx * c->mesh_m;
+    d.mesh_e = c->d_mesh_e;
+    d.mesh_e_f = c->d_mesh_e_f;
+    d.mesh_lc = c->mesh_lc;
+    d.mesh_chunks = c->mesh_chunks;
     const int cnt[kKinds] = {
         tc ? table_ctas(d.n_ext) : 0,
         tc ? tc_rows_ctas(d.npair, d.row_lo, d.row_hi) : 0,
-        d.feedback && !c->mesh ? bond_ctas(d.ncx, d.nff) : 0,
+        !d.feedback ? 0
+        : c->mesh   ? mesh_partial_ctas(c->mesh_chunks, d.nff)
+                    : bond_ctas(d.ncx, d.nff),
         d.feedback ? dft_ctas(d.nd) : 0,
         grouped && d.feedback ? d.gy_off[3] : 0,
         contract_ctas(d.nl, d.nff, grouped),

@@ -226,8 +226,13 @@ __global__ void products_rows_kernel(const PointDesc* __restrict__ pts,
     put(Xh, e, nff, S, q >= 0 ? to_t<T>(rp[ch1 + q]) : (T)0);
   }
   __syncthreads();
+  // on a non-uniform mesh a channel's derivative vanishes off its own mesh
+  // (the images a row serves carry the representative's weights)
   const double sc = scaled ? pd.lam[1] : 1.0;
-  products_in_smem<T, NF>(sm, nff, sc, sc, dybase + off, chan);
+  const int l0 = pd.rowimg[pd.rowimg_ptr[row]].x;
+  const double sc_p = pd.mesh_w && pd.mesh_w[l0] == 0.0 ? 0.0 : sc;
+  const double sc_cd = pd.mesh_w && pd.mesh_w[pd.nl + l0] == 0.0 ? 0.0 : sc;
+  products_in_smem<T, NF>(sm, nff, sc_p, sc_cd, dybase + off, chan);
 }
 
 }  // namespace

@@ -280,70 +280,152 @@ __global__ void __launch_bounds__(256)
 }
 
 // Non-uniform meshes: the Fourier values of the keys as quadratures over the
-// source channel's mesh, Bh(X) = nl sum_{l'} w_S(l') e^{i l'.X} B^S(l') (the
-// factor nl undoes the phase sums' 1/nl), then F = C^T Bh(X) C.  One CTA per
-// (source, X); the mesh in chunks of kMeshChunk points whose weighted phases
-// sit in shared memory (l = -pi + 2 pi j / (nc m)).
-constexpr int kMeshChunk = 512;
+// source channel's mesh, Bh(X) = sum_{l'} E_S(X, l') B^S(l') with the
+// scale-independent E_S(X, l') = nl w_S(l') e^{i l'.X} (the factor nl undoes
+// the phase sums' 1/nl; P's weights for S = P, mesh_CD's for C and D), then
+// F = C^T Bh(X) C -- a complex-by-real matrix product over the mesh points,
+// split over chunks of points:
+//   mesh_dft_partial -- per (source, chunk, tile of 64 entries ab): the partial
+//     sums of every position X over the chunk's points, staged kMeshSub points
+//     at a time in shared memory; thread: kXT positions x 4 entries;
+//   mesh_dft_reduce  -- per (source, X): the chunks' sum in a fixed order, then
+//     the basis change.
+// kWedge: the state is given at the rows' representatives only and B(l) =
+// R^g B(l0) R^g^T is read through the (row, g) serving l, as in bond_dft1.
+constexpr int kMeshSub = 32;
+
+__host__ __device__ inline int mesh_ab_tiles(int nff) { return (nff * nff + kMeshAB - 1) / kMeshAB; }
+
+template <class T>
+__device__ __forceinline__ const typename C2<T>::type* mesh_e_of(const PointDesc& pd);
+template <>
+__device__ __forceinline__ const double2* mesh_e_of<double>(const PointDesc& pd) {
+  return pd.mesh_e;
+}
+template <>
+__device__ __forceinline__ const float2* mesh_e_of<float>(const PointDesc& pd) {
+  return pd.mesh_e_f;
+}
+
+template <class T, int kXT, bool kWedge>
+__global__ void __launch_bounds__(256)
+    mesh_dft_partial_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
+                            int np, const T* __restrict__ ybase,
+                            typename C2<T>::type* __restrict__ pbase) {
+  using V = typename C2<T>::type;
+  constexpr int kXP = 16 * kXT;  // positions per CTA (padded)
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nff = pd.nff, nff2 = nff * nff, nx = pd.nd * pd.nd, nl = pd.nl;
+  const int tiles = mesh_ab_tiles(nff), chunks = pd.mesh_chunks;
+  const int loc = blockIdx.x - prefix[p];
+  const int tile = loc % tiles, chunk = (loc / tiles) % chunks, src = loc / (tiles * chunks);
+  const int ab0 = tile * kMeshAB;
+  const int l0 = chunk * pd.mesh_lc, l1 = min(nl, l0 + pd.mesh_lc);
+  extern __shared__ double2 sm2[];
+  V* Es = reinterpret_cast<V*>(sm2);                           // [kMeshSub][kXP]
+  T* Bs = reinterpret_cast<T*>(Es + kMeshSub * kXP);           // [kMeshSub][kMeshAB]
+  int* toff = reinterpret_cast<int*>(Bs + kMeshSub * kMeshAB);  // [8][kMeshAB] wedge
+  const V* E = mesh_e_of<T>(pd) + (size_t)(src == 0 ? 0 : 1) * nx * nl;
+  const T* B = kWedge ? ybase + pd.off_wstate : ybase + pd.off_state + (size_t)src * nl * nff2;
+  if (kWedge)
+    for (int e = threadIdx.x; e < 8 * kMeshAB; e += blockDim.x) {
+      const int g = e / kMeshAB, ab = ab0 + e % kMeshAB;
+      int o = 0;
+      if (ab < nff2) {
+        const int a = ab / nff, b = ab - a * nff;
+        o = __ldg(pd.symperm + g * nff + a) * nff + __ldg(pd.symperm + g * nff + b) + 1;
+        if (__ldg(pd.symsign + g * nff + a) * __ldg(pd.symsign + g * nff + b) < 0) o = -o;
+      }
+      toff[e] = o;
+    }
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  V acc[kXT][4];
+#pragma unroll
+  for (int i = 0; i < kXT; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[i][k] = {0, 0};
+  for (int ls = l0; ls < l1; ls += kMeshSub) {
+    __syncthreads();  // the previous stage is consumed (and toff written)
+    for (int e = threadIdx.x; e < kMeshSub * kXP; e += blockDim.x) {
+      const int x = e / kMeshSub, j = e % kMeshSub;  // consecutive points per position
+      Es[j * kXP + x] = x < nx && ls + j < l1 ? E[(size_t)x * nl + ls + j] : V{0, 0};
+    }
+    for (int e = threadIdx.x; e < kMeshSub * kMeshAB; e += blockDim.x) {
+      const int j = e / kMeshAB, c = e % kMeshAB, l = ls + j;
+      T b = 0;
+      if (l < l1 && ab0 + c < nff2) {
+        if (kWedge) {
+          const int2 rg = pd.lrow[l];
+          const int o = toff[rg.y * kMeshAB + c];
+          const T v = __ldg(B + (size_t)(src * pd.nrow + rg.x) * nff2 + abs(o) - 1);
+          b = o > 0 ? v : -v;
+        } else {
+          b = __ldg(B + (size_t)l * nff2 + ab0 + c);
+        }
+      }
+      Bs[e] = b;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < kMeshSub; ++j) {
+      T bv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) bv[k] = Bs[j * kMeshAB + tx + 16 * k];
+#pragma unroll
+      for (int i = 0; i < kXT; ++i) {
+        const V e = Es[j * kXP + ty + 16 * i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc[i][k].x = fma(e.x, bv[k], acc[i][k].x);
+          acc[i][k].y = fma(e.y, bv[k], acc[i][k].y);
+        }
+      }
+    }
+  }
+  V* out = pbase + pd.off_bt + (size_t)(src * chunks + chunk) * nx * nff2;
+#pragma unroll
+  for (int i = 0; i < kXT; ++i) {
+    const int x = ty + 16 * i;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int ab = ab0 + tx + 16 * k;
+      if (x < nx && ab < nff2) out[(size_t)x * nff2 + ab] = acc[i][k];
+    }
+  }
+}
 
 template <class T, int NF>
 __global__ void __launch_bounds__(256)
-    mesh_dft_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int np,
-                    const T* __restrict__ ybase, typename C2<T>::type* __restrict__ fkbase) {
+    mesh_dft_reduce_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
+                           int np, const typename C2<T>::type* __restrict__ pbase,
+                           typename C2<T>::type* __restrict__ fkbase) {
   using V = typename C2<T>::type;
   const int p = point_of(prefix, np, blockIdx.x);
   const PointDesc& pd = pts[p];
   if (pd.skip && *pd.skip) return;
   const int nff = NF ? NF : pd.nff, nb = NF ? NF : pd.nb, nff2 = nff * nff;
-  const int nd = pd.nd, nl = pd.nl, div = pd.mesh_div, dmax = (nd - 1) / 2;
+  const int nd = pd.nd, nx = nd * nd, chunks = pd.mesh_chunks;
   const int loc = blockIdx.x - prefix[p];
-  const int dy = loc % nd, dx = (loc / nd) % nd, src = loc / (nd * nd);
+  const int x = loc % nx, src = loc / nx;
   extern __shared__ double2 sm2[];
   V* cs = reinterpret_cast<V*>(sm2);  // [nff][nb]
   V* Bh = cs + nff * nb;              // [nff][nff]
   V* tmp = Bh + nff2;                 // [nff][nb]
-  V* ph = tmp + nff * nb;             // [kMeshChunk] weighted phases
   for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, T());
-  const double* w = pd.mesh_w + (src == 0 ? 0 : nl);
-  const T* B = ybase + pd.off_state + (size_t)src * nl * nff2;
-  constexpr int kR = (kMaxNf * kMaxNf + 255) / 256;
-  V acc[kR];
-#pragma unroll
-  for (int r = 0; r < kR; ++r) acc[r] = {0, 0};
-  for (int l0 = 0; l0 < nl; l0 += kMeshChunk) {
-    const int cn = min(kMeshChunk, nl - l0);
-    __syncthreads();  // the previous chunk is consumed
-    for (int j = threadIdx.x; j < cn; j += blockDim.x) {
-      const int2 q = pd.mesh_pts[l0 + j];
-      // l.X / pi with 2X = (dx - dmax, dy - dmax)
-      const double t = ((double)((2 * q.x - div) * (dx - dmax)) +
-                        (double)((2 * q.y - div) * (dy - dmax))) / (2.0 * div);
-      double sn, c;
-      sincospi(t, &sn, &c);
-      const double wt = w[l0 + j] * nl;
-      ph[j] = {(T)(wt * c), (T)(wt * sn)};
+  const V* part = pbase + pd.off_bt + ((size_t)src * chunks * nx + x) * nff2;
+  for (int ab = threadIdx.x; ab < nff2; ab += blockDim.x) {
+    V acc = {0, 0};
+    for (int c = 0; c < chunks; ++c) {
+      const V v = part[(size_t)c * nx * nff2 + ab];
+      acc.x += v.x;
+      acc.y += v.y;
     }
-    __syncthreads();
-    for (int j = 0; j < cn; ++j) {
-      const V e = ph[j];
-      const T* Bl = B + (size_t)(l0 + j) * nff2;
-#pragma unroll
-      for (int r = 0; r < kR; ++r) {
-        const int ab = threadIdx.x + 256 * r;
-        if (ab < nff2) {
-          const T b = Bl[ab];
-          acc[r].x = fma(e.x, b, acc[r].x);
-          acc[r].y = fma(e.y, b, acc[r].y);
-        }
-      }
-    }
+    Bh[ab] = acc;
   }
-#pragma unroll
-  for (int r = 0; r < kR; ++r)
-    if (threadIdx.x + 256 * r < nff2) Bh[threadIdx.x + 256 * r] = acc[r];
   __syncthreads();
-  keys_from_bh(cs, Bh, tmp, nff, nb,
-               fkbase + pd.off_fkey + ((size_t)(src * nd + dx) * nd + dy) * nb * nb);
+  keys_from_bh(cs, Bh, tmp, nff, nb, fkbase + pd.off_fkey + ((size_t)src * nx + x) * nb * nb);
 }
 
 // Element offset of the state and couplings of channel t at output slot q
@@ -716,10 +798,22 @@ size_t dft2_smem(const MultiView& v) {
   return sizeof(typename C2<T>::type) *
          (2 * (size_t)v.nff_max * v.nb_max + (size_t)v.nff_max * v.nff_max + m);
 }
+// positions per thread of the mesh partial sums (16 threads per position
+// column): 6 up to 96 positions, 8 up to 128 (nd <= 11)
+int mesh_xt(const MultiView& v) {
+  int nx = 0;
+  for (const PointDesc& d : v.h) nx = std::max(nx, d.nd * d.nd);
+  return nx <= 96 ? 6 : 8;
+}
 template <class T>
-size_t mesh_dft_smem(const MultiView& v) {
+size_t mesh_partial_smem(int xt) {
+  return sizeof(typename C2<T>::type) * kMeshSub * 16 * xt + sizeof(T) * kMeshSub * kMeshAB +
+         sizeof(int) * 8 * kMeshAB;
+}
+template <class T>
+size_t mesh_reduce_smem(const MultiView& v) {
   return sizeof(typename C2<T>::type) *
-         (2 * (size_t)v.nff_max * v.nb_max + (size_t)v.nff_max * v.nff_max + kMeshChunk);
+         (2 * (size_t)v.nff_max * v.nb_max + (size_t)v.nff_max * v.nff_max);
 }
 template <class T>
 size_t overlap_smem(const MultiView& v) {
@@ -753,10 +847,23 @@ tufrg_status prepare_typed(const MultiView& v) {
   const int smem = smem_optin();
   // (the two contract kernels also hold a few bytes of static shared memory)
   if ((int)dft1_smem<T>(v) > smem || (int)dft2_smem<T>(v) > smem ||
-      (int)mesh_dft_smem<T>(v) > smem ||
+      (int)mesh_partial_smem<T>(8) > smem ||
       (int)overlap_smem<T>(v) > smem ||
       (int)contract_terms_smem<T>(v) + 64 > smem)
     return TUFRG_ERR_ARG;
+  if (v.mesh) {
+    int nx = 0;
+    for (const PointDesc& d : v.h) nx = std::max(nx, d.nd * d.nd);
+    if (nx > 128) return TUFRG_ERR_ARG;
+  }
+  TUFRG_CUDA(cudaFuncSetAttribute(mesh_dft_partial_kernel<T, 6, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  TUFRG_CUDA(cudaFuncSetAttribute(mesh_dft_partial_kernel<T, 6, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  TUFRG_CUDA(cudaFuncSetAttribute(mesh_dft_partial_kernel<T, 8, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  TUFRG_CUDA(cudaFuncSetAttribute(mesh_dft_partial_kernel<T, 8, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   TUFRG_CUDA(cudaFuncSetAttribute(bond_dft1_kernel<T, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   TUFRG_CUDA(cudaFuncSetAttribute(bond_dft1_kernel<T, true>,
@@ -768,7 +875,7 @@ tufrg_status prepare_typed(const MultiView& v) {
       e = cudaFuncSetAttribute(bond_dft2_kernel<T, NF>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mesh_dft_kernel<T, NF>,
+      e = cudaFuncSetAttribute(mesh_dft_reduce_kernel<T, NF>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(contract_terms_kernel<T, NF>, smem);
     if (e == cudaSuccess)
@@ -786,7 +893,21 @@ tufrg_status project_typed(const MultiView& v, const T* y, T* out, void* btv,
   using V = typename C2<T>::type;
   V* bt = reinterpret_cast<V*>(btv);
   V* fkey = reinterpret_cast<V*>(fkv);
-  if (v.total(kKindBond) > 0) {
+  if (v.total(kKindBond) > 0 && v.mesh) {
+    const int xt = mesh_xt(v);
+    const size_t sm = mesh_partial_smem<T>(xt);
+    const int n = v.total(kKindBond);
+    const int* pre = v.dprefix(kKindBond);
+    if (xt == 6 && rows)
+      mesh_dft_partial_kernel<T, 6, true><<<n, 256, sm, st>>>(v.d, pre, v.n, y, bt);
+    else if (xt == 6)
+      mesh_dft_partial_kernel<T, 6, false><<<n, 256, sm, st>>>(v.d, pre, v.n, y, bt);
+    else if (rows)
+      mesh_dft_partial_kernel<T, 8, true><<<n, 256, sm, st>>>(v.d, pre, v.n, y, bt);
+    else
+      mesh_dft_partial_kernel<T, 8, false><<<n, 256, sm, st>>>(v.d, pre, v.n, y, bt);
+    TUFRG_CUDA(cudaGetLastError());
+  } else if (v.total(kKindBond) > 0) {
     if (rows)
       bond_dft1_kernel<T, true><<<v.total(kKindBond), kDft1Threads, dft1_smem<T>(v), st>>>(
           v.d, v.dprefix(kKindBond), v.n, y, bt);
@@ -797,8 +918,9 @@ tufrg_status project_typed(const MultiView& v, const T* y, T* out, void* btv,
   }
   if (v.total(kKindDft) > 0 && v.mesh) {
     with_nf(v.nf_uniform, [&](auto nf) {
-      mesh_dft_kernel<T, decltype(nf)::value><<<v.total(kKindDft), 256, mesh_dft_smem<T>(v),
-                                                 st>>>(v.d, v.dprefix(kKindDft), v.n, y, fkey);
+      constexpr int NF = decltype(nf)::value;
+      mesh_dft_reduce_kernel<T, NF><<<v.total(kKindDft), 256, mesh_reduce_smem<T>(v), st>>>(
+          v.d, v.dprefix(kKindDft), v.n, bt, fkey);
     });
     TUFRG_CUDA(cudaGetLastError());
   } else if (v.total(kKindDft) > 0) {
@@ -848,6 +970,18 @@ int contract_ctas(int nl, int nff, bool grouped) {
 
 size_t bt_region(int ncx, int nd, int nff, int ny_total) {
   return std::max((size_t)3 * ncx * nd * nff * nff, (size_t)ny_total * hstride(nff));
+}
+
+int mesh_partial_ctas(int chunks, int nff) { return 3 * chunks * mesh_ab_tiles(nff); }
+
+size_t mesh_partial_elems(int chunks, int nd, int nff) {
+  return (size_t)3 * chunks * nd * nd * nff * nff;
+}
+
+size_t ctx_bt_elems(const tufrg_ctx* c) {
+  const int nd = 2 * c->proj.dmax + 1;
+  const size_t b = bt_region(c->ncx, nd, c->nff, c->proj.gy_off[3]);
+  return c->mesh ? std::max(b, mesh_partial_elems(c->mesh_chunks, nd, c->nff)) : b;
 }
 
 tufrg_status prepare_project_multi(const MultiView& v) {

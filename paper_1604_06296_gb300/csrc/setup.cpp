@@ -248,8 +248,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
   // are signed permutations g ranges over C4v; otherwise over {e, -1}
   // (R^g = diag(parity), which leaves the parity-allowed loops unchanged).
   std::vector<int> symperm, symsign;
-  const bool c4v =
-      !c->mesh && c->ncx == c->ncy && c->nfx == c->nfy && B.point_group(symperm, symsign);
+  const bool c4v = c->ncx == c->ncy && c->nfx == c->nfy && B.point_group(symperm, symsign);
   if (!c4v) {
     symperm.assign(8 * (size_t)nff, 0);
     symsign.assign(8 * (size_t)nff, 1);
@@ -260,14 +259,35 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
   std::vector<int> rowimg_ptr(1, 0);
   std::vector<char> served(c->nl, 0);
   const int hcx = c->ncx / 2, hcy = c->ncy / 2;
-  // a non-uniform mesh: one row per mesh point, l/2 in fine-grid steps
-  // (-pi/2 + pi j / (nc m)) / (2 pi / nf)
-  for (int l = 0; c->mesh && l < c->nl; ++l) {
-    const int div = c->ncx * c->mesh_m;
-    rowimg.push_back(make_int2(l, 0));
-    rowimg_ptr.push_back((int)rowimg.size());
-    rowshift.push_back(make_int2(-c->nfx / 4 + c->mesh_pts[l].x * (c->nfx / (2 * div)),
-                                 -c->nfy / 4 + c->mesh_pts[l].y * (c->nfy / (2 * div))));
+  // A non-uniform mesh: the same classes on the mesh's lattice (u = j - nc m
+  // / 2), where g serves l when the image g l is a mesh point with the same
+  // two quadrature weights (then the projections of a covariant state are
+  // covariant too); l/2 in fine-grid steps (-pi/2 + pi j / (nc m)) / (2 pi / nf)
+  if (c->mesh) {
+    const int div = c->ncx * c->mesh_m, hd = div / 2;
+    std::map<std::pair<int, int>, int> at;
+    for (int l = 0; l < c->nl; ++l) at[{c->mesh_pts[l].x, c->mesh_pts[l].y}] = l;
+    const double* wp = c->mesh_w.data();
+    const double* wc = wp + c->nl;
+    for (int l = 0; l < c->nl; ++l) {
+      if (served[l]) continue;
+      const int ux = c->mesh_pts[l].x - hd, uy = c->mesh_pts[l].y - hd;
+      for (int g = 0; g < 8; ++g) {
+        if (!c4v && g != 0 && g != 2) continue;
+        const int vx = kC4v[g][0][0] * ux + kC4v[g][0][1] * uy;
+        const int vy = kC4v[g][1][0] * ux + kC4v[g][1][1] * uy;
+        if (vx < -hd || vx >= div - hd || vy < -hd || vy >= div - hd) continue;
+        const auto it = at.find({vx + hd, vy + hd});
+        if (it == at.end()) continue;
+        const int lg = it->second;
+        if (served[lg] || wp[lg] != wp[l] || wc[lg] != wc[l]) continue;
+        served[lg] = 1;
+        rowimg.push_back(make_int2(lg, c4v ? g : 0));
+      }
+      rowimg_ptr.push_back((int)rowimg.size());
+      rowshift.push_back(make_int2(-c->nfx / 4 + c->mesh_pts[l].x * (c->nfx / (2 * div)),
+                                   -c->nfy / 4 + c->mesh_pts[l].y * (c->nfy / (2 * div))));
+    }
   }
   for (int jx = 0; !c->mesh && jx < c->ncx; ++jx)
     for (int jy = 0; jy < c->ncy; ++jy) {
@@ -499,7 +519,7 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
     TUFRG_CHECK(alloc(&c->d_chi, (size_t)2 * c->nl * nff * nff));
     TUFRG_CHECK(alloc(&c->d_V, (size_t)3 * c->nl * nff * nff));
     if (c->p.precision != TUFRG_FP64) TUFRG_CHECK(alloc(&c->d_y32, (size_t)3 * c->nl * nff * nff));
-    TUFRG_CHECK(alloc(&c->d_bt, bt_region(c->ncx, 2 * P.dmax + 1, nff, P.gy_off[3])));
+    TUFRG_CHECK(alloc(&c->d_bt, ctx_bt_elems(c)));
     TUFRG_CHECK(alloc(&c->d_fkey, fkey_elems(2 * P.dmax + 1, nb)));
     // the loop kernels write only the parity-allowed pairs
     TUFRG_CUDA(cudaMemsetAsync(c->d_chi, 0, sizeof(double) * 2 * c->nl * nff * nff, st));
@@ -601,6 +621,35 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
       }
     TUFRG_CHECK(upload(&c->d_mesh_w, c->mesh_w, st));
     TUFRG_CHECK(upload(&c->d_mesh_pts, c->mesh_pts, st));
+    // nl w(l) e^{i l.X} at the key positions X = ((dx - dmax)/2, (dy - dmax)/2)
+    // for both weight sets: l.X = pi n / (2 nc m) with an integer n, reduced
+    // modulo 4 nc m before the sine and cosine
+    const int nd = 2 * P.dmax + 1, nx = nd * nd;
+    std::vector<double2> e((size_t)2 * nx * c->nl);
+    std::vector<float2> e_f(e.size());
+    for (int ws = 0; ws < 2; ++ws)
+      for (int x = 0; x < nx; ++x) {
+        const int dx = x / nd - P.dmax, dy = x % nd - P.dmax;
+        for (int l = 0; l < c->nl; ++l) {
+          const int2 j = c->mesh_pts[l];
+          long long n = (long long)(2 * j.x - div) * dx + (long long)(2 * j.y - div) * dy;
+          n %= 4LL * div;
+          const double a = M_PI * (double)n / (2.0 * div);
+          const double w = c->mesh_w[(size_t)ws * c->nl + l] * c->nl;
+          const size_t o = ((size_t)ws * nx + x) * c->nl + l;
+          e[o] = make_double2(w * std::cos(a), w * std::sin(a));
+          e_f[o] = make_float2((float)e[o].x, (float)e[o].y);
+        }
+      }
+    TUFRG_CHECK(upload(&c->d_mesh_e, e, st));
+    TUFRG_CHECK(upload(&c->d_mesh_e_f, e_f, st));
+    // chunks of mesh points for about two waves of partial-sum CTAs
+    const int tiles = 3 * ((c->nff * c->nff + kMeshAB - 1) / kMeshAB);
+    int chunks = std::max(1, (2 * sm_count() + tiles - 1) / tiles);
+    int lc = (c->nl + chunks - 1) / chunks;
+    lc = (lc + 31) / 32 * 32;
+    c->mesh_lc = lc;
+    c->mesh_chunks = (c->nl + lc - 1) / lc;
   }
   TUFRG_CHECK(upload(&c->d_yphase, yph, st));
   TUFRG_CHECK(upload(&c->d_yphase_f, yph_f, st));
@@ -614,7 +663,8 @@ void free_device(tufrg_ctx* c) {
   view_free(c->view);
   void* own[] = {c->d_ext,     c->d_xiext, c->d_err, c->d_tab, c->d_lambda, c->d_partial,
                  c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey, c->d_y32,
-                 c->d_atensor, c->d_par,   c->d_mesh_w, c->d_mesh_pts};
+                 c->d_atensor, c->d_par,   c->d_mesh_w, c->d_mesh_pts, c->d_mesh_e,
+                 c->d_mesh_e_f};
   for (void* p : own)
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {

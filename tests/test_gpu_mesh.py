@@ -192,3 +192,72 @@ def test_invalid_meshes_and_refused_features(torch):
             call()
         assert e.value.status == -7
     sv.close()
+
+
+def _mesh_classes(nc, m, pts, wp, wc):
+    """Loop rows of a mesh: classes of l under the point-group elements whose
+    image lies in the zone without a fold and is a mesh point with the same
+    two weights (union-find over the pairs)."""
+    div, hd = nc * m, nc * m // 2
+    at = {tuple(p): i for i, p in enumerate(np.asarray(pts).tolist())}
+    parent = list(range(len(pts)))
+
+    def find(i):
+        while parent[i] != i:
+            parent[i] = parent[parent[i]]
+            i = parent[i]
+        return i
+
+    group = [((1, 0), (0, 1)), ((0, -1), (1, 0)), ((-1, 0), (0, -1)), ((0, 1), (-1, 0)),
+             ((1, 0), (0, -1)), ((-1, 0), (0, 1)), ((0, 1), (1, 0)), ((0, -1), (-1, 0))]
+    for i, (jx, jy) in enumerate(np.asarray(pts).tolist()):
+        ux, uy = jx - hd, jy - hd
+        for (a, b), (c, d) in group:
+            vx, vy = a * ux + b * uy, c * ux + d * uy
+            if not (-hd <= vx < hd and -hd <= vy < hd):
+                continue
+            j = at.get((vx + hd, vy + hd))
+            if j is not None and wp[j] == wp[i] and wc[j] == wc[i]:
+                parent[find(j)] = find(i)
+    return len({find(i) for i in range(len(pts))})
+
+
+def test_symmetric_meshes_get_point_group_rows(torch):
+    from paper_1604_06296_gb300 import Solver, _abi
+    for nc, m, nf, radius in ((6, 3, 36, 0.9), (8, 3, 48, 1.3), (4, 5, 40, 0.9)):
+        mesh = _mesh(nc, m, radius)
+        sv = Solver(T, TP, MU, U, W.bonds_for_shells(1), nc, nf,
+                    mesh=(m, mesh.points, mesh.w_p, mesh.w_cd))
+        nrow, _ = _abi.tufrg_row_info(sv.ctx)
+        assert nrow == _mesh_classes(nc, m, mesh.points, mesh.w_p, mesh.w_cd)
+        assert 3 * nrow < mesh.n
+        sv.close()
+    M = W.PRODUCTION_MESH
+    pts, wp, wc = W.channel_mesh(M["nc"], M["m"], M["p"], M["cd"])
+    sv = Solver(T, TP, MU, U, W.bonds_for_shells(3), M["nc"], 480, precision="bf16x3",
+                mesh=(M["m"], pts, wp, wc))
+    nrow, _ = _abi.tufrg_row_info(sv.ctx)
+    assert nrow == _mesh_classes(M["nc"], M["m"], pts, wp, wc) and 6 * nrow < len(pts)
+    sv.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_mesh_rk4_flow_from_a_non_covariant_state(torch, prec):
+    """A random start is not covariant: the flow runs on every mesh point."""
+    from oracle import flow as ofl
+    from oracle import mesh as ms
+    prob, mesh, sv = _pair(1, 6, 3, 36, prec)
+    y0 = _state(13, mesh, prob.nff, 0.2)
+    lam0, lam1, steps = 4.0, 1.0, 3
+    h = (np.log(lam1) - np.log(lam0)) / steps
+    y, res, _ = sv.flow(torch.from_numpy(y0).cuda(), lambda0=lam0, lambda_min=lam1,
+                        threshold=1e9, h0=abs(h), method="rk4")
+
+    def f(s, yy):
+        lam = np.exp(s)
+        return lam * ms.rhs_mesh(prob, mesh, lam, yy)
+
+    _, yref = ofl.rk4(f, np.log(lam0), y0, h, steps)
+    assert res["n_accepted"] == steps
+    assert _rel(y.cpu().numpy(), yref) <= (1e-9 if prec == "fp64" else 1e-4)
+    sv.close()

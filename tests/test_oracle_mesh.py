@@ -106,3 +106,47 @@ def test_production_mesh_sizes():
     # about the paper's 992 (P) and 6632 (C, D) points
     assert (wp > 0).sum() == 1080 and (wc > 0).sum() == 6384 and len(pts) == 6384
     assert abs(wp.sum() - 1) < 1e-13 and abs(wc.sum() - 1) < 1e-13
+
+
+def test_symmetric_mesh_flow_is_covariant_where_the_mesh_is():
+    """On a point-group symmetric mesh the flowing state, its projections and
+    its right-hand side satisfy X(g l) = C^g X(l) C^g^T for every (l, g)
+    whose image g l lies in the zone without a fold and is a mesh point with
+    the same two weights (the relation the GPU's wedge rows use); images that
+    need a fold do not (the half momentum moves by pi)."""
+    from oracle import flow as fl
+    from oracle import formfactors as ffm
+    nc, m = 6, 3
+    prob = make_problem(shells=1, nc=nc, nf=36, tp=-0.3, U=3.0)
+    mesh = ms.refined_mesh(nc, m, [(0.0, 0.0)], [(PI, PI), (PI, 0.0), (0.0, PI)], 0.9)
+
+    def f(s, y):
+        lam = np.exp(s)
+        return lam * ms.rhs_mesh(prob, mesh, lam, y)
+
+    _, y = fl.rk4(f, np.log(4.0), np.zeros((3, mesh.n, prob.nff, prob.nff)),
+                  np.log(0.5 / 4.0) / 3, 3)
+    V = ms.project_mesh(prob, mesh, y)
+    dy = ms.rhs_mesh(prob, mesh, 0.5, y)
+    div, hd = nc * m, nc * m // 2
+    at = {tuple(p): i for i, p in enumerate(mesh.points)}
+    u = mesh.points - hd
+    for X in (y, V, dy):
+        sc = np.abs(X).max()
+        assert sc > 0.05
+        held, broken = 0, 0.0
+        for S in ffm.POINT_GROUP:
+            C = prob.basis.rep_matrix(S)
+            for li in range(mesh.n):
+                v = S @ u[li]
+                lj = at.get(tuple((v + hd) % div))
+                if lj is None or mesh.w_p[lj] != mesh.w_p[li] or mesh.w_cd[lj] != mesh.w_cd[li]:
+                    continue
+                err = np.abs(X[:, lj] - C @ X[:, li] @ C.T).max() / sc
+                if np.all((v >= -hd) & (v < hd)):
+                    assert err <= 1e-13
+                    held += 1
+                else:
+                    broken = max(broken, err)
+        assert held > 6 * mesh.n
+        assert broken > 1e-7          # far above rounding: the fold is a real break
