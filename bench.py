@@ -709,7 +709,7 @@ def run_learned(args, rank, world, local):
     import torch
     import paper_1604_06296_gb300 as tufrg
     torch.cuda.set_device(local)
-    c = W.config(WORKLOAD)
+    c = W.config("cfg2")
     bonds = W.bonds_for_shells(c["shells"])
     held = -0.25
 
@@ -780,7 +780,7 @@ def run_learned(args, rank, world, local):
     best = {k: v["best_within_1pct"]["time_s"] for k, v in out_paths.items()
             if v["best_within_1pct"]}
     out = {"metric": METRIC, "workload": "learned loop surrogate, config 4",
-           "config": {"point": workload_desc(held), "train_tprime": train_tp,
+           "config": {"point": workload_desc(held, "cfg2"), "train_tprime": train_tp,
                       "mu": "4 t'", "samples": int(X.shape[0]), "network": "5 -> embed 25 -> "
                       "4 x 256 SiLU -> 98 (BF16 hi/lo operands, FP32 accumulation)",
                       "epochs": args.epochs, "batch": 4096, "judge_every": 8},

@@ -251,6 +251,8 @@ struct tufrg_ctx {
   void* d_ref_xis = nullptr;
   void* d_ref_ffs = nullptr;
   int* d_ref_bonds = nullptr;
+  void* d_ref_part = nullptr;  // [nseg][2][rows][npair] the row segments' sums
+  int ref_nseg = 1, ref_klen = 0;
   // non-uniform bosonic meshes (tufrg_setup_mesh): the l are mesh points
   // l = -pi + 2 pi j / (nc m) of the union of mesh_P and mesh_CD, with each
   // channel's quadrature weights (zero off its mesh)

@@ -346,18 +346,28 @@ __global__ void __launch_bounds__(256)
   for (int i = 0; i < kXT; ++i)
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[i][k] = {0, 0};
-  for (int ls = l0; ls < l1; ls += kMeshSub) {
-    __syncthreads();  // the previous stage is consumed (and toff written)
-    for (int e = threadIdx.x; e < kMeshSub * kXP; e += blockDim.x) {
+  // FP32: a stage's operands are loaded into registers during the previous
+  // stage's arithmetic, then stored to shared memory (FP64: loaded just
+  // before, the accumulators leave no registers for a second stage)
+  constexpr bool kPre = sizeof(T) == 4;
+  constexpr int kEPer = kMeshSub * kXP / 256, kBPer = kMeshSub * kMeshAB / 256;
+  V ereg[kEPer];
+  T breg[kBPer];
+  auto fetch = [&](int ls) {
+#pragma unroll
+    for (int u = 0; u < kEPer; ++u) {
+      const int e = threadIdx.x + 256 * u;
       const int x = e / kMeshSub, j = e % kMeshSub;  // consecutive points per position
-      Es[j * kXP + x] = x < nx && ls + j < l1 ? E[(size_t)x * nl + ls + j] : V{0, 0};
+      ereg[u] = x < nx && ls + j < l1 ? __ldg(E + (size_t)x * nl + ls + j) : V{0, 0};
     }
-    for (int e = threadIdx.x; e < kMeshSub * kMeshAB; e += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < kBPer; ++u) {
+      const int e = threadIdx.x + 256 * u;
       const int j = e / kMeshAB, c = e % kMeshAB, l = ls + j;
       T b = 0;
       if (l < l1 && ab0 + c < nff2) {
         if (kWedge) {
-          const int2 rg = pd.lrow[l];
+          const int2 rg = __ldg(pd.lrow + l);
           const int o = toff[rg.y * kMeshAB + c];
           const T v = __ldg(B + (size_t)(src * pd.nrow + rg.x) * nff2 + abs(o) - 1);
           b = o > 0 ? v : -v;
@@ -365,9 +375,23 @@ __global__ void __launch_bounds__(256)
           b = __ldg(B + (size_t)l * nff2 + ab0 + c);
         }
       }
-      Bs[e] = b;
+      breg[u] = b;
     }
+  };
+  __syncthreads();  // toff written
+  if (kPre && l0 < l1) fetch(l0);
+  for (int ls = l0; ls < l1; ls += kMeshSub) {
+    if (!kPre) fetch(ls);
+    __syncthreads();  // the previous stage is consumed
+#pragma unroll
+    for (int u = 0; u < kEPer; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      Es[(e % kMeshSub) * kXP + e / kMeshSub] = ereg[u];
+    }
+#pragma unroll
+    for (int u = 0; u < kBPer; ++u) Bs[threadIdx.x + 256 * u] = breg[u];
     __syncthreads();
+    if (kPre && ls + kMeshSub < l1) fetch(ls + kMeshSub);
 #pragma unroll 4
     for (int j = 0; j < kMeshSub; ++j) {
       T bv[4];
