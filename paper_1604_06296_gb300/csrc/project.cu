@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(256)
 // split over chunks of points:
 //   mesh_dft_partial -- per (source, chunk, tile of 64 entries ab): the partial
 //     sums of every position X over the chunk's points, staged kMeshSub points
-//     at a time in shared memory; thread: kXT positions x 4 entries;
+//     at a time in shared memory; thread: kXT adjacent positions x 4 adjacent
+//     entries;
 //   mesh_dft_reduce  -- per (source, X): the chunks' sum in a fixed order, then
 //     the basis change.
 // kWedge: the state is given at the rows' representatives only and B(l) =
@@ -308,7 +309,7 @@ __device__ __forceinline__ const float2* mesh_e_of<float>(const PointDesc& pd) {
 }
 
 template <class T, int kXT, bool kWedge>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     mesh_dft_partial_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
                             int np, const T* __restrict__ ybase,
                             typename C2<T>::type* __restrict__ pbase) {
@@ -346,10 +347,10 @@ __global__ void __launch_bounds__(256)
   for (int i = 0; i < kXT; ++i)
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[i][k] = {0, 0};
-  // FP32: a stage's operands are loaded into registers during the previous
-  // stage's arithmetic, then stored to shared memory (FP64: loaded just
-  // before, the accumulators leave no registers for a second stage)
-  constexpr bool kPre = sizeof(T) == 4;
+  // a stage's operands are loaded into registers, then stored to shared
+  // memory (kPre: during the previous stage's arithmetic; off: the registers
+  // are better spent on two CTAs per SM, FP32, or the FP64 accumulators)
+  constexpr bool kPre = false;
   constexpr int kEPer = kMeshSub * kXP / 256, kBPer = kMeshSub * kMeshAB / 256;
   V ereg[kEPer];
   T breg[kBPer];
@@ -392,18 +393,35 @@ __global__ void __launch_bounds__(256)
     for (int u = 0; u < kBPer; ++u) Bs[threadIdx.x + 256 * u] = breg[u];
     __syncthreads();
     if (kPre && ls + kMeshSub < l1) fetch(ls + kMeshSub);
-#pragma unroll 4
+#pragma unroll 2
     for (int j = 0; j < kMeshSub; ++j) {
+      // the thread's kXT adjacent positions and 4 adjacent entries: 16-byte
+      // shared-memory loads (the warp's two position slices are broadcasts)
       T bv[4];
+      V ev[kXT];
+      if constexpr (sizeof(T) == 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(Bs + j * kMeshAB + 4 * tx);
+        bv[0] = b4.x, bv[1] = b4.y, bv[2] = b4.z, bv[3] = b4.w;
+        const float4* ep = reinterpret_cast<const float4*>(Es + j * kXP + kXT * ty);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) bv[k] = Bs[j * kMeshAB + tx + 16 * k];
+        for (int i = 0; i < kXT / 2; ++i) {
+          const float4 q = ep[i];
+          ev[2 * i] = {q.x, q.y};
+          ev[2 * i + 1] = {q.z, q.w};
+        }
+      } else {
+        const double2* bp = reinterpret_cast<const double2*>(Bs + j * kMeshAB + 4 * tx);
+        const double2 b0 = bp[0], b1 = bp[1];
+        bv[0] = b0.x, bv[1] = b0.y, bv[2] = b1.x, bv[3] = b1.y;
+#pragma unroll
+        for (int i = 0; i < kXT; ++i) ev[i] = Es[j * kXP + kXT * ty + i];
+      }
 #pragma unroll
       for (int i = 0; i < kXT; ++i) {
-        const V e = Es[j * kXP + ty + 16 * i];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          acc[i][k].x = fma(e.x, bv[k], acc[i][k].x);
-          acc[i][k].y = fma(e.y, bv[k], acc[i][k].y);
+          acc[i][k].x = fma(ev[i].x, bv[k], acc[i][k].x);
+          acc[i][k].y = fma(ev[i].y, bv[k], acc[i][k].y);
         }
       }
     }
@@ -411,10 +429,10 @@ __global__ void __launch_bounds__(256)
   V* out = pbase + pd.off_bt + (size_t)(src * chunks + chunk) * nx * nff2;
 #pragma unroll
   for (int i = 0; i < kXT; ++i) {
-    const int x = ty + 16 * i;
+    const int x = kXT * ty + i;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int ab = ab0 + tx + 16 * k;
+      const int ab = ab0 + 4 * tx + k;
       if (x < nx && ab < nff2) out[(size_t)x * nff2 + ab] = acc[i][k];
     }
   }

@@ -643,9 +643,10 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
       }
     TUFRG_CHECK(upload(&c->d_mesh_e, e, st));
     TUFRG_CHECK(upload(&c->d_mesh_e_f, e_f, st));
-    // chunks of mesh points for about two waves of partial-sum CTAs
+    // chunks of mesh points for at most one wave of partial-sum CTAs at two
+    // CTAs per SM (the FP32 kernel's residency)
     const int tiles = 3 * ((c->nff * c->nff + kMeshAB - 1) / kMeshAB);
-    int chunks = std::max(1, (2 * sm_count() + tiles - 1) / tiles);
+    int chunks = std::max(1, 2 * sm_count() / tiles);
     int lc = (c->nl + chunks - 1) / chunks;
     lc = (lc + 31) / 32 * 32;
     c->mesh_lc = lc;
