@@ -87,7 +87,11 @@ typedef struct {
   int32_t n_bonds;        /* bond list: lattice vectors (x, y), host memory */
   const int32_t* bonds;   /* [n_bonds][2]; must be complete shells 0..n, n <= 6 */
   int32_t nc_x, nc_y;     /* coarse grid; even, >= 2*max|R|+1 */
-  int32_t nf_x, nf_y;     /* fine grid; nf % (2 nc) == 0 and nf % 4 == 0 */
+  int32_t nf_x, nf_y;     /* fine grid; nf % 4 == 0; nf % (2 nc) == 0 puts p +- l/2
+                             on the fine grid (table mode, every precision); other
+                             grids run in the analytic-xi mode, FP64 loops only:
+                             xi(p +- l/2) from per-row cosine tables (Sec. 3,
+                             Eq. hubb-disp), no refinement (TUFRG_ERR_STATE) */
   int32_t precision;      /* tufrg_precision of the loop contraction */
   int32_t feedback;       /* 1 = full inter-channel projections (Eqs. proj_VP..VD);
                              0 = projections off: V^P = V0 - P, V^C = V0 + C,

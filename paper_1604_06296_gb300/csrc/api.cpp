@@ -38,7 +38,10 @@ tufrg_status validate(const tufrg_params* p) {
     return TUFRG_ERR_ARG;
   if (p->nc_x < 2 || p->nc_y < 2 || (p->nc_x & 1) || (p->nc_y & 1)) return TUFRG_ERR_ARG;
   if (p->nf_x < 4 || p->nf_y < 4) return TUFRG_ERR_ARG;
-  if (p->nf_x % (2 * p->nc_x) || p->nf_y % (2 * p->nc_y)) return TUFRG_ERR_ARG;
+  // p +- l/2 on the fine grid (table mode) unless the loops are FP64, which
+  // also evaluate xi there analytically
+  if ((p->nf_x % (2 * p->nc_x) || p->nf_y % (2 * p->nc_y)) && p->precision != TUFRG_FP64)
+    return TUFRG_ERR_ARG;
   if (p->nf_x % 4 || p->nf_y % 4) return TUFRG_ERR_ARG;
   if ((long long)p->nf_x * p->nf_y > (1LL << 26)) return TUFRG_ERR_ARG;
   if ((long long)p->nc_x * p->nc_y > (1LL << 16)) return TUFRG_ERR_ARG;
@@ -275,7 +278,7 @@ tufrg_status tufrg_products(tufrg_ctx* c, const double* v_dev, const double* chi
 tufrg_status tufrg_set_refinement(tufrg_ctx* c, int32_t s, double kappa, double lambda_on,
                                   void* stream) {
   if (!c || !c->d_V) return TUFRG_ERR_ARG;
-  if (c->mesh) return TUFRG_ERR_STATE;  // refinement of the coarse grid's loop rows only
+  if (c->mesh || c->analytic) return TUFRG_ERR_STATE;  // table-mode coarse-grid rows only
   return tufrg::set_refinement(c, s, kappa, lambda_on, (cudaStream_t)stream);
 }
 

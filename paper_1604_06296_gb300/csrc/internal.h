@@ -252,6 +252,10 @@ struct tufrg_ctx {
   void* d_ref_ffs = nullptr;
   int* d_ref_bonds = nullptr;
   void* d_ref_part = nullptr;  // [nseg][2][rows][npair] the row segments' sums
+  // analytic-xi mode (nf not a multiple of 2 nc, FP64 loops): per loop row the
+  // cosines of p +- l/2 per direction, [nrow][2 nfx + 2 nfy]
+  bool analytic = false;
+  double* d_acos = nullptr;
   int ref_nseg = 1, ref_klen = 0;
   // non-uniform bosonic meshes (tufrg_setup_mesh): the l are mesh points
   // l = -pi + 2 pi j / (nc m) of the union of mesh_P and mesh_CD, with each

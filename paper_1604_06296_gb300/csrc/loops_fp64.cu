@@ -12,6 +12,8 @@
 //   chi_dot^ph weight = +(xi_a xi_b > 0 ? D : S) / 4
 // for xi_a = xi(p + l/2), xi_b = xi(p - l/2) (both loops share the pair since
 // xi is even).  The -1/4 and 1/4 are applied in the reduction.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace tufrg {
@@ -53,12 +55,34 @@ __device__ __forceinline__ void weights(const double4_32a& ta, const double4_32a
   wph = same ? D : S;
 }
 
-template <int RM>
+// Analytic-xi mode (fine grids whose points p +- l/2 fall between grid
+// points, nf not a multiple of 2 nc): per loop row the cosines
+// cos(p_x + l_x/2), cos(p_x - l_x/2) [nfx each], cos(p_y + l_y/2),
+// cos(p_y - l_y/2) [nfy each] (row stride alen), xi = -2t (cx + cy) -
+// 4t' cx cy - mu, and A, H per propagator as the per-scale table has them.
+struct AnalyticXi {
+  const double* acos;  // null: the table mode
+  int alen;
+  double t, tp, mu;
+};
+
+__device__ __forceinline__ double4_32a analytic_entry(double cx, double cy, const AnalyticXi& z,
+                                                      double om) {
+  double4_32a e;
+  e.x = -2.0 * z.t * (cx + cy) - 4.0 * z.tp * cx * cy - z.mu;
+  const double x = fabs(e.x), a = 1.0 / (om + x);
+  e.y = a;
+  e.z = x * (om + 3.0 * x) * a * a * a;
+  e.w = 0.0;
+  return e;
+}
+
+template <int RM, bool kAnalytic>
 __global__ void __launch_bounds__(NT)
 loops_fp64_kernel(const double4_32a* __restrict__ tab, const int2* __restrict__ kidx,
                   const double* __restrict__ F, const int2* __restrict__ shift,
                   const double* __restrict__ lam, int nfx, int nfy, int nrow, int kpad,
-                  int kchunk, int mpad, double* __restrict__ partial) {
+                  int kchunk, int mpad, double* __restrict__ partial, AnalyticXi z) {
   constexpr int MT = 16 * RM;
   __shared__ double sW[2][KC][LT];
   __shared__ double sF[KC][MT];
@@ -90,10 +114,16 @@ loops_fp64_kernel(const double4_32a* __restrict__ tab, const int2* __restrict__ 
       const int2 p = kidx[k0 + kk];
       double wpp = 0.0, wph = 0.0;
       if (l < nrow && p.x >= 0) {
-        const int2 s = shift[l];
-        const int ax = wrap(p.x + s.x, nfx), ay = wrap(p.y + s.y, nfy);
-        const int bx = wrap(p.x - s.x, nfx), by = wrap(p.y - s.y, nfy);
-        weights(tab[ax * nfy + ay], tab[bx * nfy + by], om, wpp, wph);
+        if (kAnalytic) {
+          const double* cr = z.acos + (size_t)l * z.alen;
+          weights(analytic_entry(cr[p.x], cr[2 * nfx + p.y], z, om),
+                  analytic_entry(cr[nfx + p.x], cr[2 * nfx + nfy + p.y], z, om), om, wpp, wph);
+        } else {
+          const int2 s = shift[l];
+          const int ax = wrap(p.x + s.x, nfx), ay = wrap(p.y + s.y, nfy);
+          const int bx = wrap(p.x - s.x, nfx), by = wrap(p.y - s.y, nfy);
+          weights(tab[ax * nfy + ay], tab[bx * nfy + by], om, wpp, wph);
+        }
       }
       sW[0][kk][ll] = wpp;
       sW[1][kk][ll] = wph;
@@ -189,21 +219,25 @@ tufrg_status launch_loops_fp64(tufrg_ctx* c, double* chi, cudaStream_t st) {
 tufrg_status launch_loops_fp64_rows(tufrg_ctx* c, cudaStream_t st, cudaEvent_t* ev) {
   dim3 grid((c->nrow + LT - 1) / LT, c->mtiles, c->ksplit);
   if (ev) TUFRG_CUDA(cudaEventRecord(ev[0], st));
-  switch (c->rm) {
-    case 1:
-      loops_fp64_kernel<1><<<grid, NT, 0, st>>>(c->d_tab, c->d_kidx, c->d_F, c->d_shift,
-                                                c->d_lambda, c->nfx, c->nfy, c->nrow, c->kpad,
-                                                c->kchunk, c->mpad, c->d_partial);
-      break;
-    case 2:
-      loops_fp64_kernel<2><<<grid, NT, 0, st>>>(c->d_tab, c->d_kidx, c->d_F, c->d_shift,
-                                                c->d_lambda, c->nfx, c->nfy, c->nrow, c->kpad,
-                                                c->kchunk, c->mpad, c->d_partial);
-      break;
-    default:
-      loops_fp64_kernel<4><<<grid, NT, 0, st>>>(c->d_tab, c->d_kidx, c->d_F, c->d_shift,
-                                                c->d_lambda, c->nfx, c->nfy, c->nrow, c->kpad,
-                                                c->kchunk, c->mpad, c->d_partial);
+  const AnalyticXi z{c->d_acos, 2 * (c->nfx + c->nfy), c->p.t, c->p.tp, c->p.mu};
+  auto go = [&](auto rm, auto an) {
+    loops_fp64_kernel<decltype(rm)::value, decltype(an)::value><<<grid, NT, 0, st>>>(
+        c->d_tab, c->d_kidx, c->d_F, c->d_shift, c->d_lambda, c->nfx, c->nfy, c->nrow, c->kpad,
+        c->kchunk, c->mpad, c->d_partial, z);
+  };
+  using T1 = std::integral_constant<int, 1>;
+  using T2 = std::integral_constant<int, 2>;
+  using T4 = std::integral_constant<int, 4>;
+  if (c->analytic) {
+    using A = std::true_type;
+    if (c->rm == 1) go(T1{}, A{});
+    else if (c->rm == 2) go(T2{}, A{});
+    else go(T4{}, A{});
+  } else {
+    using A = std::false_type;
+    if (c->rm == 1) go(T1{}, A{});
+    else if (c->rm == 2) go(T2{}, A{});
+    else go(T4{}, A{});
   }
   TUFRG_CUDA(cudaGetLastError());
   if (ev) TUFRG_CUDA(cudaEventRecord(ev[1], st));
@@ -218,19 +252,19 @@ tufrg_status launch_loops_fp64_buffers(const LoopBuffers& b, double* chi, cudaSt
   dim3 grid((b.nrow + LT - 1) / LT, b.mtiles, b.ksplit);
   switch (b.rm) {
     case 1:
-      loops_fp64_kernel<1><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
-                                                b.nfy, b.nrow, b.kpad, b.kchunk, b.mpad,
-                                                b.partial);
+      loops_fp64_kernel<1, false><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda,
+                                                       b.nfx, b.nfy, b.nrow, b.kpad, b.kchunk,
+                                                       b.mpad, b.partial, AnalyticXi{});
       break;
     case 2:
-      loops_fp64_kernel<2><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
-                                                b.nfy, b.nrow, b.kpad, b.kchunk, b.mpad,
-                                                b.partial);
+      loops_fp64_kernel<2, false><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda,
+                                                       b.nfx, b.nfy, b.nrow, b.kpad, b.kchunk,
+                                                       b.mpad, b.partial, AnalyticXi{});
       break;
     default:
-      loops_fp64_kernel<4><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda, b.nfx,
-                                                b.nfy, b.nrow, b.kpad, b.kchunk, b.mpad,
-                                                b.partial);
+      loops_fp64_kernel<4, false><<<grid, NT, 0, st>>>(b.tab, b.kidx, b.F, b.shift, b.lambda,
+                                                       b.nfx, b.nfy, b.nrow, b.kpad, b.kchunk,
+                                                       b.mpad, b.partial, AnalyticXi{});
   }
   TUFRG_CUDA(cudaGetLastError());
   TUFRG_CUDA(cudaMemsetAsync(chi, 0, sizeof(double) * 2 * b.nl * b.nff * b.nff, st));

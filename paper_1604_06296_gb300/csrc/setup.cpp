@@ -468,6 +468,32 @@ tufrg_status setup_device(tufrg_ctx* c, cudaStream_t st, const SetupShare& share
   TUFRG_CHECK(alloc(&c->d_err, 1));
   TUFRG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
 
+  // analytic-xi mode: l/2 off the fine grid (nf not a multiple of 2 nc); the
+  // FP64 loops take xi(p +- l/2) from per-row cosine tables (the row's
+  // representative l = (jx, jy), l/2 = -pi/2 + pi j / nc)
+  c->analytic = (c->nfx % (2 * c->ncx)) != 0 || (c->nfy % (2 * c->ncy)) != 0;
+  if (dl) {
+    c->d_acos = dl->d_acos;
+  } else if (c->analytic) {
+    const int alen = 2 * (c->nfx + c->nfy);
+    std::vector<double> ac((size_t)c->nrow * alen);
+    for (int r = 0; r < c->nrow; ++r) {
+      const int l = rowimg[rowimg_ptr[r]].x, jx = l / c->ncy, jy = l % c->ncy;
+      const double hx = -0.5 * M_PI + M_PI * jx / c->ncx, hy = -0.5 * M_PI + M_PI * jy / c->ncy;
+      double* row = ac.data() + (size_t)r * alen;
+      for (int i = 0; i < c->nfx; ++i) {
+        const double px = -M_PI + two_pi * i / c->nfx;
+        row[i] = std::cos(px + hx);
+        row[c->nfx + i] = std::cos(px - hx);
+      }
+      for (int i = 0; i < c->nfy; ++i) {
+        const double py = -M_PI + two_pi * i / c->nfy;
+        row[2 * c->nfx + i] = std::cos(py + hy);
+        row[2 * c->nfx + c->nfy + i] = std::cos(py - hy);
+      }
+    }
+    TUFRG_CHECK(upload(&c->d_acos, ac, st));
+  }
   if (!dl) {
     TUFRG_CHECK(upload(&c->d_shift, rowshift, st));
     TUFRG_CHECK(upload(&c->d_rowimg_ptr, rowimg_ptr, st));
@@ -674,7 +700,7 @@ void free_device(tufrg_ctx* c) {
                      c->d_rowimg,  c->d_lrow,      c->d_symperm, c->d_symsign, c->d_kidx,
                      c->d_lgather,
                      c->d_F,       c->d_pairidx,
-                     c->d_shift,   c->d_pair};
+                     c->d_shift,   c->d_pair,      c->d_acos};
     for (void* p : loops)
       if (p) cudaFree(p);
   }

@@ -93,7 +93,8 @@ def _params(abi, **over):
 
 
 @pytest.mark.parametrize("over", [
-    dict(lattice=1), dict(nc_x=7), dict(nf_x=100), dict(nf_y=88), dict(precision=5),
+    dict(lattice=1), dict(nc_x=7), dict(nf_x=100, precision=2), dict(nf_y=88, precision=1),
+    dict(nf_x=98), dict(precision=5),
     dict(feedback=2), dict(t=0.0), dict(U=float("nan")), dict(nc_x=2, nc_y=2, nf_x=8, nf_y=8),
 ])
 def test_setup_rejects_invalid_parameters_before_device_work(abi, over):
