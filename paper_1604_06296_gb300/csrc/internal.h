@@ -137,7 +137,7 @@ struct PointDesc {
   const double* mesh_w;
   const int2* mesh_pts;
   int mesh_div;       // nc m: the lattice of the mesh points
-  // [2][nd^2][nl] nl w(l) e^{i l.X} of mesh_P and mesh_CD at the key positions
+  // [2][nl][nd^2] nl w(l) e^{i l.X} of mesh_P and mesh_CD at the key positions
   // X; the key DFT sums mesh points in mesh_chunks chunks of mesh_lc
   const double2* mesh_e;
   const float2* mesh_e_f;
@@ -266,7 +266,7 @@ struct tufrg_ctx {
   std::vector<double> mesh_w;      // [2][nl]: weights of mesh_P, of mesh_CD
   double* d_mesh_w = nullptr;
   int2* d_mesh_pts = nullptr;
-  double2* d_mesh_e = nullptr;  // [2][nd^2][nl] nl w e^{i l.X} (FP64, FP32 copy)
+  double2* d_mesh_e = nullptr;  // [2][nl][nd^2] nl w e^{i l.X} (FP64, FP32 copy)
   float2* d_mesh_e_f = nullptr;
   int mesh_lc = 0, mesh_chunks = 0;
 

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256)
 // scale-independent E_S(X, l') = nl w_S(l') e^{i l'.X} (the factor nl undoes
 // the phase sums' 1/nl; P's weights for S = P, mesh_CD's for C and D), then
 // F = C^T Bh(X) C -- a complex-by-real matrix product over the mesh points,
-// split over chunks of points:
+// split over chunks of points (E stored point-major, [2][nl][nd^2]):
 //   mesh_dft_partial -- per (source, chunk, tile of 64 entries ab): the partial
 //     sums of every position X over the chunk's points, staged kMeshSub points
 //     at a time in shared memory; thread: kXT adjacent positions x 4 adjacent
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
   // a stage's operands are loaded into registers, then stored to shared
   // memory (kPre: during the previous stage's arithmetic; off: the registers
   // are better spent on two CTAs per SM, FP32, or the FP64 accumulators)
-  constexpr bool kPre = false;
+  constexpr bool kPre = sizeof(T) == 4;
   constexpr int kEPer = kMeshSub * kXP / 256, kBPer = kMeshSub * kMeshAB / 256;
   V ereg[kEPer];
   T breg[kBPer];
@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
     for (int u = 0; u < kEPer; ++u) {
       const int e = threadIdx.x + 256 * u;
-      const int x = e / kMeshSub, j = e % kMeshSub;  // consecutive points per position
-      ereg[u] = x < nx && ls + j < l1 ? __ldg(E + (size_t)x * nl + ls + j) : V{0, 0};
+      const int j = e / kXP, x = e % kXP;  // consecutive positions per point
+      ereg[u] = x < nx && ls + j < l1 ? __ldg(E + (size_t)(ls + j) * nx + x) : V{0, 0};
     }
 #pragma unroll
     for (int u = 0; u < kBPer; ++u) {
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
     for (int u = 0; u < kEPer; ++u) {
       const int e = threadIdx.x + 256 * u;
-      Es[(e % kMeshSub) * kXP + e / kMeshSub] = ereg[u];
+      Es[e] = ereg[u];  // [j][x]: contiguous, conflict-free
     }
 #pragma unroll
     for (int u = 0; u < kBPer; ++u) Bs[threadIdx.x + 256 * u] = breg[u];

@@ -662,7 +662,7 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
           n %= 4LL * div;
           const double a = M_PI * (double)n / (2.0 * div);
           const double w = c->mesh_w[(size_t)ws * c->nl + l] * c->nl;
-          const size_t o = ((size_t)ws * nx + x) * c->nl + l;
+          const size_t o = ((size_t)ws * c->nl + l) * nx + x;  // [2][nl][nd^2]
           e[o] = make_double2(w * std::cos(a), w * std::sin(a));
           e_f[o] = make_float2((float)e[o].x, (float)e[o].y);
         }
