@@ -1286,10 +1286,63 @@ def run_point(args, rank, world, local):
         e1.record()
         e1.synchronize()
         ems.append(e0.elapsed_time(e1))
-    e2e = {"value": world * len(ems) / (sum(ems) / 1e3), "unit": UNIT,
+    serial = world * len(ems) / (sum(ems) / 1e3)
+    # the same steps pipelined as a caller streaming states would run them:
+    # step i's host-to-device copy (copy stream) and step i-1's device-to-host
+    # copy (a second copy stream) overlap step i-1's and i's RHS; two pinned
+    # host buffers and two device staging buffers per direction, the RHS on
+    # one fixed (y, dy) pair (its captured graph is reused); every step's
+    # copies are inside the timed region
+    ks = torch.cuda.current_stream()
+    cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
+    yh = [y_host, y_host.clone().pin_memory()]
+    dyh = [dy_host, torch.empty_like(dy_host).pin_memory()]
+    yst = [solver.empty(3), solver.empty(3)]
+    dyst = [solver.empty(3), solver.empty(3)]
+    ev = lambda: torch.cuda.Event()
+    h2d, in_free, out_ready, d2h = ([ev(), ev()] for _ in range(4))
+    n_pipe = max(args.steps, 10)
+
+    def pipelined(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ks)
+        cs_in.wait_event(e0)
+        cs_out.wait_event(e0)
+        for i in range(n):
+            bi = i % 2
+            if i >= 2:
+                cs_in.wait_event(in_free[bi])
+            with torch.cuda.stream(cs_in):
+                yst[bi].copy_(yh[bi], non_blocking=True)
+            h2d[bi].record(cs_in)
+            ks.wait_event(h2d[bi])
+            y_dev.copy_(yst[bi])
+            in_free[bi].record(ks)
+            if i >= 2:
+                ks.wait_event(d2h[bi])
+            solver.rhs(0.5, y_dev, out=dy_dev)
+            dyst[bi].copy_(dy_dev)
+            out_ready[bi].record(ks)
+            cs_out.wait_event(out_ready[bi])
+            with torch.cuda.stream(cs_out):
+                dyh[bi].copy_(dyst[bi], non_blocking=True)
+            d2h[bi].record(cs_out)
+        ks.wait_event(d2h[(n - 1) % 2])
+        ks.wait_event(d2h[n % 2])
+        e1.record(ks)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    pipelined(4)
+    pipe_ms = pipelined(n_pipe)
+    e2e = {"value": world * n_pipe / (pipe_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": y_host.numel() * 8, "d2h_bytes_per_step": dy_host.numel() * 8,
-           "call": "tufrg_rhs with pinned host copies in/out"}
-    del y_host, dy_host, y_dev, dy_dev
+           "call": "tufrg_rhs with pinned host copies in/out, pipelined over "
+                   f"{n_pipe} steps (copies of neighbouring steps overlap the RHS)",
+           "serial_value": serial,
+           "serial": "each step's copy in, RHS and copy out one after another (L2 flushed "
+                     "before each step)"}
+    del y_host, dy_host, y_dev, dy_dev, yh, dyh, yst, dyst
 
     if pg:
         pg.destroy_process_group()
