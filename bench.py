@@ -668,9 +668,14 @@ def run_large_batch(args, rank, world, local):
         f1.record()
         f1.synchronize()
         ems.append(f0.elapsed_time(f1))
-    e2e = {"value": world * batch.n * len(ems) / (sum(ems) / 1e3), "unit": UNIT,
+    n_pipe = max(args.steps, 10)
+    pipe_ms = pipelined_e2e_ms(torch, lambda y, dy: batch.rhs(0.5, y, out=dy), y_host, dy_host,
+                               y_dev, dy_dev, batch.empty, n_pipe)
+    e2e = {"value": world * batch.n * n_pipe / (pipe_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": y_host.numel() * 8, "d2h_bytes_per_step": dy_host.numel() * 8,
-           "call": "tufrg_batch_rhs of all points with pinned host copies in/out"}
+           "call": "tufrg_batch_rhs of all points with pinned host copies in/out, pipelined "
+                   f"over {n_pipe} steps (copies of neighbouring steps overlap the RHS)",
+           "serial_value": world * batch.n * len(ems) / (sum(ems) / 1e3)}
     per_stage = 10  # the grouped projections (Nff = 25): one more kernel per stage
     launches = per_stage + (6 * per_stage + 3) * attempts
 
@@ -1158,6 +1163,55 @@ def run_mesh(args, rank, world, local):
     return 0
 
 
+def pipelined_e2e_ms(torch, rhs, y_host, dy_host, y_dev, dy_dev, empty, n):
+    """Device time (ms) of n end-to-end steps pipelined as a caller streaming
+    states runs them: step i's host-to-device copy (one copy stream) and step
+    i-1's device-to-host copy (a second copy stream) overlap the RHS of the
+    neighbouring steps; two pinned host buffers and two device staging buffers
+    per direction, the RHS always on the same (y_dev, dy_dev) pair (its
+    captured graph is reused).  Every step's copies are inside the timed
+    region.  One warm-up pass of 4 steps first."""
+    ks = torch.cuda.current_stream()
+    cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
+    yh = [y_host, y_host.clone().pin_memory()]
+    dyh = [dy_host, torch.empty_like(dy_host).pin_memory()]
+    yst, dyst = [empty(), empty()], [empty(), empty()]
+    h2d, in_free, out_ready, d2h = ([torch.cuda.Event(), torch.cuda.Event()] for _ in range(4))
+
+    def run(k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ks)
+        cs_in.wait_event(e0)
+        cs_out.wait_event(e0)
+        for i in range(k):
+            b = i % 2
+            if i >= 2:
+                cs_in.wait_event(in_free[b])
+            with torch.cuda.stream(cs_in):
+                yst[b].copy_(yh[b], non_blocking=True)
+            h2d[b].record(cs_in)
+            ks.wait_event(h2d[b])
+            y_dev.copy_(yst[b])
+            in_free[b].record(ks)
+            if i >= 2:
+                ks.wait_event(d2h[b])
+            rhs(y_dev, dy_dev)
+            dyst[b].copy_(dy_dev)
+            out_ready[b].record(ks)
+            cs_out.wait_event(out_ready[b])
+            with torch.cuda.stream(cs_out):
+                dyh[b].copy_(dyst[b], non_blocking=True)
+            d2h[b].record(cs_out)
+        ks.wait_event(d2h[(k - 1) % 2])
+        ks.wait_event(d2h[k % 2])
+        e1.record(ks)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    run(4)
+    return run(n)
+
+
 def run_point(args, rank, world, local):
     """One phase-diagram point per rank (the production or the large point)."""
     import torch
@@ -1287,54 +1341,9 @@ def run_point(args, rank, world, local):
         e1.synchronize()
         ems.append(e0.elapsed_time(e1))
     serial = world * len(ems) / (sum(ems) / 1e3)
-    # the same steps pipelined as a caller streaming states would run them:
-    # step i's host-to-device copy (copy stream) and step i-1's device-to-host
-    # copy (a second copy stream) overlap step i-1's and i's RHS; two pinned
-    # host buffers and two device staging buffers per direction, the RHS on
-    # one fixed (y, dy) pair (its captured graph is reused); every step's
-    # copies are inside the timed region
-    ks = torch.cuda.current_stream()
-    cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
-    yh = [y_host, y_host.clone().pin_memory()]
-    dyh = [dy_host, torch.empty_like(dy_host).pin_memory()]
-    yst = [solver.empty(3), solver.empty(3)]
-    dyst = [solver.empty(3), solver.empty(3)]
-    ev = lambda: torch.cuda.Event()
-    h2d, in_free, out_ready, d2h = ([ev(), ev()] for _ in range(4))
     n_pipe = max(args.steps, 10)
-
-    def pipelined(n):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(ks)
-        cs_in.wait_event(e0)
-        cs_out.wait_event(e0)
-        for i in range(n):
-            bi = i % 2
-            if i >= 2:
-                cs_in.wait_event(in_free[bi])
-            with torch.cuda.stream(cs_in):
-                yst[bi].copy_(yh[bi], non_blocking=True)
-            h2d[bi].record(cs_in)
-            ks.wait_event(h2d[bi])
-            y_dev.copy_(yst[bi])
-            in_free[bi].record(ks)
-            if i >= 2:
-                ks.wait_event(d2h[bi])
-            solver.rhs(0.5, y_dev, out=dy_dev)
-            dyst[bi].copy_(dy_dev)
-            out_ready[bi].record(ks)
-            cs_out.wait_event(out_ready[bi])
-            with torch.cuda.stream(cs_out):
-                dyh[bi].copy_(dyst[bi], non_blocking=True)
-            d2h[bi].record(cs_out)
-        ks.wait_event(d2h[(n - 1) % 2])
-        ks.wait_event(d2h[n % 2])
-        e1.record(ks)
-        e1.synchronize()
-        return e0.elapsed_time(e1)
-
-    pipelined(4)
-    pipe_ms = pipelined(n_pipe)
+    pipe_ms = pipelined_e2e_ms(torch, lambda y, dy: solver.rhs(0.5, y, out=dy), y_host, dy_host,
+                               y_dev, dy_dev, solver.empty, n_pipe)
     e2e = {"value": world * n_pipe / (pipe_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": y_host.numel() * 8, "d2h_bytes_per_step": dy_host.numel() * 8,
            "call": "tufrg_rhs with pinned host copies in/out, pipelined over "
@@ -1342,7 +1351,7 @@ def run_point(args, rank, world, local):
            "serial_value": serial,
            "serial": "each step's copy in, RHS and copy out one after another (L2 flushed "
                      "before each step)"}
-    del y_host, dy_host, y_dev, dy_dev, yh, dyh, yst, dyst
+    del y_host, dy_host, y_dev, dy_dev
 
     if pg:
         pg.destroy_process_group()
