@@ -73,20 +73,25 @@ struct Prec<TUFRG_3XTF32> {
   };
 };
 
-template <int PREC>
+// CU: use of the A-operand collector buffer -- 0: none, 1: fill (A read from
+// shared memory and kept), 2: lastuse (A from the collector, then released)
+template <int PREC, int CU = 0>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t acc) {
+#define TUFRG_MMA(KIND, COLL)                                                          \
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"                          \
+               " tcgen05.mma.cta_group::1.kind::" KIND COLL " [%0], %1, %2, %3, p;\n}\n" \
+               ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc))
   if constexpr (PREC == TUFRG_BF16X3) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    if constexpr (CU == 1) TUFRG_MMA("f16", ".collector::a::fill");
+    else if constexpr (CU == 2) TUFRG_MMA("f16", ".collector::a::lastuse");
+    else TUFRG_MMA("f16", "");
   } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    if constexpr (CU == 1) TUFRG_MMA("tf32", ".collector::a::fill");
+    else if constexpr (CU == 2) TUFRG_MMA("tf32", ".collector::a::lastuse");
+    else TUFRG_MMA("tf32", "");
   }
+#undef TUFRG_MMA
 }
 
 // approximate reciprocal (PTX rcp.approx: relative error below 2^-22)
@@ -423,9 +428,11 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
             const uint32_t d = tmem + (uint32_t)((2 * set + ch) * npad);
             const uint64_t ah = smem_desc(st + (2 * ch) * kWTile + o);
             const uint64_t al = smem_desc(st + (2 * ch + 1) * kWTile + o);
-            mma<PREC>(d, ah, bh, idesc, !(first && kk == 0));
+            // the two products of W_hi in a row: the second takes W_hi from
+            // the tensor core's A collector instead of shared memory
+            mma<PREC, 1>(d, ah, bh, idesc, !(first && kk == 0));
+            mma<PREC, 2>(d, ah, bl, idesc, 1);
             mma<PREC>(d, al, bh, idesc, 1);
-            mma<PREC>(d, ah, bl, idesc, 1);
           }
         }
         mma_commit(bar_empty + 8 * s);
