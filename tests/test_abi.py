@@ -112,3 +112,37 @@ def test_null_arguments_rejected(abi):
     assert L.tufrg_check(None, None) == -1
     assert L.tufrg_selftest_wait(None, 1000, None) == -1
     assert abi.tufrg_status_string(-3) == "non-finite state"
+
+
+def test_setup_mesh_rejects_invalid_meshes_before_device_work(abi):
+    """tufrg_setup_mesh validates the mesh on the host (odd m, square coarse
+    grid, nf a multiple of 2 nc m, points in range and distinct, weights
+    non-negative summing to one per channel, every point in a mesh)."""
+    p, keep = _params(abi, nc_x=6, nc_y=6, nf_x=36, nf_y=36)
+    pts, wp, wc = W.channel_mesh(6, 3, ([(0.0, 0.0)], 0.9), ([(-np.pi, -np.pi)], 0.9))
+    bad = []
+    bad.append((2, pts, wp, wc))                                   # even m
+    out = pts.copy()
+    out[0, 0] = 18
+    bad.append((3, out, wp, wc))                                   # outside the lattice
+    dup = pts.copy()
+    dup[1] = dup[0]
+    bad.append((3, dup, wp, wc))                                   # a point twice
+    bad.append((3, pts, 2 * wp, wc))                               # weights not summing to one
+    neg = wc.copy()
+    neg[np.argmax(neg)] *= -1
+    bad.append((3, pts, wp, neg))                                  # negative weight
+    i = int(np.argmax(wp))
+    bad.append((3, pts, np.where(np.arange(len(wp)) == i, 0.0, wp), wc))  # sum off by w_i
+    for m, q, a, b in bad:
+        with pytest.raises(abi.TufrgError) as e:
+            abi.tufrg_setup_mesh(p, m, q, a, b)
+        assert e.value.status == -1
+    p2, keep2 = _params(abi, nc_x=6, nc_y=8, nf_x=36, nf_y=48)
+    with pytest.raises(abi.TufrgError) as e:                       # rectangular coarse grid
+        abi.tufrg_setup_mesh(p2, 3, pts, wp, wc)
+    assert e.value.status == -1
+    p3, keep3 = _params(abi, nc_x=6, nc_y=6, nf_x=24, nf_y=24)
+    with pytest.raises(abi.TufrgError) as e:                       # nf not a multiple of 2 nc m
+        abi.tufrg_setup_mesh(p3, 3, pts, wp, wc)
+    assert e.value.status == -1
