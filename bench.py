@@ -47,8 +47,8 @@ L2_FLUSH_BYTES = 512 << 20
 GROUPED_NFF = 21
 
 
-def workload_desc(tp, name=WORKLOAD):
-    c = W.config(name)
+def workload_desc(tp, name=WORKLOAD, **over):
+    c = W.config(name, **over)
     r2 = int(max((b ** 2).sum() for b in np.asarray(W.bonds_for_shells(c["shells"]))))
     rad = f"{int(r2 ** 0.5)}" if int(r2 ** 0.5) ** 2 == r2 else f"sqrt({r2})"
     return (f"t-t' Hubbard square lattice, t'={tp}, mu=4t', U={c['U']}; coarse "
@@ -1100,6 +1100,8 @@ def run_mesh(args, rank, world, local):
     if rank != 0:
         return 0
     c = W.config("cfg2")
+    if args.shells:
+        c["shells"] = args.shells
     M = W.PRODUCTION_MESH
     bonds = W.bonds_for_shells(c["shells"])
     tp = c["tp"]
@@ -1154,7 +1156,8 @@ def run_mesh(args, rank, world, local):
            "value": rates["meshes"]["rhs_evals_per_s"], "n_gpus": 1, "steps": n, "warmup": 1,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": args.precision, "data": "synthetic",
-           "config": {"workload": workload_desc(tp, "cfg2") + "; mesh_P 1080 points (5x5 "
+           "config": {"workload": workload_desc(tp, "cfg2", shells=c["shells"]) +
+                                  "; mesh_P 1080 points (5x5 "
                                   "refinement within 0.6 of l=0), mesh_CD 6384 points (within "
                                   "1.6 of l=0 and (pi,pi)); nf 480",
                       "l2": "inputs resident, not flushed (RHS rate of repeated calls)"},
@@ -1448,6 +1451,10 @@ def main():
                          "(table, contraction, split-K combination), for a profiler")
     ap.add_argument("--points", type=int, default=256, help="scan: points per GPU")
     ap.add_argument("--epochs", type=int, default=40, help="learned: training epochs")
+    ap.add_argument("--shells", type=int, default=0,
+                    help="mesh: bond shells of the form-factor basis (0: the production "
+                         "point's 3, Nff 13; 5: the paper's fifth-nearest-neighbour "
+                         "truncation, Nff 25)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
