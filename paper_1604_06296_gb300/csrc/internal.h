@@ -142,6 +142,16 @@ struct PointDesc {
   const double2* mesh_e;
   const float2* mesh_e_f;
   int mesh_lc, mesh_chunks;
+  // FP32 arithmetic on the tensor cores (null: the CUDA-core quadrature):
+  // BF16 hi/lo operands A [2][mesh_mpad][mesh_lp] (the phases' real and
+  // imaginary parts per position) and B [3][mesh_npad][mesh_lp] (the state,
+  // packed per right-hand side); the points in mesh_kz splits of mesh_kbs
+  // K-blocks of 64
+  const void* mesh_ahi;
+  const void* mesh_alo;
+  void* mesh_bhi;
+  void* mesh_blo;
+  int mesh_lp, mesh_mpad, mesh_npad, mesh_kz, mesh_kbs;
 };
 
 // kinds of multi-point launches: per point, a fixed number of CTAs
@@ -269,6 +279,12 @@ struct tufrg_ctx {
   double2* d_mesh_e = nullptr;  // [2][nl][nd^2] nl w e^{i l.X} (FP64, FP32 copy)
   float2* d_mesh_e_f = nullptr;
   int mesh_lc = 0, mesh_chunks = 0;
+  // tensor-core quadrature operands (FP32-arithmetic contexts)
+  void* d_mesh_ahi = nullptr;
+  void* d_mesh_alo = nullptr;
+  void* d_mesh_bhi = nullptr;
+  void* d_mesh_blo = nullptr;
+  int mesh_lp = 0, mesh_mpad = 0, mesh_npad = 0, mesh_kz = 0, mesh_kbs = 0;
 
   // tensor-core loop path (precision BF16X3 / 3XTF32)
   int tc_npad = 0, tc_kpad = 0, tc_nkb = 0, tc_nrow_pad = 0;
@@ -449,6 +465,12 @@ int mesh_partial_ctas(int chunks, int nff);
 size_t mesh_partial_elems(int chunks, int nd, int nff);
 // projection workspace of a context (complex elements)
 size_t ctx_bt_elems(const tufrg_ctx* c);
+// tensor-core quadrature of the mesh key DFT (FP32 arithmetic): packs the
+// state (wedge: from the rows' representatives) and writes the FP32 partial
+// products [3][kz][mpad][npad] to part
+tufrg_status prepare_mesh_tc();
+tufrg_status launch_mesh_tc(const PointDesc& d, const float* y, bool wedge, float* part, int* err,
+                            cudaStream_t st);
 // projections and products of every point; bt, fkey: packed workspaces.
 // rows: the state in the wedge layout (a point-group covariant state at the
 // representative l of each loop row), the projected couplings at the

@@ -219,6 +219,15 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.mesh_e_f = c->d_mesh_e_f;
     d.mesh_lc = c->mesh_lc;
     d.mesh_chunks = c->mesh_chunks;
+    d.mesh_ahi = c->d_mesh_ahi;
+    d.mesh_alo = c->d_mesh_alo;
+    d.mesh_bhi = c->d_mesh_bhi;
+    d.mesh_blo = c->d_mesh_blo;
+    d.mesh_lp = c->mesh_lp;
+    d.mesh_mpad = c->mesh_mpad;
+    d.mesh_npad = c->mesh_npad;
+    d.mesh_kz = c->mesh_kz;
+    d.mesh_kbs = c->mesh_kbs;
     const int cnt[kKinds] = {
         tc ? table_ctas(d.n_ext) : 0,
         tc ? tc_rows_ctas(d.npair, d.row_lo, d.row_hi) : 0,

@@ -470,6 +470,40 @@ __global__ void __launch_bounds__(256)
   keys_from_bh(cs, Bh, tmp, nff, nb, fkbase + pd.off_fkey + ((size_t)src * nx + x) * nb * nb);
 }
 
+// The tensor-core quadrature's partial products (FP32 [3][kz][mpad][npad],
+// rows 2x and 2x + 1 the real and imaginary part of position x) added over
+// the splits in a fixed order, then the basis change.  One CTA per (source, X).
+template <int NF>
+__global__ void __launch_bounds__(256)
+    mesh_tc_reduce_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
+                          int np, const float* __restrict__ part, float2* __restrict__ fkbase) {
+  using V = float2;
+  const int p = point_of(prefix, np, blockIdx.x);
+  const PointDesc& pd = pts[p];
+  if (pd.skip && *pd.skip) return;
+  const int nff = NF ? NF : pd.nff, nb = NF ? NF : pd.nb, nff2 = nff * nff;
+  const int nd = pd.nd, nx = nd * nd, kz = pd.mesh_kz, mpad = pd.mesh_mpad, npad = pd.mesh_npad;
+  const int loc = blockIdx.x - prefix[p];
+  const int x = loc % nx, src = loc / nx;
+  extern __shared__ double2 sm2[];
+  V* cs = reinterpret_cast<V*>(sm2);  // [nff][nb]
+  V* Bh = cs + nff * nb;              // [nff][nff]
+  V* tmp = Bh + nff2;                 // [nff][nb]
+  for (int e = threadIdx.x; e < nff * nb; e += blockDim.x) cs[e] = coef_at(pd, e, float());
+  const float* pr = part + (size_t)src * kz * mpad * npad + (size_t)(2 * x) * npad;
+  for (int ab = threadIdx.x; ab < nff2; ab += blockDim.x) {
+    V acc = {0.f, 0.f};
+    for (int z = 0; z < kz; ++z) {
+      const float* q = pr + (size_t)z * mpad * npad + ab;
+      acc.x += q[0];
+      acc.y += q[npad];
+    }
+    Bh[ab] = acc;
+  }
+  __syncthreads();
+  keys_from_bh(cs, Bh, tmp, nff, nb, fkbase + pd.off_fkey + ((size_t)src * nx + x) * nb * nb);
+}
+
 // Element offset of the state and couplings of channel t at output slot q
 // (transfer momentum l): l in the full layout, or row q in the wedge layout.
 __device__ __forceinline__ size_t slot_offset(const PointDesc& pd, int rows, int t, int q, int l,
@@ -897,6 +931,7 @@ tufrg_status prepare_typed(const MultiView& v) {
     int nx = 0;
     for (const PointDesc& d : v.h) nx = std::max(nx, d.nd * d.nd);
     if (nx > 128) return TUFRG_ERR_ARG;
+    TUFRG_CHECK(prepare_mesh_tc());
   }
   TUFRG_CUDA(cudaFuncSetAttribute(mesh_dft_partial_kernel<T, 6, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -919,6 +954,9 @@ tufrg_status prepare_typed(const MultiView& v) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mesh_dft_reduce_kernel<T, NF>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mesh_tc_reduce_kernel<NF>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(contract_terms_kernel<T, NF>, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(overlap_kernel<T, NF>,
@@ -935,7 +973,14 @@ tufrg_status project_typed(const MultiView& v, const T* y, T* out, void* btv,
   using V = typename C2<T>::type;
   V* bt = reinterpret_cast<V*>(btv);
   V* fkey = reinterpret_cast<V*>(fkv);
-  if (v.total(kKindBond) > 0 && v.mesh) {
+  const bool mesh_tc = sizeof(T) == 4 && v.mesh && v.h[0].mesh_ahi;
+  if (v.total(kKindBond) > 0 && mesh_tc) {
+    // the quadrature on the tensor cores (the partials in the bt region)
+    TUFRG_CHECK(launch_mesh_tc(v.h[0], reinterpret_cast<const float*>(y) +
+                                           (rows ? v.h[0].off_wstate : v.h[0].off_state),
+                               rows, reinterpret_cast<float*>(bt) + 2 * v.h[0].off_bt, v.d_err,
+                               st));
+  } else if (v.total(kKindBond) > 0 && v.mesh) {
     const int xt = mesh_xt(v);
     const size_t sm = mesh_partial_smem<T>(xt);
     const int n = v.total(kKindBond);
@@ -961,6 +1006,14 @@ tufrg_status project_typed(const MultiView& v, const T* y, T* out, void* btv,
   if (v.total(kKindDft) > 0 && v.mesh) {
     with_nf(v.nf_uniform, [&](auto nf) {
       constexpr int NF = decltype(nf)::value;
+      if constexpr (sizeof(T) == 4) {
+        if (mesh_tc) {
+          mesh_tc_reduce_kernel<NF><<<v.total(kKindDft), 256, mesh_reduce_smem<T>(v), st>>>(
+              v.d, v.dprefix(kKindDft), v.n,
+              reinterpret_cast<const float*>(bt) + 2 * v.h[0].off_bt, fkey);
+          return;
+        }
+      }
       mesh_dft_reduce_kernel<T, NF><<<v.total(kKindDft), 256, mesh_reduce_smem<T>(v), st>>>(
           v.d, v.dprefix(kKindDft), v.n, bt, fkey);
     });
@@ -1022,8 +1075,13 @@ size_t mesh_partial_elems(int chunks, int nd, int nff) {
 
 size_t ctx_bt_elems(const tufrg_ctx* c) {
   const int nd = 2 * c->proj.dmax + 1;
-  const size_t b = bt_region(c->ncx, nd, c->nff, c->proj.gy_off[3]);
-  return c->mesh ? std::max(b, mesh_partial_elems(c->mesh_chunks, nd, c->nff)) : b;
+  size_t b = bt_region(c->ncx, nd, c->nff, c->proj.gy_off[3]);
+  if (c->mesh) b = std::max(b, mesh_partial_elems(c->mesh_chunks, nd, c->nff));
+  // the tensor-core quadrature's FP32 partials [3][kz][mpad][npad] (a complex
+  // element holds four of them in FP32 contexts)
+  if (c->mesh && c->d_mesh_ahi)
+    b = std::max(b, ((size_t)3 * c->mesh_kz * c->mesh_mpad * c->mesh_npad + 3) / 4);
+  return b;
 }
 
 tufrg_status prepare_project_multi(const MultiView& v) {

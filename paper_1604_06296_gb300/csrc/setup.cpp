@@ -669,6 +669,45 @@ tufrg_status setup_proj(tufrg_ctx* c, cudaStream_t st) {
       }
     TUFRG_CHECK(upload(&c->d_mesh_e, e, st));
     TUFRG_CHECK(upload(&c->d_mesh_e_f, e_f, st));
+    if (c->p.precision != TUFRG_FP64) {
+      // tensor-core operands of the FP32 quadrature: A [2][mpad][lp] BF16 hi/lo
+      // (row 2x: Re, 2x + 1: Im of the phases of position x; zero padding),
+      // B [3][npad][lp] packed per right-hand side; splits of the points for
+      // about one CTA per SM
+      const int lp = (c->nl + 63) / 64 * 64;
+      const int mpad = (2 * nx + 127) / 128 * 128;
+      const int npad = (c->nff * c->nff + 127) / 128 * 128;
+      std::vector<uint16_t> ahi((size_t)2 * mpad * lp, 0), alo(ahi.size(), 0);
+      for (int ws = 0; ws < 2; ++ws)
+        for (int l = 0; l < c->nl; ++l)
+          for (int x = 0; x < nx; ++x) {
+            const double2 v = e[((size_t)ws * c->nl + l) * nx + x];
+            const double part[2] = {v.x, v.y};
+            for (int q = 0; q < 2; ++q) {
+              const float f = (float)part[q];
+              const uint16_t h = bf16_rne(f);
+              const size_t o = ((size_t)ws * mpad + 2 * x + q) * lp + l;
+              ahi[o] = h;
+              alo[o] = bf16_rne(f - bf16_value(h));
+            }
+          }
+      uint16_t *dah = nullptr, *dal = nullptr, *dbh = nullptr, *dbl = nullptr;
+      TUFRG_CHECK(upload(&dah, ahi, st));
+      c->d_mesh_ahi = dah;
+      TUFRG_CHECK(upload(&dal, alo, st));
+      c->d_mesh_alo = dal;
+      TUFRG_CHECK(alloc(&dbh, (size_t)3 * npad * lp));
+      c->d_mesh_bhi = dbh;
+      TUFRG_CHECK(alloc(&dbl, (size_t)3 * npad * lp));
+      c->d_mesh_blo = dbl;
+      const int tiles = 3 * (mpad / 128) * (npad / 128), nkb = lp / 64;
+      int kz = std::max(1, std::min(nkb, sm_count() / tiles));
+      c->mesh_kbs = (nkb + kz - 1) / kz;
+      c->mesh_kz = (nkb + c->mesh_kbs - 1) / c->mesh_kbs;
+      c->mesh_lp = lp;
+      c->mesh_mpad = mpad;
+      c->mesh_npad = npad;
+    }
     // chunks of mesh points for at most one wave of partial-sum CTAs at two
     // CTAs per SM (the FP32 kernel's residency)
     const int tiles = 3 * ((c->nff * c->nff + kMeshAB - 1) / kMeshAB);
@@ -691,7 +730,7 @@ void free_device(tufrg_ctx* c) {
   void* own[] = {c->d_ext,     c->d_xiext, c->d_err, c->d_tab, c->d_lambda, c->d_partial,
                  c->d_chi,     c->d_V,     c->d_bt,  c->d_fkey, c->d_y32,
                  c->d_atensor, c->d_par,   c->d_mesh_w, c->d_mesh_pts, c->d_mesh_e,
-                 c->d_mesh_e_f};
+                 c->d_mesh_e_f, c->d_mesh_ahi, c->d_mesh_alo, c->d_mesh_bhi, c->d_mesh_blo};
   for (void* p : own)
     if (p) cudaFree(p);
   if (!c->borrowed_loops) {
