@@ -143,21 +143,11 @@ __global__ void __launch_bounds__(kThr, 1) mesh_gemm_kernel(MeshTcArgs a) {
   if (nk > 1) load(1, 1);
   for (int kb = 0; kb < nk; ++kb) {
     const int st_i = kb % kStages;
-    if (kb + 2 < nk) {
-      // stage (kb + 2) % 3 was read by the MMAs of K-block kb - 1
-      if (kb >= 1 && !mbar_wait(ctrl + 8 * ((kb - 1) % kStages), ((kb - 1) / kStages) & 1)) {
-        atomicOr(a.err, 16);
-        *abort_flag = 1;
-      }
-      __syncthreads();
-      if (*abort_flag) break;
-      load(kb + 2, (kb + 2) % kStages);
-      asm volatile("cp.async.wait_group 2;" ::: "memory");
-    } else if (kb + 1 < nk) {
+    // this K-block's copies (groups up to kb + 1 are committed)
+    if (kb + 1 < nk)
       asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
+    else
       asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
@@ -184,6 +174,17 @@ __global__ void __launch_bounds__(kThr, 1) mesh_gemm_kernel(MeshTcArgs a) {
       mma_commit(ctrl + 8 * st_i);
     }
     last = kb;
+    if (kb + 2 < nk) {
+      // refill the stage of K-block kb - 1 once its MMAs have completed (the
+      // MMAs of kb are queued behind them meanwhile)
+      if (kb >= 1 && !mbar_wait(ctrl + 8 * ((kb - 1) % kStages), ((kb - 1) / kStages) & 1)) {
+        atomicOr(a.err, 16);
+        *abort_flag = 1;
+      }
+      __syncthreads();
+      if (*abort_flag) break;
+      load(kb + 2, (kb + 2) % kStages);
+    }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (last >= 0 && !mbar_wait(ctrl + 8 * (last % kStages), (last / kStages) & 1)) {
