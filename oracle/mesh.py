@@ -25,7 +25,7 @@ gives the meshes only as a figure):
     nf a multiple of 2 nc m), the products of a channel at its own mesh.
 
 Pins (tests/test_oracle_mesh.py): the uniform coarse mesh reproduces
-projections.project and rhs.rhs; a mesh refined everywhere reproduces them on
+projections.project and rhs.rhs; rhs_mesh_at equals rhs_mesh at its points; a mesh refined everywhere reproduces them on
 the uniform grid of nc m points (coarse grids that do not alias the bond
 sums, so the term lists agree); the quadrature weights sum to one per
 channel; entries off a channel's mesh stay zero.
@@ -131,6 +131,43 @@ def project_pair_mesh(prob, mesh, target, source, B, w):
     T = np.zeros((mesh.n, nb * nb), dtype=np.complex128)
     np.add.at(T.T, t[:, 0] * nb + t[:, 1], (ph_y * F[None, :]).T)
     return np.einsum("mi,nj,lij->lmn", c, c, T.reshape(mesh.n, nb, nb)).real
+
+
+def project_pair_mesh_at(prob, mesh, target, source, B, w, out):
+    """project_pair_mesh at the mesh points out only (the source's quadrature
+    still runs over its whole mesh)."""
+    c = prob.basis.coefficients()
+    nb = c.shape[1]
+    Bt = np.einsum("ai,bj,lab->lij", c, c, B)
+    t, X, Y = _terms(prob, SIGNATURES[(target, source)])
+    lv = mesh.l_values
+    F = np.einsum("l,lt,lt->t", w, np.exp(1j * (lv @ X.T)), Bt[:, t[:, 2], t[:, 3]])
+    ph_y = np.exp(1j * (lv[out] @ Y.T))                  # [len(out)][terms]
+    T = np.zeros((len(out), nb * nb), dtype=np.complex128)
+    np.add.at(T.T, t[:, 0] * nb + t[:, 1], (ph_y * F[None, :]).T)
+    return np.einsum("mi,nj,lij->lmn", c, c, T.reshape(len(out), nb, nb)).real
+
+
+def rhs_mesh_at(prob, mesh, lam, y, out):
+    """rhs_mesh at the mesh points out only: [3][len(out)][Nff][Nff]."""
+    out = np.asarray(out)
+    P, C, D = y
+    bare = prob.bare_matrix()[None]
+    wp, wc = mesh.w_p, mesh.w_cd
+    if prob.feedback:
+        VP = bare - P[out] + project_pair_mesh_at(prob, mesh, "P", "C", C, wc, out) \
+            + project_pair_mesh_at(prob, mesh, "P", "D", D, wc, out)
+        VC = bare - project_pair_mesh_at(prob, mesh, "C", "P", P, wp, out) + C[out] \
+            + project_pair_mesh_at(prob, mesh, "C", "D", D, wc, out)
+        VD = bare - project_pair_mesh_at(prob, mesh, "D", "P", P, wp, out) \
+            + project_pair_mesh_at(prob, mesh, "D", "C", C, wc, out) + D[out]
+    else:
+        VP, VC, VD = bare - P[out], bare + C[out], bare + D[out]
+    pp, ph = chi_dot_at(prob, lam, mesh.l_values[out])
+    dy = products(np.stack([VP, VC, VD]), pp, ph)
+    dy[0][mesh.w_p[out] == 0] = 0.0
+    dy[1:, mesh.w_cd[out] == 0] = 0.0
+    return dy
 
 
 def project_mesh(prob, mesh, y):

@@ -261,3 +261,32 @@ def test_mesh_rk4_flow_from_a_non_covariant_state(torch, prec):
     assert res["n_accepted"] == steps
     assert _rel(y.cpu().numpy(), yref) <= (1e-9 if prec == "fp64" else 1e-4)
     sv.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+def test_production_mesh_rhs_sampled(torch, prec):
+    """The production-sized meshes (mesh_P 1080, mesh_CD 6384 points, coarse
+    24x24, Nff 13, fine 480x480): one right-hand side on every mesh point,
+    checked against the oracle at 12 points spread over the mesh (zone
+    boundary, refined and coarse cells, points off mesh_P).  BF16x3 runs the
+    key quadrature on the tensor cores, FP64 on the CUDA cores."""
+    from oracle import mesh as ms
+    from paper_1604_06296_gb300 import Solver
+    c = W.config("cfg2")
+    M = W.PRODUCTION_MESH
+    pts, wp, wc = W.channel_mesh(M["nc"], M["m"], M["p"], M["cd"])
+    mesh = ms.Mesh(M["nc"], M["m"], pts.astype(np.int64), wp, wc)
+    tp = c["tp"]
+    prob = make_problem(shells=c["shells"], nc=c["nc"], nf=c["nf"], t=c["t"], tp=tp, mu=4 * tp,
+                        U=c["U"])
+    sv = Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"], c["nf"],
+                precision=prec, mesh=(M["m"], pts, wp, wc))
+    y = W.random_state(21, mesh.n, prob.nff, 0.1)
+    y[0][wp == 0] = 0.0
+    y[1:, wc == 0] = 0.0
+    got = sv.rhs(0.3, torch.from_numpy(y).cuda()).cpu().numpy()
+    out = np.linspace(0, mesh.n - 1, 12).astype(int)
+    assert (wp[out] == 0).any() and (wp[out] > 0).any()
+    ref = ms.rhs_mesh_at(prob, mesh, 0.3, y, out)
+    assert _rel(got[:, out], ref) <= (1e-10 if prec == "fp64" else 2e-5)
+    sv.close()

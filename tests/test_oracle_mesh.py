@@ -150,3 +150,17 @@ def test_symmetric_mesh_flow_is_covariant_where_the_mesh_is():
                     broken = max(broken, err)
         assert held > 6 * mesh.n
         assert broken > 1e-7          # far above rounding: the fold is a real break
+
+
+@pytest.mark.parametrize("feedback", [True, False])
+def test_rhs_at_selected_points_equals_the_full_rhs(feedback):
+    nc, m = 6, 3
+    prob = make_problem(shells=2, nc=nc, nf=36, tp=-0.3, U=2.8, feedback=feedback)
+    mesh = ms.refined_mesh(nc, m, [(0.0, 0.0)], [(PI, PI), (PI, 0.0)], 0.9)
+    y = W.random_state(12, mesh.n, prob.nff, 0.3)
+    y[0][mesh.w_p == 0] = 0.0
+    y[1:, mesh.w_cd == 0] = 0.0
+    full = ms.rhs_mesh(prob, mesh, 0.25, y)
+    out = np.array([0, 3, mesh.n // 2, mesh.n - 1, 7])
+    got = ms.rhs_mesh_at(prob, mesh, 0.25, y, out)
+    assert np.abs(got - full[:, out]).max() <= 1e-13 * np.abs(full).max()
