@@ -93,3 +93,26 @@ def test_refinement_rejects_bad_settings(torch):
             sv.set_refinement(*args)
         assert e.value.status == -1
     sv.close()
+
+
+def test_refined_loops_production_size_sampled(torch):
+    """The production point (coarse 24x24, Nff 13, fine 480x480, BF16x3) with
+    refinement s = 5, kappa = 8 at Lambda = 0.03: the loops of every l on the
+    GPU against the oracle's refined loops at six l (zone boundary, interior,
+    near the pairing momentum 0)."""
+    from oracle import refine as rf
+    from paper_1604_06296_gb300 import Solver
+    c = W.config("cfg2")
+    tp = c["tp"]
+    prob = make_problem(shells=c["shells"], nc=c["nc"], nf=c["nf"], t=c["t"], tp=tp, mu=4 * tp,
+                        U=c["U"])
+    sv = Solver(c["t"], tp, 4 * tp, c["U"], W.bonds_for_shells(c["shells"]), c["nc"], c["nf"],
+                precision="bf16x3")
+    sv.set_refinement(s=5, kappa=8.0, lambda_on=0.1)
+    om = 0.03
+    got = sv.loops(om).cpu().numpy()
+    ls = np.array([0, 13, 150, 288, 301, 575])
+    pp, ph = rf.chi_dot_refined(prob, om, s=5, kappa=8.0, lam_on=0.1, l_index=ls)
+    for ch, ref in enumerate((pp, ph)):
+        assert np.abs(got[ch][ls] - ref).max() <= 1e-5 * np.abs(ref).max()
+    sv.close()
