@@ -28,7 +28,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kMT = 128;  // rows (positions' parts) per CTA
 constexpr int kNT = 128;  // columns (entries) per CTA
 constexpr int kKB = 64;   // points per K-block (128 bytes of bf16)
-constexpr int kThr = 128;
+constexpr int kThr = 512;  // 16 warps: warp w reads TMEM lanes 32 (w % 4), columns 32 (w / 4)
 constexpr int kStages = 3;
 
 struct MeshTcArgs {
@@ -47,15 +47,16 @@ __device__ __forceinline__ void split_bf16(float v, bf16& hi, bf16& lo) {
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// B_S[n][l] for 32 x 32 tiles (n: entries, l: points) through shared memory:
-// reads coalesced along the entries of one point, writes along the points.
+// B_S[n][l] for tiles of 64 points x 32 entries through shared memory: reads
+// coalesced along the entries of one point, writes along the points as
+// BF16 pairs (two adjacent points per thread).
 __global__ void __launch_bounds__(256)
     mesh_pack_kernel(MeshTcArgs a, const float* __restrict__ y, int wedge) {
-  __shared__ float tile[32][33];
-  const int l0 = blockIdx.x * 32, n0 = blockIdx.y * 32, s = blockIdx.z;
+  __shared__ float tile[64][33];
+  const int l0 = blockIdx.x * 64, n0 = blockIdx.y * 32, s = blockIdx.z;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 8 rows of 32
   const int nff2 = a.nff * a.nff;
-  for (int r = ty; r < 32; r += 8) {
+  for (int r = ty; r < 64; r += 8) {
     const int l = l0 + r, n = n0 + tx;
     float v = 0.f;
     if (l < a.nl && n < nff2) {
@@ -74,12 +75,13 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
-    const int n = n0 + r, l = l0 + tx;  // n < npad, l < lp by the grid
-    bf16 hi, lo;
-    split_bf16(tile[tx][r], hi, lo);
+    const int n = n0 + r, l = l0 + 2 * tx;  // n < npad, l + 1 < lp by the grid
+    bf16 h0, g0, h1, g1;
+    split_bf16(tile[2 * tx][r], h0, g0);
+    split_bf16(tile[2 * tx + 1][r], h1, g1);
     const size_t o = ((size_t)s * a.npad + n) * a.lp + l;
-    a.bhi[o] = hi;
-    a.blo[o] = lo;
+    *reinterpret_cast<__nv_bfloat162*>(a.bhi + o) = __halves2bfloat162(h0, h1);
+    *reinterpret_cast<__nv_bfloat162*>(a.blo + o) = __halves2bfloat162(g0, g1);
   }
 }
 
@@ -195,11 +197,13 @@ __global__ void __launch_bounds__(kThr, 1) mesh_gemm_kernel(MeshTcArgs a) {
   const bool ok = !*abort_flag && nk > 0 && last == nk - 1;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // partials [s][z][mpad][npad]: the thread's row m, 16 entries per load
-  float* out = a.part + (((size_t)s * a.kz + z) * a.mpad + m0 + warp * 32 + lane) * a.npad + n0;
-  for (int c0 = 0; c0 < kNT; c0 += 16) {
+  constexpr int kCols = kNT / (kThr / 128);  // columns per warp
+  const int quad = warp & 3, part = warp >> 2;
+  float* out = a.part + (((size_t)s * a.kz + z) * a.mpad + m0 + quad * 32 + lane) * a.npad + n0;
+  for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += 16) {
     float v[16];
     if (ok) {
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
     } else {
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = 0.f;  // no points in this split (or a timeout)
@@ -248,7 +252,7 @@ tufrg_status launch_mesh_tc(const PointDesc& d, const float* y, bool wedge, floa
   a.npad = d.mesh_npad;
   a.kz = d.mesh_kz;
   a.kbs = d.mesh_kbs;
-  const dim3 pg((unsigned)(a.lp / 32), (unsigned)(a.npad / 32), 3);
+  const dim3 pg((unsigned)(a.lp / 64), (unsigned)(a.npad / 32), 3);
   mesh_pack_kernel<<<pg, 256, 0, st>>>(a, y, wedge ? 1 : 0);
   TUFRG_CUDA(cudaGetLastError());
   const dim3 gg((unsigned)(a.mpad / kMT), (unsigned)(a.npad / kNT), (unsigned)(3 * a.kz));
