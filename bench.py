@@ -756,8 +756,8 @@ def run_learned(args, rank, world, local):
     """Learned loop surrogate at production size (coarse 24x24, Nff 13, fine
     480x480): trained on ~1e6 exact loop rows of 16 seeded t' (mu = 4t',
     t' = -0.25 held out); flows at the held-out point with the surrogate
-    (judge every 8 accepted steps) against the mixed and FP64 GPU flows at
-    equal Lambda_c accuracy."""
+    (judge every 8 accepted steps; exact loops in BF16x3 or in FP64) against
+    the mixed and FP64 GPU flows at equal Lambda_c accuracy."""
     import torch
     import paper_1604_06296_gb300 as tufrg
     torch.cuda.set_device(local)
@@ -816,7 +816,9 @@ def run_learned(args, rank, world, local):
     ladder = [(1e-6, 1e-8), (1e-5, 1e-7), (1e-4, 1e-6)]
     out_paths = {}
     for name, s, tol in (("fp64", ref_s, None), (args.precision, probe, None),
-                         ("learned_tol1e-3", probe, 1e-3), ("learned_tol1e-2", probe, 1e-2)):
+                         ("learned_tol1e-3", probe, 1e-3), ("learned_tol1e-2", probe, 1e-2),
+                         ("learned_fp64_judge_tol1e-3", ref_s, 1e-3),
+                         ("learned_fp64_judge_tol1e-2", ref_s, 1e-2)):
         s.attach_surrogate(sur if tol else None, judge_every=8, tol=tol or 1e-3)
         timed(s, *ladder[-1])  # warm-up (graph capture)
         rungs = []
