@@ -155,7 +155,7 @@ struct TcArgs {
   const PointDesc* pts;
   const int4* items;  // (point, l-tile, first K-block, K-blocks), costliest first
   int n_items;
-  int* counter;       // next item (zero before the launch)
+  int* counter;       // items claimed after the first gridDim.x (zero before the launch)
   float* partial;     // per point [ksplit][2][npad][nrow_pad] at off_partial
   int* err;
   int kbps;           // K-blocks per full item: split = first K-block / kbps
@@ -218,9 +218,15 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
   uint32_t g = 0;  // K-blocks this CTA has put through the pipeline
   uint32_t j = 0;  // items this CTA has finished (phase of bar_done)
   int tma_last = -1;  // warp 0, lane 0: last K-block (count g) whose F it requested
+  // thread 0: the CTA's next item -- its own index first (the launch has at
+  // most one CTA per item), then claimed from the counter during the current
+  // item's last K-blocks, so that the claim's round trip overlaps them
+  // (-1: claim at the top of the loop)
+  int next_it = blockIdx.x;
   for (;;) {
     if (threadIdx.x == 0) {
-      const int it = atomicAdd(a.counter, 1);
+      const int it = next_it >= 0 ? next_it : (int)gridDim.x + atomicAdd(a.counter, 1);
+      next_it = -1;
       const int4 v = it < a.n_items ? a.items[it] : make_int4(-1, 0, 0, 0);
       s_item->x = v.x;
       s_item->y = v.y;
@@ -357,6 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1) loops_tc_kernel(TcArgs a) {
                         static_cast<const unsigned char*>(pd.tmap) + 128, k0, 0,
                         bar_tma + 8 * s);
             tma_last = (int)gk;
+            if (kb == (cnt > 2 ? cnt - 2 : 0)) next_it = (int)gridDim.x + atomicAdd(a.counter, 1);
           }
           unsigned char* stg = gbase + (st - base);
           // (after the item's last K-block the ring gathers this one's first
