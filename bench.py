@@ -833,7 +833,7 @@ def run_learned(args, rank, world, local):
         s.attach_surrogate(None)
     best = {k: v["best_within_1pct"]["time_s"] for k, v in out_paths.items()
             if v["best_within_1pct"]}
-    out = {"metric": METRIC, "workload": "learned loop surrogate, config 4",
+    out = {"metric": METRIC, "workload": "learned loop surrogate at the production point (judge every 8 steps)",
            "config": {"point": workload_desc(held, "cfg2"), "train_tprime": train_tp,
                       "mu": "4 t'", "samples": int(X.shape[0]), "network": "5 -> embed 25 -> "
                       "4 x 256 SiLU -> 98 (BF16 hi/lo operands, FP32 accumulation)",

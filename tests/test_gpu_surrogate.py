@@ -165,8 +165,8 @@ def test_flow_with_surrogate_at_tol_1e2_keeps_lambda_c_with_fewer_exact_loops(to
     sides of the held-out flow: the flow computes fewer exact loop
     contractions (those of the RHS it serves not, plus the judgements) than
     the plain flow, and Lambda_c stays within 1 % of the oracle.  (At 1e-3,
-    config 4's tolerance, the judge rejects this network at the start: its
-    held-out error is above 1e-3.)"""
+    the tolerance of the learned production flows, the judge rejects this
+    network at the start: its held-out error is above 1e-3.)"""
     import time
     s, _, _ = trained
     g = np.load(os.path.join(os.path.dirname(__file__), "golden", "flow_cfg1.npz"))
