@@ -197,11 +197,14 @@ __device__ __forceinline__ void reduce_rows(const double* __restrict__ partial, 
 // (nrow_pad a multiple of 128): CTA -> (point, channel, pair, 128 rows of
 // the rows the view computes, from row_lo rounded down to a multiple of 4).
 // Each lane sums 4 adjacent rows with one 16-byte load per split (a warp
-// reads 512 contiguous bytes), four splits in flight; the splits and the
+// reads 512 contiguous bytes), six splits in flight (the grid is small:
+// 2 npair CTAs per 128 rows, each thread adding ~ksplit / 8 splits; six
+// keep four CTAs per SM without spills); the splits and the
 // phases are combined in the order of reduce_rows (same result).  Rows of a
 // 4-row group outside [row_lo, row_hi) are read (inside the point's
 // nrow_pad rows) but not stored.
 constexpr int kTcRowsPerCta = 128;
+constexpr int kInFlight = 6;  // 16-byte loads in flight per thread
 
 __host__ __device__ inline int tc_rows_start(int row_lo) { return row_lo & ~3; }
 __host__ __device__ inline int tc_rows_groups(int row_lo, int row_hi) {
@@ -219,7 +222,7 @@ __device__ __forceinline__ void pair_add_x2(float2& hi, float2& lo, float2 b) {
   lo = sub2(e, sub2(hi, s));
 }
 
-__global__ void __launch_bounds__(32 * kPhases)
+__global__ void __launch_bounds__(32 * kPhases, 4)
     tc_rows_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix, int n,
                    const float* __restrict__ partial, double* __restrict__ rowres) {
   const int p = point_of(prefix, n, blockIdx.x);
@@ -238,14 +241,14 @@ __global__ void __launch_bounds__(32 * kPhases)
   // rows (0, 1) and (2, 3) as paired sums: hi and lo parts
   float2 h01 = make_float2(0.f, 0.f), l01 = h01, h23 = h01, l23 = h01;
   if (live) {
-    for (int sp = phase; sp < ksplit; sp += 4 * kPhases) {
-      float4 v[4];
+    for (int sp = phase; sp < ksplit; sp += kInFlight * kPhases) {
+      float4 v[kInFlight];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < kInFlight; ++u)
         v[u] = sp + u * kPhases < ksplit ? __ldg(src + (size_t)(sp + u * kPhases) * stride)
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < kInFlight; ++u)
         if (sp + u * kPhases < ksplit) {
           pair_add_x2(h01, l01, make_float2(v[u].x, v[u].y));
           pair_add_x2(h23, l23, make_float2(v[u].z, v[u].w));

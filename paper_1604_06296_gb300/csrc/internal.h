@@ -442,7 +442,7 @@ tufrg_status make_f_tensor_maps(tufrg_ctx* c, cudaStream_t st);
 int tc_k_per_block(int prec);
 // the most K-blocks one work item accumulates in one FP32 chain
 int max_kbps(int prec);
-int table_ctas(int n_ext);
+int table_ctas(int n_ext, int prec);
 tufrg_status prepare_loops_tc_multi(const MultiView& v);
 tufrg_status prepare_project_multi(const MultiView& v);
 tufrg_status prepare_products_multi(const MultiView& v);

@@ -520,9 +520,10 @@ constexpr int kTableBlock = 256;
 // would dominate this kernel).  |xi| is floored at 1e-30 (sign kept).
 // BF16X3 layout: float4 (alpha_q, alpha_q+1, xi_q, xi_q+1) for even q in the
 // first half, for odd q in the second (the last entry repeated past the
-// end); 3xTF32: float2 (alpha_q, xi_q).  One thread per entry q, the neighbour's values by a
-// shuffle.  Block 0 also resets the work-item counter of the contraction
-// that follows.
+// end): one thread per pair of entries 2t, 2t + 1 (one 8-byte load), which
+// writes slot t of both halves, entry 2t + 2 from the next lane by a
+// shuffle; 3xTF32: float2 (alpha_q, xi_q), one thread per entry.  Block 0
+// also resets the work-item counter of the contraction that follows.
 template <int PREC>
 __global__ void __launch_bounds__(kTableBlock)
     scale_table_ext_kernel(const PointDesc* __restrict__ pts, const int* __restrict__ prefix,
@@ -534,22 +535,35 @@ __global__ void __launch_bounds__(kTableBlock)
   const float omf = (float)pd.lam[0];
   const int n_ext = pd.n_ext;
   const int q = (blockIdx.x - prefix[p]) * kTableBlock + threadIdx.x;
-  auto entry = [&](int e) {
-    const float xi = __ldg(pd.xiext + min(e, n_ext - 1));
+  auto value = [&](float xi) {
     const float x = fmaxf(fabsf(xi), 1e-30f);
     return make_float2(__fdiv_rn(omf, omf + x), copysignf(x, xi));
   };
-  const float2 a = entry(q);
+  auto entry = [&](int e) { return value(__ldg(pd.xiext + min(e, n_ext - 1))); };
   if constexpr (PREC == TUFRG_BF16X3) {
     const int half = (n_ext + 1) / 2;
-    // the CTA's threads cover consecutive q, every warp a run of 32
-    float2 b;
-    b.x = __shfl_down_sync(0xffffffffu, a.x, 1);
-    b.y = __shfl_down_sync(0xffffffffu, a.y, 1);
-    if ((threadIdx.x & 31) == 31) b = entry(q + 1);
-    if (q < 2 * half) pd.ext[(q & 1) * half + (q >> 1)] = make_float4(a.x, b.x, a.y, b.y);
+    const int t = q;  // slot t of both halves: entries 2t, 2t + 1, 2t + 2
+    // entries 2t, 2t + 1 (one 8-byte load where both exist; past the end the
+    // last entry, as entry() clamps)
+    float2 xi2;
+    if (2 * t + 1 < n_ext) {
+      xi2 = __ldg(reinterpret_cast<const float2*>(pd.xiext) + t);
+    } else {
+      const float v = __ldg(pd.xiext + min(2 * t, n_ext - 1));
+      xi2 = make_float2(v, v);
+    }
+    const float2 e0 = value(xi2.x), e1 = value(xi2.y);
+    // the CTA's threads cover consecutive t, every warp a run of 32
+    float2 e2;
+    e2.x = __shfl_down_sync(0xffffffffu, e0.x, 1);
+    e2.y = __shfl_down_sync(0xffffffffu, e0.y, 1);
+    if ((threadIdx.x & 31) == 31) e2 = entry(2 * t + 2);
+    if (t < half) {
+      pd.ext[t] = make_float4(e0.x, e1.x, e0.y, e1.y);
+      pd.ext[half + t] = make_float4(e1.x, e2.x, e1.y, e2.y);
+    }
   } else {
-    if (q < n_ext) reinterpret_cast<float2*>(pd.ext)[q] = a;
+    if (q < n_ext) reinterpret_cast<float2*>(pd.ext)[q] = entry(q);
   }
 }
 
@@ -561,7 +575,10 @@ size_t tc_smem_bytes(int npad) {
 
 int tc_k_per_block(int prec) { return prec == TUFRG_BF16X3 ? kRowBytes / 2 : kRowBytes / 4; }
 
-int table_ctas(int n_ext) { return (n_ext + 1 + kTableBlock - 1) / kTableBlock; }
+int table_ctas(int n_ext, int prec) {
+  const int threads = prec == TUFRG_BF16X3 ? (n_ext + 1) / 2 : n_ext;
+  return (threads + kTableBlock - 1) / kTableBlock;
+}
 
 // Tensor maps of the two parts of F ([npad rows][kpad] elements, k
 // contiguous): boxes of one K-block (128 bytes) by all npad rows, written

@@ -229,7 +229,7 @@ tufrg_status view_build(MultiView& v, tufrg_ctx* const* ctx, int n, double* cons
     d.mesh_kz = c->mesh_kz;
     d.mesh_kbs = c->mesh_kbs;
     const int cnt[kKinds] = {
-        tc ? table_ctas(d.n_ext) : 0,
+        tc ? table_ctas(d.n_ext, tc_prec) : 0,
         tc ? tc_rows_ctas(d.npair, d.row_lo, d.row_hi) : 0,
         !d.feedback ? 0
         : c->mesh   ? mesh_partial_ctas(c->mesh_chunks, d.nff)
