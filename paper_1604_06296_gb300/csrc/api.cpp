@@ -304,12 +304,9 @@ tufrg_status tufrg_project_atensor(tufrg_ctx* c, const double* y_dev, double* v_
 
 namespace {
 
-// The right-hand side as a graph on the context's stream: captured for the
-// (y, dy) pair of the call, reused while the pair repeats.
-tufrg_status rhs_graph(tufrg_ctx* c, const double* y_dev, double* dy_dev) {
-  if (c->rhs_graph && c->rhs_y == y_dev && c->rhs_dy == dy_dev) return TUFRG_OK;
-  if (c->rhs_graph) cudaGraphExecDestroy(c->rhs_graph);
-  c->rhs_graph = nullptr;
+// One right-hand side captured on the context's stream and instantiated.
+tufrg_status capture_rhs(tufrg_ctx* c, const double* y_dev, double* dy_dev,
+                         cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   TUFRG_CUDA(cudaStreamBeginCapture(c->fstream, cudaStreamCaptureModeThreadLocal));
   const tufrg_status s = tufrg::rhs_device(c, c->p.precision, y_dev, dy_dev, false, c->fstream);
@@ -319,11 +316,42 @@ tufrg_status rhs_graph(tufrg_ctx* c, const double* y_dev, double* dy_dev) {
     return s;
   }
   TUFRG_CUDA(e);
-  e = cudaGraphInstantiate(&c->rhs_graph, g, 0);
+  e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
+  if (e != cudaSuccess) *exec = nullptr;
   TUFRG_CUDA(e);
-  c->rhs_y = y_dev;
-  c->rhs_dy = dy_dev;
+  return TUFRG_OK;
+}
+
+// The right-hand side as a graph on the context's stream: one per (y, dy)
+// pair, captured at the pair's first call and replayed after; the least
+// recently used of the kRhsGraphs kept makes room for a new pair (an
+// executable graph still in flight is freed when it completes).
+tufrg_status rhs_graph(tufrg_ctx* c, const double* y_dev, double* dy_dev,
+                       cudaGraphExec_t* exec) {
+  tufrg_ctx::RhsGraph* slot = nullptr;
+  for (auto& r : c->rhs_graphs)
+    if (r.exec && r.y == y_dev && r.dy == dy_dev) {
+      slot = &r;
+      break;
+    }
+  if (!slot) {
+    slot = &c->rhs_graphs[0];  // an empty entry, else the least recently used
+    for (auto& r : c->rhs_graphs) {
+      if (!r.exec) {
+        slot = &r;
+        break;
+      }
+      if (r.used < slot->used) slot = &r;
+    }
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    *slot = tufrg_ctx::RhsGraph{};
+    TUFRG_CHECK(capture_rhs(c, y_dev, dy_dev, &slot->exec));
+    slot->y = y_dev;
+    slot->dy = dy_dev;
+  }
+  slot->used = ++c->rhs_calls;
+  *exec = slot->exec;
   return TUFRG_OK;
 }
 
@@ -339,10 +367,11 @@ tufrg_status tufrg_rhs(tufrg_ctx* c, double lambda, const double* y_dev, double*
   }
   TUFRG_CUDA(cudaEventRecord(c->ev_in, st));
   TUFRG_CUDA(cudaStreamWaitEvent(c->fstream, c->ev_in, 0));
-  tufrg_status s = rhs_graph(c, y_dev, dy_dev);
+  cudaGraphExec_t exec = nullptr;
+  tufrg_status s = rhs_graph(c, y_dev, dy_dev, &exec);
   if (s == TUFRG_OK) s = tufrg::launch_set_scalar(c->d_lambda, lambda, c->fstream);
   if (s == TUFRG_OK) {
-    const cudaError_t e = cudaGraphLaunch(c->rhs_graph, c->fstream);
+    const cudaError_t e = cudaGraphLaunch(exec, c->fstream);
     if (e != cudaSuccess) s = tufrg_cuda_fail_at(e, __FILE__, __LINE__);
   }
   if (cudaEventRecord(c->ev_out, c->fstream) != cudaSuccess ||

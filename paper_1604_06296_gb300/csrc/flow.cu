@@ -505,10 +505,10 @@ void fill_progress(tufrg_ctx* c, tufrg_result* r) {
 }  // namespace
 
 void flow_drop_graphs(tufrg_ctx* c) {
-  if (c->rhs_graph) cudaGraphExecDestroy(c->rhs_graph);
-  c->rhs_graph = nullptr;
-  c->rhs_y = nullptr;
-  c->rhs_dy = nullptr;
+  for (auto& r : c->rhs_graphs) {
+    if (r.exec) cudaGraphExecDestroy(r.exec);
+    r = tufrg_ctx::RhsGraph{};
+  }
   if (!c->flow) return;
   for (auto& g : c->flow->attempt) {
     if (g) cudaGraphExecDestroy(g);

@@ -323,11 +323,19 @@ struct tufrg_ctx {
   double sur_tol = 1e-3;           // largest accepted relative error of its loops
   cudaStream_t fstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  // tufrg_rhs: the right-hand side captured as a graph for the last (y, dy)
-  // pair it was called with (launched on fstream after the scale is set)
-  cudaGraphExec_t rhs_graph = nullptr;
-  const double* rhs_y = nullptr;
-  double* rhs_dy = nullptr;
+  // tufrg_rhs: the right-hand side captured as a graph per (y, dy) pair it
+  // was called with, for the last kRhsGraphs pairs (a caller cycling through
+  // a few buffer pairs replays their graphs; launched on fstream after the
+  // scale is set)
+  static constexpr int kRhsGraphs = 4;
+  struct RhsGraph {
+    cudaGraphExec_t exec = nullptr;
+    const double* y = nullptr;
+    double* dy = nullptr;
+    unsigned long long used = 0;  // call count at the last use
+  };
+  RhsGraph rhs_graphs[kRhsGraphs];
+  unsigned long long rhs_calls = 0;
   // the projections of a right-hand side run on their own stream, beside the
   // loop contraction (fork after the stage combination, join before the
   // products; branches of the captured flow graphs)

@@ -119,6 +119,15 @@ def test_rhs_repeated_with_alternating_buffers(torch, precision, bar):
     s.flow(threshold=50.0, rtol=1e-6, atol=1e-8, h0=0.05, max_steps=5)
     got = s.rhs(0.5, yd[1], out=outs[1]).cpu().numpy()
     assert rel(got, orhs.rhs(p, 0.5, ys[1])) < bar
+    # more (y, dy) pairs than the context keeps graphs for (four): every
+    # pair cycled through twice, so each call captures or replays
+    more = [s.empty(3) for _ in range(4)]
+    pairs = [(0, o) for o in more] + [(1, outs[0])]
+    refs = [orhs.rhs(p, 0.4 + 0.1 * k, ys[i]) for k, (i, _) in enumerate(pairs)]
+    for rep in range(2):
+        for k, (i, o) in enumerate(pairs):
+            got = s.rhs(0.4 + 0.1 * k, yd[i], out=o).cpu().numpy()
+            assert rel(got, refs[k]) < bar
     s.close()
 
 
