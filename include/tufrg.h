@@ -243,9 +243,11 @@ tufrg_status tufrg_products(tufrg_ctx* ctx, const double* v_dev, const double* c
  * stream-ordered (not concurrent).  The kernels run on the context's own
  * stream, ordered after the work on cuda_stream and before later work on it;
  * they are captured into a CUDA graph on the first call with a given
- * (y_dev, dy_dev) pair and replayed while the pair repeats (a new pair
- * captures afresh), so the first call is slower and should not fall inside a
- * stream capture of the caller. */
+ * (y_dev, dy_dev) pair and replayed at the pair's later calls; the graphs of
+ * the four most recently used pairs are kept (a caller double-buffering its
+ * states replays both), a fifth pair replaces the least recently used one.
+ * The first call with a pair is therefore slower and should not fall inside
+ * a stream capture of the caller. */
 tufrg_status tufrg_rhs(tufrg_ctx* ctx, double lambda, const double* y_dev, double* dy_dev,
                        void* cuda_stream);
 
